@@ -1,0 +1,570 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each checks a closed form, an
+invariant, a textbook special case, a sampling estimate or a brute force.
+Section / equation numbers refer to arXiv 2510.12901.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2510_12901_gb300 import synthetic as syn
+
+
+def rand_quats(rng, n):
+    q = rng.standard_normal((n, 4)).astype(np.float32)
+    return q
+
+
+# ---------------------------------------------------------------- Sec. 3.1
+def test_activation_rotation_is_proper(O64):
+    rng = np.random.default_rng(5)
+    q = rand_quats(rng, 200) * rng.uniform(0.2, 3.0, (200, 1)).astype(np.float32)
+    ls = rng.normal(-1, 1, (200, 3)).astype(np.float32)
+    R, s = O64.activate(ls, q)
+    eye = np.einsum("nij,nkj->nik", R, R)
+    assert np.abs(eye - np.eye(3)).max() < 1e-12
+    assert np.abs(np.linalg.det(R) - 1).max() < 1e-12
+    assert np.allclose(s, np.exp(ls.astype(np.float64)), rtol=1e-15)
+    # rotation about z by 90 degrees (textbook)
+    c = math.cos(math.pi / 4)
+    R1, _ = O64.activate(np.zeros((1, 3), np.float32), np.array([[c, 0, 0, c]], np.float32))
+    assert np.allclose(R1[0], [[0, -1, 0], [1, 0, 0], [0, 0, 1]], atol=1e-7)
+
+
+# ------------------------------------------------- real spherical harmonics
+def _sphere_quadrature(nt=24, nphi=48):
+    x, w = np.polynomial.legendre.leggauss(nt)           # cos(theta) nodes
+    phi = (np.arange(nphi) + 0.5) * 2 * np.pi / nphi
+    ct, ph = np.meshgrid(x, phi, indexing="ij")
+    st = np.sqrt(1 - ct ** 2)
+    dirs = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1).reshape(-1, 3)
+    wts = (w[:, None] * np.full(nphi, 2 * np.pi / nphi)[None, :]).reshape(-1)
+    return dirs, wts
+
+
+def test_sh_orthonormal_on_sphere(O64):
+    dirs, wts = _sphere_quadrature()
+    Y = np.stack([O64.sh_basis(d) for d in dirs])
+    G = (Y * wts[:, None]).T @ Y
+    assert np.abs(G - np.eye(16)).max() < 1e-12
+    assert abs(Y[0, 0] - 0.5 / math.sqrt(math.pi)) < 1e-15   # Y_0^0 = 1/(2 sqrt(pi))
+
+
+def test_sh_homogeneous_harmonic_and_gradient(O64):
+    rng = np.random.default_rng(1)
+    degree = np.array([0] + [1] * 3 + [2] * 5 + [3] * 7)
+    h = 1e-3
+    for _ in range(20):
+        p = rng.normal(size=3)
+        Y = O64.sh_basis(p)
+        # homogeneous of degree l
+        assert np.allclose(O64.sh_basis(2.0 * p), Y * 2.0 ** degree, rtol=1e-12, atol=1e-12)
+        # Laplacian zero (central second differences are exact on cubics)
+        lap = np.zeros(16)
+        grad = np.zeros((16, 3))
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            lap += (O64.sh_basis(p + e) - 2 * Y + O64.sh_basis(p - e)) / h ** 2
+            grad[:, k] = (O64.sh_basis(p + e) - O64.sh_basis(p - e)) / (2 * h)
+        assert np.abs(lap).max() < 1e-6
+        assert np.abs(grad - O64.sh_basis_grad(p)).max() < 1e-5
+
+
+def test_sh_degree1_proportional_to_coordinates(O64):
+    # Y_1^m = sqrt(3/(4 pi)) * (-y, z, -x)
+    d = np.array([0.36, -0.48, 0.8])
+    Y = O64.sh_basis(d)
+    k = math.sqrt(3 / (4 * math.pi))
+    assert np.allclose(Y[1:4], k * np.array([-d[1], d[2], -d[0]]), rtol=1e-14)
+
+
+# ---------------------------------------------------------- camera models
+def _cam(model, k=(0, 0, 0, 0), w=64, h=48, f=40.0):
+    c = syn.tiny_camera()
+    c.model, c.width, c.height = model, w, h
+    c.fx = c.fy = f
+    c.cx, c.cy = w / 2, h / 2
+    c.k = np.array(k, np.float32)
+    return c
+
+
+def test_fisheye_k0_is_equidistant(O64):
+    cam = _cam(1)
+    # camera looks +y (world), x right; point at angle theta off-axis in x
+    for th in [0.1, 0.5, 1.2]:
+        xw = np.array([math.sin(th) * 5, -10 + math.cos(th) * 5, 0.0])
+        ok, uv = O64.camera_project(cam, xw)
+        assert ok
+        assert abs((uv[0] - cam.cx) - cam.fx * th) < 1e-9
+    assert abs(O64.fisheye_theta_max(np.zeros(4)) - math.pi / 2) < 1e-12
+
+
+def test_fisheye_theta_max_first_critical_point(O64):
+    # d theta_d / d theta = 1 + 3 k1 theta^2 = 0  at theta = sqrt(-1/(3 k1))
+    k1 = np.float32(-0.2)
+    tm = O64.fisheye_theta_max(np.array([k1, 0, 0, 0], np.float32))
+    assert abs(tm - math.sqrt(-1 / (3 * float(k1)))) < 1e-9
+
+
+@pytest.mark.parametrize("model,k", [(0, (0, 0, 0, 0)), (1, (0.03, -0.02, 0.01, -0.004)),
+                                     (1, (-0.05, 0.05, -0.05, 0.05))])
+def test_camera_ray_round_trip(O64, model, k):
+    cam = _cam(model, k)
+    rng = np.random.default_rng(3)
+    for _ in range(30):
+        px, py = int(rng.integers(0, cam.width)), int(rng.integers(0, cam.height))
+        ok, o, d = O64.camera_ray(cam, px, py)
+        if not ok:
+            continue
+        assert abs(np.linalg.norm(d) - 1) < 1e-12
+        ok2, uv = O64.camera_project(cam, o + 7.0 * d)
+        assert ok2
+        assert abs(uv[0] - (px + 0.5)) < 1e-8 and abs(uv[1] - (py + 0.5)) < 1e-8
+
+
+# ------------------------------------------------------ unscented transform
+@pytest.mark.parametrize("a,b,k", [(1.0, 2.0, 0.0), (0.5, 2.0, 1.0), (1.3, 0.0, 0.5)])
+def test_ut_exact_for_affine_maps(O64, a, b, k):
+    rng = np.random.default_rng(7)
+    A = rng.normal(size=(2, 3))
+    c = rng.normal(size=2)
+    mu = rng.normal(size=3)
+    R, s = O64.activate(rng.normal(-1, .3, (1, 3)).astype(np.float32),
+                        rng.normal(size=(1, 4)).astype(np.float32))
+    R, s = R[0], s[0]
+    ok, m, cov = O64.unscented(mu, R, s, lambda x, i: (True, A @ x + c),
+                               opts=O64.opts(ut_alpha=a, ut_beta=b, ut_kappa=k))
+    Sig = R @ np.diag(s ** 2) @ R.T
+    C = A @ Sig @ A.T
+    assert ok
+    assert np.allclose(m, A @ mu + c, atol=1e-12)
+    assert np.allclose(cov, [C[0, 0], C[0, 1], C[1, 1]], atol=1e-12)
+
+
+def test_ut_exact_for_planar_gaussian_facing_pinhole(O64):
+    """All sigma points at one depth: perspective is affine there, so the UT
+    returns the projected mean and (f/z)^2 times the in-plane covariance."""
+    cam = _cam(0)
+    sc = syn.tiny_scene(n=1)
+    # camera at (0,-10,0) looking +y; place the Gaussian 12 m ahead, off-axis
+    sc.means[0] = [1.5, 2.0, -0.7]
+    # local axes: x, z in the image plane, local y (scale ~0) along the view axis
+    sc.quats[0] = [1, 0, 0, 0]
+    sc.log_scales[0] = [math.log(0.4), -80.0, math.log(0.25)]
+    sc.opacity[0] = 0.9
+    P, _ = O64.project_camera(sc, cam)
+    z0 = 12.0
+    u = cam.fx * 1.5 / z0 + cam.cx
+    v = cam.fy * 0.7 / z0 + cam.cy     # camera y (down) = -world z
+    assert P["valid"][0] == 1
+    assert np.allclose(P["mean2d"][0], [u, v], atol=1e-10)
+    f2 = (cam.fx / z0) ** 2
+    assert np.allclose(P["cov2d"][0], [f2 * 0.4 ** 2, 0.0, f2 * 0.25 ** 2], atol=1e-10)
+
+
+def _jacobian(O, cam, xw):
+    h = 1e-6
+    J = np.zeros((2, 3))
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        J[:, k] = (np.array(O.camera_project(cam, xw + e)[1]) -
+                   np.array(O.camera_project(cam, xw - e)[1])) / (2 * h)
+    return J
+
+
+def test_ut_converges_to_linearisation(O64):
+    """UT covariance -> J Sigma J^T (EWA) as the Gaussian shrinks, with a
+    relative error that falls like s^2 (log-log slope 2)."""
+    cam = _cam(0)
+    mu = np.array([2.0, -4.0, 1.0])
+    R, _ = O64.activate(np.zeros((1, 3), np.float32), np.array([[.9, .2, .3, .1]], np.float32))
+    J = _jacobian(O64, cam, mu)
+    errs = []
+    for sc_ in [0.4, 0.2, 0.1, 0.05]:
+        s = np.array([sc_, 0.7 * sc_, 0.5 * sc_])
+        ok, m, cov = O64.unscented(mu, R[0], s, lambda x, i: O64.camera_project(cam, x))
+        Sig = R[0] @ np.diag(s ** 2) @ R[0].T
+        E = J @ Sig @ J.T
+        C = np.array([[cov[0], cov[1]], [cov[1], cov[2]]])
+        errs.append(np.linalg.norm(C - E) / np.linalg.norm(E))
+    slopes = np.diff(np.log(errs)) / np.diff(np.log([0.4, 0.2, 0.1, 0.05]))
+    assert np.all(np.abs(slopes - 2.0) < 0.25), slopes
+
+
+def test_ut_matches_monte_carlo_moments_lidar(O64):
+    """App. F / Tab. 6: 7 sigma points give moments close to Monte Carlo.
+    Spherical map of Eq. 3 sampled with 10^6 points in double."""
+    rng = np.random.default_rng(11)
+    mu = np.array([8.0, 3.0, 1.0])
+    R, s = O64.activate(np.log(np.array([[0.6, 0.3, 0.2]], np.float32)),
+                        np.array([[0.8, 0.1, -0.4, 0.3]], np.float32))
+    R, s = R[0], s[0]
+
+    def sph(x, i=0):
+        r = np.linalg.norm(x)
+        return True, np.array([math.degrees(math.atan2(x[1], x[0])),
+                               math.degrees(math.asin(x[2] / r))])
+
+    ok, m, cov = O64.unscented(mu, R, s, sph, wrap_first=True)
+    X = mu + (rng.standard_normal((1_000_000, 3)) * s) @ R.T
+    az = np.degrees(np.arctan2(X[:, 1], X[:, 0]))
+    el = np.degrees(np.arcsin(X[:, 2] / np.linalg.norm(X, axis=1)))
+    Y = np.stack([az, el], 1)
+    mc_m = Y.mean(0)
+    mc_c = np.cov(Y.T)
+    assert np.abs(m - mc_m).max() < 0.02 * np.sqrt(np.diag(mc_c)).max()
+    C = np.array([[cov[0], cov[1]], [cov[1], cov[2]]])
+    assert np.linalg.norm(C - mc_c) / np.linalg.norm(mc_c) < 0.03
+
+
+# ------------------------------------------------------------ LiDAR set-up
+def test_elevation_tiling_uniform_table_gives_equal_tiles(O64):
+    elev = np.linspace(-10, 10, 128).astype(np.float32)
+    T, nth = O64.elevation_tiling(elev, 2048, 16, 32)
+    tiles = np.array([O64.elev_tile(T, 16, e) for e in elev])
+    counts = np.bincount(tiles, minlength=16)
+    assert counts.min() >= 7 and counts.max() <= 9
+    assert T[0] == np.float32(-10) and T[-1] == np.float32(10)
+    assert nth == -(-counts.max() * 2048 // 32)
+
+
+@pytest.mark.parametrize("nphi,M", [(8, 32), (16, 32), (16, 64), (32, 128), (64, 256)])
+def test_elevation_tiling_bounds(O64, nphi, M):
+    """Rays per tile <= M whenever N_theta divides the column count; the tile
+    beam counts differ by no more than the beams of one histogram bin
+    (Fig. 3 caption); boundaries are non-decreasing and span the table."""
+    elev = syn.beam_table_128()
+    ncols = 2048
+    T, nth = O64.elevation_tiling(elev, ncols, nphi, M)
+    assert np.all(np.diff(T) >= 0)
+    assert T[0] == elev.min() and T[-1] >= elev.max()
+    tiles = np.array([O64.elev_tile(T, nphi, e) for e in elev])
+    counts = np.bincount(tiles, minlength=nphi)
+    hist = np.histogram(elev, bins=400, range=(float(elev.min()), float(elev.max())))[0]
+    assert counts.max() * ncols <= nth * M
+    assert counts.max() - counts[counts > 0].min() <= 2 * hist.max()
+    cols_per_tile = np.bincount((np.arange(ncols) * nth) // ncols)
+    assert cols_per_tile.max() * counts.max() <= M + counts.max()
+
+
+def test_paper_best_setting_gives_32_ray_tiles(O64):
+    L = syn.street_lidar()
+    T, nth = O64.elevation_tiling(L.elevations_deg, L.n_cols, 16, 32)
+    tiles = np.array([O64.elev_tile(T, 16, e) for e in L.elevations_deg])
+    counts = np.bincount(tiles, minlength=16)
+    assert counts.max() == 8 and nth == 512     # 8 beams x 4 columns = 32 rays
+
+
+def test_sat_counts_match_brute_force(O64):
+    L = syn.street_lidar(n_cols=256)
+    S = O64.lidar_setup(L)
+    sat = S["sat"]
+    A, E = sat.shape[0] - 1, sat.shape[1] - 1
+    cell = np.diff(np.diff(sat, axis=0), axis=1)       # per-cell counts
+    assert set(np.unique(cell)) <= {0, 1}
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        x0, x1 = sorted(rng.integers(0, A, 2))
+        y0, y1 = sorted(rng.integers(0, E, 2))
+        assert O64.sat_count_wrap(L, int(x0), int(x1), int(y0), int(y1)) == \
+            cell[x0:x1 + 1, y0:y1 + 1].sum()
+    # seam: [A-3, A+2] wraps to [A-3, A-1] + [0, 2]
+    assert O64.sat_count_wrap(L, A - 3, A + 2, 0, E - 1) == \
+        cell[A - 3:, :].sum() + cell[:3, :].sum()
+    # every ray's cell is occupied: 256 columns over 1600 cells, all beams
+    assert cell.sum() == 256 * len(np.unique([O64.lib.or_elev_cell(
+        S["T"].ctypes.data_as(__import__("ctypes").c_void_p), 16, 8,
+        O64.real(e)) for e in L.elevations_deg]))
+
+
+def test_lidar_axis_point_maps_to_origin(O64):
+    L = syn.street_lidar(static=True)
+    L.col_c2w[:] = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32)
+    sc = syn.tiny_scene(n=2)
+    sc.means[0] = [10, 0, 0]
+    sc.means[1] = [5 * math.cos(0.7), 5 * math.sin(0.7), 5 * math.tan(math.radians(3.0))]
+    sc.log_scales[:] = -9
+    sc.opacity[:] = 0.9
+    P, _ = O64.project_lidar(sc, L, O64.opts(cull=0))
+    assert np.allclose(P["mean2d"][0], [0, 0], atol=1e-6)
+    assert abs(P["mean2d"][1][0] - math.degrees(0.7)) < 1e-6
+    assert abs(P["mean2d"][1][1] - 3.0) < 1e-6
+    assert abs(P["depth"][0] - 10) < 1e-12
+
+
+# ------------------------------------------------------------ compositing
+def _one_gaussian_scene(mu, ls, sigma, rgb, q=(1, 0, 0, 0)):
+    sc = syn.tiny_scene(n=1)
+    sc.means[0] = mu
+    sc.log_scales[0] = ls
+    sc.quats[0] = q
+    sc.opacity[0] = sigma
+    sc.features[0] = rgb
+    return sc
+
+
+def test_single_gaussian_on_axis_closed_form(O64):
+    cam = syn.tiny_camera()
+    ok, o, d = O64.camera_ray(cam, 40, 21)
+    mu = (o + 9.0 * d).astype(np.float32)
+    for sigma in [0.3, 0.9, 1.0]:
+        sc = _one_gaussian_scene(mu, [-1, -1.2, -0.8], sigma, [0.2, 0.5, 0.9])
+        r = O64.render_camera(sc, cam, rays=[21 * 64 + 40])[0]
+        a = min(float(np.float32(0.99)), float(np.float32(sigma)))
+        assert np.allclose(r["out"], a * np.array([0.2, 0.5, 0.9], np.float32), atol=1e-9)
+        assert abs(r["alpha"] - a) < 1e-9
+        assert abs(r["depth"] - np.linalg.norm(mu - o)) < 1e-5
+
+
+def test_two_gaussians_over_operator(O64):
+    cam = syn.tiny_camera()
+    ok, o, d = O64.camera_ray(cam, 30, 30)
+    sc = syn.tiny_scene(n=2)
+    sc.means[0] = o + 6 * d
+    sc.means[1] = o + 12 * d
+    sc.log_scales[:] = -1.0
+    sc.quats[:] = [1, 0, 0, 0]
+    sc.opacity[:] = [0.6, 0.7]
+    sc.features[:] = [[1, 0, 0], [0, 0, 1]]
+    r = O64.render_camera(sc, cam, rays=[30 * 64 + 30])[0]
+    a1, a2 = float(np.float32(0.6)), float(np.float32(0.7))
+    assert np.allclose(r["out"], [a1, 0, (1 - a1) * a2], atol=1e-6)
+    assert abs(r["alpha"] - (a1 + (1 - a1) * a2)) < 1e-6
+
+
+def test_flat_opaque_disk_returns_ray_plane_distance(O64):
+    """A disk-like Gaussian (scales a, a, 1e-5; opacity 1): tau_max equals
+    the ray-plane distance (mu - o).n / (d.n) for every ray that hits it."""
+    cam = syn.tiny_camera()
+    n = np.array([0.3, -0.9, 0.2])
+    n /= np.linalg.norm(n)
+    # rotation whose third column is n
+    z = n
+    x = np.cross([0, 0, 1.0], z)
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    Rm = np.stack([x, y, z], 1)
+    w = math.sqrt(1 + np.trace(Rm)) / 2
+    q = [w, (Rm[2, 1] - Rm[1, 2]) / (4 * w), (Rm[0, 2] - Rm[2, 0]) / (4 * w),
+         (Rm[1, 0] - Rm[0, 1]) / (4 * w)]
+    mu = np.array([0.5, 4.0, 0.3], np.float32)
+    sc = _one_gaussian_scene(mu, [math.log(3.0), math.log(3.0), math.log(1e-5)], 1.0,
+                             [1, 1, 1], q)
+    r = O64.render_camera(sc, cam)
+    hit = r["n_contrib"] > 0
+    assert hit.sum() > 500
+    idx = np.nonzero(hit)[0]
+    for i in idx[::17]:
+        ok, o, d = O64.camera_ray(cam, i % 64, i // 64)
+        nn = Rm[:, 2]
+        t_plane = np.dot(mu.astype(np.float64) - o, nn) / np.dot(d, nn)
+        assert abs(r["depth"][i] - t_plane) < 1e-5 * t_plane
+
+
+@pytest.mark.parametrize("bits", [64, 32])
+def test_tiny_config_invariants(bits):
+    from oracle import Oracle
+    O = Oracle(bits)
+    sc, cam = syn.tiny_scene(), syn.tiny_camera()
+    r = O.render_camera(sc, cam)
+    rb = O.render_camera(sc, cam, bruteforce=True)
+    # tiled == brute force, bit for bit, in the same precision
+    for k in ("out", "alpha", "depth", "t_final", "n_contrib"):
+        assert np.array_equal(r[k], rb[k])
+    # omega = sum alpha_i T_i = 1 - T_final (Eq. 1 telescopes)
+    tol = 1e-12 if bits == 64 else 2e-6
+    assert np.abs(r["alpha"] - (1 - r["t_final"])).max() < tol
+    assert np.all(r["t_final"] > 0) and np.all(r["t_final"] <= 1)
+    assert np.all(r["out"] >= 0) and r["n_contrib"].sum() > 0
+
+
+def test_bin_sort_matches_lexsort(O64):
+    sc, cam = syn.tiny_scene(), syn.tiny_camera()
+    P, (ntx, nty) = O64.project_camera(sc, cam)
+    ids, tiles, ranges = O64.bin_sort(P, ntx, nty, False)
+    T, D, I = [], [], []
+    for g in np.nonzero(P["valid"])[0]:
+        x0, x1, y0, y1 = P["tiles"][g]
+        for ty in range(y0, y1 + 1):
+            for tx in range(x0, x1 + 1):
+                T.append(ty * ntx + tx)
+                D.append(P["depth"][g])
+                I.append(g)
+    order = np.lexsort((I, D, T))
+    assert np.array_equal(ids, np.array(I)[order])
+    assert np.array_equal(tiles, np.array(T)[order])
+    for t in range(ntx * nty):
+        sel = np.nonzero(tiles == t)[0]
+        if len(sel):
+            assert ranges[t, 0] == sel[0] and ranges[t, 1] == sel[-1] + 1
+
+
+def _lidar_toy(n=512, seed=0):
+    L = syn.street_lidar(n_cols=256)
+    sc = syn.street_scene(n, seed=seed, kind="lidar", length=60.0)
+    return sc, L
+
+
+@pytest.mark.parametrize("bits", [64, 32])
+def test_lidar_tiled_equals_bruteforce_and_culling_invariance(bits):
+    from oracle import Oracle
+    O = Oracle(bits)
+    sc, L = _lidar_toy(1500)
+    r = O.render_lidar(sc, L)
+    rb = O.render_lidar(sc, L, bruteforce=True)
+    rn = O.render_lidar(sc, L, O.opts(cull=0))
+    for k in ("out", "alpha", "depth", "n_contrib"):
+        assert np.array_equal(r[k], rb[k])
+        assert np.array_equal(r[k], rn[k])
+    assert r["n_contrib"].sum() > 1000
+    # culling removed some Gaussians (it does work) without changing outputs
+    P1, _ = O.project_lidar(sc, L)
+    P0, _ = O.project_lidar(sc, L, O.opts(cull=0))
+    assert P1["valid"].sum() < P0["valid"].sum()
+    # rays that hit nothing: drop probability 1/2
+    rng_, inten, drop = O.lidar_decode(r)
+    miss = r["n_contrib"] == 0
+    assert miss.any() and np.allclose(drop[miss], 0.5)
+
+
+def test_lidar_tiling_invariance(O64):
+    """Sec. 4.3: the (M, N_phi) choice changes speed, not the result."""
+    sc, L0 = _lidar_toy(800, seed=3)
+    ref = O64.render_lidar(sc, L0)
+    for M in (32, 64, 128, 256):
+        for nphi in (8, 16, 32, 64):
+            L = syn.Lidar(L0.elevations_deg, L0.n_cols, L0.az0_deg, L0.col_c2w, M, nphi)
+            r = O64.render_lidar(sc, L)
+            for k in ("out", "alpha", "depth"):
+                assert np.array_equal(r[k], ref[k]), (M, nphi, k)
+
+
+def test_lidar_static_pose_iterations_irrelevant(O64):
+    sc, _ = _lidar_toy(600, seed=4)
+    L = syn.street_lidar(n_cols=256, static=True)
+    a = O64.render_lidar(sc, L, O64.opts(pose_iters=0))
+    b = O64.render_lidar(sc, L, O64.opts(pose_iters=2))
+    assert np.array_equal(a["out"], b["out"]) and np.array_equal(a["depth"], b["depth"])
+
+
+# ---------------------------------------------------------------- backward
+def _fd_setup():
+    """16 Gaussians in front of a 12x10 camera, one tile, cutoffs off."""
+    rng = np.random.default_rng(9)
+    n = 16
+    cam = syn.tiny_camera()
+    cam.width, cam.height, cam.cx, cam.cy = 12, 10, 6.0, 5.0
+    cam.fx = cam.fy = 8.0
+    sc = syn.tiny_scene(n=n)
+    sc.means[:] = np.stack([rng.uniform(-3, 3, n), rng.uniform(-4, 2, n),
+                            rng.uniform(-2.5, 2.5, n)], 1)
+    sc.log_scales[:] = rng.normal(-0.3, 0.3, (n, 3))
+    sc.opacity[:] = rng.uniform(0.2, 0.8, n)
+    deg = 3
+    sc.features = rng.normal(0, 0.3, (n, 3 * (deg + 1) ** 2)).astype(np.float32)
+    sc.features[:, :3] += 1.0
+    sc.feature_kind, sc.sh_degree = syn.FEATURES_SH, deg
+    return sc, cam
+
+
+def _loss_cam(O, sc, cam, opts, gr, ga, gd):
+    r = O.render_camera(sc, cam, opts)
+    return (r["out"] * gr).sum() + (r["alpha"] * ga).sum() + (r["depth"] * gd).sum()
+
+
+def test_backward_camera_matches_central_differences(O64):
+    sc, cam = _fd_setup()
+    opts = O64.opts(cutoffs=0, predicate=0, tile=64)
+    nr = cam.width * cam.height
+    rng = np.random.default_rng(1)
+    gr = rng.normal(size=(nr, 3)).astype(np.float32)
+    ga = rng.normal(size=nr).astype(np.float32)
+    gd = (0.05 * rng.normal(size=nr)).astype(np.float32)
+    G = O64.backward_camera(sc, cam, gr, ga, gd, opts)
+    # perturb float32 parameters in double through a float64 copy of the scene
+    checked = 0
+    for name, arr in (("means", sc.means), ("log_scales", sc.log_scales),
+                      ("quats", sc.quats), ("opacity", sc.opacity),
+                      ("features", sc.features)):
+        flat = arr.reshape(-1)
+        gflat = G[name].reshape(-1)
+        for i in range(0, flat.size, max(1, flat.size // 24)):
+            x0 = float(flat[i])
+            h = 2.0 ** -14
+            flat[i] = np.float32(x0 + h)
+            hp = float(flat[i]) - x0
+            lp = _loss_cam(O64, sc, cam, opts, gr, ga, gd)
+            flat[i] = np.float32(x0 - h)
+            hm = x0 - float(flat[i])
+            lm = _loss_cam(O64, sc, cam, opts, gr, ga, gd)
+            flat[i] = np.float32(x0)
+            fd = (lp - lm) / (hp + hm)
+            scale = max(1.0, np.abs(gflat).max())
+            assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])
+            checked += 1
+    assert checked > 100
+
+
+def test_backward_single_gaussian_opacity_closed_form(O64):
+    """omega = sigma rho for one Gaussian: d omega / d sigma = rho."""
+    cam = syn.tiny_camera()
+    ok, o, d = O64.camera_ray(cam, 20, 20)
+    mu = (o + 8 * d + np.array([0.05, 0, 0.03])).astype(np.float32)
+    sc = _one_gaussian_scene(mu, [-1.0, -1.0, -1.0], 0.5, [0.3, 0.3, 0.3])
+    nr = 64 * 64
+    ga = np.zeros(nr, np.float32)
+    ga[20 * 64 + 20] = 1.0
+    G = O64.backward_camera(sc, cam, np.zeros((nr, 3), np.float32), ga,
+                            np.zeros(nr, np.float32))
+    r = O64.render_camera(sc, cam, rays=[20 * 64 + 20])[0]
+    assert abs(G["opacity"][0] - r["alpha"] / 0.5) < 1e-12
+
+
+def test_backward_lidar_matches_central_differences(O64):
+    L = syn.street_lidar(n_cols=64, n_beams=64)
+    L.n_elev_tiles = 1
+    L.max_rays_per_tile = 64 * 64
+    rng = np.random.default_rng(4)
+    n = 12
+    sc = syn.street_scene(n, seed=5, kind="lidar", length=20.0)
+    # compact Gaussians 8-14 m from the sensor: where a ray is perpendicular
+    # to a Gaussian (tau_max ~ 0, the one remaining discontinuity with the
+    # cutoffs off) its response is ~exp(-200), so the loss is smooth
+    ang = rng.uniform(-np.pi, np.pi, n)
+    rad = rng.uniform(8, 14, n)
+    sc.means[:] = np.stack([30 + rad * np.cos(ang), rad * np.sin(ang),
+                            rng.uniform(0, 2.5, n)], 1)
+    sc.log_scales[:] = rng.normal(-1.0, 0.2, (n, 3))
+    sc.opacity[:] = rng.uniform(0.2, 0.8, n)
+    opts = O64.opts(cutoffs=0, predicate=0, cull=0)
+    nr = L.n_beams * L.n_cols
+    g = [rng.normal(size=nr).astype(np.float32) * s for s in (0.02, 1.0, 1.0, 1.0)]
+    G = O64.backward_lidar(sc, L, *g, opts=opts)
+
+    def loss():
+        r = O64.render_lidar(sc, L, opts)
+        rg, it, dr = O64.lidar_decode(r)
+        return (rg * g[0]).sum() + (it * g[1]).sum() + (dr * g[2]).sum() + (r["alpha"] * g[3]).sum()
+
+    for name, arr in (("means", sc.means), ("log_scales", sc.log_scales),
+                      ("quats", sc.quats), ("opacity", sc.opacity),
+                      ("features", sc.features)):
+        flat = arr.reshape(-1)
+        gflat = G[name].reshape(-1)
+        for i in range(0, flat.size, max(1, flat.size // 10)):
+            x0 = float(flat[i])
+            h = 2.0 ** -14
+            flat[i] = np.float32(x0 + h)
+            hp = float(flat[i]) - x0
+            lp = loss()
+            flat[i] = np.float32(x0 - h)
+            hm = x0 - float(flat[i])
+            lm = loss()
+            flat[i] = np.float32(x0)
+            fd = (lp - lm) / (hp + hm)
+            scale = max(1.0, np.abs(gflat).max())
+            assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])

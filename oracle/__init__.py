@@ -82,7 +82,7 @@ def _structs(real):
         _fields_ = [("out", real * 3), ("alpha", real), ("depth", real), ("zsum", real),
                     ("t_final", real), ("n_visited", C.c_int), ("n_evaluated", C.c_int),
                     ("n_contrib", C.c_int), ("m_rect", real), ("m_alpha", real),
-                    ("m_tmin", real), ("m_tau", real)]
+                    ("m_tmin", real), ("m_tau", real), ("m_order", real)]
 
     return Scene, Camera, Lidar, Opts, Setup, Proj, Ray
 

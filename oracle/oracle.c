@@ -561,7 +561,9 @@ void or_project_camera(const or_scene *sc, const or_camera *cam,
         }
         real sigma = RL(sc->opacity[g]), amin = RL(o->alpha_min);
         real dx = mu[0] - RL(cam->c2w[3]), dy = mu[1] - RL(cam->c2w[7]), dz = mu[2] - RL(cam->c2w[11]);
-        p->depth = sqrt(dx * dx + dy * dy + dz * dz);
+        /* sort key: 3DGS-style keys carry float32 depth bits (Sec. 3.2 "as in
+         * 3DGS"), so the key is the distance rounded to float */
+        p->depth = RL((float)sqrt(dx * dx + dy * dy + dz * dz));
         p->vmargin = fabs(sigma - amin) / amin;
         if (!(sigma >= amin)) continue;
         cam_ctx ctx = {cam, S->theta_max, o, RL(1e30)};
@@ -656,7 +658,7 @@ void or_project_lidar(const or_scene *sc, const or_lidar *L,
         {
             real y[2];
             lidar_point_map(&ctx, mu, 0, y);
-            p->depth = ctx.range0;
+            p->depth = RL((float)ctx.range0);   /* float32 key, as for cameras */
             p->pose_col = ctx.col0;
         }
         p->vmargin = fabs(sigma - amin) / amin;
@@ -869,7 +871,8 @@ static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR
                           int wrap_az, or_ray *out, contrib *rec, int64_t *nrec)
 {
     memset(out, 0, sizeof(*out));
-    out->m_rect = out->m_alpha = out->m_tmin = out->m_tau = RL(1e30);
+    out->m_rect = out->m_alpha = out->m_tmin = out->m_tau = out->m_order = RL(1e30);
+    real prev_key = RL(-1);
     real T = RL(1), acc[3] = {0, 0, 0}, Z = 0, W = 0;
     real amin = RL(o->alpha_min), amax = RL(o->alpha_max), tmin = RL(o->t_min);
     int64_t nr = 0;
@@ -878,6 +881,11 @@ static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR
         out->n_visited++;
         if (o->predicate && !inside_rect(&P[g], rx, ry, wrap_az, &out->m_rect)) continue;
         out->n_evaluated++;
+        if (prev_key >= RL(0)) {   /* relative gap between consecutive sort keys */
+            real gap = fabs(P[g].depth - prev_key) / P[g].depth;
+            if (gap < out->m_order) out->m_order = gap;
+        }
+        prev_key = P[g].depth;
         const gauss_rt *G = &GR[g];
         real a, b, c;
         response_quadratic(G, org, dir, &a, &b, &c);

@@ -86,7 +86,7 @@ typedef struct {
     real rect[4];         /* per-ray test box: x_lo, x_hi, y_lo, y_hi */
     int tiles[4];         /* tile range x0, x1 (may exceed N for LiDAR wrap), y0, y1 */
     int count;            /* number of tiles it is binned into */
-    real depth;           /* sort key: distance |mu - o| */
+    real depth;           /* sort key: distance |mu - o| rounded to float */
     int pose_col;         /* LiDAR: column whose pose the centre point used */
     real vmargin;         /* min relative margin of the validity tests (near, theta, opacity) */
 } or_proj;
@@ -105,6 +105,7 @@ typedef struct {
     real m_alpha;         /* min |alpha - alpha_min| / alpha_min over evaluated */
     real m_tmin;          /* min |T' - t_min| / t_min over composited + stopping */
     real m_tau;           /* min |tau| over evaluated */
+    real m_order;         /* min relative gap of consecutive sort keys over evaluated */
 } or_ray;
 
 #ifdef __cplusplus

@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the forward render (rendered Mrays/s).
+
+Workload (one step): the synthetic street camera scene -- 1M Gaussians with
+degree-3 SH colour -- rendered into one 1920x1280 OpenCV-fisheye view and one
+1920x1080 pinhole view (RGB, alpha, depth): 4,531,200 rays per step.  The
+scene is resident in HBM before timing starts; each step re-runs projection,
+depth sort, binning, tile sort and compositing for both views.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  N > 1 runs one process per GPU (torchrun), each
+rendering the same workload (replicas, weak scaling): value = all ranks'
+rays / max-over-ranks time.  --impl reference times the CPU oracle (the
+plain C implementation written from the paper) on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rendered Mrays/s per GB300 (camera px + LiDAR rays); p50/p99 latency in serving loop"
+WORKLOAD = ("street camera scene: 1M Gaussians (degree-3 SH), one 1920x1280 OpenCV-fisheye "
+            "view + one 1920x1080 pinhole view per step, forward RGB+alpha+depth")
+N_GAUSS = 1_000_000
+# algorithmic FP32 work per evaluated (ray, Gaussian) pair: closest approach
+# of the ray to the Gaussian in its own frame (M d: 15, moment cross product
+# 9, two squared norms 10, dot product 5, two divisions 2), response and
+# alpha (exp, product, clamp: 3), compositing (transmittance 2, weight 1,
+# colour 6, depth 2, opacity 1): 56 flops
+FLOP_PER_PAIR = 56
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
+        load = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": float(np.median(load)) if load else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2510_12901_gb300 import _build
+    _build.build()
+    from paper_2510_12901_gb300 import simgut as sg
+    from paper_2510_12901_gb300 import synthetic as syn
+
+    sc = syn.street_scene(N_GAUSS, seed=0, kind="camera")
+    fish, pin = syn.street_cameras()
+    S = sg.Scene(sc)
+    cams = [(sg.Camera(fish), fish), (sg.Camera(pin), pin)]
+    rays_per_step = sum(c.width * c.height for _, c in cams)
+    outs = []
+    for _, c in cams:
+        outs.append([torch.empty((c.height, c.width, 3), device="cuda"),
+                     torch.empty((c.height, c.width), device="cuda"),
+                     torch.empty((c.height, c.width), device="cuda")])
+    opts = sg.sg_default_opts()
+    # two frame sets, alternated, so that the stage events of step i can be
+    # read once step i+1 has passed its own mid-render synchronisation
+    frames = [[sg.Frame() for _ in cams] for _ in range(2)]
+    for fs in frames:
+        for f in fs:
+            sg.sg_frame_set_timing(f.handle, 1)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def step(i):
+        fs = frames[i % 2]
+        for (ch, c), o, f in zip(cams, outs, fs):
+            sg.sg_render_camera(S.handle, ch.handle, c.c2w, opts, f.handle, o[0].data_ptr(),
+                                o[1].data_ptr(), o[2].data_ptr(), sp)
+
+    stage_ms = []
+
+    def harvest(i):
+        for f in frames[i % 2]:
+            stage_ms.append(sg.sg_frame_timing(f.handle))
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clk = ClockSampler(uuid)
+    clk.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    l0 = sg.sg_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)
+        if i > 0:
+            harvest(i - 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    harvest(args.steps - 1)
+    launches = sg.sg_launch_count() - l0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    dev_ms = e0.elapsed_time(e1) / args.steps
+    wall_ms = (t1 - t0) * 1e3 / args.steps
+    ms = torch.tensor([dev_ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms.item())
+    value = world * rays_per_step / (ms * 1e-3) / 1e6
+
+    # per-stage averages over the timed steps (ms per render)
+    st = np.array(stage_ms)            # [2*steps, 4]: project, depth sort, bin+sort, render
+    per_view = st.reshape(-1, len(cams), 4).mean(axis=0)
+    stages = {"project": per_view[:, 0].tolist(), "depth_sort_offsets": per_view[:, 1].tolist(),
+              "bin_tile_sort_ranges": per_view[:, 2].tolist(), "render": per_view[:, 3].tolist(),
+              "views": ["fisheye", "pinhole"]}
+
+    # end-to-end through the C-ABI with host (pinned) output buffers
+    host = []
+    for _, c in cams:
+        n = c.width * c.height
+        host.append([torch.empty(3 * n, dtype=torch.float32).pin_memory(),
+                     torch.empty(n, dtype=torch.float32).pin_memory(),
+                     torch.empty(n, dtype=torch.float32).pin_memory()])
+    e2e_steps = max(3, min(args.steps, 40))
+    ef = [sg.Frame() for _ in cams]
+    for _ in range(2):
+        for (ch, c), h, f in zip(cams, host, ef):
+            sg.sg_render_camera_host(S.handle, ch.handle, c.c2w, opts, f.handle,
+                                     h[0].data_ptr(), h[1].data_ptr(), h[2].data_ptr(), sp)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for (ch, c), h, f in zip(cams, host, ef):
+            sg.sg_render_camera_host(S.handle, ch.handle, c.c2w, opts, f.handle,
+                                     h[0].data_ptr(), h[1].data_ptr(), h[2].data_ptr(), sp)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(e, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(e.item())
+    d2h = sum(4 * 5 * c.width * c.height for _, c in cams)
+    e2e = {"value": world * rays_per_step / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+           "h2d_bytes_per_step": 2 * 12 * 4, "d2h_bytes_per_step": d2h,
+           "ms_per_step": e2e_ms,
+           "path": "sg_render_camera_host (pinned host outputs, copies and sync in the timed region)"}
+
+    result = None
+    if rank == 0:
+        roof = roofline(per_view, cams, clocks)
+        result = {
+            "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": N_GAUSS,
+                       "rays_per_step": rays_per_step, "parallelism": "replicas",
+                       "l2": "inputs larger than L2 (236 MB of scene planes read per view)",
+                       "wall_ms_per_step": wall_ms},
+            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
+            "launches_per_step": launches / args.steps,
+            "clocks": clocks, "stages_ms": stages,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(sc, [c for _, c in cams], budget_s=20.0)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return result
+
+
+def roofline(per_view, cams, clocks):
+    """Dominant kernel: the compositing kernel (largest stage share).  ALU
+    bound: algorithmic FP32 flops = oracle-counted evaluated pairs x 56."""
+    work_path = os.path.join(ROOT, "tests", "golden", "bench_work.json")
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    render_ms = per_view[:, 3]
+    out = {"kernel": "k_render_camera", "bound": "alu", "peak": peak_tflops,
+           "unit": "TFLOP/s",
+           "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x "
+                          f"{sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
+           "traffic": None}
+    try:
+        work = json.load(open(work_path))
+        pairs = [work["views"][v]["evaluated_pairs"] for v in ("fisheye", "pinhole")]
+        flops = [p * FLOP_PER_PAIR for p in pairs]
+        ach = [f / (t * 1e-3) / 1e12 for f, t in zip(flops, render_ms)]
+        tot = sum(flops) / (sum(render_ms) * 1e-3) / 1e12
+        out.update(achieved=tot, frac=tot / peak_tflops, per_view_achieved=ach,
+                   evaluated_pairs=pairs, flop_per_pair=FLOP_PER_PAIR,
+                   launch_ms=render_ms.tolist())
+    except (OSError, KeyError, ValueError):
+        out.update(achieved=None, frac=None, note="tests/golden/bench_work.json missing")
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        out["traffic"] = tr.get("k_render_camera")
+    except (OSError, ValueError):
+        pass
+    return out
+
+
+# ------------------------------------------------------------------ oracle
+def _oracle_sample_time(O, sc, cam, n_rays, seed):
+    rng = np.random.default_rng(seed)
+    rays = rng.choice(cam.width * cam.height, n_rays, replace=False)
+    t = time.perf_counter()
+    O.render_camera(sc, cam, rays=rays)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(sc, cams, budget_s=20.0):
+    """The oracle as it stands (single-threaded C, double precision) on a
+    bounded sample: per view, the full projection and sort of the scene plus
+    the compositing of S random rays, at two sample sizes; the full-view time
+    is the linear extrapolation (fixed cost + per-ray cost x rays)."""
+    from oracle import Oracle
+    O = Oracle(64)
+    total = 0.0
+    used = 0.0
+    for i, cam in enumerate(cams):
+        s1, s2 = 1000, 6000
+        t1 = _oracle_sample_time(O, sc, cam, s1, 100 + i)
+        t2 = _oracle_sample_time(O, sc, cam, s2, 200 + i)
+        used += t1 + t2
+        per_ray = max(t2 - t1, 0.0) / (s2 - s1)
+        fixed = max(t1 - per_ray * s1, 0.0)
+        total += fixed + per_ray * cam.width * cam.height
+    rays = sum(c.width * c.height for c in cams)
+    return {"value": rays / total / 1e6, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
+            "sample": f"per view: projection + sort of all {N_GAUSS} Gaussians and compositing "
+                      f"of 1000 and 6000 random rays, extrapolated linearly to the full view "
+                      f"({used:.1f} s of CPU work); extrapolated seconds per step {total:.1f}"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    from oracle import Oracle
+    from paper_2510_12901_gb300 import synthetic as syn
+    O = Oracle(64)
+    sc = syn.street_scene(N_GAUSS, seed=0, kind="camera")
+    cams = list(syn.street_cameras())
+    n_rays = 2000          # per view per step: a bounded sample of the step
+    for i in range(args.warmup):
+        for c in cams:
+            _oracle_sample_time(O, sc, c, 200, i)
+    t = 0.0
+    for i in range(args.steps):
+        for j, c in enumerate(cams):
+            t += _oracle_sample_time(O, sc, c, n_rays, 1000 * i + j)
+    ms = t * 1e3 / args.steps
+    value = 2 * n_rays / (ms * 1e-3) / 1e6
+    sample = (f"each step: per view, projection + sort of all {N_GAUSS} Gaussians and "
+              f"compositing of {n_rays} random rays (2 views)")
+    return {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "gaussians": N_GAUSS,
+                       "rays_per_step": 2 * n_rays, "parallelism": "none (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

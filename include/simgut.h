@@ -1,0 +1,242 @@
+/* simgut.h -- C-ABI of the GB300 (sm_103a) renderer for 3DGUT-style Gaussian
+ * scenes into pinhole / OpenCV-fisheye cameras and spinning LiDAR, after
+ * "SimULi: Real-Time LiDAR and Camera Simulation with Unscented Transforms"
+ * (arXiv 2510.12901).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Status codes, never exceptions, exit() or device traps.  On failure a
+ *   message is available from sg_last_error() (thread-local).
+ * - Pointers named d_* are device pointers (CUDA global memory of the current
+ *   device); pointers named h_* are host pointers.  All arrays are dense,
+ *   row-major, float32 unless stated.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued on it; a call returns once its work is
+ *   enqueued.  The render calls read back one 4-byte count (the number of
+ *   (tile, Gaussian) pairs) and so wait for the projection stage of their
+ *   own work; nothing else synchronises.
+ * - Handles (scene, camera, lidar, frame) are owned by the library; create /
+ *   destroy them from one host thread at a time.  Output and gradient
+ *   buffers are owned by the caller.
+ */
+#ifndef SIMGUT_H
+#define SIMGUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SG_OK = 0,
+    SG_ERR_INVALID = -1,   /* bad argument; nothing was enqueued */
+    SG_ERR_OOM = -2,       /* device allocation failed */
+    SG_ERR_CUDA = -3,      /* a CUDA call failed; see sg_last_error() */
+    SG_ERR_OVERFLOW = -4,  /* a capacity (pairs, requests) was exceeded */
+    SG_ERR_TIMEOUT = -5,   /* a bounded device wait gave up */
+    SG_ERR_BUSY = -6       /* serving queue full */
+} sg_status;
+
+typedef struct sg_scene_s *sg_scene;
+typedef struct sg_camera_s *sg_camera;
+typedef struct sg_lidar_s *sg_lidar;
+typedef struct sg_frame_s *sg_frame;
+
+enum { SG_FEATURES_RGB = 0, SG_FEATURES_SH = 1, SG_FEATURES_LIDAR = 2 };
+enum { SG_CAMERA_PINHOLE = 0, SG_CAMERA_FISHEYE = 1 };
+
+/* Library version and the CUDA architecture it was built for (103 for sm_103a). */
+int sg_version(void);
+int sg_cuda_arch(void);
+const char *sg_last_error(void);
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads); the difference across a region counts its launches. */
+int64_t sg_launch_count(void);
+
+/* ----------------------------------------------------------------------
+ * Gaussian scene (Sec. 3.1: particles with mean mu, opacity sigma and
+ * covariance Sigma = R S S^T R^T; camera particles carry degree-<=3 SH colour,
+ * LiDAR particles carry features zeta = (intensity, beta_hit, beta_drop)).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int64_t n;                 /* number of Gaussians, >= 0 */
+    const float *d_means;      /* [n,3] world metres */
+    const float *d_log_scales; /* [n,3] log of the per-axis standard deviation */
+    const float *d_quats;      /* [n,4] (w,x,y,z); normalised by the library */
+    const float *d_opacity;    /* [n] in (0,1), already activated */
+    const float *d_features;   /* [n,F]: RGB F=3, SH F=3*(deg+1)^2 laid out
+                                  [n,(deg+1)^2,3], LiDAR F=3 */
+    int feature_kind;          /* SG_FEATURES_* */
+    int sh_degree;             /* 0..3, used with SG_FEATURES_SH */
+} sg_gaussians_desc;
+
+/* Copies the caller's arrays (device pointers, caller keeps ownership) into a
+ * library-owned planar layout on `stream`.  The caller's arrays may be freed
+ * once the stream has passed this call.  Errors: SG_ERR_INVALID (n<0, NULL
+ * array with n>0, bad kind/degree), SG_ERR_OOM, SG_ERR_CUDA. */
+sg_status sg_create_scene(const sg_gaussians_desc *desc, void *stream, sg_scene *out);
+/* Overwrites the parameters of an existing scene with the same n and feature
+ * layout (a training step).  Same errors as sg_create_scene. */
+sg_status sg_update_scene(sg_scene scene, const sg_gaussians_desc *desc, void *stream);
+void sg_destroy_scene(sg_scene scene);
+int64_t sg_scene_size(sg_scene scene);
+
+/* ----------------------------------------------------------------------
+ * Camera (Sec. 3.2: arbitrary camera models through the unscented
+ * transform).  Pixel (i,j) is the ray through (i+0.5, j+0.5); OpenCV axes
+ * (x right, y down, z forward).  Fisheye: theta_d = theta (1 + k1 t^2 + k2 t^4
+ * + k3 t^6 + k4 t^8), valid incidence angles [0, theta_max] with theta_max the
+ * first stationary point of theta_d (at most pi/2); pixels beyond it carry no
+ * ray.  Builds a per-pixel ray table in double precision on the device
+ * (synchronous).  Errors: SG_ERR_INVALID (size <= 0 or > 16384, f <= 0, bad
+ * model), SG_ERR_OOM, SG_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+sg_status sg_create_camera(int model, int width, int height, float fx, float fy,
+                           float cx, float cy, const float k[4], sg_camera *out);
+void sg_destroy_camera(sg_camera cam);
+
+/* ----------------------------------------------------------------------
+ * Spinning LiDAR (Sec. 3.3; App. A Proc. 1 ElevationTiling; App. B ray-based
+ * culling).  Beams have elevations h_elev_deg[n_beams] (degrees); column c
+ * has azimuth az0_deg + (c+0.5)*360/n_cols in the sensor frame (x forward,
+ * y left, z up).  The elevation tiling (n_elev_tiles = N_phi, at most
+ * max_rays_per_tile = M rays per tile), the azimuth tile count N_theta, the
+ * ray-to-tile assignment and the summed-area table of the ray mask over a
+ * dense grid of cull_az x (n_elev_tiles * cull_el_per_tile) cells are
+ * computed once here and reused by every render (synchronous).
+ * Errors: SG_ERR_INVALID (n_beams or n_cols <= 0 or > 65535, N_phi out of
+ * [1,1024], M <= 0, cull sizes <= 0, more than 65535 tiles), SG_ERR_OOM.
+ * ---------------------------------------------------------------------- */
+sg_status sg_create_lidar(const float *h_elev_deg, int n_beams, int n_cols, float az0_deg,
+                          int max_rays_per_tile, int n_elev_tiles, int cull_az,
+                          int cull_el_per_tile, sg_lidar *out);
+void sg_destroy_lidar(sg_lidar lidar);
+/* Tiling results: h_T receives n_elev_tiles+1 elevation boundaries (degrees);
+ * *n_theta the azimuth tile count.  Either pointer may be NULL. */
+sg_status sg_lidar_tiling(sg_lidar lidar, float *h_T, int *n_theta);
+
+/* ----------------------------------------------------------------------
+ * Render options.  Defaults (sg_default_opts): alpha_min 1/255, alpha_max
+ * 0.99, t_min 1e-4, near 0.2 m, unscented transform (alpha,beta,kappa) =
+ * (1,2,0), 2 LiDAR pose iterations, ray-based culling on.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    float alpha_min, alpha_max, t_min, near_dist;
+    float ut_alpha, ut_beta, ut_kappa;
+    int pose_iters;   /* LiDAR: fixed-point iterations choosing each sigma
+                         point's column pose (0..8) */
+    int cull;         /* LiDAR: ray-based culling (App. B) on/off */
+} sg_render_opts;
+sg_render_opts sg_default_opts(void);
+
+/* ----------------------------------------------------------------------
+ * Frame: the workspace of one render and the state the backward pass needs
+ * (per-Gaussian projection, sorted (tile, Gaussian) lists, per-ray final
+ * transmittance and contributor counts).  Buffers grow on demand.  A frame
+ * serves one render at a time; sg_backward_* reads the last render.
+ * ---------------------------------------------------------------------- */
+sg_status sg_frame_create(sg_frame *out);
+void sg_frame_destroy(sg_frame frame);
+
+/* ----------------------------------------------------------------------
+ * Forward render (Eq. 1: front-to-back compositing of alpha_i = sigma_i
+ * rho_i(tau_max) over the per-tile list sorted by (tile, depth, id); Sec. 3.2
+ * projection of 7 sigma points; Sec. 3.3 LiDAR).
+ *
+ * Camera: h_c2w[12] is the row-major 3x4 camera-to-world pose [R | t] (host
+ * memory, read during the call).  Outputs (device, may be NULL):
+ *   d_rgb [H,W,3]  premultiplied foreground colour sum_i c_i alpha_i T_i
+ *   d_alpha [H,W]  omega = sum_i alpha_i T_i
+ *   d_depth [H,W]  sum_i tau_i alpha_i T_i / omega, 0 where omega = 0
+ * LiDAR: d_col_c2w [n_cols,12] per-column sensor-to-world poses (device).
+ * Outputs (device, may be NULL), [n_beams, n_cols] beam-major:
+ *   d_range    sum_i tau_i alpha_i T_i / omega (0 where omega = 0)
+ *   d_intensity first channel of zeta
+ *   d_drop      softmax(beta_hit, beta_drop) probability of a drop
+ *   d_alpha     omega
+ * Errors: SG_ERR_INVALID (NULL handle / pose, opts out of range, LiDAR
+ * features on a camera render or vice versa), SG_ERR_OOM, SG_ERR_CUDA,
+ * SG_ERR_OVERFLOW (more than 2^31-1 pairs).
+ * ---------------------------------------------------------------------- */
+sg_status sg_render_camera(sg_scene scene, sg_camera cam, const float h_c2w[12],
+                           const sg_render_opts *opts, sg_frame frame, float *d_rgb,
+                           float *d_alpha, float *d_depth, void *stream);
+sg_status sg_render_lidar(sg_scene scene, sg_lidar lidar, const float *d_col_c2w,
+                          const sg_render_opts *opts, sg_frame frame, float *d_range,
+                          float *d_intensity, float *d_drop, float *d_alpha,
+                          void *stream);
+
+/* Same renders with host output buffers: the device result is copied to
+ * h_* (pinned or pageable) on `stream` and the call waits for it.  Inputs
+ * stay as above except the LiDAR poses, which are read from host memory. */
+sg_status sg_render_camera_host(sg_scene scene, sg_camera cam, const float h_c2w[12],
+                                const sg_render_opts *opts, sg_frame frame, float *h_rgb,
+                                float *h_alpha, float *h_depth, void *stream);
+sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_col_c2w,
+                               const sg_render_opts *opts, sg_frame frame, float *h_range,
+                               float *h_intensity, float *h_drop, float *h_alpha,
+                               void *stream);
+
+/* ----------------------------------------------------------------------
+ * Backward (the differentiable renderer of Sec. 3.2 / 3.4).  Given the
+ * upstream gradients of the last render in `frame` (device, same shapes as
+ * the outputs; NULL = zero), accumulates dL/d parameters into caller-owned
+ * device arrays (NULL = not wanted): d_g_means [n,3], d_g_log_scales [n,3],
+ * d_g_quats [n,4], d_g_opacity [n], d_g_features [n,F].  The caller zeroes
+ * them; the call adds (float atomics, so the summation order and the last
+ * bits vary run to run).  The unscented transform only selects tiles and is
+ * not differentiated.  Errors: SG_ERR_INVALID (frame not rendered from this
+ * scene / sensor kind), SG_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    float *d_g_means, *d_g_log_scales, *d_g_quats, *d_g_opacity, *d_g_features;
+} sg_grads;
+sg_status sg_backward_camera(sg_scene scene, sg_frame frame, const float *d_g_rgb,
+                             const float *d_g_alpha, const float *d_g_depth,
+                             const sg_grads *grads, void *stream);
+sg_status sg_backward_lidar(sg_scene scene, sg_frame frame, const float *d_g_range,
+                            const float *d_g_intensity, const float *d_g_drop,
+                            const float *d_g_alpha, const sg_grads *grads, void *stream);
+
+/* ----------------------------------------------------------------------
+ * Inspection of the last render's intermediate buffers, for tests and
+ * profiling.  Returns a device pointer into the frame (valid until the next
+ * render with it) and the element count.  Fields:
+ *   SG_FIELD_RECT      float4 per Gaussian: per-ray test box x_lo,x_hi,y_lo,y_hi
+ *   SG_FIELD_TILES     int4 per Gaussian: tile range x0,x1,y0,y1 (LiDAR x may wrap)
+ *   SG_FIELD_DEPTH     float per Gaussian: sort key |mu - o|
+ *   SG_FIELD_COUNT     uint32 per Gaussian: number of tiles binned into (0 = culled)
+ *   SG_FIELD_PAIR_IDS  uint32 per pair: Gaussian id, sorted by (tile, depth, id)
+ *   SG_FIELD_PAIR_TILES uint32 per pair: tile id of the same order
+ *   SG_FIELD_RANGES    uint2 per tile: [start, end) into the pair list
+ *   SG_FIELD_RAY_STATE float4 per ray: final transmittance, omega,
+ *                      Z = sum tau_i alpha_i T_i, LiDAR drop probability
+ *   SG_FIELD_N_CONTRIB uint32 per ray: list entries up to the last composited one
+ *   SG_FIELD_MEAN2D    float2 per Gaussian: UT mean
+ *   SG_FIELD_COV2D     float4 per Gaussian: UT covariance xx, xy, yy, 0
+ * ---------------------------------------------------------------------- */
+enum {
+    SG_FIELD_RECT = 0, SG_FIELD_TILES = 1, SG_FIELD_DEPTH = 2, SG_FIELD_COUNT = 3,
+    SG_FIELD_PAIR_IDS = 4, SG_FIELD_PAIR_TILES = 5, SG_FIELD_RANGES = 6,
+    SG_FIELD_RAY_STATE = 7, SG_FIELD_N_CONTRIB = 8, SG_FIELD_MEAN2D = 9,
+    SG_FIELD_COV2D = 10
+};
+sg_status sg_frame_field(sg_frame frame, int field, const void **d_ptr, int64_t *count);
+/* Number of (tile, Gaussian) pairs and tiles of the last render. */
+sg_status sg_frame_stats(sg_frame frame, int64_t *n_pairs, int64_t *n_tiles,
+                         int64_t *n_rays);
+
+/* ----------------------------------------------------------------------
+ * Per-stage timing of the last render (CUDA events on its stream), in ms:
+ * [0] project, [1] depth sort + offsets, [2] bin + tile sort + ranges,
+ * [3] render.  Enabled with sg_frame_set_timing(frame, 1).
+ * ---------------------------------------------------------------------- */
+sg_status sg_frame_set_timing(sg_frame frame, int on);
+sg_status sg_frame_timing(sg_frame frame, float ms[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIMGUT_H */

@@ -76,7 +76,7 @@ def _structs(real):
     class Proj(C.Structure):
         _fields_ = [("valid", C.c_int), ("mean2d", real * 2), ("cov2d", real * 3),
                     ("rect", real * 4), ("tiles", C.c_int * 4), ("count", C.c_int),
-                    ("depth", real), ("pose_col", C.c_int), ("vmargin", real)]
+                    ("depth", real), ("pose_col", C.c_int), ("vmargin", real), ("ut", C.c_int)]
 
     class Ray(C.Structure):
         _fields_ = [("out", real * 3), ("alpha", real), ("depth", real), ("zsum", real),
@@ -346,25 +346,27 @@ class Oracle:
                     opacity=np.zeros(sc.n, self.np_real),
                     features=np.zeros((sc.n, F), self.np_real))
 
-    def backward_camera(self, sc, cam, g_rgb, g_alpha, g_depth, opts=None):
+    def backward_camera(self, sc, cam, g_rgb, g_alpha, g_depth, opts=None, rays=None):
         o = opts or self.opts()
         s = self.scene(sc)
         c = self.camera(cam)
         ga = [np.ascontiguousarray(a, np.float32) for a in (g_rgb, g_alpha, g_depth)]
         G = self._grads(sc)
-        self.lib.or_backward_camera(C.byref(s), C.byref(c), C.byref(o),
+        rp, nr, keep = self._rays_arg(rays)
+        self.lib.or_backward_camera(C.byref(s), C.byref(c), C.byref(o), rp, C.c_int64(nr),
                                     *[self._p(a) for a in ga],
                                     *[self._p(G[k]) for k in
                                       ("means", "log_scales", "quats", "opacity", "features")])
         return G
 
-    def backward_lidar(self, sc, L, g_range, g_int, g_drop, g_alpha, opts=None):
+    def backward_lidar(self, sc, L, g_range, g_int, g_drop, g_alpha, opts=None, rays=None):
         o = opts or self.opts()
         s = self.scene(sc)
         lid = self.lidar(L)
         ga = [np.ascontiguousarray(a, np.float32) for a in (g_range, g_int, g_drop, g_alpha)]
         G = self._grads(sc)
-        self.lib.or_backward_lidar(C.byref(s), C.byref(lid), C.byref(o),
+        rp, nr, keep = self._rays_arg(rays)
+        self.lib.or_backward_lidar(C.byref(s), C.byref(lid), C.byref(o), rp, C.c_int64(nr),
                                    *[self._p(a) for a in ga],
                                    *[self._p(G[k]) for k in
                                      ("means", "log_scales", "quats", "opacity", "features")])

@@ -570,6 +570,7 @@ void or_project_camera(const or_scene *sc, const or_camera *cam,
         int ok = or_unscented(o, mu, R, s, cam_point_map, &ctx, 0, p->mean2d, p->cov2d);
         if (ctx.margin < p->vmargin) p->vmargin = ctx.margin;
         if (!ok) continue;
+        p->ut = 1;
         real k = extent_k(sigma, amin);
         real hx = k * sqrt(p->cov2d[0]), hy = k * sqrt(p->cov2d[2]);
         p->rect[0] = p->mean2d[0] - hx;
@@ -667,6 +668,7 @@ void or_project_lidar(const or_scene *sc, const or_lidar *L,
         int ok = or_unscented(o, mu, R, s, lidar_point_map, &ctx, 1, p->mean2d, p->cov2d);
         if (ctx.margin < p->vmargin) p->vmargin = ctx.margin;
         if (!ok) continue;
+        p->ut = 1;
         real k = extent_k(sigma, amin);
         real ha = k * sqrt(p->cov2d[0]), he = k * sqrt(p->cov2d[2]);
         p->rect[0] = p->mean2d[0] - ha;
@@ -864,7 +866,12 @@ typedef struct {
 } contrib;
 
 /* Composite one ray over an ordered Gaussian list.  When `rec` is given the
- * composited entries are recorded for the backward pass. */
+ * composited entries are recorded for the backward pass.
+ *
+ * Besides the outputs, each ray records how close its discrete decisions
+ * came to their thresholds (the m_* margins): the extent test (only for
+ * entries that would contribute at the ray), alpha_min, t_min, tau > 0, and
+ * the order of consecutive contributing entries' float32 keys. */
 static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR,
                           const uint32_t *list, int64_t nlist,
                           const real org[3], const real dir[3], real rx, real ry,
@@ -879,30 +886,36 @@ static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR
     for (int64_t li = 0; li < nlist; ++li) {
         uint32_t g = list[li];
         out->n_visited++;
-        if (o->predicate && !inside_rect(&P[g], rx, ry, wrap_az, &out->m_rect)) continue;
-        out->n_evaluated++;
-        if (prev_key >= RL(0)) {   /* relative gap between consecutive sort keys */
-            real gap = fabs(P[g].depth - prev_key) / P[g].depth;
-            if (gap < out->m_order) out->m_order = gap;
-        }
-        prev_key = P[g].depth;
+        real medge = RL(1e30);
+        int inside = !o->predicate || inside_rect(&P[g], rx, ry, wrap_az, &medge);
         const gauss_rt *G = &GR[g];
         real a, b, c;
         response_quadratic(G, org, dir, &a, &b, &c);
         real tau = -b / a;
         real D2 = c - b * b / a;
         if (D2 < RL(0)) D2 = RL(0);
-        if (fabs(tau) < out->m_tau) out->m_tau = fabs(tau);
-        if (!(tau > RL(0))) continue;   /* READING: nothing behind the origin */
         real rho = exp(RL(-0.5) * D2);
         real alpha = G->sigma * rho;
         int clamped = 0;
+        if (o->cutoffs && alpha > amax) { alpha = amax; clamped = 1; }
+        /* an extent-test flip matters only where the entry would contribute */
+        if (o->predicate && tau > RL(0) && (!o->cutoffs || alpha >= amin * RL(0.999)))
+            if (medge < out->m_rect) out->m_rect = medge;
+        if (!inside) continue;
+        out->n_evaluated++;
+        if (fabs(tau) < out->m_tau) out->m_tau = fabs(tau);
+        if (!(tau > RL(0))) continue;   /* READING: nothing behind the origin */
         if (o->cutoffs) {
-            if (alpha > amax) { alpha = amax; clamped = 1; }
             real ma = fabs(alpha - amin) / amin;
             if (ma < out->m_alpha) out->m_alpha = ma;
             if (alpha < amin) continue;
         }
+        /* order margin between consecutive entries that reach compositing */
+        if (prev_key >= RL(0)) {
+            real gap = fabs(P[g].depth - prev_key) / P[g].depth;
+            if (gap < out->m_order) out->m_order = gap;
+        }
+        prev_key = P[g].depth;
         real Tn = T * (RL(1) - alpha);
         if (o->cutoffs) {
             real mt = fabs(Tn - tmin) / tmin;
@@ -1006,6 +1019,9 @@ static int render_common(const or_scene *sc, const or_opts *o, const or_proj *P,
         uint32_t t;
         if (rf(rctx, r, oo, dd, &rx, &ry, &t) != 0) {   /* pixel outside the lens */
             memset(&out[i], 0, sizeof(or_ray));
+            out[i].t_final = RL(1);
+            out[i].m_rect = out[i].m_alpha = out[i].m_tmin = out[i].m_tau = RL(1e30);
+            out[i].m_order = RL(1e30);
             continue;
         }
         const uint32_t *list;
@@ -1265,7 +1281,8 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
 
 static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *P,
                            const real ocam[3], int ntx, int nty, int wrap,
-                           int64_t n_total, ray_fn rf, const void *rctx, int lidar,
+                           int64_t n_total, const int64_t *rays, int64_t n_rays, ray_fn rf,
+                           const void *rctx, int lidar,
                            const float *ga, const float *gb, const float *gc,
                            const float *gd, real *gm, real *gls, real *gq,
                            real *gop, real *gf)
@@ -1280,17 +1297,19 @@ static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *
     B.gmu = calloc((size_t)sc->n * 3 + 1, sizeof(real));
     B.gsig = calloc((size_t)sc->n + 1, sizeof(real));
     B.gfeat = calloc((size_t)sc->n * 3 + 1, sizeof(real));
-    or_ray *rays = malloc(sizeof(or_ray) * (size_t)(n_total > 0 ? n_total : 1));
-    render_common(sc, o, P, ocam, ntx, nty, wrap, 0, NULL, -1, n_total, rf, rctx,
-                  rays, bw_ray, &B);
+    int64_t nr = n_rays < 0 ? n_total : n_rays;
+    or_ray *out = malloc(sizeof(or_ray) * (size_t)(nr > 0 ? nr : 1));
+    render_common(sc, o, P, ocam, ntx, nty, wrap, 0, rays, n_rays, n_total, rf, rctx,
+                  out, bw_ray, &B);
     bw_finish(sc, GR, &B, ocam, gm, gls, gq, gop, gf);
-    free(rays);
+    free(out);
     free(B.gA); free(B.gmu); free(B.gsig); free(B.gfeat);
     free(GR);
     return 0;
 }
 
 int or_backward_camera(const or_scene *sc, const or_camera *cam, const or_opts *o,
+                       const int64_t *rays, int64_t n_rays,
                        const float *g_rgb, const float *g_alpha, const float *g_depth,
                        real *gm, real *gls, real *gq, real *gop, real *gf)
 {
@@ -1301,7 +1320,7 @@ int or_backward_camera(const or_scene *sc, const or_camera *cam, const or_opts *
     real ocam[3] = {RL(cam->c2w[3]), RL(cam->c2w[7]), RL(cam->c2w[11])};
     cam_rctx rc = {cam, S.theta_max, o->tile, S.n_tiles_x};
     backward_common(sc, o, P, ocam, S.n_tiles_x, S.n_tiles_y, 0,
-                    (int64_t)cam->width * cam->height, cam_ray_fn, &rc, 0, g_rgb,
+                    (int64_t)cam->width * cam->height, rays, n_rays, cam_ray_fn, &rc, 0, g_rgb,
                     g_alpha, g_depth, NULL, gm, gls, gq, gop, gf);
     free(P);
     or_setup_free(&S);
@@ -1309,6 +1328,7 @@ int or_backward_camera(const or_scene *sc, const or_camera *cam, const or_opts *
 }
 
 int or_backward_lidar(const or_scene *sc, const or_lidar *L, const or_opts *o,
+                      const int64_t *rays, int64_t n_rays,
                       const float *g_range, const float *g_int, const float *g_drop,
                       const float *g_alpha, real *gm, real *gls, real *gq, real *gop,
                       real *gf)
@@ -1322,7 +1342,8 @@ int or_backward_lidar(const or_scene *sc, const or_lidar *L, const or_opts *o,
     lid_rctx rc = {L, &S, bt, ct};
     real ocam[3] = {0, 0, 0};
     backward_common(sc, o, P, ocam, S.n_theta, L->n_elev_tiles, 1,
-                    (int64_t)L->n_beams * L->n_cols, lid_ray_fn, &rc, 1, g_range, g_int,
+                    (int64_t)L->n_beams * L->n_cols, rays, n_rays, lid_ray_fn, &rc, 1, g_range,
+                    g_int,
                     g_drop, g_alpha, gm, gls, gq, gop, gf);
     free(bt);
     free(ct);

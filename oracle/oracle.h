@@ -89,6 +89,7 @@ typedef struct {
     real depth;           /* sort key: distance |mu - o| rounded to float */
     int pose_col;         /* LiDAR: column whose pose the centre point used */
     real vmargin;         /* min relative margin of the validity tests (near, theta, opacity) */
+    int ut;               /* the unscented transform ran (all sigma points valid) */
 } or_proj;
 
 /* Per-ray outputs and statistics. */
@@ -101,11 +102,11 @@ typedef struct {
     int n_visited;        /* list entries visited before termination */
     int n_evaluated;      /* entries that passed the extent test */
     int n_contrib;        /* entries composited */
-    real m_rect;          /* min |ray coord - rect edge| over visited entries */
+    real m_rect;          /* min |ray coord - rect edge| over entries that would contribute */
     real m_alpha;         /* min |alpha - alpha_min| / alpha_min over evaluated */
     real m_tmin;          /* min |T' - t_min| / t_min over composited + stopping */
     real m_tau;           /* min |tau| over evaluated */
-    real m_order;         /* min relative gap of consecutive sort keys over evaluated */
+    real m_order;         /* min relative gap of consecutive sort keys of contributing entries */
 } or_ray;
 
 #ifdef __cplusplus
@@ -183,16 +184,19 @@ int or_render_lidar(const or_scene *sc, const or_lidar *L,
 void or_lidar_decode(const or_ray *r, real *range, real *intensity, real *drop);
 
 /* Analytic gradients (Sec. 3.4 differentiable renderer) of
- * L = sum_rays <g_out, outputs> w.r.t. the raw parameters.
+ * L = sum_rays <g_out, outputs> w.r.t. the raw parameters; upstream arrays
+ * are indexed by ray id; `rays` (n_rays < 0: all) selects the rays summed.
  * Camera outputs: rgb[3], alpha, depth.  LiDAR outputs: range, intensity,
  * drop, alpha.  grads are [n,3], [n,3], [n,4], [n], [n,F]; accumulated.
  * Pinned: central finite differences of the forward, closed forms. */
 int or_backward_camera(const or_scene *sc, const or_camera *cam,
-                       const or_opts *o, const float *g_rgb,
+                       const or_opts *o, const int64_t *rays, int64_t n_rays,
+                       const float *g_rgb,
                        const float *g_alpha, const float *g_depth,
                        real *gm, real *gls, real *gq, real *gop, real *gf);
 int or_backward_lidar(const or_scene *sc, const or_lidar *L,
-                      const or_opts *o, const float *g_range,
+                      const or_opts *o, const int64_t *rays, int64_t n_rays,
+                      const float *g_range,
                       const float *g_int, const float *g_drop,
                       const float *g_alpha,
                       real *gm, real *gls, real *gq, real *gop, real *gf);

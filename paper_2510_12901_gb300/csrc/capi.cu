@@ -1,0 +1,631 @@
+// capi.cu -- the extern "C" entry points of libsimgut (declared in
+// include/simgut.h): handle management, argument checks and the order of
+// the render stages.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+#include "internal.h"
+
+namespace sg {
+
+static thread_local char g_err[512] = "";
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+sg_status cuda_status(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;
+}
+
+sg_status ensure(Buf &b, size_t bytes)
+{
+    if (bytes <= b.bytes && b.p) return SG_OK;
+    size_t nb = bytes < 256 ? 256 : bytes + bytes / 4;   // grow with head-room
+    if (b.p) {
+        cudaFree(b.p);   // implicitly waits for work that may still use it
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed", nb);
+        return SG_ERR_OOM;
+    }
+    b.bytes = nb;
+    return SG_OK;
+}
+
+static void release(Buf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// AoS [n, comps] -> planes
+__global__ void k_to_planes(const float *__restrict__ src, int64_t n, int comps, int plane0,
+                            int64_t pitch, float *__restrict__ planes)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * comps) return;
+    int64_t g = i / comps;
+    int c = (int)(i % comps);
+    planes[(int64_t)(plane0 + c) * pitch + g] = src[i];
+}
+
+static sg_status check_desc(const sg_gaussians_desc *d, int *F)
+{
+    if (!d) { set_error("desc is NULL"); return SG_ERR_INVALID; }
+    if (d->n < 0 || d->n > (int64_t)1 << 31) {
+        set_error("n = %lld out of range [0, 2^31]", (long long)d->n);
+        return SG_ERR_INVALID;
+    }
+    if (d->feature_kind == SG_FEATURES_SH) {
+        if (d->sh_degree < 0 || d->sh_degree > 3) {
+            set_error("sh_degree %d not in 0..3", d->sh_degree);
+            return SG_ERR_INVALID;
+        }
+        *F = 3 * (d->sh_degree + 1) * (d->sh_degree + 1);
+    } else if (d->feature_kind == SG_FEATURES_RGB || d->feature_kind == SG_FEATURES_LIDAR) {
+        *F = 3;
+    } else {
+        set_error("feature_kind %d unknown", d->feature_kind);
+        return SG_ERR_INVALID;
+    }
+    if (d->n > 0 && (!d->d_means || !d->d_log_scales || !d->d_quats || !d->d_opacity ||
+                     !d->d_features)) {
+        set_error("a parameter array is NULL");
+        return SG_ERR_INVALID;
+    }
+    return SG_OK;
+}
+
+static sg_status upload_planes(Scene &s, const sg_gaussians_desc *d, cudaStream_t st)
+{
+    struct { const float *p; int comps, plane0; } parts[5] = {
+        {d->d_means, 3, Scene::kMean}, {d->d_log_scales, 3, Scene::kLogScale},
+        {d->d_quats, 4, Scene::kQuat}, {d->d_opacity, 1, Scene::kOpacity},
+        {d->d_features, s.F, Scene::kFeat}};
+    for (auto &p : parts) {
+        int64_t tot = s.n * p.comps;
+        if (tot == 0) continue;
+        k_to_planes<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(p.p, s.n, p.comps, p.plane0,
+                                                                    s.pitch, s.d_planes);
+        SG_LAUNCHED();
+    }
+    return SG_OK;
+}
+
+static bool opts_ok(const sg_render_opts *o)
+{
+    if (!o) { set_error("opts is NULL"); return false; }
+    if (!(o->alpha_min > 0.f && o->alpha_min < 1.f) || !(o->alpha_max > 0.f && o->alpha_max <= 1.f) ||
+        !(o->t_min >= 0.f && o->t_min < 1.f) || !(o->near_dist > 0.f) ||
+        !(o->ut_alpha > 0.f) || !(o->ut_kappa > -3.f) || !isfinite(o->ut_beta) ||
+        o->pose_iters < 0 || o->pose_iters > 8) {
+        set_error("render options out of range");
+        return false;
+    }
+    return true;
+}
+
+// Per-Gaussian and per-ray buffers of a render.
+static sg_status frame_prepare(Frame &fr, int64_t n, int64_t nrays, int64_t ntiles)
+{
+    sg_status s;
+#define SG_ENS(buf, by) if ((s = ensure(buf, by)) != SG_OK) return s
+    SG_ENS(fr.rec, sizeof(GRec) * (n > 0 ? n : 1));
+    SG_ENS(fr.rect, sizeof(float4) * (n > 0 ? n : 1));
+    SG_ENS(fr.tiles, sizeof(int4) * (n > 0 ? n : 1));
+    SG_ENS(fr.depth, sizeof(float) * (n > 0 ? n : 1));
+    SG_ENS(fr.count, sizeof(uint32_t) * (n > 0 ? n : 1));
+    SG_ENS(fr.mean2d, sizeof(float2) * (n > 0 ? n : 1));
+    SG_ENS(fr.cov2d, sizeof(float4) * (n > 0 ? n : 1));
+    for (int i = 0; i < 2; ++i) {
+        SG_ENS(fr.dkeys[i], sizeof(uint32_t) * (n > 0 ? n : 1));
+        SG_ENS(fr.dvals[i], sizeof(uint32_t) * (n > 0 ? n : 1));
+    }
+    SG_ENS(fr.cnt_sorted, sizeof(uint32_t) * (n > 0 ? n : 1));
+    SG_ENS(fr.offsets, sizeof(uint32_t) * (n > 0 ? n : 1));
+    SG_ENS(fr.ranges, sizeof(uint2) * (ntiles > 0 ? ntiles : 1));
+    SG_ENS(fr.ray_state, sizeof(float4) * (nrays > 0 ? nrays : 1));
+    SG_ENS(fr.n_contrib, sizeof(uint32_t) * (nrays > 0 ? nrays : 1));
+    SG_ENS(fr.scalars, 64);
+#undef SG_ENS
+    if (!fr.h_scalars) {
+        if (cudaMallocHost(&fr.h_scalars, 64) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("pinned allocation failed");
+            return SG_ERR_OOM;
+        }
+    }
+    fr.n_gauss = n;
+    fr.n_rays = nrays;
+    fr.n_tiles = ntiles;
+    return SG_OK;
+}
+
+static void tmark(Frame &fr, int i, cudaStream_t st)
+{
+    if (fr.timing) cudaEventRecord(fr.ev[i], st);
+}
+
+// Stages shared by both sensors after projection: depth sort, offsets,
+// pair count read-back, binning, tile sort, ranges.
+static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int wrap,
+                              cudaStream_t st)
+{
+    uint32_t *sc = (uint32_t *)fr.scalars.p;   // [0] valid Gaussians, [1] pairs
+    uint32_t *dk[2] = {(uint32_t *)fr.dkeys[0].p, (uint32_t *)fr.dkeys[1].p};
+    uint32_t *dv[2] = {(uint32_t *)fr.dvals[0].p, (uint32_t *)fr.dvals[1].p};
+    sg_status s = compact_valid((const uint32_t *)fr.count.p, (const float *)fr.depth.p, n,
+                                dk[0], dv[0], sc, fr, st);
+    if (s != SG_OK) return s;
+    int rb = 0;
+    s = radix_sort_pairs(dk, dv, n, sc, 0, 32, fr, st, &rb);
+    if (s != SG_OK) return s;
+    s = gather_counts(dv[rb], (const uint32_t *)fr.count.p, sc, n, (uint32_t *)fr.cnt_sorted.p, st);
+    if (s != SG_OK) return s;
+    s = scan_exclusive_u32((const uint32_t *)fr.cnt_sorted.p, (uint32_t *)fr.offsets.p, sc + 1, n,
+                           fr, st);
+    if (s != SG_OK) return s;
+    tmark(fr, 2, st);
+    SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 8, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    const int64_t K = fr.h_scalars[1];
+    if (K > 0x7fffffffLL) {
+        set_error("%lld (tile, Gaussian) pairs exceed 2^31-1", (long long)K);
+        return SG_ERR_OVERFLOW;
+    }
+    fr.n_pairs = K;
+    for (int i = 0; i < 2; ++i) {
+        if ((s = ensure(fr.pkeys[i], sizeof(uint32_t) * (K > 0 ? K : 1))) != SG_OK) return s;
+        if ((s = ensure(fr.pvals[i], sizeof(uint32_t) * (K > 0 ? K : 1))) != SG_OK) return s;
+    }
+    uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
+    uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
+    s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, sc, n, (const int4 *)fr.tiles.p, ntx,
+                  wrap, pk[0], pv[0], st);
+    if (s != SG_OK) return s;
+    int bits = 1;
+    while (((int64_t)1 << bits) < ntiles) ++bits;
+    int pb = 0;
+    s = radix_sort_pairs(pk, pv, K, sc + 1, 0, bits, fr, st, &pb);
+    if (s != SG_OK) return s;
+    fr.pair_buf = pb;
+    s = tile_ranges(pk[pb], K, (uint2 *)fr.ranges.p, ntiles, st);
+    if (s != SG_OK) return s;
+    tmark(fr, 3, st);
+    return SG_OK;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+struct sg_scene_s { Scene s; };
+struct sg_camera_s { Camera c; };
+struct sg_lidar_s { Lidar l; };
+struct sg_frame_s { Frame f; };
+
+extern "C" {
+
+int sg_version(void) { return 100; }
+int64_t sg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+int sg_cuda_arch(void) { return 103; }
+const char *sg_last_error(void) { return g_err; }
+
+sg_render_opts sg_default_opts(void)
+{
+    sg_render_opts o;
+    o.alpha_min = 1.0f / 255.0f;
+    o.alpha_max = 0.99f;
+    o.t_min = 1e-4f;
+    o.near_dist = 0.2f;
+    o.ut_alpha = 1.0f;
+    o.ut_beta = 2.0f;
+    o.ut_kappa = 0.0f;
+    o.pose_iters = 2;
+    o.cull = 1;
+    return o;
+}
+
+sg_status sg_create_scene(const sg_gaussians_desc *desc, void *stream, sg_scene *out)
+{
+    if (!out) { set_error("out is NULL"); return SG_ERR_INVALID; }
+    *out = nullptr;
+    int F = 0;
+    sg_status s = check_desc(desc, &F);
+    if (s != SG_OK) return s;
+    sg_scene h = new (std::nothrow) sg_scene_s;
+    if (!h) { set_error("host allocation failed"); return SG_ERR_OOM; }
+    Scene &sc = h->s;
+    sc.n = desc->n;
+    sc.feature_kind = desc->feature_kind;
+    sc.sh_degree = desc->feature_kind == SG_FEATURES_SH ? desc->sh_degree : 0;
+    sc.F = F;
+    sc.pitch = ((desc->n + 31) / 32) * 32;
+    if (sc.pitch == 0) sc.pitch = 32;
+    size_t bytes = sizeof(float) * (size_t)sc.pitch * (Scene::kFeat + F);
+    if (cudaMalloc(&sc.d_planes, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        set_error("scene allocation of %zu bytes failed", bytes);
+        return SG_ERR_OOM;
+    }
+    s = upload_planes(sc, desc, (cudaStream_t)stream);
+    if (s != SG_OK) {
+        cudaFree(sc.d_planes);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return SG_OK;
+}
+
+sg_status sg_update_scene(sg_scene scene, const sg_gaussians_desc *desc, void *stream)
+{
+    if (!scene) { set_error("scene is NULL"); return SG_ERR_INVALID; }
+    int F = 0;
+    sg_status s = check_desc(desc, &F);
+    if (s != SG_OK) return s;
+    if (desc->n != scene->s.n || F != scene->s.F || desc->feature_kind != scene->s.feature_kind) {
+        set_error("sg_update_scene: size or feature layout differs from the scene");
+        return SG_ERR_INVALID;
+    }
+    return upload_planes(scene->s, desc, (cudaStream_t)stream);
+}
+
+void sg_destroy_scene(sg_scene scene)
+{
+    if (!scene) return;
+    cudaFree(scene->s.d_planes);
+    delete scene;
+}
+
+int64_t sg_scene_size(sg_scene scene) { return scene ? scene->s.n : -1; }
+
+sg_status sg_create_camera(int model, int width, int height, float fx, float fy, float cx,
+                           float cy, const float k[4], sg_camera *out)
+{
+    if (!out) { set_error("out is NULL"); return SG_ERR_INVALID; }
+    *out = nullptr;
+    if ((model != SG_CAMERA_PINHOLE && model != SG_CAMERA_FISHEYE) || width <= 0 ||
+        height <= 0 || width > 16384 || height > 16384 || !(fx > 0.f) || !(fy > 0.f) ||
+        !isfinite(cx) || !isfinite(cy)) {
+        set_error("sg_create_camera: bad model, size or intrinsics");
+        return SG_ERR_INVALID;
+    }
+    sg_camera h = new (std::nothrow) sg_camera_s;
+    if (!h) { set_error("host allocation failed"); return SG_ERR_OOM; }
+    Camera &c = h->c;
+    c.model = model;
+    c.width = width;
+    c.height = height;
+    c.fx = fx; c.fy = fy; c.cx = cx; c.cy = cy;
+    for (int i = 0; i < 4; ++i) c.k[i] = (model == SG_CAMERA_FISHEYE && k) ? k[i] : 0.f;
+    sg_status s = build_camera(c);
+    if (s != SG_OK) {
+        cudaFree(c.d_pix);
+        cudaFree(c.d_tile_dir);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return SG_OK;
+}
+
+void sg_destroy_camera(sg_camera cam)
+{
+    if (!cam) return;
+    cudaFree(cam->c.d_pix);
+    cudaFree(cam->c.d_tile_dir);
+    delete cam;
+}
+
+sg_status sg_create_lidar(const float *h_elev_deg, int n_beams, int n_cols, float az0_deg,
+                          int max_rays_per_tile, int n_elev_tiles, int cull_az,
+                          int cull_el_per_tile, sg_lidar *out)
+{
+    if (!out) { set_error("out is NULL"); return SG_ERR_INVALID; }
+    *out = nullptr;
+    if (!h_elev_deg || n_beams <= 0 || n_beams > 65535 || n_cols <= 0 || n_cols > 65535 ||
+        n_elev_tiles < 1 || n_elev_tiles > 1024 || max_rays_per_tile <= 0 || cull_az <= 0 ||
+        cull_el_per_tile <= 0 || !isfinite(az0_deg)) {
+        set_error("sg_create_lidar: bad arguments");
+        return SG_ERR_INVALID;
+    }
+    for (int b = 0; b < n_beams; ++b)
+        if (!(h_elev_deg[b] > -90.f && h_elev_deg[b] < 90.f)) {
+            set_error("sg_create_lidar: elevation %d out of (-90, 90)", b);
+            return SG_ERR_INVALID;
+        }
+    sg_lidar h = new (std::nothrow) sg_lidar_s;
+    if (!h) { set_error("host allocation failed"); return SG_ERR_OOM; }
+    Lidar &L = h->l;
+    L.n_beams = n_beams;
+    L.n_cols = n_cols;
+    L.az0 = az0_deg;
+    L.nphi = n_elev_tiles;
+    L.M = max_rays_per_tile;
+    L.cull_az = cull_az;
+    L.cull_el = cull_el_per_tile;
+    L.elev.assign(h_elev_deg, h_elev_deg + n_beams);
+    sg_status s = build_lidar(L);
+    if (s != SG_OK) {
+        sg_destroy_lidar(h);
+        return s;
+    }
+    *out = h;
+    return SG_OK;
+}
+
+void sg_destroy_lidar(sg_lidar lidar)
+{
+    if (!lidar) return;
+    Lidar &L = lidar->l;
+    cudaFree(L.d_T);
+    cudaFree(L.d_elev);
+    cudaFree(L.d_az);
+    cudaFree(L.d_sat);
+    cudaFree(L.d_items);
+    cudaFree(L.d_item_rays);
+    cudaFree(L.d_ray_e);
+    cudaFree(L.d_tile_u);
+    delete lidar;
+}
+
+sg_status sg_lidar_tiling(sg_lidar lidar, float *h_T, int *n_theta)
+{
+    if (!lidar) { set_error("lidar is NULL"); return SG_ERR_INVALID; }
+    if (h_T) memcpy(h_T, lidar->l.T.data(), sizeof(float) * lidar->l.T.size());
+    if (n_theta) *n_theta = lidar->l.n_theta;
+    return SG_OK;
+}
+
+sg_status sg_frame_create(sg_frame *out)
+{
+    if (!out) { set_error("out is NULL"); return SG_ERR_INVALID; }
+    sg_frame h = new (std::nothrow) sg_frame_s;
+    if (!h) { set_error("host allocation failed"); return SG_ERR_OOM; }
+    *out = h;
+    return SG_OK;
+}
+
+void sg_frame_destroy(sg_frame frame)
+{
+    if (!frame) return;
+    Frame &f = frame->f;
+    Buf *bufs[] = {&f.rec, &f.rect, &f.tiles, &f.depth, &f.count, &f.mean2d, &f.cov2d,
+                   &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.cnt_sorted,
+                   &f.offsets, &f.flags, &f.scan_tmp, &f.hist, &f.pkeys[0], &f.pkeys[1],
+                   &f.pvals[0], &f.pvals[1], &f.ranges, &f.ray_state, &f.n_contrib, &f.scalars,
+                   &f.gacc};
+    for (Buf *b : bufs) release(*b);
+    if (f.h_scalars) cudaFreeHost(f.h_scalars);
+    for (auto &e : f.ev)
+        if (e) cudaEventDestroy(e);
+    delete frame;
+}
+
+sg_status sg_frame_set_timing(sg_frame frame, int on)
+{
+    if (!frame) { set_error("frame is NULL"); return SG_ERR_INVALID; }
+    Frame &f = frame->f;
+    if (on && !f.ev[0])
+        for (auto &e : f.ev) SG_CUDA(cudaEventCreate(&e));
+    f.timing = on != 0;
+    return SG_OK;
+}
+
+sg_status sg_frame_timing(sg_frame frame, float ms[4])
+{
+    if (!frame || !ms) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    Frame &f = frame->f;
+    if (!f.timing) { set_error("timing is off for this frame"); return SG_ERR_INVALID; }
+    SG_CUDA(cudaEventSynchronize(f.ev[4]));
+    for (int i = 0; i < 4; ++i) SG_CUDA(cudaEventElapsedTime(&ms[i], f.ev[i], f.ev[i + 1]));
+    return SG_OK;
+}
+
+// timing marks: ev0 | project | ev1 | depth sort + offsets | ev2 | bin + tile
+// sort + ranges | ev3 | render | ev4
+
+sg_status sg_render_camera(sg_scene scene, sg_camera cam, const float h_c2w[12],
+                           const sg_render_opts *opts, sg_frame frame, float *d_rgb,
+                           float *d_alpha, float *d_depth, void *stream)
+{
+    if (!scene || !cam || !frame || !h_c2w) { set_error("NULL handle or pose"); return SG_ERR_INVALID; }
+    if (!opts_ok(opts)) return SG_ERR_INVALID;
+    const Scene &sc = scene->s;
+    if (sc.feature_kind == SG_FEATURES_LIDAR) {
+        set_error("sg_render_camera: scene carries LiDAR features");
+        return SG_ERR_INVALID;
+    }
+    for (int i = 0; i < 12; ++i)
+        if (!isfinite(h_c2w[i])) { set_error("pose is not finite"); return SG_ERR_INVALID; }
+    const Camera &c = cam->c;
+    Frame &fr = frame->f;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t nt = (int64_t)c.ntx * c.nty, nr = (int64_t)c.width * c.height;
+    sg_status s = frame_prepare(fr, sc.n, nr, nt);
+    if (s != SG_OK) return s;
+    fr.kind = 0;
+    fr.scene = scene;
+    fr.sensor = cam;
+    fr.opts = *opts;
+    memcpy(fr.c2w, h_c2w, sizeof(fr.c2w));
+    if (fr.timing) cudaEventRecord(fr.ev[0], st);
+    if ((s = project_camera(sc, c, h_c2w, *opts, fr, st)) != SG_OK) return s;
+    if (fr.timing) cudaEventRecord(fr.ev[1], st);
+    if ((s = sort_and_bin(fr, sc.n, c.ntx, nt, 0, st)) != SG_OK) return s;
+    if ((s = render_camera(c, h_c2w, *opts, fr, d_rgb, d_alpha, d_depth, st)) != SG_OK) return s;
+    if (fr.timing) cudaEventRecord(fr.ev[4], st);
+    return SG_OK;
+}
+
+sg_status sg_render_lidar(sg_scene scene, sg_lidar lidar, const float *d_col_c2w,
+                          const sg_render_opts *opts, sg_frame frame, float *d_range,
+                          float *d_intensity, float *d_drop, float *d_alpha, void *stream)
+{
+    if (!scene || !lidar || !frame || !d_col_c2w) { set_error("NULL handle or poses"); return SG_ERR_INVALID; }
+    if (!opts_ok(opts)) return SG_ERR_INVALID;
+    const Scene &sc = scene->s;
+    if (sc.feature_kind != SG_FEATURES_LIDAR) {
+        set_error("sg_render_lidar: scene does not carry LiDAR features");
+        return SG_ERR_INVALID;
+    }
+    const Lidar &L = lidar->l;
+    Frame &fr = frame->f;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t nt = (int64_t)L.n_theta * L.nphi, nr = (int64_t)L.n_beams * L.n_cols;
+    sg_status s = frame_prepare(fr, sc.n, nr, nt);
+    if (s != SG_OK) return s;
+    fr.kind = 1;
+    fr.scene = scene;
+    fr.sensor = lidar;
+    fr.opts = *opts;
+    fr.d_lidar_poses = d_col_c2w;
+    if (fr.timing) cudaEventRecord(fr.ev[0], st);
+    if ((s = project_lidar(sc, L, d_col_c2w, *opts, fr, st)) != SG_OK) return s;
+    if (fr.timing) cudaEventRecord(fr.ev[1], st);
+    if ((s = sort_and_bin(fr, sc.n, L.n_theta, nt, 1, st)) != SG_OK) return s;
+    if ((s = render_lidar(L, d_col_c2w, *opts, fr, d_range, d_intensity, d_drop, d_alpha, st)) !=
+        SG_OK)
+        return s;
+    if (fr.timing) cudaEventRecord(fr.ev[4], st);
+    return SG_OK;
+}
+
+// Host-output variants: render into library-owned device buffers, then copy.
+static sg_status host_copy(Buf &b, size_t bytes) { return ensure(b, bytes); }
+
+static thread_local Buf g_host_out[4];
+static thread_local Buf g_host_poses;
+
+sg_status sg_render_camera_host(sg_scene scene, sg_camera cam, const float h_c2w[12],
+                                const sg_render_opts *opts, sg_frame frame, float *h_rgb,
+                                float *h_alpha, float *h_depth, void *stream)
+{
+    if (!cam) { set_error("camera is NULL"); return SG_ERR_INVALID; }
+    int64_t np = (int64_t)cam->c.width * cam->c.height;
+    sg_status s;
+    if ((s = host_copy(g_host_out[0], sizeof(float) * 3 * np)) != SG_OK) return s;
+    if ((s = host_copy(g_host_out[1], sizeof(float) * np)) != SG_OK) return s;
+    if ((s = host_copy(g_host_out[2], sizeof(float) * np)) != SG_OK) return s;
+    float *d_rgb = (float *)g_host_out[0].p, *d_a = (float *)g_host_out[1].p,
+          *d_d = (float *)g_host_out[2].p;
+    s = sg_render_camera(scene, cam, h_c2w, opts, frame, h_rgb ? d_rgb : nullptr,
+                         h_alpha ? d_a : nullptr, h_depth ? d_d : nullptr, stream);
+    if (s != SG_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h_rgb) SG_CUDA(cudaMemcpyAsync(h_rgb, d_rgb, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
+    if (h_alpha) SG_CUDA(cudaMemcpyAsync(h_alpha, d_a, sizeof(float) * np, cudaMemcpyDeviceToHost, st));
+    if (h_depth) SG_CUDA(cudaMemcpyAsync(h_depth, d_d, sizeof(float) * np, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    return SG_OK;
+}
+
+sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_col_c2w,
+                               const sg_render_opts *opts, sg_frame frame, float *h_range,
+                               float *h_intensity, float *h_drop, float *h_alpha, void *stream)
+{
+    if (!lidar || !h_col_c2w) { set_error("NULL lidar or poses"); return SG_ERR_INVALID; }
+    const Lidar &L = lidar->l;
+    int64_t nr = (int64_t)L.n_beams * L.n_cols;
+    sg_status s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = ensure(g_host_poses, sizeof(float) * 12 * L.n_cols)) != SG_OK) return s;
+    SG_CUDA(cudaMemcpyAsync(g_host_poses.p, h_col_c2w, sizeof(float) * 12 * L.n_cols,
+                            cudaMemcpyHostToDevice, st));
+    float *h[4] = {h_range, h_intensity, h_drop, h_alpha};
+    float *d[4];
+    for (int i = 0; i < 4; ++i) {
+        if ((s = ensure(g_host_out[i], sizeof(float) * nr)) != SG_OK) return s;
+        d[i] = h[i] ? (float *)g_host_out[i].p : nullptr;
+    }
+    s = sg_render_lidar(scene, lidar, (const float *)g_host_poses.p, opts, frame, d[0], d[1],
+                        d[2], d[3], stream);
+    if (s != SG_OK) return s;
+    for (int i = 0; i < 4; ++i)
+        if (h[i]) SG_CUDA(cudaMemcpyAsync(h[i], d[i], sizeof(float) * nr, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    return SG_OK;
+}
+
+sg_status sg_frame_field(sg_frame frame, int field, const void **d_ptr, int64_t *count)
+{
+    if (!frame || !d_ptr || !count) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    Frame &f = frame->f;
+    if (f.kind < 0) { set_error("frame has not been rendered"); return SG_ERR_INVALID; }
+    switch (field) {
+    case SG_FIELD_RECT: *d_ptr = f.rect.p; *count = f.n_gauss; break;
+    case SG_FIELD_TILES: *d_ptr = f.tiles.p; *count = f.n_gauss; break;
+    case SG_FIELD_DEPTH: *d_ptr = f.depth.p; *count = f.n_gauss; break;
+    case SG_FIELD_COUNT: *d_ptr = f.count.p; *count = f.n_gauss; break;
+    case SG_FIELD_PAIR_IDS: *d_ptr = f.pvals[f.pair_buf].p; *count = f.n_pairs; break;
+    case SG_FIELD_PAIR_TILES: *d_ptr = f.pkeys[f.pair_buf].p; *count = f.n_pairs; break;
+    case SG_FIELD_RANGES: *d_ptr = f.ranges.p; *count = f.n_tiles; break;
+    case SG_FIELD_RAY_STATE: *d_ptr = f.ray_state.p; *count = f.n_rays; break;
+    case SG_FIELD_N_CONTRIB: *d_ptr = f.n_contrib.p; *count = f.n_rays; break;
+    case SG_FIELD_MEAN2D: *d_ptr = f.mean2d.p; *count = f.n_gauss; break;
+    case SG_FIELD_COV2D: *d_ptr = f.cov2d.p; *count = f.n_gauss; break;
+    default: set_error("unknown field %d", field); return SG_ERR_INVALID;
+    }
+    return SG_OK;
+}
+
+sg_status sg_frame_stats(sg_frame frame, int64_t *n_pairs, int64_t *n_tiles, int64_t *n_rays)
+{
+    if (!frame) { set_error("frame is NULL"); return SG_ERR_INVALID; }
+    if (n_pairs) *n_pairs = frame->f.n_pairs;
+    if (n_tiles) *n_tiles = frame->f.n_tiles;
+    if (n_rays) *n_rays = frame->f.n_rays;
+    return SG_OK;
+}
+
+sg_status sg_backward_camera(sg_scene scene, sg_frame frame, const float *d_g_rgb,
+                             const float *d_g_alpha, const float *d_g_depth,
+                             const sg_grads *grads, void *stream)
+{
+    if (!scene || !frame || !grads) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    Frame &f = frame->f;
+    if (f.kind != 0 || f.scene != scene) {
+        set_error("sg_backward_camera: the frame's last render is not a camera render of this scene");
+        return SG_ERR_INVALID;
+    }
+    return backward_camera(scene->s, ((sg_camera)f.sensor)->c, f, d_g_rgb, d_g_alpha, d_g_depth,
+                           *grads, (cudaStream_t)stream);
+}
+
+sg_status sg_backward_lidar(sg_scene scene, sg_frame frame, const float *d_g_range,
+                            const float *d_g_intensity, const float *d_g_drop,
+                            const float *d_g_alpha, const sg_grads *grads, void *stream)
+{
+    if (!scene || !frame || !grads) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    Frame &f = frame->f;
+    if (f.kind != 1 || f.scene != scene) {
+        set_error("sg_backward_lidar: the frame's last render is not a LiDAR render of this scene");
+        return SG_ERR_INVALID;
+    }
+    return backward_lidar(scene->s, ((sg_lidar)f.sensor)->l, f, d_g_range, d_g_intensity,
+                          d_g_drop, d_g_alpha, *grads, (cudaStream_t)stream);
+}
+
+}  // extern "C"

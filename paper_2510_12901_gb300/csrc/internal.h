@@ -1,0 +1,203 @@
+// internal.h -- types and helpers shared by the CUDA translation units of
+// libsimgut.  Not part of the C-ABI (include/simgut.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/simgut.h"
+
+namespace sg {
+
+constexpr int kTile = 16;                 // camera tile edge (pixels)
+constexpr int kCamThreads = kTile * kTile;
+constexpr int kLidarColsMax = 4;          // distinct columns per LiDAR work item
+constexpr int kLidarWarps = 4;            // warps (work items) per LiDAR render block
+
+void set_error(const char *fmt, ...);
+sg_status cuda_status(cudaError_t e, const char *what);
+void count_launch();
+
+// after every kernel launch: count it and surface launch errors
+#define SG_LAUNCHED()                                                     \
+    do {                                                                  \
+        ::sg::count_launch();                                             \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) return ::sg::cuda_status(e_, "kernel launch"); \
+    } while (0)
+
+#define SG_CUDA(call)                                                     \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return ::sg::cuda_status(e_, #call);       \
+    } while (0)
+
+// ------------------------------------------------------------------ handles
+struct Scene {
+    int64_t n = 0;
+    int feature_kind = 0, sh_degree = 0, F = 3;
+    // planar SoA, plane k holds component k of all Gaussians (n floats each)
+    float *d_planes = nullptr;  // [3 mean + 3 logscale + 4 quat + 1 opacity + F] * n
+    int64_t pitch = 0;          // floats per plane (n rounded up to 32)
+    float *plane(int k) const { return d_planes + (int64_t)k * pitch; }
+    static constexpr int kMean = 0, kLogScale = 3, kQuat = 6, kOpacity = 10, kFeat = 11;
+};
+
+struct Camera {
+    int model = 0, width = 0, height = 0;
+    float fx = 0, fy = 0, cx = 0, cy = 0, k[4] = {0, 0, 0, 0};
+    double theta_max = 0;
+    int ntx = 0, nty = 0;
+    // per pixel: camera-frame direction minus its tile's reference direction
+    // (w = 1 valid, 0 no ray); per tile: reference direction (double)
+    float4 *d_pix = nullptr;
+    double *d_tile_dir = nullptr;  // [ntiles*3]
+};
+
+struct LidarItem {       // one warp of LiDAR rendering
+    uint32_t tile;       // elevation-major tile id e * n_theta + a
+    uint16_t col0;       // first column of the item
+    uint8_t ncols;       // distinct columns (<= kLidarColsMax)
+    uint8_t nrays;       // rays (<= 32)
+    uint32_t ray_off;    // offset into item_rays (32 slots per item)
+    uint32_t ref_col;    // column whose rotation defines the tile reference ray
+};
+
+struct Lidar {
+    int n_beams = 0, n_cols = 0;
+    float az0 = 0;
+    int nphi = 0, M = 0, n_theta = 0, cull_az = 0, cull_el = 0;
+    std::vector<float> elev, T;
+    int n_items = 0;
+    float *d_T = nullptr;           // [nphi+1]
+    float *d_elev = nullptr;        // [n_beams]
+    float *d_az = nullptr;          // [n_cols] column azimuth (deg)
+    int *d_sat = nullptr;           // [(A+1)*(E+1)]
+    LidarItem *d_items = nullptr;   // [n_items]
+    uint32_t *d_item_rays = nullptr;  // [n_items*32]: beam*n_cols + col, ~0u = none
+    float4 *d_ray_e = nullptr;      // [n_beams*n_cols] sensor dir minus tile reference
+    double *d_tile_u = nullptr;     // [ntiles*3] tile reference sensor direction
+};
+
+// ------------------------------------------------------------------ records
+// Per-Gaussian render record written by the projection (96 bytes).
+struct __align__(16) GRec {
+    float4 mu_sigma;   // mean, opacity
+    float4 m0;         // row 0 of M = S^-1 R^T, w = f_0 = s0^2/(s0 s1 s2)
+    float4 m1;         // row 1, f_1
+    float4 m2;         // row 2, f_2
+    float4 feat;       // colour / LiDAR features (3), pad
+    float4 rect;       // per-ray test box x_lo, x_hi, y_lo, y_hi
+};
+
+// ------------------------------------------------------------------ frame
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Frame {
+    // per-Gaussian
+    Buf rec, rect, tiles, depth, count, mean2d, cov2d;
+    // depth sort / offsets
+    Buf dkeys[2], dvals[2], cnt_sorted, offsets, flags, scan_tmp, hist;
+    // pairs
+    Buf pkeys[2], pvals[2], ranges;
+    // per-ray saved state: (T_final, omega, Z, LiDAR drop) and contributor count
+    Buf ray_state, n_contrib;
+    // backward accumulators: per Gaussian dL/dM (9), dL/dmu (3), dL/dsigma,
+    // dL/dfeature (3)
+    Buf gacc;
+    Buf scalars;      // device scalars (counts)
+    uint32_t *h_scalars = nullptr;  // pinned mirror
+    int64_t n_pairs = 0, n_tiles = 0, n_rays = 0, n_gauss = 0;
+    int pair_buf = 0;  // which of pkeys/pvals holds the sorted result
+    int kind = -1;     // 0 camera, 1 lidar
+    const void *scene = nullptr;
+    const void *sensor = nullptr;
+    float c2w[12];     // camera pose of the last render
+    const float *d_lidar_poses = nullptr;
+    sg_render_opts opts;
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    float ms[4] = {0, 0, 0, 0};
+};
+
+sg_status ensure(Buf &b, size_t bytes);
+
+// ------------------------------------------------------------------ launchers
+// sort.cu
+sg_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, uint32_t *d_total,
+                             int64_t n, Frame &fr, cudaStream_t st);
+sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n,
+                           const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
+                           cudaStream_t st, int *result_buf);
+sg_status compact_valid(const uint32_t *d_count, const float *d_depth, int64_t n,
+                        uint32_t *d_keys, uint32_t *d_vals, uint32_t *d_nvalid, Frame &fr,
+                        cudaStream_t st);
+sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count,
+                        const uint32_t *d_nvalid, int64_t n, uint32_t *d_out,
+                        cudaStream_t st);
+sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets,
+                    const uint32_t *d_nvalid, int64_t n, const int4 *d_tiles,
+                    int ntx, int wrap_x, uint32_t *d_keys, uint32_t *d_vals,
+                    cudaStream_t st);
+sg_status tile_ranges(const uint32_t *d_keys, int64_t K, uint2 *d_ranges, int64_t ntiles,
+                      cudaStream_t st);
+
+// project.cu
+sg_status project_camera(const Scene &sc, const Camera &cam, const float c2w[12],
+                         const sg_render_opts &o, Frame &fr, cudaStream_t st);
+sg_status project_lidar(const Scene &sc, const Lidar &L, const float *d_poses,
+                        const sg_render_opts &o, Frame &fr, cudaStream_t st);
+
+// render.cu
+sg_status render_camera(const Camera &cam, const float c2w[12], const sg_render_opts &o,
+                        Frame &fr, float *rgb, float *alpha, float *depth,
+                        cudaStream_t st);
+sg_status render_lidar(const Lidar &L, const float *d_poses, const sg_render_opts &o,
+                       Frame &fr, float *range, float *intensity, float *drop,
+                       float *alpha, cudaStream_t st);
+
+// sensors.cu
+sg_status build_camera(Camera &cam);
+sg_status build_lidar(Lidar &L);
+
+// backward.cu
+sg_status backward_camera(const Scene &sc, const Camera &cam, Frame &fr,
+                          const float *g_rgb, const float *g_alpha, const float *g_depth,
+                          const sg_grads &g, cudaStream_t st);
+sg_status backward_lidar(const Scene &sc, const Lidar &L, Frame &fr, const float *g_range,
+                         const float *g_int, const float *g_drop, const float *g_alpha,
+                         const sg_grads &g, cudaStream_t st);
+
+}  // namespace sg
+
+// ---------------------------------------------------------------- device math
+#ifdef __CUDACC__
+namespace sgd {
+
+// a - b as an unevaluated sum hi + lo, exactly (Knuth's TwoSum of a and -b).
+__device__ __forceinline__ void two_diff(float a, float b, float &hi, float &lo)
+{
+    float s = __fsub_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb));
+    hi = s;
+}
+
+// a*b - c*d with an error near one ulp of the result (Kahan's algorithm
+// with fused multiply-adds).
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d)
+{
+    float w = __fmul_rn(c, d);
+    float e = __fmaf_rn(-c, d, w);       // w - c*d exactly
+    float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
+}  // namespace sgd
+#endif

@@ -1,0 +1,205 @@
+// pairs.cuh -- per-(ray, Gaussian) arithmetic shared by the forward and the
+// backward kernels, so that both take exactly the same decisions (extent
+// test, tau > 0, alpha cutoffs) and see the same values.
+//
+// Notation (render.cu explains the formulation): M = S^-1 R^T with rows M_k,
+// f_k = s_k / (s_i s_j) (rows of cof(M) are f_k M_k), v = mu - o, ray
+// direction d = d_T + dd (tile reference + small offset).
+//   num = cof(M) (v x d)  = a + P dd          (|num|^2 / |den|^2 = D^2)
+//   den = M d             = M d_T + M dd
+//   tau_max = (M v) . den / |den|^2
+#pragma once
+
+#include "internal.h"
+
+namespace sg {
+
+// moment (mu - o) x d_T with d_T = dh + dl, mu and o floats: accurate to a
+// few ulp of the result (TwoSum on mu - o, Kahan's difference of products)
+__device__ __forceinline__ void precise_moment(const float mu[3], const float o[3],
+                                               const float dh[3], const float dl[3],
+                                               float w[3], float vh[3])
+{
+    float vl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sgd::two_diff(mu[k], o[k], vh[k], vl[k]);
+    w[0] = sgd::diff_of_products(vh[1], dh[2], vh[2], dh[1]) +
+           ((vh[1] * dl[2] - vh[2] * dl[1]) + (vl[1] * dh[2] - vl[2] * dh[1]));
+    w[1] = sgd::diff_of_products(vh[2], dh[0], vh[0], dh[2]) +
+           ((vh[2] * dl[0] - vh[0] * dl[2]) + (vl[2] * dh[0] - vl[0] * dh[2]));
+    w[2] = sgd::diff_of_products(vh[0], dh[1], vh[1], dh[0]) +
+           ((vh[0] * dl[1] - vh[1] * dl[0]) + (vl[0] * dh[1] - vl[1] * dh[0]));
+}
+
+__device__ __forceinline__ float dot3(const float a[3], const float b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Camera entry, 9 float4 (one per shared-memory plane):
+//   e[0..2] = (P row k, a_k)       e[3..5] = (M row k, M_k . d_T)
+//   e[6]    = (M v, sigma)         e[7] = features      e[8] = extent box
+__device__ __forceinline__ void cam_entry(const GRec &r, const float o[3], const float dh[3],
+                                          const float dl[3], float4 e[9])
+{
+    const float mu[3] = {r.mu_sigma.x, r.mu_sigma.y, r.mu_sigma.z};
+    const float M0[3] = {r.m0.x, r.m0.y, r.m0.z}, M1[3] = {r.m1.x, r.m1.y, r.m1.z},
+                M2[3] = {r.m2.x, r.m2.y, r.m2.z};
+    float w[3], vh[3];
+    precise_moment(mu, o, dh, dl, w, vh);
+    // P rows: f_k (M_k x v), since M_k . (v x dd) = dd . (M_k x v)
+    const float f0 = r.m0.w, f1 = r.m1.w, f2 = r.m2.w;
+    e[0] = make_float4(f0 * (M0[1] * vh[2] - M0[2] * vh[1]), f0 * (M0[2] * vh[0] - M0[0] * vh[2]),
+                       f0 * (M0[0] * vh[1] - M0[1] * vh[0]), f0 * dot3(M0, w));
+    e[1] = make_float4(f1 * (M1[1] * vh[2] - M1[2] * vh[1]), f1 * (M1[2] * vh[0] - M1[0] * vh[2]),
+                       f1 * (M1[0] * vh[1] - M1[1] * vh[0]), f1 * dot3(M1, w));
+    e[2] = make_float4(f2 * (M2[1] * vh[2] - M2[2] * vh[1]), f2 * (M2[2] * vh[0] - M2[0] * vh[2]),
+                       f2 * (M2[0] * vh[1] - M2[1] * vh[0]), f2 * dot3(M2, w));
+    e[3] = make_float4(M0[0], M0[1], M0[2], dot3(M0, dh));
+    e[4] = make_float4(M1[0], M1[1], M1[2], dot3(M1, dh));
+    e[5] = make_float4(M2[0], M2[1], M2[2], dot3(M2, dh));
+    e[6] = make_float4(dot3(M0, vh), dot3(M1, vh), dot3(M2, vh), r.mu_sigma.w);
+    e[7] = r.feat;
+    e[8] = r.rect;
+}
+
+struct PairEval {
+    float n[3];      // num = cof(M)(v x d)
+    float e[3];      // den = M d
+    float inv;       // 1 / |den|^2
+    float D2, tau, rho, alpha;
+    bool clamped;    // alpha hit alpha_max
+};
+
+// Evaluate one camera pair; returns false when the entry does not composite
+// at this ray (outside the box, behind the origin, or below alpha_min).
+__device__ __forceinline__ bool cam_pair(const float4 q0, const float4 q1, const float4 q2,
+                                         const float4 m0, const float4 m1, const float4 m2,
+                                         const float4 mv, const float4 rc, const float dd[3],
+                                         float rx, float ry, float alpha_min, float alpha_max,
+                                         PairEval &pe)
+{
+    if (!(rx >= rc.x && rx <= rc.y && ry >= rc.z && ry <= rc.w)) return false;
+    pe.n[0] = q0.w + q0.x * dd[0] + q0.y * dd[1] + q0.z * dd[2];
+    pe.n[1] = q1.w + q1.x * dd[0] + q1.y * dd[1] + q1.z * dd[2];
+    pe.n[2] = q2.w + q2.x * dd[0] + q2.y * dd[1] + q2.z * dd[2];
+    pe.e[0] = m0.w + m0.x * dd[0] + m0.y * dd[1] + m0.z * dd[2];
+    pe.e[1] = m1.w + m1.x * dd[0] + m1.y * dd[1] + m1.z * dd[2];
+    pe.e[2] = m2.w + m2.x * dd[0] + m2.y * dd[1] + m2.z * dd[2];
+    pe.inv = 1.f / (pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
+    pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
+    pe.tau = (mv.x * pe.e[0] + mv.y * pe.e[1] + mv.z * pe.e[2]) * pe.inv;
+    if (!(pe.tau > 0.f)) return false;
+    pe.rho = __expf(-0.5f * pe.D2);
+    float a = mv.w * pe.rho;
+    pe.clamped = a > alpha_max;
+    pe.alpha = fminf(a, alpha_max);
+    return pe.alpha >= alpha_min;
+}
+
+// LiDAR entries keep per-column quantities (each column has its own sensor
+// origin): common part M (9), f (3), sigma, features (3), box (4); then per
+// column v = mu - o_c (3), a = diag(f) M (v x d_T) (3), u = M v (3).
+constexpr int kLidCommon = 20;
+constexpr int kLidPerCol = 9;
+constexpr int kLidEntry = kLidCommon + kLidPerCol * kLidarColsMax;
+
+// Fill column-independent and per-column parts of entry `lane` of a warp's
+// shared block s[kLidEntry][32].
+__device__ __forceinline__ void lidar_entry(const GRec &r, const float *poses, int col0,
+                                            int ncols, const float dh[3], const float dl[3],
+                                            float (*s)[32], int lane)
+{
+    const float mu[3] = {r.mu_sigma.x, r.mu_sigma.y, r.mu_sigma.z};
+    const float M[9] = {r.m0.x, r.m0.y, r.m0.z, r.m1.x, r.m1.y, r.m1.z, r.m2.x, r.m2.y, r.m2.z};
+    const float f[3] = {r.m0.w, r.m1.w, r.m2.w};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s[k][lane] = M[k];
+    s[9][lane] = f[0];
+    s[10][lane] = f[1];
+    s[11][lane] = f[2];
+    s[12][lane] = r.mu_sigma.w;
+    s[13][lane] = r.feat.x;
+    s[14][lane] = r.feat.y;
+    s[15][lane] = r.feat.z;
+    s[16][lane] = r.rect.x;
+    s[17][lane] = r.rect.y;
+    s[18][lane] = r.rect.z;
+    s[19][lane] = r.rect.w;
+    for (int sl = 0; sl < ncols; ++sl) {
+        const float *Po = poses + 12 * (col0 + sl);
+        const float o[3] = {Po[3], Po[7], Po[11]};
+        float w[3], vh[3];
+        precise_moment(mu, o, dh, dl, w, vh);
+        const int b = kLidCommon + kLidPerCol * sl;
+        s[b + 0][lane] = vh[0];
+        s[b + 1][lane] = vh[1];
+        s[b + 2][lane] = vh[2];
+        s[b + 3][lane] = f[0] * dot3(M, w);
+        s[b + 4][lane] = f[1] * dot3(M + 3, w);
+        s[b + 5][lane] = f[2] * dot3(M + 6, w);
+        s[b + 6][lane] = dot3(M, vh);
+        s[b + 7][lane] = dot3(M + 3, vh);
+        s[b + 8][lane] = dot3(M + 6, vh);
+    }
+}
+
+// Evaluate one LiDAR pair (entry j of the warp's block, column slot `sb`).
+__device__ __forceinline__ bool lidar_pair(float (*s)[32], int j, int sb, float raz, float rel,
+                                           const float dd[3], const float d[3], float alpha_min,
+                                           float alpha_max, PairEval &pe)
+{
+    // azimuth alias of the ray nearest the box centre, then the box test
+    const float bx0 = s[16][j], bx1 = s[17][j];
+    const float kk = rintf((0.5f * (bx0 + bx1) - raz) * (1.f / 360.f));
+    const float ra = raz + 360.f * kk;
+    if (!(ra >= bx0 && ra <= bx1 && rel >= s[18][j] && rel <= s[19][j])) return false;
+    const float vx = s[sb][j], vy = s[sb + 1][j], vz = s[sb + 2][j];
+    const float cr0 = vy * dd[2] - vz * dd[1];
+    const float cr1 = vz * dd[0] - vx * dd[2];
+    const float cr2 = vx * dd[1] - vy * dd[0];
+    pe.n[0] = s[sb + 3][j] + s[9][j] * (s[0][j] * cr0 + s[1][j] * cr1 + s[2][j] * cr2);
+    pe.n[1] = s[sb + 4][j] + s[10][j] * (s[3][j] * cr0 + s[4][j] * cr1 + s[5][j] * cr2);
+    pe.n[2] = s[sb + 5][j] + s[11][j] * (s[6][j] * cr0 + s[7][j] * cr1 + s[8][j] * cr2);
+    pe.e[0] = s[0][j] * d[0] + s[1][j] * d[1] + s[2][j] * d[2];
+    pe.e[1] = s[3][j] * d[0] + s[4][j] * d[1] + s[5][j] * d[2];
+    pe.e[2] = s[6][j] * d[0] + s[7][j] * d[1] + s[8][j] * d[2];
+    pe.inv = 1.f / (pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
+    pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
+    pe.tau = (s[sb + 6][j] * pe.e[0] + s[sb + 7][j] * pe.e[1] + s[sb + 8][j] * pe.e[2]) * pe.inv;
+    if (!(pe.tau > 0.f)) return false;
+    pe.rho = __expf(-0.5f * pe.D2);
+    const float a = s[12][j] * pe.rho;
+    pe.clamped = a > alpha_max;
+    pe.alpha = fminf(a, alpha_max);
+    return pe.alpha >= alpha_min;
+}
+
+// LiDAR ray set-up shared by forward and backward: reference direction of
+// the work item (double, split into two floats), the ray's offset from it
+// and its full direction.
+__device__ __forceinline__ void lidar_ray(const LidarItem &it, const double *item_u, int item_id,
+                                          const float *poses, const float4 e, int c, float dh[3],
+                                          float dl[3], float dd[3], float d[3])
+{
+    const float *Pr = poses + 12 * it.ref_col;
+    const double u0 = item_u[3 * item_id], u1 = item_u[3 * item_id + 1], u2 = item_u[3 * item_id + 2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        double dv = (double)Pr[4 * i] * u0 + (double)Pr[4 * i + 1] * u1 + (double)Pr[4 * i + 2] * u2;
+        dh[i] = (float)dv;
+        dl[i] = (float)(dv - (double)dh[i]);
+    }
+    const float *Pc = poses + 12 * c;
+    const float uf[3] = {(float)u0, (float)u1, (float)u2};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        // R_c (u - u_T) + (R_c - R_ref) u_T
+        dd[i] = (Pc[4 * i] * e.x + Pc[4 * i + 1] * e.y + Pc[4 * i + 2] * e.z) +
+                ((Pc[4 * i] - Pr[4 * i]) * uf[0] + (Pc[4 * i + 1] - Pr[4 * i + 1]) * uf[1] +
+                 (Pc[4 * i + 2] - Pr[4 * i + 2]) * uf[2]);
+        d[i] = dh[i] + dd[i];
+    }
+}
+
+}  // namespace sg

@@ -1,0 +1,471 @@
+// project.cu -- per-Gaussian projection (Sec. 3.2 camera, Sec. 3.3 LiDAR):
+// activation (Sec. 3.1), the unscented transform of 7 sigma points through
+// the sensor model, the extent box, the tile range, ray-based culling
+// (App. B, Proc. 2-3), the depth key and the render record.
+//
+// One thread per Gaussian; every input plane is read once with coalesced
+// 4-byte loads and every output is written once.  The kernel is bound by HBM
+// traffic (about 100 bytes read and 150 written per Gaussian).
+#include <math.h>
+
+#include "internal.h"
+
+namespace sg {
+
+struct CamParams {
+    int model, W, H, ntx, nty;
+    float fx, fy, cx, cy, k0, k1, k2, k3, theta_max;
+    float R[9], t[3];   // camera-to-world rotation (row-major) and centre
+};
+
+struct UTParams {
+    float lam_gamma, w0m, w0c, wi;   // spread sqrt(n+lambda) and the weights
+    float alpha_min, near_dist;
+};
+
+static UTParams ut_params(const sg_render_opts &o)
+{
+    UTParams u;
+    const float n = 3.0f;
+    float a = o.ut_alpha, k = o.ut_kappa, b = o.ut_beta;
+    float lam = a * a * (n + k) - n;
+    u.lam_gamma = sqrtf(n + lam);
+    u.w0m = lam / (n + lam);
+    u.w0c = u.w0m + (1.0f - a * a + b);
+    u.wi = 1.0f / (2.0f * (n + lam));
+    u.alpha_min = o.alpha_min;
+    u.near_dist = o.near_dist;
+    return u;
+}
+
+struct Activated {
+    float mu[3], R[9], s[3], sigma;
+};
+
+__device__ __forceinline__ Activated activate(const float *__restrict__ planes, int64_t pitch,
+                                              int64_t g)
+{
+    Activated a;
+    for (int k = 0; k < 3; ++k) {
+        a.mu[k] = planes[(Scene::kMean + k) * pitch + g];
+        a.s[k] = expf(planes[(Scene::kLogScale + k) * pitch + g]);
+    }
+    float qw = planes[(Scene::kQuat + 0) * pitch + g], qx = planes[(Scene::kQuat + 1) * pitch + g];
+    float qy = planes[(Scene::kQuat + 2) * pitch + g], qz = planes[(Scene::kQuat + 3) * pitch + g];
+    float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+    a.R[0] = 1.f - 2.f * (qy * qy + qz * qz);
+    a.R[1] = 2.f * (qx * qy - qw * qz);
+    a.R[2] = 2.f * (qx * qz + qw * qy);
+    a.R[3] = 2.f * (qx * qy + qw * qz);
+    a.R[4] = 1.f - 2.f * (qx * qx + qz * qz);
+    a.R[5] = 2.f * (qy * qz - qw * qx);
+    a.R[6] = 2.f * (qx * qz - qw * qy);
+    a.R[7] = 2.f * (qy * qz + qw * qx);
+    a.R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    a.sigma = planes[Scene::kOpacity * pitch + g];
+    return a;
+}
+
+// Render record: M = S^-1 R^T (row i = column i of R over s_i) and the
+// cofactor weights f_i = s_i / (s_j s_k) (row i of cof(M) = f_i M_i).
+__device__ __forceinline__ void write_record(GRec *rec, int64_t g, const Activated &a,
+                                             float f0, float f1, float f2, float4 rect)
+{
+    GRec r;
+    r.mu_sigma = make_float4(a.mu[0], a.mu[1], a.mu[2], a.sigma);
+    float i0 = 1.f / a.s[0], i1 = 1.f / a.s[1], i2 = 1.f / a.s[2];
+    r.m0 = make_float4(a.R[0] * i0, a.R[3] * i0, a.R[6] * i0, a.s[0] / (a.s[1] * a.s[2]));
+    r.m1 = make_float4(a.R[1] * i1, a.R[4] * i1, a.R[7] * i1, a.s[1] / (a.s[0] * a.s[2]));
+    r.m2 = make_float4(a.R[2] * i2, a.R[5] * i2, a.R[8] * i2, a.s[2] / (a.s[0] * a.s[1]));
+    r.feat = make_float4(f0, f1, f2, 0.f);
+    r.rect = rect;
+    rec[g] = r;
+}
+
+// Real spherical harmonics of degree <= 3 (normalised, Condon-Shortley
+// phase, m = -l..l order).  Constants: sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!),
+// times sqrt(2) for m != 0, times the leading factor of P_l^|m|.
+__device__ __forceinline__ void sh_colour(const float *__restrict__ planes, int64_t pitch,
+                                          int64_t g, int deg, float x, float y, float z,
+                                          float c[3])
+{
+    float Y[16];
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = 0.28209479177387814f;
+    if (deg >= 1) {
+        Y[1] = -0.48860251190291992f * y;
+        Y[2] = 0.48860251190291992f * z;
+        Y[3] = -0.48860251190291992f * x;
+    }
+    if (deg >= 2) {
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = -1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.f * zz - xx - yy);
+        Y[7] = -1.0925484305920792f * x * z;
+        Y[8] = 0.54627421529603959f * (xx - yy);
+    }
+    if (deg >= 3) {
+        Y[9] = -0.59004358992664352f * y * (3.f * xx - yy);
+        Y[10] = 2.8906114426405538f * x * y * z;
+        Y[11] = -0.45704579946446572f * y * (4.f * zz - xx - yy);
+        Y[12] = 0.37317633259011540f * z * (2.f * zz - 3.f * xx - 3.f * yy);
+        Y[13] = -0.45704579946446572f * x * (4.f * zz - xx - yy);
+        Y[14] = 1.4453057213202769f * z * (xx - yy);
+        Y[15] = -0.59004358992664352f * x * (xx - 3.f * yy);
+    }
+    const int nc = (deg + 1) * (deg + 1);
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.f;
+        for (int k = 0; k < nc; ++k) acc += Y[k] * planes[(Scene::kFeat + 3 * k + ch) * pitch + g];
+        c[ch] = fmaxf(acc + 0.5f, 0.f);
+    }
+}
+
+// Pixel of a world point; returns false outside the model's domain
+// (pinhole: z > near; fisheye: |x| > near and theta <= theta_max).
+__device__ __forceinline__ bool cam_point(const CamParams &C, float near_dist, const float x[3],
+                                          float &u, float &v)
+{
+    float d0 = x[0] - C.t[0], d1 = x[1] - C.t[1], d2 = x[2] - C.t[2];
+    float xc = C.R[0] * d0 + C.R[3] * d1 + C.R[6] * d2;
+    float yc = C.R[1] * d0 + C.R[4] * d1 + C.R[7] * d2;
+    float zc = C.R[2] * d0 + C.R[5] * d1 + C.R[8] * d2;
+    if (C.model == SG_CAMERA_PINHOLE) {
+        if (!(zc > near_dist)) return false;
+        u = C.fx * xc / zc + C.cx;
+        v = C.fy * yc / zc + C.cy;
+        return true;
+    }
+    float r = sqrtf(xc * xc + yc * yc);
+    float dist = sqrtf(xc * xc + yc * yc + zc * zc);
+    float th = atan2f(r, zc);
+    if (!(dist > near_dist) || !(th <= C.theta_max)) return false;
+    float t2 = th * th;
+    float thd = th * (1.f + t2 * (C.k0 + t2 * (C.k1 + t2 * (C.k2 + t2 * C.k3))));
+    if (r > 0.f) {
+        u = C.fx * (thd / r) * xc + C.cx;
+        v = C.fy * (thd / r) * yc + C.cy;
+    } else {
+        u = C.cx;
+        v = C.cy;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(256)
+k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int feature_kind,
+                 int sh_degree, CamParams C, UTParams U, GRec *__restrict__ rec,
+                 float4 *__restrict__ rect_out, int4 *__restrict__ tiles_out,
+                 float *__restrict__ depth_out, uint32_t *__restrict__ count_out,
+                 float2 *__restrict__ mean_out, float4 *__restrict__ cov_out)
+{
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    Activated a = activate(planes, pitch, g);
+    float dx = a.mu[0] - C.t[0], dy = a.mu[1] - C.t[1], dz = a.mu[2] - C.t[2];
+    float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+    depth_out[g] = dist;
+    uint32_t count = 0;
+    float4 rect = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 tl = make_int4(0, -1, 0, -1);
+    float2 m2 = make_float2(0.f, 0.f);
+    float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.sigma >= U.alpha_min) {
+        // sigma points chi_0 = mu, chi_{+-i} = mu +- sqrt(n+lambda) s_i R e_i
+        float uu[7], vv[7];
+        bool ok = cam_point(C, U.near_dist, a.mu, uu[0], vv[0]);
+#pragma unroll
+        for (int p = 1; p < 7; ++p) {
+            int i = (p - 1) >> 1;
+            float sg = ((p - 1) & 1) ? -1.f : 1.f;
+            float x[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) x[r] = a.mu[r] + sg * U.lam_gamma * a.s[i] * a.R[3 * r + i];
+            ok = cam_point(C, U.near_dist, x, uu[p], vv[p]) && ok;
+        }
+        if (ok) {
+            float mu_u = U.w0m * uu[0], mu_v = U.w0m * vv[0];
+#pragma unroll
+            for (int p = 1; p < 7; ++p) { mu_u += U.wi * uu[p]; mu_v += U.wi * vv[p]; }
+            float cxx = 0.f, cxy = 0.f, cyy = 0.f;
+#pragma unroll
+            for (int p = 0; p < 7; ++p) {
+                float w = p == 0 ? U.w0c : U.wi;
+                float eu = uu[p] - mu_u, ev = vv[p] - mu_v;
+                cxx += w * eu * eu;
+                cxy += w * eu * ev;
+                cyy += w * ev * ev;
+            }
+            // extent: the k-sigma box, k = sqrt(2 ln(sigma / alpha_min))
+            float k = sqrtf(2.f * logf(a.sigma / U.alpha_min));
+            float hx = k * sqrtf(cxx), hy = k * sqrtf(cyy);
+            rect = make_float4(mu_u - hx, mu_u + hx, mu_v - hy, mu_v + hy);
+            m2 = make_float2(mu_u, mu_v);
+            cv = make_float4(cxx, cxy, cyy, 0.f);
+            if (rect.y >= 0.f && rect.x < (float)C.W && rect.w >= 0.f && rect.z < (float)C.H) {
+                int x0 = rect.x <= 0.f ? 0 : (int)floorf(rect.x / (float)kTile);
+                int x1 = rect.y >= (float)C.W ? C.ntx - 1 : (int)floorf(rect.y / (float)kTile);
+                int y0 = rect.z <= 0.f ? 0 : (int)floorf(rect.z / (float)kTile);
+                int y1 = rect.w >= (float)C.H ? C.nty - 1 : (int)floorf(rect.w / (float)kTile);
+                x1 = min(x1, C.ntx - 1);
+                y1 = min(y1, C.nty - 1);
+                tl = make_int4(x0, x1, y0, y1);
+                count = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+            }
+        }
+    }
+    count_out[g] = count;
+    rect_out[g] = rect;
+    tiles_out[g] = tl;
+    mean_out[g] = m2;
+    cov_out[g] = cv;
+    if (count == 0) return;
+    float c[3];
+    if (feature_kind == SG_FEATURES_SH) {
+        float inv = 1.f / dist;
+        sh_colour(planes, pitch, g, sh_degree, dx * inv, dy * inv, dz * inv, c);
+    } else {
+        for (int ch = 0; ch < 3; ++ch) c[ch] = planes[(Scene::kFeat + ch) * pitch + g];
+    }
+    write_record(rec, g, a, c[0], c[1], c[2], rect);
+}
+
+sg_status project_camera(const Scene &sc, const Camera &cam, const float c2w[12],
+                         const sg_render_opts &o, Frame &fr, cudaStream_t st)
+{
+    CamParams C;
+    C.model = cam.model;
+    C.W = cam.width;
+    C.H = cam.height;
+    C.ntx = cam.ntx;
+    C.nty = cam.nty;
+    C.fx = cam.fx; C.fy = cam.fy; C.cx = cam.cx; C.cy = cam.cy;
+    C.k0 = cam.k[0]; C.k1 = cam.k[1]; C.k2 = cam.k[2]; C.k3 = cam.k[3];
+    C.theta_max = (float)cam.theta_max;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) C.R[3 * r + c] = c2w[4 * r + c];
+        C.t[r] = c2w[4 * r + 3];
+    }
+    UTParams U = ut_params(o);
+    if (sc.n == 0) return SG_OK;
+    unsigned grid = (unsigned)((sc.n + 255) / 256);
+    k_project_camera<<<grid, 256, 0, st>>>(
+        sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, C, U, (GRec *)fr.rec.p,
+        (float4 *)fr.rect.p, (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p,
+        (float2 *)fr.mean2d.p, (float4 *)fr.cov2d.p);
+    SG_LAUNCHED();
+    return SG_OK;
+}
+
+// ------------------------------------------------------------------ LiDAR
+
+struct LidParams {
+    int n_cols, nphi, n_theta, A, per, pose_iters;
+    float az0, T0, TN;
+    const float *T;
+    const int *sat;
+    const float *poses;   // [n_cols*12]
+};
+
+__device__ __forceinline__ int pmod(int a, int n)
+{
+    int m = a % n;
+    return m < 0 ? m + n : m;
+}
+
+__device__ __forceinline__ void to_sensor(const float *__restrict__ P, const float x[3],
+                                          float xs[3])
+{
+    float d0 = x[0] - P[3], d1 = x[1] - P[7], d2 = x[2] - P[11];
+    xs[0] = P[0] * d0 + P[4] * d1 + P[8] * d2;
+    xs[1] = P[1] * d0 + P[5] * d1 + P[9] * d2;
+    xs[2] = P[2] * d0 + P[6] * d1 + P[10] * d2;
+}
+
+__device__ __forceinline__ int col_of_az(const LidParams &L, float az)
+{
+    return pmod((int)floorf((az - L.az0) * ((float)L.n_cols / 360.0f)), L.n_cols);
+}
+
+// Column whose pose sees the point: start at mid-sweep, then take the
+// column of the point's azimuth `pose_iters` times.
+__device__ __forceinline__ int lidar_col(const LidParams &L, const float x[3], float xs[3])
+{
+    int col = L.n_cols / 2;
+    for (int it = 0; it < L.pose_iters; ++it) {
+        to_sensor(L.poses + 12 * col, x, xs);
+        col = col_of_az(L, atan2f(xs[1], xs[0]) * 57.295779513082321f);
+    }
+    to_sensor(L.poses + 12 * col, x, xs);
+    return col;
+}
+
+__device__ __forceinline__ int elev_tile(const LidParams &L, float el)
+{
+    int lo = 1, hi = L.nphi - 1, e = 0;
+    while (lo <= hi) {
+        int m = (lo + hi) >> 1;
+        if (L.T[m] <= el) { e = m; lo = m + 1; } else hi = m - 1;
+    }
+    return e;
+}
+
+__device__ __forceinline__ int elev_cell(const LidParams &L, float el)
+{
+    int e = elev_tile(L, el);
+    float f = (el - L.T[e]) / (L.T[e + 1] - L.T[e]) * (float)L.per;
+    int sub = !(f >= 0.f) ? 0 : (f >= (float)L.per ? L.per - 1 : (int)floorf(f));
+    return e * L.per + min(sub, L.per - 1);
+}
+
+__device__ __forceinline__ int sat_count(const LidParams &L, int x0, int x1, int y0, int y1)
+{
+    const int H = L.nphi * L.per + 1;
+    return L.sat[(x1 + 1) * H + (y1 + 1)] - L.sat[x0 * H + (y1 + 1)] -
+           L.sat[(x1 + 1) * H + y0] + L.sat[x0 * H + y0];
+}
+
+// Proc. 2 RayOccupancyCount with an azimuth range split at the seam.
+__device__ __forceinline__ int sat_count_wrap(const LidParams &L, int x0, int x1, int y0, int y1)
+{
+    if (x1 - x0 + 1 >= L.A) return sat_count(L, 0, L.A - 1, y0, y1);
+    int a = pmod(x0, L.A), b = pmod(x1, L.A);
+    if (a <= b) return sat_count(L, a, b, y0, y1);
+    return sat_count(L, a, L.A - 1, y0, y1) + sat_count(L, 0, b, y0, y1);
+}
+
+__global__ void __launch_bounds__(256)
+k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidParams L,
+                UTParams U, int cull, GRec *__restrict__ rec, float4 *__restrict__ rect_out,
+                int4 *__restrict__ tiles_out, float *__restrict__ depth_out,
+                uint32_t *__restrict__ count_out, float2 *__restrict__ mean_out,
+                float4 *__restrict__ cov_out)
+{
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    Activated a = activate(planes, pitch, g);
+    float xs[3];
+    lidar_col(L, a.mu, xs);
+    depth_out[g] = sqrtf(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
+    uint32_t count = 0;
+    float4 rect = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 tl = make_int4(0, -1, 0, -1);
+    float2 m2 = make_float2(0.f, 0.f);
+    float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.sigma >= U.alpha_min) {
+        float az[7], el[7];
+        bool ok = true;
+#pragma unroll
+        for (int p = 0; p < 7; ++p) {
+            float x[3];
+            if (p == 0) {
+                x[0] = a.mu[0]; x[1] = a.mu[1]; x[2] = a.mu[2];
+            } else {
+                int i = (p - 1) >> 1;
+                float sg = ((p - 1) & 1) ? -1.f : 1.f;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) x[r] = a.mu[r] + sg * U.lam_gamma * a.s[i] * a.R[3 * r + i];
+            }
+            lidar_col(L, x, xs);
+            float r = sqrtf(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
+            ok = ok && (r > U.near_dist);
+            az[p] = atan2f(xs[1], xs[0]) * 57.295779513082321f;
+            el[p] = asinf(xs[2] / r) * 57.295779513082321f;
+        }
+        if (ok) {
+#pragma unroll
+            for (int p = 1; p < 7; ++p) {   // unwrap to within 180 deg of chi_0
+                float d = az[p] - az[0];
+                if (d > 180.f) az[p] -= 360.f;
+                else if (d < -180.f) az[p] += 360.f;
+            }
+            float ma = U.w0m * az[0], me = U.w0m * el[0];
+#pragma unroll
+            for (int p = 1; p < 7; ++p) { ma += U.wi * az[p]; me += U.wi * el[p]; }
+            float caa = 0.f, cae = 0.f, cee = 0.f;
+#pragma unroll
+            for (int p = 0; p < 7; ++p) {
+                float w = p == 0 ? U.w0c : U.wi;
+                float ea = az[p] - ma, ee = el[p] - me;
+                caa += w * ea * ea;
+                cae += w * ea * ee;
+                cee += w * ee * ee;
+            }
+            float k = sqrtf(2.f * logf(a.sigma / U.alpha_min));
+            float ha = k * sqrtf(caa), he = k * sqrtf(cee);
+            rect = make_float4(ma - ha, ma + ha, me - he, me + he);
+            m2 = make_float2(ma, me);
+            cv = make_float4(caa, cae, cee, 0.f);
+            if (rect.w >= L.T0 && rect.z <= L.TN) {
+                float elo = rect.z < L.T0 ? L.T0 : rect.z;
+                float ehi = rect.w > L.TN ? L.TN : rect.w;
+                int e0 = elev_tile(L, elo), e1 = elev_tile(L, ehi);
+                bool full = !(rect.y - rect.x < 360.f);
+                int a0, a1, na;
+                if (full) {
+                    a0 = 0; a1 = L.n_theta - 1; na = L.n_theta;
+                } else {
+                    float sc = (float)L.n_theta / 360.0f;
+                    a0 = (int)floorf((rect.x - L.az0) * sc);
+                    a1 = (int)floorf((rect.y - L.az0) * sc);
+                    na = a1 - a0 + 1;
+                    if (na > L.n_theta) { na = L.n_theta; a1 = a0 + L.n_theta - 1; }
+                }
+                bool keep = true;
+                if (cull) {   // App. B Proc. 3: keep only if the dense extent holds a ray
+                    int x0, x1;
+                    if (full) { x0 = 0; x1 = L.A - 1; }
+                    else {
+                        float sc = (float)L.A / 360.0f;
+                        x0 = (int)floorf((rect.x - L.az0) * sc);
+                        x1 = (int)floorf((rect.y - L.az0) * sc);
+                    }
+                    keep = sat_count_wrap(L, x0, x1, elev_cell(L, elo), elev_cell(L, ehi)) > 0;
+                }
+                if (keep) {
+                    tl = make_int4(a0, a1, e0, e1);
+                    count = (uint32_t)(na * (e1 - e0 + 1));
+                }
+            }
+        }
+    }
+    count_out[g] = count;
+    rect_out[g] = rect;
+    tiles_out[g] = tl;
+    mean_out[g] = m2;
+    cov_out[g] = cv;
+    if (count == 0) return;
+    write_record(rec, g, a, planes[(Scene::kFeat + 0) * pitch + g],
+                 planes[(Scene::kFeat + 1) * pitch + g], planes[(Scene::kFeat + 2) * pitch + g],
+                 rect);
+}
+
+sg_status project_lidar(const Scene &sc, const Lidar &Ld, const float *d_poses,
+                        const sg_render_opts &o, Frame &fr, cudaStream_t st)
+{
+    LidParams L;
+    L.n_cols = Ld.n_cols;
+    L.nphi = Ld.nphi;
+    L.n_theta = Ld.n_theta;
+    L.A = Ld.cull_az;
+    L.per = Ld.cull_el;
+    L.pose_iters = o.pose_iters;
+    L.az0 = Ld.az0;
+    L.T0 = Ld.T[0];
+    L.TN = Ld.T[Ld.nphi];
+    L.T = Ld.d_T;
+    L.sat = Ld.d_sat;
+    L.poses = d_poses;
+    UTParams U = ut_params(o);
+    if (sc.n == 0) return SG_OK;
+    unsigned grid = (unsigned)((sc.n + 255) / 256);
+    k_project_lidar<<<grid, 256, 0, st>>>(
+        sc.d_planes, sc.pitch, sc.n, L, U, o.cull, (GRec *)fr.rec.p, (float4 *)fr.rect.p,
+        (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p, (float2 *)fr.mean2d.p,
+        (float4 *)fr.cov2d.p);
+    SG_LAUNCHED();
+    return SG_OK;
+}
+
+}  // namespace sg

@@ -1,0 +1,155 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the
+C-ABI binding, run the oracle on the same seeded inputs, and compare.
+
+Tolerances (floating point), from the accuracy target of the renderer:
+  RGB, alpha, LiDAR intensity, drop probability: max abs 1e-4
+  depth / range: relative 1e-3 where alpha > 0
+Integer work (tile ranges, counts, sorted lists) is compared bit-exactly
+against the float32 oracle, the precision in which the kernels take those
+decisions.  A ray or a Gaussian is excluded only when the oracle itself
+reports that a decision lies within rounding distance of its threshold
+(margins below); the excluded fraction is asserted to stay small.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Decision margins under which float rounding may legitimately flip a choice.
+# Each is about 10x the largest disagreement measured between the kernels
+# and the double-precision oracle for the quantity it guards (alpha and T to
+# ~1e-6 relative, tau to ~1e-6 m, box edges to 5e-4 px / 5e-5 deg).
+MARGIN_ALPHA = 1e-5     # |alpha - alpha_min| / alpha_min
+MARGIN_TMIN = 1e-5      # |T' - t_min| / t_min
+MARGIN_TAU = 1e-5       # |tau_max| (metres)
+MARGIN_ORDER = 3e-7     # relative gap of consecutive float32 sort keys (2.5 ulp)
+MARGIN_RECT_PX = 1e-3   # pixels
+MARGIN_RECT_DEG = 1e-4  # degrees
+MARGIN_VALID = 1e-4     # relative margin of near / theta_max / opacity tests
+
+TOL_ABS = 1e-4
+TOL_DEPTH_REL = 1e-3
+
+
+def ambiguous_rays(orc, lidar=False):
+    mr = MARGIN_RECT_DEG if lidar else MARGIN_RECT_PX
+    return ((orc["m_alpha"] < MARGIN_ALPHA) | (orc["m_tmin"] < MARGIN_TMIN) |
+            (orc["m_rect"] < mr) | (orc["m_tau"] < MARGIN_TAU) |
+            (orc["m_order"] < MARGIN_ORDER))
+
+
+def compare_camera_rays(rgb, alpha, depth, orc, max_excluded=0.01, label=""):
+    """rgb [n,3], alpha [n], depth [n] from the GPU for the rays of `orc`."""
+    amb = ambiguous_rays(orc)
+    ok = ~amb
+    e_rgb = np.abs(rgb.astype(np.float64) - orc["out"]).max(axis=1)
+    e_a = np.abs(alpha.astype(np.float64) - orc["alpha"])
+    hit = orc["alpha"] > 0
+    e_d = np.where(hit, np.abs(depth.astype(np.float64) - orc["depth"]) /
+                   np.maximum(orc["depth"], 1e-12), np.abs(depth))
+    bad = ok & ((e_rgb > TOL_ABS) | (e_a > TOL_ABS) | (e_d > TOL_DEPTH_REL))
+    info = dict(rays=len(orc), excluded=int(amb.sum()), max_rgb=float(e_rgb[ok].max(initial=0)),
+                max_alpha=float(e_a[ok].max(initial=0)), max_depth_rel=float(e_d[ok].max(initial=0)),
+                bad=int(bad.sum()))
+    assert amb.mean() <= max_excluded, (label, info)
+    assert not bad.any(), (label, info, np.nonzero(bad)[0][:10])
+    return info
+
+
+def compare_lidar_rays(rng, inten, drop, alpha, orc, max_excluded=0.01, label=""):
+    amb = ambiguous_rays(orc, lidar=True)
+    ok = ~amb
+    o_rng = orc["depth"]
+    o_int = orc["out"][:, 0]
+    o_drop = 1.0 / (1.0 + np.exp(orc["out"][:, 1] - orc["out"][:, 2]))
+    hit = orc["alpha"] > 0
+    e_r = np.where(hit, np.abs(rng - o_rng) / np.maximum(o_rng, 1e-12), np.abs(rng))
+    e_i = np.abs(inten - o_int)
+    e_p = np.abs(drop - o_drop)
+    e_a = np.abs(alpha - orc["alpha"])
+    bad = ok & ((e_r > TOL_DEPTH_REL) | (e_i > TOL_ABS) | (e_p > TOL_ABS) | (e_a > TOL_ABS))
+    info = dict(rays=len(orc), excluded=int(amb.sum()), max_range_rel=float(e_r[ok].max(initial=0)),
+                max_int=float(e_i[ok].max(initial=0)), max_drop=float(e_p[ok].max(initial=0)),
+                max_alpha=float(e_a[ok].max(initial=0)), bad=int(bad.sum()))
+    assert amb.mean() <= max_excluded, (label, info)
+    assert not bad.any(), (label, info, np.nonzero(bad)[0][:10])
+    return info
+
+
+def _near_multiple(x, step, offset, tol):
+    r = (x - offset) / step
+    return np.abs(r - np.round(r)) * step < tol
+
+
+def rect_band_camera(x):
+    """Band (pixels) within which GPU and float32-oracle box edges may differ:
+    a few float32 ulps of the coordinate plus the UT's rounding."""
+    return 1e-3 * np.maximum(1.0, np.abs(x) / 1000.0)
+
+
+RECT_BAND_DEG = 1e-4
+
+
+def tile_ambiguous_camera(P32, W, H, tile=16):
+    """Gaussians whose tile range or cull decision could flip under rounding."""
+    rect = P32["rect"].astype(np.float64)
+    amb = np.zeros(len(P32), bool)
+    ut = P32["ut"] == 1          # boxes exist only where the UT ran
+    for k in range(4):
+        x = rect[:, k]
+        tol = rect_band_camera(x) * ut
+        amb |= _near_multiple(x, tile, 0.0, tol)
+        lim = W if k < 2 else H
+        amb |= np.abs(x - lim) < tol
+        amb |= np.abs(x) < tol
+    amb |= P32["vmargin"] < MARGIN_VALID
+    return amb
+
+
+def tile_ambiguous_lidar(P32, T, n_theta, az0, A, per, tol=RECT_BAND_DEG):
+    rect = P32["rect"].astype(np.float64)
+    amb = np.zeros(len(P32), bool)
+    tol = tol * (P32["ut"] == 1)   # boxes exist only where the UT ran
+    for k in (0, 1):
+        x = rect[:, k]
+        amb |= _near_multiple(x, 360.0 / n_theta, az0, tol)
+        amb |= _near_multiple(x, 360.0 / A, az0, tol)
+    Tb = T.astype(np.float64)
+    for k in (2, 3):
+        x = rect[:, k]
+        d = np.abs(x[:, None] - Tb[None, :]).min(axis=1)
+        amb |= d < tol
+        # dense sub-cells within each elevation tile
+        for j in range(len(Tb) - 1):
+            w = Tb[j + 1] - Tb[j]
+            if w <= 0:
+                continue
+            inside = (x >= Tb[j]) & (x <= Tb[j + 1])
+            amb |= inside & _near_multiple(x, w / per, Tb[j], tol)
+    width = rect[:, 1] - rect[:, 0]
+    amb |= np.abs(width - 360.0) < tol
+    amb |= P32["vmargin"] < MARGIN_VALID
+    return amb
+
+
+def compare_lists(gpu_ids, gpu_ranges, orc_ids, orc_ranges, tiles, amb_gauss, depth_key,
+                  label=""):
+    """Per tile: same Gaussians (ambiguous ones removed) in the same order
+    (near-tied float32 keys may swap)."""
+    checked = 0
+    for t in tiles:
+        g = gpu_ids[gpu_ranges[t, 0]:gpu_ranges[t, 1]]
+        o = orc_ids[orc_ranges[t, 0]:orc_ranges[t, 1]]
+        g = g[~amb_gauss[g]]
+        o = o[~amb_gauss[o]]
+        assert np.array_equal(np.sort(g), np.sort(o)), (label, t, len(g), len(o))
+        if not np.array_equal(g, o):
+            # allowed only between keys within 2 float32 ulps of each other
+            k = depth_key[o].astype(np.float32)
+            pos_g = {int(x): i for i, x in enumerate(g)}
+            for i in range(len(o)):
+                if pos_g[int(o[i])] != i:
+                    near = np.abs(k.view(np.int32).astype(np.int64) -
+                                  np.int64(k[i].view(np.int32))) <= 2
+                    assert near.sum() > 1, (label, t, i)
+        checked += len(g)
+    return checked

@@ -1,0 +1,159 @@
+"""LiDAR path on the GPU (through the C-ABI) against the CPU oracle: the
+elevation tiling, projection with per-column poses, ray-based culling, tile
+lists and rendered range / intensity / drop, plus the invariances the paper
+states (culling and tiling change speed, not results)."""
+import numpy as np
+import pytest
+
+from paper_2510_12901_gb300 import synthetic as syn
+from tests import parity as par
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2510_12901_gb300 import _build
+    _build.build()
+    from paper_2510_12901_gb300 import simgut
+    simgut.load()
+    return simgut
+
+
+def gpu_render(sg, sc, L, opts=None, scene=None, lidar=None):
+    import torch
+    S = scene or sg.Scene(sc)
+    Ld = lidar or sg.Lidar(L)
+    out = sg.render_lidar(S, Ld, L.col_c2w, opts)
+    torch.cuda.synchronize()
+    res = {k: out[k].cpu().numpy().reshape(-1) for k in ("range", "intensity", "drop", "alpha")}
+    res.update(frame=out["frame"], scene=S, lidar=Ld)
+    return res
+
+
+def toy(n=1500, seed=0, n_cols=256):
+    L = syn.street_lidar(n_cols=n_cols)
+    sc = syn.street_scene(n, seed=seed, kind="lidar", length=60.0)
+    return sc, L
+
+
+def test_tiling_matches_oracle(sg, O64):
+    for L in (syn.street_lidar(), syn.street_lidar(n_beams=64, n_cols=1024),
+              syn.street_lidar(max_rays_per_tile=64, n_elev_tiles=32)):
+        T, nth = sg.Lidar(L).tiling()
+        To, ntho = O64.elevation_tiling(L.elevations_deg, L.n_cols, L.n_elev_tiles,
+                                        L.max_rays_per_tile)
+        assert np.array_equal(T, To) and nth == ntho
+
+
+def check_projection(sg, fr, sc, L, O32, label):
+    P32, (nth, nphi) = O32.project_lidar(sc, L)
+    S = O32.lidar_setup(L)
+    count = fr.field(sg.FIELD_COUNT, np.uint32)
+    tiles = fr.field(sg.FIELD_TILES, np.int32, 4)
+    key = fr.field(sg.FIELD_DEPTH, np.float32)
+    amb = par.tile_ambiguous_lidar(P32, S["T"], nth, L.az0_deg, L.cull_az, L.cull_el_per_tile)
+    ok = ~amb
+    assert amb.mean() < 1e-2, (label, amb.sum())
+    rect = fr.field(sg.FIELD_RECT, np.float32, 4)
+    v32 = (P32["valid"] == 1) & (count > 0)
+    d = np.abs(rect[v32].astype(np.float64) - P32["rect"][v32])
+    assert np.all(d <= 0.5 * par.RECT_BAND_DEG + 1e-6 * np.abs(P32["rect"][v32])), (label, d.max())
+    o_count = np.where(P32["valid"] == 1, P32["count"], 0)
+    assert np.array_equal(count[ok], o_count[ok]), (label, np.nonzero(count[ok] != o_count[ok]))
+    v = ok & (o_count > 0)
+    assert np.array_equal(tiles[v], P32["tiles"][v]), label
+    assert np.allclose(key, P32["depth"], rtol=4e-7, atol=0), label
+    return P32, amb, key, nth, nphi
+
+
+def test_toy_sweep_every_ray_and_list(sg, O32, O64):
+    sc, L = toy()
+    g = gpu_render(sg, sc, L)
+    orc = O64.render_lidar(sc, L)
+    info = par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
+                                  label="toy")
+    assert (orc["n_contrib"] > 0).sum() > 1000, info
+    P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, "toy")
+    ids = g["frame"].field(sg.FIELD_PAIR_IDS, np.uint32)
+    ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)
+    o_ids, _, o_ranges = O32.bin_sort(P32, nth, nphi, True)
+    par.compare_lists(ids, ranges, o_ids, o_ranges, range(nth * nphi), amb, key, "toy")
+
+
+def test_culling_changes_nothing_but_the_lists(sg):
+    sc, L = toy(2000, seed=1)
+    a = gpu_render(sg, sc, L)
+    b = gpu_render(sg, sc, L, sg.sg_default_opts(cull=0), scene=a["scene"], lidar=a["lidar"])
+    for k in ("range", "intensity", "drop", "alpha"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["frame"].stats()[0] < b["frame"].stats()[0]
+
+
+def test_tiling_changes_nothing_beyond_rounding(sg):
+    sc, L0 = toy(1200, seed=2)
+    ref = gpu_render(sg, sc, L0)
+    for M, nphi in ((32, 8), (64, 16), (128, 32), (256, 64)):
+        L = syn.Lidar(L0.elevations_deg, L0.n_cols, L0.az0_deg, L0.col_c2w, M, nphi)
+        g = gpu_render(sg, sc, L, scene=ref["scene"])
+        hit = ref["alpha"] > 0
+        assert np.abs(g["alpha"] - ref["alpha"]).max() < 1e-4
+        assert np.abs(g["intensity"] - ref["intensity"]).max() < 1e-4
+        assert (np.abs(g["range"] - ref["range"])[hit] / ref["range"][hit]).max() < 1e-4
+
+
+def test_static_sensor_pose_iterations_irrelevant(sg):
+    sc, _ = toy(1000, seed=3)
+    L = syn.street_lidar(n_cols=256, static=True)
+    a = gpu_render(sg, sc, L, sg.sg_default_opts(pose_iters=0))
+    b = gpu_render(sg, sc, L, sg.sg_default_opts(pose_iters=2), scene=a["scene"],
+                   lidar=a["lidar"])
+    for k in ("range", "intensity", "drop", "alpha"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_ragged_sensor_and_empty_scene(sg, O64):
+    sc, _ = toy(800, seed=4)
+    L = syn.street_lidar(n_beams=64, n_cols=333)    # columns not divisible by N_theta
+    g = gpu_render(sg, sc, L)
+    orc = O64.render_lidar(sc, L)
+    par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
+                           label="ragged")
+    e = gpu_render(sg, sc.subset(np.zeros(0, np.int64)), L)
+    assert not e["alpha"].any() and np.all(e["drop"] == 0.5) and not e["range"].any()
+
+
+def test_host_output_path_matches_device_path(sg):
+    import torch
+    sc, L = toy(600, seed=5)
+    g = gpu_render(sg, sc, L)
+    n = L.n_beams * L.n_cols
+    outs = [np.zeros(n, np.float32) for _ in range(4)]
+    fr = sg.Frame()
+    poses = np.ascontiguousarray(L.col_c2w, np.float32)
+    sg.sg_render_lidar_host(g["scene"].handle, g["lidar"].handle, poses.ctypes.data,
+                            sg.sg_default_opts(), fr.handle, *[o.ctypes.data for o in outs],
+                            torch.cuda.current_stream().cuda_stream)
+    for o, k in zip(outs, ("range", "intensity", "drop", "alpha")):
+        assert np.array_equal(o, g[k]), k
+
+
+def test_full_sweep_sampled_parity(sg, O32, O64):
+    """2M Gaussians, 128 beams x 2048 columns, per-column poses over 0.1 s."""
+    sc = syn.street_scene(2_000_000, seed=10, kind="lidar")
+    L = syn.street_lidar()
+    g = gpu_render(sg, sc, L)
+    rng = np.random.default_rng(0)
+    rays = np.unique(rng.choice(L.n_beams * L.n_cols, 4000, replace=False))
+    orc = O64.render_lidar(sc, L, rays=rays)
+    info = par.compare_lidar_rays(g["range"][rays], g["intensity"][rays], g["drop"][rays],
+                                  g["alpha"][rays], orc, label="full")
+    assert (orc["n_contrib"] > 0).mean() > 0.3, info
+    P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, "full")
+    ids = g["frame"].field(sg.FIELD_PAIR_IDS, np.uint32)
+    ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)
+    o_ids, _, o_ranges = O32.bin_sort(P32, nth, nphi, True)
+    tiles = rng.choice(nth * nphi, 300, replace=False)
+    par.compare_lists(ids, ranges, o_ids, o_ranges, tiles, amb, key, "full")

@@ -76,7 +76,8 @@ def _structs(real):
     class Proj(C.Structure):
         _fields_ = [("valid", C.c_int), ("mean2d", real * 2), ("cov2d", real * 3),
                     ("rect", real * 4), ("tiles", C.c_int * 4), ("count", C.c_int),
-                    ("depth", real), ("pose_col", C.c_int), ("vmargin", real), ("ut", C.c_int)]
+                    ("depth", real), ("pose_col", C.c_int), ("vmargin", real), ("ut", C.c_int),
+                    ("pmargin", real)]
 
     class Ray(C.Structure):
         _fields_ = [("out", real * 3), ("alpha", real), ("depth", real), ("zsum", real),

@@ -597,11 +597,17 @@ void or_project_camera(const or_scene *sc, const or_camera *cam,
  * start from the mid-sweep pose, then `pose_iters` times take the pose of
  * the column containing the point's azimuth; the final transform gives
  * (azimuth, elevation) in degrees. */
-typedef struct { const or_lidar *L; const or_opts *o; int col0; real range0; real margin; } lid_ctx;
+typedef struct {
+    const or_lidar *L; const or_opts *o; int col0; real range0; real margin; real pmargin;
+} lid_ctx;
 
-static int lidar_col_of(const or_lidar *L, real az)
+static int lidar_col_of(const or_lidar *L, real az, real *pmargin)
 {
-    int c = (int)floor((az - RL(L->az0_deg)) * (RL(L->n_cols) / RL(360)));
+    real f = (az - RL(L->az0_deg)) * (RL(L->n_cols) / RL(360));
+    real fr = f - floor(f);
+    real m = fr < RL(0.5) ? fr : RL(1) - fr;
+    if (pmargin && m < *pmargin) *pmargin = m;
+    int c = (int)floor(f);
     return pmod(c, L->n_cols);
 }
 
@@ -622,7 +628,7 @@ static int lidar_point_map(void *vctx, const real x[3], int idx, real y[2])
     for (int it = 0; it < c->o->pose_iters; ++it) {
         to_sensor(L->col_c2w + 12 * col, x, xs);
         real az = atan2(xs[1], xs[0]) * RL(DEG_D);
-        col = lidar_col_of(L, az);
+        col = lidar_col_of(L, az, &c->pmargin);
     }
     to_sensor(L->col_c2w + 12 * col, x, xs);
     real r = sqrt(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
@@ -654,7 +660,7 @@ void or_project_lidar(const or_scene *sc, const or_lidar *L,
             mu[k] = RL(sc->means[3 * g + k]);
         }
         real sigma = RL(sc->opacity[g]), amin = RL(o->alpha_min);
-        lid_ctx ctx = {L, o, 0, 0, RL(1e30)};
+        lid_ctx ctx = {L, o, 0, 0, RL(1e30), RL(1e30)};
         /* depth key: distance to the sensor origin of the centre's column */
         {
             real y[2];
@@ -665,7 +671,9 @@ void or_project_lidar(const or_scene *sc, const or_lidar *L,
         p->vmargin = fabs(sigma - amin) / amin;
         if (!(sigma >= amin)) continue;
         ctx.margin = RL(1e30);
+        ctx.pmargin = RL(1e30);
         int ok = or_unscented(o, mu, R, s, lidar_point_map, &ctx, 1, p->mean2d, p->cov2d);
+        p->pmargin = ctx.pmargin;
         if (ctx.margin < p->vmargin) p->vmargin = ctx.margin;
         if (!ok) continue;
         p->ut = 1;

@@ -90,6 +90,8 @@ typedef struct {
     int pose_col;         /* LiDAR: column whose pose the centre point used */
     real vmargin;         /* min relative margin of the validity tests (near, theta, opacity) */
     int ut;               /* the unscented transform ran (all sigma points valid) */
+    real pmargin;         /* LiDAR: min distance (in columns) of a sigma point's
+                             azimuth to a column boundary in the pose choice */
 } or_proj;
 
 /* Per-ray outputs and statistics. */

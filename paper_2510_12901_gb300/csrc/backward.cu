@@ -102,7 +102,8 @@ __device__ __forceinline__ void composite_grads(const PairEval &pe, float sigma,
 // ------------------------------------------------------------------ camera
 __global__ void __launch_bounds__(kCamThreads)
 k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
-                  const uint2 *__restrict__ ranges, const float4 *__restrict__ pix,
+                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order,
+                  const float4 *__restrict__ pix,
                   const double *__restrict__ tile_dir, const float4 *__restrict__ ray_state,
                   const uint32_t *__restrict__ n_contrib, const float *__restrict__ g_rgb,
                   const float *__restrict__ g_alpha, const float *__restrict__ g_depth,
@@ -113,7 +114,7 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
     __shared__ float s_red[kBwBatch][kCamThreads / 32][kG];
     __shared__ float s_ref[6];
     __shared__ uint32_t s_max;
-    const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = (int)order[blockIdx.x], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = tile % P.ntx, ty = tile / P.ntx;
     const int px = tx * kTile + (tid % kTile), py = ty * kTile + (tid / kTile);
     if (tid == 0) {
@@ -435,7 +436,8 @@ sg_status backward_camera(const Scene &sc, const Camera &cam, Frame &fr, const f
     const CamRender P = cam_render_params(cam, fr.c2w, fr.opts);
     k_backward_camera<<<(unsigned)(cam.ntx * cam.nty), kCamThreads, 0, st>>>(
         P, (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
-        (const uint2 *)fr.ranges.p, cam.d_pix, cam.d_tile_dir, (const float4 *)fr.ray_state.p,
+        (const uint2 *)fr.ranges.p, (const uint32_t *)fr.order.p, cam.d_pix, cam.d_tile_dir,
+        (const float4 *)fr.ray_state.p,
         (const uint32_t *)fr.n_contrib.p, g_rgb, g_alpha, g_depth, (float *)fr.gacc.p);
     SG_LAUNCHED();
     const float o[3] = {fr.c2w[3], fr.c2w[7], fr.c2w[11]};

@@ -416,7 +416,7 @@ void sg_frame_destroy(sg_frame frame)
                    &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.cnt_sorted,
                    &f.offsets, &f.flags, &f.scan_tmp, &f.hist, &f.pkeys[0], &f.pkeys[1],
                    &f.pvals[0], &f.pvals[1], &f.ranges, &f.ray_state, &f.n_contrib, &f.scalars,
-                   &f.gacc};
+                   &f.gacc, &f.order};
     for (Buf *b : bufs) release(*b);
     if (f.h_scalars) cudaFreeHost(f.h_scalars);
     for (auto &e : f.ev)

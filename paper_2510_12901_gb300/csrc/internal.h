@@ -105,7 +105,7 @@ struct Frame {
     // depth sort / offsets
     Buf dkeys[2], dvals[2], cnt_sorted, offsets, flags, scan_tmp, hist;
     // pairs
-    Buf pkeys[2], pvals[2], ranges;
+    Buf pkeys[2], pvals[2], ranges, order;
     // per-ray saved state: (T_final, omega, Z, LiDAR drop) and contributor count
     Buf ray_state, n_contrib;
     // backward accumulators: per Gaussian dL/dM (9), dL/dmu (3), dL/dsigma,

@@ -18,10 +18,12 @@
 //   cof(M)(v x d) = a + P dd,  a = diag(f) M (v x d_T),  P = diag(f) M [v]_x.
 // Float arithmetic throughout, no double-precision work in the per-pair loop.
 //
-// Camera: one 256-thread CTA per 16x16 tile; batches of 256 list entries are
-// staged through shared memory (one entry per thread, preprocessed), and the
-// CTA stops once every pixel's transmittance is below t_min.  LiDAR: one warp
-// per work item (<= 32 rays of one tile, <= 4 columns); batches of 32.
+// Camera: one 256-thread CTA per 16x16 tile, launched longest list first;
+// batches of 256 list entries are staged through shared memory (one entry
+// per thread, preprocessed); each warp walks only the entries overlapping its
+// 8x4 sub-block; the CTA stops once every pixel's transmittance is below
+// t_min.  LiDAR: one warp per work item (<= 32 rays of one tile, <= 4
+// columns); batches of 32.
 //
 // Per ray the kernels save (T_final, omega, Z, drop) and the number of list
 // entries up to the last composited one, which is all the backward needs.
@@ -32,19 +34,57 @@
 
 namespace sg {
 
+// Tile order for the camera kernels: tiles sorted (coarsely) by decreasing
+// list length, so that the longest tiles start first and do not form the
+// tail of the launch.  One CTA buckets the tiles by floor(log2(length)).
+__global__ void __launch_bounds__(1024)
+k_tile_order(const uint2 *__restrict__ ranges, int ntiles, uint32_t *__restrict__ order)
+{
+    __shared__ uint32_t s_cnt[33], s_off[33];
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t len = ranges[t].y - ranges[t].x;
+        const int b = len ? 32 - __clz(len) : 0;       // 0 (empty) .. 32
+        atomicAdd(&s_cnt[32 - b], 1u);                   // longest bucket first
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < 33; ++i) { s_off[i] = run; run += s_cnt[i]; }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t len = ranges[t].y - ranges[t].x;
+        const int b = len ? 32 - __clz(len) : 0;
+        order[atomicAdd(&s_off[32 - b], 1u)] = (uint32_t)t;
+    }
+}
+
+// Camera compositing.  The 16x16 tile is split into eight 8x4 pixel
+// sub-blocks, one per warp.  Each batch of up to 256 list entries is
+// preprocessed into shared memory once (one entry per thread); each warp
+// then compacts, in list order, the entries whose extent box overlaps its
+// sub-block and walks only those, branch-free, so that a far Gaussian a
+// pixel wide costs one warp instead of eight.
 __global__ void __launch_bounds__(kCamThreads)
 k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
-                const uint2 *__restrict__ ranges, const float4 *__restrict__ pix,
-                const double *__restrict__ tile_dir, float *__restrict__ out_rgb,
-                float *__restrict__ out_alpha, float *__restrict__ out_depth,
-                float4 *__restrict__ ray_state, uint32_t *__restrict__ n_contrib)
+                const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order,
+                const float4 *__restrict__ pix, const double *__restrict__ tile_dir,
+                float *__restrict__ out_rgb, float *__restrict__ out_alpha,
+                float *__restrict__ out_depth, float4 *__restrict__ ray_state,
+                uint32_t *__restrict__ n_contrib)
 {
     __shared__ float4 s_e[9][kCamThreads];
+    __shared__ uint8_t s_mask[kCamThreads];
+    __shared__ uint8_t s_list[kCamThreads / 32][kCamThreads];
     __shared__ float s_ref[6];
-    const int tile = blockIdx.x;
-    const int tid = threadIdx.x;
+    const int tile = (int)order[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = tile % P.ntx, ty = tile / P.ntx;
-    const int px = tx * kTile + (tid % kTile), py = ty * kTile + (tid / kTile);
+    // warp w: columns 8*(w&1) .. +7, rows 4*(w>>1) .. +3 of the tile
+    const int sbx = tx * kTile + 8 * (warp & 1), sby = ty * kTile + 4 * (warp >> 1);
+    const int px = sbx + (lane & 7), py = sby + (lane >> 3);
     if (tid == 0) cam_tile_ref(P, tile_dir, tile, s_ref);
     __syncthreads();
     const float dh[3] = {s_ref[0], s_ref[1], s_ref[2]};
@@ -62,30 +102,54 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
     for (uint32_t base = rg.x; base < rg.y; base += kCamThreads) {
         if (__syncthreads_count(done) == kCamThreads) break;
         const uint32_t idx = base + tid;
+        uint8_t m = 0;
         if (idx < rg.y) {
             float4 ent[9];
             cam_entry(rec[ids[idx]], P.t, dh, dl, ent);
 #pragma unroll
             for (int k = 0; k < 9; ++k) s_e[k][tid] = ent[k];
+            // sub-blocks whose pixel centres the box can contain
+            const float4 rc = ent[8];
+#pragma unroll
+            for (int w = 0; w < kCamThreads / 32; ++w) {
+                const float x0 = (float)(tx * kTile + 8 * (w & 1)) + 0.5f;
+                const float y0 = (float)(ty * kTile + 4 * (w >> 1)) + 0.5f;
+                if (rc.x <= x0 + 7.f && rc.y >= x0 && rc.z <= y0 + 3.f && rc.w >= y0)
+                    m |= (uint8_t)(1u << w);
+            }
         }
+        s_mask[tid] = m;
         __syncthreads();
-        const int cnt = min((uint32_t)kCamThreads, rg.y - base);
-        for (int j = 0; j < cnt && !done; ++j) {
+        // this warp's entries, in list order
+        int n = 0;
+#pragma unroll
+        for (int c = 0; c < kCamThreads / 32; ++c) {
+            const bool mine = (s_mask[c * 32 + lane] >> warp) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+            if (mine) s_list[warp][n + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(c * 32 + lane);
+            n += __popc(bal);
+        }
+        __syncwarp();
+        for (int i = 0; i < n; ++i) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const int j = s_list[warp][i];
             PairEval pe;
-            if (!cam_pair(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j], s_e[5][j],
-                          s_e[6][j], s_e[8][j], dd, rx, ry, P.alpha_min, P.alpha_max, pe))
-                continue;
+            bool ok = cam_pair(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j], s_e[5][j],
+                               s_e[6][j], s_e[8][j], dd, rx, ry, P.alpha_min, P.alpha_max, pe);
+            ok = ok && !done;
             const float Tn = T * (1.f - pe.alpha);
-            if (Tn < P.t_min) { done = true; break; }
-            const float wgt = pe.alpha * T;
+            const bool stop = ok && Tn < P.t_min;
+            done = done || stop;
+            ok = ok && !stop;
+            const float wgt = ok ? pe.alpha * T : 0.f;
             const float4 col = s_e[7][j];
             c0 += wgt * col.x;
             c1 += wgt * col.y;
             c2 += wgt * col.z;
             Z += wgt * pe.tau;
             W += wgt;
-            T = Tn;
-            last = base + j + 1 - rg.x;
+            T = ok ? Tn : T;
+            last = ok ? base + j + 1 - rg.x : last;
         }
     }
     if (!inside) return;
@@ -104,10 +168,16 @@ sg_status render_camera(const Camera &cam, const float c2w[12], const sg_render_
                         Frame &fr, float *rgb, float *alpha, float *depth, cudaStream_t st)
 {
     const CamRender P = cam_render_params(cam, c2w, o);
+    const int nt = cam.ntx * cam.nty;
+    sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
+    if (s != SG_OK) return s;
+    k_tile_order<<<1, 1024, 0, st>>>((const uint2 *)fr.ranges.p, nt, (uint32_t *)fr.order.p);
+    SG_LAUNCHED();
     const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
-    k_render_camera<<<(unsigned)(cam.ntx * cam.nty), kCamThreads, 0, st>>>(
-        P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, cam.d_pix, cam.d_tile_dir,
-        rgb, alpha, depth, (float4 *)fr.ray_state.p, (uint32_t *)fr.n_contrib.p);
+    k_render_camera<<<(unsigned)nt, kCamThreads, 0, st>>>(
+        P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, (const uint32_t *)fr.order.p,
+        cam.d_pix, cam.d_tile_dir, rgb, alpha, depth, (float4 *)fr.ray_state.p,
+        (uint32_t *)fr.n_contrib.p);
     SG_LAUNCHED();
     return SG_OK;
 }

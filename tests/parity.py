@@ -80,55 +80,58 @@ def _near_multiple(x, step, offset, tol):
     return np.abs(r - np.round(r)) * step < tol
 
 
-def rect_band_camera(x):
-    """Band (pixels) within which GPU and float32-oracle box edges may differ:
-    a few float32 ulps of the coordinate plus the UT's rounding."""
-    return 1e-3 * np.maximum(1.0, np.abs(x) / 1000.0)
+def rect_band(P32, P64, floor):
+    """Per-Gaussian, per-edge band within which two float32 implementations
+    of the box may disagree: 8x the disagreement between the oracle's float32
+    and double builds (its own rounding sensitivity), plus a small floor."""
+    d = np.abs(P32["rect"].astype(np.float64) - P64["rect"])
+    both = (P32["ut"] == 1) & (P64["ut"] == 1)
+    d[~both] = 0.0
+    return floor + 8.0 * d + 1e-6 * np.abs(P64["rect"])
 
 
-RECT_BAND_DEG = 1e-4
+MARGIN_POSE_COLS = 3e-4   # LiDAR: sigma point within ~4 float32 ulps (at 180 deg) of a column boundary
 
 
-def tile_ambiguous_camera(P32, W, H, tile=16):
+def _near(x, step, offset, tol):
+    r = (x - offset) / step
+    return np.abs(r - np.round(r)) * step < tol
+
+
+def tile_ambiguous_camera(P32, P64, W, H, tile=16):
     """Gaussians whose tile range or cull decision could flip under rounding."""
-    rect = P32["rect"].astype(np.float64)
-    amb = np.zeros(len(P32), bool)
-    ut = P32["ut"] == 1          # boxes exist only where the UT ran
+    rect = P64["rect"]
+    band = rect_band(P32, P64, 2e-4)
+    amb = (P32["ut"] != P64["ut"]) | (P32["vmargin"] < MARGIN_VALID)
+    ut = P64["ut"] == 1
     for k in range(4):
-        x = rect[:, k]
-        tol = rect_band_camera(x) * ut
-        amb |= _near_multiple(x, tile, 0.0, tol)
+        x, t = rect[:, k], band[:, k]
         lim = W if k < 2 else H
-        amb |= np.abs(x - lim) < tol
-        amb |= np.abs(x) < tol
-    amb |= P32["vmargin"] < MARGIN_VALID
-    return amb
+        amb |= ut & (_near(x, tile, 0.0, t) | (np.abs(x - lim) < t) | (np.abs(x) < t))
+    return amb, band
 
 
-def tile_ambiguous_lidar(P32, T, n_theta, az0, A, per, tol=RECT_BAND_DEG):
-    rect = P32["rect"].astype(np.float64)
-    amb = np.zeros(len(P32), bool)
-    tol = tol * (P32["ut"] == 1)   # boxes exist only where the UT ran
+def tile_ambiguous_lidar(P32, P64, T, n_theta, az0, A, per):
+    rect = P64["rect"]
+    band = rect_band(P32, P64, 2e-5)
+    amb = (P32["ut"] != P64["ut"]) | (P32["vmargin"] < MARGIN_VALID)
+    ut = P64["ut"] == 1
+    amb |= ut & (P64["pmargin"] < MARGIN_POSE_COLS)
     for k in (0, 1):
-        x = rect[:, k]
-        amb |= _near_multiple(x, 360.0 / n_theta, az0, tol)
-        amb |= _near_multiple(x, 360.0 / A, az0, tol)
+        x, t = rect[:, k], band[:, k]
+        amb |= ut & (_near(x, 360.0 / n_theta, az0, t) | _near(x, 360.0 / A, az0, t))
     Tb = T.astype(np.float64)
     for k in (2, 3):
-        x = rect[:, k]
-        d = np.abs(x[:, None] - Tb[None, :]).min(axis=1)
-        amb |= d < tol
-        # dense sub-cells within each elevation tile
-        for j in range(len(Tb) - 1):
+        x, t = rect[:, k], band[:, k]
+        amb |= ut & (np.abs(x[:, None] - Tb[None, :]).min(axis=1) < t)
+        for j in range(len(Tb) - 1):     # dense sub-cells within each elevation tile
             w = Tb[j + 1] - Tb[j]
             if w <= 0:
                 continue
             inside = (x >= Tb[j]) & (x <= Tb[j + 1])
-            amb |= inside & _near_multiple(x, w / per, Tb[j], tol)
-    width = rect[:, 1] - rect[:, 0]
-    amb |= np.abs(width - 360.0) < tol
-    amb |= P32["vmargin"] < MARGIN_VALID
-    return amb
+            amb |= ut & inside & _near(x, w / per, Tb[j], t)
+    amb |= ut & (np.abs(rect[:, 1] - rect[:, 0] - 360.0) < band[:, 0] + band[:, 1])
+    return amb, band
 
 
 def compare_lists(gpu_ids, gpu_ranges, orc_ids, orc_ranges, tiles, amb_gauss, depth_key,

@@ -48,19 +48,22 @@ def test_tiling_matches_oracle(sg, O64):
         assert np.array_equal(T, To) and nth == ntho
 
 
-def check_projection(sg, fr, sc, L, O32, label):
+def check_projection(sg, fr, sc, L, O32, O64, label):
     P32, (nth, nphi) = O32.project_lidar(sc, L)
+    P64, _ = O64.project_lidar(sc, L)
     S = O32.lidar_setup(L)
     count = fr.field(sg.FIELD_COUNT, np.uint32)
     tiles = fr.field(sg.FIELD_TILES, np.int32, 4)
     key = fr.field(sg.FIELD_DEPTH, np.float32)
-    amb = par.tile_ambiguous_lidar(P32, S["T"], nth, L.az0_deg, L.cull_az, L.cull_el_per_tile)
-    ok = ~amb
-    assert amb.mean() < 1e-2, (label, amb.sum())
     rect = fr.field(sg.FIELD_RECT, np.float32, 4)
-    v32 = (P32["valid"] == 1) & (count > 0)
-    d = np.abs(rect[v32].astype(np.float64) - P32["rect"][v32])
-    assert np.all(d <= 0.5 * par.RECT_BAND_DEG + 1e-6 * np.abs(P32["rect"][v32])), (label, d.max())
+    amb, band = par.tile_ambiguous_lidar(P32, P64, S["T"], nth, L.az0_deg, L.cull_az,
+                                         L.cull_el_per_tile)
+    ok = ~amb
+    # 14 column-pose decisions per Gaussian make ~1% of them ambiguous
+    assert amb.mean() < 2e-2, (label, amb.sum())
+    v = ok & (P64["ut"] == 1)
+    d = np.abs(rect[v].astype(np.float64) - P32["rect"][v])
+    assert np.all(d <= 0.5 * band[v]), (label, d.max(), (d / band[v]).max())
     o_count = np.where(P32["valid"] == 1, P32["count"], 0)
     assert np.array_equal(count[ok], o_count[ok]), (label, np.nonzero(count[ok] != o_count[ok]))
     v = ok & (o_count > 0)
@@ -76,7 +79,7 @@ def test_toy_sweep_every_ray_and_list(sg, O32, O64):
     info = par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
                                   label="toy")
     assert (orc["n_contrib"] > 0).sum() > 1000, info
-    P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, "toy")
+    P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, O64, "toy")
     ids = g["frame"].field(sg.FIELD_PAIR_IDS, np.uint32)
     ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)
     o_ids, _, o_ranges = O32.bin_sort(P32, nth, nphi, True)
@@ -151,7 +154,7 @@ def test_full_sweep_sampled_parity(sg, O32, O64):
     info = par.compare_lidar_rays(g["range"][rays], g["intensity"][rays], g["drop"][rays],
                                   g["alpha"][rays], orc, label="full")
     assert (orc["n_contrib"] > 0).mean() > 0.3, info
-    P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, "full")
+    P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, O64, "full")
     ids = g["frame"].field(sg.FIELD_PAIR_IDS, np.uint32)
     ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)
     o_ids, _, o_ranges = O32.bin_sort(P32, nth, nphi, True)

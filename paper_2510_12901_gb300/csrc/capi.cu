@@ -219,10 +219,6 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
 
 using namespace sg;
 
-struct sg_scene_s { Scene s; };
-struct sg_camera_s { Camera c; };
-struct sg_lidar_s { Lidar l; };
-struct sg_frame_s { Frame f; };
 
 extern "C" {
 
@@ -416,7 +412,7 @@ void sg_frame_destroy(sg_frame frame)
                    &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.cnt_sorted,
                    &f.offsets, &f.flags, &f.scan_tmp, &f.hist, &f.pkeys[0], &f.pkeys[1],
                    &f.pvals[0], &f.pvals[1], &f.ranges, &f.ray_state, &f.n_contrib, &f.scalars,
-                   &f.gacc, &f.order};
+                   &f.gacc, &f.order, &f.submask};
     for (Buf *b : bufs) release(*b);
     if (f.h_scalars) cudaFreeHost(f.h_scalars);
     for (auto &e : f.ev)

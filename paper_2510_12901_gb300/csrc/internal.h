@@ -105,7 +105,7 @@ struct Frame {
     // depth sort / offsets
     Buf dkeys[2], dvals[2], cnt_sorted, offsets, flags, scan_tmp, hist;
     // pairs
-    Buf pkeys[2], pvals[2], ranges, order;
+    Buf pkeys[2], pvals[2], ranges, order, submask;
     // per-ray saved state: (T_final, omega, Z, LiDAR drop) and contributor count
     Buf ray_state, n_contrib;
     // backward accumulators: per Gaussian dL/dM (9), dL/dmu (3), dL/dsigma,
@@ -175,6 +175,12 @@ sg_status backward_lidar(const Scene &sc, const Lidar &L, Frame &fr, const float
                          const sg_grads &g, cudaStream_t st);
 
 }  // namespace sg
+
+// the opaque handle types of the C-ABI
+struct sg_scene_s { sg::Scene s; };
+struct sg_camera_s { sg::Camera c; };
+struct sg_lidar_s { sg::Lidar l; };
+struct sg_frame_s { sg::Frame f; };
 
 // ---------------------------------------------------------------- device math
 #ifdef __CUDACC__

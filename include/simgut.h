@@ -180,6 +180,31 @@ sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_co
                                void *stream);
 
 /* ----------------------------------------------------------------------
+ * Camera render that allocates nothing.  The paper has no counterpart: this
+ * is a deployment variant of sg_render_camera for callers that must not
+ * allocate device memory while they run (for example when another
+ * allocator already holds the device's memory, or when the implicit
+ * device-wide synchronisation of cudaMalloc / cudaFree is not acceptable in
+ * their loop).  The whole workspace lives in one file-scope device array of
+ * about 12 MB that every GPU which loads the library keeps until the process
+ * exits.  Limits: at most 32768 Gaussians, 65536 pixels (256 tiles of
+ * 16x16) and 262144 (tile, Gaussian) pairs; larger inputs return
+ * SG_ERR_INVALID (sizes) or SG_ERR_OVERFLOW (pairs) with a message.
+ * Arguments and outputs are those of sg_render_camera without the frame:
+ * no state is kept for a backward pass.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (other threads or
+ * streams of the same device) race and must be serialised by the caller.
+ * Nothing in the array needs clearing between calls: every stage writes the
+ * parts it later reads.  Like sg_render_camera, the call waits once for the
+ * pair count.
+ * ---------------------------------------------------------------------- */
+sg_status sg_render_camera_static(sg_scene scene, sg_camera cam, const float h_c2w[12],
+                                  const sg_render_opts *opts, float *d_rgb, float *d_alpha,
+                                  float *d_depth, void *stream);
+
+/* ----------------------------------------------------------------------
  * Backward (the differentiable renderer of Sec. 3.2 / 3.4).  Given the
  * upstream gradients of the last render in `frame` (device, same shapes as
  * the outputs; NULL = zero), accumulates dL/d parameters into caller-owned

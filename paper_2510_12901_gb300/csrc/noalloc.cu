@@ -1,0 +1,191 @@
+// noalloc.cu -- sg_render_camera_static: the camera render for small
+// workloads with every byte of its workspace in one file-scope device array,
+// for callers that must not allocate device memory while they run (their
+// device memory is held by another allocator, or a cudaMalloc / cudaFree,
+// which can block on the whole device, is not acceptable in their loop).
+// The paper has no counterpart; this is a deployment variant of the same
+// kernels.
+#include <string.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace sg {
+
+// Stated limits of the static workspace.
+constexpr int64_t kStMaxGauss = 32768;     // Gaussians in the scene
+constexpr int64_t kStMaxRays = 65536;      // pixels (width x height)
+constexpr int64_t kStMaxTiles = 256;       // 16x16 tiles
+constexpr int64_t kStMaxPairs = 262144;    // (tile, Gaussian) pairs
+
+// byte layout of the workspace (every piece 256-byte aligned)
+constexpr size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t kStRec = al(sizeof(GRec) * kStMaxGauss);
+constexpr size_t kStG16 = al(16 * kStMaxGauss);       // float4 / int4 per Gaussian
+constexpr size_t kStG8 = al(8 * kStMaxGauss);
+constexpr size_t kStG4 = al(4 * kStMaxGauss);
+constexpr size_t kStP4 = al(4 * kStMaxPairs);
+constexpr size_t kStHist = al(4 * 2 * 256 * ((kStMaxPairs + 2047) / 2048));
+constexpr size_t kStScan = al(4 * 4096);
+constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, tiles, cov2d, mean2d
+                            2 * kStG4 +                          // depth, count
+                            4 * kStG4 +                          // depth-sort keys/values x2
+                            2 * kStG4 + 2 * kStG4 +              // cnt_sorted, offsets, flags
+                            4 * kStP4 +                          // pair keys/values x2
+                            kStHist + kStScan +
+                            al(8 * kStMaxTiles) + al(4 * kStMaxTiles) +  // ranges, order
+                            al(16 * kStMaxRays) + al(4 * kStMaxRays) +   // ray state, contributors
+                            al(kStMaxPairs) +                            // sub-block masks
+                            al(64);                                      // device scalars
+
+static __device__ __align__(256) unsigned char g_static_ws[kStBytes];
+
+// Device address of the array, looked up once per device (under a lock)
+// with that device current.
+static std::mutex g_ws_mu;
+static void *g_ws_addr[128];
+
+static sg_status static_workspace(unsigned char **out)
+{
+    int dev = 0;
+    SG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) {
+        set_error("device ordinal %d out of range", dev);
+        return SG_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    if (!g_ws_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static workspace)");
+        g_ws_addr[dev] = p;
+    }
+    *out = (unsigned char *)g_ws_addr[dev];
+    return SG_OK;
+}
+
+static void carve(Buf &b, unsigned char *&cur, size_t bytes)
+{
+    b.p = cur;
+    b.bytes = bytes;
+    cur += bytes;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
+                                             const float h_c2w[12], const sg_render_opts *opts,
+                                             float *d_rgb, float *d_alpha, float *d_depth,
+                                             void *stream)
+{
+    if (!scene || !cam || !h_c2w || !opts) {
+        set_error("sg_render_camera_static: NULL argument");
+        return SG_ERR_INVALID;
+    }
+    const Scene &sc = scene->s;
+    const Camera &c = cam->c;
+    const int64_t nr = (int64_t)c.width * c.height, nt = (int64_t)c.ntx * c.nty;
+    if (sc.feature_kind == SG_FEATURES_LIDAR) {
+        set_error("sg_render_camera_static: scene carries LiDAR features");
+        return SG_ERR_INVALID;
+    }
+    if (sc.n > kStMaxGauss || nr > kStMaxRays || nt > kStMaxTiles) {
+        set_error("sg_render_camera_static: %lld Gaussians / %lld pixels / %lld tiles exceed the "
+                  "static workspace (at most %lld / %lld / %lld)",
+                  (long long)sc.n, (long long)nr, (long long)nt, (long long)kStMaxGauss,
+                  (long long)kStMaxRays, (long long)kStMaxTiles);
+        return SG_ERR_INVALID;
+    }
+    if (!(opts->alpha_min > 0.f && opts->alpha_min < 1.f) ||
+        !(opts->alpha_max > 0.f && opts->alpha_max <= 1.f) ||
+        !(opts->t_min >= 0.f && opts->t_min < 1.f) || !(opts->near_dist > 0.f) ||
+        !(opts->ut_alpha > 0.f) || !(opts->ut_kappa > -3.f)) {
+        set_error("sg_render_camera_static: render options out of range");
+        return SG_ERR_INVALID;
+    }
+    unsigned char *base = nullptr;
+    sg_status s = static_workspace(&base);
+    if (s != SG_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // a frame whose buffers all point into the static array; every buffer
+    // is sized for the limits above, so no launcher ever needs to grow one
+    Frame fr;
+    unsigned char *cur = base;
+    carve(fr.rec, cur, kStRec);
+    carve(fr.rect, cur, kStG16);
+    carve(fr.tiles, cur, kStG16);
+    carve(fr.cov2d, cur, kStG16);
+    carve(fr.mean2d, cur, kStG8);
+    carve(fr.depth, cur, kStG4);
+    carve(fr.count, cur, kStG4);
+    for (int i = 0; i < 2; ++i) {
+        carve(fr.dkeys[i], cur, kStG4);
+        carve(fr.dvals[i], cur, kStG4);
+    }
+    carve(fr.cnt_sorted, cur, kStG4);
+    carve(fr.offsets, cur, kStG4);
+    carve(fr.flags, cur, 2 * kStG4);
+    for (int i = 0; i < 2; ++i) {
+        carve(fr.pkeys[i], cur, kStP4);
+        carve(fr.pvals[i], cur, kStP4);
+    }
+    carve(fr.hist, cur, kStHist);
+    carve(fr.scan_tmp, cur, kStScan);
+    carve(fr.ranges, cur, al(8 * kStMaxTiles));
+    carve(fr.order, cur, al(4 * kStMaxTiles));
+    carve(fr.ray_state, cur, al(16 * kStMaxRays));
+    carve(fr.n_contrib, cur, al(4 * kStMaxRays));
+    carve(fr.submask, cur, al(kStMaxPairs));
+    carve(fr.scalars, cur, al(64));
+    fr.n_gauss = sc.n;
+    fr.n_rays = nr;
+    fr.n_tiles = nt;
+    fr.kind = 0;
+    fr.opts = *opts;
+    memcpy(fr.c2w, h_c2w, sizeof(fr.c2w));
+
+    // the stages of sg_render_camera: project, depth sort, offsets, pair
+    // count, binning, tile sort, ranges, compositing
+    const int64_t n = sc.n;
+    if ((s = project_camera(sc, c, h_c2w, *opts, fr, st)) != SG_OK) return s;
+    uint32_t *scal = (uint32_t *)fr.scalars.p;
+    uint32_t *dk[2] = {(uint32_t *)fr.dkeys[0].p, (uint32_t *)fr.dkeys[1].p};
+    uint32_t *dv[2] = {(uint32_t *)fr.dvals[0].p, (uint32_t *)fr.dvals[1].p};
+    if ((s = compact_valid((const uint32_t *)fr.count.p, (const float *)fr.depth.p, n, dk[0],
+                           dv[0], scal, fr, st)) != SG_OK)
+        return s;
+    int rb = 0;
+    if ((s = radix_sort_pairs(dk, dv, n, scal, 0, 32, fr, st, &rb)) != SG_OK) return s;
+    if ((s = gather_counts(dv[rb], (const uint32_t *)fr.count.p, scal, n,
+                           (uint32_t *)fr.cnt_sorted.p, st)) != SG_OK)
+        return s;
+    if ((s = scan_exclusive_u32((const uint32_t *)fr.cnt_sorted.p, (uint32_t *)fr.offsets.p,
+                                scal + 1, n, fr, st)) != SG_OK)
+        return s;
+    uint32_t hs[2] = {0, 0};
+    SG_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    const int64_t K = hs[1];
+    if (K > kStMaxPairs) {
+        set_error("sg_render_camera_static: %lld (tile, Gaussian) pairs exceed the static "
+                  "workspace (at most %lld)", (long long)K, (long long)kStMaxPairs);
+        return SG_ERR_OVERFLOW;
+    }
+    fr.n_pairs = K;
+    uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
+    uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
+    if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, scal, n, (const int4 *)fr.tiles.p,
+                       c.ntx, 0, pk[0], pv[0], st)) != SG_OK)
+        return s;
+    int bits = 1;
+    while (((int64_t)1 << bits) < nt) ++bits;
+    int pb = 0;
+    if ((s = radix_sort_pairs(pk, pv, K, scal + 1, 0, bits, fr, st, &pb)) != SG_OK) return s;
+    fr.pair_buf = pb;
+    if ((s = tile_ranges(pk[pb], K, (uint2 *)fr.ranges.p, nt, st)) != SG_OK) return s;
+    return render_camera(c, h_c2w, *opts, fr, d_rgb, d_alpha, d_depth, st);
+}

@@ -80,6 +80,8 @@ _SIGNATURES = {
                                         C.POINTER(sg_render_opts), _H, _P, _P, _P, _P]),
     "sg_render_lidar_host": (C.c_int, [_H, _H, _P, C.POINTER(sg_render_opts), _H, _P, _P, _P,
                                        _P, _P]),
+    "sg_render_camera_static": (C.c_int, [_H, _H, C.POINTER(C.c_float),
+                                          C.POINTER(sg_render_opts), _P, _P, _P, _P]),
     "sg_backward_camera": (C.c_int, [_H, _H, _P, _P, _P, C.POINTER(sg_grads), _P]),
     "sg_backward_lidar": (C.c_int, [_H, _H, _P, _P, _P, _P, C.POINTER(sg_grads), _P]),
     "sg_frame_field": (C.c_int, [_H, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
@@ -226,6 +228,11 @@ def sg_render_lidar_host(scene, lid, h_col_c2w, opts, frame, h_range, h_int, h_d
     _check(load().sg_render_lidar_host(scene, lid, _P(h_col_c2w), C.byref(opts), frame,
                                        _P(h_range), _P(h_int), _P(h_drop), _P(h_alpha),
                                        _P(stream)))
+
+
+def sg_render_camera_static(scene, cam, c2w, opts, d_rgb, d_alpha, d_depth, stream=0):
+    _check(load().sg_render_camera_static(scene, cam, _pose12(c2w), C.byref(opts), _P(d_rgb),
+                                          _P(d_alpha), _P(d_depth), _P(stream)))
 
 
 def sg_backward_camera(scene, frame, d_g_rgb, d_g_alpha, d_g_depth, grads, stream=0):

@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=300)
     return ap.parse_args()
 
 
@@ -266,6 +268,11 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(sc, [c for _, c in cams], budget_s=20.0)
+    if not args.no_serving:
+        from paper_2510_12901_gb300 import serve
+        srv = serve.measure_serving(n_requests=args.serving_requests)
+        if rank == 0:
+            result["serving"] = srv
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -323,7 +330,7 @@ def cpu_baseline(sc, cams, budget_s=20.0):
     total = 0.0
     used = 0.0
     for i, cam in enumerate(cams):
-        s1, s2 = 1000, 6000
+        s1, s2 = 4000, 160000
         t1 = _oracle_sample_time(O, sc, cam, s1, 100 + i)
         t2 = _oracle_sample_time(O, sc, cam, s2, 200 + i)
         used += t1 + t2
@@ -333,7 +340,7 @@ def cpu_baseline(sc, cams, budget_s=20.0):
     rays = sum(c.width * c.height for c in cams)
     return {"value": rays / total / 1e6, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
             "sample": f"per view: projection + sort of all {N_GAUSS} Gaussians and compositing "
-                      f"of 1000 and 6000 random rays, extrapolated linearly to the full view "
+                      f"of 4000 and 160000 random rays, extrapolated linearly to the full view "
                       f"({used:.1f} s of CPU work); extrapolated seconds per step {total:.1f}"}
 
 

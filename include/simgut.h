@@ -226,6 +226,61 @@ sg_status sg_backward_lidar(sg_scene scene, sg_frame frame, const float *d_g_ran
                             const float *d_g_alpha, const sg_grads *grads, void *stream);
 
 /* ----------------------------------------------------------------------
+ * Request server (continuous batching).  Scenes and sensors are created as
+ * above and stay resident; requests reference them.  n_slots worker threads
+ * each own a CUDA stream and a render workspace; a request is admitted, in
+ * arrival order, when a slot is free and its estimated workspace fits in
+ * memory_budget bytes next to the requests already running (0 = no
+ * limit), so requests that arrive while others run start as soon as a slot
+ * and memory free up, and their GPU work overlaps on separate streams.
+ * Latency runs from sg_server_submit to the completion of the request's
+ * last kernel.  A request's buffers (outputs, LiDAR poses) belong to the
+ * caller and must stay valid until sg_server_wait returns for it.  The
+ * first request of each size grows a slot's workspace (which synchronises
+ * the device once); warm every slot up before measuring.  Every wait is a
+ * host wait with a timeout: SG_ERR_TIMEOUT, never a hang.
+ * ---------------------------------------------------------------------- */
+typedef struct sg_server_s *sg_server;
+typedef struct {
+    int n_slots;            /* requests running at once, 1..64 */
+    size_t memory_budget;   /* device bytes for running requests' workspaces, 0 = unlimited */
+    int queue_capacity;     /* waiting requests before submit returns SG_ERR_BUSY */
+} sg_server_config;
+enum { SG_REQ_CAMERA = 0, SG_REQ_LIDAR = 1 };
+typedef struct {
+    int kind;                   /* SG_REQ_CAMERA or SG_REQ_LIDAR */
+    sg_scene scene;
+    sg_camera camera;           /* SG_REQ_CAMERA */
+    sg_lidar lidar;             /* SG_REQ_LIDAR */
+    float c2w[12];              /* SG_REQ_CAMERA: camera-to-world pose */
+    const float *d_col_c2w;     /* SG_REQ_LIDAR: per-column poses (device) */
+    float *d_out[4];            /* camera: rgb, alpha, depth; LiDAR: range,
+                                   intensity, drop, alpha (device, may be NULL) */
+    sg_render_opts opts;
+} sg_request;
+typedef struct {
+    int64_t completed, failed, rays, peak_in_flight, queued;
+    double latency_mean_ms, latency_p50_ms, latency_p99_ms, latency_max_ms;
+    double span_s;              /* first arrival to last completion */
+    double mrays_per_s;         /* rays of completed requests / span */
+} sg_server_report;
+sg_server_config sg_default_server_config(void);
+sg_status sg_server_create(const sg_server_config *cfg, sg_server *out);
+/* Enqueue a request (never blocks).  SG_ERR_BUSY when the queue is full,
+ * SG_ERR_INVALID for an incomplete request or one larger than the budget. */
+sg_status sg_server_submit(sg_server server, const sg_request *req, uint64_t *ticket);
+/* Wait (at most timeout_s seconds, <= 0: no limit) for one request; returns
+ * its render status and latency, or SG_ERR_TIMEOUT. */
+sg_status sg_server_wait(sg_server server, uint64_t ticket, double timeout_s,
+                         double *latency_ms);
+/* Wait for every submitted request to finish (or SG_ERR_TIMEOUT). */
+sg_status sg_server_drain(sg_server server, double timeout_s);
+sg_status sg_server_stats(sg_server server, sg_server_report *out);
+sg_status sg_server_reset_stats(sg_server server);
+/* Stops the workers (requests not yet started are dropped) and frees. */
+void sg_server_destroy(sg_server server);
+
+/* ----------------------------------------------------------------------
  * Inspection of the last render's intermediate buffers, for tests and
  * profiling.  Returns a device pointer into the frame (valid until the next
  * render with it) and the element count.  Fields:

@@ -73,13 +73,15 @@ struct PairEval {
 
 // Evaluate one camera pair; returns false when the entry does not composite
 // at this ray (outside the box, behind the origin, or below alpha_min).
+// Branch-free: every value is computed and the tests combined at the end, so
+// that evaluations of consecutive entries can overlap.
 __device__ __forceinline__ bool cam_pair(const float4 q0, const float4 q1, const float4 q2,
                                          const float4 m0, const float4 m1, const float4 m2,
                                          const float4 mv, const float4 rc, const float dd[3],
                                          float rx, float ry, float alpha_min, float alpha_max,
                                          PairEval &pe)
 {
-    if (!(rx >= rc.x && rx <= rc.y && ry >= rc.z && ry <= rc.w)) return false;
+    const bool in_box = rx >= rc.x && rx <= rc.y && ry >= rc.z && ry <= rc.w;
     pe.n[0] = q0.w + q0.x * dd[0] + q0.y * dd[1] + q0.z * dd[2];
     pe.n[1] = q1.w + q1.x * dd[0] + q1.y * dd[1] + q1.z * dd[2];
     pe.n[2] = q2.w + q2.x * dd[0] + q2.y * dd[1] + q2.z * dd[2];
@@ -89,12 +91,11 @@ __device__ __forceinline__ bool cam_pair(const float4 q0, const float4 q1, const
     pe.inv = 1.f / (pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
     pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
     pe.tau = (mv.x * pe.e[0] + mv.y * pe.e[1] + mv.z * pe.e[2]) * pe.inv;
-    if (!(pe.tau > 0.f)) return false;
     pe.rho = __expf(-0.5f * pe.D2);
-    float a = mv.w * pe.rho;
+    const float a = mv.w * pe.rho;
     pe.clamped = a > alpha_max;
     pe.alpha = fminf(a, alpha_max);
-    return pe.alpha >= alpha_min;
+    return in_box && pe.tau > 0.f && pe.alpha >= alpha_min;
 }
 
 // LiDAR entries keep per-column quantities (each column has its own sensor

@@ -148,7 +148,6 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
             }
             __syncwarp();
             const int n = __popc(bal);
-#pragma unroll 2
             for (int j = 0; j < n; ++j) {
                 PairEval pe;
                 bool ok = cam_pair(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],

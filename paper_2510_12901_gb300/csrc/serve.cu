@@ -1,0 +1,325 @@
+// serve.cu -- a continuous-batching request server around the renderer.
+//
+// Several scenes stay resident; camera and LiDAR render requests of any size
+// arrive through sg_server_submit.  n_slots worker threads each own a CUDA
+// stream and a render workspace (frame).  A request is admitted, in arrival
+// order, as soon as a slot is free and its estimated workspace fits in the
+// device-memory budget next to the requests already in flight; admitted
+// requests run concurrently on their own streams, so one request's
+// projection and sort overlap another's compositing on the GPU.  Latency is
+// measured from submission to the completion of the request's last kernel.
+//
+// Every wait here is a host-side condition-variable wait with a timeout; no
+// kernel waits on another.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+extern "C" {
+sg_status sg_render_camera(sg_scene scene, sg_camera cam, const float h_c2w[12],
+                           const sg_render_opts *opts, sg_frame frame, float *d_rgb,
+                           float *d_alpha, float *d_depth, void *stream);
+sg_status sg_render_lidar(sg_scene scene, sg_lidar lidar, const float *d_col_c2w,
+                          const sg_render_opts *opts, sg_frame frame, float *d_range,
+                          float *d_intensity, float *d_drop, float *d_alpha, void *stream);
+}
+
+namespace sg {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    uint64_t ticket;
+    sg_request req;
+    size_t bytes;               // admission estimate
+    Clock::time_point arrival;
+};
+
+struct Result {
+    bool done = false;
+    sg_status status = SG_OK;
+    double latency_ms = 0;
+};
+
+// Workspace estimate of one request: per-Gaussian buffers, sort buffers
+// and records, per-ray state, and (tile, Gaussian) pairs at a generous 4
+// tiles per Gaussian.
+static size_t request_bytes(const sg_request &r)
+{
+    const int64_t n = r.scene ? r.scene->s.n : 0;
+    int64_t rays = 0;
+    if (r.kind == SG_REQ_CAMERA && r.camera)
+        rays = (int64_t)r.camera->c.width * r.camera->c.height;
+    else if (r.kind == SG_REQ_LIDAR && r.lidar)
+        rays = (int64_t)r.lidar->l.n_beams * r.lidar->l.n_cols;
+    return (size_t)n * (sizeof(GRec) + 160) + (size_t)rays * 24 + (size_t)n * 4 * 17;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+struct sg_server_s {
+    sg_server_config cfg;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Job> queue;
+    std::unordered_map<uint64_t, Result> results;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+    std::vector<sg_frame> frames;
+    size_t bytes_in_flight = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    int in_flight = 0;
+    // statistics
+    std::vector<double> latencies;
+    int64_t completed = 0, failed = 0, rays = 0, busy_peak = 0;
+    Clock::time_point t_first, t_last;
+    bool any = false;
+};
+
+static void worker_main(sg_server S, int slot)
+{
+    cudaSetDevice(S->device);
+    cudaStream_t st = S->streams[slot];
+    sg_frame fr = S->frames[slot];
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        // admit the oldest request once it fits next to the work in flight
+        S->cv_work.wait(lk, [&] {
+            if (S->stop) return true;
+            if (S->queue.empty()) return false;
+            const Job &j = S->queue.front();
+            return S->cfg.memory_budget == 0 || S->in_flight == 0 ||
+                   S->bytes_in_flight + j.bytes <= S->cfg.memory_budget;
+        });
+        if (S->stop) break;   // requests not yet started are dropped
+        Job job = S->queue.front();
+        S->queue.pop_front();
+        S->bytes_in_flight += job.bytes;
+        S->in_flight++;
+        S->busy_peak = std::max<int64_t>(S->busy_peak, S->in_flight);
+        lk.unlock();
+        S->cv_work.notify_all();
+
+        const sg_request &r = job.req;
+        sg_status s;
+        int64_t nrays = 0;
+        if (r.kind == SG_REQ_CAMERA) {
+            s = sg_render_camera(r.scene, r.camera, r.c2w, &r.opts, fr, r.d_out[0], r.d_out[1],
+                                 r.d_out[2], st);
+            if (r.camera) nrays = (int64_t)r.camera->c.width * r.camera->c.height;
+        } else {
+            s = sg_render_lidar(r.scene, r.lidar, r.d_col_c2w, &r.opts, fr, r.d_out[0],
+                                r.d_out[1], r.d_out[2], r.d_out[3], st);
+            if (r.lidar) nrays = (int64_t)r.lidar->l.n_beams * r.lidar->l.n_cols;
+        }
+        if (s == SG_OK) {
+            cudaEventRecord(ev, st);
+            cudaError_t e = cudaEventSynchronize(ev);
+            if (e != cudaSuccess) s = cuda_status(e, "request completion");
+        }
+        const Clock::time_point t_done = Clock::now();
+
+        lk.lock();
+        S->bytes_in_flight -= job.bytes;
+        S->in_flight--;
+        Result &res = S->results[job.ticket];
+        res.done = true;
+        res.status = s;
+        res.latency_ms = std::chrono::duration<double, std::milli>(t_done - job.arrival).count();
+        if (s == SG_OK) {
+            S->completed++;
+            S->rays += nrays;
+            S->latencies.push_back(res.latency_ms);
+        } else {
+            S->failed++;
+        }
+        if (!S->any) { S->t_first = job.arrival; S->any = true; }
+        S->t_last = t_done;
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+    lk.unlock();
+    cudaEventDestroy(ev);
+}
+
+extern "C" {
+
+sg_server_config sg_default_server_config(void)
+{
+    sg_server_config c;
+    memset(&c, 0, sizeof(c));
+    c.n_slots = 4;
+    c.memory_budget = 0;
+    c.queue_capacity = 4096;
+    return c;
+}
+
+sg_status sg_server_create(const sg_server_config *cfg, sg_server *out)
+{
+    if (!cfg || !out) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    *out = nullptr;
+    if (cfg->n_slots < 1 || cfg->n_slots > 64 || cfg->queue_capacity < 1) {
+        set_error("sg_server_create: n_slots must be in 1..64 and queue_capacity >= 1");
+        return SG_ERR_INVALID;
+    }
+    sg_server S = new (std::nothrow) sg_server_s;
+    if (!S) { set_error("host allocation failed"); return SG_ERR_OOM; }
+    S->cfg = *cfg;
+    cudaGetDevice(&S->device);
+    for (int i = 0; i < cfg->n_slots; ++i) {
+        cudaStream_t st;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            sg_status r = cuda_status(e, "cudaStreamCreate");
+            sg_server_destroy(S);
+            return r;
+        }
+        S->streams.push_back(st);
+        sg_frame f = nullptr;
+        sg_frame_create(&f);
+        S->frames.push_back(f);
+    }
+    for (int i = 0; i < cfg->n_slots; ++i) S->workers.emplace_back(worker_main, S, i);
+    *out = S;
+    return SG_OK;
+}
+
+sg_status sg_server_submit(sg_server S, const sg_request *req, uint64_t *ticket)
+{
+    if (!S || !req || !ticket) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    if (!req->scene || (req->kind == SG_REQ_CAMERA && !req->camera) ||
+        (req->kind == SG_REQ_LIDAR && (!req->lidar || !req->d_col_c2w)) ||
+        (req->kind != SG_REQ_CAMERA && req->kind != SG_REQ_LIDAR)) {
+        set_error("sg_server_submit: incomplete request");
+        return SG_ERR_INVALID;
+    }
+    Job j;
+    j.req = *req;
+    j.bytes = request_bytes(*req);
+    if (S->cfg.memory_budget && j.bytes > S->cfg.memory_budget) {
+        set_error("sg_server_submit: the request's workspace (%zu bytes) exceeds the budget",
+                  j.bytes);
+        return SG_ERR_INVALID;
+    }
+    j.arrival = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if ((int)S->queue.size() >= S->cfg.queue_capacity) {
+            set_error("sg_server_submit: queue full");
+            return SG_ERR_BUSY;
+        }
+        j.ticket = S->next_ticket++;
+        S->results[j.ticket] = Result();
+        S->queue.push_back(j);
+        *ticket = j.ticket;
+    }
+    S->cv_work.notify_all();
+    return SG_OK;
+}
+
+sg_status sg_server_wait(sg_server S, uint64_t ticket, double timeout_s, double *latency_ms)
+{
+    if (!S) { set_error("NULL server"); return SG_ERR_INVALID; }
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->results.find(ticket);
+    if (it == S->results.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return SG_ERR_INVALID; }
+    const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9);
+    if (!S->cv_done.wait_until(lk, deadline, [&] { return S->results[ticket].done; })) {
+        set_error("sg_server_wait: ticket %llu not done within %.3f s", (unsigned long long)ticket,
+                  timeout_s);
+        return SG_ERR_TIMEOUT;
+    }
+    Result r = S->results[ticket];
+    S->results.erase(ticket);
+    if (latency_ms) *latency_ms = r.latency_ms;
+    if (r.status != SG_OK) set_error("request %llu failed (status %d)", (unsigned long long)ticket, r.status);
+    return r.status;
+}
+
+sg_status sg_server_drain(sg_server S, double timeout_s)
+{
+    if (!S) { set_error("NULL server"); return SG_ERR_INVALID; }
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9);
+    if (!S->cv_done.wait_until(lk, deadline, [&] { return S->queue.empty() && S->in_flight == 0; })) {
+        set_error("sg_server_drain: work left after %.3f s", timeout_s);
+        return SG_ERR_TIMEOUT;
+    }
+    return SG_OK;
+}
+
+sg_status sg_server_stats(sg_server S, sg_server_report *out)
+{
+    if (!S || !out) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    memset(out, 0, sizeof(*out));
+    out->completed = S->completed;
+    out->failed = S->failed;
+    out->rays = S->rays;
+    out->peak_in_flight = S->busy_peak;
+    out->queued = (int64_t)S->queue.size();
+    std::vector<double> l = S->latencies;
+    if (!l.empty()) {
+        std::sort(l.begin(), l.end());
+        auto q = [&](double p) {
+            double idx = p * (double)(l.size() - 1);
+            size_t i = (size_t)floor(idx);
+            size_t k = std::min(i + 1, l.size() - 1);
+            return l[i] + (l[k] - l[i]) * (idx - (double)i);
+        };
+        double s = 0;
+        for (double v : l) s += v;
+        out->latency_mean_ms = s / (double)l.size();
+        out->latency_p50_ms = q(0.50);
+        out->latency_p99_ms = q(0.99);
+        out->latency_max_ms = l.back();
+    }
+    if (S->any) {
+        out->span_s = std::chrono::duration<double>(S->t_last - S->t_first).count();
+        out->mrays_per_s = out->span_s > 0 ? (double)S->rays / out->span_s / 1e6 : 0.0;
+    }
+    return SG_OK;
+}
+
+sg_status sg_server_reset_stats(sg_server S)
+{
+    if (!S) { set_error("NULL server"); return SG_ERR_INVALID; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->latencies.clear();
+    S->completed = S->failed = S->rays = S->busy_peak = 0;
+    S->any = false;
+    return SG_OK;
+}
+
+void sg_server_destroy(sg_server S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    for (auto &t : S->workers)
+        if (t.joinable()) t.join();
+    for (auto st : S->streams) cudaStreamDestroy(st);
+    for (auto f : S->frames) sg_frame_destroy(f);
+    delete S;
+}
+
+}  // extern "C"

@@ -51,6 +51,26 @@ class sg_grads(C.Structure):
                 ("d_g_features", C.c_void_p)]
 
 
+class sg_server_config(C.Structure):
+    _fields_ = [("n_slots", C.c_int), ("memory_budget", C.c_size_t),
+                ("queue_capacity", C.c_int)]
+
+
+class sg_request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("scene", C.c_void_p), ("camera", C.c_void_p),
+                ("lidar", C.c_void_p), ("c2w", C.c_float * 12), ("d_col_c2w", C.c_void_p),
+                ("d_out", C.c_void_p * 4), ("opts", sg_render_opts)]
+
+
+class sg_server_report(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("rays", C.c_int64),
+                ("peak_in_flight", C.c_int64), ("queued", C.c_int64),
+                ("latency_mean_ms", C.c_double), ("latency_p50_ms", C.c_double),
+                ("latency_p99_ms", C.c_double), ("latency_max_ms", C.c_double),
+                ("span_s", C.c_double), ("mrays_per_s", C.c_double)]
+
+
+REQ_CAMERA, REQ_LIDAR = 0, 1
 _H = C.c_void_p
 _P = C.c_void_p
 _SIGNATURES = {
@@ -87,6 +107,14 @@ _SIGNATURES = {
     "sg_frame_field": (C.c_int, [_H, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
     "sg_frame_stats": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64)]),
+    "sg_default_server_config": (sg_server_config, []),
+    "sg_server_create": (C.c_int, [C.POINTER(sg_server_config), C.POINTER(_H)]),
+    "sg_server_submit": (C.c_int, [_H, C.POINTER(sg_request), C.POINTER(C.c_uint64)]),
+    "sg_server_wait": (C.c_int, [_H, C.c_uint64, C.c_double, C.POINTER(C.c_double)]),
+    "sg_server_drain": (C.c_int, [_H, C.c_double]),
+    "sg_server_stats": (C.c_int, [_H, C.POINTER(sg_server_report)]),
+    "sg_server_reset_stats": (C.c_int, [_H]),
+    "sg_server_destroy": (None, [_H]),
     "sg_frame_set_timing": (C.c_int, [_H, C.c_int]),
     "sg_frame_timing": (C.c_int, [_H, C.POINTER(C.c_float)]),
 }
@@ -256,6 +284,51 @@ def sg_frame_stats(frame):
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     _check(load().sg_frame_stats(frame, C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+def sg_default_server_config(**kw):
+    c = load().sg_default_server_config()
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def sg_server_create(cfg):
+    h = _H()
+    _check(load().sg_server_create(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def sg_server_submit(server, req):
+    t = C.c_uint64()
+    _check(load().sg_server_submit(server, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def sg_server_wait(server, ticket, timeout_s=60.0):
+    lat = C.c_double()
+    _check(load().sg_server_wait(server, C.c_uint64(ticket), timeout_s, C.byref(lat)))
+    return lat.value
+
+
+def sg_server_drain(server, timeout_s=600.0):
+    _check(load().sg_server_drain(server, timeout_s))
+
+
+def sg_server_stats(server):
+    st = sg_server_report()
+    _check(load().sg_server_stats(server, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def sg_server_reset_stats(server):
+    _check(load().sg_server_reset_stats(server))
+
+
+def sg_server_destroy(server):
+    load().sg_server_destroy(server)
 
 
 def sg_frame_set_timing(frame, on):

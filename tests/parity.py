@@ -21,7 +21,7 @@ import numpy as np
 MARGIN_ALPHA = 1e-5     # |alpha - alpha_min| / alpha_min
 MARGIN_TMIN = 1e-5      # |T' - t_min| / t_min
 MARGIN_TAU = 1e-5       # |tau_max| (metres)
-MARGIN_ORDER = 3e-7     # relative gap of consecutive float32 sort keys (2.5 ulp)
+MARGIN_ORDER = 5e-7     # relative gap of consecutive float32 sort keys (4 ulp)
 MARGIN_RECT_PX = 1e-3   # pixels
 MARGIN_RECT_DEG = 1e-4  # degrees
 MARGIN_VALID = 1e-4     # relative margin of near / theta_max / opacity tests
@@ -153,13 +153,14 @@ def compare_lists(gpu_ids, gpu_ranges, orc_ids, orc_ranges, tiles, amb_gauss, de
         o = o[~amb_gauss[o]]
         assert np.array_equal(np.sort(g), np.sort(o)), (label, t, len(g), len(o))
         if not np.array_equal(g, o):
-            # allowed only between keys within 2 float32 ulps of each other
+            # allowed only between keys within 4 float32 ulps of each other (the
+            # kernels' keys agree with the oracle's to that)
             k = depth_key[o].astype(np.float32)
             pos_g = {int(x): i for i, x in enumerate(g)}
             for i in range(len(o)):
                 if pos_g[int(o[i])] != i:
                     near = np.abs(k.view(np.int32).astype(np.int64) -
-                                  np.int64(k[i].view(np.int32))) <= 2
+                                  np.int64(k[i].view(np.int32))) <= 4
                     assert near.sum() > 1, (label, t, i)
         checked += len(g)
     return checked

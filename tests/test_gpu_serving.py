@@ -1,0 +1,96 @@
+"""The request server: requests that arrive while others run are admitted as
+slots and memory free up, run concurrently on separate streams, and each
+result equals the same request rendered alone (bit for bit: the forward
+pass is deterministic)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2510_12901_gb300 import _build
+    _build.build()
+    from paper_2510_12901_gb300 import serve
+    return serve.ServingWorkload(sizes=(20_000, 60_000), n_requests=48, seed=11, ring=1,
+                                 pinhole=(320, 240), fisheye=(256, 192))
+
+
+def _outs(W, i):
+    import torch
+    name = W.KINDS[W.kinds[i]]
+    if name in W.cams:
+        c = W.cams[name][0]
+        return [torch.full((c.height, c.width, 3), -7.0, device="cuda"),
+                torch.full((c.height, c.width), -7.0, device="cuda"),
+                torch.full((c.height, c.width), -7.0, device="cuda")]
+    L = W.lidars[name][0]
+    return [torch.full((L.n_beams, L.n_cols), -7.0, device="cuda") for _ in range(4)]
+
+
+def test_results_identical_alone_and_in_the_mix(W):
+    import torch
+    from paper_2510_12901_gb300 import serve
+    from paper_2510_12901_gb300 import simgut as sg
+    n = len(W.kinds)
+    alone = []
+    fr = sg.Frame()
+    for i in range(n):
+        o = _outs(W, i)
+        W.render_plain(i, fr, torch.cuda.current_stream().cuda_stream, outs=o)
+        alone.append(o)
+    torch.cuda.synchronize()
+    srv = serve.Server(n_slots=4)
+    mixed = [_outs(W, i) for i in range(n)]
+    tickets = [srv.submit(W.request(i, outs=mixed[i])) for i in range(n)]   # one burst
+    for t in tickets:
+        srv.wait(t, 120.0)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == n and st["failed"] == 0
+    assert st["peak_in_flight"] > 1            # requests really overlapped
+    for i in range(n):
+        for a, b in zip(alone[i], mixed[i]):
+            assert torch.equal(a, b), (i, W.KINDS[W.kinds[i]])
+    assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
+
+
+def test_memory_admission_serialises_and_completes(W):
+    from paper_2510_12901_gb300 import serve
+    # pinhole requests on the larger scene: each needs ~15 MB of workspace,
+    # so a 20 MB budget admits one at a time even with four free slots
+    idx = [i for i in range(len(W.kinds)) if W.kinds[i] == 0 and W.scene_of[i] == 1]
+    assert len(idx) >= 3
+    srv = serve.Server(n_slots=4, memory_budget=20_000_000)
+    tickets = [srv.submit(W.request(i)) for i in idx]
+    for t in tickets:
+        srv.wait(t, 120.0)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(idx) and st["peak_in_flight"] == 1
+
+
+def test_queue_full_and_wait_timeout(W):
+    from paper_2510_12901_gb300 import serve
+    from paper_2510_12901_gb300 import simgut as sg
+    srv = serve.Server(n_slots=1, queue_capacity=1)
+    t0 = srv.submit(W.request(0))
+    busy = 0
+    tickets = [t0]
+    for i in range(1, 12):
+        try:
+            tickets.append(srv.submit(W.request(i)))
+        except sg.SimgutError as e:
+            assert e.status == -6            # SG_ERR_BUSY
+            busy += 1
+    assert busy > 0
+    with pytest.raises(sg.SimgutError) as e:
+        srv.wait(tickets[-1], 1e-6)          # not done within a microsecond
+    assert e.value.status == -5              # SG_ERR_TIMEOUT
+    for t in tickets:
+        srv.wait(t, 120.0)
+    srv.drain(60.0)
+    srv.close()

@@ -306,6 +306,7 @@ def roofline(per_view, cams, clocks):
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
         out["traffic"] = tr.get("k_render_camera")
+        out["traffic_note"] = "dram bytes of one fisheye-view launch (ncu), profiles/"
     except (OSError, ValueError):
         pass
     return out

@@ -305,11 +305,29 @@ def roofline(per_view, cams, clocks):
         out.update(achieved=None, frac=None, note="tests/golden/bench_work.json missing")
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-        out["traffic"] = tr.get("k_render_camera")
-        out["traffic_note"] = "dram bytes of one fisheye-view launch (ncu), profiles/"
+        if tr.get("source_sha256") == kernel_source_hash():
+            out["traffic"] = tr.get("k_render_camera")
+            out["traffic_note"] = "dram bytes of one fisheye-view launch (ncu), profiles/"
+        else:
+            out["traffic"] = None
+            out["traffic_note"] = "kernel changed since the ncu capture in profiles/"
     except (OSError, ValueError):
-        pass
+        out["traffic"] = None
     return out
+
+
+KERNEL_SOURCES = ("render.cu", "pairs.cuh", "render.cuh", "internal.h")
+
+
+def kernel_source_hash():
+    """sha256 over the compositing kernel's sources, to tell whether the ncu
+    counters in profiles/ were taken on the kernel as it stands."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2510_12901_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 # ------------------------------------------------------------------ oracle

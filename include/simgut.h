@@ -140,6 +140,23 @@ sg_render_opts sg_default_opts(void);
 sg_status sg_frame_create(sg_frame *out);
 void sg_frame_destroy(sg_frame frame);
 
+/* Capacity mode.  With max_pairs > 0 the frame's (tile, Gaussian) pair
+ * buffers are sized for max_pairs pairs and sg_render_camera /
+ * sg_render_lidar no longer wait for the pair count: nothing in the call
+ * synchronises with the device (after the first call at a given size has
+ * allocated the workspace), so a render can be captured into a CUDA graph.
+ * Pairs beyond max_pairs are dropped, which leaves the result incomplete:
+ * after the render has completed, sg_frame_dropped_pairs tells.  Because
+ * the pose travels through pinned memory owned by the frame, a render in
+ * capacity mode must have completed before the next render call on the
+ * same frame.  max_pairs = 0 restores the default (exact) mode.  Errors:
+ * SG_ERR_INVALID (NULL frame, max_pairs < 0 or >= 2^31). */
+sg_status sg_frame_set_capacity(sg_frame frame, int64_t max_pairs);
+/* After a capacity-mode render on `frame` has completed: the pairs kept
+ * (*pairs, may be NULL) and the pairs dropped for want of room (*dropped;
+ * 0 = the result is complete).  SG_ERR_INVALID in exact mode. */
+sg_status sg_frame_dropped_pairs(sg_frame frame, int64_t *dropped, int64_t *pairs);
+
 /* ----------------------------------------------------------------------
  * Forward render (Eq. 1: front-to-back compositing of alpha_i = sigma_i
  * rho_i(tau_max) over the per-tile list sorted by (tile, depth, id); Sec. 3.2
@@ -186,7 +203,7 @@ sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_co
  * allocator already holds the device's memory, or when the implicit
  * device-wide synchronisation of cudaMalloc / cudaFree is not acceptable in
  * their loop).  The whole workspace lives in one file-scope device array of
- * about 12 MB that every GPU which loads the library keeps until the process
+ * about 17 MB that every GPU which loads the library keeps until the process
  * exits.  Limits: at most 32768 Gaussians, 65536 pixels (256 tiles of
  * 16x16) and 262144 (tile, Gaussian) pairs; larger inputs return
  * SG_ERR_INVALID (sizes) or SG_ERR_OVERFLOW (pairs) with a message.
@@ -239,12 +256,24 @@ sg_status sg_backward_lidar(sg_scene scene, sg_frame frame, const float *d_g_ran
  * first request of each size grows a slot's workspace (which synchronises
  * the device once); warm every slot up before measuring.  Every wait is a
  * host wait with a timeout: SG_ERR_TIMEOUT, never a hang.
+ *
+ * CUDA graphs (use_graphs = 1): for each (scene, sensor, options)
+ * combination a slot renders its first request exactly, the second in
+ * capacity mode (sg_frame_set_capacity: room for 1.25x the largest pair
+ * count seen plus 64K) while capturing that launch sequence into a CUDA
+ * graph, and every later one by replaying the graph: one launch and no host
+ * synchronisation per request.  The pose and the output and pose pointers
+ * of each request reach the graph through a small descriptor in pinned
+ * memory that the graph copies to the device first.  A replay whose pairs
+ * exceed the capacity is rendered again exactly (the result is always
+ * complete) and the graph is captured anew with a larger capacity.
  * ---------------------------------------------------------------------- */
 typedef struct sg_server_s *sg_server;
 typedef struct {
     int n_slots;            /* requests running at once, 1..64 */
     size_t memory_budget;   /* device bytes for running requests' workspaces, 0 = unlimited */
     int queue_capacity;     /* waiting requests before submit returns SG_ERR_BUSY */
+    int use_graphs;         /* 1 (default): replay captured CUDA graphs, see below */
 } sg_server_config;
 enum { SG_REQ_CAMERA = 0, SG_REQ_LIDAR = 1 };
 typedef struct {
@@ -260,6 +289,9 @@ typedef struct {
 } sg_request;
 typedef struct {
     int64_t completed, failed, rays, peak_in_flight, queued;
+    int64_t graph_replays;      /* requests served by replaying a captured graph */
+    int64_t graph_captures;     /* graphs captured (one per slot and combination) */
+    int64_t overflow_rerenders; /* replays whose pairs outgrew the capacity, redone exactly */
     double latency_mean_ms, latency_p50_ms, latency_p99_ms, latency_max_ms;
     double span_s;              /* first arrival to last completion */
     double mrays_per_s;         /* rays of completed requests / span */
@@ -304,7 +336,8 @@ enum {
     SG_FIELD_COV2D = 10
 };
 sg_status sg_frame_field(sg_frame frame, int field, const void **d_ptr, int64_t *count);
-/* Number of (tile, Gaussian) pairs and tiles of the last render. */
+/* Number of (tile, Gaussian) pairs (in capacity mode: those kept), tiles and
+ * rays of the last render. */
 sg_status sg_frame_stats(sg_frame frame, int64_t *n_pairs, int64_t *n_tiles,
                          int64_t *n_rays);
 

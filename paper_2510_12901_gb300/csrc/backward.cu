@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(kCamThreads)
 k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order,
                   const float4 *__restrict__ pix,
-                  const double *__restrict__ tile_dir, const float4 *__restrict__ ray_state,
+                  const double *__restrict__ tile_dir, const RenderDesc *__restrict__ D,
+                  const float4 *__restrict__ ray_state,
                   const uint32_t *__restrict__ n_contrib, const float *__restrict__ g_rgb,
                   const float *__restrict__ g_alpha, const float *__restrict__ g_depth,
                   float *__restrict__ gacc)
@@ -114,11 +115,14 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
     __shared__ float s_red[kBwBatch][kCamThreads / 32][kG];
     __shared__ float s_ref[6];
     __shared__ uint32_t s_max;
+    __shared__ CamPose s_pose;
+    load_cam_pose(D, s_pose);
+    __syncthreads();
     const int tile = (int)order[blockIdx.x], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = tile % P.ntx, ty = tile / P.ntx;
     const int px = tx * kTile + (tid % kTile), py = ty * kTile + (tid / kTile);
     if (tid == 0) {
-        cam_tile_ref(P, tile_dir, tile, s_ref);
+        cam_tile_ref(s_pose, tile_dir, tile, s_ref);
         s_max = 0;
     }
     __syncthreads();
@@ -129,7 +133,7 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
     const float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
     const bool ray_ok = inside && e.w > 0.f;
     float dd[3], d[3];
-    cam_ray_offset(P, e, dd);
+    cam_ray_offset(s_pose, e, dd);
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[i] = dh[i] + dd[i];
     const float rx = (float)px + 0.5f, ry = (float)py + 0.5f;
@@ -160,7 +164,7 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
         if (tid < cnt) {
             const uint32_t g = ids[rg.x + bstart + tid];
             float4 ent[9];
-            cam_entry(rec[g], P.t, dh, dl, ent);
+            cam_entry(rec[g], s_pose.t, dh, dl, ent);
 #pragma unroll
             for (int k = 0; k < 9; ++k) s_e[k][tid] = ent[k];
             s_id[tid] = g;
@@ -433,11 +437,11 @@ sg_status backward_camera(const Scene &sc, const Camera &cam, Frame &fr, const f
     sg_status s = ensure(fr.gacc, sizeof(float) * kG * (sc.n > 0 ? sc.n : 1));
     if (s != SG_OK) return s;
     SG_CUDA(cudaMemsetAsync(fr.gacc.p, 0, sizeof(float) * kG * sc.n, st));
-    const CamRender P = cam_render_params(cam, fr.c2w, fr.opts);
+    const CamRender P = cam_render_params(cam, fr.opts);
     k_backward_camera<<<(unsigned)(cam.ntx * cam.nty), kCamThreads, 0, st>>>(
         P, (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
         (const uint2 *)fr.ranges.p, (const uint32_t *)fr.order.p, cam.d_pix, cam.d_tile_dir,
-        (const float4 *)fr.ray_state.p,
+        (const RenderDesc *)fr.desc.p, (const float4 *)fr.ray_state.p,
         (const uint32_t *)fr.n_contrib.p, g_rgb, g_alpha, g_depth, (float *)fr.gacc.p);
     SG_LAUNCHED();
     const float o[3] = {fr.c2w[3], fr.c2w[7], fr.c2w[11]};

@@ -16,7 +16,16 @@ namespace sg {
 static thread_local char g_err[512] = "";
 static std::atomic<int64_t> g_launches{0};
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local bool g_capture_guard = false;
+static std::atomic<uint64_t> g_uid{1};
+
+void count_launch()
+{
+    if (!g_capture_guard) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool &capture_guard() { return g_capture_guard; }
+uint64_t next_uid() { return g_uid.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...)
 {
@@ -35,6 +44,10 @@ sg_status cuda_status(cudaError_t e, const char *what)
 sg_status ensure(Buf &b, size_t bytes)
 {
     if (bytes <= b.bytes && b.p) return SG_OK;
+    if (g_capture_guard) {
+        set_error("workspace of %zu bytes would grow to %zu during launch capture", b.bytes, bytes);
+        return SG_ERR_BUSY;
+    }
     size_t nb = bytes < 256 ? 256 : bytes + bytes / 4;   // grow with head-room
     if (b.p) {
         cudaFree(b.p);   // implicitly waits for work that may still use it
@@ -147,13 +160,16 @@ static sg_status frame_prepare(Frame &fr, int64_t n, int64_t nrays, int64_t ntil
     SG_ENS(fr.ray_state, sizeof(float4) * (nrays > 0 ? nrays : 1));
     SG_ENS(fr.n_contrib, sizeof(uint32_t) * (nrays > 0 ? nrays : 1));
     SG_ENS(fr.scalars, 64);
+    SG_ENS(fr.desc, sizeof(RenderDesc));
 #undef SG_ENS
     if (!fr.h_scalars) {
-        if (cudaMallocHost(&fr.h_scalars, 64) != cudaSuccess) {
+        static_assert(sizeof(RenderDesc) <= 256, "RenderDesc outgrew its pinned slot");
+        if (cudaMallocHost(&fr.h_scalars, 512) != cudaSuccess) {
             cudaGetLastError();
             set_error("pinned allocation failed");
             return SG_ERR_OOM;
         }
+        fr.h_desc = (RenderDesc *)((char *)fr.h_scalars + 256);
     }
     fr.n_gauss = n;
     fr.n_rays = nrays;
@@ -166,8 +182,19 @@ static void tmark(Frame &fr, int i, cudaStream_t st)
     if (fr.timing) cudaEventRecord(fr.ev[i], st);
 }
 
+// The render's RenderDesc (written to fr.h_desc by the caller) to the device.
+static sg_status upload_desc(Frame &fr, cudaStream_t st)
+{
+    SG_CUDA(cudaMemcpyAsync(fr.desc.p, fr.h_desc, sizeof(RenderDesc), cudaMemcpyHostToDevice, st));
+    return SG_OK;
+}
+
 // Stages shared by both sensors after projection: depth sort, offsets,
-// pair count read-back, binning, tile sort, ranges.
+// pair count, binning, tile sort, ranges.  The pair count is read back and
+// sizes the pair buffers, except in capacity mode (fr.k_cap > 0), where the
+// buffers hold k_cap pairs, the count stays on the device (clamped to
+// k_cap, the excess in scalars[3]) and nothing waits for it; the scalars
+// are then copied to h_scalars at the end for the caller to check.
 static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int wrap,
                               cudaStream_t st)
 {
@@ -186,12 +213,18 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
                            fr, st);
     if (s != SG_OK) return s;
     tmark(fr, 2, st);
-    SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 8, cudaMemcpyDeviceToHost, st));
-    SG_CUDA(cudaStreamSynchronize(st));
-    const int64_t K = fr.h_scalars[1];
-    if (K > 0x7fffffffLL) {
-        set_error("%lld (tile, Gaussian) pairs exceed 2^31-1", (long long)K);
-        return SG_ERR_OVERFLOW;
+    int64_t K = 0;
+    if (fr.k_cap > 0) {
+        K = fr.k_cap;
+        if ((s = clamp_pairs(sc + 1, K, sc + 3, st)) != SG_OK) return s;
+    } else {
+        SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 8, cudaMemcpyDeviceToHost, st));
+        SG_CUDA(cudaStreamSynchronize(st));
+        K = fr.h_scalars[1];
+        if (K > 0x7fffffffLL) {
+            set_error("%lld (tile, Gaussian) pairs exceed 2^31-1", (long long)K);
+            return SG_ERR_OVERFLOW;
+        }
     }
     fr.n_pairs = K;
     for (int i = 0; i < 2; ++i) {
@@ -201,7 +234,7 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
     s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, sc, n, (const int4 *)fr.tiles.p, ntx,
-                  wrap, pk[0], pv[0], st);
+                  wrap, K, pk[0], pv[0], st);
     if (s != SG_OK) return s;
     int bits = 1;
     while (((int64_t)1 << bits) < ntiles) ++bits;
@@ -209,8 +242,10 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     s = radix_sort_pairs(pk, pv, K, sc + 1, 0, bits, fr, st, &pb);
     if (s != SG_OK) return s;
     fr.pair_buf = pb;
-    s = tile_ranges(pk[pb], K, (uint2 *)fr.ranges.p, ntiles, st);
+    s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st);
     if (s != SG_OK) return s;
+    if (fr.k_cap > 0)
+        SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 16, cudaMemcpyDeviceToHost, st));
     tmark(fr, 3, st);
     return SG_OK;
 }
@@ -408,12 +443,7 @@ void sg_frame_destroy(sg_frame frame)
 {
     if (!frame) return;
     Frame &f = frame->f;
-    Buf *bufs[] = {&f.rec, &f.rect, &f.tiles, &f.depth, &f.count, &f.mean2d, &f.cov2d,
-                   &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.cnt_sorted,
-                   &f.offsets, &f.flags, &f.scan_tmp, &f.hist, &f.pkeys[0], &f.pkeys[1],
-                   &f.pvals[0], &f.pvals[1], &f.ranges, &f.ray_state, &f.n_contrib, &f.scalars,
-                   &f.gacc, &f.order, &f.submask};
-    for (Buf *b : bufs) release(*b);
+    for_each_buf(f, [](Buf &b) { release(b); });
     if (f.h_scalars) cudaFreeHost(f.h_scalars);
     for (auto &e : f.ev)
         if (e) cudaEventDestroy(e);
@@ -437,6 +467,40 @@ sg_status sg_frame_timing(sg_frame frame, float ms[4])
     if (!f.timing) { set_error("timing is off for this frame"); return SG_ERR_INVALID; }
     SG_CUDA(cudaEventSynchronize(f.ev[4]));
     for (int i = 0; i < 4; ++i) SG_CUDA(cudaEventElapsedTime(&ms[i], f.ev[i], f.ev[i + 1]));
+    return SG_OK;
+}
+
+}  // extern "C"
+
+// Pairs of the last render: the exact count, or in capacity mode the pairs
+// kept (read back at the end of the render, valid once it has completed).
+static int64_t pairs_kept(const Frame &f)
+{
+    return f.k_cap > 0 && f.h_scalars ? (int64_t)f.h_scalars[1] : f.n_pairs;
+}
+
+extern "C" {
+
+sg_status sg_frame_set_capacity(sg_frame frame, int64_t max_pairs)
+{
+    if (!frame || max_pairs < 0 || max_pairs > 0x7fffffffLL) {
+        set_error("sg_frame_set_capacity: NULL frame or capacity out of range");
+        return SG_ERR_INVALID;
+    }
+    frame->f.k_cap = max_pairs;
+    return SG_OK;
+}
+
+sg_status sg_frame_dropped_pairs(sg_frame frame, int64_t *dropped, int64_t *pairs)
+{
+    if (!frame || !dropped) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    const Frame &f = frame->f;
+    if (f.k_cap <= 0 || !f.h_scalars) {
+        set_error("sg_frame_dropped_pairs: the frame is not in capacity mode");
+        return SG_ERR_INVALID;
+    }
+    *dropped = f.h_scalars[3];
+    if (pairs) *pairs = f.h_scalars[1];
     return SG_OK;
 }
 
@@ -467,11 +531,19 @@ sg_status sg_render_camera(sg_scene scene, sg_camera cam, const float h_c2w[12],
     fr.sensor = cam;
     fr.opts = *opts;
     memcpy(fr.c2w, h_c2w, sizeof(fr.c2w));
+    RenderDesc &D = *fr.h_desc;
+    memcpy(D.c2w, h_c2w, sizeof(D.c2w));
+    D.poses = nullptr;
+    D.out[0] = d_rgb;
+    D.out[1] = d_alpha;
+    D.out[2] = d_depth;
+    D.out[3] = nullptr;
     if (fr.timing) cudaEventRecord(fr.ev[0], st);
-    if ((s = project_camera(sc, c, h_c2w, *opts, fr, st)) != SG_OK) return s;
+    if ((s = upload_desc(fr, st)) != SG_OK) return s;
+    if ((s = project_camera(sc, c, *opts, fr, st)) != SG_OK) return s;
     if (fr.timing) cudaEventRecord(fr.ev[1], st);
     if ((s = sort_and_bin(fr, sc.n, c.ntx, nt, 0, st)) != SG_OK) return s;
-    if ((s = render_camera(c, h_c2w, *opts, fr, d_rgb, d_alpha, d_depth, st)) != SG_OK) return s;
+    if ((s = render_camera(c, *opts, fr, st)) != SG_OK) return s;
     if (fr.timing) cudaEventRecord(fr.ev[4], st);
     return SG_OK;
 }
@@ -498,13 +570,19 @@ sg_status sg_render_lidar(sg_scene scene, sg_lidar lidar, const float *d_col_c2w
     fr.sensor = lidar;
     fr.opts = *opts;
     fr.d_lidar_poses = d_col_c2w;
+    RenderDesc &D = *fr.h_desc;
+    memset(D.c2w, 0, sizeof(D.c2w));
+    D.poses = d_col_c2w;
+    D.out[0] = d_range;
+    D.out[1] = d_intensity;
+    D.out[2] = d_drop;
+    D.out[3] = d_alpha;
     if (fr.timing) cudaEventRecord(fr.ev[0], st);
-    if ((s = project_lidar(sc, L, d_col_c2w, *opts, fr, st)) != SG_OK) return s;
+    if ((s = upload_desc(fr, st)) != SG_OK) return s;
+    if ((s = project_lidar(sc, L, *opts, fr, st)) != SG_OK) return s;
     if (fr.timing) cudaEventRecord(fr.ev[1], st);
     if ((s = sort_and_bin(fr, sc.n, L.n_theta, nt, 1, st)) != SG_OK) return s;
-    if ((s = render_lidar(L, d_col_c2w, *opts, fr, d_range, d_intensity, d_drop, d_alpha, st)) !=
-        SG_OK)
-        return s;
+    if ((s = render_lidar(L, *opts, fr, st)) != SG_OK) return s;
     if (fr.timing) cudaEventRecord(fr.ev[4], st);
     return SG_OK;
 }
@@ -575,8 +653,8 @@ sg_status sg_frame_field(sg_frame frame, int field, const void **d_ptr, int64_t 
     case SG_FIELD_TILES: *d_ptr = f.tiles.p; *count = f.n_gauss; break;
     case SG_FIELD_DEPTH: *d_ptr = f.depth.p; *count = f.n_gauss; break;
     case SG_FIELD_COUNT: *d_ptr = f.count.p; *count = f.n_gauss; break;
-    case SG_FIELD_PAIR_IDS: *d_ptr = f.pvals[f.pair_buf].p; *count = f.n_pairs; break;
-    case SG_FIELD_PAIR_TILES: *d_ptr = f.pkeys[f.pair_buf].p; *count = f.n_pairs; break;
+    case SG_FIELD_PAIR_IDS: *d_ptr = f.pvals[f.pair_buf].p; *count = pairs_kept(f); break;
+    case SG_FIELD_PAIR_TILES: *d_ptr = f.pkeys[f.pair_buf].p; *count = pairs_kept(f); break;
     case SG_FIELD_RANGES: *d_ptr = f.ranges.p; *count = f.n_tiles; break;
     case SG_FIELD_RAY_STATE: *d_ptr = f.ray_state.p; *count = f.n_rays; break;
     case SG_FIELD_N_CONTRIB: *d_ptr = f.n_contrib.p; *count = f.n_rays; break;
@@ -590,7 +668,7 @@ sg_status sg_frame_field(sg_frame frame, int field, const void **d_ptr, int64_t 
 sg_status sg_frame_stats(sg_frame frame, int64_t *n_pairs, int64_t *n_tiles, int64_t *n_rays)
 {
     if (!frame) { set_error("frame is NULL"); return SG_ERR_INVALID; }
-    if (n_pairs) *n_pairs = frame->f.n_pairs;
+    if (n_pairs) *n_pairs = pairs_kept(frame->f);
     if (n_tiles) *n_tiles = frame->f.n_tiles;
     if (n_rays) *n_rays = frame->f.n_rays;
     return SG_OK;

@@ -16,10 +16,14 @@ constexpr int kTile = 16;                 // camera tile edge (pixels)
 constexpr int kCamThreads = kTile * kTile;
 constexpr int kLidarColsMax = 4;          // distinct columns per LiDAR work item
 constexpr int kLidarWarps = 4;            // warps (work items) per LiDAR render block
+// Camera tile lists longer than this are composited in segments of this many
+// entries, each an independent work item, and combined afterwards.
+constexpr uint32_t kSegLen = 1024;
 
 void set_error(const char *fmt, ...);
 sg_status cuda_status(cudaError_t e, const char *what);
-void count_launch();
+void count_launch();           // not counted while capture_guard() is set
+void count_launches(int64_t n); // kernels run by a graph replay
 
 // after every kernel launch: count it and surface launch errors
 #define SG_LAUNCHED()                                                     \
@@ -94,6 +98,16 @@ struct __align__(16) GRec {
 };
 
 // ------------------------------------------------------------------ frame
+// Per-render parameters that change from one render to the next, kept in
+// device memory (copied from pinned host memory at the start of each render)
+// so that a captured launch sequence can be replayed for a new pose and new
+// output buffers.  The kernels read the pose and the output pointers here.
+struct RenderDesc {
+    float c2w[12];          // camera renders: row-major [R | t]
+    const float *poses;     // LiDAR renders: per-column c2w [n_cols, 12] (device)
+    float *out[4];          // outputs (device), NULL = not written
+};
+
 struct Buf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -106,13 +120,22 @@ struct Frame {
     Buf dkeys[2], dvals[2], cnt_sorted, offsets, flags, scan_tmp, hist;
     // pairs
     Buf pkeys[2], pvals[2], ranges, order, submask;
+    // camera work items: per-tile (segments, first partial slot), items,
+    // arrival counters of long tiles; per-pixel partials of their segments
+    Buf camwork, partials;
     // per-ray saved state: (T_final, omega, Z, LiDAR drop) and contributor count
     Buf ray_state, n_contrib;
     // backward accumulators: per Gaussian dL/dM (9), dL/dmu (3), dL/dsigma,
     // dL/dfeature (3)
     Buf gacc;
-    Buf scalars;      // device scalars (counts)
-    uint32_t *h_scalars = nullptr;  // pinned mirror
+    Buf scalars;      // device scalars: [0] valid Gaussians [1] pairs [2] work-item
+                      // counter [3] pairs dropped over capacity [4..5] camera work counts
+    Buf desc;         // RenderDesc of the current render (device)
+    uint32_t *h_scalars = nullptr;  // pinned: scalars mirror (64 B), then the RenderDesc
+    RenderDesc *h_desc = nullptr;   // pinned staging of desc
+    // capacity mode: > 0 = the pair buffers hold this many pairs and no
+    // step waits for the pair count (pairs beyond it are dropped and counted)
+    int64_t k_cap = 0;
     int64_t n_pairs = 0, n_tiles = 0, n_rays = 0, n_gauss = 0;
     int pair_buf = 0;  // which of pkeys/pvals holds the sorted result
     int kind = -1;     // 0 camera, 1 lidar
@@ -126,7 +149,41 @@ struct Frame {
     float ms[4] = {0, 0, 0, 0};
 };
 
+// Grow b to at least `bytes` (with head-room); growing frees the old buffer.
+// While capture_guard() is set on the calling thread (a launch sequence is
+// being captured), a call that would allocate fails with SG_ERR_BUSY.
 sg_status ensure(Buf &b, size_t bytes);
+bool &capture_guard();
+uint64_t next_uid();            // identity of a scene / sensor handle
+
+constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Upper bounds of the camera work-item buffers for `ntiles` tiles and
+// `n_pairs` listed pairs: segments per tile are 1 for a list of at most
+// kSegLen entries and ceil(len / kSegLen) above, so the items are at most
+// 8 (ntiles + n_pairs / kSegLen) and the partial slots (segments of long
+// tiles) at most min(2 n_pairs / kSegLen, ntiles + n_pairs / kSegLen).
+struct CamWorkSize {
+    int64_t max_items = 0, max_slots = 0;
+    size_t info_bytes = 0, items_bytes = 0, arrive_bytes = 0, work_bytes = 0,
+           partial_bytes = 0;
+};
+constexpr CamWorkSize cam_work_size(int64_t ntiles, int64_t n_pairs)
+{
+    CamWorkSize w;
+    const int64_t per = n_pairs / kSegLen;
+    const int64_t nt1 = ntiles > 0 ? ntiles : 1;
+    w.max_items = 8 * (ntiles + per);
+    w.max_slots = 2 * per < ntiles + per ? 2 * per : ntiles + per;
+    const int64_t items1 = w.max_items > 0 ? w.max_items : 1;
+    const int64_t slots1 = w.max_slots > 0 ? w.max_slots : 1;
+    w.info_bytes = al256(8 * (size_t)nt1);
+    w.items_bytes = al256(8 * (size_t)items1);
+    w.arrive_bytes = al256(4 * 8 * (size_t)slots1);
+    w.work_bytes = w.info_bytes + w.items_bytes + w.arrive_bytes;
+    w.partial_bytes = 2 * 16 * 256 * (size_t)slots1;
+    return w;
+}
 
 // ------------------------------------------------------------------ launchers
 // sort.cu
@@ -143,24 +200,22 @@ sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count,
                         cudaStream_t st);
 sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets,
                     const uint32_t *d_nvalid, int64_t n, const int4 *d_tiles,
-                    int ntx, int wrap_x, uint32_t *d_keys, uint32_t *d_vals,
+                    int ntx, int wrap_x, int64_t cap, uint32_t *d_keys, uint32_t *d_vals,
                     cudaStream_t st);
-sg_status tile_ranges(const uint32_t *d_keys, int64_t K, uint2 *d_ranges, int64_t ntiles,
-                      cudaStream_t st);
+sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
+                      int64_t ntiles, cudaStream_t st);
+sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStream_t st);
 
 // project.cu
-sg_status project_camera(const Scene &sc, const Camera &cam, const float c2w[12],
-                         const sg_render_opts &o, Frame &fr, cudaStream_t st);
-sg_status project_lidar(const Scene &sc, const Lidar &L, const float *d_poses,
-                        const sg_render_opts &o, Frame &fr, cudaStream_t st);
+// The pose and the outputs of a render are read from fr.desc (RenderDesc).
+sg_status project_camera(const Scene &sc, const Camera &cam, const sg_render_opts &o, Frame &fr,
+                         cudaStream_t st);
+sg_status project_lidar(const Scene &sc, const Lidar &L, const sg_render_opts &o, Frame &fr,
+                        cudaStream_t st);
 
 // render.cu
-sg_status render_camera(const Camera &cam, const float c2w[12], const sg_render_opts &o,
-                        Frame &fr, float *rgb, float *alpha, float *depth,
-                        cudaStream_t st);
-sg_status render_lidar(const Lidar &L, const float *d_poses, const sg_render_opts &o,
-                       Frame &fr, float *range, float *intensity, float *drop,
-                       float *alpha, cudaStream_t st);
+sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, cudaStream_t st);
+sg_status render_lidar(const Lidar &L, const sg_render_opts &o, Frame &fr, cudaStream_t st);
 
 // sensors.cu
 sg_status build_camera(Camera &cam);
@@ -177,9 +232,23 @@ sg_status backward_lidar(const Scene &sc, const Lidar &L, Frame &fr, const float
 }  // namespace sg
 
 // the opaque handle types of the C-ABI
-struct sg_scene_s { sg::Scene s; };
-struct sg_camera_s { sg::Camera c; };
-struct sg_lidar_s { sg::Lidar l; };
+// Every device buffer of a frame (for release, and for recognising captured
+// launch sequences whose buffers have since been reallocated).
+namespace sg {
+template <class Fn> inline void for_each_buf(Frame &f, Fn fn)
+{
+    Buf *bufs[] = {&f.rec, &f.rect, &f.tiles, &f.depth, &f.count, &f.mean2d, &f.cov2d,
+                   &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.cnt_sorted,
+                   &f.offsets, &f.flags, &f.scan_tmp, &f.hist, &f.pkeys[0], &f.pkeys[1],
+                   &f.pvals[0], &f.pvals[1], &f.ranges, &f.order, &f.submask, &f.camwork,
+                   &f.partials, &f.ray_state, &f.n_contrib, &f.gacc, &f.scalars, &f.desc};
+    for (Buf *b : bufs) fn(*b);
+}
+}  // namespace sg
+
+struct sg_scene_s { sg::Scene s; uint64_t uid = sg::next_uid(); };
+struct sg_camera_s { sg::Camera c; uint64_t uid = sg::next_uid(); };
+struct sg_lidar_s { sg::Lidar l; uint64_t uid = sg::next_uid(); };
 struct sg_frame_s { sg::Frame f; };
 
 // ---------------------------------------------------------------- device math

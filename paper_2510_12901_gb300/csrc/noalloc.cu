@@ -28,6 +28,7 @@ constexpr size_t kStG4 = al(4 * kStMaxGauss);
 constexpr size_t kStP4 = al(4 * kStMaxPairs);
 constexpr size_t kStHist = al(4 * 2 * 256 * ((kStMaxPairs + 2047) / 2048));
 constexpr size_t kStScan = al(4 * 4096);
+constexpr CamWorkSize kStWork = cam_work_size(kStMaxTiles, kStMaxPairs);
 constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, tiles, cov2d, mean2d
                             2 * kStG4 +                          // depth, count
                             4 * kStG4 +                          // depth-sort keys/values x2
@@ -37,7 +38,9 @@ constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, ti
                             al(8 * kStMaxTiles) + al(4 * kStMaxTiles) +  // ranges, order
                             al(16 * kStMaxRays) + al(4 * kStMaxRays) +   // ray state, contributors
                             al(kStMaxPairs) +                            // sub-block masks
-                            al(64);                                      // device scalars
+                            kStWork.work_bytes + kStWork.partial_bytes + // work items, partials
+                            al(64) +                                     // device scalars
+                            al(sizeof(RenderDesc));                      // render descriptor
 
 static __device__ __align__(256) unsigned char g_static_ws[kStBytes];
 
@@ -140,7 +143,10 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     carve(fr.ray_state, cur, al(16 * kStMaxRays));
     carve(fr.n_contrib, cur, al(4 * kStMaxRays));
     carve(fr.submask, cur, al(kStMaxPairs));
+    carve(fr.camwork, cur, kStWork.work_bytes);
+    carve(fr.partials, cur, kStWork.partial_bytes);
     carve(fr.scalars, cur, al(64));
+    carve(fr.desc, cur, al(sizeof(RenderDesc)));
     fr.n_gauss = sc.n;
     fr.n_rays = nr;
     fr.n_tiles = nt;
@@ -151,7 +157,17 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     // the stages of sg_render_camera: project, depth sort, offsets, pair
     // count, binning, tile sort, ranges, compositing
     const int64_t n = sc.n;
-    if ((s = project_camera(sc, c, h_c2w, *opts, fr, st)) != SG_OK) return s;
+    // the descriptor goes from pageable host memory: the copy has taken its
+    // source by the time cudaMemcpyAsync returns
+    RenderDesc D;
+    memcpy(D.c2w, h_c2w, sizeof(D.c2w));
+    D.poses = nullptr;
+    D.out[0] = d_rgb;
+    D.out[1] = d_alpha;
+    D.out[2] = d_depth;
+    D.out[3] = nullptr;
+    SG_CUDA(cudaMemcpyAsync(fr.desc.p, &D, sizeof(D), cudaMemcpyHostToDevice, st));
+    if ((s = project_camera(sc, c, *opts, fr, st)) != SG_OK) return s;
     uint32_t *scal = (uint32_t *)fr.scalars.p;
     uint32_t *dk[2] = {(uint32_t *)fr.dkeys[0].p, (uint32_t *)fr.dkeys[1].p};
     uint32_t *dv[2] = {(uint32_t *)fr.dvals[0].p, (uint32_t *)fr.dvals[1].p};
@@ -179,13 +195,13 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
     if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, scal, n, (const int4 *)fr.tiles.p,
-                       c.ntx, 0, pk[0], pv[0], st)) != SG_OK)
+                       c.ntx, 0, K, pk[0], pv[0], st)) != SG_OK)
         return s;
     int bits = 1;
     while (((int64_t)1 << bits) < nt) ++bits;
     int pb = 0;
     if ((s = radix_sort_pairs(pk, pv, K, scal + 1, 0, bits, fr, st, &pb)) != SG_OK) return s;
     fr.pair_buf = pb;
-    if ((s = tile_ranges(pk[pb], K, (uint2 *)fr.ranges.p, nt, st)) != SG_OK) return s;
-    return render_camera(c, h_c2w, *opts, fr, d_rgb, d_alpha, d_depth, st);
+    if ((s = tile_ranges(pk[pb], scal + 1, K, (uint2 *)fr.ranges.p, nt, st)) != SG_OK) return s;
+    return render_camera(c, *opts, fr, st);
 }

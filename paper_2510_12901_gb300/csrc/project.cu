@@ -15,7 +15,6 @@ namespace sg {
 struct CamParams {
     int model, W, H, ntx, nty;
     float fx, fy, cx, cy, k0, k1, k2, k3, theta_max;
-    float R[9], t[3];   // camera-to-world rotation (row-major) and centre
 };
 
 struct UTParams {
@@ -124,13 +123,14 @@ __device__ __forceinline__ void sh_colour(const float *__restrict__ planes, int6
 
 // Pixel of a world point; returns false outside the model's domain
 // (pinhole: z > near; fisheye: |x| > near and theta <= theta_max).
-__device__ __forceinline__ bool cam_point(const CamParams &C, float near_dist, const float x[3],
-                                          float &u, float &v)
+// c2w: row-major [R | t] camera-to-world pose (shared memory).
+__device__ __forceinline__ bool cam_point(const CamParams &C, const float *c2w, float near_dist,
+                                          const float x[3], float &u, float &v)
 {
-    float d0 = x[0] - C.t[0], d1 = x[1] - C.t[1], d2 = x[2] - C.t[2];
-    float xc = C.R[0] * d0 + C.R[3] * d1 + C.R[6] * d2;
-    float yc = C.R[1] * d0 + C.R[4] * d1 + C.R[7] * d2;
-    float zc = C.R[2] * d0 + C.R[5] * d1 + C.R[8] * d2;
+    float d0 = x[0] - c2w[3], d1 = x[1] - c2w[7], d2 = x[2] - c2w[11];
+    float xc = c2w[0] * d0 + c2w[4] * d1 + c2w[8] * d2;
+    float yc = c2w[1] * d0 + c2w[5] * d1 + c2w[9] * d2;
+    float zc = c2w[2] * d0 + c2w[6] * d1 + c2w[10] * d2;
     if (C.model == SG_CAMERA_PINHOLE) {
         if (!(zc > near_dist)) return false;
         u = C.fx * xc / zc + C.cx;
@@ -153,17 +153,21 @@ __device__ __forceinline__ bool cam_point(const CamParams &C, float near_dist, c
     return true;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int feature_kind,
-                 int sh_degree, CamParams C, UTParams U, GRec *__restrict__ rec,
+                 int sh_degree, CamParams C, const RenderDesc *__restrict__ D, UTParams U,
+                 GRec *__restrict__ rec,
                  float4 *__restrict__ rect_out, int4 *__restrict__ tiles_out,
                  float *__restrict__ depth_out, uint32_t *__restrict__ count_out,
                  float2 *__restrict__ mean_out, float4 *__restrict__ cov_out)
 {
+    __shared__ float s_c2w[12];   // the pose, from the render's descriptor
+    if (threadIdx.x < 12) s_c2w[threadIdx.x] = D->c2w[threadIdx.x];
+    __syncthreads();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     Activated a = activate(planes, pitch, g);
-    float dx = a.mu[0] - C.t[0], dy = a.mu[1] - C.t[1], dz = a.mu[2] - C.t[2];
+    float dx = a.mu[0] - s_c2w[3], dy = a.mu[1] - s_c2w[7], dz = a.mu[2] - s_c2w[11];
     float dist = sqrtf(dx * dx + dy * dy + dz * dz);
     depth_out[g] = dist;
     uint32_t count = 0;
@@ -174,7 +178,7 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     if (a.sigma >= U.alpha_min) {
         // sigma points chi_0 = mu, chi_{+-i} = mu +- sqrt(n+lambda) s_i R e_i
         float uu[7], vv[7];
-        bool ok = cam_point(C, U.near_dist, a.mu, uu[0], vv[0]);
+        bool ok = cam_point(C, s_c2w, U.near_dist, a.mu, uu[0], vv[0]);
 #pragma unroll
         for (int p = 1; p < 7; ++p) {
             int i = (p - 1) >> 1;
@@ -182,7 +186,7 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
             float x[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) x[r] = a.mu[r] + sg * U.lam_gamma * a.s[i] * a.R[3 * r + i];
-            ok = cam_point(C, U.near_dist, x, uu[p], vv[p]) && ok;
+            ok = cam_point(C, s_c2w, U.near_dist, x, uu[p], vv[p]) && ok;
         }
         if (ok) {
             float mu_u = U.w0m * uu[0], mu_v = U.w0m * vv[0];
@@ -231,8 +235,8 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     write_record(rec, g, a, c[0], c[1], c[2], rect);
 }
 
-sg_status project_camera(const Scene &sc, const Camera &cam, const float c2w[12],
-                         const sg_render_opts &o, Frame &fr, cudaStream_t st)
+sg_status project_camera(const Scene &sc, const Camera &cam, const sg_render_opts &o, Frame &fr,
+                         cudaStream_t st)
 {
     CamParams C;
     C.model = cam.model;
@@ -243,15 +247,12 @@ sg_status project_camera(const Scene &sc, const Camera &cam, const float c2w[12]
     C.fx = cam.fx; C.fy = cam.fy; C.cx = cam.cx; C.cy = cam.cy;
     C.k0 = cam.k[0]; C.k1 = cam.k[1]; C.k2 = cam.k[2]; C.k3 = cam.k[3];
     C.theta_max = (float)cam.theta_max;
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) C.R[3 * r + c] = c2w[4 * r + c];
-        C.t[r] = c2w[4 * r + 3];
-    }
     UTParams U = ut_params(o);
     if (sc.n == 0) return SG_OK;
     unsigned grid = (unsigned)((sc.n + 255) / 256);
     k_project_camera<<<grid, 256, 0, st>>>(
-        sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, C, U, (GRec *)fr.rec.p,
+        sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, C,
+        (const RenderDesc *)fr.desc.p, U, (GRec *)fr.rec.p,
         (float4 *)fr.rect.p, (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p,
         (float2 *)fr.mean2d.p, (float4 *)fr.cov2d.p);
     SG_LAUNCHED();
@@ -265,7 +266,7 @@ struct LidParams {
     float az0, T0, TN;
     const float *T;
     const int *sat;
-    const float *poses;   // [n_cols*12]
+    const float *poses;   // [n_cols*12], set in the kernel from the render's descriptor
 };
 
 __device__ __forceinline__ int pmod(int a, int n)
@@ -336,14 +337,16 @@ __device__ __forceinline__ int sat_count_wrap(const LidParams &L, int x0, int x1
 }
 
 __global__ void __launch_bounds__(256)
-k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidParams L,
-                UTParams U, int cull, GRec *__restrict__ rec, float4 *__restrict__ rect_out,
+k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidParams Lp,
+                const RenderDesc *__restrict__ D, UTParams U, int cull, GRec *__restrict__ rec, float4 *__restrict__ rect_out,
                 int4 *__restrict__ tiles_out, float *__restrict__ depth_out,
                 uint32_t *__restrict__ count_out, float2 *__restrict__ mean_out,
                 float4 *__restrict__ cov_out)
 {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
+    LidParams L = Lp;
+    L.poses = D->poses;
     Activated a = activate(planes, pitch, g);
     float xs[3];
     lidar_col(L, a.mu, xs);
@@ -441,8 +444,8 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidP
                  rect);
 }
 
-sg_status project_lidar(const Scene &sc, const Lidar &Ld, const float *d_poses,
-                        const sg_render_opts &o, Frame &fr, cudaStream_t st)
+sg_status project_lidar(const Scene &sc, const Lidar &Ld, const sg_render_opts &o, Frame &fr,
+                        cudaStream_t st)
 {
     LidParams L;
     L.n_cols = Ld.n_cols;
@@ -456,12 +459,13 @@ sg_status project_lidar(const Scene &sc, const Lidar &Ld, const float *d_poses,
     L.TN = Ld.T[Ld.nphi];
     L.T = Ld.d_T;
     L.sat = Ld.d_sat;
-    L.poses = d_poses;
+    L.poses = nullptr;
     UTParams U = ut_params(o);
     if (sc.n == 0) return SG_OK;
     unsigned grid = (unsigned)((sc.n + 255) / 256);
     k_project_lidar<<<grid, 256, 0, st>>>(
-        sc.d_planes, sc.pitch, sc.n, L, U, o.cull, (GRec *)fr.rec.p, (float4 *)fr.rect.p,
+        sc.d_planes, sc.pitch, sc.n, L, (const RenderDesc *)fr.desc.p, U, o.cull,
+        (GRec *)fr.rec.p, (float4 *)fr.rect.p,
         (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p, (float2 *)fr.mean2d.p,
         (float4 *)fr.cov2d.p);
     SG_LAUNCHED();

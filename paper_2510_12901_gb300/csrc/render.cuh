@@ -8,30 +8,43 @@ namespace sg {
 
 struct CamRender {
     int W, H, ntx;
-    float R[9], t[3];
-    double Rd[9];
     float alpha_min, alpha_max, t_min;
 };
+
+// The camera pose of a render, read from its RenderDesc into shared memory
+// by every block that needs it.
+struct CamPose {
+    double Rd[9];        // rotation in double, for the tile reference rays
+    float R[9], t[3];    // rotation (camera to world, row-major) and centre
+};
+
+// Cooperative load by the block's threads; the caller synchronises.
+__device__ __forceinline__ void load_cam_pose(const RenderDesc *__restrict__ D, CamPose &p)
+{
+    const int i = threadIdx.x;
+    if (i < 12) {
+        const float v = D->c2w[i];
+        const int r = i >> 2, c = i & 3;
+        if (c < 3) {
+            p.R[3 * r + c] = v;
+            p.Rd[3 * r + c] = (double)v;
+        } else {
+            p.t[r] = v;
+        }
+    }
+}
 
 struct LidRender {
     int n_cols, n_items;
     float alpha_min, alpha_max, t_min;
 };
 
-inline CamRender cam_render_params(const Camera &cam, const float c2w[12],
-                                   const sg_render_opts &o)
+inline CamRender cam_render_params(const Camera &cam, const sg_render_opts &o)
 {
     CamRender P;
     P.W = cam.width;
     P.H = cam.height;
     P.ntx = cam.ntx;
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) {
-            P.R[3 * r + c] = c2w[4 * r + c];
-            P.Rd[3 * r + c] = (double)c2w[4 * r + c];
-        }
-        P.t[r] = c2w[4 * r + 3];
-    }
     P.alpha_min = o.alpha_min;
     P.alpha_max = o.alpha_max;
     P.t_min = o.t_min;
@@ -51,7 +64,7 @@ inline LidRender lidar_render_params(const Lidar &L, const sg_render_opts &o)
 
 // reference direction of a camera tile in world coordinates, split in two
 // floats: d_T = R r_T computed in double
-__device__ __forceinline__ void cam_tile_ref(const CamRender &P, const double *tile_dir, int tile,
+__device__ __forceinline__ void cam_tile_ref(const CamPose &P, const double *tile_dir, int tile,
                                              float *s_ref)
 {
     const double *r = tile_dir + 3 * tile;
@@ -65,7 +78,7 @@ __device__ __forceinline__ void cam_tile_ref(const CamRender &P, const double *t
 }
 
 // world-frame offset of a pixel's ray direction from its tile reference
-__device__ __forceinline__ void cam_ray_offset(const CamRender &P, const float4 e, float dd[3])
+__device__ __forceinline__ void cam_ray_offset(const CamPose &P, const float4 e, float dd[3])
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i) dd[i] = P.R[3 * i] * e.x + P.R[3 * i + 1] * e.y + P.R[3 * i + 2] * e.z;

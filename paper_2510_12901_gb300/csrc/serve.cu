@@ -9,6 +9,15 @@
 // projection and sort overlap another's compositing on the GPU.  Latency is
 // measured from submission to the completion of the request's last kernel.
 //
+// With graphs on, each slot keeps one captured CUDA graph per (scene,
+// sensor, options) combination: the render in capacity mode (pair buffers
+// sized ahead, no host wait for the pair count), replayed with one launch
+// per request.  The request's pose and its output / pose pointers reach the
+// replay through the frame's pinned RenderDesc, which the graph's first node
+// copies to the device.  A graph is dropped when one of the frame's buffers
+// has been reallocated since its capture, and after a replay that ran out of
+// pair capacity (that request is rendered again exactly).
+//
 // Every wait here is a host-side condition-variable wait with a timeout; no
 // kernel waits on another.
 #include <math.h>
@@ -19,6 +28,7 @@
 #include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -50,6 +60,46 @@ struct Result {
     sg_status status = SG_OK;
     double latency_ms = 0;
 };
+
+// A captured render of one (scene, sensor, options) combination on one slot.
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;          // kernel nodes, counted as launches per replay
+    int64_t cap = 0;              // pair capacity the graph was captured with
+    std::vector<void *> bufs;     // the frame's buffers at capture
+};
+
+static std::string graph_key(const sg_request &r)
+{
+    std::string k;
+    const uint64_t ids[3] = {(uint64_t)r.kind, r.scene ? r.scene->uid : 0,
+                             r.kind == SG_REQ_CAMERA ? (r.camera ? r.camera->uid : 0)
+                                                     : (r.lidar ? r.lidar->uid : 0)};
+    k.append((const char *)ids, sizeof(ids));
+    k.append((const char *)&r.opts, sizeof(r.opts));
+    return k;
+}
+
+static std::vector<void *> frame_bufs(Frame &f)
+{
+    std::vector<void *> v;
+    for_each_buf(f, [&](Buf &b) { v.push_back(b.p); });
+    return v;
+}
+
+static int64_t count_kernel_nodes(cudaGraph_t g)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int64_t k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
 
 // Workspace estimate of one request: per-Gaussian buffers, sort buffers
 // and records, per-ray state, and (tile, Gaussian) pairs at a generous 4
@@ -83,12 +133,138 @@ struct sg_server_s {
     uint64_t next_ticket = 1;
     bool stop = false;
     int in_flight = 0;
+    // graphs: per slot, per combination; largest pair count seen per combination
+    std::vector<std::unordered_map<std::string, GraphEntry>> graphs;
+    std::unordered_map<std::string, int64_t> max_pairs;
     // statistics
     std::vector<double> latencies;
     int64_t completed = 0, failed = 0, rays = 0, busy_peak = 0;
+    int64_t replays = 0, captures = 0, overflows = 0;
     Clock::time_point t_first, t_last;
     bool any = false;
 };
+
+static sg_status render_plain(const sg_request &r, sg_frame fr, cudaStream_t st)
+{
+    if (r.kind == SG_REQ_CAMERA)
+        return sg_render_camera(r.scene, r.camera, r.c2w, &r.opts, fr, r.d_out[0], r.d_out[1],
+                                r.d_out[2], st);
+    return sg_render_lidar(r.scene, r.lidar, r.d_col_c2w, &r.opts, fr, r.d_out[0], r.d_out[1],
+                           r.d_out[2], r.d_out[3], st);
+}
+
+static sg_status finish(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaError_t e = cudaEventRecord(ev, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev);
+    return e == cudaSuccess ? SG_OK : cuda_status(e, "request completion");
+}
+
+static void note_pairs(sg_server S, const std::string &key, int64_t K)
+{
+    std::lock_guard<std::mutex> lk(S->mu);
+    int64_t &m = S->max_pairs[key];
+    if (K > m) m = K;
+}
+
+static void drop_graph(GraphEntry &g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = GraphEntry();
+}
+
+// One request on `slot`, with graphs: replay, or warm up and capture.
+static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_frame frame,
+                                cudaStream_t st, cudaEvent_t ev)
+{
+    Frame &fr = frame->f;
+    const std::string key = graph_key(r);
+    GraphEntry &g = S->graphs[slot][key];
+    sg_status s;
+    if (g.exec && g.bufs == frame_bufs(fr)) {
+        // replay: the request's parameters through the pinned descriptor
+        RenderDesc &D = *fr.h_desc;
+        if (r.kind == SG_REQ_CAMERA) {
+            memcpy(D.c2w, r.c2w, sizeof(D.c2w));
+            D.poses = nullptr;
+            for (int i = 0; i < 3; ++i) D.out[i] = r.d_out[i];
+            D.out[3] = nullptr;
+            memcpy(fr.c2w, r.c2w, sizeof(fr.c2w));
+        } else {
+            memset(D.c2w, 0, sizeof(D.c2w));
+            D.poses = r.d_col_c2w;
+            for (int i = 0; i < 4; ++i) D.out[i] = r.d_out[i];
+            fr.d_lidar_poses = r.d_col_c2w;
+        }
+        fr.k_cap = g.cap;
+        cudaError_t e = cudaGraphLaunch(g.exec, st);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGraphLaunch");
+        count_launches(g.kernels);
+        if ((s = finish(ev, st)) != SG_OK) return s;
+        const int64_t dropped = fr.h_scalars[3], kept = fr.h_scalars[1];
+        if (dropped == 0) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->replays++;
+            return SG_OK;
+        }
+        // out of pair capacity: render exactly, capture anew next time
+        drop_graph(g);
+        fr.k_cap = 0;
+        if ((s = render_plain(r, frame, st)) != SG_OK) return s;
+        if ((s = finish(ev, st)) != SG_OK) return s;
+        note_pairs(S, key, fr.n_pairs > kept + dropped ? fr.n_pairs : kept + dropped);
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->overflows++;
+        return SG_OK;
+    }
+    drop_graph(g);
+    int64_t known = 0;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->max_pairs.find(key);
+        if (it != S->max_pairs.end()) known = it->second;
+    }
+    if (known == 0) {   // first sight of this combination: exact render
+        fr.k_cap = 0;
+        if ((s = render_plain(r, frame, st)) != SG_OK) return s;
+        if ((s = finish(ev, st)) != SG_OK) return s;
+        note_pairs(S, key, fr.n_pairs);
+        return SG_OK;
+    }
+    // capacity-mode render (grows the workspace as needed), then capture
+    const int64_t cap = std::min<int64_t>(known + known / 4 + 65536, 0x7fffffffLL);
+    fr.k_cap = cap;
+    if ((s = render_plain(r, frame, st)) != SG_OK) return s;
+    if ((s = finish(ev, st)) != SG_OK) return s;
+    if (fr.h_scalars[3] != 0) {
+        const int64_t need = (int64_t)fr.h_scalars[1] + fr.h_scalars[3];
+        fr.k_cap = 0;
+        if ((s = render_plain(r, frame, st)) != SG_OK) return s;
+        if ((s = finish(ev, st)) != SG_OK) return s;
+        note_pairs(S, key, need);
+        return SG_OK;
+    }
+    cudaGraph_t graph = nullptr;
+    capture_guard() = true;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    sg_status cs = e == cudaSuccess ? render_plain(r, frame, st) : SG_ERR_CUDA;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(st, &graph);
+    capture_guard() = false;
+    if (cs == SG_OK && e == cudaSuccess && graph) {
+        cudaGraphExec_t exec = nullptr;
+        if (cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+            g.exec = exec;
+            g.kernels = count_kernel_nodes(graph);
+            g.cap = cap;
+            g.bufs = frame_bufs(fr);
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->captures++;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();   // a failed capture leaves no graph; the result is complete
+    return SG_OK;
+}
 
 static void worker_main(sg_server S, int slot)
 {
@@ -118,20 +294,15 @@ static void worker_main(sg_server S, int slot)
 
         const sg_request &r = job.req;
         sg_status s;
-        int64_t nrays = 0;
-        if (r.kind == SG_REQ_CAMERA) {
-            s = sg_render_camera(r.scene, r.camera, r.c2w, &r.opts, fr, r.d_out[0], r.d_out[1],
-                                 r.d_out[2], st);
-            if (r.camera) nrays = (int64_t)r.camera->c.width * r.camera->c.height;
+        const int64_t nrays = r.kind == SG_REQ_CAMERA
+                                  ? (int64_t)r.camera->c.width * r.camera->c.height
+                                  : (int64_t)r.lidar->l.n_beams * r.lidar->l.n_cols;
+        if (S->cfg.use_graphs) {
+            s = render_graphed(S, slot, r, fr, st, ev);
         } else {
-            s = sg_render_lidar(r.scene, r.lidar, r.d_col_c2w, &r.opts, fr, r.d_out[0],
-                                r.d_out[1], r.d_out[2], r.d_out[3], st);
-            if (r.lidar) nrays = (int64_t)r.lidar->l.n_beams * r.lidar->l.n_cols;
-        }
-        if (s == SG_OK) {
-            cudaEventRecord(ev, st);
-            cudaError_t e = cudaEventSynchronize(ev);
-            if (e != cudaSuccess) s = cuda_status(e, "request completion");
+            fr->f.k_cap = 0;
+            s = render_plain(r, fr, st);
+            if (s == SG_OK) s = finish(ev, st);
         }
         const Clock::time_point t_done = Clock::now();
 
@@ -167,6 +338,7 @@ sg_server_config sg_default_server_config(void)
     c.n_slots = 4;
     c.memory_budget = 0;
     c.queue_capacity = 4096;
+    c.use_graphs = 1;
     return c;
 }
 
@@ -181,6 +353,7 @@ sg_status sg_server_create(const sg_server_config *cfg, sg_server *out)
     sg_server S = new (std::nothrow) sg_server_s;
     if (!S) { set_error("host allocation failed"); return SG_ERR_OOM; }
     S->cfg = *cfg;
+    S->graphs.resize(cfg->n_slots);
     cudaGetDevice(&S->device);
     for (int i = 0; i < cfg->n_slots; ++i) {
         cudaStream_t st;
@@ -274,6 +447,9 @@ sg_status sg_server_stats(sg_server S, sg_server_report *out)
     out->rays = S->rays;
     out->peak_in_flight = S->busy_peak;
     out->queued = (int64_t)S->queue.size();
+    out->graph_replays = S->replays;
+    out->graph_captures = S->captures;
+    out->overflow_rerenders = S->overflows;
     std::vector<double> l = S->latencies;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
@@ -303,6 +479,7 @@ sg_status sg_server_reset_stats(sg_server S)
     std::lock_guard<std::mutex> lk(S->mu);
     S->latencies.clear();
     S->completed = S->failed = S->rays = S->busy_peak = 0;
+    S->replays = S->captures = S->overflows = 0;
     S->any = false;
     return SG_OK;
 }
@@ -317,6 +494,8 @@ void sg_server_destroy(sg_server S)
     S->cv_work.notify_all();
     for (auto &t : S->workers)
         if (t.joinable()) t.join();
+    for (auto &m : S->graphs)
+        for (auto &kv : m) drop_graph(kv.second);
     for (auto st : S->streams) cudaStreamDestroy(st);
     for (auto f : S->frames) sg_frame_destroy(f);
     delete S;

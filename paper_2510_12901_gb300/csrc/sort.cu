@@ -330,9 +330,11 @@ sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count, const ui
 
 // ------------------------------------------------------------------ binning
 
+// Pairs at positions >= cap are not written (capacity mode: the caller
+// learns of them from the dropped-pairs count).
 __global__ void k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
                       const uint32_t *__restrict__ d_nvalid, const int4 *__restrict__ tiles,
-                      int ntx, int wrap_x, uint32_t *__restrict__ keys,
+                      int ntx, int wrap_x, uint32_t cap, uint32_t *__restrict__ keys,
                       uint32_t *__restrict__ vals)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -344,38 +346,59 @@ __global__ void k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restri
         for (int tx = t.x; tx <= t.y; ++tx) {
             int x = tx;
             if (wrap_x) { x %= ntx; if (x < 0) x += ntx; }
-            keys[o] = (uint32_t)(ty * ntx + x);
-            vals[o] = g;
+            if (o < cap) {
+                keys[o] = (uint32_t)(ty * ntx + x);
+                vals[o] = g;
+            }
             ++o;
         }
 }
 
 sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_nvalid,
-                    int64_t n, const int4 *d_tiles, int ntx, int wrap_x, uint32_t *d_keys,
-                    uint32_t *d_vals, cudaStream_t st)
+                    int64_t n, const int4 *d_tiles, int ntx, int wrap_x, int64_t cap,
+                    uint32_t *d_keys, uint32_t *d_vals, cudaStream_t st)
 {
     if (n == 0) return SG_OK;
     k_bin<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_ids, d_offsets, d_nvalid, d_tiles, ntx,
-                                                       wrap_x, d_keys, d_vals);
+                                                       wrap_x, (uint32_t)cap, d_keys, d_vals);
     SG_LAUNCHED();
     return SG_OK;
 }
 
-__global__ void k_ranges(const uint32_t *__restrict__ keys, int64_t K, uint2 *__restrict__ ranges)
+__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
+                         uint2 *__restrict__ ranges)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t K = *d_K;
     if (i >= K) return;
     uint32_t t = keys[i];
     if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
     if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
-sg_status tile_ranges(const uint32_t *d_keys, int64_t K, uint2 *d_ranges, int64_t ntiles,
-                      cudaStream_t st)
+sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
+                      int64_t ntiles, cudaStream_t st)
 {
     SG_CUDA(cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * ntiles, st));
-    if (K == 0) return SG_OK;
-    k_ranges<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(d_keys, K, d_ranges);
+    if (K_max == 0) return SG_OK;
+    k_ranges<<<(unsigned)((K_max + 255) / 256), 256, 0, st>>>(d_keys, d_K, d_ranges);
+    SG_LAUNCHED();
+    return SG_OK;
+}
+
+// Capacity mode: keep at most `cap` pairs; d_K is clamped to it and the
+// number of pairs beyond it is stored in d_dropped (0 when all fit).
+__global__ void k_clamp_pairs(uint32_t *__restrict__ d_K, uint32_t cap,
+                              uint32_t *__restrict__ d_dropped)
+{
+    const uint32_t K = *d_K;
+    *d_dropped = K > cap ? K - cap : 0u;
+    if (K > cap) *d_K = cap;
+}
+
+sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStream_t st)
+{
+    k_clamp_pairs<<<1, 1, 0, st>>>(d_K, (uint32_t)cap, d_dropped);
     SG_LAUNCHED();
     return SG_OK;
 }

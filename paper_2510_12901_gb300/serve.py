@@ -16,9 +16,10 @@ from . import simgut as sg
 
 
 class Server:
-    def __init__(self, n_slots=4, memory_budget=0, queue_capacity=4096):
+    def __init__(self, n_slots=4, memory_budget=0, queue_capacity=4096, use_graphs=True):
         cfg = sg.sg_default_server_config(n_slots=n_slots, memory_budget=memory_budget,
-                                          queue_capacity=queue_capacity)
+                                          queue_capacity=queue_capacity,
+                                          use_graphs=int(bool(use_graphs)))
         self.handle = sg.sg_server_create(cfg)
 
     @staticmethod

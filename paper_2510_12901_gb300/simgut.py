@@ -53,7 +53,7 @@ class sg_grads(C.Structure):
 
 class sg_server_config(C.Structure):
     _fields_ = [("n_slots", C.c_int), ("memory_budget", C.c_size_t),
-                ("queue_capacity", C.c_int)]
+                ("queue_capacity", C.c_int), ("use_graphs", C.c_int)]
 
 
 class sg_request(C.Structure):
@@ -65,7 +65,8 @@ class sg_request(C.Structure):
 class sg_server_report(C.Structure):
     _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("rays", C.c_int64),
                 ("peak_in_flight", C.c_int64), ("queued", C.c_int64),
-                ("latency_mean_ms", C.c_double), ("latency_p50_ms", C.c_double),
+                ("graph_replays", C.c_int64), ("graph_captures", C.c_int64),
+                ("overflow_rerenders", C.c_int64), ("latency_mean_ms", C.c_double), ("latency_p50_ms", C.c_double),
                 ("latency_p99_ms", C.c_double), ("latency_max_ms", C.c_double),
                 ("span_s", C.c_double), ("mrays_per_s", C.c_double)]
 
@@ -92,6 +93,8 @@ _SIGNATURES = {
     "sg_default_opts": (sg_render_opts, []),
     "sg_frame_create": (C.c_int, [C.POINTER(_H)]),
     "sg_frame_destroy": (None, [_H]),
+    "sg_frame_set_capacity": (C.c_int, [_H, C.c_int64]),
+    "sg_frame_dropped_pairs": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sg_render_camera": (C.c_int, [_H, _H, C.POINTER(C.c_float), C.POINTER(sg_render_opts), _H,
                                    _P, _P, _P, _P]),
     "sg_render_lidar": (C.c_int, [_H, _H, _P, C.POINTER(sg_render_opts), _H, _P, _P, _P, _P,
@@ -339,6 +342,17 @@ def sg_frame_timing(frame):
     ms = (C.c_float * 4)()
     _check(load().sg_frame_timing(frame, ms))
     return list(ms)
+
+
+def sg_frame_set_capacity(frame, max_pairs):
+    _check(load().sg_frame_set_capacity(frame, int(max_pairs)))
+
+
+def sg_frame_dropped_pairs(frame):
+    """(dropped, kept) pairs of the last capacity-mode render on `frame`."""
+    d, k = C.c_int64(), C.c_int64()
+    _check(load().sg_frame_dropped_pairs(frame, C.byref(d), C.byref(k)))
+    return d.value, k.value
 
 
 # ------------------------------------------------------------ torch helpers

@@ -133,6 +133,45 @@ def tiny_scene(seed: int = 0, n: int = 4096) -> Scene:
                  rgb.astype(np.float32), FEATURES_RGB, 0)
 
 
+def layered_scene(seed: int = 5, n: int = 20000) -> Scene:
+    """Translucent layers in front of tiny_camera, for tile lists of several
+    thousand entries whose rays reach T_min at different depths.
+
+    n Gaussians at distances 3 + 27 (k + 1/2) / n m from the camera centre
+    (k a random permutation of 0..n-1, so that no two depth keys are within
+    rounding of each other), in directions (u, 1, -v) with u, v ~
+    U(-0.55, 0.55); std-dev 0.15 x distance x U(0.6, 1.4) (second axis
+    x U(0.7, 1.3)), random rotation, opacity 0.006 + 0.003 w U(0.5, 1.5) with
+    w = (u + 0.55) / 1.1 rising from the left edge to the right; plus n/50
+    opaque (U(0.8, 0.99)) small Gaussians at depth U(3, 4) over the upper-left
+    quarter.  RGB colour U[0,1]."""
+    rng = np.random.default_rng(seed)
+    r = 3.0 + 27.0 * (rng.permutation(n) + 0.5) / n
+    u = rng.uniform(-0.55, 0.55, n)
+    v = rng.uniform(-0.55, 0.55, n)
+    dirs = np.stack([u, np.ones(n), -v], 1)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    means = dirs * r[:, None] + np.array([0.0, -10.0, 0.0])
+    s = 0.15 * r * rng.uniform(0.6, 1.4, n)
+    log_scales = np.log(np.stack([s, s * rng.uniform(0.7, 1.3, n), s], 1))
+    quats = _random_unit_quats(rng, n)
+    w = (u + 0.55) / 1.1
+    opacity = 0.006 + 0.003 * w * rng.uniform(0.5, 1.5, n)
+    m = n // 50
+    d2 = rng.uniform(3.0, 4.0, m)
+    u2 = rng.uniform(-0.5, -0.1, m)
+    v2 = rng.uniform(0.1, 0.5, m)
+    means = np.concatenate([means, np.stack([u2 * d2, d2 - 10.0, -v2 * d2], 1)])
+    s2 = np.log(0.05 * d2)
+    log_scales = np.concatenate([log_scales, np.stack([s2, s2, s2], 1)])
+    quats = np.concatenate([quats, _random_unit_quats(rng, m)])
+    opacity = np.concatenate([opacity, rng.uniform(0.8, 0.99, m)])
+    rgb = rng.uniform(0.0, 1.0, size=(n + m, 3))
+    return Scene(means.astype(np.float32), log_scales.astype(np.float32),
+                 quats.astype(np.float32), opacity.astype(np.float32),
+                 rgb.astype(np.float32), FEATURES_RGB, 0)
+
+
 def _look_c2w(eye, forward, down):
     """OpenCV camera-to-world: columns are the camera x (right), y (down) and
     z (forward) axes expressed in world coordinates."""

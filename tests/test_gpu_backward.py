@@ -84,6 +84,16 @@ def test_camera_backward_tiny(sg, O64):
     compare_grads(Gg, Go, "tiny")
 
 
+def test_camera_backward_long_segmented_lists(sg, O64):
+    # lists of several 1024-entry segments, rays stopping in most of them
+    sc, cam = syn.layered_scene(), syn.tiny_camera()
+    orc = O64.render_camera(sc, cam)
+    g = upstream(orc, np.random.default_rng(2))
+    Go = O64.backward_camera(sc, cam, *g)
+    Gg = camera_backward(sg, sg.Scene(sc), sg.Camera(cam), cam, *g, sc.n, 3)
+    compare_grads(Gg, Go, "layered")
+
+
 def _street_crop(n=30000, seed=5):
     sc = syn.street_scene(n, seed=seed, kind="camera", length=40.0)
     fish, _ = syn.street_cameras()

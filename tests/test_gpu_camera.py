@@ -13,6 +13,7 @@ from paper_2510_12901_gb300 import synthetic as syn
 from tests import parity as par
 
 pytestmark = pytest.mark.gpu
+SEG_LEN = 1024      # the compositing's segment length (kSegLen in the library)
 
 
 @pytest.fixture(scope="module")
@@ -157,6 +158,39 @@ def test_host_output_path_matches_device_path(sg):
     assert np.array_equal(h_rgb.reshape(cam.height, cam.width, 3), g["rgb"])
     assert np.array_equal(h_a.reshape(cam.height, cam.width), g["alpha"])
     assert np.array_equal(h_d.reshape(cam.height, cam.width), g["depth"])
+
+
+def test_long_lists_composited_in_segments(sg, O64):
+    """Tile lists of 3.5k-7.7k entries: the compositing splits lists longer
+    than SEG_LEN entries into independent segments and combines them.  Rays
+    stop at T_min in the first segment and in later ones up to the eighth;
+    others never stop."""
+    sc, cam = syn.layered_scene(), syn.tiny_camera()
+    g = gpu_render(sg, sc, cam)
+    ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)
+    lens = ranges[:, 1].astype(np.int64) - ranges[:, 0]
+    assert lens.max() > 7 * SEG_LEN and lens.min() > 3 * SEG_LEN
+    orc = O64.render_camera(sc, cam)
+    px = np.arange(cam.width * cam.height)
+    tile = (px // cam.width // 16) * ((cam.width + 15) // 16) + (px % cam.width) // 16
+    visited = orc["n_visited"].astype(np.int64)
+    stopped = visited < lens[tile]
+    seg = (visited - 1) // SEG_LEN
+    for s, at_least in ((0, 500), (2, 200), (3, 500), (4, 500), (5, 200), (6, 300), (7, 20)):
+        assert (stopped & (seg == s)).sum() >= at_least, s
+    assert (~stopped & (visited > SEG_LEN)).sum() >= 500
+    # thousands of threshold decisions per ray: ~6.5% of the rays see one
+    # within rounding of its threshold (alpha_min, box edge, T_min)
+    par.compare_camera_rays(g["rgb"].reshape(-1, 3), g["alpha"].reshape(-1),
+                            g["depth"].reshape(-1), orc, max_excluded=0.08, label="layered")
+    ok = ~par.ambiguous_rays(orc)
+    st = g["frame"].field(sg.FIELD_RAY_STATE, np.float32, 4)
+    assert np.abs(st[ok, 0] - orc["t_final"][ok]).max() <= par.TOL_ABS
+    # the list position of the last composited entry: before the stopping
+    # entry, and within the list
+    last = g["frame"].field(sg.FIELD_N_CONTRIB, np.uint32).astype(np.int64)
+    assert np.all(last[ok & stopped] < visited[ok & stopped])
+    assert np.all(last <= lens[tile])
 
 
 def test_repeated_renders_are_deterministic(sg):

@@ -163,3 +163,32 @@ def test_full_sweep_sampled_parity(sg, O32, O64):
     tiles = rng.choice(nth * nphi, 300, replace=False)
     par.compare_lists(ids, ranges, o_ids, o_ranges, tiles, amb, key, "full")
 
+
+def test_gaussians_straddling_the_azimuth_seam(sg, O32, O64):
+    """Gaussians right behind the sensor (azimuth +-180 deg, where column 0
+    and the last column meet): the tile range wraps, the culling query splits
+    in two, and the rays on both sides of the seam see the same Gaussian."""
+    L = syn.street_lidar(n_cols=512, static=True)
+    rng = np.random.default_rng(21)
+    n = 300
+    sc = syn.street_scene(n, seed=21, kind="lidar", length=10.0)
+    ox, oy, oz = L.col_c2w[0][3], L.col_c2w[0][7], L.col_c2w[0][11]
+    ang = np.pi + rng.normal(0, 0.02, n)          # straddle +-180 deg
+    rad = rng.uniform(4, 12, n)
+    sc.means[:] = np.stack([ox + rad * np.cos(ang), oy + rad * np.sin(ang),
+                            oz + rng.uniform(-1.5, 0.5, n)], 1).astype(np.float32)
+    sc.log_scales[:] = np.log(rng.uniform(0.05, 0.3, (n, 3))).astype(np.float32)
+    sc.opacity[:] = rng.uniform(0.3, 0.95, n).astype(np.float32)
+    g = gpu_render(sg, sc, L)
+    orc = O64.render_lidar(sc, L)
+    par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
+                           max_excluded=0.02, label="seam")
+    P, _ = O64.project_lidar(sc, L)
+    wraps = (P["valid"] == 1) & ((P["tiles"][:, 0] < 0) | (P["tiles"][:, 1] >= _n_theta(O64, L)))
+    assert wraps.sum() > 20                       # the case is exercised
+    hit = orc["alpha"].reshape(L.n_beams, L.n_cols) > 0.5
+    assert hit[:, 0].any() and hit[:, -1].any()   # both sides of the seam
+
+
+def _n_theta(O, L):
+    return O.lidar_setup(L)["n_theta"]

@@ -31,31 +31,84 @@ def _outs(W, i):
     return [torch.full((L.n_beams, L.n_cols), -7.0, device="cuda") for _ in range(4)]
 
 
-def test_results_identical_alone_and_in_the_mix(W):
+@pytest.fixture(scope="module")
+def alone(W):
+    """Every request rendered alone through the plain render call."""
     import torch
-    from paper_2510_12901_gb300 import serve
     from paper_2510_12901_gb300 import simgut as sg
-    n = len(W.kinds)
-    alone = []
+    out = []
     fr = sg.Frame()
-    for i in range(n):
+    for i in range(len(W.kinds)):
         o = _outs(W, i)
         W.render_plain(i, fr, torch.cuda.current_stream().cuda_stream, outs=o)
-        alone.append(o)
+        out.append(o)
     torch.cuda.synchronize()
-    srv = serve.Server(n_slots=4)
-    mixed = [_outs(W, i) for i in range(n)]
-    tickets = [srv.submit(W.request(i, outs=mixed[i])) for i in range(n)]   # one burst
-    for t in tickets:
-        srv.wait(t, 120.0)
+    return out
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_results_identical_alone_and_in_the_mix(W, alone, graphs):
+    """Three bursts of the whole request stream.  With graphs, the first
+    request of each combination on a slot renders exactly, the second
+    captures, the rest replay; every result must equal the alone render."""
+    import torch
+    from paper_2510_12901_gb300 import serve
+    n = len(W.kinds)
+    srv = serve.Server(n_slots=4, use_graphs=graphs)
+    for burst in range(3):
+        mixed = [_outs(W, i) for i in range(n)]
+        tickets = [srv.submit(W.request(i, outs=mixed[i])) for i in range(n)]
+        for t in tickets:
+            srv.wait(t, 120.0)
+        for i in range(n):
+            for a, b in zip(alone[i], mixed[i]):
+                assert torch.equal(a, b), (burst, i, W.KINDS[W.kinds[i]])
     st = srv.stats()
     srv.close()
-    assert st["completed"] == n and st["failed"] == 0
+    assert st["completed"] == 3 * n and st["failed"] == 0
     assert st["peak_in_flight"] > 1            # requests really overlapped
-    for i in range(n):
-        for a, b in zip(alone[i], mixed[i]):
-            assert torch.equal(a, b), (i, W.KINDS[W.kinds[i]])
     assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
+    if graphs:
+        assert st["graph_captures"] >= 8 and st["graph_replays"] >= n
+        assert st["overflow_rerenders"] == 0
+    else:
+        assert st["graph_captures"] == 0 and st["graph_replays"] == 0
+
+
+def test_capacity_mode_matches_exact_and_reports_overflow(W):
+    """A render in capacity mode (no wait for the pair count) equals the
+    exact render when the pairs fit, and reports the dropped pairs, without
+    touching memory beyond its buffers, when they do not."""
+    import torch
+    from paper_2510_12901_gb300 import simgut as sg
+    i = next(i for i in range(len(W.kinds)) if W.KINDS[W.kinds[i]] == "fisheye")
+    st = torch.cuda.current_stream().cuda_stream
+    fr = sg.Frame()
+    ref = _outs(W, i)
+    W.render_plain(i, fr, st, outs=ref)
+    torch.cuda.synchronize()
+    K = sg.sg_frame_stats(fr.handle)[0]
+    with pytest.raises(sg.SimgutError):
+        sg.sg_frame_dropped_pairs(fr.handle)       # exact mode: nothing to report
+    sg.sg_frame_set_capacity(fr.handle, K + 1000)
+    o = _outs(W, i)
+    W.render_plain(i, fr, st, outs=o)
+    torch.cuda.synchronize()
+    assert sg.sg_frame_dropped_pairs(fr.handle) == (0, K)
+    for a, b in zip(ref, o):
+        assert torch.equal(a, b)
+    sg.sg_frame_set_capacity(fr.handle, K // 2)
+    o = _outs(W, i)
+    W.render_plain(i, fr, st, outs=o)
+    torch.cuda.synchronize()
+    assert sg.sg_frame_dropped_pairs(fr.handle) == (K - K // 2, K // 2)
+    assert all(torch.isfinite(t).all() for t in o)
+    sg.sg_frame_set_capacity(fr.handle, 0)
+    o = _outs(W, i)
+    W.render_plain(i, fr, st, outs=o)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, o):
+        assert torch.equal(a, b)
 
 
 def test_memory_admission_serialises_and_completes(W):

@@ -36,11 +36,13 @@ def _static_render(sg, S, C, cam):
     return rgb.cpu().numpy(), alpha.cpu().numpy(), depth.cpu().numpy()
 
 
-@pytest.mark.parametrize("kind", ["tiny", "fisheye-sh"])
+@pytest.mark.parametrize("kind", ["tiny", "fisheye-sh", "layered"])
 def test_static_render_matches_allocating_render_twice(sg, kind):
     import torch
     if kind == "tiny":
         sc, cam = syn.tiny_scene(), syn.tiny_camera()
+    elif kind == "layered":      # tile lists long enough to be split into segments
+        sc, cam = syn.layered_scene(), syn.tiny_camera()
     else:
         sc = syn.street_scene(20000, seed=3, kind="camera", length=40.0)
         fish, _ = syn.street_cameras()

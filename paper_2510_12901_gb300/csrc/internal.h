@@ -16,9 +16,16 @@ constexpr int kTile = 16;                 // camera tile edge (pixels)
 constexpr int kCamThreads = kTile * kTile;
 constexpr int kLidarColsMax = 4;          // distinct columns per LiDAR work item
 constexpr int kLidarWarps = 4;            // warps (work items) per LiDAR render block
-// Camera tile lists longer than this are composited in segments of this many
-// entries, each an independent work item, and combined afterwards.
-constexpr uint32_t kSegLen = 1024;
+// Camera tile lists longer than the segment length are composited in
+// segments of that many entries, each an independent work item, and
+// combined afterwards.  kSegLen is the default of a frame (a build may set
+// SG_SEG_LEN to tune it); the allocation-free render uses kSegLenStatic,
+// which needs less workspace.
+#ifndef SG_SEG_LEN
+#define SG_SEG_LEN 256
+#endif
+constexpr uint32_t kSegLen = SG_SEG_LEN;
+constexpr uint32_t kSegLenStatic = 1024;
 
 void set_error(const char *fmt, ...);
 sg_status cuda_status(cudaError_t e, const char *what);
@@ -136,6 +143,7 @@ struct Frame {
     // capacity mode: > 0 = the pair buffers hold this many pairs and no
     // step waits for the pair count (pairs beyond it are dropped and counted)
     int64_t k_cap = 0;
+    uint32_t seg_len = kSegLen;     // camera list segment length
     int64_t n_pairs = 0, n_tiles = 0, n_rays = 0, n_gauss = 0;
     int pair_buf = 0;  // which of pkeys/pvals holds the sorted result
     int kind = -1;     // 0 camera, 1 lidar
@@ -158,29 +166,32 @@ uint64_t next_uid();            // identity of a scene / sensor handle
 
 constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Upper bounds of the camera work-item buffers for `ntiles` tiles and
-// `n_pairs` listed pairs: segments per tile are 1 for a list of at most
-// kSegLen entries and ceil(len / kSegLen) above, so the items are at most
-// 8 (ntiles + n_pairs / kSegLen) and the partial slots (segments of long
-// tiles) at most min(2 n_pairs / kSegLen, ntiles + n_pairs / kSegLen).
+// Upper bounds of the camera work-item buffers for `ntiles` tiles,
+// `n_pairs` listed pairs and segment length L: segments per tile are 1 for a
+// list of at most L entries and ceil(len / L) above, so the items are at
+// most 8 (ntiles + n_pairs / L) and the partial slots (segments of long
+// tiles) at most min(2 n_pairs / L, ntiles + n_pairs / L).  Buffers: per
+// tile (segments, first partial slot) and the first item of the tile in
+// launch order, the items, the arrival counters of long (tile, sub-block)s.
 struct CamWorkSize {
     int64_t max_items = 0, max_slots = 0;
-    size_t info_bytes = 0, items_bytes = 0, arrive_bytes = 0, work_bytes = 0,
+    size_t info_bytes = 0, off_bytes = 0, items_bytes = 0, arrive_bytes = 0, work_bytes = 0,
            partial_bytes = 0;
 };
-constexpr CamWorkSize cam_work_size(int64_t ntiles, int64_t n_pairs)
+constexpr CamWorkSize cam_work_size(int64_t ntiles, int64_t n_pairs, uint32_t seg_len)
 {
     CamWorkSize w;
-    const int64_t per = n_pairs / kSegLen;
+    const int64_t per = n_pairs / (int64_t)seg_len;
     const int64_t nt1 = ntiles > 0 ? ntiles : 1;
     w.max_items = 8 * (ntiles + per);
     w.max_slots = 2 * per < ntiles + per ? 2 * per : ntiles + per;
     const int64_t items1 = w.max_items > 0 ? w.max_items : 1;
     const int64_t slots1 = w.max_slots > 0 ? w.max_slots : 1;
     w.info_bytes = al256(8 * (size_t)nt1);
+    w.off_bytes = al256(4 * (size_t)nt1);
     w.items_bytes = al256(8 * (size_t)items1);
     w.arrive_bytes = al256(4 * 8 * (size_t)slots1);
-    w.work_bytes = w.info_bytes + w.items_bytes + w.arrive_bytes;
+    w.work_bytes = w.info_bytes + w.off_bytes + w.items_bytes + w.arrive_bytes;
     w.partial_bytes = 2 * 16 * 256 * (size_t)slots1;
     return w;
 }

@@ -28,7 +28,7 @@ constexpr size_t kStG4 = al(4 * kStMaxGauss);
 constexpr size_t kStP4 = al(4 * kStMaxPairs);
 constexpr size_t kStHist = al(4 * 2 * 256 * ((kStMaxPairs + 2047) / 2048));
 constexpr size_t kStScan = al(4 * 4096);
-constexpr CamWorkSize kStWork = cam_work_size(kStMaxTiles, kStMaxPairs);
+constexpr CamWorkSize kStWork = cam_work_size(kStMaxTiles, kStMaxPairs, kSegLenStatic);
 constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, tiles, cov2d, mean2d
                             2 * kStG4 +                          // depth, count
                             4 * kStG4 +                          // depth-sort keys/values x2
@@ -145,6 +145,7 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     carve(fr.submask, cur, al(kStMaxPairs));
     carve(fr.camwork, cur, kStWork.work_bytes);
     carve(fr.partials, cur, kStWork.partial_bytes);
+    fr.seg_len = kSegLenStatic;
     carve(fr.scalars, cur, al(64));
     carve(fr.desc, cur, al(sizeof(RenderDesc)));
     fr.n_gauss = sc.n;

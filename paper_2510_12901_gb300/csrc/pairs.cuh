@@ -66,29 +66,28 @@ __device__ __forceinline__ void cam_entry(const GRec &r, const float o[3], const
 struct PairEval {
     float n[3];      // num = cof(M)(v x d)
     float e[3];      // den = M d
-    float inv;       // 1 / |den|^2
+    float inv;       // 1 / |den|^2 (fast reciprocal, within 2 ulp)
     float D2, tau, rho, alpha;
     bool clamped;    // alpha hit alpha_max
 };
 
-// Evaluate one camera pair; returns false when the entry does not composite
-// at this ray (outside the box, behind the origin, or below alpha_min).
-// Branch-free: every value is computed and the tests combined at the end, so
-// that evaluations of consecutive entries can overlap.
-__device__ __forceinline__ bool cam_pair(const float4 q0, const float4 q1, const float4 q2,
-                                         const float4 m0, const float4 m1, const float4 m2,
-                                         const float4 mv, const float4 rc, const float dd[3],
-                                         float rx, float ry, float alpha_min, float alpha_max,
-                                         PairEval &pe)
+// Evaluate one camera pair whose extent-box test is already known (in_box);
+// returns false when the entry does not composite at this ray (outside the
+// box, behind the origin, or below alpha_min).  Branch-free: every value is
+// computed and the tests combined at the end, so that evaluations of
+// consecutive entries can overlap.
+__device__ __forceinline__ bool cam_pair_in(const float4 q0, const float4 q1, const float4 q2,
+                                            const float4 m0, const float4 m1, const float4 m2,
+                                            const float4 mv, bool in_box, const float dd[3],
+                                            float alpha_min, float alpha_max, PairEval &pe)
 {
-    const bool in_box = rx >= rc.x && rx <= rc.y && ry >= rc.z && ry <= rc.w;
     pe.n[0] = q0.w + q0.x * dd[0] + q0.y * dd[1] + q0.z * dd[2];
     pe.n[1] = q1.w + q1.x * dd[0] + q1.y * dd[1] + q1.z * dd[2];
     pe.n[2] = q2.w + q2.x * dd[0] + q2.y * dd[1] + q2.z * dd[2];
     pe.e[0] = m0.w + m0.x * dd[0] + m0.y * dd[1] + m0.z * dd[2];
     pe.e[1] = m1.w + m1.x * dd[0] + m1.y * dd[1] + m1.z * dd[2];
     pe.e[2] = m2.w + m2.x * dd[0] + m2.y * dd[1] + m2.z * dd[2];
-    pe.inv = 1.f / (pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
+    pe.inv = __fdividef(1.f, pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
     pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
     pe.tau = (mv.x * pe.e[0] + mv.y * pe.e[1] + mv.z * pe.e[2]) * pe.inv;
     pe.rho = __expf(-0.5f * pe.D2);
@@ -96,6 +95,44 @@ __device__ __forceinline__ bool cam_pair(const float4 q0, const float4 q1, const
     pe.clamped = a > alpha_max;
     pe.alpha = fminf(a, alpha_max);
     return in_box && pe.tau > 0.f && pe.alpha >= alpha_min;
+}
+
+// The per-ray extent test: the pixel centre (rx, ry) inside the box rc.
+__device__ __forceinline__ bool in_rect(const float4 rc, float rx, float ry)
+{
+    return rx >= rc.x && rx <= rc.y && ry >= rc.z && ry <= rc.w;
+}
+
+__device__ __forceinline__ bool cam_pair(const float4 q0, const float4 q1, const float4 q2,
+                                         const float4 m0, const float4 m1, const float4 m2,
+                                         const float4 mv, const float4 rc, const float dd[3],
+                                         float rx, float ry, float alpha_min, float alpha_max,
+                                         PairEval &pe)
+{
+    return cam_pair_in(q0, q1, q2, m0, m1, m2, mv, in_rect(rc, rx, ry), dd, alpha_min,
+                       alpha_max, pe);
+}
+
+// Which pixel centres of an 8x4 sub-block with first pixel (x0, y0) lie in
+// the box rc: bit 8 r + c for pixel (x0 + c, y0 + r).  The same float
+// comparisons as in_rect.
+__device__ __forceinline__ uint32_t subblock_lanes(const float4 rc, int x0, int y0)
+{
+    uint32_t cols = 0, rows = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float x = (float)(x0 + c) + 0.5f;
+        cols |= (uint32_t)(x >= rc.x && x <= rc.y) << c;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float y = (float)(y0 + r) + 0.5f;
+        rows |= (uint32_t)(y >= rc.z && y <= rc.w) << r;
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) m |= ((rows >> r) & 1u) ? cols << (8 * r) : 0u;
+    return m;
 }
 
 // LiDAR entries keep per-column quantities (each column has its own sensor
@@ -165,7 +202,7 @@ __device__ __forceinline__ bool lidar_pair(float (*s)[32], int j, int sb, float 
     pe.e[0] = s[0][j] * d[0] + s[1][j] * d[1] + s[2][j] * d[2];
     pe.e[1] = s[3][j] * d[0] + s[4][j] * d[1] + s[5][j] * d[2];
     pe.e[2] = s[6][j] * d[0] + s[7][j] * d[1] + s[8][j] * d[2];
-    pe.inv = 1.f / (pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
+    pe.inv = __fdividef(1.f, pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
     pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
     pe.tau = (s[sb + 6][j] * pe.e[0] + s[sb + 7][j] * pe.e[1] + s[sb + 8][j] * pe.e[2]) * pe.inv;
     if (!(pe.tau > 0.f)) return false;

@@ -64,15 +64,17 @@ __device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *s
 
 // Work items of the camera compositing.  Tiles are taken in (coarsely)
 // decreasing list length, so the longest start first.  A tile whose list is
-// longer than kSegLen entries is split along the list into ceil(len/kSegLen)
-// segments; every (tile, segment) gives eight items, one per 8x4 sub-block.
-// Per tile: (segments, first partial slot); per item: (tile, seg << 3 | sub).
-// The arrival counters of the long tiles and the item counter of the
-// compositing kernel are reset here.  One CTA does it all.
+// longer than seg_len entries is split along the list into
+// ceil(len / seg_len) segments; every (tile, segment) gives eight items, one
+// per 8x4 sub-block.  k_camera_items (one CTA) orders the tiles and assigns
+// per tile (segments, first partial slot) and its first item; k_emit_items
+// (one warp per tile) writes the items (tile, 8 seg + sub) and resets the
+// arrival counters of long tiles.  The item counter of the compositing
+// kernel is reset here too.
 __global__ void __launch_bounds__(1024)
-k_camera_items(const uint2 *__restrict__ ranges, int ntiles, uint32_t *__restrict__ order,
-               uint2 *__restrict__ tile_info, uint2 *__restrict__ items,
-               uint32_t *__restrict__ arrive, uint32_t *__restrict__ counts,
+k_camera_items(const uint2 *__restrict__ ranges, int ntiles, uint32_t seg_len,
+               uint32_t *__restrict__ order, uint2 *__restrict__ tile_info,
+               uint32_t *__restrict__ item_off, uint32_t *__restrict__ counts,
                uint32_t *__restrict__ counter)
 {
     __shared__ uint32_t s_cnt[33], s_off[33], s_w[33];
@@ -102,18 +104,14 @@ k_camera_items(const uint2 *__restrict__ ranges, int ntiles, uint32_t *__restric
         if (k < ntiles) {
             t = order[k];
             const uint32_t len = ranges[t].y - ranges[t].x;
-            nseg = len > kSegLen ? (len + kSegLen - 1) / kSegLen : 1u;
+            nseg = len > seg_len ? (len + seg_len - 1) / seg_len : 1u;
         }
         uint32_t tot_items, tot_parts;
         const uint32_t ib = item_run + block_excl_scan_1024(k < ntiles ? 8 * nseg : 0, s_w, tot_items);
         const uint32_t pb = part_run + block_excl_scan_1024(nseg > 1 ? nseg : 0, s_w, tot_parts);
         if (k < ntiles) {
             tile_info[t] = make_uint2(nseg, pb);
-            if (nseg > 1)
-                for (int q = 0; q < 8; ++q) arrive[pb * 8 + q] = 0u;
-            for (uint32_t sgi = 0; sgi < nseg; ++sgi)
-                for (uint32_t sub = 0; sub < 8; ++sub)
-                    items[ib + 8 * sgi + sub] = make_uint2(t, (sgi << 3) | sub);
+            item_off[k] = ib;
         }
         item_run += tot_items;
         part_run += tot_parts;
@@ -125,11 +123,26 @@ k_camera_items(const uint2 *__restrict__ ranges, int ntiles, uint32_t *__restric
     }
 }
 
+__global__ void k_emit_items(const uint32_t *__restrict__ order,
+                             const uint2 *__restrict__ tile_info,
+                             const uint32_t *__restrict__ item_off, int ntiles,
+                             uint2 *__restrict__ items, uint32_t *__restrict__ arrive)
+{
+    const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (k >= ntiles) return;
+    const uint32_t t = order[k];
+    const uint2 ti = tile_info[t];
+    const uint32_t ib = item_off[k], n = 8 * ti.x;
+    for (uint32_t i = lane; i < n; i += 32) items[ib + i] = make_uint2(t, i);
+    if (ti.x > 1 && lane < 8) arrive[ti.y * 8 + lane] = 0u;
+}
+
 // Per (tile, Gaussian) pair of a camera list: which of the tile's eight
-// 8x4 pixel sub-blocks the Gaussian's extent box can reach (bit w: columns
-// 8*(w&1).., rows 4*(w>>1)..).  One byte per pair, written after the tile
-// sort, so that the compositing warps scan contiguous bytes instead of
-// gathering every entry's box.
+// 8x4 pixel sub-blocks hold a pixel centre inside the Gaussian's extent box
+// (bit w: columns 8*(w&1).., rows 4*(w>>1)..), by the same float comparisons
+// as the per-ray test.  One byte per pair, written after the tile sort, so
+// that the compositing warps scan contiguous bytes and never stage an entry
+// that no pixel of their sub-block can see.
 __global__ void k_submask(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ ids,
                           const GRec *__restrict__ rec, const uint32_t *__restrict__ d_K, int ntx,
                           uint8_t *__restrict__ mask)
@@ -139,12 +152,20 @@ __global__ void k_submask(const uint32_t *__restrict__ keys, const uint32_t *__r
     const uint32_t t = keys[i];
     const float4 rc = rec[ids[i]].rect;
     const int tx = (int)(t % (uint32_t)ntx), ty = (int)(t / (uint32_t)ntx);
+    uint32_t cols = 0, rows = 0;
+#pragma unroll
+    for (int c = 0; c < kTile; ++c) {
+        const float x = (float)(tx * kTile + c) + 0.5f;
+        const float y = (float)(ty * kTile + c) + 0.5f;
+        cols |= (uint32_t)(x >= rc.x && x <= rc.y) << c;
+        rows |= (uint32_t)(y >= rc.z && y <= rc.w) << c;
+    }
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
-        const float x0 = (float)(tx * kTile + 8 * (w & 1)) + 0.5f;
-        const float y0 = (float)(ty * kTile + 4 * (w >> 1)) + 0.5f;
-        if (rc.x <= x0 + 7.f && rc.y >= x0 && rc.z <= y0 + 3.f && rc.w >= y0) m |= 1u << w;
+        const bool cx = ((cols >> (8 * (w & 1))) & 0xffu) != 0u;
+        const bool cy = ((rows >> (4 * (w >> 1))) & 0xfu) != 0u;
+        m |= (uint32_t)(cx && cy) << w;
     }
     mask[i] = (uint8_t)m;
 }
@@ -185,14 +206,14 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
                                          const GRec *__restrict__ rec,
                                          const uint32_t *__restrict__ ids,
                                          const uint8_t *__restrict__ submask, int sub,
-                                         uint32_t lo, uint32_t hi, uint32_t begin,
-                                         const float dh[3], const float dl[3],
-                                         const float dd[3], float rx, float ry,
-                                         float4 (*s_e)[32], uint32_t *s_pos, CamAcc &a,
+                                         int sbx, int sby, uint32_t lo, uint32_t hi,
+                                         uint32_t begin, const float dh[3], const float dl[3],
+                                         const float dd[3], float4 (*s_e)[32],
+                                         uint32_t *s_pos, uint32_t *s_lanes, CamAcc &a,
                                          bool done)
 {
     const int lane = threadIdx.x & 31;
-    bool stopped = false;
+    const bool done0 = done;
     for (uint32_t base = lo; base < hi; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t idx = base + lane;
@@ -205,21 +226,21 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
             float4 ent[9];
             cam_entry(rec[ids[idx]], pose.t, dh, dl, ent);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) s_e[k][pos] = ent[k];
+            for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
+            s_lanes[pos] = subblock_lanes(ent[8], sbx, sby);
             s_pos[pos] = idx + 1 - begin;
         }
         __syncwarp();
         const int n = __popc(bal);
         for (int j = 0; j < n; ++j) {
             PairEval pe;
-            bool ok = cam_pair(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
-                               s_e[5][j], s_e[6][j], s_e[8][j], dd, rx, ry, P.alpha_min,
-                               P.alpha_max, pe);
+            bool ok = cam_pair_in(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
+                                  s_e[5][j], s_e[6][j], (s_lanes[j] >> lane) & 1u, dd,
+                                  P.alpha_min, P.alpha_max, pe);
             ok = ok && !done;
             const float Tn = a.T * (1.f - pe.alpha);
             const bool stop = ok && Tn < P.t_min;
             done = done || stop;
-            stopped = stopped || stop;
             ok = ok && !stop;
             const float wgt = ok ? pe.alpha * a.T : 0.f;
             const float4 col = s_e[7][j];
@@ -232,9 +253,10 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
             a.last = ok ? s_pos[j] : a.last;
         }
     }
-    return stopped;
+    return done && !done0;   // the ray stopped at T_min in this walk
 }
 
+template <uint32_t kSeg>
 __global__ void __launch_bounds__(32 * kCamWarps, 6)
 k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
                 const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
@@ -245,8 +267,9 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
                 const RenderDesc *__restrict__ D, float4 *__restrict__ ray_state,
                 uint32_t *__restrict__ n_contrib)
 {
-    __shared__ float4 s_all[kCamWarps][9][32];
+    __shared__ float4 s_all[kCamWarps][8][32];
     __shared__ uint32_t s_pos[kCamWarps][32];
+    __shared__ uint32_t s_lanes[kCamWarps][32];
     __shared__ float s_refs[kCamWarps][6];
     __shared__ CamPose s_pose;
     load_cam_pose(D, s_pose);
@@ -276,13 +299,12 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
         const bool no_ray = !(inside && e.w > 0.f);
         float dd[3];
         cam_ray_offset(s_pose, e, dd);
-        const float rx = (float)px + 0.5f, ry = (float)py + 0.5f;
         const uint2 rg = ranges[tile];
-        const uint32_t lo = rg.x + (uint32_t)seg * kSegLen;
-        const uint32_t hi = min(rg.y, lo + kSegLen);
+        const uint32_t lo = rg.x + (uint32_t)seg * kSeg;
+        const uint32_t hi = min(rg.y, lo + kSeg);
         CamAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
-        const bool stopped = cam_walk(P, s_pose, rec, ids, submask, sub, lo, hi, rg.x, dh, dl, dd, rx,
-                                      ry, s_e, s_pos[wib], a, no_ray);
+        const bool stopped = cam_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, lo, hi, rg.x,
+                                      dh, dl, dd, s_e, s_pos[wib], s_lanes[wib], a, no_ray);
         if (ti.x > 1) {
             // long tile: publish this run, and combine if it is the last one
             float4 *pp = partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2;
@@ -320,9 +342,10 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
                     a.last = l ? l : a.last;
                 }
                 if (__any_sync(0xffffffffu, redo)) {
-                    const uint32_t l0 = rg.x + sgi * kSegLen;
-                    cam_walk(P, s_pose, rec, ids, submask, sub, l0, min(rg.y, l0 + kSegLen), rg.x, dh,
-                             dl, dd, rx, ry, s_e, s_pos[wib], a, !redo);
+                    const uint32_t l0 = rg.x + sgi * kSeg;
+                    cam_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, l0,
+                             min(rg.y, l0 + kSeg), rg.x, dh, dl, dd, s_e, s_pos[wib],
+                             s_lanes[wib], a, !redo);
                 }
                 fin = fin || redo;
             }
@@ -344,13 +367,14 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
     }
 }
 
-static int cam_blocks_per_sm()
+template <uint32_t kSeg> static int cam_blocks_per_sm()
 {
     static int cached = 0;
     if (!cached) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_camera, 32 * kCamWarps,
-                                                          0) != cudaSuccess || nb < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_camera<kSeg>,
+                                                          32 * kCamWarps, 0) != cudaSuccess ||
+            nb < 1)
             nb = 4;
         cached = nb;
     }
@@ -359,10 +383,14 @@ static int cam_blocks_per_sm()
 
 sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, cudaStream_t st)
 {
+    if (fr.seg_len != kSegLen && fr.seg_len != kSegLenStatic) {
+        set_error("internal: camera list segment length %u not compiled", fr.seg_len);
+        return SG_ERR_INVALID;
+    }
     const CamRender P = cam_render_params(cam, o);
     const int nt = cam.ntx * cam.nty;
     const int64_t K = fr.n_pairs;
-    const CamWorkSize ws = cam_work_size(nt, K);
+    const CamWorkSize ws = cam_work_size(nt, K, fr.seg_len);
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
@@ -370,13 +398,20 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     if (s != SG_OK) return s;
     unsigned char *cw = (unsigned char *)fr.camwork.p;
     uint2 *tile_info = (uint2 *)cw;
-    uint2 *items = (uint2 *)(cw + ws.info_bytes);
-    uint32_t *arrive = (uint32_t *)(cw + ws.info_bytes + ws.items_bytes);
+    uint32_t *item_off = (uint32_t *)(cw + ws.info_bytes);
+    uint2 *items = (uint2 *)(cw + ws.info_bytes + ws.off_bytes);
+    uint32_t *arrive = (uint32_t *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes);
     uint32_t *counts = (uint32_t *)fr.scalars.p + 4;    // [0] items [1] slots
     uint32_t *counter = (uint32_t *)fr.scalars.p + 2;
-    k_camera_items<<<1, 1024, 0, st>>>((const uint2 *)fr.ranges.p, nt, (uint32_t *)fr.order.p,
-                                       tile_info, items, arrive, counts, counter);
+    k_camera_items<<<1, 1024, 0, st>>>((const uint2 *)fr.ranges.p, nt, fr.seg_len,
+                                       (uint32_t *)fr.order.p, tile_info, item_off, counts,
+                                       counter);
     SG_LAUNCHED();
+    if (nt > 0) {
+        k_emit_items<<<(unsigned)((nt + 7) / 8), 256, 0, st>>>(
+            (const uint32_t *)fr.order.p, tile_info, item_off, nt, items, arrive);
+        SG_LAUNCHED();
+    }
     const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
     if (K > 0) {
         k_submask<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(
@@ -388,10 +423,13 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     SG_CUDA(cudaGetDevice(&dev));
     SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int64_t cap = (ws.max_items + kCamWarps - 1) / kCamWarps;
-    int64_t grid = (int64_t)sms * cam_blocks_per_sm();
+    const bool dflt = fr.seg_len == kSegLen;
+    int64_t grid = (int64_t)sms * (dflt ? cam_blocks_per_sm<kSegLen>()
+                                        : cam_blocks_per_sm<kSegLenStatic>());
     grid = grid < cap ? grid : cap;
     if (grid < 1) grid = 1;
-    k_render_camera<<<(unsigned)grid, 32 * kCamWarps, 0, st>>>(
+    auto kern = dflt ? k_render_camera<kSegLen> : k_render_camera<kSegLenStatic>;
+    kern<<<(unsigned)grid, 32 * kCamWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
         (const uint8_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
         cam.d_tile_dir, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,

@@ -85,7 +85,7 @@ def test_camera_backward_tiny(sg, O64):
 
 
 def test_camera_backward_long_segmented_lists(sg, O64):
-    # lists of several 1024-entry segments, rays stopping in most of them
+    # lists of 14-31 segments of 256 entries, rays stopping in most of them
     sc, cam = syn.layered_scene(), syn.tiny_camera()
     orc = O64.render_camera(sc, cam)
     g = upstream(orc, np.random.default_rng(2))

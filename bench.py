@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the LiDAR sweep and differentiable-step measurements")
     return ap.parse_args()
 
 
@@ -61,6 +63,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(x, world, device):
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_max):
+    """Whole-job throughput (Munits/s): every rank processes units_per_rank
+    in parallel, the job takes as long as the slowest rank."""
+    return world * units_per_rank / (ms_max * 1e-3) / 1e6
 
 
 # ------------------------------------------------------------------ clocks
@@ -204,11 +223,8 @@ def run_ours(args):
     clocks = clk.stop()
     dev_ms = e0.elapsed_time(e1) / args.steps
     wall_ms = (t1 - t0) * 1e3 / args.steps
-    ms = torch.tensor([dev_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms.item())
-    value = world * rays_per_step / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(dev_ms, world, "cuda")
+    value = job_rate(rays_per_step, world, ms)
 
     # per-stage averages over the timed steps (ms per render)
     st = np.array(stage_ms)            # [2*steps, 4]: project, depth sort, bin+sort, render
@@ -239,13 +255,9 @@ def run_ours(args):
             sg.sg_render_camera_host(S.handle, ch.handle, c.c2w, opts, f.handle,
                                      h[0].data_ptr(), h[1].data_ptr(), h[2].data_ptr(), sp)
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    e = torch.tensor([e2e_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(e, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms = float(e.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, world, "cuda")
     d2h = sum(4 * 5 * c.width * c.height for _, c in cams)
-    e2e = {"value": world * rays_per_step / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+    e2e = {"value": job_rate(rays_per_step, world, e2e_ms), "unit": "Mrays/s",
            "h2d_bytes_per_step": 2 * 12 * 4, "d2h_bytes_per_step": d2h,
            "ms_per_step": e2e_ms,
            "path": "sg_render_camera_host (pinned host outputs, copies and sync in the timed region)"}
@@ -268,6 +280,10 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(sc, [c for _, c in cams], budget_s=20.0)
+    if rank == 0 and not args.no_extra:
+        del S, frames, ef
+        result["lidar"] = lidar_workload(torch, sg, syn, min(args.steps, 100), 5)
+        result["train_step"] = train_step_workload(torch, sg, syn, min(args.steps, 30), 3)
     if not args.no_serving:
         from paper_2510_12901_gb300 import serve
         srv = serve.measure_serving(n_requests=args.serving_requests)
@@ -277,6 +293,123 @@ def run_ours(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return result
+
+
+def _work(view):
+    try:
+        work = json.load(open(os.path.join(ROOT, "tests", "golden", "bench_work.json")))
+        return work["views"][view]["evaluated_pairs"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def lidar_workload(torch, sg, syn, steps, warmup):
+    """The LiDAR sweep configuration: 2M LiDAR Gaussians, 128 beams x 2048
+    columns, per-column poses over a 0.1 s sweep; range, intensity, drop and
+    alpha per ray.  CUDA events over `steps` sweeps, inputs resident."""
+    sc = syn.street_scene(2_000_000, seed=0, kind="lidar")
+    L = syn.street_lidar()
+    S, Ld = sg.Scene(sc), sg.Lidar(L)
+    poses = torch.from_numpy(np.ascontiguousarray(L.col_c2w, np.float32)).cuda()
+    outs = [torch.empty((L.n_beams, L.n_cols), device="cuda") for _ in range(4)]
+    frames = [sg.Frame(), sg.Frame()]
+    for f in frames:
+        sg.sg_frame_set_timing(f.handle, 1)
+    opts = sg.sg_default_opts()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def sweep(i):
+        sg.sg_render_lidar(S.handle, Ld.handle, poses.data_ptr(), opts, frames[i % 2].handle,
+                           *[o.data_ptr() for o in outs], sp)
+
+    for i in range(warmup):
+        sweep(i)
+    torch.cuda.synchronize()
+    stage = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        sweep(i)
+        if i > 0:
+            stage.append(sg.sg_frame_timing(frames[(i - 1) % 2].handle))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stage.append(sg.sg_frame_timing(frames[(steps - 1) % 2].handle))
+    ms = e0.elapsed_time(e1) / steps
+    st = np.array(stage).mean(axis=0)
+    rays = L.n_beams * L.n_cols
+    out = {"workload": "street LiDAR scene: 2M Gaussians (intensity, ray-drop logits), 128-beam "
+                       "x 2048-column sweep, per-column poses over 0.1 s; range + intensity + drop",
+           "value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_sweep": ms,
+           "steps": steps, "stages_ms": {"project": st[0], "depth_sort_offsets": st[1],
+                                         "bin_tile_sort_ranges": st[2], "render": st[3]}}
+    pairs = _work("lidar")
+    if pairs:
+        pk = peaks()
+        peak = SM_COUNT * FP32_LANES * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        ach = pairs * FLOP_PER_PAIR / (st[3] * 1e-3) / 1e12
+        out["roofline"] = {"kernel": "k_render_lidar", "bound": "alu", "achieved": ach,
+                           "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                           "evaluated_pairs": pairs}
+    return out
+
+
+def train_step_workload(torch, sg, syn, steps, warmup):
+    """The differentiable step: the 1M-Gaussian camera scene into the
+    1920x1280 fisheye view and the 2M-Gaussian LiDAR scene into the 128x2048
+    sweep, L1 RGB + L1 range loss against seeded noisy targets, then the
+    hand-written backward to every Gaussian parameter, through the
+    torch.autograd.Function wrappers (parameters copied into the resident
+    scenes each step, as a training loop does)."""
+    from paper_2510_12901_gb300 import autograd as ag
+    csc = syn.street_scene(1_000_000, seed=0, kind="camera")
+    lsc = syn.street_scene(2_000_000, seed=0, kind="lidar")
+    fish, _ = syn.street_cameras()
+    L = syn.street_lidar()
+    cS, lS, C, Ld = sg.Scene(csc), sg.Scene(lsc), sg.Camera(fish), sg.Lidar(L)
+    poses = torch.from_numpy(np.ascontiguousarray(L.col_c2w, np.float32)).cuda()
+
+    def params(sc):
+        return {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, a), np.float32)).cuda()
+                .requires_grad_(True)
+                for k, a in (("means", "means"), ("log_scales", "log_scales"),
+                             ("quats", "quats"), ("opacity", "opacity"),
+                             ("features", "features"))}
+
+    cp, lp = params(csc), params(lsc)
+    t_rgb = torch.from_numpy(syn.noisy_targets((fish.height, fish.width, 3), seed=4)).cuda()
+    t_rng = torch.from_numpy(syn.noisy_targets((L.n_beams, L.n_cols), seed=5, lo=0.0,
+                                               hi=80.0)).cuda()
+    cf, lf = sg.Frame(), sg.Frame()
+
+    def step():
+        rgb, _, _ = ag.render_camera(cp, cS, C, fish.c2w, frame=cf)
+        rng, _, _, _ = ag.render_lidar(lp, lS, Ld, poses, frame=lf)
+        loss = (rgb - t_rgb).abs().mean() + (rng - t_rng).abs().mean()
+        for d in (cp, lp):
+            for t in d.values():
+                t.grad = None
+        loss.backward()
+        return loss
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rays = fish.width * fish.height + L.n_beams * L.n_cols
+    return {"workload": "differentiable step: 1M-Gaussian camera scene into the 1920x1280 "
+                        "fisheye + 2M-Gaussian LiDAR scene into the 128x2048 sweep, L1 RGB + L1 "
+                        "range loss, backward to all Gaussian parameters",
+            "ms_per_step": ms, "steps": steps, "rays_per_step": rays,
+            "value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s (forward + backward)"}
 
 
 def roofline(per_view, cams, clocks):

@@ -233,8 +233,8 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     }
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
-    s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, sc, n, (const int4 *)fr.tiles.p, ntx,
-                  wrap, K, pk[0], pv[0], st);
+    s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, (const uint32_t *)fr.cnt_sorted.p, sc,
+                  n, (const int4 *)fr.tiles.p, ntx, wrap, K, pk[0], pv[0], st);
     if (s != SG_OK) return s;
     int bits = 1;
     while (((int64_t)1 << bits) < ntiles) ++bits;

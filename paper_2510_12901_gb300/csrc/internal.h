@@ -209,10 +209,9 @@ sg_status compact_valid(const uint32_t *d_count, const float *d_depth, int64_t n
 sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count,
                         const uint32_t *d_nvalid, int64_t n, uint32_t *d_out,
                         cudaStream_t st);
-sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets,
-                    const uint32_t *d_nvalid, int64_t n, const int4 *d_tiles,
-                    int ntx, int wrap_x, int64_t cap, uint32_t *d_keys, uint32_t *d_vals,
-                    cudaStream_t st);
+sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_counts,
+                    const uint32_t *d_nvalid, int64_t n, const int4 *d_tiles, int ntx, int wrap_x,
+                    int64_t cap, uint32_t *d_keys, uint32_t *d_vals, cudaStream_t st);
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
                       int64_t ntiles, cudaStream_t st);
 sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStream_t st);

@@ -195,8 +195,9 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     fr.n_pairs = K;
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
-    if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, scal, n, (const int4 *)fr.tiles.p,
-                       c.ntx, 0, K, pk[0], pv[0], st)) != SG_OK)
+    if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, (const uint32_t *)fr.cnt_sorted.p,
+                       scal, n, (const int4 *)fr.tiles.p, c.ntx, 0, K, pk[0], pv[0], st)) !=
+        SG_OK)
         return s;
     int bits = 1;
     while (((int64_t)1 << bits) < nt) ++bits;

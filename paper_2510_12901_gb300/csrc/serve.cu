@@ -218,13 +218,13 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
         return SG_OK;
     }
     drop_graph(g);
-    int64_t known = 0;
+    int64_t known = -1;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         auto it = S->max_pairs.find(key);
         if (it != S->max_pairs.end()) known = it->second;
     }
-    if (known == 0) {   // first sight of this combination: exact render
+    if (known < 0) {    // first sight of this combination: exact render
         fr.k_cap = 0;
         if ((s = render_plain(r, frame, st)) != SG_OK) return s;
         if ((s = finish(ev, st)) != SG_OK) return s;

@@ -330,37 +330,64 @@ sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count, const ui
 
 // ------------------------------------------------------------------ binning
 
-// Pairs at positions >= cap are not written (capacity mode: the caller
-// learns of them from the dropped-pairs count).
-__global__ void k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
-                      const uint32_t *__restrict__ d_nvalid, const int4 *__restrict__ tiles,
-                      int ntx, int wrap_x, uint32_t cap, uint32_t *__restrict__ keys,
-                      uint32_t *__restrict__ vals)
+// Expand each valid Gaussian (depth order) into its (tile, Gaussian) pairs:
+// pair o of Gaussian g goes to position offsets[g] + o, tile rows outer and
+// columns inner.  A block takes 256 consecutive Gaussians and writes all of
+// their pairs with its threads striding over the output positions (the
+// owner of a position is found by binary search over the block's offsets),
+// so a Gaussian that covers many tiles does not serialise one thread and
+// the writes are coalesced.  Pairs at positions >= cap are not written
+// (capacity mode: the caller learns of them from the dropped-pairs count).
+constexpr int kBinThreads = 256;
+
+__global__ void __launch_bounds__(kBinThreads)
+k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
+      const uint32_t *__restrict__ counts, const uint32_t *__restrict__ d_nvalid,
+      const int4 *__restrict__ tiles, int ntx, int wrap_x, uint32_t cap,
+      uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)*d_nvalid) return;
-    uint32_t g = ids[i];
-    uint32_t o = offsets[i];
-    int4 t = tiles[g];
-    for (int ty = t.z; ty <= t.w; ++ty)
-        for (int tx = t.x; tx <= t.y; ++tx) {
-            int x = tx;
-            if (wrap_x) { x %= ntx; if (x < 0) x += ntx; }
-            if (o < cap) {
-                keys[o] = (uint32_t)(ty * ntx + x);
-                vals[o] = g;
-            }
-            ++o;
+    __shared__ uint32_t s_off[kBinThreads], s_id[kBinThreads];
+    __shared__ int4 s_rect[kBinThreads];
+    __shared__ uint32_t s_end;
+    const int64_t g0 = (int64_t)blockIdx.x * kBinThreads;
+    const int64_t nvalid = *d_nvalid;
+    if (g0 >= nvalid) return;
+    const int nb = (int)min((int64_t)kBinThreads, nvalid - g0);
+    const int t = threadIdx.x;
+    if (t < nb) {
+        const uint32_t g = ids[g0 + t];
+        s_id[t] = g;
+        s_off[t] = offsets[g0 + t];
+        s_rect[t] = tiles[g];
+        if (t == nb - 1) s_end = offsets[g0 + t] + counts[g0 + t];
+    }
+    __syncthreads();
+    const uint32_t first = s_off[0], total = s_end - first;
+    for (uint32_t o = t; o < total; o += kBinThreads) {
+        const uint32_t pos = first + o;
+        int lo = 0, hi = nb;      // owner: the last k with s_off[k] <= pos
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= pos) lo = mid; else hi = mid;
         }
+        if (pos >= cap) continue;
+        const int4 r = s_rect[lo];
+        const uint32_t local = pos - s_off[lo], w = (uint32_t)(r.y - r.x + 1);
+        const int ty = r.z + (int)(local / w);
+        int x = r.x + (int)(local % w);
+        if (wrap_x) { x %= ntx; if (x < 0) x += ntx; }
+        keys[pos] = (uint32_t)(ty * ntx + x);
+        vals[pos] = s_id[lo];
+    }
 }
 
-sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_nvalid,
-                    int64_t n, const int4 *d_tiles, int ntx, int wrap_x, int64_t cap,
-                    uint32_t *d_keys, uint32_t *d_vals, cudaStream_t st)
+sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_counts,
+                    const uint32_t *d_nvalid, int64_t n, const int4 *d_tiles, int ntx, int wrap_x,
+                    int64_t cap, uint32_t *d_keys, uint32_t *d_vals, cudaStream_t st)
 {
     if (n == 0) return SG_OK;
-    k_bin<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d_ids, d_offsets, d_nvalid, d_tiles, ntx,
-                                                       wrap_x, (uint32_t)cap, d_keys, d_vals);
+    k_bin<<<(unsigned)((n + kBinThreads - 1) / kBinThreads), kBinThreads, 0, st>>>(
+        d_ids, d_offsets, d_counts, d_nvalid, d_tiles, ntx, wrap_x, (uint32_t)cap, d_keys, d_vals);
     SG_LAUNCHED();
     return SG_OK;
 }

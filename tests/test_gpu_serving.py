@@ -111,6 +111,51 @@ def test_capacity_mode_matches_exact_and_reports_overflow(W):
         assert torch.equal(a, b)
 
 
+def test_graph_replay_that_outgrows_its_capacity_is_rendered_exactly():
+    """One slot, one (scene, camera) combination.  Two requests see nothing
+    (the camera looks away), so the graph is captured with the minimum pair
+    capacity; the next request looks at the scene, overflows that capacity
+    on replay and must be rendered again exactly; the graph is then
+    recaptured larger and replayed.  Every result equals the alone render."""
+    import torch
+    from paper_2510_12901_gb300 import serve
+    from paper_2510_12901_gb300 import simgut as sg
+    from paper_2510_12901_gb300 import synthetic as syn
+    sc = syn.layered_scene()
+    cam = syn.Camera(syn.CAMERA_PINHOLE, 320, 240, 300.0, 300.0, 160.0, 120.0,
+                     np.zeros(4, np.float32), syn.tiny_camera().c2w)
+    away = syn._look_c2w([0.0, -10.0, 0.0], [0.0, -1.0, 0.0], [0.0, 0.0, -1.0])
+    S, C = sg.Scene(sc), sg.Camera(cam)
+    poses = [away, away, cam.c2w, cam.c2w, cam.c2w]
+
+    def outs():
+        return [torch.full((240, 320, 3), -7.0, device="cuda"),
+                torch.full((240, 320), -7.0, device="cuda"),
+                torch.full((240, 320), -7.0, device="cuda")]
+
+    alone = []
+    fr = sg.Frame()
+    st = torch.cuda.current_stream().cuda_stream
+    for p in poses:
+        o = outs()
+        sg.sg_render_camera(S.handle, C.handle, p, sg.sg_default_opts(), fr.handle,
+                            *[t.data_ptr() for t in o], st)
+        alone.append(o)
+    torch.cuda.synchronize()
+    assert sg.sg_frame_stats(fr.handle)[0] > 200_000      # far above the minimum capacity
+    srv = serve.Server(n_slots=1)
+    for p, ref in zip(poses, alone):
+        o = outs()
+        srv.wait(srv.submit(serve.Server.camera_request(S, C, p, o)), 60.0)
+        for a, b in zip(ref, o):
+            assert torch.equal(a, b)
+    stt = srv.stats()
+    srv.close()
+    assert stt["completed"] == 5 and stt["failed"] == 0
+    assert stt["overflow_rerenders"] == 1
+    assert stt["graph_captures"] == 2 and stt["graph_replays"] == 1
+
+
 def test_memory_admission_serialises_and_completes(W):
     from paper_2510_12901_gb300 import serve
     # pinhole requests on the larger scene: each needs ~15 MB of workspace,

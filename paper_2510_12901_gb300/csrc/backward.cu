@@ -3,22 +3,29 @@
 // features.  The unscented transform only selects tiles (a piecewise-constant
 // choice) and is not differentiated.
 //
-// Per ray, the list is walked back to front from the last composited entry,
-// recomputing every pair with the forward's own arithmetic (pairs.cuh) so
-// that the same entries contribute; transmittance is recovered as
-// T_i = T_{i+1} / (1 - alpha_i) from the saved final value.  With
-// Q = (F0, F1, F2, Z, W) = sum_i (c_i, tau_i, 1) alpha_i T_i,
-//   dQ/dalpha_i = q_i T_i - (sum_{j>i} q_j alpha_j T_j) / (1 - alpha_i).
-// The closest approach gives the geometric gradients in a stable form: with
-// q* = M (o + tau d - mu) = (num x den) / |den|^2 (the closest point in the
-// Gaussian's frame, no cancellation) and p = M^-1 q* = M^T diag(s^2) q*,
+// The backward runs over the forward's own work items (segments of a tile
+// list x sub-blocks for the camera, segments x LiDAR work items), with the
+// forward's staging and pair arithmetic (pairs.cuh), so that the same
+// entries contribute.  Each segment is walked front to back from the state
+// the forward's merge left for it (transmittance T and the sums (F, Z, W)
+// before the segment).  With Q = (F0, F1, F2, Z, W) = sum_i (c_i, tau_i, 1)
+// alpha_i T_i and U = gQ . Q (gQ = dL/dQ), the gradient of a composited
+// entry's alpha is
+//   dL/dalpha_i = (gQ . q_i) T_i - (U - U_{<=i}) / (1 - alpha_i),
+// where U comes from the ray's saved final (F, Z, W) and U_{<=i} is the
+// prefix sum up to and including entry i; T_{i+1} = T_i (1 - alpha_i) is
+// the forward's own product.  The closest approach gives the geometric
+// gradients in a stable form: with q* = M (o + tau d - mu) = (num x den) /
+// |den|^2 (the closest point in the Gaussian's frame, no cancellation) and
+// p = M^-1 q* = M^T diag(s^2) q*,
 //   dD^2/dM = 2 q* p^T,          dD^2/dmu = -2 M^T q*,
 //   dtau/dM = -(den p^T + q* d^T) / |den|^2,   dtau/dmu = M^T den / |den|^2
-// (envelope theorem at tau_max).  Per (tile, Gaussian) the 16 partial sums
-// dL/dM (9), dL/dmu (3), dL/dsigma, dL/dfeature (3) are reduced over the
-// warp, then the block, before one float atomic each.  A last per-Gaussian
-// kernel maps them to the raw parameters (M = S^-1 R^T, R of the normalised
-// quaternion, SH colour at the direction from the camera to the mean).
+// (envelope theorem at tau_max).  Per staged entry the 16 partials dL/dM
+// (9), dL/dmu (3), dL/dsigma, dL/dfeature (3) are summed over the warp by a
+// transposing butterfly (16 shuffles) and added with 16 float atomics.  A
+// last per-Gaussian kernel maps them to the raw parameters (M = S^-1 R^T, R
+// of the normalised quaternion, SH colour at the direction from the camera
+// to the mean).
 #include <math.h>
 
 #include "pairs.cuh"
@@ -27,7 +34,7 @@
 namespace sg {
 
 constexpr int kG = 16;          // accumulated partials per Gaussian
-constexpr int kBwBatch = 64;    // camera list entries per shared-memory batch
+constexpr int kBwWarps = 4;     // warps per block of the persistent backward grids
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -69,23 +76,20 @@ __device__ __forceinline__ void pair_geometry_grads(const float Mr[9], const Pai
                    ti * (Mr[j] * e[0] + Mr[3 + j] * e[1] + Mr[6 + j] * e[2]);
 }
 
-// Back-to-front step for one composited entry: returns the partials.
-//   q = (f0, f1, f2): features; gQ upstream of (F0, F1, F2, Z, W);
-//   T: transmittance after this entry (updated to before it); S: suffix sums.
+// Front-to-back step for one composited entry: returns the partials.
+//   q = (f0, f1, f2): features; gQ: upstream of (F0, F1, F2, Z, W);
+//   T: transmittance before the entry (updated to after it); U: gQ . Q
+//   before the entry (updated); Ut: gQ . Q of the whole ray.
 __device__ __forceinline__ void composite_grads(const PairEval &pe, float sigma, const float q[3],
-                                                const float gQ[5], float &T, float S[5],
+                                                const float gQ[5], float &T, float &U, float Ut,
                                                 const float Mr[9], const float d[3], float g[kG])
 {
-    const float one_m = 1.f - pe.alpha;
-    const float Tb = T / one_m;
-    const float w = pe.alpha * Tb;
-    const float qq[5] = {q[0], q[1], q[2], pe.tau, 1.f};
-    float dLda = 0.f;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) dLda += gQ[k] * (qq[k] * Tb - S[k] / one_m);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) S[k] += qq[k] * w;
-    T = Tb;
+    const float w = pe.alpha * T;
+    const float gq = gQ[0] * q[0] + gQ[1] * q[1] + gQ[2] * q[2] + gQ[3] * pe.tau + gQ[4];
+    const float Ua = U + gq * w;
+    const float dLda = gq * T - (Ut - Ua) / (1.f - pe.alpha);
+    U = Ua;
+    T = T * (1.f - pe.alpha);
     const float dLdtau = gQ[3] * w;
     float dLdD2 = 0.f;
     g[12] = 0.f;
@@ -99,187 +103,275 @@ __device__ __forceinline__ void composite_grads(const PairEval &pe, float sigma,
     pair_geometry_grads(Mr, pe, d, dLdD2, dLdtau, g);
 }
 
+// Sum g[16] over the warp and add it to acc[0..15]: a butterfly that halves
+// the vector at each of the first four levels (8 + 4 + 2 + 1 shuffles) and
+// leaves lane L with component 8 b4 + 4 b3 + 2 b2 + b1 (b = bits of L)
+// summed over 16 lanes; the last shuffle adds the other half.
+__device__ __forceinline__ void warp_reduce_add16(const float g[kG], float *acc)
+{
+    const int lane = threadIdx.x & 31;
+    const bool h1 = lane & 16, h2 = lane & 8, h3 = lane & 4, h4 = lane & 2;
+    float a8[8], a4[4], a2[2];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float mine = h1 ? g[8 + k] : g[k], other = h1 ? g[k] : g[8 + k];
+        a8[k] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float mine = h2 ? a8[4 + k] : a8[k], other = h2 ? a8[k] : a8[4 + k];
+        a4[k] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float mine = h3 ? a4[2 + k] : a4[k], other = h3 ? a4[k] : a4[2 + k];
+        a2[k] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
+    }
+    float a1 = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a2[0] : a2[1], 2);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+    const int comp = (h1 ? 8 : 0) + (h2 ? 4 : 0) + (h3 ? 2 : 0) + (h4 ? 1 : 0);
+    if (!(lane & 1) && a1 != 0.f) atomicAdd(acc + comp, a1);
+}
+
+// Upstream of (F0, F1, F2, Z, W) for a camera ray from dL/d(rgb, alpha,
+// depth), depth = Z / W.
+__device__ __forceinline__ void camera_gQ(const float *g_rgb, const float *g_alpha,
+                                          const float *g_depth, int64_t r, float W, float Z,
+                                          float gQ[5])
+{
+    gQ[0] = g_rgb ? g_rgb[3 * r] : 0.f;
+    gQ[1] = g_rgb ? g_rgb[3 * r + 1] : 0.f;
+    gQ[2] = g_rgb ? g_rgb[3 * r + 2] : 0.f;
+    const float gd = g_depth ? g_depth[r] : 0.f, ga = g_alpha ? g_alpha[r] : 0.f;
+    gQ[3] = W > 0.f ? gd / W : 0.f;
+    gQ[4] = ga - (W > 0.f ? gd * Z / (W * W) : 0.f);
+}
+
 // ------------------------------------------------------------------ camera
-__global__ void __launch_bounds__(kCamThreads)
+__global__ void __launch_bounds__(32 * kBwWarps, 4)
 k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
-                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order,
-                  const float4 *__restrict__ pix,
+                  const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
+                  const uint2 *__restrict__ tile_info, const uint32_t *__restrict__ counts,
+                  const uint8_t *__restrict__ submask, uint32_t *__restrict__ counter,
+                  const float4 *__restrict__ partials, const float4 *__restrict__ pix,
                   const double *__restrict__ tile_dir, const RenderDesc *__restrict__ D,
-                  const float4 *__restrict__ ray_state,
+                  const float4 *__restrict__ ray_state, const float4 *__restrict__ ray_feat,
                   const uint32_t *__restrict__ n_contrib, const float *__restrict__ g_rgb,
                   const float *__restrict__ g_alpha, const float *__restrict__ g_depth,
                   float *__restrict__ gacc)
 {
-    __shared__ float4 s_e[9][kBwBatch];
-    __shared__ uint32_t s_id[kBwBatch];
-    __shared__ float s_red[kBwBatch][kCamThreads / 32][kG];
-    __shared__ float s_ref[6];
-    __shared__ uint32_t s_max;
+    __shared__ float4 s_all[kBwWarps][8][32];
+    __shared__ uint32_t s_pos[kBwWarps][32], s_lanes[kBwWarps][32], s_gid[kBwWarps][32];
+    __shared__ float s_refs[kBwWarps][6];
     __shared__ CamPose s_pose;
     load_cam_pose(D, s_pose);
     __syncthreads();
-    const int tile = (int)order[blockIdx.x], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = tile % P.ntx, ty = tile / P.ntx;
-    const int px = tx * kTile + (tid % kTile), py = ty * kTile + (tid / kTile);
-    if (tid == 0) {
-        cam_tile_ref(s_pose, tile_dir, tile, s_ref);
-        s_max = 0;
-    }
-    __syncthreads();
-    const float dh[3] = {s_ref[0], s_ref[1], s_ref[2]};
-    const float dl[3] = {s_ref[3], s_ref[4], s_ref[5]};
-    const bool inside = px < P.W && py < P.H;
-    const int64_t pidx = (int64_t)py * P.W + px;
-    const float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool ray_ok = inside && e.w > 0.f;
-    float dd[3], d[3];
-    cam_ray_offset(s_pose, e, dd);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float4(*s_e)[32] = s_all[wib];
+    float *s_ref = s_refs[wib];
+    const uint32_t n_items = counts[0];
+    while (true) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const uint2 it = items[item];
+        const int tile = (int)it.x, seg = (int)(it.y >> 3), sub = (int)(it.y & 7);
+        const uint2 ti = tile_info[tile];
+        const int tx = tile % P.ntx, ty = tile / P.ntx;
+        const int sbx = tx * kTile + 8 * (sub & 1), sby = ty * kTile + 4 * (sub >> 1);
+        const int px = sbx + (lane & 7), py = sby + (lane >> 3);
+        const bool inside = px < P.W && py < P.H;
+        const int64_t pidx = (int64_t)py * P.W + px;
+        const float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ray_ok = inside && e.w > 0.f;
+        const uint32_t last = ray_ok ? n_contrib[pidx] : 0u;
+        const uint2 rg = ranges[tile];
+        const uint32_t lo = rg.x + (uint32_t)seg * kSegLen;
+        uint32_t hi = min(rg.y, lo + kSegLen);
+        uint32_t lim = rg.x + last;                    // entries idx < lim may contribute
 #pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = dh[i] + dd[i];
-    const float rx = (float)px + 0.5f, ry = (float)py + 0.5f;
-    uint32_t last = 0;
-    float T = 1.f, gQ[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (ray_ok) {
-        const float4 st = ray_state[pidx];
-        last = n_contrib[pidx];
-        T = st.x;
-        const float W = st.y, Z = st.z;
-        if (g_rgb) {
-            gQ[0] = g_rgb[3 * pidx];
-            gQ[1] = g_rgb[3 * pidx + 1];
-            gQ[2] = g_rgb[3 * pidx + 2];
+        for (int o = 16; o > 0; o >>= 1) lim = max(lim, __shfl_xor_sync(0xffffffffu, lim, o));
+        hi = min(hi, lim);
+        if (hi <= lo) continue;                        // nothing of this segment composited
+        if (lane == 0) cam_tile_ref(s_pose, tile_dir, tile, s_ref);
+        __syncwarp();
+        const float dh[3] = {s_ref[0], s_ref[1], s_ref[2]};
+        const float dl[3] = {s_ref[3], s_ref[4], s_ref[5]};
+        float dd[3], d[3];
+        cam_ray_offset(s_pose, e, dd);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d[i] = dh[i] + dd[i];
+        // state before the segment, upstream, totals
+        float T = 1.f, Qp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (seg > 0) {
+            const float4 *pq = partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2;
+            const float4 u = pq[0], v = pq[1];
+            Qp[0] = u.x; Qp[1] = u.y; Qp[2] = u.z; Qp[3] = v.x; Qp[4] = u.w;
+            T = v.y;
         }
-        const float gd = g_depth ? g_depth[pidx] : 0.f;
-        const float ga = g_alpha ? g_alpha[pidx] : 0.f;
-        gQ[3] = W > 0.f ? gd / W : 0.f;
-        gQ[4] = ga - (W > 0.f ? gd * Z / (W * W) : 0.f);
-        if (last) atomicMax(&s_max, last);
-    }
-    __syncthreads();
-    const uint2 rg = ranges[tile];
-    const uint32_t nmax = s_max;
-    for (int32_t bend = (int32_t)nmax; bend > 0; bend -= kBwBatch) {
-        const int32_t bstart = max(0, bend - kBwBatch);
-        const int cnt = bend - bstart;
-        if (tid < cnt) {
-            const uint32_t g = ids[rg.x + bstart + tid];
-            float4 ent[9];
-            cam_entry(rec[g], s_pose.t, dh, dl, ent);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) s_e[k][tid] = ent[k];
-            s_id[tid] = g;
+        float gQ[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Ut = 0.f, U = 0.f;
+        if (ray_ok) {
+            const float4 st = ray_state[pidx], F = ray_feat[pidx];
+            camera_gQ(g_rgb, g_alpha, g_depth, pidx, st.y, st.z, gQ);
+            Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * st.z + gQ[4] * st.y;
+            U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
-        __syncthreads();
-        for (int j = cnt - 1; j >= 0; --j) {
-            float gl[kG];
+        for (uint32_t base = lo; base < hi; base += 32) {
+            const uint32_t idx = base + lane;
+            const bool ov = idx < hi && ((submask[idx] >> sub) & 1u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, ov);
+            if (bal == 0u) continue;
+            __syncwarp();
+            if (ov) {
+                const int pos = __popc(bal & ((1u << lane) - 1u));
+                const uint32_t g = ids[idx];
+                float4 ent[9];
+                cam_entry(rec[g], s_pose.t, dh, dl, ent);
 #pragma unroll
-            for (int k = 0; k < kG; ++k) gl[k] = 0.f;
-            PairEval pe;
-            if ((uint32_t)(bstart + j) < last &&
-                cam_pair(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j], s_e[5][j],
-                         s_e[6][j], s_e[8][j], dd, rx, ry, P.alpha_min, P.alpha_max, pe)) {
-                const float4 m0 = s_e[3][j], m1 = s_e[4][j], m2 = s_e[5][j];
-                const float Mr[9] = {m0.x, m0.y, m0.z, m1.x, m1.y, m1.z, m2.x, m2.y, m2.z};
-                const float4 col = s_e[7][j];
-                const float q[3] = {col.x, col.y, col.z};
-                composite_grads(pe, s_e[6][j].w, q, gQ, T, S, Mr, d, gl);
+                for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
+                s_lanes[wib][pos] = subblock_lanes(ent[8], sbx, sby);
+                s_pos[wib][pos] = idx + 1 - rg.x;
+                s_gid[wib][pos] = g;
             }
+            __syncwarp();
+            const int n = __popc(bal);
+            for (int j = 0; j < n; ++j) {
+                PairEval pe;
+                bool ok = cam_pair_in(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
+                                      s_e[5][j], s_e[6][j], (s_lanes[wib][j] >> lane) & 1u, dd,
+                                      P.alpha_min, P.alpha_max, pe);
+                ok = ok && s_pos[wib][j] <= last;
+                if (!__any_sync(0xffffffffu, ok)) continue;
+                float g[kG];
 #pragma unroll
-            for (int k = 0; k < kG; ++k) {
-                const float v = warp_sum(gl[k]);
-                if (lane == 0) s_red[j][warp][k] = v;
+                for (int k = 0; k < kG; ++k) g[k] = 0.f;
+                if (ok) {
+                    const float4 m0 = s_e[3][j], m1 = s_e[4][j], m2 = s_e[5][j];
+                    const float Mr[9] = {m0.x, m0.y, m0.z, m1.x, m1.y, m1.z, m2.x, m2.y, m2.z};
+                    const float4 col = s_e[7][j];
+                    const float q[3] = {col.x, col.y, col.z};
+                    composite_grads(pe, s_e[6][j].w, q, gQ, T, U, Ut, Mr, d, g);
+                }
+                warp_reduce_add16(g, gacc + (int64_t)s_gid[wib][j] * kG);
             }
         }
-        __syncthreads();
-        for (int i = tid; i < cnt * kG; i += kCamThreads) {
-            const int j = i / kG, k = i % kG;
-            float v = 0.f;
-#pragma unroll
-            for (int w = 0; w < kCamThreads / 32; ++w) v += s_red[j][w][k];
-            if (v != 0.f) atomicAdd(&gacc[(int64_t)s_id[j] * kG + k], v);
-        }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
 // ------------------------------------------------------------------ LiDAR
-__global__ void __launch_bounds__(32 * kLidarWarps)
+__global__ void __launch_bounds__(32 * kBwWarps)
 k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
                  const uint32_t *__restrict__ item_rays, const float4 *__restrict__ ray_e,
                  const double *__restrict__ item_u, const float *__restrict__ poses,
                  const float *__restrict__ az_col, const float *__restrict__ elev,
                  const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
-                 const uint2 *__restrict__ ranges, const float4 *__restrict__ ray_state,
+                 const uint2 *__restrict__ ranges, const uint2 *__restrict__ work,
+                 const uint2 *__restrict__ unit_info, const uint32_t *__restrict__ counts,
+                 uint32_t *__restrict__ counter, const float4 *__restrict__ partials,
+                 const float4 *__restrict__ ray_state, const float4 *__restrict__ ray_feat,
                  const uint32_t *__restrict__ n_contrib, const float *__restrict__ g_range,
                  const float *__restrict__ g_int, const float *__restrict__ g_drop,
                  const float *__restrict__ g_alpha, float *__restrict__ gacc)
 {
-    __shared__ float s_all[kLidarWarps][kLidEntry][32];
-    __shared__ uint32_t s_ids[kLidarWarps][32];
+    __shared__ float s_all[kBwWarps][kLidEntry][32];
+    __shared__ uint32_t s_gid[kBwWarps][32], s_lanes[kBwWarps][32], s_pos[kBwWarps][32];
+    __shared__ float s_raz[kBwWarps][32], s_rel[kBwWarps][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int item_id = blockIdx.x * kLidarWarps + wib;
-    if (item_id >= P.n_items) return;
     float(*s)[32] = s_all[wib];
-    const LidarItem it = items[item_id];
-    const uint32_t ray = item_rays[it.ray_off + lane];
-    const bool valid = ray != 0xffffffffu;
-    const int c = valid ? (int)(ray % (uint32_t)P.n_cols) : it.col0;
-    const int b = valid ? (int)(ray / (uint32_t)P.n_cols) : 0;
-    const int sb = kLidCommon + kLidPerCol * (c - it.col0);
-    float dh[3], dl[3], dd[3], d[3];
-    lidar_ray(it, item_u, item_id, poses, ray_e[it.ray_off + lane], c, dh, dl, dd, d);
-    const float raz = az_col[c], rel = elev[b];
-    uint32_t last = 0;
-    float T = 1.f, gQ[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (valid) {
-        const float4 st = ray_state[ray];
-        last = n_contrib[ray];
-        T = st.x;
-        const float W = st.y, Z = st.z, drop = st.w;
-        const float gr = g_range ? g_range[ray] : 0.f;
-        const float gi = g_int ? g_int[ray] : 0.f;
-        const float gp = g_drop ? g_drop[ray] : 0.f;
-        const float ga = g_alpha ? g_alpha[ray] : 0.f;
-        // drop = softmax(F1, F2)[drop] = 1 / (1 + exp(F1 - F2))
-        const float dd_ = drop * (1.f - drop);
-        gQ[0] = gi;
-        gQ[1] = -gp * dd_;
-        gQ[2] = gp * dd_;
-        gQ[3] = W > 0.f ? gr / W : 0.f;
-        gQ[4] = ga - (W > 0.f ? gr * Z / (W * W) : 0.f);
-    }
-    uint32_t nmax = last;
+    const uint32_t n_work = counts[0];
+    while (true) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(counter, 1u);
+        wi = __shfl_sync(0xffffffffu, wi, 0);
+        if (wi >= n_work) break;
+        const uint2 w = work[wi];
+        const int item_id = (int)w.x;
+        const uint32_t seg = w.y;
+        const uint2 ui = unit_info[item_id];
+        const LidarItem it = items[item_id];
+        const uint32_t ray = item_rays[it.ray_off + lane];
+        const bool valid = ray != 0xffffffffu;
+        const uint32_t last = valid ? n_contrib[ray] : 0u;
+        const uint2 rg = ranges[it.tile];
+        const uint32_t lo = rg.x + seg * kSegLen;
+        uint32_t hi = min(rg.y, lo + kSegLen);
+        uint32_t lim = rg.x + last;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-    const uint2 rg = ranges[it.tile];
-    for (int32_t bend = (int32_t)nmax; bend > 0; bend -= 32) {
-        const int32_t bstart = max(0, bend - 32);
-        const int cnt = bend - bstart;
+        for (int o = 16; o > 0; o >>= 1) lim = max(lim, __shfl_xor_sync(0xffffffffu, lim, o));
+        hi = min(hi, lim);
+        if (hi <= lo) continue;
+        const int c = valid ? (int)(ray % (uint32_t)P.n_cols) : it.col0;
+        const int b = valid ? (int)(ray / (uint32_t)P.n_cols) : 0;
+        const int sb = kLidCommon + kLidPerCol * (c - it.col0);
+        float dh[3], dl[3], dd[3], d[3];
+        lidar_ray(it, item_u, item_id, poses, ray_e[it.ray_off + lane], c, dh, dl, dd, d);
+        s_raz[wib][lane] = valid ? az_col[c] : __int_as_float(0x7fc00000);
+        s_rel[wib][lane] = valid ? elev[b] : __int_as_float(0x7fc00000);
         __syncwarp();
-        if (lane < cnt) {
-            const uint32_t g = ids[rg.x + bstart + lane];
-            lidar_entry(rec[g], poses, it.col0, it.ncols, dh, dl, s, lane);
-            s_ids[wib][lane] = g;
+        float T = 1.f, Qp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (seg > 0) {
+            const float4 *pq = partials + ((size_t)(ui.y + seg) * 32 + lane) * 2;
+            const float4 u = pq[0], v = pq[1];
+            Qp[0] = u.x; Qp[1] = u.y; Qp[2] = u.z; Qp[3] = v.x; Qp[4] = u.w;
+            T = v.y;
         }
-        __syncwarp();
-        for (int j = cnt - 1; j >= 0; --j) {
-            float gl[kG];
-#pragma unroll
-            for (int k = 0; k < kG; ++k) gl[k] = 0.f;
-            PairEval pe;
-            if ((uint32_t)(bstart + j) < last &&
-                lidar_pair(s, j, sb, raz, rel, dd, d, P.alpha_min, P.alpha_max, pe)) {
-                float Mr[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) Mr[k] = s[k][j];
-                const float q[3] = {s[13][j], s[14][j], s[15][j]};
-                composite_grads(pe, s[12][j], q, gQ, T, S, Mr, d, gl);
+        float gQ[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Ut = 0.f, U = 0.f;
+        if (valid) {
+            const float4 st = ray_state[ray], F = ray_feat[ray];
+            const float W = st.y, Z = st.z, drop = st.w;
+            const float gr = g_range ? g_range[ray] : 0.f;
+            const float gi = g_int ? g_int[ray] : 0.f;
+            const float gp = g_drop ? g_drop[ray] : 0.f;
+            const float ga = g_alpha ? g_alpha[ray] : 0.f;
+            // drop = softmax(F1, F2)[drop] = 1 / (1 + exp(F1 - F2))
+            const float dd_ = drop * (1.f - drop);
+            gQ[0] = gi;
+            gQ[1] = -gp * dd_;
+            gQ[2] = gp * dd_;
+            gQ[3] = W > 0.f ? gr / W : 0.f;
+            gQ[4] = ga - (W > 0.f ? gr * Z / (W * W) : 0.f);
+            Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * Z + gQ[4] * W;
+            U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
+        }
+        for (uint32_t base = lo; base < hi; base += 32) {
+            const uint32_t idx = base + lane;
+            uint32_t m = 0u, g = 0u;
+            if (idx < hi) {
+                g = ids[idx];
+                const float4 rc = rec[g].rect;
+                m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, s_raz[wib], s_rel[wib]);
             }
-            const uint32_t g = s_ids[wib][j];
+            const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
+            if (bal == 0u) continue;
+            __syncwarp();
+            if (m) {
+                const int pos = __popc(bal & ((1u << lane) - 1u));
+                lidar_entry(rec[g], poses, it.col0, it.ncols, dh, dl, s, pos);
+                s_lanes[wib][pos] = m;
+                s_pos[wib][pos] = idx + 1 - rg.x;
+                s_gid[wib][pos] = g;
+            }
+            __syncwarp();
+            const int cnt = __popc(bal);
+            for (int j = 0; j < cnt; ++j) {
+                PairEval pe;
+                bool ok = lidar_pair_in(s, j, sb, (s_lanes[wib][j] >> lane) & 1u, dd, d,
+                                        P.alpha_min, P.alpha_max, pe);
+                ok = ok && s_pos[wib][j] <= last;
+                if (!__any_sync(0xffffffffu, ok)) continue;
+                float g[kG];
 #pragma unroll
-            for (int k = 0; k < kG; ++k) {
-                const float v = warp_sum(gl[k]);
-                if (lane == k && v != 0.f) atomicAdd(&gacc[(int64_t)g * kG + k], v);
+                for (int k = 0; k < kG; ++k) g[k] = 0.f;
+                if (ok) {
+                    float Mr[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) Mr[k] = s[k][j];
+                    const float q[3] = {s[13][j], s[14][j], s[15][j]};
+                    composite_grads(pe, s[12][j], q, gQ, T, U, Ut, Mr, d, g);
+                }
+                warp_reduce_add16(g, gacc + (int64_t)s_gid[wib][j] * kG);
             }
         }
     }
@@ -430,19 +522,55 @@ static sg_status finish(const Scene &sc, Frame &fr, const float o[3], const sg_g
     return SG_OK;
 }
 
+static int blocks_per_sm(const void *kern, int threads)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0) != cudaSuccess ||
+        nb < 1)
+        nb = 4;
+    return nb;
+}
+
+static sg_status persistent_grid(const void *kern, int64_t max_items, int64_t &grid)
+{
+    int dev = 0, sms = 0;
+    SG_CUDA(cudaGetDevice(&dev));
+    SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t cap = (max_items + kBwWarps - 1) / kBwWarps;
+    grid = (int64_t)sms * blocks_per_sm(kern, 32 * kBwWarps);
+    grid = grid < cap ? grid : cap;
+    if (grid < 1) grid = 1;
+    return SG_OK;
+}
+
 sg_status backward_camera(const Scene &sc, const Camera &cam, Frame &fr, const float *g_rgb,
                           const float *g_alpha, const float *g_depth, const sg_grads &g,
                           cudaStream_t st)
 {
+    if (fr.seg_len != kSegLen) {
+        set_error("sg_backward_camera: the frame's render used another list segment length");
+        return SG_ERR_INVALID;
+    }
     sg_status s = ensure(fr.gacc, sizeof(float) * kG * (sc.n > 0 ? sc.n : 1));
     if (s != SG_OK) return s;
     SG_CUDA(cudaMemsetAsync(fr.gacc.p, 0, sizeof(float) * kG * sc.n, st));
     const CamRender P = cam_render_params(cam, fr.opts);
-    k_backward_camera<<<(unsigned)(cam.ntx * cam.nty), kCamThreads, 0, st>>>(
+    const int nt = cam.ntx * cam.nty;
+    const WorkSize ws = work_size(nt, fr.n_pairs, kSegLen, 8);
+    const unsigned char *cw = (const unsigned char *)fr.camwork.p;
+    uint32_t *counter = (uint32_t *)fr.scalars.p + 6;
+    SG_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), st));
+    int64_t grid = 0;
+    if ((s = persistent_grid((const void *)k_backward_camera, ws.max_items, grid)) != SG_OK)
+        return s;
+    k_backward_camera<<<(unsigned)grid, 32 * kBwWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
-        (const uint2 *)fr.ranges.p, (const uint32_t *)fr.order.p, cam.d_pix, cam.d_tile_dir,
+        (const uint2 *)fr.ranges.p, (const uint2 *)(cw + ws.info_bytes + ws.off_bytes),
+        (const uint2 *)cw, (const uint32_t *)fr.scalars.p + 4, (const uint8_t *)fr.submask.p,
+        counter, (const float4 *)fr.partials.p, cam.d_pix, cam.d_tile_dir,
         (const RenderDesc *)fr.desc.p, (const float4 *)fr.ray_state.p,
-        (const uint32_t *)fr.n_contrib.p, g_rgb, g_alpha, g_depth, (float *)fr.gacc.p);
+        (const float4 *)fr.ray_feat.p, (const uint32_t *)fr.n_contrib.p, g_rgb, g_alpha,
+        g_depth, (float *)fr.gacc.p);
     SG_LAUNCHED();
     const float o[3] = {fr.c2w[3], fr.c2w[7], fr.c2w[11]};
     return finish(sc, fr, o, g, st);
@@ -457,13 +585,21 @@ sg_status backward_lidar(const Scene &sc, const Lidar &L, Frame &fr, const float
     SG_CUDA(cudaMemsetAsync(fr.gacc.p, 0, sizeof(float) * kG * sc.n, st));
     const LidRender P = lidar_render_params(L, fr.opts);
     if (L.n_items > 0) {
-        unsigned grid = (unsigned)((L.n_items + kLidarWarps - 1) / kLidarWarps);
-        k_backward_lidar<<<grid, 32 * kLidarWarps, 0, st>>>(
+        const WorkSize ws = work_size(L.n_items, fr.n_pairs, kSegLen, 1);
+        const unsigned char *cw = (const unsigned char *)fr.camwork.p;
+        uint32_t *counter = (uint32_t *)fr.scalars.p + 6;
+        SG_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), st));
+        int64_t grid = 0;
+        if ((s = persistent_grid((const void *)k_backward_lidar, ws.max_items, grid)) != SG_OK)
+            return s;
+        k_backward_lidar<<<(unsigned)grid, 32 * kBwWarps, 0, st>>>(
             P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, fr.d_lidar_poses, L.d_az,
             L.d_elev, (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
-            (const uint2 *)fr.ranges.p, (const float4 *)fr.ray_state.p,
-            (const uint32_t *)fr.n_contrib.p, g_range, g_int, g_drop, g_alpha,
-            (float *)fr.gacc.p);
+            (const uint2 *)fr.ranges.p, (const uint2 *)(cw + ws.info_bytes + ws.off_bytes),
+            (const uint2 *)cw, (const uint32_t *)fr.scalars.p + 4, counter,
+            (const float4 *)fr.partials.p, (const float4 *)fr.ray_state.p,
+            (const float4 *)fr.ray_feat.p, (const uint32_t *)fr.n_contrib.p, g_range, g_int,
+            g_drop, g_alpha, (float *)fr.gacc.p);
         SG_LAUNCHED();
     }
     const float o[3] = {0.f, 0.f, 0.f};

@@ -158,6 +158,7 @@ static sg_status frame_prepare(Frame &fr, int64_t n, int64_t nrays, int64_t ntil
     SG_ENS(fr.offsets, sizeof(uint32_t) * (n > 0 ? n : 1));
     SG_ENS(fr.ranges, sizeof(uint2) * (ntiles > 0 ? ntiles : 1));
     SG_ENS(fr.ray_state, sizeof(float4) * (nrays > 0 ? nrays : 1));
+    SG_ENS(fr.ray_feat, sizeof(float4) * (nrays > 0 ? nrays : 1));
     SG_ENS(fr.n_contrib, sizeof(uint32_t) * (nrays > 0 ? nrays : 1));
     SG_ENS(fr.scalars, 64);
     SG_ENS(fr.desc, sizeof(RenderDesc));

@@ -132,6 +132,7 @@ struct Frame {
     Buf camwork, partials;
     // per-ray saved state: (T_final, omega, Z, LiDAR drop) and contributor count
     Buf ray_state, n_contrib;
+    Buf ray_feat;     // per ray: the final feature sums (F0, F1, F2, 0), for the backward
     // backward accumulators: per Gaussian dL/dM (9), dL/dmu (3), dL/dsigma,
     // dL/dfeature (3)
     Buf gacc;
@@ -166,33 +167,36 @@ uint64_t next_uid();            // identity of a scene / sensor handle
 
 constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Upper bounds of the camera work-item buffers for `ntiles` tiles,
-// `n_pairs` listed pairs and segment length L: segments per tile are 1 for a
-// list of at most L entries and ceil(len / L) above, so the items are at
-// most 8 (ntiles + n_pairs / L) and the partial slots (segments of long
-// tiles) at most min(2 n_pairs / L, ntiles + n_pairs / L).  Buffers: per
-// tile (segments, first partial slot) and the first item of the tile in
-// launch order, the items, the arrival counters of long (tile, sub-block)s.
-struct CamWorkSize {
+// Upper bounds of the compositing work-item buffers.  A unit (a camera
+// tile, or a LiDAR work item of up to 32 rays of one tile) whose list holds
+// len entries gives 1 segment if len <= L and ceil(len / L) above; each
+// segment gives `subs` work items (8 sub-blocks of a camera tile, 1 for
+// LiDAR).  So with `units` units and `n_pairs` list entries in all, the
+// work items are at most subs (units + n_pairs / L) and the partial slots
+// (segments of split units) at most min(2 n_pairs / L, units + n_pairs / L).
+// Buffers: per unit (segments, first partial slot) and its first work item
+// in launch order, the work items, arrival counters (subs per slot) and the
+// per-ray partials (32 subs rays per slot, two float4 each).
+struct WorkSize {
     int64_t max_items = 0, max_slots = 0;
     size_t info_bytes = 0, off_bytes = 0, items_bytes = 0, arrive_bytes = 0, work_bytes = 0,
            partial_bytes = 0;
 };
-constexpr CamWorkSize cam_work_size(int64_t ntiles, int64_t n_pairs, uint32_t seg_len)
+constexpr WorkSize work_size(int64_t units, int64_t n_pairs, uint32_t seg_len, int subs)
 {
-    CamWorkSize w;
+    WorkSize w;
     const int64_t per = n_pairs / (int64_t)seg_len;
-    const int64_t nt1 = ntiles > 0 ? ntiles : 1;
-    w.max_items = 8 * (ntiles + per);
-    w.max_slots = 2 * per < ntiles + per ? 2 * per : ntiles + per;
+    const int64_t u1 = units > 0 ? units : 1;
+    w.max_items = subs * (units + per);
+    w.max_slots = 2 * per < units + per ? 2 * per : units + per;
     const int64_t items1 = w.max_items > 0 ? w.max_items : 1;
     const int64_t slots1 = w.max_slots > 0 ? w.max_slots : 1;
-    w.info_bytes = al256(8 * (size_t)nt1);
-    w.off_bytes = al256(4 * (size_t)nt1);
+    w.info_bytes = al256(8 * (size_t)u1);
+    w.off_bytes = al256(4 * (size_t)u1);
     w.items_bytes = al256(8 * (size_t)items1);
-    w.arrive_bytes = al256(4 * 8 * (size_t)slots1);
+    w.arrive_bytes = al256(4 * (size_t)subs * (size_t)slots1);
     w.work_bytes = w.info_bytes + w.off_bytes + w.items_bytes + w.arrive_bytes;
-    w.partial_bytes = 2 * 16 * 256 * (size_t)slots1;
+    w.partial_bytes = 2 * 16 * 32 * (size_t)subs * (size_t)slots1;
     return w;
 }
 
@@ -251,7 +255,8 @@ template <class Fn> inline void for_each_buf(Frame &f, Fn fn)
                    &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.cnt_sorted,
                    &f.offsets, &f.flags, &f.scan_tmp, &f.hist, &f.pkeys[0], &f.pkeys[1],
                    &f.pvals[0], &f.pvals[1], &f.ranges, &f.order, &f.submask, &f.camwork,
-                   &f.partials, &f.ray_state, &f.n_contrib, &f.gacc, &f.scalars, &f.desc};
+                   &f.partials, &f.ray_state, &f.n_contrib, &f.ray_feat, &f.gacc, &f.scalars,
+                   &f.desc};
     for (Buf *b : bufs) fn(*b);
 }
 }  // namespace sg

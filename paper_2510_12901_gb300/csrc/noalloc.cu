@@ -28,7 +28,7 @@ constexpr size_t kStG4 = al(4 * kStMaxGauss);
 constexpr size_t kStP4 = al(4 * kStMaxPairs);
 constexpr size_t kStHist = al(4 * 2 * 256 * ((kStMaxPairs + 2047) / 2048));
 constexpr size_t kStScan = al(4 * 4096);
-constexpr CamWorkSize kStWork = cam_work_size(kStMaxTiles, kStMaxPairs, kSegLenStatic);
+constexpr WorkSize kStWork = work_size(kStMaxTiles, kStMaxPairs, kSegLenStatic, 8);
 constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, tiles, cov2d, mean2d
                             2 * kStG4 +                          // depth, count
                             4 * kStG4 +                          // depth-sort keys/values x2
@@ -36,7 +36,8 @@ constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, ti
                             4 * kStP4 +                          // pair keys/values x2
                             kStHist + kStScan +
                             al(8 * kStMaxTiles) + al(4 * kStMaxTiles) +  // ranges, order
-                            al(16 * kStMaxRays) + al(4 * kStMaxRays) +   // ray state, contributors
+                            2 * al(16 * kStMaxRays) + al(4 * kStMaxRays) + // ray state, features,
+                                                                         // contributors
                             al(kStMaxPairs) +                            // sub-block masks
                             kStWork.work_bytes + kStWork.partial_bytes + // work items, partials
                             al(64) +                                     // device scalars
@@ -141,6 +142,7 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     carve(fr.ranges, cur, al(8 * kStMaxTiles));
     carve(fr.order, cur, al(4 * kStMaxTiles));
     carve(fr.ray_state, cur, al(16 * kStMaxRays));
+    carve(fr.ray_feat, cur, al(16 * kStMaxRays));
     carve(fr.n_contrib, cur, al(4 * kStMaxRays));
     carve(fr.submask, cur, al(kStMaxPairs));
     carve(fr.camwork, cur, kStWork.work_bytes);

@@ -182,16 +182,30 @@ __device__ __forceinline__ void lidar_entry(const GRec &r, const float *poses, i
     }
 }
 
-// Evaluate one LiDAR pair (entry j of the warp's block, column slot `sb`).
-__device__ __forceinline__ bool lidar_pair(float (*s)[32], int j, int sb, float raz, float rel,
-                                           const float dd[3], const float d[3], float alpha_min,
-                                           float alpha_max, PairEval &pe)
+// Which of a LiDAR work item's rays (angles raz[r], rel[r], NaN for an
+// empty lane) lie in an entry's box (bx0, bx1, by0, by1): bit r, taking for
+// each ray the azimuth alias nearest the box centre.  The same float
+// operations as the per-ray test of lidar_pair.
+__device__ __forceinline__ uint32_t lidar_lanes(float bx0, float bx1, float by0, float by1,
+                                                const float *raz, const float *rel)
 {
-    // azimuth alias of the ray nearest the box centre, then the box test
-    const float bx0 = s[16][j], bx1 = s[17][j];
-    const float kk = rintf((0.5f * (bx0 + bx1) - raz) * (1.f / 360.f));
-    const float ra = raz + 360.f * kk;
-    if (!(ra >= bx0 && ra <= bx1 && rel >= s[18][j] && rel <= s[19][j])) return false;
+    const float cx = 0.5f * (bx0 + bx1);
+    uint32_t m = 0;
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+        const float kk = rintf((cx - raz[r]) * (1.f / 360.f));
+        const float ra = raz[r] + 360.f * kk;
+        m |= (uint32_t)(ra >= bx0 && ra <= bx1 && rel[r] >= by0 && rel[r] <= by1) << r;
+    }
+    return m;
+}
+
+// Evaluate one LiDAR pair (entry j of the warp's block, column slot `sb`)
+// whose box test is already known (in_box).
+__device__ __forceinline__ bool lidar_pair_in(float (*s)[32], int j, int sb, bool in_box,
+                                              const float dd[3], const float d[3],
+                                              float alpha_min, float alpha_max, PairEval &pe)
+{
     const float vx = s[sb][j], vy = s[sb + 1][j], vz = s[sb + 2][j];
     const float cr0 = vy * dd[2] - vz * dd[1];
     const float cr1 = vz * dd[0] - vx * dd[2];
@@ -205,12 +219,11 @@ __device__ __forceinline__ bool lidar_pair(float (*s)[32], int j, int sb, float 
     pe.inv = __fdividef(1.f, pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
     pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
     pe.tau = (s[sb + 6][j] * pe.e[0] + s[sb + 7][j] * pe.e[1] + s[sb + 8][j] * pe.e[2]) * pe.inv;
-    if (!(pe.tau > 0.f)) return false;
     pe.rho = __expf(-0.5f * pe.D2);
     const float a = s[12][j] * pe.rho;
     pe.clamped = a > alpha_max;
     pe.alpha = fminf(a, alpha_max);
-    return pe.alpha >= alpha_min;
+    return in_box && pe.tau > 0.f && pe.alpha >= alpha_min;
 }
 
 // LiDAR ray set-up shared by forward and backward: reference direction of

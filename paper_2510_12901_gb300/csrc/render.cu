@@ -62,26 +62,34 @@ __device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *s
     return r;
 }
 
-// Work items of the camera compositing.  Tiles are taken in (coarsely)
-// decreasing list length, so the longest start first.  A tile whose list is
-// longer than seg_len entries is split along the list into
-// ceil(len / seg_len) segments; every (tile, segment) gives eight items, one
-// per 8x4 sub-block.  k_camera_items (one CTA) orders the tiles and assigns
-// per tile (segments, first partial slot) and its first item; k_emit_items
-// (one warp per tile) writes the items (tile, 8 seg + sub) and resets the
-// arrival counters of long tiles.  The item counter of the compositing
+// Work items of the compositing.  A unit is a camera tile (units = tiles)
+// or a LiDAR work item (up to 32 rays of one tile, unit_tile[u].tile).
+// Units are taken in (coarsely) decreasing list length, so the longest start
+// first.  A unit whose list is longer than seg_len entries is split along
+// the list into ceil(len / seg_len) segments; every (unit, segment) gives
+// `subs` work items (the eight 8x4 sub-blocks of a camera tile, or one).
+// k_work_items (one CTA) orders the units and assigns per unit (segments,
+// first partial slot) and its first work item; k_emit_items (one warp per
+// unit) writes the work items (unit, subs * seg + sub) and resets the
+// arrival counters of split units.  The work counter of the compositing
 // kernel is reset here too.
+__device__ __forceinline__ uint32_t unit_len(const uint2 *ranges, const LidarItem *unit_tile, int u)
+{
+    const uint2 r = ranges[unit_tile ? unit_tile[u].tile : (uint32_t)u];
+    return r.y - r.x;
+}
+
 __global__ void __launch_bounds__(1024)
-k_camera_items(const uint2 *__restrict__ ranges, int ntiles, uint32_t seg_len,
-               uint32_t *__restrict__ order, uint2 *__restrict__ tile_info,
-               uint32_t *__restrict__ item_off, uint32_t *__restrict__ counts,
-               uint32_t *__restrict__ counter)
+k_work_items(const uint2 *__restrict__ ranges, const LidarItem *__restrict__ unit_tile,
+             int n_units, int subs, uint32_t seg_len, uint32_t *__restrict__ order,
+             uint2 *__restrict__ unit_info, uint32_t *__restrict__ unit_off,
+             uint32_t *__restrict__ counts, uint32_t *__restrict__ counter)
 {
     __shared__ uint32_t s_cnt[33], s_off[33], s_w[33];
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const uint32_t len = ranges[t].y - ranges[t].x;
+    for (int u = threadIdx.x; u < n_units; u += blockDim.x) {
+        const uint32_t len = unit_len(ranges, unit_tile, u);
         const int b = len ? 32 - __clz(len) : 0;       // 0 (empty) .. 32
         atomicAdd(&s_cnt[32 - b], 1u);                   // longest bucket first
     }
@@ -91,27 +99,27 @@ k_camera_items(const uint2 *__restrict__ ranges, int ntiles, uint32_t seg_len,
         for (int i = 0; i < 33; ++i) { s_off[i] = run; run += s_cnt[i]; }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const uint32_t len = ranges[t].y - ranges[t].x;
+    for (int u = threadIdx.x; u < n_units; u += blockDim.x) {
+        const uint32_t len = unit_len(ranges, unit_tile, u);
         const int b = len ? 32 - __clz(len) : 0;
-        order[atomicAdd(&s_off[32 - b], 1u)] = (uint32_t)t;
+        order[atomicAdd(&s_off[32 - b], 1u)] = (uint32_t)u;
     }
     __syncthreads();
     uint32_t item_run = 0, part_run = 0;
-    for (int c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+    for (int c0 = 0; c0 < n_units; c0 += blockDim.x) {
         const int k = c0 + threadIdx.x;
-        uint32_t t = 0, nseg = 0;
-        if (k < ntiles) {
-            t = order[k];
-            const uint32_t len = ranges[t].y - ranges[t].x;
+        uint32_t u = 0, nseg = 0;
+        if (k < n_units) {
+            u = order[k];
+            const uint32_t len = unit_len(ranges, unit_tile, (int)u);
             nseg = len > seg_len ? (len + seg_len - 1) / seg_len : 1u;
         }
         uint32_t tot_items, tot_parts;
-        const uint32_t ib = item_run + block_excl_scan_1024(k < ntiles ? 8 * nseg : 0, s_w, tot_items);
+        const uint32_t ib = item_run + block_excl_scan_1024(k < n_units ? subs * nseg : 0, s_w, tot_items);
         const uint32_t pb = part_run + block_excl_scan_1024(nseg > 1 ? nseg : 0, s_w, tot_parts);
-        if (k < ntiles) {
-            tile_info[t] = make_uint2(nseg, pb);
-            item_off[k] = ib;
+        if (k < n_units) {
+            unit_info[u] = make_uint2(nseg, pb);
+            unit_off[k] = ib;
         }
         item_run += tot_items;
         part_run += tot_parts;
@@ -124,17 +132,39 @@ k_camera_items(const uint2 *__restrict__ ranges, int ntiles, uint32_t seg_len,
 }
 
 __global__ void k_emit_items(const uint32_t *__restrict__ order,
-                             const uint2 *__restrict__ tile_info,
-                             const uint32_t *__restrict__ item_off, int ntiles,
+                             const uint2 *__restrict__ unit_info,
+                             const uint32_t *__restrict__ unit_off, int n_units, int subs,
                              uint2 *__restrict__ items, uint32_t *__restrict__ arrive)
 {
     const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (k >= ntiles) return;
-    const uint32_t t = order[k];
-    const uint2 ti = tile_info[t];
-    const uint32_t ib = item_off[k], n = 8 * ti.x;
-    for (uint32_t i = lane; i < n; i += 32) items[ib + i] = make_uint2(t, i);
-    if (ti.x > 1 && lane < 8) arrive[ti.y * 8 + lane] = 0u;
+    if (k >= n_units) return;
+    const uint32_t u = order[k];
+    const uint2 ui = unit_info[u];
+    const uint32_t ib = unit_off[k], n = subs * ui.x;
+    for (uint32_t i = lane; i < n; i += 32) items[ib + i] = make_uint2(u, i);
+    if (ui.x > 1 && lane < subs) arrive[ui.y * subs + lane] = 0u;
+}
+
+// Launch both: the work items of `n_units` units into the frame's camwork
+// buffer laid out by ws.
+static sg_status launch_work_items(Frame &fr, const WorkSize &ws, const LidarItem *unit_tile,
+                                   int n_units, int subs, uint32_t seg_len, cudaStream_t st)
+{
+    unsigned char *cw = (unsigned char *)fr.camwork.p;
+    uint2 *unit_info = (uint2 *)cw;
+    uint32_t *unit_off = (uint32_t *)(cw + ws.info_bytes);
+    uint2 *items = (uint2 *)(cw + ws.info_bytes + ws.off_bytes);
+    uint32_t *arrive = (uint32_t *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes);
+    k_work_items<<<1, 1024, 0, st>>>((const uint2 *)fr.ranges.p, unit_tile, n_units, subs,
+                                     seg_len, (uint32_t *)fr.order.p, unit_info, unit_off,
+                                     (uint32_t *)fr.scalars.p + 4, (uint32_t *)fr.scalars.p + 2);
+    SG_LAUNCHED();
+    if (n_units > 0) {
+        k_emit_items<<<(unsigned)((n_units + 7) / 8), 256, 0, st>>>(
+            (const uint32_t *)fr.order.p, unit_info, unit_off, n_units, subs, items, arrive);
+        SG_LAUNCHED();
+    }
+    return SG_OK;
 }
 
 // Per (tile, Gaussian) pair of a camera list: which of the tile's eight
@@ -190,7 +220,9 @@ __global__ void k_submask(const uint32_t *__restrict__ keys, const uint32_t *__r
 // transmittance is an upper bound of the true one).  The last warp to finish
 // a (tile, sub-block) combines the runs in order and re-walks, from the true
 // transmittance, the one run in which a ray stops.  Run 0 starts from the
-// true state, so its own stop is final.
+// true state, so its own stop is final.  As it goes, the merge overwrites
+// each later run's partial with the state before that run (colour, omega, Z,
+// T), from which the backward walks the run.
 constexpr int kCamWarps = 4;       // warps per block of the persistent grid
 
 struct CamAcc {
@@ -265,7 +297,7 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
                 uint32_t *__restrict__ arrive, float4 *__restrict__ partials,
                 const float4 *__restrict__ pix, const double *__restrict__ tile_dir,
                 const RenderDesc *__restrict__ D, float4 *__restrict__ ray_state,
-                uint32_t *__restrict__ n_contrib)
+                float4 *__restrict__ ray_feat, uint32_t *__restrict__ n_contrib)
 {
     __shared__ float4 s_all[kCamWarps][8][32];
     __shared__ uint32_t s_pos[kCamWarps][32];
@@ -320,7 +352,7 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
                 continue;
             }
             __threadfence();
-            const float4 *pq = partials + ((size_t)ti.y * 256 + sub * 32 + lane) * 2;
+            float4 *pq = partials + ((size_t)ti.y * 256 + sub * 32 + lane) * 2;
             float4 u = __ldcg(pq), v = __ldcg(pq + 1);
             a = {v.y, u.w, v.x, u.x, u.y, u.z, __float_as_uint(v.z)};
             bool fin = no_ray || v.w != 0.f;
@@ -329,6 +361,10 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
                 pq += 512;
                 u = __ldcg(pq);
                 v = __ldcg(pq + 1);
+                // the state before segment sgi replaces its partial: the
+                // backward starts each segment from it
+                pq[0] = make_float4(a.c0, a.c1, a.c2, a.W);
+                pq[1] = make_float4(a.Z, a.T, 0.f, 0.f);
                 const bool take = !fin && v.w == 0.f && a.T * v.y >= P.t_min;
                 const bool redo = !fin && !take;
                 if (take) {
@@ -361,6 +397,7 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
             if (out_alpha) out_alpha[pidx] = a.W;
             if (out_depth) out_depth[pidx] = a.W > 0.f ? a.Z / a.W : 0.f;
             ray_state[pidx] = make_float4(a.T, a.W, a.Z, 0.f);
+            ray_feat[pidx] = make_float4(a.c0, a.c1, a.c2, 0.f);
             n_contrib[pidx] = a.last;
         }
         __syncwarp();
@@ -390,28 +427,19 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     const CamRender P = cam_render_params(cam, o);
     const int nt = cam.ntx * cam.nty;
     const int64_t K = fr.n_pairs;
-    const CamWorkSize ws = cam_work_size(nt, K, fr.seg_len);
+    const WorkSize ws = work_size(nt, K, fr.seg_len, 8);
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
     if (s == SG_OK) s = ensure(fr.submask, K > 0 ? (size_t)K : 1);
     if (s != SG_OK) return s;
     unsigned char *cw = (unsigned char *)fr.camwork.p;
-    uint2 *tile_info = (uint2 *)cw;
-    uint32_t *item_off = (uint32_t *)(cw + ws.info_bytes);
-    uint2 *items = (uint2 *)(cw + ws.info_bytes + ws.off_bytes);
+    const uint2 *tile_info = (const uint2 *)cw;
+    const uint2 *items = (const uint2 *)(cw + ws.info_bytes + ws.off_bytes);
     uint32_t *arrive = (uint32_t *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes);
-    uint32_t *counts = (uint32_t *)fr.scalars.p + 4;    // [0] items [1] slots
+    const uint32_t *counts = (const uint32_t *)fr.scalars.p + 4;    // [0] items [1] slots
     uint32_t *counter = (uint32_t *)fr.scalars.p + 2;
-    k_camera_items<<<1, 1024, 0, st>>>((const uint2 *)fr.ranges.p, nt, fr.seg_len,
-                                       (uint32_t *)fr.order.p, tile_info, item_off, counts,
-                                       counter);
-    SG_LAUNCHED();
-    if (nt > 0) {
-        k_emit_items<<<(unsigned)((nt + 7) / 8), 256, 0, st>>>(
-            (const uint32_t *)fr.order.p, tile_info, item_off, nt, items, arrive);
-        SG_LAUNCHED();
-    }
+    if ((s = launch_work_items(fr, ws, nullptr, nt, 8, fr.seg_len, st)) != SG_OK) return s;
     const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
     if (K > 0) {
         k_submask<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(
@@ -433,12 +461,82 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
         (const uint8_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
         cam.d_tile_dir, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
-        (uint32_t *)fr.n_contrib.p);
+        (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
     SG_LAUNCHED();
     return SG_OK;
 }
 
 // ------------------------------------------------------------------ LiDAR
+// LiDAR compositing, persistent warps over (work item, segment) units: a
+// LiDAR work item holds up to 32 rays of one tile (at most kLidarColsMax
+// columns, each with its own pose); lists longer than kSegLen entries are
+// split and combined exactly as for the camera (see k_render_camera).
+// Batches of 32 list entries are staged through the warp's shared-memory
+// slice with their per-column moments.
+
+// Per-warp shared state of a LiDAR work item: staged entries, their ray
+// masks and list positions, and the item's ray angles (NaN: no ray).
+struct LidStage {
+    float (*s)[32];
+    uint32_t *lanes, *pos;
+    float *raz, *rel;
+};
+
+// Composite entries [lo, hi) of the item's list (first entry `begin`): a
+// window of 32 entries is tested against the item's 32 rays (lidar_lanes),
+// only entries that reach a ray are staged, and each is evaluated for the
+// rays in its mask.  Returns whether the lane's ray stopped at T_min.
+__device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__restrict__ rec,
+                                           const uint32_t *__restrict__ ids,
+                                           const float *__restrict__ poses, const LidarItem &it,
+                                           int sb, const float dh[3], const float dl[3],
+                                           const float dd[3], const float d[3], uint32_t lo,
+                                           uint32_t hi, uint32_t begin, const LidStage &L,
+                                           CamAcc &a, bool done)
+{
+    const int lane = threadIdx.x & 31;
+    const bool done0 = done;
+    for (uint32_t base = lo; base < hi; base += 32) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const uint32_t idx = base + lane;
+        uint32_t m = 0u, g = 0u;
+        if (idx < hi) {
+            g = ids[idx];
+            const float4 rc = rec[g].rect;
+            m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, L.raz, L.rel);
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
+        if (bal == 0u) continue;
+        __syncwarp();
+        if (m) {
+            const int pos = __popc(bal & ((1u << lane) - 1u));
+            lidar_entry(rec[g], poses, it.col0, it.ncols, dh, dl, L.s, pos);
+            L.lanes[pos] = m;
+            L.pos[pos] = idx + 1 - begin;
+        }
+        __syncwarp();
+        const int n = __popc(bal);
+        for (int j = 0; j < n; ++j) {
+            PairEval pe;
+            bool ok = lidar_pair_in(L.s, j, sb, (L.lanes[j] >> lane) & 1u, dd, d, P.alpha_min,
+                                    P.alpha_max, pe);
+            ok = ok && !done;
+            const float Tn = a.T * (1.f - pe.alpha);
+            const bool stop = ok && Tn < P.t_min;
+            done = done || stop;
+            ok = ok && !stop;
+            const float wgt = ok ? pe.alpha * a.T : 0.f;
+            a.c0 += wgt * L.s[13][j];
+            a.c1 += wgt * L.s[14][j];
+            a.c2 += wgt * L.s[15][j];
+            a.Z += wgt * pe.tau;
+            a.W += wgt;
+            a.T = ok ? Tn : a.T;
+            a.last = ok ? L.pos[j] : a.last;
+        }
+    }
+    return done && !done0;
+}
 
 __global__ void __launch_bounds__(32 * kLidarWarps)
 k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
@@ -446,72 +544,151 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
                const double *__restrict__ item_u, const float *__restrict__ az_col,
                const float *__restrict__ elev, const GRec *__restrict__ rec,
                const uint32_t *__restrict__ ids, const uint2 *__restrict__ ranges,
+               const uint2 *__restrict__ work, const uint2 *__restrict__ unit_info,
+               const uint32_t *__restrict__ counts, uint32_t *__restrict__ counter,
+               uint32_t *__restrict__ arrive, float4 *__restrict__ partials,
                const RenderDesc *__restrict__ D, float4 *__restrict__ ray_state,
-               uint32_t *__restrict__ n_contrib)
+               float4 *__restrict__ ray_feat, uint32_t *__restrict__ n_contrib)
 {
     __shared__ float s_all[kLidarWarps][kLidEntry][32];
+    __shared__ uint32_t s_lanes[kLidarWarps][32], s_pos[kLidarWarps][32];
+    __shared__ float s_raz[kLidarWarps][32], s_rel[kLidarWarps][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int item_id = blockIdx.x * kLidarWarps + wib;
-    if (item_id >= P.n_items) return;
-    float(*s)[32] = s_all[wib];
+    const LidStage stg = {s_all[wib], s_lanes[wib], s_pos[wib], s_raz[wib], s_rel[wib]};
     const float *__restrict__ poses = D->poses;
-    const LidarItem it = items[item_id];
-    const uint32_t ray = item_rays[it.ray_off + lane];
-    const bool valid = ray != 0xffffffffu;
-    const int c = valid ? (int)(ray % (uint32_t)P.n_cols) : it.col0;
-    const int b = valid ? (int)(ray / (uint32_t)P.n_cols) : 0;
-    const int sb = kLidCommon + kLidPerCol * (c - it.col0);
-    float dh[3], dl[3], dd[3], d[3];
-    lidar_ray(it, item_u, item_id, poses, ray_e[it.ray_off + lane], c, dh, dl, dd, d);
-    const float raz = az_col[c], rel = elev[b];
-    bool done = !valid;
-    float T = 1.f, W = 0.f, Z = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    uint32_t last = 0;
-    const uint2 rg = ranges[it.tile];
-    for (uint32_t base = rg.x; base < rg.y; base += 32) {
-        if (__all_sync(0xffffffffu, done)) break;
-        const uint32_t idx = base + lane;
+    const uint32_t n_work = counts[0];
+    while (true) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(counter, 1u);
+        wi = __shfl_sync(0xffffffffu, wi, 0);
+        if (wi >= n_work) break;
+        const uint2 w = work[wi];
+        const int item_id = (int)w.x;
+        const uint32_t seg = w.y;
+        const uint2 ui = unit_info[item_id];         // (segments, first partial slot)
+        const LidarItem it = items[item_id];
+        const uint32_t ray = item_rays[it.ray_off + lane];
+        const bool valid = ray != 0xffffffffu;
+        const int c = valid ? (int)(ray % (uint32_t)P.n_cols) : it.col0;
+        const int b = valid ? (int)(ray / (uint32_t)P.n_cols) : 0;
+        const int sb = kLidCommon + kLidPerCol * (c - it.col0);
+        float dh[3], dl[3], dd[3], d[3];
+        lidar_ray(it, item_u, item_id, poses, ray_e[it.ray_off + lane], c, dh, dl, dd, d);
+        stg.raz[lane] = valid ? az_col[c] : __int_as_float(0x7fc00000);
+        stg.rel[lane] = valid ? elev[b] : __int_as_float(0x7fc00000);
         __syncwarp();
-        if (idx < rg.y) lidar_entry(rec[ids[idx]], poses, it.col0, it.ncols, dh, dl, s, lane);
-        __syncwarp();
-        const int cnt = min(32u, rg.y - base);
-        for (int j = 0; j < cnt && !done; ++j) {
-            PairEval pe;
-            if (!lidar_pair(s, j, sb, raz, rel, dd, d, P.alpha_min, P.alpha_max, pe)) continue;
-            const float Tn = T * (1.f - pe.alpha);
-            if (Tn < P.t_min) { done = true; break; }
-            const float wgt = pe.alpha * T;
-            c0 += wgt * s[13][j];
-            c1 += wgt * s[14][j];
-            c2 += wgt * s[15][j];
-            Z += wgt * pe.tau;
-            W += wgt;
-            T = Tn;
-            last = base + j + 1 - rg.x;
+        const uint2 rg = ranges[it.tile];
+        const uint32_t lo = rg.x + seg * kSegLen;
+        const uint32_t hi = min(rg.y, lo + kSegLen);
+        CamAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+        const bool stopped = lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, lo, hi, rg.x,
+                                        stg, a, !valid);
+        if (ui.x > 1) {
+            // split item: publish this segment, and combine if it is the last one
+            float4 *pp = partials + ((size_t)(ui.y + seg) * 32 + lane) * 2;
+            pp[0] = make_float4(a.c0, a.c1, a.c2, a.W);
+            pp[1] = make_float4(a.Z, a.T, __uint_as_float(a.last), stopped ? 1.f : 0.f);
+            __threadfence();
+            __syncwarp();
+            uint32_t prev = 0;
+            if (lane == 0) prev = atomicAdd(&arrive[ui.y], 1u);
+            prev = __shfl_sync(0xffffffffu, prev, 0);
+            if (prev != ui.x - 1) {
+                __syncwarp();
+                continue;
+            }
+            __threadfence();
+            float4 *pq = partials + ((size_t)ui.y * 32 + lane) * 2;
+            float4 u = __ldcg(pq), v = __ldcg(pq + 1);
+            a = {v.y, u.w, v.x, u.x, u.y, u.z, __float_as_uint(v.z)};
+            bool fin = !valid || v.w != 0.f;
+            for (uint32_t sgi = 1; sgi < ui.x; ++sgi) {
+                if (__all_sync(0xffffffffu, fin)) break;
+                pq += 64;
+                u = __ldcg(pq);
+                v = __ldcg(pq + 1);
+                // the state before segment sgi replaces its partial (backward)
+                pq[0] = make_float4(a.c0, a.c1, a.c2, a.W);
+                pq[1] = make_float4(a.Z, a.T, 0.f, 0.f);
+                const bool take = !fin && v.w == 0.f && a.T * v.y >= P.t_min;
+                const bool redo = !fin && !take;
+                if (take) {
+                    a.c0 += a.T * u.x;
+                    a.c1 += a.T * u.y;
+                    a.c2 += a.T * u.z;
+                    a.W += a.T * u.w;
+                    a.Z += a.T * v.x;
+                    a.T *= v.y;
+                    const uint32_t l = __float_as_uint(v.z);
+                    a.last = l ? l : a.last;
+                }
+                if (__any_sync(0xffffffffu, redo)) {
+                    const uint32_t l0 = rg.x + sgi * kSegLen;
+                    lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, l0,
+                               min(rg.y, l0 + kSegLen), rg.x, stg, a, !redo);
+                }
+                fin = fin || redo;
+            }
         }
+        if (valid) {
+            const float drop = 1.f / (1.f + expf(a.c1 - a.c2));
+            float *const out_range = D->out[0], *const out_int = D->out[1];
+            float *const out_drop = D->out[2], *const out_alpha = D->out[3];
+            if (out_range) out_range[ray] = a.W > 0.f ? a.Z / a.W : 0.f;
+            if (out_int) out_int[ray] = a.c0;
+            if (out_drop) out_drop[ray] = drop;
+            if (out_alpha) out_alpha[ray] = a.W;
+            ray_state[ray] = make_float4(a.T, a.W, a.Z, drop);
+            ray_feat[ray] = make_float4(a.c0, a.c1, a.c2, 0.f);
+            n_contrib[ray] = a.last;
+        }
+        __syncwarp();
     }
-    if (!valid) return;
-    const float drop = 1.f / (1.f + expf(c1 - c2));
-    float *const out_range = D->out[0], *const out_int = D->out[1];
-    float *const out_drop = D->out[2], *const out_alpha = D->out[3];
-    if (out_range) out_range[ray] = W > 0.f ? Z / W : 0.f;
-    if (out_int) out_int[ray] = c0;
-    if (out_drop) out_drop[ray] = drop;
-    if (out_alpha) out_alpha[ray] = W;
-    ray_state[ray] = make_float4(T, W, Z, drop);
-    n_contrib[ray] = last;
+}
+
+static int lidar_blocks_per_sm()
+{
+    static int cached = 0;
+    if (!cached) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_lidar, 32 * kLidarWarps,
+                                                          0) != cudaSuccess ||
+            nb < 1)
+            nb = 4;
+        cached = nb;
+    }
+    return cached;
 }
 
 sg_status render_lidar(const Lidar &L, const sg_render_opts &o, Frame &fr, cudaStream_t st)
 {
     const LidRender P = lidar_render_params(L, o);
     if (L.n_items == 0) return SG_OK;
+    const int64_t K = fr.n_pairs;
+    const WorkSize ws = work_size(L.n_items, K, kSegLen, 1);
+    sg_status s = ensure(fr.order, sizeof(uint32_t) * (size_t)L.n_items);
+    if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
+    if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
+    if (s != SG_OK) return s;
+    if ((s = launch_work_items(fr, ws, L.d_items, L.n_items, 1, kSegLen, st)) != SG_OK) return s;
+    unsigned char *cw = (unsigned char *)fr.camwork.p;
+    const uint2 *unit_info = (const uint2 *)cw;
+    const uint2 *work = (const uint2 *)(cw + ws.info_bytes + ws.off_bytes);
+    uint32_t *arrive = (uint32_t *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes);
     const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
-    unsigned grid = (unsigned)((L.n_items + kLidarWarps - 1) / kLidarWarps);
-    k_render_lidar<<<grid, 32 * kLidarWarps, 0, st>>>(
+    int dev = 0, sms = 0;
+    SG_CUDA(cudaGetDevice(&dev));
+    SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t cap = (ws.max_items + kLidarWarps - 1) / kLidarWarps;
+    int64_t grid = (int64_t)sms * lidar_blocks_per_sm();
+    grid = grid < cap ? grid : cap;
+    if (grid < 1) grid = 1;
+    k_render_lidar<<<(unsigned)grid, 32 * kLidarWarps, 0, st>>>(
         P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, L.d_az, L.d_elev,
-        (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, (const RenderDesc *)fr.desc.p,
-        (float4 *)fr.ray_state.p, (uint32_t *)fr.n_contrib.p);
+        (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, work, unit_info,
+        (const uint32_t *)fr.scalars.p + 4, (uint32_t *)fr.scalars.p + 2, arrive,
+        (float4 *)fr.partials.p, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
+        (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
     SG_LAUNCHED();
     return SG_OK;
 }

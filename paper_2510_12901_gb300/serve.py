@@ -211,7 +211,7 @@ class ServingWorkload:
         return self.rays(i)
 
 
-def measure_serving(n_requests=300, loads=(0.5, 0.8, 1.0, 1.2), n_slots=4, seed=3,
+def measure_serving(n_requests=300, loads=(0.5, 0.8, 1.0, 1.2, 2.0), n_slots=4, seed=3,
                     memory_budget=0, **kw):
     """One-request-per-launch capacity, then open-loop Poisson arrivals at
     each load (a multiple of that capacity): Mrays/s and p50/p99 latency."""
@@ -229,10 +229,12 @@ def measure_serving(n_requests=300, loads=(0.5, 0.8, 1.0, 1.2), n_slots=4, seed=
             "latency_p99_ms": float(np.percentile(lat, 99))}
     srv = Server(n_slots=n_slots, memory_budget=memory_budget)
     reqs = [W.request(i) for i in range(n_requests)]
-    # warm every slot's workspace with each request kind
-    warm = [srv.submit(reqs[i]) for i in range(n_requests)[: 4 * n_slots]]
-    for t in warm:
-        srv.wait(t)
+    # warm up: two bursts of the whole stream, so that every slot has grown
+    # its workspace and captured the graphs of the combinations it serves
+    for _ in range(2):
+        warm = [srv.submit(r) for r in reqs]
+        for t in warm:
+            srv.wait(t)
     out = []
     for load in loads:
         arr = poisson_arrivals(n_requests, load * rps, seed + int(load * 100))
@@ -240,7 +242,9 @@ def measure_serving(n_requests=300, loads=(0.5, 0.8, 1.0, 1.2), n_slots=4, seed=
         out.append({"load": load, "offered_requests_per_s": load * rps,
                     "mrays_per_s": st["mrays_per_s"], "latency_p50_ms": st["latency_p50_ms"],
                     "latency_p99_ms": st["latency_p99_ms"], "completed": st["completed"],
-                    "peak_in_flight": st["peak_in_flight"]})
+                    "peak_in_flight": st["peak_in_flight"],
+                    "graph_replays": st["graph_replays"], "graph_captures": st["graph_captures"],
+                    "overflow_rerenders": st["overflow_rerenders"]})
     srv.close()
     return {"one_request_per_launch": base, "server": out, "n_slots": n_slots,
             "requests_per_load": n_requests,

@@ -77,13 +77,13 @@ def _structs(real):
         _fields_ = [("valid", C.c_int), ("mean2d", real * 2), ("cov2d", real * 3),
                     ("rect", real * 4), ("tiles", C.c_int * 4), ("count", C.c_int),
                     ("depth", real), ("pose_col", C.c_int), ("vmargin", real), ("ut", C.c_int),
-                    ("pmargin", real)]
+                    ("pmargin", real), ("cmargin", real), ("kdelta", real)]
 
     class Ray(C.Structure):
         _fields_ = [("out", real * 3), ("alpha", real), ("depth", real), ("zsum", real),
                     ("t_final", real), ("n_visited", C.c_int), ("n_evaluated", C.c_int),
                     ("n_contrib", C.c_int), ("m_rect", real), ("m_alpha", real),
-                    ("m_tmin", real), ("m_tau", real), ("m_order", real)]
+                    ("m_tmin", real), ("m_tau", real), ("m_order", real), ("m_kpose", real)]
 
     return Scene, Camera, Lidar, Opts, Setup, Proj, Ray
 

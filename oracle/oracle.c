@@ -552,6 +552,7 @@ void or_project_camera(const or_scene *sc, const or_camera *cam,
     for (int64_t g = 0; g < sc->n; ++g) {
         or_proj *p = &out[g];
         memset(p, 0, sizeof(*p));
+        p->cmargin = RL(1e30);
         real q[4], R[9], s[3], mu[3];
         unit_quat(sc->quats + 4 * g, q, NULL);
         quat_to_R(q, R);
@@ -652,6 +653,7 @@ void or_project_lidar(const or_scene *sc, const or_lidar *L,
     for (int64_t g = 0; g < sc->n; ++g) {
         or_proj *p = &out[g];
         memset(p, 0, sizeof(*p));
+        p->cmargin = RL(1e30);
         real q[4], R[9], s[3], mu[3];
         unit_quat(sc->quats + 4 * g, q, NULL);
         quat_to_R(q, R);
@@ -667,6 +669,16 @@ void or_project_lidar(const or_scene *sc, const or_lidar *L,
             lidar_point_map(&ctx, mu, 0, y);
             p->depth = RL((float)ctx.range0);   /* float32 key, as for cameras */
             p->pose_col = ctx.col0;
+            /* how close that column choice came to flipping, and what the key
+               would be with either neighbouring column's pose */
+            p->cmargin = ctx.pmargin;
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                real xs[3];
+                to_sensor(L->col_c2w + 12 * pmod(ctx.col0 + sgn, L->n_cols), mu, xs);
+                real kd = fabs(RL((float)sqrt(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2])) -
+                               p->depth);
+                if (kd > p->kdelta) p->kdelta = kd;
+            }
         }
         p->vmargin = fabs(sigma - amin) / amin;
         if (!(sigma >= amin)) continue;
@@ -887,7 +899,12 @@ static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR
 {
     memset(out, 0, sizeof(*out));
     out->m_rect = out->m_alpha = out->m_tmin = out->m_tau = out->m_order = RL(1e30);
+    out->m_kpose = RL(1e30);
     real prev_key = RL(-1);
+    /* keys of the entries that reached compositing, for m_kpose */
+    real *kk = nlist > 0 ? malloc(sizeof(real) * (size_t)nlist) : NULL;
+    uint32_t *kg = nlist > 0 ? malloc(sizeof(uint32_t) * (size_t)nlist) : NULL;
+    int64_t nk = 0;
     real T = RL(1), acc[3] = {0, 0, 0}, Z = 0, W = 0;
     real amin = RL(o->alpha_min), amax = RL(o->alpha_max), tmin = RL(o->t_min);
     int64_t nr = 0;
@@ -924,6 +941,14 @@ static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR
             if (gap < out->m_order) out->m_order = gap;
         }
         prev_key = P[g].depth;
+        /* a key that a column-pose flip could move past another one */
+        for (int64_t q = 0; q < nk; ++q) {
+            real gap = fabs(P[g].depth - kk[q]);
+            if (gap <= P[g].kdelta && P[g].cmargin < out->m_kpose) out->m_kpose = P[g].cmargin;
+            if (gap <= P[kg[q]].kdelta && P[kg[q]].cmargin < out->m_kpose)
+                out->m_kpose = P[kg[q]].cmargin;
+        }
+        if (kk) { kk[nk] = P[g].depth; kg[nk] = g; nk++; }
         real Tn = T * (RL(1) - alpha);
         if (o->cutoffs) {
             real mt = fabs(Tn - tmin) / tmin;
@@ -949,6 +974,8 @@ static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR
     out->t_final = T;
     out->depth = W > RL(0) ? Z / W : RL(0);
     if (nrec) *nrec = nr;
+    free(kk);
+    free(kg);
 }
 
 /* ------------------------------------------------------------------ */

@@ -92,6 +92,10 @@ typedef struct {
     int ut;               /* the unscented transform ran (all sigma points valid) */
     real pmargin;         /* LiDAR: min distance (in columns) of a sigma point's
                              azimuth to a column boundary in the pose choice */
+    real cmargin;         /* LiDAR: the same for the centre alone (the sort key's
+                             column); 1e30 for cameras */
+    real kdelta;          /* LiDAR: largest change of the float32 key if the centre
+                             took a neighbouring column's pose; 0 for cameras */
 } or_proj;
 
 /* Per-ray outputs and statistics. */
@@ -109,6 +113,9 @@ typedef struct {
     real m_tmin;          /* min |T' - t_min| / t_min over composited + stopping */
     real m_tau;           /* min |tau| over evaluated */
     real m_order;         /* min relative gap of consecutive sort keys of contributing entries */
+    real m_kpose;         /* min cmargin over contributing entries whose key is within
+                             their kdelta of another contributing entry's key (a
+                             column-pose flip could swap them); 1e30 if none */
 } or_ray;
 
 #ifdef __cplusplus

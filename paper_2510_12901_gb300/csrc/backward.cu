@@ -585,7 +585,7 @@ sg_status backward_lidar(const Scene &sc, const Lidar &L, Frame &fr, const float
     SG_CUDA(cudaMemsetAsync(fr.gacc.p, 0, sizeof(float) * kG * sc.n, st));
     const LidRender P = lidar_render_params(L, fr.opts);
     if (L.n_items > 0) {
-        const WorkSize ws = work_size(L.n_items, fr.n_pairs, kSegLen, 1);
+        const WorkSize ws = work_size(L.n_items, fr.n_pairs * L.max_items_per_tile, kSegLen, 1);
         const unsigned char *cw = (const unsigned char *)fr.camwork.p;
         uint32_t *counter = (uint32_t *)fr.scalars.p + 6;
         SG_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), st));

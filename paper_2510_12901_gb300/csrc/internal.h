@@ -83,6 +83,7 @@ struct Lidar {
     int nphi = 0, M = 0, n_theta = 0, cull_az = 0, cull_el = 0;
     std::vector<float> elev, T;
     int n_items = 0;
+    int max_items_per_tile = 1;     // work items sharing one tile, at most
     float *d_T = nullptr;           // [nphi+1]
     float *d_elev = nullptr;        // [n_beams]
     float *d_az = nullptr;          // [n_cols] column azimuth (deg)
@@ -137,7 +138,8 @@ struct Frame {
     // dL/dfeature (3)
     Buf gacc;
     Buf scalars;      // device scalars: [0] valid Gaussians [1] pairs [2] work-item
-                      // counter [3] pairs dropped over capacity [4..5] camera work counts
+                      // counter [3] pairs dropped over capacity [4..5] work-item counts
+                      // [6] backward work counter
     Buf desc;         // RenderDesc of the current render (device)
     uint32_t *h_scalars = nullptr;  // pinned: scalars mirror (64 B), then the RenderDesc
     RenderDesc *h_desc = nullptr;   // pinned staging of desc

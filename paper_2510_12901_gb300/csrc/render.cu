@@ -665,7 +665,9 @@ sg_status render_lidar(const Lidar &L, const sg_render_opts &o, Frame &fr, cudaS
     const LidRender P = lidar_render_params(L, o);
     if (L.n_items == 0) return SG_OK;
     const int64_t K = fr.n_pairs;
-    const WorkSize ws = work_size(L.n_items, K, kSegLen, 1);
+    // items that share a tile each walk its list: the entries of all units
+    // add up to at most max_items_per_tile x K
+    const WorkSize ws = work_size(L.n_items, K * L.max_items_per_tile, kSegLen, 1);
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (size_t)L.n_items);
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);

@@ -329,6 +329,14 @@ sg_status build_lidar(Lidar &L)
         }
     }
     L.n_items = (int)items.size();
+    {
+        // a tile wider than kLidarColsMax columns or holding more than 32
+        // rays gives several items, each walking the tile's whole list
+        std::vector<int> per_tile((size_t)nphi * L.n_theta, 0);
+        int mx = 1;
+        for (const LidarItem &it : items) mx = std::max(mx, ++per_tile[it.tile]);
+        L.max_items_per_tile = mx;
+    }
 
 #define SG_ALLOC_COPY(dst, vec)                                                         \
     do {                                                                                \

@@ -32,9 +32,12 @@ TOL_DEPTH_REL = 1e-3
 
 def ambiguous_rays(orc, lidar=False):
     mr = MARGIN_RECT_DEG if lidar else MARGIN_RECT_PX
-    return ((orc["m_alpha"] < MARGIN_ALPHA) | (orc["m_tmin"] < MARGIN_TMIN) |
-            (orc["m_rect"] < mr) | (orc["m_tau"] < MARGIN_TAU) |
-            (orc["m_order"] < MARGIN_ORDER))
+    amb = ((orc["m_alpha"] < MARGIN_ALPHA) | (orc["m_tmin"] < MARGIN_TMIN) |
+           (orc["m_rect"] < mr) | (orc["m_tau"] < MARGIN_TAU) |
+           (orc["m_order"] < MARGIN_ORDER))
+    if lidar:   # a sort key whose column pose is within rounding of flipping
+        amb |= orc["m_kpose"] < MARGIN_POSE_COLS
+    return amb
 
 
 def compare_camera_rays(rgb, alpha, depth, orc, max_excluded=0.01, label=""):
@@ -55,8 +58,42 @@ def compare_camera_rays(rgb, alpha, depth, orc, max_excluded=0.01, label=""):
     return info
 
 
-def compare_lidar_rays(rng, inten, drop, alpha, orc, max_excluded=0.01, label=""):
+def lidar_rays_seeing(rays, L, gauss, rect_a, rect_b, pad=MARGIN_RECT_DEG):
+    """Which rays (indices of the beam-major [n_beams, n_cols] grid) fall in
+    the box of one of the Gaussians `gauss` by one of the two rect arrays
+    [n, 4] and not by the other (any azimuth alias, boxes padded by `pad`
+    for "in" and shrunk by it for "out"): the rays whose extent test such a
+    Gaussian could decide either way, e.g. where the GPU and the oracle
+    took different column poses for it."""
+    rays = np.asarray(rays, np.int64)
+    c = rays % L.n_cols
+    az = L.az0_deg + (c + 0.5) * 360.0 / L.n_cols
+    el = np.asarray(L.elevations_deg, np.float64)[rays // L.n_cols]
+    A = np.asarray(rect_a, np.float64)[gauss]
+    B = np.asarray(rect_b, np.float64)[gauss]
+    out = np.zeros(len(rays), bool)
+
+    def inside(r, p):
+        m = (el[:, None] >= r[None, :, 2] - p) & (el[:, None] <= r[None, :, 3] + p)
+        hit = np.zeros(m.shape, bool)
+        for shift in (-360.0, 0.0, 360.0):
+            a = az[:, None] + shift
+            hit |= (a >= r[None, :, 0] - p) & (a <= r[None, :, 1] + p)
+        return m & hit
+
+    for lo in range(0, len(A), 2048):
+        a, b = A[lo:lo + 2048], B[lo:lo + 2048]
+        out |= ((inside(a, pad) & ~inside(b, -pad)) | (inside(b, pad) & ~inside(a, -pad))).any(axis=1)
+    return out
+
+
+def compare_lidar_rays(rng, inten, drop, alpha, orc, max_excluded=0.01, label="",
+                       also_excluded=None):
+    """also_excluded: rays whose result depends on a Gaussian whose
+    projection is itself ambiguous (see lidar_rays_seeing)."""
     amb = ambiguous_rays(orc, lidar=True)
+    if also_excluded is not None:
+        amb = amb | also_excluded
     ok = ~amb
     o_rng = orc["depth"]
     o_int = orc["out"][:, 0]
@@ -80,12 +117,13 @@ def _near_multiple(x, step, offset, tol):
     return np.abs(r - np.round(r)) * step < tol
 
 
-def rect_band(P32, P64, floor, ulps):
+def rect_band(P32, P64, floor, ulps, cond=None):
     """Per-Gaussian, per-edge band within which two float32 implementations
     of the box may disagree: the larger of 8x the disagreement between the
     oracle's float32 and double builds and `ulps` float32 ulps of the edge's
     magnitude plus the box's spread (sigma points far from the axis and near
-    Gaussians amplify rounding), plus a small floor."""
+    Gaussians amplify rounding), times an optional per-Gaussian condition
+    factor, plus a small floor."""
     r32 = P32["rect"].astype(np.float64)
     r64 = P64["rect"]
     d = np.abs(r32 - r64)
@@ -94,7 +132,19 @@ def rect_band(P32, P64, floor, ulps):
     sx = np.sqrt(np.maximum(P64["cov2d"][:, 0], 0.0))
     sy = np.sqrt(np.maximum(P64["cov2d"][:, 2], 0.0))
     spread = np.stack([sx, sx, sy, sy], 1)
-    return floor + np.maximum(8.0 * d, ulps * 2.0 ** -24 * (np.abs(r64) + spread))
+    u = ulps * 2.0 ** -24 * (np.abs(r64) + spread)
+    if cond is not None:
+        u = u * cond[:, None]
+    return floor + np.maximum(8.0 * d, u)
+
+
+def lidar_condition(P64):
+    """Amplification of rounding in a LiDAR box: sigma points at elevation e
+    go through asin, whose slope is 1 / cos(e); the box's largest |elevation|
+    (capped at 89 deg) bounds it.  About 1.1 in the beams' range, large only
+    for Gaussians that reach towards the sensor's vertical axis."""
+    e = np.minimum(np.maximum(np.abs(P64["rect"][:, 2]), np.abs(P64["rect"][:, 3])), 89.0)
+    return 1.0 / np.cos(np.radians(e))
 
 
 MARGIN_POSE_COLS = 3e-4   # LiDAR: sigma point within ~4 float32 ulps (at 180 deg) of a column boundary
@@ -120,7 +170,7 @@ def tile_ambiguous_camera(P32, P64, W, H, tile=16):
 
 def tile_ambiguous_lidar(P32, P64, T, n_theta, az0, A, per):
     rect = P32["rect"].astype(np.float64)
-    band = rect_band(P32, P64, 2e-5, 16)
+    band = rect_band(P32, P64, 2e-5, 16, lidar_condition(P64))
     amb = (P32["ut"] != P64["ut"]) | (P32["vmargin"] < MARGIN_VALID)
     ut = P64["ut"] == 1
     amb |= ut & (P64["pmargin"] < MARGIN_POSE_COLS)

@@ -145,18 +145,33 @@ def test_host_output_path_matches_device_path(sg):
         assert np.array_equal(o, g[k]), k
 
 
-def test_full_sweep_sampled_parity(sg, O32, O64):
-    """2M Gaussians, 128 beams x 2048 columns, per-column poses over 0.1 s."""
+@pytest.mark.parametrize("beams", [128, 64])
+def test_full_sweep_sampled_parity(sg, O32, O64, beams):
+    """2M Gaussians, 128 beams x 2048 columns (or 64 x 1024, where a tile of
+    32 rays spans 8 columns and is walked by two work items), per-column
+    poses over 0.1 s; tile lists of thousands of entries, split in segments."""
     sc = syn.street_scene(2_000_000, seed=10, kind="lidar")
-    L = syn.street_lidar()
+    L = syn.street_lidar() if beams == 128 else syn.street_lidar(n_beams=64, n_cols=1024)
     g = gpu_render(sg, sc, L)
+    lens = np.diff(g["frame"].field(sg.FIELD_RANGES, np.uint32, 2).astype(np.int64), axis=1)
+    assert lens.max() > 8 * 256
     rng = np.random.default_rng(0)
     rays = np.unique(rng.choice(L.n_beams * L.n_cols, 4000, replace=False))
     orc = O64.render_lidar(sc, L, rays=rays)
-    info = par.compare_lidar_rays(g["range"][rays], g["intensity"][rays], g["drop"][rays],
-                                  g["alpha"][rays], orc, label="full")
-    assert (orc["n_contrib"] > 0).mean() > 0.3, info
     P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, O64, "full")
+    # rays inside the box of a Gaussian whose column-pose choice is within
+    # rounding (its box differs by up to a column's motion between the two)
+    P64, _ = O64.project_lidar(sc, L)
+    pose_amb = (P64["ut"] == 1) & (P64["pmargin"] < par.MARGIN_POSE_COLS)
+    seen = par.lidar_rays_seeing(rays, L, pose_amb,
+                                 g["frame"].field(sg.FIELD_RECT, np.float32, 4), P64["rect"])
+    # each Gaussian takes 14 column-pose decisions: about 1% of the rays see
+    # one within rounding (box or key order), more with 64 beams (two work
+    # items per tile, larger per-column motion)
+    info = par.compare_lidar_rays(g["range"][rays], g["intensity"][rays], g["drop"][rays],
+                                  g["alpha"][rays], orc, max_excluded=0.02,
+                                  label=f"full-{beams}", also_excluded=seen)
+    assert (orc["n_contrib"] > 0).mean() > 0.3, info
     ids = g["frame"].field(sg.FIELD_PAIR_IDS, np.uint32)
     ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)
     o_ids, _, o_ranges = O32.bin_sort(P32, nth, nphi, True)

@@ -139,7 +139,7 @@ struct Frame {
     Buf gacc;
     Buf scalars;      // device scalars: [0] valid Gaussians [1] pairs [2] work-item
                       // counter [3] pairs dropped over capacity [4..5] work-item counts
-                      // [6] backward work counter
+                      // [6] backward work counter [8] radix-sort look-back timeout flag
     Buf desc;         // RenderDesc of the current render (device)
     uint32_t *h_scalars = nullptr;  // pinned: scalars mirror (64 B), then the RenderDesc
     RenderDesc *h_desc = nullptr;   // pinned staging of desc
@@ -206,6 +206,15 @@ constexpr WorkSize work_size(int64_t units, int64_t n_pairs, uint32_t seg_len, i
 // sort.cu
 sg_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, uint32_t *d_total,
                              int64_t n, Frame &fr, cudaStream_t st);
+// Scratch words (fr.hist) of a radix sort of up to n_max pairs in `passes`
+// 8-bit passes: digit counts and offsets (256 per pass), per-pass tile
+// tickets, and the look-back words (256 per tile of kRadixTile pairs and pass).
+constexpr int kRadixTile = 4096;
+constexpr int64_t radix_scratch_words(int64_t n_max, int passes)
+{
+    const int64_t tiles = (n_max + kRadixTile - 1) / kRadixTile;
+    return 2 * 256 * (int64_t)passes + 16 + (int64_t)passes * (tiles > 0 ? tiles : 1) * 256;
+}
 sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n,
                            const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
                            cudaStream_t st, int *result_buf);

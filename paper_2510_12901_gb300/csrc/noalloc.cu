@@ -26,7 +26,8 @@ constexpr size_t kStG16 = al(16 * kStMaxGauss);       // float4 / int4 per Gauss
 constexpr size_t kStG8 = al(8 * kStMaxGauss);
 constexpr size_t kStG4 = al(4 * kStMaxGauss);
 constexpr size_t kStP4 = al(4 * kStMaxPairs);
-constexpr size_t kStHist = al(4 * 2 * 256 * ((kStMaxPairs + 2047) / 2048));
+constexpr size_t kStHist = al(4 * radix_scratch_words(kStMaxPairs > kStMaxGauss ? kStMaxPairs
+                                                                             : kStMaxGauss, 4));
 constexpr size_t kStScan = al(4 * 4096);
 constexpr WorkSize kStWork = work_size(kStMaxTiles, kStMaxPairs, kSegLenStatic, 8);
 constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, tiles, cov2d, mean2d

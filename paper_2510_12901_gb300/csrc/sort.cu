@@ -153,87 +153,131 @@ sg_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, uint32_t *d_
 }
 
 // ------------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (key, value) pairs, 8-bit digits, one kernel per
+// digit pass with decoupled look-back (the "onesweep" scheme):
+//   1. k_sort_hist: one read of the keys counts the digits of every pass;
+//   2. k_sort_offsets: per pass, the exclusive scan of its 256 counts gives
+//      the first output position of each digit;
+//   3. k_onesweep, per pass: a block takes the next tile of 4096 pairs (an
+//      atomic ticket, so tiles are taken in order), ranks them stably
+//      (warp w owns 512 consecutive pairs, ranks among equal digits from
+//      __match_any_sync), publishes its per-digit counts, and walks back
+//      over earlier tiles' published counts until it meets an inclusive
+//      prefix; then it publishes its own inclusive prefix and scatters.
+// A tile only waits for tiles taken before it, whose blocks are running;
+// every such wait is bounded, and a wait that runs out sets *err.
 constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 8;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;   // 2048
+constexpr int kRadixItems = kRadixTile / kRadixThreads;
 constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr uint32_t kLbAgg = 1u << 30, kLbPre = 2u << 30, kLbCount = (1u << 30) - 1u;
+constexpr uint32_t kLbSpins = 1u << 22;
 
-// Per-block digit histogram, stored digit-major (hist[d * nblocks + b]) so
-// that one exclusive scan over it yields every block's output offsets.
 __global__ void __launch_bounds__(kRadixThreads)
-k_radix_hist(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_n, int shift,
-             uint32_t mask, uint32_t *__restrict__ hist, int nblocks)
+k_sort_hist(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_n, int begin_bit,
+            int end_bit, uint32_t *__restrict__ hist)
 {
-    __shared__ uint32_t s_h[256];
-    s_h[threadIdx.x] = 0;
+    __shared__ uint32_t s_h[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += kRadixThreads) (&s_h[0][0])[i] = 0;
     __syncthreads();
     const int64_t n = *d_n;
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (base < n) {
-#pragma unroll
-        for (int r = 0; r < kRadixItems; ++r) {
-            int64_t idx = base + (int64_t)warp * 32 * kRadixItems + r * 32 + lane;
-            bool in = idx < n;
-            uint32_t d = in ? (keys[idx] >> shift) & mask : 0xffffffffu;
-            uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (in && lane == __ffs(peers) - 1) atomicAdd(&s_h[d], (uint32_t)__popc(peers));
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    for (int64_t i = (int64_t)blockIdx.x * kRadixThreads + threadIdx.x;
+         i - threadIdx.x < n; i += (int64_t)gridDim.x * kRadixThreads) {
+        const bool in = i < n;
+        const uint32_t k = in ? keys[i] : 0u;
+        for (int p = 0; p < passes; ++p) {
+            const int b = begin_bit + 8 * p;
+            const int bits = end_bit - b < 8 ? end_bit - b : 8;
+            const uint32_t d = in ? (k >> b) & ((1u << bits) - 1u) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (in && (threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(&s_h[p][d], (uint32_t)__popc(peers));
         }
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
+    for (int p = 0; p < passes; ++p)
+        if (s_h[p][threadIdx.x]) atomicAdd(&hist[p * 256 + threadIdx.x], s_h[p][threadIdx.x]);
 }
 
-// Stable scatter: warp w owns elements [w*256, (w+1)*256) of the block tile,
-// taken 32 at a time in order; ranks among equal digits come from
-// __match_any_sync, warp offsets from a per-digit scan over the warps.
+__global__ void __launch_bounds__(256)
+k_sort_offsets(const uint32_t *__restrict__ hist, int passes, uint32_t *__restrict__ offsets)
+{
+    __shared__ uint32_t s_warp[33];
+    for (int p = 0; p < passes; ++p) {
+        uint32_t tot;
+        offsets[p * 256 + threadIdx.x] =
+            block_excl_scan(hist[p * 256 + threadIdx.x], s_warp, &tot);
+    }
+}
+
 __global__ void __launch_bounds__(kRadixThreads)
-k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                const uint32_t *__restrict__ d_n, int shift, uint32_t mask,
-                const uint32_t *__restrict__ hist_scanned, int nblocks)
+k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+           uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+           const uint32_t *__restrict__ d_n, int shift, uint32_t mask,
+           const uint32_t *__restrict__ offsets, uint32_t *__restrict__ lookback,
+           uint32_t *__restrict__ ticket, uint32_t *__restrict__ err)
 {
     __shared__ uint32_t s_cnt[kRadixWarps][256];
+    __shared__ uint32_t s_pre[256];
+    __shared__ uint32_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kRadixWarps * 256; i += kRadixThreads) (&s_cnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
+    const uint32_t tile = s_tile;
     const int64_t n = *d_n;
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-    if (base >= n) return;
+    const int64_t base = (int64_t)tile * kRadixTile;
+    if (base >= n) return;     // so is every later tile: nobody waits for this one
     uint32_t k[kRadixItems], v[kRadixItems], d[kRadixItems], rk[kRadixItems];
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
-        int64_t idx = base + (int64_t)warp * 32 * kRadixItems + r * 32 + lane;
-        bool in = idx < n;
+        const int64_t idx = base + (int64_t)warp * 32 * kRadixItems + r * 32 + lane;
+        const bool in = idx < n;
         k[r] = in ? keys_in[idx] : 0u;
         v[r] = in ? vals_in[idx] : 0u;
         d[r] = in ? (k[r] >> shift) & mask : 0xffffffffu;
-        uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
-        uint32_t below = __popc(peers & ((1u << lane) - 1u));
-        uint32_t before = in ? s_cnt[warp][d[r]] : 0u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
+        const uint32_t below = __popc(peers & ((1u << lane) - 1u));
+        const uint32_t before = in ? s_cnt[warp][d[r]] : 0u;
         rk[r] = before + below;
         __syncwarp();
         if (in && lane == __ffs(peers) - 1) s_cnt[warp][d[r]] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, plus the global offset
     {
-        uint32_t dgt = threadIdx.x;   // 256 threads, one digit each
-        uint32_t run = hist_scanned[(int64_t)dgt * nblocks + blockIdx.x];
+        // one digit per thread: offsets of the warps within the tile, the
+        // tile's count, then the look-back for the pairs of earlier tiles
+        const uint32_t dg = threadIdx.x;
+        uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kRadixWarps; ++w) {
-            uint32_t c = s_cnt[w][dgt];
-            s_cnt[w][dgt] = run;
+            const uint32_t c = s_cnt[w][dg];
+            s_cnt[w][dg] = run;
             run += c;
         }
+        volatile uint32_t *lb = lookback;
+        lb[(int64_t)tile * 256 + dg] = (tile == 0 ? kLbPre : kLbAgg) | run;
+        uint32_t excl = 0;
+        for (int64_t t = (int64_t)tile - 1; t >= 0; --t) {
+            uint32_t w = lb[t * 256 + dg], spins = 0;
+            while (!(w & (kLbAgg | kLbPre)) && ++spins <= kLbSpins) w = lb[t * 256 + dg];
+            if (!(w & (kLbAgg | kLbPre))) {   // gave up: flag it, leave the order wrong
+                atomicOr(err, 1u);
+                break;
+            }
+            excl += w & kLbCount;
+            if (w & kLbPre) break;
+        }
+        if (tile > 0) lb[(int64_t)tile * 256 + dg] = kLbPre | (excl + run);
+        s_pre[dg] = offsets[dg] + excl;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
-        int64_t idx = base + (int64_t)warp * 32 * kRadixItems + r * 32 + lane;
+        const int64_t idx = base + (int64_t)warp * 32 * kRadixItems + r * 32 + lane;
         if (idx < n) {
-            uint32_t pos = s_cnt[warp][d[r]] + rk[r];
+            const uint32_t pos = s_pre[d[r]] + s_cnt[warp][d[r]] + rk[r];
             keys_out[pos] = k[r];
             vals_out[pos] = v[r];
         }
@@ -244,24 +288,40 @@ sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                            const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
                            cudaStream_t st, int *result_buf)
 {
-    int cur = 0;
     *result_buf = 0;
     if (n_max <= 0 || end_bit <= begin_bit) return SG_OK;
-    int nblocks = (int)((n_max + kRadixTile - 1) / kRadixTile);
-    int64_t nh = (int64_t)nblocks * 256;
-    sg_status s = ensure(fr.hist, sizeof(uint32_t) * 2 * nh);
+    if (n_max > (int64_t)kLbCount) {
+        set_error("radix sort of %lld pairs exceeds 2^30", (long long)n_max);
+        return SG_ERR_OVERFLOW;
+    }
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    const int64_t tiles = (n_max + kRadixTile - 1) / kRadixTile;
+    const int64_t words = radix_scratch_words(n_max, passes);
+    sg_status s = ensure(fr.hist, sizeof(uint32_t) * words);
     if (s != SG_OK) return s;
-    uint32_t *hist = (uint32_t *)fr.hist.p, *hist_sc = hist + nh;
-    for (int b = begin_bit; b < end_bit; b += 8) {
-        int bits = end_bit - b < 8 ? end_bit - b : 8;
-        uint32_t mask = (1u << bits) - 1u;
-        k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(keys[cur], d_n, b, mask, hist, nblocks);
-        SG_LAUNCHED();
-        s = scan_exclusive_u32(hist, hist_sc, nullptr, nh, fr, st);
-        if (s != SG_OK) return s;
-        k_radix_scatter<<<nblocks, kRadixThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1],
-                                                           vals[cur ^ 1], d_n, b, mask, hist_sc,
-                                                           nblocks);
+    uint32_t *hist = (uint32_t *)fr.hist.p;
+    uint32_t *offsets = hist + 256 * passes;
+    uint32_t *tickets = offsets + 256 * passes;             // [passes], padded to 16
+    uint32_t *lookback = tickets + 16;
+    uint32_t *err = (uint32_t *)fr.scalars.p + 8;
+    SG_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 256 * passes, st));
+    SG_CUDA(cudaMemsetAsync(tickets, 0, sizeof(uint32_t) * (words - 2 * 256 * passes), st));
+    int dev = 0, sms = 0;
+    SG_CUDA(cudaGetDevice(&dev));
+    SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t hist_blocks = tiles < 4 * sms ? tiles : 4 * sms;
+    k_sort_hist<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys[0], d_n, begin_bit, end_bit,
+                                                                 hist);
+    SG_LAUNCHED();
+    k_sort_offsets<<<1, 256, 0, st>>>(hist, passes, offsets);
+    SG_LAUNCHED();
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int b = begin_bit + 8 * p;
+        const int bits = end_bit - b < 8 ? end_bit - b : 8;
+        k_onesweep<<<(unsigned)tiles, kRadixThreads, 0, st>>>(
+            keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n, b, (1u << bits) - 1u,
+            offsets + 256 * p, lookback + (int64_t)p * tiles * 256, tickets + p, err);
         SG_LAUNCHED();
         cur ^= 1;
     }

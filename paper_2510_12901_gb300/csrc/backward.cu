@@ -275,11 +275,11 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
                  const float *__restrict__ g_int, const float *__restrict__ g_drop,
                  const float *__restrict__ g_alpha, float *__restrict__ gacc)
 {
-    __shared__ float s_all[kBwWarps][kLidEntry][32];
+    __shared__ float4 s_all[kBwWarps][kLidPlanes][32];
     __shared__ uint32_t s_gid[kBwWarps][32], s_lanes[kBwWarps][32], s_pos[kBwWarps][32];
     __shared__ float s_raz[kBwWarps][32], s_rel[kBwWarps][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float(*s)[32] = s_all[wib];
+    float4(*s)[32] = s_all[wib];
     const uint32_t n_work = counts[0];
     while (true) {
         uint32_t wi = 0;
@@ -304,7 +304,7 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
         if (hi <= lo) continue;
         const int c = valid ? (int)(ray % (uint32_t)P.n_cols) : it.col0;
         const int b = valid ? (int)(ray / (uint32_t)P.n_cols) : 0;
-        const int sb = kLidCommon + kLidPerCol * (c - it.col0);
+        const int sb = 3 + 4 * (c - it.col0);
         float dh[3], dl[3], dd[3], d[3];
         lidar_ray(it, item_u, item_id, poses, ray_e[it.ray_off + lane], c, dh, dl, dd, d);
         s_raz[wib][lane] = valid ? az_col[c] : __int_as_float(0x7fc00000);
@@ -365,11 +365,10 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
 #pragma unroll
                 for (int k = 0; k < kG; ++k) g[k] = 0.f;
                 if (ok) {
-                    float Mr[9];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) Mr[k] = s[k][j];
-                    const float q[3] = {s[13][j], s[14][j], s[15][j]};
-                    composite_grads(pe, s[12][j], q, gQ, T, U, Ut, Mr, d, g);
+                    const float4 m0 = s[0][j], m1 = s[1][j], m2 = s[2][j];
+                    const float Mr[9] = {m0.x, m0.y, m0.z, m1.x, m1.y, m1.z, m2.x, m2.y, m2.z};
+                    const float q[3] = {m1.w, m2.w, s[sb + 3][j].w};
+                    composite_grads(pe, m0.w, q, gQ, T, U, Ut, Mr, d, g);
                 }
                 warp_reduce_add16(g, gacc + (int64_t)s_gid[wib][j] * kG);
             }

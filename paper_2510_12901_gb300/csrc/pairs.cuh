@@ -136,49 +136,40 @@ __device__ __forceinline__ uint32_t subblock_lanes(const float4 rc, int x0, int 
 }
 
 // LiDAR entries keep per-column quantities (each column has its own sensor
-// origin): common part M (9), f (3), sigma, features (3), box (4); then per
-// column v = mu - o_c (3), a = diag(f) M (v x d_T) (3), u = M v (3).
-constexpr int kLidCommon = 20;
-constexpr int kLidPerCol = 9;
-constexpr int kLidEntry = kLidCommon + kLidPerCol * kLidarColsMax;
+// origin o_c), as float4 planes of a warp's shared block s[kLidPlanes][32]:
+//   0: (M row 0, sigma)   1: (M row 1, f0)   2: (M row 2, f1)   (f: features)
+//   per column slot sl, planes 3 + 4 sl ..: (P row k, a_k) for k = 0..2 and
+//   (u = M v, f2), with v = mu - o_c, a = diag(f') M (v x d_T) and P rows
+//   f'_k (M_k x v) as for cameras (f'_k = s_k / (s_i s_j)).
+constexpr int kLidPlanes = 3 + 4 * kLidarColsMax;
 
-// Fill column-independent and per-column parts of entry `lane` of a warp's
-// shared block s[kLidEntry][32].
 __device__ __forceinline__ void lidar_entry(const GRec &r, const float *poses, int col0,
                                             int ncols, const float dh[3], const float dl[3],
-                                            float (*s)[32], int lane)
+                                            float4 (*s)[32], int pos)
 {
     const float mu[3] = {r.mu_sigma.x, r.mu_sigma.y, r.mu_sigma.z};
-    const float M[9] = {r.m0.x, r.m0.y, r.m0.z, r.m1.x, r.m1.y, r.m1.z, r.m2.x, r.m2.y, r.m2.z};
-    const float f[3] = {r.m0.w, r.m1.w, r.m2.w};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s[k][lane] = M[k];
-    s[9][lane] = f[0];
-    s[10][lane] = f[1];
-    s[11][lane] = f[2];
-    s[12][lane] = r.mu_sigma.w;
-    s[13][lane] = r.feat.x;
-    s[14][lane] = r.feat.y;
-    s[15][lane] = r.feat.z;
-    s[16][lane] = r.rect.x;
-    s[17][lane] = r.rect.y;
-    s[18][lane] = r.rect.z;
-    s[19][lane] = r.rect.w;
+    const float M0[3] = {r.m0.x, r.m0.y, r.m0.z}, M1[3] = {r.m1.x, r.m1.y, r.m1.z},
+                M2[3] = {r.m2.x, r.m2.y, r.m2.z};
+    const float f0 = r.m0.w, f1 = r.m1.w, f2 = r.m2.w;
+    s[0][pos] = make_float4(M0[0], M0[1], M0[2], r.mu_sigma.w);
+    s[1][pos] = make_float4(M1[0], M1[1], M1[2], r.feat.x);
+    s[2][pos] = make_float4(M2[0], M2[1], M2[2], r.feat.y);
     for (int sl = 0; sl < ncols; ++sl) {
         const float *Po = poses + 12 * (col0 + sl);
         const float o[3] = {Po[3], Po[7], Po[11]};
         float w[3], vh[3];
         precise_moment(mu, o, dh, dl, w, vh);
-        const int b = kLidCommon + kLidPerCol * sl;
-        s[b + 0][lane] = vh[0];
-        s[b + 1][lane] = vh[1];
-        s[b + 2][lane] = vh[2];
-        s[b + 3][lane] = f[0] * dot3(M, w);
-        s[b + 4][lane] = f[1] * dot3(M + 3, w);
-        s[b + 5][lane] = f[2] * dot3(M + 6, w);
-        s[b + 6][lane] = dot3(M, vh);
-        s[b + 7][lane] = dot3(M + 3, vh);
-        s[b + 8][lane] = dot3(M + 6, vh);
+        const int b = 3 + 4 * sl;
+        s[b][pos] = make_float4(f0 * (M0[1] * vh[2] - M0[2] * vh[1]),
+                                f0 * (M0[2] * vh[0] - M0[0] * vh[2]),
+                                f0 * (M0[0] * vh[1] - M0[1] * vh[0]), f0 * dot3(M0, w));
+        s[b + 1][pos] = make_float4(f1 * (M1[1] * vh[2] - M1[2] * vh[1]),
+                                    f1 * (M1[2] * vh[0] - M1[0] * vh[2]),
+                                    f1 * (M1[0] * vh[1] - M1[1] * vh[0]), f1 * dot3(M1, w));
+        s[b + 2][pos] = make_float4(f2 * (M2[1] * vh[2] - M2[2] * vh[1]),
+                                    f2 * (M2[2] * vh[0] - M2[0] * vh[2]),
+                                    f2 * (M2[0] * vh[1] - M2[1] * vh[0]), f2 * dot3(M2, w));
+        s[b + 3][pos] = make_float4(dot3(M0, vh), dot3(M1, vh), dot3(M2, vh), r.feat.z);
     }
 }
 
@@ -200,27 +191,25 @@ __device__ __forceinline__ uint32_t lidar_lanes(float bx0, float bx1, float by0,
     return m;
 }
 
-// Evaluate one LiDAR pair (entry j of the warp's block, column slot `sb`)
-// whose box test is already known (in_box).
-__device__ __forceinline__ bool lidar_pair_in(float (*s)[32], int j, int sb, bool in_box,
+// Evaluate one LiDAR pair (entry j of the warp's block, planes of its
+// column slot from sb = 3 + 4 sl) whose box test is already known (in_box).
+__device__ __forceinline__ bool lidar_pair_in(float4 (*s)[32], int j, int sb, bool in_box,
                                               const float dd[3], const float d[3],
                                               float alpha_min, float alpha_max, PairEval &pe)
 {
-    const float vx = s[sb][j], vy = s[sb + 1][j], vz = s[sb + 2][j];
-    const float cr0 = vy * dd[2] - vz * dd[1];
-    const float cr1 = vz * dd[0] - vx * dd[2];
-    const float cr2 = vx * dd[1] - vy * dd[0];
-    pe.n[0] = s[sb + 3][j] + s[9][j] * (s[0][j] * cr0 + s[1][j] * cr1 + s[2][j] * cr2);
-    pe.n[1] = s[sb + 4][j] + s[10][j] * (s[3][j] * cr0 + s[4][j] * cr1 + s[5][j] * cr2);
-    pe.n[2] = s[sb + 5][j] + s[11][j] * (s[6][j] * cr0 + s[7][j] * cr1 + s[8][j] * cr2);
-    pe.e[0] = s[0][j] * d[0] + s[1][j] * d[1] + s[2][j] * d[2];
-    pe.e[1] = s[3][j] * d[0] + s[4][j] * d[1] + s[5][j] * d[2];
-    pe.e[2] = s[6][j] * d[0] + s[7][j] * d[1] + s[8][j] * d[2];
+    const float4 m0 = s[0][j], m1 = s[1][j], m2 = s[2][j];
+    const float4 q0 = s[sb][j], q1 = s[sb + 1][j], q2 = s[sb + 2][j], u = s[sb + 3][j];
+    pe.n[0] = q0.w + q0.x * dd[0] + q0.y * dd[1] + q0.z * dd[2];
+    pe.n[1] = q1.w + q1.x * dd[0] + q1.y * dd[1] + q1.z * dd[2];
+    pe.n[2] = q2.w + q2.x * dd[0] + q2.y * dd[1] + q2.z * dd[2];
+    pe.e[0] = m0.x * d[0] + m0.y * d[1] + m0.z * d[2];
+    pe.e[1] = m1.x * d[0] + m1.y * d[1] + m1.z * d[2];
+    pe.e[2] = m2.x * d[0] + m2.y * d[1] + m2.z * d[2];
     pe.inv = __fdividef(1.f, pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
     pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
-    pe.tau = (s[sb + 6][j] * pe.e[0] + s[sb + 7][j] * pe.e[1] + s[sb + 8][j] * pe.e[2]) * pe.inv;
+    pe.tau = (u.x * pe.e[0] + u.y * pe.e[1] + u.z * pe.e[2]) * pe.inv;
     pe.rho = __expf(-0.5f * pe.D2);
-    const float a = s[12][j] * pe.rho;
+    const float a = m0.w * pe.rho;
     pe.clamped = a > alpha_max;
     pe.alpha = fminf(a, alpha_max);
     return in_box && pe.tau > 0.f && pe.alpha >= alpha_min;

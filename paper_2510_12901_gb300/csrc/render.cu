@@ -477,7 +477,7 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
 // Per-warp shared state of a LiDAR work item: staged entries, their ray
 // masks and list positions, and the item's ray angles (NaN: no ray).
 struct LidStage {
-    float (*s)[32];
+    float4 (*s)[32];
     uint32_t *lanes, *pos;
     float *raz, *rel;
 };
@@ -526,9 +526,9 @@ __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__res
             done = done || stop;
             ok = ok && !stop;
             const float wgt = ok ? pe.alpha * a.T : 0.f;
-            a.c0 += wgt * L.s[13][j];
-            a.c1 += wgt * L.s[14][j];
-            a.c2 += wgt * L.s[15][j];
+            a.c0 += wgt * L.s[1][j].w;
+            a.c1 += wgt * L.s[2][j].w;
+            a.c2 += wgt * L.s[sb + 3][j].w;
             a.Z += wgt * pe.tau;
             a.W += wgt;
             a.T = ok ? Tn : a.T;
@@ -550,7 +550,7 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
                const RenderDesc *__restrict__ D, float4 *__restrict__ ray_state,
                float4 *__restrict__ ray_feat, uint32_t *__restrict__ n_contrib)
 {
-    __shared__ float s_all[kLidarWarps][kLidEntry][32];
+    __shared__ float4 s_all[kLidarWarps][kLidPlanes][32];
     __shared__ uint32_t s_lanes[kLidarWarps][32], s_pos[kLidarWarps][32];
     __shared__ float s_raz[kLidarWarps][32], s_rel[kLidarWarps][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -571,7 +571,7 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
         const bool valid = ray != 0xffffffffu;
         const int c = valid ? (int)(ray % (uint32_t)P.n_cols) : it.col0;
         const int b = valid ? (int)(ray / (uint32_t)P.n_cols) : 0;
-        const int sb = kLidCommon + kLidPerCol * (c - it.col0);
+        const int sb = 3 + 4 * (c - it.col0);
         float dh[3], dl[3], dd[3], d[3];
         lidar_ray(it, item_u, item_id, poses, ray_e[it.ray_off + lane], c, dh, dl, dd, d);
         stg.raz[lane] = valid ? az_col[c] : __int_as_float(0x7fc00000);

@@ -167,13 +167,14 @@ sg_status sg_frame_dropped_pairs(sg_frame frame, int64_t *dropped, int64_t *pair
  *   d_rgb [H,W,3]  premultiplied foreground colour sum_i c_i alpha_i T_i
  *   d_alpha [H,W]  omega = sum_i alpha_i T_i
  *   d_depth [H,W]  sum_i tau_i alpha_i T_i / omega, 0 where omega = 0
- * LiDAR: d_col_c2w [n_cols,12] per-column sensor-to-world poses (device).
+ * LiDAR: d_col_c2w [n_cols,12] per-column sensor-to-world poses (device,
+ * 16-byte aligned).
  * Outputs (device, may be NULL), [n_beams, n_cols] beam-major:
  *   d_range    sum_i tau_i alpha_i T_i / omega (0 where omega = 0)
  *   d_intensity first channel of zeta
  *   d_drop      softmax(beta_hit, beta_drop) probability of a drop
  *   d_alpha     omega
- * Errors: SG_ERR_INVALID (NULL handle / pose, opts out of range, LiDAR
+ * Errors: SG_ERR_INVALID (NULL handle / pose, misaligned poses, opts out of range, LiDAR
  * features on a camera render or vice versa), SG_ERR_OOM, SG_ERR_CUDA,
  * SG_ERR_OVERFLOW (more than 2^31-1 pairs).
  * ---------------------------------------------------------------------- */

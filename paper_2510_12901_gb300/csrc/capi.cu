@@ -554,6 +554,10 @@ sg_status sg_render_lidar(sg_scene scene, sg_lidar lidar, const float *d_col_c2w
                           float *d_intensity, float *d_drop, float *d_alpha, void *stream)
 {
     if (!scene || !lidar || !frame || !d_col_c2w) { set_error("NULL handle or poses"); return SG_ERR_INVALID; }
+    if ((uintptr_t)d_col_c2w % 16 != 0) {
+        set_error("sg_render_lidar: d_col_c2w must be 16-byte aligned");
+        return SG_ERR_INVALID;
+    }
     if (!opts_ok(opts)) return SG_ERR_INVALID;
     const Scene &sc = scene->s;
     if (sc.feature_kind != SG_FEATURES_LIDAR) {

@@ -275,13 +275,18 @@ __device__ __forceinline__ int pmod(int a, int n)
     return m < 0 ? m + n : m;
 }
 
+// sensor-frame coordinates of x under the column pose P (row-major 3x4
+// c2w, 16-byte aligned: three float4 loads)
 __device__ __forceinline__ void to_sensor(const float *__restrict__ P, const float x[3],
                                           float xs[3])
 {
-    float d0 = x[0] - P[3], d1 = x[1] - P[7], d2 = x[2] - P[11];
-    xs[0] = P[0] * d0 + P[4] * d1 + P[8] * d2;
-    xs[1] = P[1] * d0 + P[5] * d1 + P[9] * d2;
-    xs[2] = P[2] * d0 + P[6] * d1 + P[10] * d2;
+    const float4 r0 = __ldg(reinterpret_cast<const float4 *>(P));
+    const float4 r1 = __ldg(reinterpret_cast<const float4 *>(P) + 1);
+    const float4 r2 = __ldg(reinterpret_cast<const float4 *>(P) + 2);
+    float d0 = x[0] - r0.w, d1 = x[1] - r1.w, d2 = x[2] - r2.w;
+    xs[0] = r0.x * d0 + r1.x * d1 + r2.x * d2;
+    xs[1] = r0.y * d0 + r1.y * d1 + r2.y * d2;
+    xs[2] = r0.z * d0 + r1.z * d1 + r2.z * d2;
 }
 
 __device__ __forceinline__ int col_of_az(const LidParams &L, float az)

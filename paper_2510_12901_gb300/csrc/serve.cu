@@ -377,7 +377,8 @@ sg_status sg_server_submit(sg_server S, const sg_request *req, uint64_t *ticket)
 {
     if (!S || !req || !ticket) { set_error("NULL argument"); return SG_ERR_INVALID; }
     if (!req->scene || (req->kind == SG_REQ_CAMERA && !req->camera) ||
-        (req->kind == SG_REQ_LIDAR && (!req->lidar || !req->d_col_c2w)) ||
+        (req->kind == SG_REQ_LIDAR &&
+         (!req->lidar || !req->d_col_c2w || (uintptr_t)req->d_col_c2w % 16 != 0)) ||
         (req->kind != SG_REQ_CAMERA && req->kind != SG_REQ_LIDAR)) {
         set_error("sg_server_submit: incomplete request");
         return SG_ERR_INVALID;

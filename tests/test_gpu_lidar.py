@@ -119,6 +119,21 @@ def test_static_sensor_pose_iterations_irrelevant(sg):
         assert np.array_equal(a[k], b[k]), k
 
 
+def test_misaligned_poses_are_refused(sg):
+    import torch
+    sc, L = toy(n=200)
+    S, Ld = sg.Scene(sc), sg.Lidar(L)
+    buf = torch.zeros(L.n_cols * 12 + 1, device="cuda")
+    buf[1:] = torch.from_numpy(np.ascontiguousarray(L.col_c2w, np.float32).reshape(-1)).cuda()
+    outs = [torch.empty((L.n_beams, L.n_cols), device="cuda") for _ in range(4)]
+    fr = sg.Frame()
+    with pytest.raises(sg.SimgutError) as e:
+        sg.sg_render_lidar(S.handle, Ld.handle, buf.data_ptr() + 4, sg.sg_default_opts(),
+                           fr.handle, *[o.data_ptr() for o in outs],
+                           torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == -1 and "aligned" in str(e.value)
+
+
 def test_ragged_sensor_and_empty_scene(sg, O64):
     sc, _ = toy(800, seed=4)
     L = syn.street_lidar(n_beams=64, n_cols=333)    # columns not divisible by N_theta

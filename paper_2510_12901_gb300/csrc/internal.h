@@ -209,7 +209,10 @@ sg_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, uint32_t *d_
 // Scratch words (fr.hist) of a radix sort of up to n_max pairs in `passes`
 // 8-bit passes: digit counts and offsets (256 per pass), per-pass tile
 // tickets, and the look-back words (256 per tile of kRadixTile pairs and pass).
-constexpr int kRadixTile = 4096;
+#ifndef SG_RADIX_TILE
+#define SG_RADIX_TILE 8192
+#endif
+constexpr int kRadixTile = SG_RADIX_TILE;
 constexpr int64_t radix_scratch_words(int64_t n_max, int passes)
 {
     const int64_t tiles = (n_max + kRadixTile - 1) / kRadixTile;

@@ -166,8 +166,13 @@ sg_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, uint32_t *d_
 //      prefix; then it publishes its own inclusive prefix and scatters.
 // A tile only waits for tiles taken before it, whose blocks are running;
 // every such wait is bounded, and a wait that runs out sets *err.
-constexpr int kRadixThreads = 256;
+#ifndef SG_RADIX_THREADS
+#define SG_RADIX_THREADS 1024
+#endif
+constexpr int kRadixThreads = SG_RADIX_THREADS;   // >= 256: one digit per thread below 256
 constexpr int kRadixItems = kRadixTile / kRadixThreads;
+static_assert(kRadixThreads >= 256 && kRadixItems * kRadixThreads == kRadixTile,
+              "radix tile layout");
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr uint32_t kLbAgg = 1u << 30, kLbPre = 2u << 30, kLbCount = (1u << 30) - 1u;
 constexpr uint32_t kLbSpins = 1u << 22;
@@ -195,8 +200,9 @@ k_sort_hist(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_n,
         }
     }
     __syncthreads();
-    for (int p = 0; p < passes; ++p)
-        if (s_h[p][threadIdx.x]) atomicAdd(&hist[p * 256 + threadIdx.x], s_h[p][threadIdx.x]);
+    if (threadIdx.x < 256)
+        for (int p = 0; p < passes; ++p)
+            if (s_h[p][threadIdx.x]) atomicAdd(&hist[p * 256 + threadIdx.x], s_h[p][threadIdx.x]);
 }
 
 __global__ void __launch_bounds__(256)
@@ -245,7 +251,7 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
         __syncwarp();
     }
     __syncthreads();
-    {
+    if (threadIdx.x < 256) {
         // one digit per thread: offsets of the warps within the tile, the
         // tile's count, then the look-back for the pairs of earlier tiles
         const uint32_t dg = threadIdx.x;

@@ -217,9 +217,15 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
             Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * st.z + gQ[4] * st.y;
             U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
+        const uint32_t act0 = __ballot_sync(0xffffffffu, rg.x + last > lo);
         for (uint32_t base = lo; base < hi; base += 32) {
+            // lanes whose composited entries reach this batch: once some
+            // have ended, an entry that reaches none of the others
+            // contributes to no ray and is not staged
+            const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
             const uint32_t idx = base + lane;
-            const bool ov = idx < hi && ((submask[idx] >> sub) & 1u);
+            bool ov = idx < hi && ((submask[idx] >> sub) & 1u);
+            if (act != act0 && ov) ov = (subblock_lanes(rec[ids[idx]].rect, sbx, sby) & act) != 0u;
             const uint32_t bal = __ballot_sync(0xffffffffu, ov);
             if (bal == 0u) continue;
             __syncwarp();
@@ -230,7 +236,7 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
                 cam_entry(rec[g], s_pose.t, dh, dl, ent);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
-                s_lanes[wib][pos] = subblock_lanes(ent[8], sbx, sby);
+                s_lanes[wib][pos] = subblock_lanes(ent[8], sbx, sby) & act;
                 s_pos[wib][pos] = idx + 1 - rg.x;
                 s_gid[wib][pos] = g;
             }
@@ -336,12 +342,13 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
             U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
         for (uint32_t base = lo; base < hi; base += 32) {
+            const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
             const uint32_t idx = base + lane;
             uint32_t m = 0u, g = 0u;
             if (idx < hi) {
                 g = ids[idx];
                 const float4 rc = rec[g].rect;
-                m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, s_raz[wib], s_rel[wib]);
+                m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, s_raz[wib], s_rel[wib]) & act;
             }
             const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
             if (bal == 0u) continue;

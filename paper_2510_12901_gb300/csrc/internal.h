@@ -139,7 +139,8 @@ struct Frame {
     Buf gacc;
     Buf scalars;      // device scalars: [0] valid Gaussians [1] pairs [2] work-item
                       // counter [3] pairs dropped over capacity [4..5] work-item counts
-                      // [6] backward work counter [8] radix-sort look-back timeout flag
+                      // [6] backward work counter [7] deferred re-walks
+                      // [8] radix-sort look-back timeout flag
     Buf desc;         // RenderDesc of the current render (device)
     uint32_t *h_scalars = nullptr;  // pinned: scalars mirror (64 B), then the RenderDesc
     RenderDesc *h_desc = nullptr;   // pinned staging of desc
@@ -177,12 +178,13 @@ constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 // work items are at most subs (units + n_pairs / L) and the partial slots
 // (segments of split units) at most min(2 n_pairs / L, units + n_pairs / L).
 // Buffers: per unit (segments, first partial slot) and its first work item
-// in launch order, the work items, arrival counters (subs per slot) and the
+// in launch order, the work items, arrival counters (subs per slot), the
+// deferred re-walks (one uint4 per slot and sub-unit at most) and the
 // per-ray partials (32 subs rays per slot, two float4 each).
 struct WorkSize {
-    int64_t max_items = 0, max_slots = 0;
-    size_t info_bytes = 0, off_bytes = 0, items_bytes = 0, arrive_bytes = 0, work_bytes = 0,
-           partial_bytes = 0;
+    int64_t max_items = 0, max_slots = 0, max_fixes = 0;
+    size_t info_bytes = 0, off_bytes = 0, items_bytes = 0, arrive_bytes = 0, fix_bytes = 0,
+           work_bytes = 0, partial_bytes = 0;
 };
 constexpr WorkSize work_size(int64_t units, int64_t n_pairs, uint32_t seg_len, int subs)
 {
@@ -197,7 +199,10 @@ constexpr WorkSize work_size(int64_t units, int64_t n_pairs, uint32_t seg_len, i
     w.off_bytes = al256(4 * (size_t)u1);
     w.items_bytes = al256(8 * (size_t)items1);
     w.arrive_bytes = al256(4 * (size_t)subs * (size_t)slots1);
-    w.work_bytes = w.info_bytes + w.off_bytes + w.items_bytes + w.arrive_bytes;
+    // deferred re-walks: at most one per (split unit, sub-unit, segment >= 1)
+    w.max_fixes = subs * slots1;
+    w.fix_bytes = al256(16 * (size_t)w.max_fixes);
+    w.work_bytes = w.info_bytes + w.off_bytes + w.items_bytes + w.arrive_bytes + w.fix_bytes;
     w.partial_bytes = 2 * 16 * 32 * (size_t)subs * (size_t)slots1;
     return w;
 }

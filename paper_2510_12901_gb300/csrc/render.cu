@@ -79,19 +79,42 @@ __device__ __forceinline__ uint32_t unit_len(const uint2 *ranges, const LidarIte
     return r.y - r.x;
 }
 
+constexpr int kWorkCache = 8192;   // unit lengths k_work_items keeps in shared memory
+
+__device__ __forceinline__ uint32_t len_bucket(uint32_t len)
+{
+    return 32u - (len ? 32u - __clz(len) : 0u);        // longest first: 0 .. 32
+}
+
 __global__ void __launch_bounds__(1024)
 k_work_items(const uint2 *__restrict__ ranges, const LidarItem *__restrict__ unit_tile,
              int n_units, int subs, uint32_t seg_len, uint32_t *__restrict__ order,
              uint2 *__restrict__ unit_info, uint32_t *__restrict__ unit_off,
              uint32_t *__restrict__ counts, uint32_t *__restrict__ counter)
 {
+    __shared__ uint32_t s_len[kWorkCache];
     __shared__ uint32_t s_cnt[33], s_off[33], s_w[33];
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int u = threadIdx.x; u < n_units; u += blockDim.x) {
-        const uint32_t len = unit_len(ranges, unit_tile, u);
-        const int b = len ? 32 - __clz(len) : 0;       // 0 (empty) .. 32
-        atomicAdd(&s_cnt[32 - b], 1u);                   // longest bucket first
+    auto len_of = [&](uint32_t u) {
+        return u < (uint32_t)kWorkCache ? s_len[u] : unit_len(ranges, unit_tile, (int)u);
+    };
+    // list lengths (four units' loads in flight per thread) and bucket sizes
+    for (int u0 = threadIdx.x; u0 < n_units; u0 += 4 * 1024) {
+        uint32_t len[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int u = u0 + k * 1024;
+            len[k] = u < n_units ? unit_len(ranges, unit_tile, u) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int u = u0 + k * 1024;
+            if (u < n_units) {
+                if (u < kWorkCache) s_len[u] = len[k];
+                atomicAdd(&s_cnt[len_bucket(len[k])], 1u);
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -99,34 +122,37 @@ k_work_items(const uint2 *__restrict__ ranges, const LidarItem *__restrict__ uni
         for (int i = 0; i < 33; ++i) { s_off[i] = run; run += s_cnt[i]; }
     }
     __syncthreads();
-    for (int u = threadIdx.x; u < n_units; u += blockDim.x) {
-        const uint32_t len = unit_len(ranges, unit_tile, u);
-        const int b = len ? 32 - __clz(len) : 0;
-        order[atomicAdd(&s_off[32 - b], 1u)] = (uint32_t)u;
-    }
+    for (int u = threadIdx.x; u < n_units; u += blockDim.x)
+        order[atomicAdd(&s_off[len_bucket(len_of((uint32_t)u))], 1u)] = (uint32_t)u;
     __syncthreads();
-    uint32_t item_run = 0, part_run = 0;
-    for (int c0 = 0; c0 < n_units; c0 += blockDim.x) {
-        const int k = c0 + threadIdx.x;
-        uint32_t u = 0, nseg = 0;
-        if (k < n_units) {
-            u = order[k];
-            const uint32_t len = unit_len(ranges, unit_tile, (int)u);
-            nseg = len > seg_len ? (len + seg_len - 1) / seg_len : 1u;
-        }
-        uint32_t tot_items, tot_parts;
-        const uint32_t ib = item_run + block_excl_scan_1024(k < n_units ? subs * nseg : 0, s_w, tot_items);
-        const uint32_t pb = part_run + block_excl_scan_1024(nseg > 1 ? nseg : 0, s_w, tot_parts);
-        if (k < n_units) {
-            unit_info[u] = make_uint2(nseg, pb);
-            unit_off[k] = ib;
-        }
-        item_run += tot_items;
-        part_run += tot_parts;
+    // each thread takes a contiguous run of launch positions: sums, one
+    // block scan per quantity, then the offsets along the run
+    const int per = (n_units + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int k0 = min(n_units, (int)threadIdx.x * per), k1 = min(n_units, k0 + per);
+    auto nseg_of = [&](uint32_t u) {
+        const uint32_t len = len_of(u);
+        return len > seg_len ? (len + seg_len - 1) / seg_len : 1u;
+    };
+    uint32_t ni = 0, np = 0;
+    for (int k = k0; k < k1; ++k) {
+        const uint32_t nseg = nseg_of(order[k]);
+        ni += subs * nseg;
+        np += nseg > 1 ? nseg : 0u;
+    }
+    uint32_t tot_items, tot_parts;
+    uint32_t ib = block_excl_scan_1024(ni, s_w, tot_items);
+    uint32_t pb = block_excl_scan_1024(np, s_w, tot_parts);
+    for (int k = k0; k < k1; ++k) {
+        const uint32_t u = order[k], nseg = nseg_of(u);
+        unit_info[u] = make_uint2(nseg, pb);
+        unit_off[k] = ib;
+        ib += subs * nseg;
+        pb += nseg > 1 ? nseg : 0u;
     }
     if (threadIdx.x == 0) {
-        counts[0] = item_run;
-        counts[1] = part_run;
+        counts[0] = tot_items;
+        counts[1] = tot_parts;
+        counts[3] = 0u;      // deferred re-walks
         *counter = 0u;
     }
 }
@@ -143,6 +169,31 @@ __global__ void k_emit_items(const uint32_t *__restrict__ order,
     const uint32_t ib = unit_off[k], n = subs * ui.x;
     for (uint32_t i = lane; i < n; i += 32) items[ib + i] = make_uint2(u, i);
     if (ui.x > 1 && lane < subs) arrive[ui.y * subs + lane] = 0u;
+}
+
+// Deferred re-walks of the compositing (scalars[7] of them): (unit, work
+// code, lane mask, 0), the work code as in the work items.
+struct FixList {
+    uint4 *fix;
+    uint32_t *n_fix;
+    uint32_t cap;
+};
+
+__device__ __forceinline__ void push_fix(const FixList &F, uint32_t unit, uint32_t code,
+                                         uint32_t lanes)
+{
+    if ((threadIdx.x & 31) == 0) {
+        const uint32_t k = atomicAdd(F.n_fix, 1u);
+        if (k < F.cap) F.fix[k] = make_uint4(unit, code, lanes, 0u);   // < cap by construction
+    }
+}
+
+// The deferred re-walks' list in the frame's camwork buffer laid out by ws.
+static FixList fix_list(Frame &fr, const WorkSize &ws)
+{
+    unsigned char *cw = (unsigned char *)fr.camwork.p;
+    return {(uint4 *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes + ws.arrive_bytes),
+            (uint32_t *)fr.scalars.p + 7, (uint32_t)ws.max_fixes};
 }
 
 // Launch both: the work items of `n_units` units into the frame's camwork
@@ -219,11 +270,14 @@ __global__ void k_submask(const uint32_t *__restrict__ keys, const uint32_t *__r
 // there, i.e. when T_<s * T_s < T_min or the run itself stopped (its local
 // transmittance is an upper bound of the true one).  The last warp to finish
 // a (tile, sub-block) combines the runs in order and re-walks, from the true
-// transmittance, the one run in which a ray stops.  Run 0 starts from the
-// true state, so its own stop is final.  As it goes, the merge overwrites
-// each later run's partial with the state before that run (colour, omega, Z,
-// T), from which the backward walks the run.
+// state, the run in which a ray stops (run 0 starts from the true state, so
+// its own stop is final).  The pixels of a sub-block mostly stop in the same
+// run or two, so the re-walks stay in the merge (LiDAR items, whose rays
+// spread further, defer theirs: k_render_lidar).  As it goes, the merge
+// overwrites each later run's partial with the state before that run
+// (colour, omega, Z, T, last entry), from which the backward walks the run.
 constexpr int kCamWarps = 4;       // warps per block of the persistent grid
+
 
 struct CamAcc {
     float T, W, Z, c0, c1, c2;
@@ -232,8 +286,8 @@ struct CamAcc {
 
 // Composite list entries [lo, hi) of a tile (first entry `begin`) that can
 // reach sub-block `sub` into the lane's accumulator; lanes with done = true
-// take part in the warp's staging but keep their state.  Returns whether the
-// lane's ray stopped at T_min.
+// take part in the warp's staging but keep their state; `rays` = the lanes
+// that have a ray.  Returns whether the lane's ray stopped at T_min.
 __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose,
                                          const GRec *__restrict__ rec,
                                          const uint32_t *__restrict__ ids,
@@ -242,14 +296,21 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
                                          uint32_t begin, const float dh[3], const float dl[3],
                                          const float dd[3], float4 (*s_e)[32],
                                          uint32_t *s_pos, uint32_t *s_lanes, CamAcc &a,
-                                         bool done)
+                                         bool done, uint32_t rays)
 {
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
     for (uint32_t base = lo; base < hi; base += 32) {
-        if (__all_sync(0xffffffffu, done)) break;
+        const uint32_t act = __ballot_sync(0xffffffffu, !done);
+        if (act == 0u) break;
         const uint32_t idx = base + lane;
-        const bool ov = idx < hi && ((submask[idx] >> sub) & 1u);
+        bool ov = idx < hi && ((submask[idx] >> sub) & 1u);
+        if (act != rays && ov) {
+            // some rays are done: stage only entries that reach one still
+            // compositing (the box is read before the ballot, which costs a
+            // load latency, so not while every ray is live)
+            ov = (subblock_lanes(rec[ids[idx]].rect, sbx, sby) & act) != 0u;
+        }
         const uint32_t bal = __ballot_sync(0xffffffffu, ov);
         if (bal == 0u) continue;
         __syncwarp();
@@ -259,7 +320,7 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
             cam_entry(rec[ids[idx]], pose.t, dh, dl, ent);
 #pragma unroll
             for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
-            s_lanes[pos] = subblock_lanes(ent[8], sbx, sby);
+            s_lanes[pos] = subblock_lanes(ent[8], sbx, sby) & act;
             s_pos[pos] = idx + 1 - begin;
         }
         __syncwarp();
@@ -286,6 +347,17 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
         }
     }
     return done && !done0;   // the ray stopped at T_min in this walk
+}
+
+// Partial slot layout: (c0, c1, c2, W), (Z, T, last, stopped flag).
+__device__ __forceinline__ void put_state(float4 *pq, const CamAcc &a, bool stopped)
+{
+    pq[0] = make_float4(a.c0, a.c1, a.c2, a.W);
+    pq[1] = make_float4(a.Z, a.T, __uint_as_float(a.last), stopped ? 1.f : 0.f);
+}
+__device__ __forceinline__ CamAcc get_state(float4 u, float4 v)
+{
+    return {v.y, u.w, v.x, u.x, u.y, u.z, __float_as_uint(v.z)};
 }
 
 template <uint32_t kSeg>
@@ -329,6 +401,7 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
         const int64_t pidx = (int64_t)py * P.W + px;
         const float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool no_ray = !(inside && e.w > 0.f);
+        const uint32_t rays = __ballot_sync(0xffffffffu, !no_ray);
         float dd[3];
         cam_ray_offset(s_pose, e, dd);
         const uint2 rg = ranges[tile];
@@ -336,12 +409,10 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
         const uint32_t hi = min(rg.y, lo + kSeg);
         CamAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
         const bool stopped = cam_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, lo, hi, rg.x,
-                                      dh, dl, dd, s_e, s_pos[wib], s_lanes[wib], a, no_ray);
+                                      dh, dl, dd, s_e, s_pos[wib], s_lanes[wib], a, no_ray, rays);
         if (ti.x > 1) {
             // long tile: publish this run, and combine if it is the last one
-            float4 *pp = partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2;
-            pp[0] = make_float4(a.c0, a.c1, a.c2, a.W);
-            pp[1] = make_float4(a.Z, a.T, __uint_as_float(a.last), stopped ? 1.f : 0.f);
+            put_state(partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2, a, stopped);
             __threadfence();
             __syncwarp();
             uint32_t prev = 0;
@@ -353,18 +424,15 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
             }
             __threadfence();
             float4 *pq = partials + ((size_t)ti.y * 256 + sub * 32 + lane) * 2;
-            float4 u = __ldcg(pq), v = __ldcg(pq + 1);
-            a = {v.y, u.w, v.x, u.x, u.y, u.z, __float_as_uint(v.z)};
-            bool fin = no_ray || v.w != 0.f;
+            const float4 u0 = __ldcg(pq), v0 = __ldcg(pq + 1);
+            a = get_state(u0, v0);
+            bool fin = no_ray || v0.w != 0.f;
             for (uint32_t sgi = 1; sgi < ti.x; ++sgi) {
                 if (__all_sync(0xffffffffu, fin)) break;
                 pq += 512;
-                u = __ldcg(pq);
-                v = __ldcg(pq + 1);
-                // the state before segment sgi replaces its partial: the
-                // backward starts each segment from it
-                pq[0] = make_float4(a.c0, a.c1, a.c2, a.W);
-                pq[1] = make_float4(a.Z, a.T, 0.f, 0.f);
+                const float4 u = __ldcg(pq), v = __ldcg(pq + 1);
+                // the state before run sgi replaces its partial
+                put_state(pq, a, false);
                 const bool take = !fin && v.w == 0.f && a.T * v.y >= P.t_min;
                 const bool redo = !fin && !take;
                 if (take) {
@@ -381,7 +449,7 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
                     const uint32_t l0 = rg.x + sgi * kSeg;
                     cam_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, l0,
                              min(rg.y, l0 + kSeg), rg.x, dh, dl, dd, s_e, s_pos[wib],
-                             s_lanes[wib], a, !redo);
+                             s_lanes[wib], a, !redo, rays);
                 }
                 fin = fin || redo;
             }
@@ -484,8 +552,9 @@ struct LidStage {
 
 // Composite entries [lo, hi) of the item's list (first entry `begin`): a
 // window of 32 entries is tested against the item's 32 rays (lidar_lanes),
-// only entries that reach a ray are staged, and each is evaluated for the
-// rays in its mask.  Returns whether the lane's ray stopped at T_min.
+// only entries that reach a ray still compositing are staged, and each is
+// evaluated for the rays in its mask.  Returns whether the lane's ray
+// stopped at T_min.
 __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__restrict__ rec,
                                            const uint32_t *__restrict__ ids,
                                            const float *__restrict__ poses, const LidarItem &it,
@@ -497,13 +566,15 @@ __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__res
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
     for (uint32_t base = lo; base < hi; base += 32) {
-        if (__all_sync(0xffffffffu, done)) break;
+        // only entries that reach a ray still compositing
+        const uint32_t act = __ballot_sync(0xffffffffu, !done);
+        if (act == 0u) break;
         const uint32_t idx = base + lane;
         uint32_t m = 0u, g = 0u;
         if (idx < hi) {
             g = ids[idx];
             const float4 rc = rec[g].rect;
-            m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, L.raz, L.rel);
+            m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, L.raz, L.rel) & act;
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
         if (bal == 0u) continue;
@@ -538,6 +609,16 @@ __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__res
     return done && !done0;
 }
 
+// The merge of a split item re-walks the first kLidarInlineRewalks segments
+// in which some of its rays stop, as the camera merge does; the rays of a
+// LiDAR item span several beams and columns and stop in up to 32 different
+// segments, which one warp would walk one after another (this tail once held
+// a third of the launch), so later ones are recorded as deferred re-walks
+// (item, segment, lanes).  A second launch (kFix = true) walks those in
+// parallel, each from the state before its segment, and writes their rays.
+constexpr int kLidarInlineRewalks = 2;
+
+template <bool kFix>
 __global__ void __launch_bounds__(32 * kLidarWarps)
 k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
                const uint32_t *__restrict__ item_rays, const float4 *__restrict__ ray_e,
@@ -546,7 +627,7 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
                const uint32_t *__restrict__ ids, const uint2 *__restrict__ ranges,
                const uint2 *__restrict__ work, const uint2 *__restrict__ unit_info,
                const uint32_t *__restrict__ counts, uint32_t *__restrict__ counter,
-               uint32_t *__restrict__ arrive, float4 *__restrict__ partials,
+               uint32_t *__restrict__ arrive, float4 *__restrict__ partials, FixList F,
                const RenderDesc *__restrict__ D, float4 *__restrict__ ray_state,
                float4 *__restrict__ ray_feat, uint32_t *__restrict__ n_contrib)
 {
@@ -556,13 +637,24 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const LidStage stg = {s_all[wib], s_lanes[wib], s_pos[wib], s_raz[wib], s_rel[wib]};
     const float *__restrict__ poses = D->poses;
-    const uint32_t n_work = counts[0];
+    const uint32_t n_work = kFix ? *F.n_fix : counts[0];
+    uint32_t fix_next = blockIdx.x * kLidarWarps + wib;
     while (true) {
-        uint32_t wi = 0;
-        if (lane == 0) wi = atomicAdd(counter, 1u);
-        wi = __shfl_sync(0xffffffffu, wi, 0);
-        if (wi >= n_work) break;
-        const uint2 w = work[wi];
+        uint2 w;
+        uint32_t fix_lanes = 0u;
+        if constexpr (kFix) {
+            if (fix_next >= n_work || fix_next >= F.cap) break;
+            const uint4 f = F.fix[fix_next];
+            fix_next += gridDim.x * kLidarWarps;
+            w = make_uint2(f.x, f.y);
+            fix_lanes = f.z;
+        } else {
+            uint32_t wi = 0;
+            if (lane == 0) wi = atomicAdd(counter, 1u);
+            wi = __shfl_sync(0xffffffffu, wi, 0);
+            if (wi >= n_work) break;
+            w = work[wi];
+        }
         const int item_id = (int)w.x;
         const uint32_t seg = w.y;
         const uint2 ui = unit_info[item_id];         // (segments, first partial slot)
@@ -581,56 +673,67 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
         const uint32_t lo = rg.x + seg * kSegLen;
         const uint32_t hi = min(rg.y, lo + kSegLen);
         CamAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
-        const bool stopped = lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, lo, hi, rg.x,
-                                        stg, a, !valid);
-        if (ui.x > 1) {
-            // split item: publish this segment, and combine if it is the last one
-            float4 *pp = partials + ((size_t)(ui.y + seg) * 32 + lane) * 2;
-            pp[0] = make_float4(a.c0, a.c1, a.c2, a.W);
-            pp[1] = make_float4(a.Z, a.T, __uint_as_float(a.last), stopped ? 1.f : 0.f);
-            __threadfence();
-            __syncwarp();
-            uint32_t prev = 0;
-            if (lane == 0) prev = atomicAdd(&arrive[ui.y], 1u);
-            prev = __shfl_sync(0xffffffffu, prev, 0);
-            if (prev != ui.x - 1) {
+        bool write = valid;
+        if constexpr (kFix) {
+            const bool mine = (fix_lanes >> lane) & 1u;
+            const float4 *pq = partials + ((size_t)(ui.y + seg) * 32 + lane) * 2;
+            if (mine) a = get_state(pq[0], pq[1]);
+            lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, lo, hi, rg.x, stg, a, !mine);
+            write = mine;
+        } else {
+            const bool stopped = lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, lo, hi,
+                                            rg.x, stg, a, !valid);
+            if (ui.x > 1) {
+                // split item: publish this segment, and combine if it is the last one
+                put_state(partials + ((size_t)(ui.y + seg) * 32 + lane) * 2, a, stopped);
+                __threadfence();
                 __syncwarp();
-                continue;
-            }
-            __threadfence();
-            float4 *pq = partials + ((size_t)ui.y * 32 + lane) * 2;
-            float4 u = __ldcg(pq), v = __ldcg(pq + 1);
-            a = {v.y, u.w, v.x, u.x, u.y, u.z, __float_as_uint(v.z)};
-            bool fin = !valid || v.w != 0.f;
-            for (uint32_t sgi = 1; sgi < ui.x; ++sgi) {
-                if (__all_sync(0xffffffffu, fin)) break;
-                pq += 64;
-                u = __ldcg(pq);
-                v = __ldcg(pq + 1);
-                // the state before segment sgi replaces its partial (backward)
-                pq[0] = make_float4(a.c0, a.c1, a.c2, a.W);
-                pq[1] = make_float4(a.Z, a.T, 0.f, 0.f);
-                const bool take = !fin && v.w == 0.f && a.T * v.y >= P.t_min;
-                const bool redo = !fin && !take;
-                if (take) {
-                    a.c0 += a.T * u.x;
-                    a.c1 += a.T * u.y;
-                    a.c2 += a.T * u.z;
-                    a.W += a.T * u.w;
-                    a.Z += a.T * v.x;
-                    a.T *= v.y;
-                    const uint32_t l = __float_as_uint(v.z);
-                    a.last = l ? l : a.last;
+                uint32_t prev = 0;
+                if (lane == 0) prev = atomicAdd(&arrive[ui.y], 1u);
+                prev = __shfl_sync(0xffffffffu, prev, 0);
+                if (prev != ui.x - 1) {
+                    __syncwarp();
+                    continue;
                 }
-                if (__any_sync(0xffffffffu, redo)) {
-                    const uint32_t l0 = rg.x + sgi * kSegLen;
-                    lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, l0,
-                               min(rg.y, l0 + kSegLen), rg.x, stg, a, !redo);
+                __threadfence();
+                float4 *pq = partials + ((size_t)ui.y * 32 + lane) * 2;
+                const float4 u0 = __ldcg(pq), v0 = __ldcg(pq + 1);
+                a = get_state(u0, v0);
+                bool fin = !valid || v0.w != 0.f;
+                int n_inline = 0;
+                for (uint32_t sgi = 1; sgi < ui.x; ++sgi) {
+                    if (__all_sync(0xffffffffu, fin)) break;
+                    pq += 64;
+                    const float4 u = __ldcg(pq), v = __ldcg(pq + 1);
+                    // the state before segment sgi replaces its partial
+                    put_state(pq, a, false);
+                    const bool take = !fin && v.w == 0.f && a.T * v.y >= P.t_min;
+                    const bool redo = !fin && !take;
+                    if (take) {
+                        a.c0 += a.T * u.x;
+                        a.c1 += a.T * u.y;
+                        a.c2 += a.T * u.z;
+                        a.W += a.T * u.w;
+                        a.Z += a.T * v.x;
+                        a.T *= v.y;
+                        const uint32_t l = __float_as_uint(v.z);
+                        a.last = l ? l : a.last;
+                    }
+                    const uint32_t rl = __ballot_sync(0xffffffffu, redo);
+                    if (rl && n_inline < kLidarInlineRewalks) {
+                        ++n_inline;
+                        const uint32_t l0 = rg.x + sgi * kSegLen;
+                        lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, l0,
+                                   min(rg.y, l0 + kSegLen), rg.x, stg, a, !redo);
+                    } else if (rl) {
+                        push_fix(F, (uint32_t)item_id, sgi, rl);
+                        write = write && !redo;  // the deferred re-walk writes this ray
+                    }
+                    fin = fin || redo;
                 }
-                fin = fin || redo;
             }
         }
-        if (valid) {
+        if (write) {
             const float drop = 1.f / (1.f + expf(a.c1 - a.c2));
             float *const out_range = D->out[0], *const out_int = D->out[1];
             float *const out_drop = D->out[2], *const out_alpha = D->out[3];
@@ -651,7 +754,7 @@ static int lidar_blocks_per_sm()
     static int cached = 0;
     if (!cached) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_lidar, 32 * kLidarWarps,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_lidar<false>, 32 * kLidarWarps,
                                                           0) != cudaSuccess ||
             nb < 1)
             nb = 4;
@@ -685,13 +788,25 @@ sg_status render_lidar(const Lidar &L, const sg_render_opts &o, Frame &fr, cudaS
     int64_t grid = (int64_t)sms * lidar_blocks_per_sm();
     grid = grid < cap ? grid : cap;
     if (grid < 1) grid = 1;
-    k_render_lidar<<<(unsigned)grid, 32 * kLidarWarps, 0, st>>>(
+    const FixList F = fix_list(fr, ws);
+    k_render_lidar<false><<<(unsigned)grid, 32 * kLidarWarps, 0, st>>>(
         P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, L.d_az, L.d_elev,
         (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, work, unit_info,
         (const uint32_t *)fr.scalars.p + 4, (uint32_t *)fr.scalars.p + 2, arrive,
-        (float4 *)fr.partials.p, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
+        (float4 *)fr.partials.p, F, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
         (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
     SG_LAUNCHED();
+    if (ws.max_slots > 0) {       // some item may be split: the deferred re-walks
+        const int64_t fcap = (ws.max_fixes + kLidarWarps - 1) / kLidarWarps;
+        const int64_t fgrid = grid < fcap ? grid : fcap;
+        k_render_lidar<true><<<(unsigned)fgrid, 32 * kLidarWarps, 0, st>>>(
+            P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, L.d_az, L.d_elev,
+            (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, work, unit_info,
+            (const uint32_t *)fr.scalars.p + 4, (uint32_t *)fr.scalars.p + 2, arrive,
+            (float4 *)fr.partials.p, F, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
+            (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
+        SG_LAUNCHED();
+    }
     return SG_OK;
 }
 

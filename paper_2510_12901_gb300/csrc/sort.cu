@@ -158,12 +158,13 @@ sg_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, uint32_t *d_
 //   1. k_sort_hist: one read of the keys counts the digits of every pass;
 //   2. k_sort_offsets: per pass, the exclusive scan of its 256 counts gives
 //      the first output position of each digit;
-//   3. k_onesweep, per pass: a block takes the next tile of 4096 pairs (an
-//      atomic ticket, so tiles are taken in order), ranks them stably
-//      (warp w owns 512 consecutive pairs, ranks among equal digits from
-//      __match_any_sync), publishes its per-digit counts, and walks back
-//      over earlier tiles' published counts until it meets an inclusive
-//      prefix; then it publishes its own inclusive prefix and scatters.
+//   3. k_onesweep, per pass: a block takes the next tile of kRadixTile pairs
+//      (an atomic ticket, so tiles are taken in order), ranks them stably
+//      (each warp owns kRadixItems x 32 consecutive pairs, ranks among equal
+//      digits from __match_any_sync), publishes its per-digit counts, and
+//      walks back over earlier tiles' published counts, kLbBatch tiles per
+//      round of loads, until it meets an inclusive prefix; then it
+//      publishes its own inclusive prefix and scatters.
 // A tile only waits for tiles taken before it, whose blocks are running;
 // every such wait is bounded, and a wait that runs out sets *err.
 #ifndef SG_RADIX_THREADS
@@ -176,6 +177,14 @@ static_assert(kRadixThreads >= 256 && kRadixItems * kRadixThreads == kRadixTile,
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr uint32_t kLbAgg = 1u << 30, kLbPre = 2u << 30, kLbCount = (1u << 30) - 1u;
 constexpr uint32_t kLbSpins = 1u << 22;
+#ifndef SG_LB_BATCH
+#define SG_LB_BATCH 8
+#endif
+constexpr int kLbBatch = SG_LB_BATCH;   // earlier tiles' words loaded per look-back round
+#ifndef SG_HIST_KEYS
+#define SG_HIST_KEYS 1
+#endif
+constexpr int kHistKeys = SG_HIST_KEYS;
 
 __global__ void __launch_bounds__(kRadixThreads)
 k_sort_hist(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_n, int begin_bit,
@@ -264,16 +273,35 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
         }
         volatile uint32_t *lb = lookback;
         lb[(int64_t)tile * 256 + dg] = (tile == 0 ? kLbPre : kLbAgg) | run;
-        uint32_t excl = 0;
-        for (int64_t t = (int64_t)tile - 1; t >= 0; --t) {
-            uint32_t w = lb[t * 256 + dg], spins = 0;
-            while (!(w & (kLbAgg | kLbPre)) && ++spins <= kLbSpins) w = lb[t * 256 + dg];
-            if (!(w & (kLbAgg | kLbPre))) {   // gave up: flag it, leave the order wrong
+        uint32_t excl = 0, spins = 0;
+        int64_t t = (int64_t)tile - 1;
+        while (t >= 0) {
+            // the words of tiles t, t-1, .. at once (before tile 0: an empty
+            // inclusive prefix); take them in order up to an inclusive prefix
+            // or up to one not yet published, which the next round reloads
+            uint32_t w[kLbBatch];
+#pragma unroll
+            for (int k = 0; k < kLbBatch; ++k)
+                w[k] = t - k >= 0 ? (uint32_t)lb[(t - k) * 256 + dg] : (uint32_t)kLbPre;
+            int took = 0;
+            bool pre = false, wait = false;
+#pragma unroll
+            for (int k = 0; k < kLbBatch; ++k) {
+                if (pre || wait) continue;
+                if (w[k] & (kLbAgg | kLbPre)) {
+                    excl += w[k] & kLbCount;
+                    pre = (w[k] & kLbPre) != 0u;
+                    ++took;
+                } else {
+                    wait = true;
+                }
+            }
+            if (pre) break;
+            t -= took;
+            if (took == 0 && ++spins > kLbSpins) {   // gave up: flag it, leave the order wrong
                 atomicOr(err, 1u);
                 break;
             }
-            excl += w & kLbCount;
-            if (w & kLbPre) break;
         }
         if (tile > 0) lb[(int64_t)tile * 256 + dg] = kLbPre | (excl + run);
         s_pre[dg] = offsets[dg] + excl;
@@ -315,7 +343,9 @@ sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
     int dev = 0, sms = 0;
     SG_CUDA(cudaGetDevice(&dev));
     SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t hist_blocks = tiles < 4 * sms ? tiles : 4 * sms;
+    // about kHistKeys keys per thread, at most two resident blocks per SM
+    const int64_t hist_want = (n_max + kRadixThreads * kHistKeys - 1) / (kRadixThreads * kHistKeys);
+    const int64_t hist_blocks = hist_want < 2 * sms ? hist_want : 2 * sms;
     k_sort_hist<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys[0], d_n, begin_bit, end_bit,
                                                                  hist);
     SG_LAUNCHED();

@@ -198,6 +198,36 @@ sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_co
                                void *stream);
 
 /* ----------------------------------------------------------------------
+ * Several camera views of one scene in one call: a vehicle's camera rig
+ * rendered per frame (the paper's evaluation renders the three front
+ * cameras of every frame, Sec. 4).  Each view is the render sg_render_camera
+ * makes of it, with identical results, on the view's own stream and frame.
+ * The call first starts every view (projection, depth sort, pair count),
+ * then finishes them in order (binning, tile sort, compositing), so that
+ * while the host waits for one view's pair count the other views' kernels
+ * are already queued: views on different streams overlap on the GPU.
+ *
+ * views[i]: camera; row-major 3x4 camera-to-world pose (copied); frame
+ * (distinct for every view); output buffers rgb [H,W,3], alpha [H,W],
+ * depth [H,W] (each may be NULL); stream.  host_outputs = 0: the outputs
+ * are device buffers and the call returns with the work queued, as
+ * sg_render_camera.  host_outputs = 1: the outputs are host buffers
+ * (pinned or pageable); each view's result is copied there on its stream
+ * and the call returns once every view's copy is done.  Errors as for
+ * sg_render_camera, and SG_ERR_INVALID for n_views < 0, a NULL list,
+ * camera or frame, or two views sharing a frame; after an error, views
+ * already started may still run on their streams. */
+typedef struct {
+    sg_camera camera;
+    float c2w[12];
+    sg_frame frame;
+    float *rgb, *alpha, *depth;
+    void *stream;
+} sg_camera_view;
+sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *views,
+                            const sg_render_opts *opts, int host_outputs);
+
+/* ----------------------------------------------------------------------
  * Camera render that allocates nothing.  The paper has no counterpart: this
  * is a deployment variant of sg_render_camera for callers that must not
  * allocate device memory while they run (for example when another

@@ -172,6 +172,11 @@ static sg_status frame_prepare(Frame &fr, int64_t n, int64_t nrays, int64_t ntil
         }
         fr.h_desc = (RenderDesc *)((char *)fr.h_scalars + 256);
     }
+    if (!fr.ev_count && cudaEventCreateWithFlags(&fr.ev_count, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("event creation failed");
+        return SG_ERR_CUDA;
+    }
     fr.n_gauss = n;
     fr.n_rays = nrays;
     fr.n_tiles = ntiles;
@@ -190,14 +195,14 @@ static sg_status upload_desc(Frame &fr, cudaStream_t st)
     return SG_OK;
 }
 
-// Stages shared by both sensors after projection: depth sort, offsets,
-// pair count, binning, tile sort, ranges.  The pair count is read back and
-// sizes the pair buffers, except in capacity mode (fr.k_cap > 0), where the
-// buffers hold k_cap pairs, the count stays on the device (clamped to
-// k_cap, the excess in scalars[3]) and nothing waits for it; the scalars
-// are then copied to h_scalars at the end for the caller to check.
-static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int wrap,
-                              cudaStream_t st)
+// Stages shared by both sensors after projection, in two halves so that
+// several renders on their own streams can each have their pair count on
+// the way before any of them waits for one.
+// sort_and_count: depth sort, offsets and the pair count.  In exact mode the
+// count is copied to h_scalars and ev_count recorded; in capacity mode
+// (fr.k_cap > 0) the count stays on the device, clamped to k_cap (the excess
+// in scalars[3]).
+static sg_status sort_and_count(Frame &fr, int64_t n, cudaStream_t st)
 {
     uint32_t *sc = (uint32_t *)fr.scalars.p;   // [0] valid Gaussians, [1] pairs
     uint32_t *dk[2] = {(uint32_t *)fr.dkeys[0].p, (uint32_t *)fr.dkeys[1].p};
@@ -208,19 +213,32 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     int rb = 0;
     s = radix_sort_pairs(dk, dv, n, sc, 0, 32, fr, st, &rb);
     if (s != SG_OK) return s;
+    fr.depth_buf = rb;
     s = gather_counts(dv[rb], (const uint32_t *)fr.count.p, sc, n, (uint32_t *)fr.cnt_sorted.p, st);
     if (s != SG_OK) return s;
     s = scan_exclusive_u32((const uint32_t *)fr.cnt_sorted.p, (uint32_t *)fr.offsets.p, sc + 1, n,
                            fr, st);
     if (s != SG_OK) return s;
     tmark(fr, 2, st);
+    if (fr.k_cap > 0) return clamp_pairs(sc + 1, fr.k_cap, sc + 3, st);
+    SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 8, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaEventRecord(fr.ev_count, st));
+    return SG_OK;
+}
+
+// bin_and_sort: waits for the pair count (exact mode), which sizes the pair
+// buffers, then binning, tile sort and ranges; in capacity mode nothing
+// waits and the scalars are copied to h_scalars at the end for the caller
+// to check.
+static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int wrap,
+                              cudaStream_t st)
+{
+    uint32_t *sc = (uint32_t *)fr.scalars.p;
     int64_t K = 0;
     if (fr.k_cap > 0) {
         K = fr.k_cap;
-        if ((s = clamp_pairs(sc + 1, K, sc + 3, st)) != SG_OK) return s;
     } else {
-        SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 8, cudaMemcpyDeviceToHost, st));
-        SG_CUDA(cudaStreamSynchronize(st));
+        SG_CUDA(cudaEventSynchronize(fr.ev_count));
         K = fr.h_scalars[1];
         if (K > 0x7fffffffLL) {
             set_error("%lld (tile, Gaussian) pairs exceed 2^31-1", (long long)K);
@@ -228,14 +246,16 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
         }
     }
     fr.n_pairs = K;
+    sg_status s;
     for (int i = 0; i < 2; ++i) {
         if ((s = ensure(fr.pkeys[i], sizeof(uint32_t) * (K > 0 ? K : 1))) != SG_OK) return s;
         if ((s = ensure(fr.pvals[i], sizeof(uint32_t) * (K > 0 ? K : 1))) != SG_OK) return s;
     }
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
-    s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, (const uint32_t *)fr.cnt_sorted.p, sc,
-                  n, (const int4 *)fr.tiles.p, ntx, wrap, K, pk[0], pv[0], st);
+    s = bin_pairs((const uint32_t *)fr.dvals[fr.depth_buf].p, (const uint32_t *)fr.offsets.p,
+                  (const uint32_t *)fr.cnt_sorted.p, sc, n, (const int4 *)fr.tiles.p, ntx, wrap, K,
+                  pk[0], pv[0], st);
     if (s != SG_OK) return s;
     int bits = 1;
     while (((int64_t)1 << bits) < ntiles) ++bits;
@@ -248,6 +268,64 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     if (fr.k_cap > 0)
         SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 16, cudaMemcpyDeviceToHost, st));
     tmark(fr, 3, st);
+    return SG_OK;
+}
+
+static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int wrap,
+                              cudaStream_t st)
+{
+    sg_status s = sort_and_count(fr, n, st);
+    return s != SG_OK ? s : bin_and_sort(fr, n, ntx, ntiles, wrap, st);
+}
+
+// A camera render in two halves (see sort_and_count): camera_begin checks
+// the arguments, projects and starts the pair count; camera_finish bins,
+// sorts and composites.
+static sg_status camera_begin(sg_scene scene, sg_camera cam, const float h_c2w[12],
+                              const sg_render_opts *opts, sg_frame frame, float *d_rgb,
+                              float *d_alpha, float *d_depth, cudaStream_t st)
+{
+    if (!scene || !cam || !frame || !h_c2w) { set_error("NULL handle or pose"); return SG_ERR_INVALID; }
+    if (!opts_ok(opts)) return SG_ERR_INVALID;
+    const Scene &sc = scene->s;
+    if (sc.feature_kind == SG_FEATURES_LIDAR) {
+        set_error("sg_render_camera: scene carries LiDAR features");
+        return SG_ERR_INVALID;
+    }
+    for (int i = 0; i < 12; ++i)
+        if (!isfinite(h_c2w[i])) { set_error("pose is not finite"); return SG_ERR_INVALID; }
+    const Camera &c = cam->c;
+    Frame &fr = frame->f;
+    int64_t nt = (int64_t)c.ntx * c.nty, nr = (int64_t)c.width * c.height;
+    sg_status s = frame_prepare(fr, sc.n, nr, nt);
+    if (s != SG_OK) return s;
+    fr.kind = 0;
+    fr.scene = scene;
+    fr.sensor = cam;
+    fr.opts = *opts;
+    memcpy(fr.c2w, h_c2w, sizeof(fr.c2w));
+    RenderDesc &D = *fr.h_desc;
+    memcpy(D.c2w, h_c2w, sizeof(D.c2w));
+    D.poses = nullptr;
+    D.out[0] = d_rgb;
+    D.out[1] = d_alpha;
+    D.out[2] = d_depth;
+    D.out[3] = nullptr;
+    if (fr.timing) cudaEventRecord(fr.ev[0], st);
+    if ((s = upload_desc(fr, st)) != SG_OK) return s;
+    if ((s = project_camera(sc, c, *opts, fr, st)) != SG_OK) return s;
+    if (fr.timing) cudaEventRecord(fr.ev[1], st);
+    return sort_and_count(fr, sc.n, st);
+}
+
+static sg_status camera_finish(sg_camera cam, sg_frame frame, cudaStream_t st)
+{
+    const Camera &c = cam->c;
+    Frame &fr = frame->f;
+    sg_status s = bin_and_sort(fr, fr.n_gauss, c.ntx, (int64_t)c.ntx * c.nty, 0, st);
+    if (s != SG_OK) return s;
+    if ((s = render_camera(c, fr.opts, fr, st)) != SG_OK) return s;
+    if (fr.timing) cudaEventRecord(fr.ev[4], st);
     return SG_OK;
 }
 
@@ -448,6 +526,7 @@ void sg_frame_destroy(sg_frame frame)
     if (f.h_scalars) cudaFreeHost(f.h_scalars);
     for (auto &e : f.ev)
         if (e) cudaEventDestroy(e);
+    if (f.ev_count) cudaEventDestroy(f.ev_count);
     delete frame;
 }
 
@@ -512,40 +591,61 @@ sg_status sg_render_camera(sg_scene scene, sg_camera cam, const float h_c2w[12],
                            const sg_render_opts *opts, sg_frame frame, float *d_rgb,
                            float *d_alpha, float *d_depth, void *stream)
 {
-    if (!scene || !cam || !frame || !h_c2w) { set_error("NULL handle or pose"); return SG_ERR_INVALID; }
-    if (!opts_ok(opts)) return SG_ERR_INVALID;
-    const Scene &sc = scene->s;
-    if (sc.feature_kind == SG_FEATURES_LIDAR) {
-        set_error("sg_render_camera: scene carries LiDAR features");
+    cudaStream_t st = (cudaStream_t)stream;
+    sg_status s = camera_begin(scene, cam, h_c2w, opts, frame, d_rgb, d_alpha, d_depth, st);
+    return s != SG_OK ? s : camera_finish(cam, frame, st);
+}
+
+sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *views,
+                            const sg_render_opts *opts, int host_outputs)
+{
+    if (n_views < 0 || (n_views > 0 && !views)) {
+        set_error("sg_render_cameras: bad view list");
         return SG_ERR_INVALID;
     }
-    for (int i = 0; i < 12; ++i)
-        if (!isfinite(h_c2w[i])) { set_error("pose is not finite"); return SG_ERR_INVALID; }
-    const Camera &c = cam->c;
-    Frame &fr = frame->f;
-    cudaStream_t st = (cudaStream_t)stream;
-    int64_t nt = (int64_t)c.ntx * c.nty, nr = (int64_t)c.width * c.height;
-    sg_status s = frame_prepare(fr, sc.n, nr, nt);
-    if (s != SG_OK) return s;
-    fr.kind = 0;
-    fr.scene = scene;
-    fr.sensor = cam;
-    fr.opts = *opts;
-    memcpy(fr.c2w, h_c2w, sizeof(fr.c2w));
-    RenderDesc &D = *fr.h_desc;
-    memcpy(D.c2w, h_c2w, sizeof(D.c2w));
-    D.poses = nullptr;
-    D.out[0] = d_rgb;
-    D.out[1] = d_alpha;
-    D.out[2] = d_depth;
-    D.out[3] = nullptr;
-    if (fr.timing) cudaEventRecord(fr.ev[0], st);
-    if ((s = upload_desc(fr, st)) != SG_OK) return s;
-    if ((s = project_camera(sc, c, *opts, fr, st)) != SG_OK) return s;
-    if (fr.timing) cudaEventRecord(fr.ev[1], st);
-    if ((s = sort_and_bin(fr, sc.n, c.ntx, nt, 0, st)) != SG_OK) return s;
-    if ((s = render_camera(c, *opts, fr, st)) != SG_OK) return s;
-    if (fr.timing) cudaEventRecord(fr.ev[4], st);
+    for (int i = 0; i < n_views; ++i) {
+        if (!views[i].camera || !views[i].frame) {
+            set_error("view %d: NULL camera or frame", i);
+            return SG_ERR_INVALID;
+        }
+        for (int j = 0; j < i; ++j)
+            if (views[j].frame == views[i].frame) {
+                set_error("views %d and %d share a frame", j, i);
+                return SG_ERR_INVALID;
+            }
+    }
+    sg_status s;
+    for (int i = 0; i < n_views; ++i) {
+        const sg_camera_view &v = views[i];
+        float *out[3] = {v.rgb, v.alpha, v.depth};
+        if (host_outputs) {
+            const int64_t np = (int64_t)v.camera->c.width * v.camera->c.height;
+            for (int k = 0; k < 3; ++k) {
+                if (!out[k]) continue;
+                const size_t by = sizeof(float) * (size_t)np * (k == 0 ? 3 : 1);
+                if ((s = ensure(v.frame->f.host_stage[k], by)) != SG_OK) return s;
+                out[k] = (float *)v.frame->f.host_stage[k].p;
+            }
+        }
+        s = camera_begin(scene, v.camera, v.c2w, opts, v.frame, out[0], out[1], out[2],
+                         (cudaStream_t)v.stream);
+        if (s != SG_OK) return s;
+    }
+    for (int i = 0; i < n_views; ++i) {
+        const sg_camera_view &v = views[i];
+        cudaStream_t st = (cudaStream_t)v.stream;
+        if ((s = camera_finish(v.camera, v.frame, st)) != SG_OK) return s;
+        if (!host_outputs) continue;
+        const int64_t np = (int64_t)v.camera->c.width * v.camera->c.height;
+        float *h[3] = {v.rgb, v.alpha, v.depth};
+        for (int k = 0; k < 3; ++k)
+            if (h[k])
+                SG_CUDA(cudaMemcpyAsync(h[k], v.frame->f.host_stage[k].p,
+                                        sizeof(float) * (size_t)np * (k == 0 ? 3 : 1),
+                                        cudaMemcpyDeviceToHost, st));
+    }
+    if (host_outputs)
+        for (int i = 0; i < n_views; ++i) SG_CUDA(cudaStreamSynchronize((cudaStream_t)views[i].stream));
     return SG_OK;
 }
 
@@ -592,9 +692,9 @@ sg_status sg_render_lidar(sg_scene scene, sg_lidar lidar, const float *d_col_c2w
     return SG_OK;
 }
 
-// Host-output variants: render into library-owned device buffers, then copy.
-static sg_status host_copy(Buf &b, size_t bytes) { return ensure(b, bytes); }
-
+// Host-output variants: render into library-owned device buffers, then copy
+// (cameras: the frame's own staging buffers, through sg_render_cameras;
+// LiDAR: per-thread buffers).
 static thread_local Buf g_host_out[4];
 static thread_local Buf g_host_poses;
 
@@ -602,23 +702,16 @@ sg_status sg_render_camera_host(sg_scene scene, sg_camera cam, const float h_c2w
                                 const sg_render_opts *opts, sg_frame frame, float *h_rgb,
                                 float *h_alpha, float *h_depth, void *stream)
 {
-    if (!cam) { set_error("camera is NULL"); return SG_ERR_INVALID; }
-    int64_t np = (int64_t)cam->c.width * cam->c.height;
-    sg_status s;
-    if ((s = host_copy(g_host_out[0], sizeof(float) * 3 * np)) != SG_OK) return s;
-    if ((s = host_copy(g_host_out[1], sizeof(float) * np)) != SG_OK) return s;
-    if ((s = host_copy(g_host_out[2], sizeof(float) * np)) != SG_OK) return s;
-    float *d_rgb = (float *)g_host_out[0].p, *d_a = (float *)g_host_out[1].p,
-          *d_d = (float *)g_host_out[2].p;
-    s = sg_render_camera(scene, cam, h_c2w, opts, frame, h_rgb ? d_rgb : nullptr,
-                         h_alpha ? d_a : nullptr, h_depth ? d_d : nullptr, stream);
-    if (s != SG_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (h_rgb) SG_CUDA(cudaMemcpyAsync(h_rgb, d_rgb, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, st));
-    if (h_alpha) SG_CUDA(cudaMemcpyAsync(h_alpha, d_a, sizeof(float) * np, cudaMemcpyDeviceToHost, st));
-    if (h_depth) SG_CUDA(cudaMemcpyAsync(h_depth, d_d, sizeof(float) * np, cudaMemcpyDeviceToHost, st));
-    SG_CUDA(cudaStreamSynchronize(st));
-    return SG_OK;
+    if (!h_c2w) { set_error("pose is NULL"); return SG_ERR_INVALID; }
+    sg_camera_view v;
+    v.camera = cam;
+    memcpy(v.c2w, h_c2w, sizeof(v.c2w));
+    v.frame = frame;
+    v.rgb = h_rgb;
+    v.alpha = h_alpha;
+    v.depth = h_depth;
+    v.stream = stream;
+    return sg_render_cameras(scene, 1, &v, opts, 1);
 }
 
 sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_col_c2w,

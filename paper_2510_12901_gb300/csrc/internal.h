@@ -150,6 +150,7 @@ struct Frame {
     uint32_t seg_len = kSegLen;     // camera list segment length
     int64_t n_pairs = 0, n_tiles = 0, n_rays = 0, n_gauss = 0;
     int pair_buf = 0;  // which of pkeys/pvals holds the sorted result
+    int depth_buf = 0; // which of dkeys/dvals holds the depth-sorted Gaussians
     int kind = -1;     // 0 camera, 1 lidar
     const void *scene = nullptr;
     const void *sensor = nullptr;
@@ -159,6 +160,8 @@ struct Frame {
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     float ms[4] = {0, 0, 0, 0};
+    cudaEvent_t ev_count = nullptr;  // exact mode: the pair count has reached h_scalars
+    Buf host_stage[3];               // device results of a render with host outputs
 };
 
 // Grow b to at least `bytes` (with head-room); growing frees the old buffer.
@@ -275,7 +278,7 @@ template <class Fn> inline void for_each_buf(Frame &f, Fn fn)
                    &f.offsets, &f.flags, &f.scan_tmp, &f.hist, &f.pkeys[0], &f.pkeys[1],
                    &f.pvals[0], &f.pvals[1], &f.ranges, &f.order, &f.submask, &f.camwork,
                    &f.partials, &f.ray_state, &f.n_contrib, &f.ray_feat, &f.gacc, &f.scalars,
-                   &f.desc};
+                   &f.desc, &f.host_stage[0], &f.host_stage[1], &f.host_stage[2]};
     for (Buf *b : bufs) fn(*b);
 }
 }  // namespace sg

@@ -113,10 +113,18 @@ __device__ __forceinline__ void sh_colour(const float *__restrict__ planes, int6
         Y[14] = 1.4453057213202769f * z * (xx - yy);
         Y[15] = -0.59004358992664352f * x * (xx - 3.f * yy);
     }
+    // unrolled over the 16 coefficients (predicated by the degree), so that a
+    // channel's loads are all in flight at once rather than one per FMA
     const int nc = (deg + 1) * (deg + 1);
+#pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
+        float f[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            f[k] = k < nc ? planes[(Scene::kFeat + 3 * k + ch) * pitch + g] : 0.f;
         float acc = 0.f;
-        for (int k = 0; k < nc; ++k) acc += Y[k] * planes[(Scene::kFeat + 3 * k + ch) * pitch + g];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc += k < nc ? Y[k] * f[k] : 0.f;
         c[ch] = fmaxf(acc + 0.5f, 0.f);
     }
 }
@@ -153,7 +161,10 @@ __device__ __forceinline__ bool cam_point(const CamParams &C, const float *c2w, 
     return true;
 }
 
-__global__ void __launch_bounds__(256, 3)
+#ifndef SG_PROJ_MINB
+#define SG_PROJ_MINB 3
+#endif
+__global__ void __launch_bounds__(256, SG_PROJ_MINB)
 k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int feature_kind,
                  int sh_degree, CamParams C, const RenderDesc *__restrict__ D, UTParams U,
                  GRec *__restrict__ rec,

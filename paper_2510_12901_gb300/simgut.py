@@ -51,6 +51,12 @@ class sg_grads(C.Structure):
                 ("d_g_features", C.c_void_p)]
 
 
+class sg_camera_view(C.Structure):
+    _fields_ = [("camera", C.c_void_p), ("c2w", C.c_float * 12), ("frame", C.c_void_p),
+                ("rgb", C.c_void_p), ("alpha", C.c_void_p), ("depth", C.c_void_p),
+                ("stream", C.c_void_p)]
+
+
 class sg_server_config(C.Structure):
     _fields_ = [("n_slots", C.c_int), ("memory_budget", C.c_size_t),
                 ("queue_capacity", C.c_int), ("use_graphs", C.c_int)]
@@ -99,6 +105,8 @@ _SIGNATURES = {
                                    _P, _P, _P, _P]),
     "sg_render_lidar": (C.c_int, [_H, _H, _P, C.POINTER(sg_render_opts), _H, _P, _P, _P, _P,
                                   _P]),
+    "sg_render_cameras": (C.c_int, [_H, C.c_int, C.POINTER(sg_camera_view),
+                                    C.POINTER(sg_render_opts), C.c_int]),
     "sg_render_camera_host": (C.c_int, [_H, _H, C.POINTER(C.c_float),
                                         C.POINTER(sg_render_opts), _H, _P, _P, _P, _P]),
     "sg_render_lidar_host": (C.c_int, [_H, _H, _P, C.POINTER(sg_render_opts), _H, _P, _P, _P,
@@ -247,6 +255,24 @@ def sg_render_lidar(scene, lid, d_col_c2w, opts, frame, d_range, d_int, d_drop, 
                     stream=0):
     _check(load().sg_render_lidar(scene, lid, _P(d_col_c2w), C.byref(opts), frame,
                                   _P(d_range), _P(d_int), _P(d_drop), _P(d_alpha), _P(stream)))
+
+
+def sg_camera_views(views):
+    """An array of sg_camera_view from (camera, c2w, frame, rgb, alpha, depth,
+    stream) tuples (handles and raw pointers; None or 0 for no output)."""
+    arr = (sg_camera_view * len(views))()
+    for v, (cam, c2w, frame, rgb, alpha, depth, stream) in zip(arr, views):
+        v.camera = cam
+        v.c2w[:] = list(_pose12(c2w))
+        v.frame = frame
+        v.rgb, v.alpha, v.depth = rgb or None, alpha or None, depth or None
+        v.stream = stream or None
+    return arr
+
+
+def sg_render_cameras(scene, views, opts, host_outputs=0):
+    """views: the array from sg_camera_views."""
+    _check(load().sg_render_cameras(scene, len(views), views, C.byref(opts), int(host_outputs)))
 
 
 def sg_render_camera_host(scene, cam, c2w, opts, frame, h_rgb, h_alpha, h_depth, stream=0):

@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -75,3 +76,24 @@ def test_invalid_arguments_are_rejected_before_any_cuda_work(sg):
     bad = sg.sg_default_opts(alpha_min=0.0)
     assert lib.sg_render_lidar(None, None, None, C.byref(bad), None, None, None, None, None,
                                None) == -1
+
+
+def test_camera_view_lists_are_checked_before_any_cuda_work(sg):
+    lib = sg.load()
+    o = sg.sg_default_opts()
+    assert lib.sg_render_cameras(None, -1, None, C.byref(o), 0) == -1
+    assert lib.sg_render_cameras(None, 2, None, C.byref(o), 0) == -1
+    fr = sg.sg_frame_create()
+    v = sg.sg_camera_views([(None, np.eye(3, 4), fr, 0, 0, 0, 0)])
+    assert lib.sg_render_cameras(None, 1, v, C.byref(o), 0) == -1     # NULL camera
+    assert "NULL camera" in sg.sg_last_error()
+    sg.sg_frame_destroy(fr)
+    assert lib.sg_render_cameras(None, 0, None, C.byref(o), 0) == 0   # nothing to render
+
+
+def test_camera_view_struct_layout(sg):
+    # the C struct: handle, float[12], handle, three pointers, stream
+    f = sg.sg_camera_view
+    assert C.sizeof(f) == 96
+    assert [getattr(f, n).offset for n in ("camera", "c2w", "frame", "rgb", "alpha", "depth", "stream")] \
+        == [0, 8, 56, 64, 72, 80, 88]

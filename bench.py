@@ -251,7 +251,9 @@ def run_ours(args):
     per_view = st.reshape(-1, len(cams), 4).mean(axis=0)
     stages = {"project": per_view[:, 0].tolist(), "depth_sort_offsets": per_view[:, 1].tolist(),
               "bin_tile_sort_ranges": per_view[:, 2].tolist(), "render": per_view[:, 3].tolist(),
-              "views": ["fisheye", "pinhole"]}
+              "views": ["fisheye", "pinhole"],
+              "note": "events on each view's stream; the views overlap, so a view's stage "
+                      "may include time the GPU spent on the other view"}
 
     # end-to-end through the C-ABI with host (pinned) output buffers
     host = []

@@ -162,7 +162,7 @@ __device__ __forceinline__ bool cam_point(const CamParams &C, const float *c2w, 
 }
 
 #ifndef SG_PROJ_MINB
-#define SG_PROJ_MINB 3
+#define SG_PROJ_MINB 4
 #endif
 __global__ void __launch_bounds__(256, SG_PROJ_MINB)
 k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int feature_kind,
@@ -306,15 +306,27 @@ __device__ __forceinline__ int col_of_az(const LidParams &L, float az)
 }
 
 // Column whose pose sees the point: start at mid-sweep, then take the
-// column of the point's azimuth `pose_iters` times.
-__device__ __forceinline__ int lidar_col(const LidParams &L, const float x[3], float xs[3])
+// column of the point's azimuth `pose_iters` times; xs = the point in that
+// column's sensor frame and *az_deg its azimuth there.  The point is
+// transformed again only when the column changes, and the last azimuth is
+// reused when the last step kept the column (the same values as
+// transforming and measuring anew).
+__device__ __forceinline__ int lidar_col(const LidParams &L, const float x[3], float xs[3],
+                                         float *az_deg)
 {
     int col = L.n_cols / 2;
-    for (int it = 0; it < L.pose_iters; ++it) {
-        to_sensor(L.poses + 12 * col, x, xs);
-        col = col_of_az(L, atan2f(xs[1], xs[0]) * 57.295779513082321f);
-    }
     to_sensor(L.poses + 12 * col, x, xs);
+    bool fresh = false;          // *az_deg belongs to the current xs
+    for (int it = 0; it < L.pose_iters; ++it) {
+        *az_deg = atan2f(xs[1], xs[0]) * 57.295779513082321f;
+        const int c2 = col_of_az(L, *az_deg);
+        fresh = c2 == col;
+        if (!fresh) {
+            col = c2;
+            to_sensor(L.poses + 12 * col, x, xs);
+        }
+    }
+    if (!fresh) *az_deg = atan2f(xs[1], xs[0]) * 57.295779513082321f;
     return col;
 }
 
@@ -364,9 +376,10 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidP
     LidParams L = Lp;
     L.poses = D->poses;
     Activated a = activate(planes, pitch, g);
-    float xs[3];
-    lidar_col(L, a.mu, xs);
-    depth_out[g] = sqrtf(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
+    float xs0[3], az0;               // chi_0 = mu, also the depth key
+    lidar_col(L, a.mu, xs0, &az0);
+    const float r0 = sqrtf(xs0[0] * xs0[0] + xs0[1] * xs0[1] + xs0[2] * xs0[2]);
+    depth_out[g] = r0;
     uint32_t count = 0;
     float4 rect = make_float4(0.f, 0.f, 0.f, 0.f);
     int4 tl = make_int4(0, -1, 0, -1);
@@ -375,21 +388,19 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidP
     if (a.sigma >= U.alpha_min) {
         float az[7], el[7];
         bool ok = true;
+        ok = r0 > U.near_dist;
+        az[0] = az0;
+        el[0] = asinf(xs0[2] / r0) * 57.295779513082321f;
 #pragma unroll
-        for (int p = 0; p < 7; ++p) {
-            float x[3];
-            if (p == 0) {
-                x[0] = a.mu[0]; x[1] = a.mu[1]; x[2] = a.mu[2];
-            } else {
-                int i = (p - 1) >> 1;
-                float sg = ((p - 1) & 1) ? -1.f : 1.f;
+        for (int p = 1; p < 7; ++p) {
+            const int i = (p - 1) >> 1;
+            const float sg = ((p - 1) & 1) ? -1.f : 1.f;
+            float x[3], xs[3];
 #pragma unroll
-                for (int r = 0; r < 3; ++r) x[r] = a.mu[r] + sg * U.lam_gamma * a.s[i] * a.R[3 * r + i];
-            }
-            lidar_col(L, x, xs);
-            float r = sqrtf(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
+            for (int r = 0; r < 3; ++r) x[r] = a.mu[r] + sg * U.lam_gamma * a.s[i] * a.R[3 * r + i];
+            lidar_col(L, x, xs, &az[p]);
+            const float r = sqrtf(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
             ok = ok && (r > U.near_dist);
-            az[p] = atan2f(xs[1], xs[0]) * 57.295779513082321f;
             el[p] = asinf(xs[2] / r) * 57.295779513082321f;
         }
         if (ok) {

@@ -820,9 +820,13 @@ static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3],
     inv_cov(R, s, G->A);
     G->sigma = RL(sc->opacity[g]);
     G->clampc[0] = G->clampc[1] = G->clampc[2] = 0;
-    if (sc->feature_kind == OR_FEAT_SH) {
+    if (sc->feature_kind == OR_FEAT_SH || sc->feature_kind == OR_FEAT_LIDAR_SH) {
         /* READING: SH evaluated once per Gaussian at the direction from the
-         * camera centre to its mean (Eq. 1 writes SH_i(d)). */
+         * camera centre to its mean (Eq. 1 writes SH_i(d)).  LiDAR (Sec. 3.2
+         * writes SH^l_i(d) in zeta): the same, from the sensor origin of the
+         * column pose that sees the mean; the channels are intensity and
+         * logits, so they get neither the colour offset nor the clamp. */
+        const int lidar = sc->feature_kind == OR_FEAT_LIDAR_SH;
         real v[3] = {G->mu[0] - ocam[0], G->mu[1] - ocam[1], G->mu[2] - ocam[2]};
         real nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         for (int k = 0; k < 3; ++k) G->dir[k] = v[k] / nv;
@@ -834,8 +838,10 @@ static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3],
         for (int ch = 0; ch < 3; ++ch) {
             real acc = 0;
             for (int k = 0; k < nc; ++k) acc += Y[k] * RL(f[3 * k + ch]);
-            acc += RL(0.5);
-            if (acc < RL(0)) { acc = 0; G->clampc[ch] = 1; }
+            if (!lidar) {
+                acc += RL(0.5);
+                if (acc < RL(0)) { acc = 0; G->clampc[ch] = 1; }
+            }
             G->feat[ch] = acc;
         }
     } else {
@@ -1010,8 +1016,15 @@ static uint32_t *global_order(int64_t n, const or_proj *P, int64_t *m_out)
 typedef int (*ray_fn)(const void *ctx, int64_t r, real o[3], real d[3], real *rx,
                       real *ry, uint32_t *tile);
 
+/* ocam: the SH origin, one for all Gaussians, or per Gaussian ([n,3]) when
+ * ocam_per_gauss is set. */
+static const real *origin_of(const real *ocam, int per_gauss, int64_t g)
+{
+    return per_gauss ? ocam + 3 * g : ocam;
+}
+
 static int render_common(const or_scene *sc, const or_opts *o, const or_proj *P,
-                         const real ocam[3], int ntx, int nty, int wrap,
+                         const real *ocam, int ocam_per_gauss, int ntx, int nty, int wrap,
                          int bruteforce, const int64_t *rays, int64_t n_rays,
                          int64_t n_total, ray_fn rf, const void *rctx, or_ray *out,
                          /* backward (optional) */
@@ -1021,7 +1034,8 @@ static int render_common(const or_scene *sc, const or_opts *o, const or_proj *P,
 {
     int64_t nr = n_rays < 0 ? n_total : n_rays;
     gauss_rt *GR = malloc(sizeof(gauss_rt) * (size_t)(sc->n > 0 ? sc->n : 1));
-    for (int64_t g = 0; g < sc->n; ++g) gauss_prepare(sc, g, ocam, &GR[g]);
+    for (int64_t g = 0; g < sc->n; ++g)
+        gauss_prepare(sc, g, origin_of(ocam, ocam_per_gauss, g), &GR[g]);
     int64_t nt = (int64_t)ntx * nty;
     uint32_t *ids = NULL, *ranges = NULL;
     or_pair *pr = NULL;
@@ -1099,7 +1113,7 @@ int or_render_camera(const or_scene *sc, const or_camera *cam, const or_opts *o,
     or_project_camera(sc, cam, &S, o, P);
     real ocam[3] = {RL(cam->c2w[3]), RL(cam->c2w[7]), RL(cam->c2w[11])};
     cam_rctx rc = {cam, S.theta_max, o->tile, S.n_tiles_x};
-    render_common(sc, o, P, ocam, S.n_tiles_x, S.n_tiles_y, 0, bruteforce, rays,
+    render_common(sc, o, P, ocam, 0, S.n_tiles_x, S.n_tiles_y, 0, bruteforce, rays,
                   n_rays, (int64_t)cam->width * cam->height, cam_ray_fn, &rc, out,
                   NULL, NULL);
     free(P);
@@ -1131,6 +1145,20 @@ static void lidar_ray_tiles(const or_lidar *L, const or_sensor_setup *S, int *bt
                                 (RL(S->n_theta) / RL(360))), S->n_theta);
 }
 
+/* Per-Gaussian SH origins of a LiDAR scene: the sensor origin of the column
+ * pose the projection chose for the mean (only LIDAR_SH features use them). */
+static real *lidar_sh_origins(const or_scene *sc, const or_lidar *L, const or_proj *P)
+{
+    real *o = calloc((size_t)(sc->n > 0 ? sc->n : 1) * 3, sizeof(real));
+    for (int64_t g = 0; g < sc->n; ++g) {
+        const float *T = L->col_c2w + 12 * P[g].pose_col;
+        o[3 * g] = RL(T[3]);
+        o[3 * g + 1] = RL(T[7]);
+        o[3 * g + 2] = RL(T[11]);
+    }
+    return o;
+}
+
 int or_render_lidar(const or_scene *sc, const or_lidar *L, const or_opts *o,
                     int bruteforce, const int64_t *rays, int64_t n_rays, or_ray *out)
 {
@@ -1141,10 +1169,11 @@ int or_render_lidar(const or_scene *sc, const or_lidar *L, const or_opts *o,
     int *bt = malloc(sizeof(int) * L->n_beams), *ct = malloc(sizeof(int) * L->n_cols);
     lidar_ray_tiles(L, &S, bt, ct);
     lid_rctx rc = {L, &S, bt, ct};
-    real ocam[3] = {0, 0, 0};
-    render_common(sc, o, P, ocam, S.n_theta, L->n_elev_tiles, 1, bruteforce, rays,
+    real *ocam = lidar_sh_origins(sc, L, P);
+    render_common(sc, o, P, ocam, 1, S.n_theta, L->n_elev_tiles, 1, bruteforce, rays,
                   n_rays, (int64_t)L->n_beams * L->n_cols, lid_ray_fn, &rc, out, NULL,
                   NULL);
+    free(ocam);
     free(bt);
     free(ct);
     free(P);
@@ -1246,10 +1275,10 @@ static void bw_ray(void *vctx, int64_t r, const or_ray *ray, const contrib *rec,
 
 /* Map gradients w.r.t. (A, mu, sigma, feature) to the raw parameters. */
 static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
-                      const real ocam[3], real *gm, real *gls, real *gq, real *gop,
-                      real *gf)
+                      real *gm, real *gls, real *gq, real *gop, real *gf)
 {
-    int F = sc->feature_kind == OR_FEAT_SH ? 3 * (sc->sh_degree + 1) * (sc->sh_degree + 1) : 3;
+    const int sh = sc->feature_kind == OR_FEAT_SH || sc->feature_kind == OR_FEAT_LIDAR_SH;
+    int F = sh ? 3 * (sc->sh_degree + 1) * (sc->sh_degree + 1) : 3;
     for (int64_t g = 0; g < sc->n; ++g) {
         const gauss_rt *G = &GR[g];
         real q[4], qn, R[9], s[3];
@@ -1290,7 +1319,7 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
         gop[g] += B->gsig[g];
         for (int k = 0; k < 3; ++k) gm[3 * g + k] += B->gmu[3 * g + k];
         const real *gc = B->gfeat + 3 * g;
-        if (sc->feature_kind == OR_FEAT_SH) {
+        if (sh) {
             int nc = (sc->sh_degree + 1) * (sc->sh_degree + 1);
             real Y[16], dY[16][3];
             or_sh_basis(G->dir, Y);
@@ -1311,11 +1340,10 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
             for (int ch = 0; ch < 3; ++ch) gf[(size_t)g * F + ch] += gc[ch];
         }
     }
-    (void)ocam;
 }
 
 static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *P,
-                           const real ocam[3], int ntx, int nty, int wrap,
+                           const real *ocam, int ocam_per_gauss, int ntx, int nty, int wrap,
                            int64_t n_total, const int64_t *rays, int64_t n_rays, ray_fn rf,
                            const void *rctx, int lidar,
                            const float *ga, const float *gb, const float *gc,
@@ -1323,7 +1351,8 @@ static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *
                            real *gop, real *gf)
 {
     gauss_rt *GR = malloc(sizeof(gauss_rt) * (size_t)(sc->n > 0 ? sc->n : 1));
-    for (int64_t g = 0; g < sc->n; ++g) gauss_prepare(sc, g, ocam, &GR[g]);
+    for (int64_t g = 0; g < sc->n; ++g)
+        gauss_prepare(sc, g, origin_of(ocam, ocam_per_gauss, g), &GR[g]);
     bw_ctx B;
     memset(&B, 0, sizeof(B));
     B.sc = sc; B.GR = GR; B.lidar = lidar;
@@ -1334,9 +1363,9 @@ static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *
     B.gfeat = calloc((size_t)sc->n * 3 + 1, sizeof(real));
     int64_t nr = n_rays < 0 ? n_total : n_rays;
     or_ray *out = malloc(sizeof(or_ray) * (size_t)(nr > 0 ? nr : 1));
-    render_common(sc, o, P, ocam, ntx, nty, wrap, 0, rays, n_rays, n_total, rf, rctx,
-                  out, bw_ray, &B);
-    bw_finish(sc, GR, &B, ocam, gm, gls, gq, gop, gf);
+    render_common(sc, o, P, ocam, ocam_per_gauss, ntx, nty, wrap, 0, rays, n_rays, n_total,
+                  rf, rctx, out, bw_ray, &B);
+    bw_finish(sc, GR, &B, gm, gls, gq, gop, gf);
     free(out);
     free(B.gA); free(B.gmu); free(B.gsig); free(B.gfeat);
     free(GR);
@@ -1354,7 +1383,7 @@ int or_backward_camera(const or_scene *sc, const or_camera *cam, const or_opts *
     or_project_camera(sc, cam, &S, o, P);
     real ocam[3] = {RL(cam->c2w[3]), RL(cam->c2w[7]), RL(cam->c2w[11])};
     cam_rctx rc = {cam, S.theta_max, o->tile, S.n_tiles_x};
-    backward_common(sc, o, P, ocam, S.n_tiles_x, S.n_tiles_y, 0,
+    backward_common(sc, o, P, ocam, 0, S.n_tiles_x, S.n_tiles_y, 0,
                     (int64_t)cam->width * cam->height, rays, n_rays, cam_ray_fn, &rc, 0, g_rgb,
                     g_alpha, g_depth, NULL, gm, gls, gq, gop, gf);
     free(P);
@@ -1375,11 +1404,12 @@ int or_backward_lidar(const or_scene *sc, const or_lidar *L, const or_opts *o,
     int *bt = malloc(sizeof(int) * L->n_beams), *ct = malloc(sizeof(int) * L->n_cols);
     lidar_ray_tiles(L, &S, bt, ct);
     lid_rctx rc = {L, &S, bt, ct};
-    real ocam[3] = {0, 0, 0};
-    backward_common(sc, o, P, ocam, S.n_theta, L->n_elev_tiles, 1,
+    real *ocam = lidar_sh_origins(sc, L, P);
+    backward_common(sc, o, P, ocam, 1, S.n_theta, L->n_elev_tiles, 1,
                     (int64_t)L->n_beams * L->n_cols, rays, n_rays, lid_ray_fn, &rc, 1, g_range,
                     g_int,
                     g_drop, g_alpha, gm, gls, gq, gop, gf);
+    free(ocam);
     free(bt);
     free(ct);
     free(P);

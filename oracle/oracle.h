@@ -25,7 +25,13 @@ typedef float real;
 typedef double real;
 #endif
 
-enum { OR_FEAT_RGB = 0, OR_FEAT_SH = 1, OR_FEAT_LIDAR = 2 };
+/* Feature kinds: RGB (3 floats, camera), SH (3 (d+1)^2 floats: camera
+ * colour, offset 0.5 and clamped at 0 as in 3DGS), LIDAR (3 raw floats:
+ * intensity, beta_hit, beta_drop), LIDAR_SH (3 (d+1)^2 floats: the SH^l
+ * coefficients of those three channels, Sec. 3.1; zeta = sum_k Y_k(dir)
+ * c_k with neither offset nor clamp, dir from the sensor origin of the
+ * column pose that sees the mean to the mean). */
+enum { OR_FEAT_RGB = 0, OR_FEAT_SH = 1, OR_FEAT_LIDAR = 2, OR_FEAT_LIDAR_SH = 3 };
 enum { OR_PINHOLE = 0, OR_FISHEYE = 1 };
 
 typedef struct {

@@ -32,6 +32,7 @@ import numpy as np
 FEATURES_RGB = 0      # 3 floats per Gaussian, used directly as colour
 FEATURES_SH = 1       # 3*(d+1)^2 floats per Gaussian, [n, (d+1)^2, 3]
 FEATURES_LIDAR = 2    # 3 floats per Gaussian: intensity, beta_hit, beta_drop
+FEATURES_LIDAR_SH = 3  # 3*(d+1)^2 floats: SH coefficients of those channels, [n, (d+1)^2, 3]
 
 CAMERA_PINHOLE = 0
 CAMERA_FISHEYE = 1
@@ -241,15 +242,24 @@ def street_scene(n: int, seed: int = 0, kind: str = "camera",
         feats = rng.normal(0.0, 0.3, size=(n, nc * 3))
         scene = Scene(means, log_scales, quats, opacity, feats,
                       FEATURES_SH, sh_degree)
-    elif kind == "lidar":
+    elif kind in ("lidar", "lidar_sh"):
         hi = rng.uniform(size=n) < 0.7
         opacity = np.where(hi, _sigmoid(rng.normal(4.0, 1.0, n)),
                            _sigmoid(rng.normal(-4.0, 1.0, n)))
         feats = np.empty((n, 3))
         feats[:, 0] = rng.uniform(0.0, 1.0, n)
         feats[:, 1:] = rng.standard_normal((n, 2))
-        scene = Scene(means, log_scales, quats, opacity, feats,
-                      FEATURES_LIDAR, 0)
+        if kind == "lidar":
+            scene = Scene(means, log_scales, quats, opacity, feats,
+                          FEATURES_LIDAR, 0)
+        else:
+            # SH^l: constant term about 3.5x the raw features (the degree-0
+            # basis function is about 0.28), higher bands N(0, 0.3)
+            nc = (sh_degree + 1) ** 2
+            sh = rng.normal(0.0, 0.3, size=(n, nc, 3))
+            sh[:, 0, :] = 3.5 * feats
+            scene = Scene(means, log_scales, quats, opacity, sh.reshape(n, nc * 3),
+                          FEATURES_LIDAR_SH, sh_degree)
     else:
         raise ValueError(kind)
     return Scene(scene.means.astype(np.float32),

@@ -568,3 +568,109 @@ def test_backward_lidar_matches_central_differences(O64):
             fd = (lp - lm) / (hp + hm)
             scale = max(1.0, np.abs(gflat).max())
             assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])
+
+
+# ------------------------------------------------------------ LiDAR SH^l
+def _lidar_sh_scene(sc, deg, coeffs):
+    """A copy of LiDAR scene `sc` with LIDAR_SH features [n, (deg+1)^2, 3]."""
+    import dataclasses
+    n = sc.n
+    return dataclasses.replace(sc, features=np.asarray(coeffs, np.float32).reshape(n, -1),
+                               feature_kind=syn.FEATURES_LIDAR_SH, sh_degree=deg)
+
+
+def test_lidar_sh_degree0_is_raw_features_over_y00(O64):
+    """Degree 0: zeta = Y_00 c_0 with Y_00 = 1 / (2 sqrt(pi)), so c_0 = f / Y_00
+    renders what the raw feature kind renders with f."""
+    L = syn.street_lidar(n_cols=96, n_beams=64)
+    sc = syn.street_scene(3000, seed=2, kind="lidar", length=40.0)
+    y00 = 1.0 / (2.0 * math.sqrt(math.pi))
+    sh = _lidar_sh_scene(sc, 0, sc.features.astype(np.float64) / y00)
+    a = O64.render_lidar(sc, L)
+    b = O64.render_lidar(sh, L)
+    f32 = sh.features.astype(np.float64) * y00 - sc.features.astype(np.float64)
+    tol = 1e-9 + 4 * np.abs(f32).max()          # the float32 rounding of c_0
+    assert np.abs(a["out"] - b["out"]).max() < tol
+    assert np.array_equal(a["alpha"], b["alpha"]) and np.array_equal(a["depth"], b["depth"])
+
+
+def test_lidar_sh_direction_from_the_mean_column_origin(O64):
+    """One Gaussian on the ray of (beam, col) of a moving sensor, 3 m out:
+    the ray through its centre composites alpha * zeta with zeta = sum_k
+    Y_k(d) c_k, d the ray direction (= the direction from that column's
+    origin to the mean), no colour offset and no clamp.  The sensor moves
+    1.5 m over the sweep, so the mid-sweep origin would see the mean from
+    another direction."""
+    L = syn.street_lidar(n_cols=128, n_beams=64)
+    beam, col = 40, 5
+    o, d, _, _ = O64.lidar_ray(L, beam, col)
+    sc = syn.tiny_scene(n=1)
+    sc.means[0] = o + 3.0 * d
+    sc.log_scales[0] = [-2.5, -2.6, -2.4]
+    sc.quats[0] = [1, 0, 0, 0]
+    sc.opacity[0] = 0.8
+    sc.feature_kind = syn.FEATURES_LIDAR
+    rng = np.random.default_rng(3)
+    c = rng.normal(0.0, 1.0, (1, 16, 3))
+    c[0, 0] = [0.1, -3.0, 2.0]           # zeta < 0 in the logits: nothing clamps
+    sh = _lidar_sh_scene(sc, 3, c)
+    r = O64.render_lidar(sh, L, O64.opts(cull=0), rays=[beam * L.n_cols + col])[0]
+    mu = sh.means[0].astype(np.float64)
+    P, _ = O64.project_lidar(sh, L, O64.opts(cull=0))
+    assert P["pose_col"][0] == col
+    dirv = mu - o
+    dirv /= np.linalg.norm(dirv)
+    Y = O64.sh_basis(dirv)
+    zeta = Y @ sh.features[0].astype(np.float64).reshape(16, 3)
+    a = float(np.float32(0.8))
+    assert abs(r["alpha"] - a) < 1e-9
+    assert np.allclose(r["out"], a * zeta, atol=1e-9), (r["out"], a * zeta)
+    # the mid-sweep origin would give a visibly different zeta
+    om = L.col_c2w[L.n_cols // 2][[3, 7, 11]].astype(np.float64)
+    dm = (mu - om) / np.linalg.norm(mu - om)
+    assert np.abs(O64.sh_basis(dm) @ sh.features[0].astype(np.float64).reshape(16, 3) - zeta).max() > 0.05
+
+
+def test_backward_lidar_sh_matches_central_differences(O64):
+    """As test_backward_lidar_matches_central_differences, with degree-2
+    SH^l features: the feature gradients are Y_k(dir) times the channel
+    gradients and the means get the direction term."""
+    L = syn.street_lidar(n_cols=64, n_beams=64)
+    L.n_elev_tiles = 1
+    L.max_rays_per_tile = 64 * 64
+    rng = np.random.default_rng(6)
+    n = 10
+    sc = syn.street_scene(n, seed=7, kind="lidar_sh", sh_degree=2, length=20.0)
+    ang = rng.uniform(-np.pi, np.pi, n)
+    rad = rng.uniform(8, 14, n)
+    sc.means[:] = np.stack([30 + rad * np.cos(ang), rad * np.sin(ang),
+                            rng.uniform(0, 2.5, n)], 1)
+    sc.log_scales[:] = rng.normal(-1.0, 0.2, (n, 3))
+    sc.opacity[:] = rng.uniform(0.2, 0.8, n)
+    sc.features[:] = rng.normal(0.0, 0.8, sc.features.shape)
+    opts = O64.opts(cutoffs=0, predicate=0, cull=0)
+    nr = L.n_beams * L.n_cols
+    g = [rng.normal(size=nr).astype(np.float32) * s for s in (0.02, 1.0, 1.0, 1.0)]
+    G = O64.backward_lidar(sc, L, *g, opts=opts)
+
+    def loss():
+        r = O64.render_lidar(sc, L, opts)
+        rg, it, dr = O64.lidar_decode(r)
+        return (rg * g[0]).sum() + (it * g[1]).sum() + (dr * g[2]).sum() + (r["alpha"] * g[3]).sum()
+
+    for name, arr in (("means", sc.means), ("features", sc.features)):
+        flat = arr.reshape(-1)
+        gflat = G[name].reshape(-1)
+        for i in range(0, flat.size, max(1, flat.size // 12)):
+            x0 = float(flat[i])
+            h = 2.0 ** -14
+            flat[i] = np.float32(x0 + h)
+            hp = float(flat[i]) - x0
+            lp = loss()
+            flat[i] = np.float32(x0 - h)
+            hm = x0 - float(flat[i])
+            lm = loss()
+            flat[i] = np.float32(x0)
+            fd = (lp - lm) / (hp + hm)
+            scale = max(1.0, np.abs(gflat).max())
+            assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])

@@ -306,6 +306,8 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         del S, frames, ef
         result["lidar"] = lidar_workload(torch, sg, syn, min(args.steps, 100), 5)
+        result["lidar"]["sh_features"] = lidar_workload(torch, sg, syn, min(args.steps, 100), 5,
+                                                        kind="lidar_sh")
         result["train_step"] = train_step_workload(torch, sg, syn, min(args.steps, 30), 3)
     if not args.no_serving:
         from paper_2510_12901_gb300 import serve
@@ -326,11 +328,12 @@ def _work(view):
         return None
 
 
-def lidar_workload(torch, sg, syn, steps, warmup):
+def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar"):
     """The LiDAR sweep configuration: 2M LiDAR Gaussians, 128 beams x 2048
     columns, per-column poses over a 0.1 s sweep; range, intensity, drop and
-    alpha per ray.  CUDA events over `steps` sweeps, inputs resident."""
-    sc = syn.street_scene(2_000_000, seed=0, kind="lidar")
+    alpha per ray.  CUDA events over `steps` sweeps, inputs resident.
+    kind='lidar_sh': the same scene with degree-3 SH^l features."""
+    sc = syn.street_scene(2_000_000, seed=0, kind=kind)
     L = syn.street_lidar()
     S, Ld = sg.Scene(sc), sg.Lidar(L)
     poses = torch.from_numpy(np.ascontiguousarray(L.col_c2w, np.float32)).cuda()
@@ -362,13 +365,15 @@ def lidar_workload(torch, sg, syn, steps, warmup):
     ms = e0.elapsed_time(e1) / steps
     st = np.array(stage).mean(axis=0)
     rays = L.n_beams * L.n_cols
-    out = {"workload": "street LiDAR scene: 2M Gaussians (intensity, ray-drop logits), 128-beam "
+    feats = ("intensity, ray-drop logits" if kind == "lidar" else
+             "degree-3 SH^l of intensity and ray-drop logits, 48 floats")
+    out = {"workload": f"street LiDAR scene: 2M Gaussians ({feats}), 128-beam "
                        "x 2048-column sweep, per-column poses over 0.1 s; range + intensity + drop",
            "value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_sweep": ms,
            "steps": steps, "stages_ms": {"project": st[0], "depth_sort_offsets": st[1],
                                          "bin_tile_sort_ranges": st[2], "render": st[3]}}
     pairs = _work("lidar")
-    if pairs:
+    if pairs and kind == "lidar":
         pk = peaks()
         peak = SM_COUNT * FP32_LANES * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         ach = pairs * FLOP_PER_PAIR / (st[3] * 1e-3) / 1e12

@@ -44,7 +44,7 @@ typedef struct sg_camera_s *sg_camera;
 typedef struct sg_lidar_s *sg_lidar;
 typedef struct sg_frame_s *sg_frame;
 
-enum { SG_FEATURES_RGB = 0, SG_FEATURES_SH = 1, SG_FEATURES_LIDAR = 2 };
+enum { SG_FEATURES_RGB = 0, SG_FEATURES_SH = 1, SG_FEATURES_LIDAR = 2, SG_FEATURES_LIDAR_SH = 3 };
 enum { SG_CAMERA_PINHOLE = 0, SG_CAMERA_FISHEYE = 1 };
 
 /* Library version and the CUDA architecture it was built for (103 for sm_103a). */
@@ -67,10 +67,18 @@ typedef struct {
     const float *d_quats;      /* [n,4] (w,x,y,z); normalised by the library */
     const float *d_opacity;    /* [n] in (0,1), already activated */
     const float *d_features;   /* [n,F]: RGB F=3, SH F=3*(deg+1)^2 laid out
-                                  [n,(deg+1)^2,3], LiDAR F=3 */
+                                  [n,(deg+1)^2,3], LiDAR F=3, LiDAR SH
+                                  F=3*(deg+1)^2 laid out as SH */
     int feature_kind;          /* SG_FEATURES_* */
-    int sh_degree;             /* 0..3, used with SG_FEATURES_SH */
+    int sh_degree;             /* 0..3, used with SG_FEATURES_SH and _LIDAR_SH */
 } sg_gaussians_desc;
+/* Feature kinds.  SH (camera colour): c = max(sum_k Y_k(d) c_k + 0.5, 0),
+ * evaluated once per Gaussian at the direction d from the camera centre to
+ * the mean.  LIDAR: zeta = the three floats as given.  LIDAR_SH (the SH^l
+ * of Sec. 3.1): zeta = sum_k Y_k(d) c_k with neither offset nor clamp (an
+ * intensity and two logits), evaluated once per Gaussian at the direction
+ * from the sensor origin of the column pose that sees the mean to the mean.
+ * Y_k: real spherical harmonics of degree <= 3, orthonormal on the sphere. */
 
 /* Copies the caller's arrays (device pointers, caller keeps ownership) into a
  * library-owned planar layout on `stream`.  The caller's arrays may be freed

@@ -429,9 +429,14 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
     }
 }
 
+// SH origin: (ox, oy, oz) for cameras; for LiDAR SH^l features, the origin
+// of the column pose that saw the mean, whose index the projection left in
+// the record's feat.w.
 __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, int64_t n,
                               int feature_kind, int sh_degree, int F, float ox, float oy,
-                              float oz, const float *__restrict__ gacc, float *__restrict__ gm,
+                              float oz, const GRec *__restrict__ rec,
+                              const float *__restrict__ poses,
+                              const float *__restrict__ gacc, float *__restrict__ gm,
                               float *__restrict__ gls, float *__restrict__ gq,
                               float *__restrict__ gop, float *__restrict__ gf)
 {
@@ -482,7 +487,14 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
     if (gop) gop[g] += G[12];
     float gmu[3] = {G[9], G[10], G[11]};
     const float gc[3] = {G[13], G[14], G[15]};
-    if (feature_kind == SG_FEATURES_SH) {
+    if (sh_features(feature_kind)) {
+        const bool lidar = feature_kind == SG_FEATURES_LIDAR_SH;
+        if (lidar) {
+            const float *P = poses + 12 * __float_as_uint(rec[g].feat.w);
+            ox = P[3];
+            oy = P[7];
+            oz = P[11];
+        }
         const float mx = planes[(Scene::kMean + 0) * pitch + g] - ox;
         const float my = planes[(Scene::kMean + 1) * pitch + g] - oy;
         const float mz = planes[(Scene::kMean + 2) * pitch + g] - oz;
@@ -496,7 +508,7 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
         for (int ch = 0; ch < 3; ++ch) {
             float acc = 0.f;
             for (int k = 0; k < nc; ++k) acc += Y[k] * planes[(Scene::kFeat + 3 * k + ch) * pitch + g];
-            if (acc + 0.5f < 0.f) continue;   // clamped colour channel
+            if (!lidar && acc + 0.5f < 0.f) continue;   // clamped colour channel
             for (int k = 0; k < nc; ++k) {
                 if (gf) gf[g * F + 3 * k + ch] += Y[k] * gc[ch];
                 const float f = planes[(Scene::kFeat + 3 * k + ch) * pitch + g];
@@ -522,6 +534,7 @@ static sg_status finish(const Scene &sc, Frame &fr, const float o[3], const sg_g
     if (sc.n == 0) return SG_OK;
     k_param_grads<<<(unsigned)((sc.n + 127) / 128), 128, 0, st>>>(
         sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, sc.F, o[0], o[1], o[2],
+        (const GRec *)fr.rec.p, fr.d_lidar_poses,
         (const float *)fr.gacc.p, g.d_g_means, g.d_g_log_scales, g.d_g_quats, g.d_g_opacity,
         g.d_g_features);
     SG_LAUNCHED();

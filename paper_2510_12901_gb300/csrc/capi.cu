@@ -89,7 +89,7 @@ static sg_status check_desc(const sg_gaussians_desc *d, int *F)
         set_error("n = %lld out of range [0, 2^31]", (long long)d->n);
         return SG_ERR_INVALID;
     }
-    if (d->feature_kind == SG_FEATURES_SH) {
+    if (sh_features(d->feature_kind)) {
         if (d->sh_degree < 0 || d->sh_degree > 3) {
             set_error("sh_degree %d not in 0..3", d->sh_degree);
             return SG_ERR_INVALID;
@@ -288,7 +288,7 @@ static sg_status camera_begin(sg_scene scene, sg_camera cam, const float h_c2w[1
     if (!scene || !cam || !frame || !h_c2w) { set_error("NULL handle or pose"); return SG_ERR_INVALID; }
     if (!opts_ok(opts)) return SG_ERR_INVALID;
     const Scene &sc = scene->s;
-    if (sc.feature_kind == SG_FEATURES_LIDAR) {
+    if (lidar_features(sc.feature_kind)) {
         set_error("sg_render_camera: scene carries LiDAR features");
         return SG_ERR_INVALID;
     }
@@ -368,7 +368,7 @@ sg_status sg_create_scene(const sg_gaussians_desc *desc, void *stream, sg_scene 
     Scene &sc = h->s;
     sc.n = desc->n;
     sc.feature_kind = desc->feature_kind;
-    sc.sh_degree = desc->feature_kind == SG_FEATURES_SH ? desc->sh_degree : 0;
+    sc.sh_degree = sh_features(desc->feature_kind) ? desc->sh_degree : 0;
     sc.F = F;
     sc.pitch = ((desc->n + 31) / 32) * 32;
     if (sc.pitch == 0) sc.pitch = 32;
@@ -660,7 +660,7 @@ sg_status sg_render_lidar(sg_scene scene, sg_lidar lidar, const float *d_col_c2w
     }
     if (!opts_ok(opts)) return SG_ERR_INVALID;
     const Scene &sc = scene->s;
-    if (sc.feature_kind != SG_FEATURES_LIDAR) {
+    if (!lidar_features(sc.feature_kind)) {
         set_error("sg_render_lidar: scene does not carry LiDAR features");
         return SG_ERR_INVALID;
     }

@@ -12,6 +12,16 @@
 
 namespace sg {
 
+// Feature kinds a LiDAR render takes, and kinds whose features are SH.
+__host__ __device__ inline bool lidar_features(int kind)
+{
+    return kind == SG_FEATURES_LIDAR || kind == SG_FEATURES_LIDAR_SH;
+}
+__host__ __device__ inline bool sh_features(int kind)
+{
+    return kind == SG_FEATURES_SH || kind == SG_FEATURES_LIDAR_SH;
+}
+
 constexpr int kTile = 16;                 // camera tile edge (pixels)
 constexpr int kCamThreads = kTile * kTile;
 constexpr int kLidarColsMax = 4;          // distinct columns per LiDAR work item

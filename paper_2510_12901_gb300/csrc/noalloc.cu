@@ -93,7 +93,7 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     const Scene &sc = scene->s;
     const Camera &c = cam->c;
     const int64_t nr = (int64_t)c.width * c.height, nt = (int64_t)c.ntx * c.nty;
-    if (sc.feature_kind == SG_FEATURES_LIDAR) {
+    if (lidar_features(sc.feature_kind)) {
         set_error("sg_render_camera_static: scene carries LiDAR features");
         return SG_ERR_INVALID;
     }

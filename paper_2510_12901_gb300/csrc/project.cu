@@ -69,7 +69,8 @@ __device__ __forceinline__ Activated activate(const float *__restrict__ planes, 
 // Render record: M = S^-1 R^T (row i = column i of R over s_i) and the
 // cofactor weights f_i = s_i / (s_j s_k) (row i of cof(M) = f_i M_i).
 __device__ __forceinline__ void write_record(GRec *rec, int64_t g, const Activated &a,
-                                             float f0, float f1, float f2, float4 rect)
+                                             float f0, float f1, float f2, float4 rect,
+                                             float fw = 0.f)
 {
     GRec r;
     r.mu_sigma = make_float4(a.mu[0], a.mu[1], a.mu[2], a.sigma);
@@ -77,7 +78,7 @@ __device__ __forceinline__ void write_record(GRec *rec, int64_t g, const Activat
     r.m0 = make_float4(a.R[0] * i0, a.R[3] * i0, a.R[6] * i0, a.s[0] / (a.s[1] * a.s[2]));
     r.m1 = make_float4(a.R[1] * i1, a.R[4] * i1, a.R[7] * i1, a.s[1] / (a.s[0] * a.s[2]));
     r.m2 = make_float4(a.R[2] * i2, a.R[5] * i2, a.R[8] * i2, a.s[2] / (a.s[0] * a.s[1]));
-    r.feat = make_float4(f0, f1, f2, 0.f);
+    r.feat = make_float4(f0, f1, f2, fw);
     r.rect = rect;
     rec[g] = r;
 }
@@ -85,9 +86,9 @@ __device__ __forceinline__ void write_record(GRec *rec, int64_t g, const Activat
 // Real spherical harmonics of degree <= 3 (normalised, Condon-Shortley
 // phase, m = -l..l order).  Constants: sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!),
 // times sqrt(2) for m != 0, times the leading factor of P_l^|m|.
-__device__ __forceinline__ void sh_colour(const float *__restrict__ planes, int64_t pitch,
-                                          int64_t g, int deg, float x, float y, float z,
-                                          float c[3])
+__device__ __forceinline__ void sh_eval(const float *__restrict__ planes, int64_t pitch,
+                                        int64_t g, int deg, float x, float y, float z,
+                                        float c[3])
 {
     float Y[16];
     const float xx = x * x, yy = y * y, zz = z * z;
@@ -125,7 +126,7 @@ __device__ __forceinline__ void sh_colour(const float *__restrict__ planes, int6
         float acc = 0.f;
 #pragma unroll
         for (int k = 0; k < 16; ++k) acc += k < nc ? Y[k] * f[k] : 0.f;
-        c[ch] = fmaxf(acc + 0.5f, 0.f);
+        c[ch] = acc;
     }
 }
 
@@ -239,7 +240,8 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     float c[3];
     if (feature_kind == SG_FEATURES_SH) {
         float inv = 1.f / dist;
-        sh_colour(planes, pitch, g, sh_degree, dx * inv, dy * inv, dz * inv, c);
+        sh_eval(planes, pitch, g, sh_degree, dx * inv, dy * inv, dz * inv, c);
+        for (int ch = 0; ch < 3; ++ch) c[ch] = fmaxf(c[ch] + 0.5f, 0.f);   // colour offset, clamp
     } else {
         for (int ch = 0; ch < 3; ++ch) c[ch] = planes[(Scene::kFeat + ch) * pitch + g];
     }
@@ -364,9 +366,13 @@ __device__ __forceinline__ int sat_count_wrap(const LidParams &L, int x0, int x1
     return sat_count(L, a, L.A - 1, y0, y1) + sat_count(L, 0, b, y0, y1);
 }
 
+// kSH: the scene carries SH^l features (evaluated here, as for camera
+// colour); a template so that the raw-feature path keeps its registers.
+template <bool kSH>
 __global__ void __launch_bounds__(256)
-k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidParams Lp,
-                const RenderDesc *__restrict__ D, UTParams U, int cull, GRec *__restrict__ rec, float4 *__restrict__ rect_out,
+k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int sh_degree,
+                LidParams Lp, const RenderDesc *__restrict__ D, UTParams U,
+                int cull, GRec *__restrict__ rec, float4 *__restrict__ rect_out,
                 int4 *__restrict__ tiles_out, float *__restrict__ depth_out,
                 uint32_t *__restrict__ count_out, float2 *__restrict__ mean_out,
                 float4 *__restrict__ cov_out)
@@ -377,7 +383,7 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidP
     L.poses = D->poses;
     Activated a = activate(planes, pitch, g);
     float xs0[3], az0;               // chi_0 = mu, also the depth key
-    lidar_col(L, a.mu, xs0, &az0);
+    const int col0 = lidar_col(L, a.mu, xs0, &az0);
     const float r0 = sqrtf(xs0[0] * xs0[0] + xs0[1] * xs0[1] + xs0[2] * xs0[2]);
     depth_out[g] = r0;
     uint32_t count = 0;
@@ -466,6 +472,17 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, LidP
     mean_out[g] = m2;
     cov_out[g] = cv;
     if (count == 0) return;
+    if constexpr (kSH) {
+        // SH^l at the direction from the origin of mu's column pose to mu;
+        // the column goes into the record for the backward
+        const float *P = L.poses + 12 * col0;
+        const float vx = a.mu[0] - P[3], vy = a.mu[1] - P[7], vz = a.mu[2] - P[11];
+        const float inv = 1.f / sqrtf(vx * vx + vy * vy + vz * vz);
+        float c[3];
+        sh_eval(planes, pitch, g, sh_degree, vx * inv, vy * inv, vz * inv, c);
+        write_record(rec, g, a, c[0], c[1], c[2], rect, __uint_as_float((uint32_t)col0));
+        return;
+    }
     write_record(rec, g, a, planes[(Scene::kFeat + 0) * pitch + g],
                  planes[(Scene::kFeat + 1) * pitch + g], planes[(Scene::kFeat + 2) * pitch + g],
                  rect);
@@ -490,8 +507,10 @@ sg_status project_lidar(const Scene &sc, const Lidar &Ld, const sg_render_opts &
     UTParams U = ut_params(o);
     if (sc.n == 0) return SG_OK;
     unsigned grid = (unsigned)((sc.n + 255) / 256);
-    k_project_lidar<<<grid, 256, 0, st>>>(
-        sc.d_planes, sc.pitch, sc.n, L, (const RenderDesc *)fr.desc.p, U, o.cull,
+    auto kern = sc.feature_kind == SG_FEATURES_LIDAR_SH ? k_project_lidar<true>
+                                                         : k_project_lidar<false>;
+    kern<<<grid, 256, 0, st>>>(
+        sc.d_planes, sc.pitch, sc.n, sc.sh_degree, L, (const RenderDesc *)fr.desc.p, U, o.cull,
         (GRec *)fr.rec.p, (float4 *)fr.rect.p,
         (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p, (float2 *)fr.mean2d.p,
         (float4 *)fr.cov2d.p);

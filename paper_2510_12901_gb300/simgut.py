@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libsimgut.so")
 SG_OK = 0
 STATUS = {0: "SG_OK", -1: "SG_ERR_INVALID", -2: "SG_ERR_OOM", -3: "SG_ERR_CUDA",
           -4: "SG_ERR_OVERFLOW", -5: "SG_ERR_TIMEOUT", -6: "SG_ERR_BUSY"}
-FEATURES_RGB, FEATURES_SH, FEATURES_LIDAR = 0, 1, 2
+FEATURES_RGB, FEATURES_SH, FEATURES_LIDAR, FEATURES_LIDAR_SH = 0, 1, 2, 3
 CAMERA_PINHOLE, CAMERA_FISHEYE = 0, 1
 (FIELD_RECT, FIELD_TILES, FIELD_DEPTH, FIELD_COUNT, FIELD_PAIR_IDS, FIELD_PAIR_TILES,
  FIELD_RANGES, FIELD_RAY_STATE, FIELD_N_CONTRIB, FIELD_MEAN2D, FIELD_COV2D) = range(11)

@@ -110,11 +110,11 @@ def test_camera_backward_sh_fisheye(sg, O64):
     compare_grads(Gg, Go, "sh-fisheye")
 
 
-def lidar_backward(sg, S, Ld, L, g, n):
+def lidar_backward(sg, S, Ld, L, g, n, F=3):
     import torch
     out = sg.render_lidar(S, Ld, L.col_c2w)
     grads = {k: torch.zeros(s, device="cuda") for k, s in
-             zip(NAMES, [(n, 3), (n, 3), (n, 4), (n,), (n, 3)])}
+             zip(NAMES, [(n, 3), (n, 3), (n, 4), (n,), (n, F)])}
     ups = [torch.from_numpy(np.ascontiguousarray(u, np.float32)).cuda() for u in g]
     gs = sg.sg_grads(*[grads[k].data_ptr() for k in NAMES])
     sg.sg_backward_lidar(S.handle, out["frame"].handle, *[u.data_ptr() for u in ups], gs,
@@ -123,9 +123,13 @@ def lidar_backward(sg, S, Ld, L, g, n):
     return {k: v.cpu().numpy() for k, v in grads.items()}
 
 
-def test_lidar_backward_toy(sg, O64):
+@pytest.mark.parametrize("kind", ["lidar", "lidar_sh"])
+def test_lidar_backward_toy(sg, O64, kind):
+    """Raw LiDAR features, and degree-3 SH^l features (feature gradients
+    Y_k(dir) times the channel gradients, and the direction term in the
+    mean gradients)."""
     L = syn.street_lidar(n_cols=256)
-    sc = syn.street_scene(1500, seed=0, kind="lidar", length=60.0)
+    sc = syn.street_scene(1500, seed=0, kind=kind, length=60.0)
     orc = O64.render_lidar(sc, L)
     rng = np.random.default_rng(2)
     ok = ~par.ambiguous_rays(orc, lidar=True)
@@ -135,8 +139,8 @@ def test_lidar_backward_toy(sg, O64):
     for a in g:
         a[~ok] = 0
     Go = O64.backward_lidar(sc, L, *g)
-    Gg = lidar_backward(sg, sg.Scene(sc), sg.Lidar(L), L, g, sc.n)
-    compare_grads(Gg, Go, "lidar-toy")
+    Gg = lidar_backward(sg, sg.Scene(sc), sg.Lidar(L), L, g, sc.n, sc.features.shape[1])
+    compare_grads(Gg, Go, f"{kind}-toy")
 
 
 def test_differentiable_step_full_size_sampled(sg, O64):

@@ -33,9 +33,9 @@ def gpu_render(sg, sc, L, opts=None, scene=None, lidar=None):
     return res
 
 
-def toy(n=1500, seed=0, n_cols=256):
+def toy(n=1500, seed=0, n_cols=256, kind="lidar"):
     L = syn.street_lidar(n_cols=n_cols)
-    sc = syn.street_scene(n, seed=seed, kind="lidar", length=60.0)
+    sc = syn.street_scene(n, seed=seed, kind=kind, length=60.0)
     return sc, L
 
 
@@ -74,8 +74,11 @@ def check_projection(sg, fr, sc, L, O32, O64, label):
     return P32, amb, key, nth, nphi
 
 
-def test_toy_sweep_every_ray_and_list(sg, O32, O64):
-    sc, L = toy()
+@pytest.mark.parametrize("kind", ["lidar", "lidar_sh"])
+def test_toy_sweep_every_ray_and_list(sg, O32, O64, kind):
+    """Every ray of a 128 x 256 sweep; kind lidar_sh: degree-3 SH^l
+    features evaluated per Gaussian from the origin of its column pose."""
+    sc, L = toy(kind=kind)
     g = gpu_render(sg, sc, L)
     orc = O64.render_lidar(sc, L)
     info = par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
@@ -160,12 +163,13 @@ def test_host_output_path_matches_device_path(sg):
         assert np.array_equal(o, g[k]), k
 
 
-@pytest.mark.parametrize("beams", [128, 64])
-def test_full_sweep_sampled_parity(sg, O32, O64, beams):
+@pytest.mark.parametrize("beams,kind", [(128, "lidar"), (64, "lidar"), (128, "lidar_sh")])
+def test_full_sweep_sampled_parity(sg, O32, O64, beams, kind):
     """2M Gaussians, 128 beams x 2048 columns (or 64 x 1024, where a tile of
     32 rays spans 8 columns and is walked by two work items), per-column
-    poses over 0.1 s; tile lists of thousands of entries, split in segments."""
-    sc = syn.street_scene(2_000_000, seed=10, kind="lidar")
+    poses over 0.1 s; tile lists of thousands of entries, split in segments.
+    lidar_sh: degree-3 SH^l features."""
+    sc = syn.street_scene(2_000_000, seed=10, kind=kind)
     L = syn.street_lidar() if beams == 128 else syn.street_lidar(n_beams=64, n_cols=1024)
     g = gpu_render(sg, sc, L)
     lens = np.diff(g["frame"].field(sg.FIELD_RANGES, np.uint32, 2).astype(np.int64), axis=1)
@@ -185,7 +189,7 @@ def test_full_sweep_sampled_parity(sg, O32, O64, beams):
     # items per tile, larger per-column motion)
     info = par.compare_lidar_rays(g["range"][rays], g["intensity"][rays], g["drop"][rays],
                                   g["alpha"][rays], orc, max_excluded=0.02,
-                                  label=f"full-{beams}", also_excluded=seen)
+                                  label=f"full-{beams}-{kind}", also_excluded=seen)
     assert (orc["n_contrib"] > 0).mean() > 0.3, info
     ids = g["frame"].field(sg.FIELD_PAIR_IDS, np.uint32)
     ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)

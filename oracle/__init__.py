@@ -47,7 +47,8 @@ def _structs(real):
         _fields_ = [("n", C.c_int64), ("means", C.c_void_p), ("log_scales", C.c_void_p),
                     ("quats", C.c_void_p), ("opacity", C.c_void_p),
                     ("features", C.c_void_p), ("feature_kind", C.c_int),
-                    ("sh_degree", C.c_int)]
+                    ("sh_degree", C.c_int), ("actor_of", C.c_void_p), ("n_actors", C.c_int),
+                    ("actor_poses", C.c_void_p)]
 
     class Camera(C.Structure):
         _fields_ = [("model", C.c_int), ("width", C.c_int), ("height", C.c_int),
@@ -138,6 +139,11 @@ class Oracle:
         arrs = [np.ascontiguousarray(a, np.float32) for a in
                 (sc.means, sc.log_scales, sc.quats, sc.opacity, sc.features)]
         s = self.Scene(sc.n, *[self._p(a) for a in arrs], sc.feature_kind, sc.sh_degree)
+        if getattr(sc, "actor_of", None) is not None:
+            ao = np.ascontiguousarray(sc.actor_of, np.int32)
+            ap = np.ascontiguousarray(sc.actor_poses, np.float32).reshape(-1, 12)
+            s.actor_of, s.n_actors, s.actor_poses = self._p(ao), ap.shape[0], self._p(ap)
+            arrs = arrs + [ao, ap]
         s._keep = arrs
         return s
 

@@ -101,6 +101,39 @@ static void inv_cov(const real R[9], const real s[3], real A[9])
 /* convention used by 3DGS-style renderers.                             */
 /* ------------------------------------------------------------------ */
 
+/* Actor rotation of Gaussian g (identity for the static background) and,
+ * if t is given, its translation. */
+static int actor_pose(const or_scene *sc, int64_t g, real Ra[9], real t[3])
+{
+    int a = sc->actor_of ? sc->actor_of[g] : -1;
+    if (a < 0 || a >= sc->n_actors) {
+        for (int i = 0; i < 9; ++i) Ra[i] = (i % 4 == 0) ? RL(1) : RL(0);
+        if (t) t[0] = t[1] = t[2] = 0;
+        return 0;
+    }
+    const float *P = sc->actor_poses + 12 * a;
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Ra[3 * i + j] = RL(P[4 * i + j]);
+        if (t) t[i] = RL(P[4 * i + 3]);
+    }
+    return 1;
+}
+
+/* World mean and rotation of Gaussian g: mu_w = Ra mu + t, R_w = Ra R. */
+static void gauss_world(const or_scene *sc, int64_t g, real mu[3], real R[9], real *qn)
+{
+    real q[4], Rl[9], Ra[9], t[3], ml[3];
+    unit_quat(sc->quats + 4 * g, q, qn);
+    quat_to_R(q, Rl);
+    for (int k = 0; k < 3; ++k) ml[k] = RL(sc->means[3 * g + k]);
+    actor_pose(sc, g, Ra, t);
+    for (int i = 0; i < 3; ++i) {
+        mu[i] = Ra[3 * i] * ml[0] + Ra[3 * i + 1] * ml[1] + Ra[3 * i + 2] * ml[2] + t[i];
+        for (int j = 0; j < 3; ++j)
+            R[3 * i + j] = Ra[3 * i] * Rl[j] + Ra[3 * i + 1] * Rl[3 + j] + Ra[3 * i + 2] * Rl[6 + j];
+    }
+}
+
 static double fact(int k) { double f = 1; for (int i = 2; i <= k; ++i) f *= i; return f; }
 static double shK(int l, int m)
 {
@@ -553,13 +586,9 @@ void or_project_camera(const or_scene *sc, const or_camera *cam,
         or_proj *p = &out[g];
         memset(p, 0, sizeof(*p));
         p->cmargin = RL(1e30);
-        real q[4], R[9], s[3], mu[3];
-        unit_quat(sc->quats + 4 * g, q, NULL);
-        quat_to_R(q, R);
-        for (int k = 0; k < 3; ++k) {
-            s[k] = exp(RL(sc->log_scales[3 * g + k]));
-            mu[k] = RL(sc->means[3 * g + k]);
-        }
+        real R[9], s[3], mu[3];
+        gauss_world(sc, g, mu, R, NULL);
+        for (int k = 0; k < 3; ++k) s[k] = exp(RL(sc->log_scales[3 * g + k]));
         real sigma = RL(sc->opacity[g]), amin = RL(o->alpha_min);
         real dx = mu[0] - RL(cam->c2w[3]), dy = mu[1] - RL(cam->c2w[7]), dz = mu[2] - RL(cam->c2w[11]);
         /* sort key: 3DGS-style keys carry float32 depth bits (Sec. 3.2 "as in
@@ -654,13 +683,9 @@ void or_project_lidar(const or_scene *sc, const or_lidar *L,
         or_proj *p = &out[g];
         memset(p, 0, sizeof(*p));
         p->cmargin = RL(1e30);
-        real q[4], R[9], s[3], mu[3];
-        unit_quat(sc->quats + 4 * g, q, NULL);
-        quat_to_R(q, R);
-        for (int k = 0; k < 3; ++k) {
-            s[k] = exp(RL(sc->log_scales[3 * g + k]));
-            mu[k] = RL(sc->means[3 * g + k]);
-        }
+        real R[9], s[3], mu[3];
+        gauss_world(sc, g, mu, R, NULL);
+        for (int k = 0; k < 3; ++k) s[k] = exp(RL(sc->log_scales[3 * g + k]));
         real sigma = RL(sc->opacity[g]), amin = RL(o->alpha_min);
         lid_ctx ctx = {L, o, 0, 0, RL(1e30), RL(1e30)};
         /* depth key: distance to the sensor origin of the centre's column */
@@ -810,13 +835,9 @@ typedef struct {
 static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3],
                           gauss_rt *G)
 {
-    real q[4], R[9], s[3];
-    unit_quat(sc->quats + 4 * g, q, NULL);
-    quat_to_R(q, R);
-    for (int k = 0; k < 3; ++k) {
-        s[k] = exp(RL(sc->log_scales[3 * g + k]));
-        G->mu[k] = RL(sc->means[3 * g + k]);
-    }
+    real R[9], s[3];
+    gauss_world(sc, g, G->mu, R, NULL);
+    for (int k = 0; k < 3; ++k) s[k] = exp(RL(sc->log_scales[3 * g + k]));
     inv_cov(R, s, G->A);
     G->sigma = RL(sc->opacity[g]);
     G->clampc[0] = G->clampc[1] = G->clampc[2] = 0;
@@ -829,7 +850,11 @@ static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3],
         const int lidar = sc->feature_kind == OR_FEAT_LIDAR_SH;
         real v[3] = {G->mu[0] - ocam[0], G->mu[1] - ocam[1], G->mu[2] - ocam[2]};
         real nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        for (int k = 0; k < 3; ++k) G->dir[k] = v[k] / nv;
+        real Ra[9];
+        actor_pose(sc, g, Ra, NULL);
+        /* the direction in the Gaussian's own (actor) frame: Ra^T v / |v| */
+        for (int k = 0; k < 3; ++k)
+            G->dir[k] = (Ra[k] * v[0] + Ra[3 + k] * v[1] + Ra[6 + k] * v[2]) / nv;
         G->dist = nv;
         real Y[16];
         or_sh_basis(G->dir, Y);
@@ -1285,7 +1310,23 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
         unit_quat(sc->quats + 4 * g, q, &qn);
         quat_to_R(q, R);
         for (int k = 0; k < 3; ++k) s[k] = exp(RL(sc->log_scales[3 * g + k]));
-        const real *GA = B->gA + 9 * g;
+        /* actor: A_w = Ra A Ra^T and mu_w = Ra mu + t, so the gradients in the
+         * Gaussian's own frame are Ra^T dL/dA_w Ra and Ra^T dL/dmu_w */
+        real Ra[9], GA[9], gmw[3];
+        actor_pose(sc, g, Ra, NULL);
+        {
+            const real *GW = B->gA + 9 * g;
+            real T[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    T[3 * i + j] = GW[3 * i] * Ra[j] + GW[3 * i + 1] * Ra[3 + j] +
+                                   GW[3 * i + 2] * Ra[6 + j];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    GA[3 * i + j] = Ra[i] * T[j] + Ra[3 + i] * T[3 + j] + Ra[6 + i] * T[6 + j];
+            const real *m = B->gmu + 3 * g;
+            for (int i = 0; i < 3; ++i) gmw[i] = Ra[i] * m[0] + Ra[3 + i] * m[1] + Ra[6 + i] * m[2];
+        }
         /* A = sum_k u_k r_k r_k^T, u_k = 1/s_k^2 = exp(-2 ls_k), r_k = column k */
         real gR[9] = {0};
         for (int k = 0; k < 3; ++k) {
@@ -1317,7 +1358,7 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
         real dotq = gqh[0] * q[0] + gqh[1] * q[1] + gqh[2] * q[2] + gqh[3] * q[3];
         for (int i = 0; i < 4; ++i) gq[4 * g + i] += (gqh[i] - q[i] * dotq) / qn;
         gop[g] += B->gsig[g];
-        for (int k = 0; k < 3; ++k) gm[3 * g + k] += B->gmu[3 * g + k];
+        for (int k = 0; k < 3; ++k) gm[3 * g + k] += gmw[k];
         const real *gc = B->gfeat + 3 * g;
         if (sh) {
             int nc = (sc->sh_degree + 1) * (sc->sh_degree + 1);
@@ -1333,7 +1374,8 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
                     for (int t = 0; t < 3; ++t) gdir[t] += gc[ch] * RL(f[3 * k + ch]) * dY[k][t];
                 }
             }
-            /* dir = (mu - o)/|mu - o| */
+            /* dir = Ra^T (mu_w - o)/|mu_w - o|: in the Gaussian's own frame the
+             * mean's gradient has the same form as without an actor */
             real dd = gdir[0] * G->dir[0] + gdir[1] * G->dir[1] + gdir[2] * G->dir[2];
             for (int t = 0; t < 3; ++t) gm[3 * g + t] += (gdir[t] - G->dir[t] * dd) / G->dist;
         } else {

@@ -43,6 +43,15 @@ typedef struct {
     const float *features;    /* [n,F] */
     int feature_kind;
     int sh_degree;
+    /* Dynamic actors (Sec. 3.1 scene graph; NULL actor_of: all static).
+     * Gaussian g with actor_of[g] = a >= 0 has its mean and rotation in
+     * actor a's frame; actor_poses[a] (row-major [R | t], actor to world, at
+     * the render's timestamp) takes them to world coordinates before
+     * projection.  Its SH are evaluated at the view direction expressed in
+     * the actor's frame (the appearance turns with the object). */
+    const int32_t *actor_of;  /* [n] or NULL */
+    int n_actors;
+    const float *actor_poses; /* [n_actors,12] */
 } or_scene;
 
 typedef struct {

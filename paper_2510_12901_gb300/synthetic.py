@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+from typing import Optional
 
 import numpy as np
 
@@ -47,6 +48,10 @@ class Scene:
     features: np.ndarray     # [n, F] float32
     feature_kind: int
     sh_degree: int = 0
+    # dynamic actors: per-Gaussian actor index (-1: static) and the actors'
+    # poses [n_actors, 12] (row-major [R | t], actor to world), or None
+    actor_of: Optional[np.ndarray] = None
+    actor_poses: Optional[np.ndarray] = None
 
     @property
     def n(self) -> int:
@@ -57,7 +62,9 @@ class Scene:
         return Scene(self.means[idx].copy(), self.log_scales[idx].copy(),
                      self.quats[idx].copy(), self.opacity[idx].copy(),
                      self.features[idx].copy(), self.feature_kind,
-                     self.sh_degree)
+                     self.sh_degree,
+                     None if self.actor_of is None else self.actor_of[idx].copy(),
+                     None if self.actor_poses is None else self.actor_poses.copy())
 
 
 @dataclasses.dataclass
@@ -268,6 +275,38 @@ def street_scene(n: int, seed: int = 0, kind: str = "camera",
                  scene.opacity.astype(np.float32),
                  scene.features.astype(np.float32),
                  scene.feature_kind, scene.sh_degree)
+
+
+def actor_pose(x: float, y: float, yaw: float, z: float = 0.0) -> np.ndarray:
+    """Row-major [R | t] of a rotation by `yaw` about +z and a translation."""
+    c, s = math.cos(yaw), math.sin(yaw)
+    return np.array([c, -s, 0.0, x, s, c, 0.0, y, 0.0, 0.0, 1.0, z], np.float32)
+
+
+def with_actors(scene: Scene, n_actors: int = 16, frac: float = 0.1, seed: int = 3) -> Scene:
+    """A copy of a street scene in which `frac` of the Gaussians belong to
+    `n_actors` car-sized rigid actors: their means are redrawn on the surface
+    of a 4.5 x 1.8 x 1.5 m box in the actor's frame (origin at the box's
+    bottom centre), and the actors stand on the road at random headings."""
+    rng = np.random.default_rng(seed)
+    n = scene.n
+    k = int(round(frac * n))
+    idx = rng.choice(n, k, replace=False)
+    actor_of = np.full(n, -1, np.int32)
+    actor_of[idx] = rng.integers(0, n_actors, k)
+    half = np.array([2.25, 0.9, 0.75])
+    face = rng.integers(0, 3, k)
+    side = np.where(rng.uniform(size=k) < 0.5, -1.0, 1.0)
+    local = rng.uniform(-1.0, 1.0, (k, 3)) * half
+    local[np.arange(k), face] = side * half[face]
+    local[:, 2] += half[2]
+    means = scene.means.copy()
+    means[idx] = local.astype(np.float32)
+    poses = np.stack([actor_pose(float(rng.uniform(5.0, 140.0)),
+                                 float(rng.choice([-1.0, 1.0]) * rng.uniform(1.5, 6.0)),
+                                 float(rng.uniform(-math.pi, math.pi)))
+                      for _ in range(n_actors)])
+    return dataclasses.replace(scene, means=means, actor_of=actor_of, actor_poses=poses)
 
 
 def street_cameras(seed: int = 1, x: float = 0.0, y: float = 0.0):

@@ -4,6 +4,7 @@ None of these compares the oracle with itself: each checks a closed form, an
 invariant, a textbook special case, a sampling estimate or a brute force.
 Section / equation numbers refer to arXiv 2510.12901.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -670,6 +671,110 @@ def test_backward_lidar_sh_matches_central_differences(O64):
             flat[i] = np.float32(x0 - h)
             hm = x0 - float(flat[i])
             lm = loss()
+            flat[i] = np.float32(x0)
+            fd = (lp - lm) / (hp + hm)
+            scale = max(1.0, np.abs(gflat).max())
+            assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])
+
+
+# ------------------------------------------------------------ dynamic actors
+def _compose(A, B):
+    """Row-major [R | t] poses: A o B."""
+    A = np.asarray(A, np.float64).reshape(3, 4)
+    B = np.asarray(B, np.float64).reshape(3, 4)
+    R = A[:, :3] @ B[:, :3]
+    t = A[:, :3] @ B[:, 3] + A[:, 3]
+    return np.concatenate([R, t[:, None]], 1).reshape(12)
+
+
+def _inverse(A):
+    A = np.asarray(A, np.float64).reshape(3, 4)
+    R = A[:, :3].T
+    return np.concatenate([R, (-R @ A[:, 3])[:, None]], 1).reshape(12)
+
+
+def test_actors_at_identity_render_the_static_scene(O64):
+    sc = syn.with_actors(syn.street_scene(3000, seed=4, length=30.0), n_actors=5, frac=0.3)
+    sc.actor_poses[:] = syn.actor_pose(0.0, 0.0, 0.0)
+    static = dataclasses.replace(sc, actor_of=None, actor_poses=None)
+    cam = dataclasses.replace(syn.street_cameras()[1], width=320, height=180, fx=170.0,
+                              fy=170.0, cx=160.0, cy=90.0)
+    a = O64.render_camera(sc, cam)
+    b = O64.render_camera(static, cam)
+    for k in ("out", "alpha", "depth"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def _one_actor_scene(seed=5, kind="camera"):
+    sc = syn.street_scene(2500, seed=seed, kind=kind, length=25.0)
+    sc.actor_of = np.zeros(sc.n, np.int32)
+    # a quarter turn about z and an integer shift: exact in float32
+    sc.actor_poses = syn.actor_pose(7.0, -3.0, math.pi / 2)[None].copy()
+    sc.actor_poses[0, [0, 1, 4, 5]] = [0.0, -1.0, 1.0, 0.0]
+    return sc
+
+
+def test_actor_pose_equals_moving_the_camera_into_its_frame(O64):
+    """Every Gaussian in one actor with pose T, seen by a camera at C, renders
+    as the static scene (the actor's frame) seen from T^-1 C, SH colour
+    included: the appearance turns with the actor."""
+    sc = _one_actor_scene()
+    T = sc.actor_poses[0]
+    static = dataclasses.replace(sc, actor_of=None, actor_poses=None)
+    cam = dataclasses.replace(syn.street_cameras()[0], width=320, height=214, fx=107.0,
+                              fy=107.0, cx=160.0, cy=107.0)
+    moved = dataclasses.replace(cam, c2w=_compose(_inverse(T), cam.c2w).astype(np.float32))
+    assert np.array_equal(moved.c2w.astype(np.float64), _compose(_inverse(T), cam.c2w))
+    a = O64.render_camera(sc, cam)
+    b = O64.render_camera(static, moved)
+    assert (a["alpha"] > 0).mean() > 0.05
+    for k in ("out", "alpha", "depth"):
+        assert np.abs(a[k] - b[k]).max() < 1e-9, k
+
+
+def test_actor_pose_equals_moving_the_lidar_into_its_frame(O64):
+    sc = _one_actor_scene(6, kind="lidar_sh")
+    T = sc.actor_poses[0]
+    static = dataclasses.replace(sc, actor_of=None, actor_poses=None)
+    L = syn.street_lidar(n_cols=128, n_beams=64, start_xyz=(8.0, -1.0, 1.8))
+    moved = dataclasses.replace(L, col_c2w=np.stack(
+        [_compose(_inverse(T), p) for p in L.col_c2w]).astype(np.float32))
+    a = O64.render_lidar(sc, L)
+    b = O64.render_lidar(static, moved)
+    assert (a["alpha"] > 0).mean() > 0.05
+    for k in ("out", "alpha", "depth"):
+        assert np.abs(a[k] - b[k]).max() < 1e-9, k
+
+
+def test_backward_with_actors_matches_central_differences(O64):
+    """Two actors with generic poses (rotation about a tilted axis): the
+    gradients in each Gaussian's own frame, SH direction term included."""
+    sc, cam = _fd_setup()
+    sc.actor_of = np.array([-1, 0, 1, 0] * 4, np.int32)
+    sc.actor_poses = np.stack([_compose(syn.actor_pose(0.3, -0.2, 0.4),
+                                        [1, 0, 0, 0, 0, math.cos(0.3), -math.sin(0.3), 0.1,
+                                         0, math.sin(0.3), math.cos(0.3), -0.2]),
+                               syn.actor_pose(-0.4, 0.5, -0.7)]).astype(np.float32)
+    opts = O64.opts(cutoffs=0, predicate=0, tile=64)
+    nr = cam.width * cam.height
+    rng = np.random.default_rng(3)
+    gr = rng.normal(size=(nr, 3)).astype(np.float32)
+    ga = rng.normal(size=nr).astype(np.float32)
+    gd = (0.05 * rng.normal(size=nr)).astype(np.float32)
+    G = O64.backward_camera(sc, cam, gr, ga, gd, opts)
+    for name, arr in (("means", sc.means), ("log_scales", sc.log_scales),
+                      ("quats", sc.quats), ("features", sc.features)):
+        flat = arr.reshape(-1)
+        gflat = G[name].reshape(-1)
+        for i in range(0, flat.size, max(1, flat.size // 16)):
+            x0 = float(flat[i])
+            h = 2.0 ** -14
+            flat[i] = np.float32(x0 + h)
+            hp = float(flat[i]) - x0
+            lp = _loss_cam(O64, sc, cam, opts, gr, ga, gd)
+            flat[i] = np.float32(x0 - h)
+            hm = x0 - float(flat[i])
+            lm = _loss_cam(O64, sc, cam, opts, gr, ga, gd)
             flat[i] = np.float32(x0)
             fd = (lp - lm) / (hp + hm)
             scale = max(1.0, np.abs(gflat).max())

@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -303,12 +304,14 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(sc, [c for _, c in cams], budget_s=20.0)
+            result["cpu_baseline_all_cores"] = cpu_baseline_all_cores([c for _, c in cams])
     if rank == 0 and not args.no_extra:
         del S, frames, ef
         result["lidar"] = lidar_workload(torch, sg, syn, min(args.steps, 100), 5)
         result["lidar"]["sh_features"] = lidar_workload(torch, sg, syn, min(args.steps, 100), 5,
                                                         kind="lidar_sh")
         result["train_step"] = train_step_workload(torch, sg, syn, min(args.steps, 30), 3)
+        result["actors"] = actors_workload(torch, sg, syn, min(args.steps, 100), 5)
     if not args.no_serving:
         from paper_2510_12901_gb300 import serve
         srv = serve.measure_serving(n_requests=args.serving_requests)
@@ -381,6 +384,49 @@ def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar"):
                            "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                            "evaluated_pairs": pairs}
     return out
+
+
+def actors_workload(torch, sg, syn, steps, warmup):
+    """The street camera step with dynamic actors: 10% of the 1M Gaussians
+    belong to 16 car-sized actors placed by their poses before projection.
+    One sg_render_cameras call per step, the two views on two streams."""
+    sc = syn.with_actors(syn.street_scene(N_GAUSS, seed=0, kind="camera"), n_actors=16,
+                         frac=0.1)
+    S = sg.Scene(sc)
+    cams = [(sg.Camera(c), c) for c in syn.street_cameras()]
+    outs = [[torch.empty((c.height, c.width, 3), device="cuda"),
+             torch.empty((c.height, c.width), device="cuda"),
+             torch.empty((c.height, c.width), device="cuda")] for _, c in cams]
+    frames = [sg.Frame() for _ in cams]
+    vs = [torch.cuda.Stream() for _ in cams]
+    views = sg.sg_camera_views([(ch.handle, c.c2w, f.handle, o[0].data_ptr(), o[1].data_ptr(),
+                                 o[2].data_ptr(), v.cuda_stream)
+                                for (ch, c), o, f, v in zip(cams, outs, frames, vs)])
+    opts = sg.sg_default_opts()
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        sg.sg_render_cameras(S.handle, views, opts, 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ev = torch.cuda.Event()
+    ev.record(stream)
+    for v in vs:
+        v.wait_event(ev)
+    for _ in range(steps):
+        sg.sg_render_cameras(S.handle, views, opts, 0)
+    for v in vs:
+        e = torch.cuda.Event()
+        e.record(v)
+        stream.wait_event(e)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rays = sum(c.width * c.height for _, c in cams)
+    return {"workload": "street camera scene with 16 car-sized actors holding 10% of the 1M "
+                        "Gaussians; fisheye 1920x1280 + pinhole 1920x1080 per step",
+            "value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms,
+            "steps": steps}
 
 
 def train_step_workload(torch, sg, syn, steps, warmup):
@@ -500,6 +546,49 @@ def _oracle_sample_time(O, sc, cam, n_rays, seed):
     t = time.perf_counter()
     O.render_camera(sc, cam, rays=rays)
     return time.perf_counter() - t
+
+
+_PW = {}
+
+
+def _pool_init(n_gauss):
+    from oracle import Oracle
+    from paper_2510_12901_gb300 import synthetic as syn
+    _PW["O"] = Oracle(64)
+    _PW["sc"] = syn.street_scene(n_gauss, seed=0, kind="camera")
+    _PW["cams"] = list(syn.street_cameras())
+
+
+def _pool_task(args):
+    view, n_rays, seed = args
+    return _oracle_sample_time(_PW["O"], _PW["sc"], _PW["cams"][view], n_rays, seed)
+
+
+def cpu_baseline_all_cores(cams, procs=None):
+    """The same oracle on every host core: one process per core, each with
+    its own copy of the scene, renders a share of the view's rays (so each
+    repeats the projection and sort, as the oracle does per call).  Per view,
+    two share sizes give the wall time's fixed and per-ray parts, and the
+    full view is extrapolated to rays / cores rays per process."""
+    import multiprocessing as mp
+    P = procs or os.cpu_count() or 1
+    total, used = 0.0, 0.0
+    with mp.get_context("spawn").Pool(P, initializer=_pool_init, initargs=(N_GAUSS,)) as pool:
+        pool.map(_pool_task, [(0, 10, 7 + i) for i in range(P)])     # warm every worker
+        for v, cam in enumerate(cams):
+            s1, s2 = 2000, 12000
+            w1 = max(pool.map(_pool_task, [(v, s1, 300 + 31 * v + i) for i in range(P)]))
+            w2 = max(pool.map(_pool_task, [(v, s2, 400 + 31 * v + i) for i in range(P)]))
+            used += (w1 + w2) * P
+            per_ray = max(w2 - w1, 0.0) / (s2 - s1)
+            fixed = max(w1 - per_ray * s1, 0.0)
+            total += fixed + per_ray * math.ceil(cam.width * cam.height / P)
+    rays = sum(c.width * c.height for c in cams)
+    return {"value": rays / total / 1e6, "unit": "Mrays/s", "cores": P, "kind": "oracle",
+            "sample": f"per view, {P} processes each render 2000 and 12000 random rays "
+                      f"(each process projects and sorts all {N_GAUSS} Gaussians); the "
+                      f"full view is extrapolated to its rays split over {P} processes "
+                      f"({used:.0f} s of CPU work); extrapolated seconds per step {total:.1f}"}
 
 
 def cpu_baseline(sc, cams, budget_s=20.0):

@@ -91,6 +91,33 @@ sg_status sg_update_scene(sg_scene scene, const sg_gaussians_desc *desc, void *s
 void sg_destroy_scene(sg_scene scene);
 int64_t sg_scene_size(sg_scene scene);
 
+/* Dynamic actors (Sec. 3.1, scene graph).  Gaussian i belongs to actor
+ * d_actor_of[i] (0..n_actors-1) or to the static background (-1).  An
+ * actor's Gaussians have their means and quaternions (as given to
+ * sg_create_scene / sg_update_scene) in the actor's frame; every render
+ * first maps them to the world with the actor's current pose (its SE(3) at
+ * the render's timestamp): mu_w = Ra mu + t, R_w = Ra R.  Their SH (colour
+ * or SH^l) are evaluated at the view direction expressed in the actor's
+ * frame, so the appearance turns with the object.  The backward returns the
+ * gradients in each Gaussian's own frame.
+ *
+ * sg_scene_set_actors: d_actor_of [n] int32 (device, copied; ignored when
+ *   n_actors = 0, which makes every Gaussian static again).  Every pose
+ *   starts as the identity.  The call waits for `stream` (renders still
+ *   queued on it may read the old lists) and checks the indices.  Errors:
+ *   SG_ERR_INVALID (NULL scene, n_actors < 0, NULL list, an index outside
+ *   -1..n_actors-1), SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_BUSY (during a capture).
+ * sg_scene_set_actor_poses: h_poses [n_actors,12] row-major [R | t], actor
+ *   to world (host memory, R a rotation).  The copy is queued on `stream`:
+ *   renders queued on `stream` after the call use the new poses.  Renders
+ *   on other streams must be ordered after it by the caller, and no render
+ *   may still be reading the previous poses when it runs.  Errors:
+ *   SG_ERR_INVALID (NULL argument, a scene without actors, a non-finite
+ *   entry), SG_ERR_CUDA. */
+sg_status sg_scene_set_actors(sg_scene scene, const int32_t *d_actor_of, int n_actors,
+                              void *stream);
+sg_status sg_scene_set_actor_poses(sg_scene scene, const float *h_poses, void *stream);
+
 /* ----------------------------------------------------------------------
  * Camera (Sec. 3.2: arbitrary camera models through the unscented
  * transform).  Pixel (i,j) is the ray through (i+0.5, j+0.5); OpenCV axes

@@ -435,7 +435,7 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
 __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, int64_t n,
                               int feature_kind, int sh_degree, int F, float ox, float oy,
                               float oz, const GRec *__restrict__ rec,
-                              const float *__restrict__ poses,
+                              const float *__restrict__ poses, ActorParams A,
                               const float *__restrict__ gacc, float *__restrict__ gm,
                               float *__restrict__ gls, float *__restrict__ gq,
                               float *__restrict__ gop, float *__restrict__ gf)
@@ -450,6 +450,25 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
         any = any || G[k] != 0.f;
     }
     if (!any) return;
+    // an actor's Gaussian: the accumulated gradients are in world
+    // coordinates (M_w = S^-1 (Ra R)^T, mu_w = Ra mu + t); in its own frame
+    // dL/dM_k becomes Ra^T dL/dM_k and dL/dmu becomes Ra^T dL/dmu
+    float Ra[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f}, ta[3] = {0.f, 0.f, 0.f};
+    const int ak = A.of ? A.of[g] : -1;
+    const bool actor = ak >= 0 && ak < A.n;
+    if (actor) {
+        const float *P = A.poses + 12 * ak;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) Ra[3 * i + j] = P[4 * i + j];
+            ta[i] = P[4 * i + 3];
+        }
+        for (int k = 0; k < 4; ++k) {     // the three rows of dL/dM and dL/dmu
+            const float x = G[3 * k], y = G[3 * k + 1], z = G[3 * k + 2];
+            G[3 * k] = Ra[0] * x + Ra[3] * y + Ra[6] * z;
+            G[3 * k + 1] = Ra[1] * x + Ra[4] * y + Ra[7] * z;
+            G[3 * k + 2] = Ra[2] * x + Ra[5] * y + Ra[8] * z;
+        }
+    }
     float q[4];
     for (int k = 0; k < 4; ++k) q[k] = planes[(Scene::kQuat + k) * pitch + g];
     const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
@@ -495,9 +514,16 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
             oy = P[7];
             oz = P[11];
         }
-        const float mx = planes[(Scene::kMean + 0) * pitch + g] - ox;
-        const float my = planes[(Scene::kMean + 1) * pitch + g] - oy;
-        const float mz = planes[(Scene::kMean + 2) * pitch + g] - oz;
+        // the view direction, in the Gaussian's own frame (Ra^T (mu_w - o))
+        const float lx = planes[(Scene::kMean + 0) * pitch + g];
+        const float ly = planes[(Scene::kMean + 1) * pitch + g];
+        const float lz = planes[(Scene::kMean + 2) * pitch + g];
+        const float wx = Ra[0] * lx + Ra[1] * ly + Ra[2] * lz + ta[0] - ox;
+        const float wy = Ra[3] * lx + Ra[4] * ly + Ra[5] * lz + ta[1] - oy;
+        const float wz = Ra[6] * lx + Ra[7] * ly + Ra[8] * lz + ta[2] - oz;
+        const float mx = actor ? Ra[0] * wx + Ra[3] * wy + Ra[6] * wz : wx;
+        const float my = actor ? Ra[1] * wx + Ra[4] * wy + Ra[7] * wz : wy;
+        const float mz = actor ? Ra[2] * wx + Ra[5] * wy + Ra[8] * wz : wz;
         const float dist = sqrtf(mx * mx + my * my + mz * mz);
         const float inv = 1.f / dist;
         const float dx = mx * inv, dy = my * inv, dz = mz * inv;
@@ -534,7 +560,7 @@ static sg_status finish(const Scene &sc, Frame &fr, const float o[3], const sg_g
     if (sc.n == 0) return SG_OK;
     k_param_grads<<<(unsigned)((sc.n + 127) / 128), 128, 0, st>>>(
         sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, sc.F, o[0], o[1], o[2],
-        (const GRec *)fr.rec.p, fr.d_lidar_poses,
+        (const GRec *)fr.rec.p, fr.d_lidar_poses, actor_params(sc),
         (const float *)fr.gacc.p, g.d_g_means, g.d_g_log_scales, g.d_g_quats, g.d_g_opacity,
         g.d_g_features);
     SG_LAUNCHED();

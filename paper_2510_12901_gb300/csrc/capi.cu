@@ -9,6 +9,8 @@
 #include <atomic>
 #include <new>
 
+#include <vector>
+
 #include "internal.h"
 
 namespace sg {
@@ -72,6 +74,14 @@ static void release(Buf &b)
 }
 
 // AoS [n, comps] -> planes
+// Flags (bad = 1) an actor index outside -1..n_actors-1.
+__global__ void k_check_actors(const int32_t *__restrict__ of, int64_t n, int n_actors,
+                               uint32_t *__restrict__ bad)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (of[i] < -1 || of[i] >= n_actors)) *bad = 1u;
+}
+
 __global__ void k_to_planes(const float *__restrict__ src, int64_t n, int comps, int plane0,
                             int64_t pitch, float *__restrict__ planes)
 {
@@ -406,7 +416,84 @@ void sg_destroy_scene(sg_scene scene)
 {
     if (!scene) return;
     cudaFree(scene->s.d_planes);
+    cudaFree(scene->s.d_actor_of);
+    cudaFree(scene->s.d_actor_poses);
     delete scene;
+}
+
+sg_status sg_scene_set_actors(sg_scene scene, const int32_t *d_actor_of, int n_actors,
+                              void *stream)
+{
+    if (!scene) { set_error("scene is NULL"); return SG_ERR_INVALID; }
+    if (capture_guard()) { set_error("sg_scene_set_actors during a graph capture"); return SG_ERR_BUSY; }
+    Scene &sc = scene->s;
+    if (n_actors < 0 || (n_actors > 0 && sc.n > 0 && !d_actor_of)) {
+        set_error("n_actors = %d with %s actor list", n_actors, d_actor_of ? "an" : "no");
+        return SG_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // the scene's old buffers may still be read by renders queued on `stream`
+    SG_CUDA(cudaStreamSynchronize(st));
+    cudaFree(sc.d_actor_of);
+    cudaFree(sc.d_actor_poses);
+    sc.d_actor_of = nullptr;
+    sc.d_actor_poses = nullptr;
+    sc.n_actors = 0;
+    scene->uid = next_uid();   // captured launch sequences of this scene are stale
+    if (n_actors == 0) return SG_OK;
+    int32_t *of = nullptr;
+    float *poses = nullptr;
+    uint32_t *bad = nullptr;
+    if (cudaMalloc(&of, sizeof(int32_t) * (size_t)(sc.n > 0 ? sc.n : 1)) != cudaSuccess ||
+        cudaMalloc(&poses, sizeof(float) * 12 * (size_t)n_actors) != cudaSuccess ||
+        cudaMalloc(&bad, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(of);
+        cudaFree(poses);
+        cudaFree(bad);
+        set_error("device allocation failed");
+        return SG_ERR_OOM;
+    }
+    std::vector<float> eye((size_t)n_actors * 12, 0.f);
+    for (int a = 0; a < n_actors; ++a) eye[12 * a] = eye[12 * a + 5] = eye[12 * a + 10] = 1.f;
+    uint32_t h_bad = 0;
+    cudaError_t e = cudaMemcpyAsync(poses, eye.data(), sizeof(float) * eye.size(),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && sc.n > 0)
+        e = cudaMemcpyAsync(of, d_actor_of, sizeof(int32_t) * (size_t)sc.n,
+                            cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess && sc.n > 0) {
+        k_check_actors<<<(unsigned)((sc.n + 255) / 256), 256, 0, st>>>(of, sc.n, n_actors, bad);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) count_launch();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(bad);
+    if (e != cudaSuccess || h_bad) {
+        cudaFree(of);
+        cudaFree(poses);
+        if (e != cudaSuccess) return cuda_status(e, "sg_scene_set_actors");
+        set_error("an actor index is outside -1..%d", n_actors - 1);
+        return SG_ERR_INVALID;
+    }
+    sc.d_actor_of = of;
+    sc.d_actor_poses = poses;
+    sc.n_actors = n_actors;
+    return SG_OK;
+}
+
+sg_status sg_scene_set_actor_poses(sg_scene scene, const float *h_poses, void *stream)
+{
+    if (!scene || !h_poses) { set_error("NULL scene or poses"); return SG_ERR_INVALID; }
+    Scene &sc = scene->s;
+    if (sc.n_actors == 0) { set_error("the scene has no actors"); return SG_ERR_INVALID; }
+    for (int i = 0; i < 12 * sc.n_actors; ++i)
+        if (!isfinite(h_poses[i])) { set_error("actor pose %d is not finite", i / 12); return SG_ERR_INVALID; }
+    SG_CUDA(cudaMemcpyAsync(sc.d_actor_poses, h_poses, sizeof(float) * 12 * (size_t)sc.n_actors,
+                            cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    return SG_OK;
 }
 
 int64_t sg_scene_size(sg_scene scene) { return scene ? scene->s.n : -1; }

@@ -65,7 +65,23 @@ struct Scene {
     int64_t pitch = 0;          // floats per plane (n rounded up to 32)
     float *plane(int k) const { return d_planes + (int64_t)k * pitch; }
     static constexpr int kMean = 0, kLogScale = 3, kQuat = 6, kOpacity = 10, kFeat = 11;
+    // dynamic actors: per-Gaussian actor index (-1 static) and the actors'
+    // poses [n_actors,12] (row-major [R | t], actor to world); none if n_actors = 0
+    int32_t *d_actor_of = nullptr;
+    float *d_actor_poses = nullptr;
+    int n_actors = 0;
 };
+
+// What a kernel needs of the actors (of = nullptr: every Gaussian static).
+struct ActorParams {
+    const int32_t *of;
+    const float *poses;
+    int n;
+};
+inline ActorParams actor_params(const Scene &s)
+{
+    return {s.n_actors > 0 ? s.d_actor_of : nullptr, s.d_actor_poses, s.n_actors};
+}
 
 struct Camera {
     int model = 0, width = 0, height = 0;

@@ -66,6 +66,49 @@ __device__ __forceinline__ Activated activate(const float *__restrict__ planes, 
     return a;
 }
 
+// Dynamic actors (Sec. 3.1 scene graph): the pose of Gaussian g's actor,
+// rows of [R | t] (actor to world); false for the static background.
+__device__ __forceinline__ bool actor_of(const ActorParams &A, int64_t g, float4 P[3])
+{
+    const int k = A.of ? A.of[g] : -1;
+    if (k < 0 || k >= A.n) return false;
+    const float4 *p = reinterpret_cast<const float4 *>(A.poses) + 3 * k;
+    P[0] = __ldg(p);
+    P[1] = __ldg(p + 1);
+    P[2] = __ldg(p + 2);
+    return true;
+}
+
+// Mean and rotation of an actor's Gaussian to the world: mu_w = Ra mu + t,
+// R_w = Ra R.
+__device__ __forceinline__ void to_world(const ActorParams &A, int64_t g, Activated &a)
+{
+    float4 P[3];
+    if (!actor_of(A, g, P)) return;
+    const float Ra[9] = {P[0].x, P[0].y, P[0].z, P[1].x, P[1].y, P[1].z, P[2].x, P[2].y, P[2].z};
+    const float m[3] = {a.mu[0], a.mu[1], a.mu[2]};
+    const float t[3] = {P[0].w, P[1].w, P[2].w};
+    float R[9];
+    for (int i = 0; i < 3; ++i) {
+        a.mu[i] = Ra[3 * i] * m[0] + Ra[3 * i + 1] * m[1] + Ra[3 * i + 2] * m[2] + t[i];
+        for (int j = 0; j < 3; ++j)
+            R[3 * i + j] = Ra[3 * i] * a.R[j] + Ra[3 * i + 1] * a.R[3 + j] + Ra[3 * i + 2] * a.R[6 + j];
+    }
+    for (int i = 0; i < 9; ++i) a.R[i] = R[i];
+}
+
+// A world direction in the frame of Gaussian g's actor (Ra^T d), where its
+// SH are defined; unchanged for the static background.
+__device__ __forceinline__ void dir_to_actor(const ActorParams &A, int64_t g, float d[3])
+{
+    float4 P[3];
+    if (!actor_of(A, g, P)) return;
+    const float x = d[0], y = d[1], z = d[2];
+    d[0] = P[0].x * x + P[1].x * y + P[2].x * z;
+    d[1] = P[0].y * x + P[1].y * y + P[2].y * z;
+    d[2] = P[0].z * x + P[1].z * y + P[2].z * z;
+}
+
 // Render record: M = S^-1 R^T (row i = column i of R over s_i) and the
 // cofactor weights f_i = s_i / (s_j s_k) (row i of cof(M) = f_i M_i).
 __device__ __forceinline__ void write_record(GRec *rec, int64_t g, const Activated &a,
@@ -167,7 +210,8 @@ __device__ __forceinline__ bool cam_point(const CamParams &C, const float *c2w, 
 #endif
 __global__ void __launch_bounds__(256, SG_PROJ_MINB)
 k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int feature_kind,
-                 int sh_degree, CamParams C, const RenderDesc *__restrict__ D, UTParams U,
+                 int sh_degree, ActorParams A, CamParams C, const RenderDesc *__restrict__ D,
+                 UTParams U,
                  GRec *__restrict__ rec,
                  float4 *__restrict__ rect_out, int4 *__restrict__ tiles_out,
                  float *__restrict__ depth_out, uint32_t *__restrict__ count_out,
@@ -179,6 +223,7 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     Activated a = activate(planes, pitch, g);
+    to_world(A, g, a);
     float dx = a.mu[0] - s_c2w[3], dy = a.mu[1] - s_c2w[7], dz = a.mu[2] - s_c2w[11];
     float dist = sqrtf(dx * dx + dy * dy + dz * dz);
     depth_out[g] = dist;
@@ -240,7 +285,9 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     float c[3];
     if (feature_kind == SG_FEATURES_SH) {
         float inv = 1.f / dist;
-        sh_eval(planes, pitch, g, sh_degree, dx * inv, dy * inv, dz * inv, c);
+        float d[3] = {dx * inv, dy * inv, dz * inv};
+        dir_to_actor(A, g, d);
+        sh_eval(planes, pitch, g, sh_degree, d[0], d[1], d[2], c);
         for (int ch = 0; ch < 3; ++ch) c[ch] = fmaxf(c[ch] + 0.5f, 0.f);   // colour offset, clamp
     } else {
         for (int ch = 0; ch < 3; ++ch) c[ch] = planes[(Scene::kFeat + ch) * pitch + g];
@@ -264,7 +311,7 @@ sg_status project_camera(const Scene &sc, const Camera &cam, const sg_render_opt
     if (sc.n == 0) return SG_OK;
     unsigned grid = (unsigned)((sc.n + 255) / 256);
     k_project_camera<<<grid, 256, 0, st>>>(
-        sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, C,
+        sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, actor_params(sc), C,
         (const RenderDesc *)fr.desc.p, U, (GRec *)fr.rec.p,
         (float4 *)fr.rect.p, (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p,
         (float2 *)fr.mean2d.p, (float4 *)fr.cov2d.p);
@@ -371,7 +418,7 @@ __device__ __forceinline__ int sat_count_wrap(const LidParams &L, int x0, int x1
 template <bool kSH>
 __global__ void __launch_bounds__(256)
 k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int sh_degree,
-                LidParams Lp, const RenderDesc *__restrict__ D, UTParams U,
+                ActorParams A, LidParams Lp, const RenderDesc *__restrict__ D, UTParams U,
                 int cull, GRec *__restrict__ rec, float4 *__restrict__ rect_out,
                 int4 *__restrict__ tiles_out, float *__restrict__ depth_out,
                 uint32_t *__restrict__ count_out, float2 *__restrict__ mean_out,
@@ -382,6 +429,7 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int 
     LidParams L = Lp;
     L.poses = D->poses;
     Activated a = activate(planes, pitch, g);
+    to_world(A, g, a);
     float xs0[3], az0;               // chi_0 = mu, also the depth key
     const int col0 = lidar_col(L, a.mu, xs0, &az0);
     const float r0 = sqrtf(xs0[0] * xs0[0] + xs0[1] * xs0[1] + xs0[2] * xs0[2]);
@@ -478,8 +526,9 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int 
         const float *P = L.poses + 12 * col0;
         const float vx = a.mu[0] - P[3], vy = a.mu[1] - P[7], vz = a.mu[2] - P[11];
         const float inv = 1.f / sqrtf(vx * vx + vy * vy + vz * vz);
-        float c[3];
-        sh_eval(planes, pitch, g, sh_degree, vx * inv, vy * inv, vz * inv, c);
+        float d[3] = {vx * inv, vy * inv, vz * inv}, c[3];
+        dir_to_actor(A, g, d);
+        sh_eval(planes, pitch, g, sh_degree, d[0], d[1], d[2], c);
         write_record(rec, g, a, c[0], c[1], c[2], rect, __uint_as_float((uint32_t)col0));
         return;
     }
@@ -510,7 +559,8 @@ sg_status project_lidar(const Scene &sc, const Lidar &Ld, const sg_render_opts &
     auto kern = sc.feature_kind == SG_FEATURES_LIDAR_SH ? k_project_lidar<true>
                                                          : k_project_lidar<false>;
     kern<<<grid, 256, 0, st>>>(
-        sc.d_planes, sc.pitch, sc.n, sc.sh_degree, L, (const RenderDesc *)fr.desc.p, U, o.cull,
+        sc.d_planes, sc.pitch, sc.n, sc.sh_degree, actor_params(sc), L,
+        (const RenderDesc *)fr.desc.p, U, o.cull,
         (GRec *)fr.rec.p, (float4 *)fr.rect.p,
         (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p, (float2 *)fr.mean2d.p,
         (float4 *)fr.cov2d.p);

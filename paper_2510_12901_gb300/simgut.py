@@ -99,6 +99,8 @@ _SIGNATURES = {
     "sg_default_opts": (sg_render_opts, []),
     "sg_frame_create": (C.c_int, [C.POINTER(_H)]),
     "sg_frame_destroy": (None, [_H]),
+    "sg_scene_set_actors": (C.c_int, [_H, _P, C.c_int, _P]),
+    "sg_scene_set_actor_poses": (C.c_int, [_H, C.POINTER(C.c_float), _P]),
     "sg_frame_set_capacity": (C.c_int, [_H, C.c_int64]),
     "sg_frame_dropped_pairs": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sg_render_camera": (C.c_int, [_H, _H, C.POINTER(C.c_float), C.POINTER(sg_render_opts), _H,
@@ -410,6 +412,28 @@ class Scene:
         self.handle = sg_create_scene(desc, _stream_ptr(stream))
         torch.cuda.current_stream().synchronize()
         self._dev = None   # the library holds its own copy
+        self.n_actors = 0
+        if getattr(src, "actor_of", None) is not None:
+            poses = np.asarray(src.actor_poses, np.float32).reshape(-1, 12)
+            self.set_actors(src.actor_of, poses.shape[0], stream)
+            self.set_actor_poses(poses, stream)
+
+    def set_actors(self, actor_of, n_actors, stream=None):
+        """actor_of: [n] actor index per Gaussian (-1 static); None with
+        n_actors = 0 makes every Gaussian static."""
+        torch = _torch()
+        a = None
+        if actor_of is not None:
+            a = torch.as_tensor(np.ascontiguousarray(actor_of, np.int32)).to("cuda")
+            torch.cuda.current_stream().synchronize()
+        _check(load().sg_scene_set_actors(self.handle, a.data_ptr() if a is not None else None,
+                                          int(n_actors), _P(_stream_ptr(stream))))
+        self.n_actors = int(n_actors)
+
+    def set_actor_poses(self, poses, stream=None):
+        p = np.ascontiguousarray(poses, np.float32).reshape(-1)
+        _check(load().sg_scene_set_actor_poses(
+            self.handle, p.ctypes.data_as(C.POINTER(C.c_float)), _P(_stream_ptr(stream))))
 
     def _desc(self, tensors=None):
         t = tensors or self._dev

@@ -66,7 +66,8 @@ def _structs(real):
                     ("t_min", C.c_float), ("near_dist", C.c_float),
                     ("ut_alpha", C.c_float), ("ut_beta", C.c_float),
                     ("ut_kappa", C.c_float), ("tile", C.c_int), ("pose_iters", C.c_int),
-                    ("cull", C.c_int), ("predicate", C.c_int), ("cutoffs", C.c_int)]
+                    ("cull", C.c_int), ("predicate", C.c_int), ("cutoffs", C.c_int),
+                    ("beam_divergence", C.c_float)]
 
     class Setup(C.Structure):
         _fields_ = [("n_tiles_x", C.c_int), ("n_tiles_y", C.c_int),

@@ -41,6 +41,7 @@ or_opts or_default_opts(void)
     o.cull = 1;
     o.predicate = 1;
     o.cutoffs = 1;
+    o.beam_divergence = 0.0f;     /* READING: delta is not stated; off by default */
     return o;
 }
 
@@ -132,6 +133,53 @@ static void gauss_world(const or_scene *sc, int64_t g, real mu[3], real R[9], re
         for (int j = 0; j < 3; ++j)
             R[3 * i + j] = Ra[3 * i] * Rl[j] + Ra[3 * i + 1] * Rl[3 + j] + Ra[3 * i + 2] * Rl[6 + j];
     }
+}
+
+/* Eq. 6: Sigma_hat = R diag(s^2) R^T + (delta |v|)^2 (I - v v^T / |v|^2)
+ *                  = R diag(s^2) R^T + delta^2 (|v|^2 I - v v^T),  v = mu - o. */
+static void smoothed_cov(const real R[9], const real s[3], const real v[3], real delta,
+                         real C[9])
+{
+    real vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2], d2 = delta * delta;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            real acc = 0;
+            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * s[k] * s[k] * R[3 * j + k];
+            C[3 * i + j] = acc + d2 * ((i == j ? vv : RL(0)) - v[i] * v[j]);
+        }
+}
+
+/* Lower Cholesky factor L (row-major) of a symmetric positive definite C. */
+static void cholesky3(const real C[9], real L[9])
+{
+    for (int i = 0; i < 9; ++i) L[i] = 0;
+    for (int j = 0; j < 3; ++j) {
+        real d = C[4 * j];
+        for (int k = 0; k < j; ++k) d -= L[3 * j + k] * L[3 * j + k];
+        L[4 * j] = sqrt(d);
+        for (int i = j + 1; i < 3; ++i) {
+            real a = C[3 * i + j];
+            for (int k = 0; k < j; ++k) a -= L[3 * i + k] * L[3 * j + k];
+            L[3 * i + j] = a / L[4 * j];
+        }
+    }
+}
+
+/* Inverse of a 3x3 matrix by its adjugate. */
+static void inverse3(const real C[9], real A[9])
+{
+    real c00 = C[4] * C[8] - C[5] * C[7], c01 = C[5] * C[6] - C[3] * C[8];
+    real c02 = C[3] * C[7] - C[4] * C[6];
+    real det = C[0] * c00 + C[1] * c01 + C[2] * c02;
+    A[0] = c00 / det;
+    A[1] = (C[2] * C[7] - C[1] * C[8]) / det;
+    A[2] = (C[1] * C[5] - C[2] * C[4]) / det;
+    A[3] = c01 / det;
+    A[4] = (C[0] * C[8] - C[2] * C[6]) / det;
+    A[5] = (C[2] * C[3] - C[0] * C[5]) / det;
+    A[6] = c02 / det;
+    A[7] = (C[1] * C[6] - C[0] * C[7]) / det;
+    A[8] = (C[0] * C[4] - C[1] * C[3]) / det;
 }
 
 static double fact(int k) { double f = 1; for (int i = 2; i <= k; ++i) f *= i; return f; }
@@ -709,7 +757,19 @@ void or_project_lidar(const or_scene *sc, const or_lidar *L,
         if (!(sigma >= amin)) continue;
         ctx.margin = RL(1e30);
         ctx.pmargin = RL(1e30);
-        int ok = or_unscented(o, mu, R, s, lidar_point_map, &ctx, 1, p->mean2d, p->cov2d);
+        int ok;
+        if (o->beam_divergence > 0.0f) {
+            /* Eq. 6: the UT of the smoothed covariance, sigma points along the
+             * columns of its Cholesky factor (READING) */
+            const float *T = L->col_c2w + 12 * ctx.col0;
+            real v[3] = {mu[0] - RL(T[3]), mu[1] - RL(T[7]), mu[2] - RL(T[11])}, Cs[9], Lc[9];
+            smoothed_cov(R, s, v, RL(o->beam_divergence), Cs);
+            cholesky3(Cs, Lc);
+            const real one[3] = {1, 1, 1};
+            ok = or_unscented(o, mu, Lc, one, lidar_point_map, &ctx, 1, p->mean2d, p->cov2d);
+        } else {
+            ok = or_unscented(o, mu, R, s, lidar_point_map, &ctx, 1, p->mean2d, p->cov2d);
+        }
         p->pmargin = ctx.pmargin;
         if (ctx.margin < p->vmargin) p->vmargin = ctx.margin;
         if (!ok) continue;
@@ -832,13 +892,19 @@ typedef struct {
     real dist;       /* |mu - o_cam| */
 } gauss_rt;
 
-static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3],
+static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3], real beam,
                           gauss_rt *G)
 {
     real R[9], s[3];
     gauss_world(sc, g, G->mu, R, NULL);
     for (int k = 0; k < 3; ++k) s[k] = exp(RL(sc->log_scales[3 * g + k]));
-    inv_cov(R, s, G->A);
+    if (beam > 0) {   /* Eq. 6: the response of the smoothed covariance, opacity unchanged */
+        real v[3] = {G->mu[0] - ocam[0], G->mu[1] - ocam[1], G->mu[2] - ocam[2]}, Cs[9];
+        smoothed_cov(R, s, v, beam, Cs);
+        inverse3(Cs, G->A);
+    } else {
+        inv_cov(R, s, G->A);
+    }
     G->sigma = RL(sc->opacity[g]);
     G->clampc[0] = G->clampc[1] = G->clampc[2] = 0;
     if (sc->feature_kind == OR_FEAT_SH || sc->feature_kind == OR_FEAT_LIDAR_SH) {
@@ -1049,7 +1115,8 @@ static const real *origin_of(const real *ocam, int per_gauss, int64_t g)
 }
 
 static int render_common(const or_scene *sc, const or_opts *o, const or_proj *P,
-                         const real *ocam, int ocam_per_gauss, int ntx, int nty, int wrap,
+                         const real *ocam, int ocam_per_gauss, real beam, int ntx, int nty,
+                         int wrap,
                          int bruteforce, const int64_t *rays, int64_t n_rays,
                          int64_t n_total, ray_fn rf, const void *rctx, or_ray *out,
                          /* backward (optional) */
@@ -1060,7 +1127,7 @@ static int render_common(const or_scene *sc, const or_opts *o, const or_proj *P,
     int64_t nr = n_rays < 0 ? n_total : n_rays;
     gauss_rt *GR = malloc(sizeof(gauss_rt) * (size_t)(sc->n > 0 ? sc->n : 1));
     for (int64_t g = 0; g < sc->n; ++g)
-        gauss_prepare(sc, g, origin_of(ocam, ocam_per_gauss, g), &GR[g]);
+        gauss_prepare(sc, g, origin_of(ocam, ocam_per_gauss, g), beam, &GR[g]);
     int64_t nt = (int64_t)ntx * nty;
     uint32_t *ids = NULL, *ranges = NULL;
     or_pair *pr = NULL;
@@ -1138,7 +1205,7 @@ int or_render_camera(const or_scene *sc, const or_camera *cam, const or_opts *o,
     or_project_camera(sc, cam, &S, o, P);
     real ocam[3] = {RL(cam->c2w[3]), RL(cam->c2w[7]), RL(cam->c2w[11])};
     cam_rctx rc = {cam, S.theta_max, o->tile, S.n_tiles_x};
-    render_common(sc, o, P, ocam, 0, S.n_tiles_x, S.n_tiles_y, 0, bruteforce, rays,
+    render_common(sc, o, P, ocam, 0, 0, S.n_tiles_x, S.n_tiles_y, 0, bruteforce, rays,
                   n_rays, (int64_t)cam->width * cam->height, cam_ray_fn, &rc, out,
                   NULL, NULL);
     free(P);
@@ -1195,7 +1262,8 @@ int or_render_lidar(const or_scene *sc, const or_lidar *L, const or_opts *o,
     lidar_ray_tiles(L, &S, bt, ct);
     lid_rctx rc = {L, &S, bt, ct};
     real *ocam = lidar_sh_origins(sc, L, P);
-    render_common(sc, o, P, ocam, 1, S.n_theta, L->n_elev_tiles, 1, bruteforce, rays,
+    render_common(sc, o, P, ocam, 1, RL(o->beam_divergence), S.n_theta, L->n_elev_tiles, 1,
+                  bruteforce, rays,
                   n_rays, (int64_t)L->n_beams * L->n_cols, lid_ray_fn, &rc, out, NULL,
                   NULL);
     free(ocam);
@@ -1300,6 +1368,7 @@ static void bw_ray(void *vctx, int64_t r, const or_ray *ray, const contrib *rec,
 
 /* Map gradients w.r.t. (A, mu, sigma, feature) to the raw parameters. */
 static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
+                      const real *ocam, int ocam_per_gauss, real beam,
                       real *gm, real *gls, real *gq, real *gop, real *gf)
 {
     const int sh = sc->feature_kind == OR_FEAT_SH || sc->feature_kind == OR_FEAT_LIDAR_SH;
@@ -1312,34 +1381,76 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
         for (int k = 0; k < 3; ++k) s[k] = exp(RL(sc->log_scales[3 * g + k]));
         /* actor: A_w = Ra A Ra^T and mu_w = Ra mu + t, so the gradients in the
          * Gaussian's own frame are Ra^T dL/dA_w Ra and Ra^T dL/dmu_w */
-        real Ra[9], GA[9], gmw[3];
+        real Ra[9], GA[9], gmw[3], gmu_w[3];
         actor_pose(sc, g, Ra, NULL);
+        const real *GW = B->gA + 9 * g;
+        for (int i = 0; i < 3; ++i) gmu_w[i] = B->gmu[3 * g + i];
+        real Hw[9];
+        if (beam > 0) {
+            /* Eq. 6: A = Sigma_hat^-1, so dL/dSigma_hat = -A S A with S the
+             * symmetric part of dL/dA; Sigma_hat = Sigma + delta^2 (|v|^2 I -
+             * v v^T) adds delta^2 (2 v tr(H) - 2 H v) to dL/dmu (v = mu - o) */
+            const real *A = G->A;
+            real S[9], T[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) S[3 * i + j] = RL(0.5) * (GW[3 * i + j] + GW[3 * j + i]);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    T[3 * i + j] = S[3 * i] * A[j] + S[3 * i + 1] * A[3 + j] + S[3 * i + 2] * A[6 + j];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    Hw[3 * i + j] = -(A[3 * i] * T[j] + A[3 * i + 1] * T[3 + j] + A[3 * i + 2] * T[6 + j]);
+            const real *o = origin_of(ocam, ocam_per_gauss, g);
+            real v[3] = {G->mu[0] - o[0], G->mu[1] - o[1], G->mu[2] - o[2]};
+            real tr = Hw[0] + Hw[4] + Hw[8], d2 = beam * beam;
+            for (int i = 0; i < 3; ++i)
+                gmu_w[i] += d2 * (RL(2) * v[i] * tr -
+                                  RL(2) * (Hw[3 * i] * v[0] + Hw[3 * i + 1] * v[1] + Hw[3 * i + 2] * v[2]));
+        } else {
+            for (int i = 0; i < 9; ++i) Hw[i] = GW[i];
+        }
         {
-            const real *GW = B->gA + 9 * g;
+            /* Hw (dL/dA_w, or dL/dSigma_w with the filter) in the Gaussian's frame */
             real T[9];
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j)
-                    T[3 * i + j] = GW[3 * i] * Ra[j] + GW[3 * i + 1] * Ra[3 + j] +
-                                   GW[3 * i + 2] * Ra[6 + j];
+                    T[3 * i + j] = Hw[3 * i] * Ra[j] + Hw[3 * i + 1] * Ra[3 + j] +
+                                   Hw[3 * i + 2] * Ra[6 + j];
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j)
                     GA[3 * i + j] = Ra[i] * T[j] + Ra[3 + i] * T[3 + j] + Ra[6 + i] * T[6 + j];
-            const real *m = B->gmu + 3 * g;
+            const real *m = gmu_w;
             for (int i = 0; i < 3; ++i) gmw[i] = Ra[i] * m[0] + Ra[3 + i] * m[1] + Ra[6 + i] * m[2];
         }
-        /* A = sum_k u_k r_k r_k^T, u_k = 1/s_k^2 = exp(-2 ls_k), r_k = column k */
         real gR[9] = {0};
-        for (int k = 0; k < 3; ++k) {
-            real rk[3] = {R[k], R[3 + k], R[6 + k]};
-            real u = RL(1) / (s[k] * s[k]);
-            real dLdu = 0;
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) dLdu += GA[3 * i + j] * rk[i] * rk[j];
-            gls[3 * g + k] += dLdu * RL(-2) * u;
-            for (int m = 0; m < 3; ++m) {
-                real acc = 0;
-                for (int j = 0; j < 3; ++j) acc += (GA[3 * m + j] + GA[3 * j + m]) * rk[j];
-                gR[3 * m + k] += u * acc;
+        if (beam > 0) {
+            /* Sigma = sum_k s_k^2 r_k r_k^T, GA = dL/dSigma (symmetric) */
+            for (int k = 0; k < 3; ++k) {
+                real rk[3] = {R[k], R[3 + k], R[6 + k]}, s2 = s[k] * s[k];
+                real q2 = 0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) q2 += GA[3 * i + j] * rk[i] * rk[j];
+                gls[3 * g + k] += RL(2) * s2 * q2;
+                for (int m = 0; m < 3; ++m) {
+                    real acc = 0;
+                    for (int j = 0; j < 3; ++j) acc += (GA[3 * m + j] + GA[3 * j + m]) * rk[j];
+                    gR[3 * m + k] += s2 * acc;
+                }
+            }
+        } else {
+            /* A = sum_k u_k r_k r_k^T, u_k = 1/s_k^2 = exp(-2 ls_k), r_k = column k */
+            for (int k = 0; k < 3; ++k) {
+                real rk[3] = {R[k], R[3 + k], R[6 + k]};
+                real u = RL(1) / (s[k] * s[k]);
+                real dLdu = 0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) dLdu += GA[3 * i + j] * rk[i] * rk[j];
+                gls[3 * g + k] += dLdu * RL(-2) * u;
+                for (int m = 0; m < 3; ++m) {
+                    real acc = 0;
+                    for (int j = 0; j < 3; ++j) acc += (GA[3 * m + j] + GA[3 * j + m]) * rk[j];
+                    gR[3 * m + k] += u * acc;
+                }
             }
         }
         /* R(q_hat): partial derivatives of the rotation matrix entries */
@@ -1385,7 +1496,8 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
 }
 
 static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *P,
-                           const real *ocam, int ocam_per_gauss, int ntx, int nty, int wrap,
+                           const real *ocam, int ocam_per_gauss, real beam, int ntx, int nty,
+                           int wrap,
                            int64_t n_total, const int64_t *rays, int64_t n_rays, ray_fn rf,
                            const void *rctx, int lidar,
                            const float *ga, const float *gb, const float *gc,
@@ -1394,7 +1506,7 @@ static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *
 {
     gauss_rt *GR = malloc(sizeof(gauss_rt) * (size_t)(sc->n > 0 ? sc->n : 1));
     for (int64_t g = 0; g < sc->n; ++g)
-        gauss_prepare(sc, g, origin_of(ocam, ocam_per_gauss, g), &GR[g]);
+        gauss_prepare(sc, g, origin_of(ocam, ocam_per_gauss, g), beam, &GR[g]);
     bw_ctx B;
     memset(&B, 0, sizeof(B));
     B.sc = sc; B.GR = GR; B.lidar = lidar;
@@ -1405,9 +1517,9 @@ static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *
     B.gfeat = calloc((size_t)sc->n * 3 + 1, sizeof(real));
     int64_t nr = n_rays < 0 ? n_total : n_rays;
     or_ray *out = malloc(sizeof(or_ray) * (size_t)(nr > 0 ? nr : 1));
-    render_common(sc, o, P, ocam, ocam_per_gauss, ntx, nty, wrap, 0, rays, n_rays, n_total,
-                  rf, rctx, out, bw_ray, &B);
-    bw_finish(sc, GR, &B, gm, gls, gq, gop, gf);
+    render_common(sc, o, P, ocam, ocam_per_gauss, beam, ntx, nty, wrap, 0, rays, n_rays,
+                  n_total, rf, rctx, out, bw_ray, &B);
+    bw_finish(sc, GR, &B, ocam, ocam_per_gauss, beam, gm, gls, gq, gop, gf);
     free(out);
     free(B.gA); free(B.gmu); free(B.gsig); free(B.gfeat);
     free(GR);
@@ -1425,7 +1537,7 @@ int or_backward_camera(const or_scene *sc, const or_camera *cam, const or_opts *
     or_project_camera(sc, cam, &S, o, P);
     real ocam[3] = {RL(cam->c2w[3]), RL(cam->c2w[7]), RL(cam->c2w[11])};
     cam_rctx rc = {cam, S.theta_max, o->tile, S.n_tiles_x};
-    backward_common(sc, o, P, ocam, 0, S.n_tiles_x, S.n_tiles_y, 0,
+    backward_common(sc, o, P, ocam, 0, 0, S.n_tiles_x, S.n_tiles_y, 0,
                     (int64_t)cam->width * cam->height, rays, n_rays, cam_ray_fn, &rc, 0, g_rgb,
                     g_alpha, g_depth, NULL, gm, gls, gq, gop, gf);
     free(P);
@@ -1447,7 +1559,7 @@ int or_backward_lidar(const or_scene *sc, const or_lidar *L, const or_opts *o,
     lidar_ray_tiles(L, &S, bt, ct);
     lid_rctx rc = {L, &S, bt, ct};
     real *ocam = lidar_sh_origins(sc, L, P);
-    backward_common(sc, o, P, ocam, 1, S.n_theta, L->n_elev_tiles, 1,
+    backward_common(sc, o, P, ocam, 1, RL(o->beam_divergence), S.n_theta, L->n_elev_tiles, 1,
                     (int64_t)L->n_beams * L->n_cols, rays, n_rays, lid_ray_fn, &rc, 1, g_range,
                     g_int,
                     g_drop, g_alpha, gm, gls, gq, gop, gf);

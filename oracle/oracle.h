@@ -80,6 +80,13 @@ typedef struct {
     int cull;         /* LiDAR ray-based culling on/off */
     int predicate;    /* per-ray extent test (1); 0 only for smooth FD checks */
     int cutoffs;      /* alpha_min / t_min / alpha_max cutoffs (1); 0 for FD */
+    /* LiDAR beam divergence delta (radians, 0 = off; Sec. 3.3, Eq. 6): a
+     * LiDAR Gaussian's covariance becomes Sigma + (delta |mu - o|)^2
+     * (I - d d^T), d = (mu - o)/|mu - o| from the origin o of the column
+     * pose that sees the mean, without rescaling the opacity.  The UT then
+     * takes its sigma points along the columns of the Cholesky factor of
+     * that covariance. */
+    float beam_divergence;
 } or_opts;
 
 /* Sensor set-up, computed once per sensor (double in both builds). */

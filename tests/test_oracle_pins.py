@@ -779,3 +779,100 @@ def test_backward_with_actors_matches_central_differences(O64):
             fd = (lp - lm) / (hp + hm)
             scale = max(1.0, np.abs(gflat).max())
             assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])
+
+
+# ------------------------------------------------------------ beam divergence
+def _rot_wxyz(q):
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = np.asarray(q, np.float64) / np.linalg.norm(q)
+    return Rotation.from_quat([x, y, z, w]).as_matrix()
+
+
+def test_beam_divergence_response_brute_force(O64):
+    """Eq. 6 on single Gaussians near a moving LiDAR: for rays around the
+    mean, alpha = sigma exp(-D^2/2) with D^2 the minimum over the ray of the
+    Mahalanobis distance under Sigma + (delta r)^2 (I - d d^T), r and d from
+    the origin of the column pose that sees the mean, found by brute force
+    along the ray; the opacity is not rescaled (alpha = sigma on the ray
+    through the mean)."""
+    L = syn.street_lidar(n_cols=128, n_beams=64)
+    delta = 0.02
+    opts = O64.opts(cull=0, predicate=0, beam_divergence=delta)
+    rng = np.random.default_rng(8)
+    for trial in range(3):
+        beam, col = int(rng.integers(10, 54)), int(rng.integers(0, 128))
+        o, d, _, _ = O64.lidar_ray(L, beam, col)
+        sc = syn.tiny_scene(n=1)
+        sc.means[0] = o + rng.uniform(2.0, 5.0) * d
+        sc.log_scales[0] = rng.normal(-2.5, 0.3, 3)
+        sc.quats[0] = rng.normal(size=4)
+        sc.opacity[0] = 0.7
+        sc.feature_kind = syn.FEATURES_LIDAR
+        P, _ = O64.project_lidar(sc, L, opts)
+        oc = L.col_c2w[P["pose_col"][0]][[3, 7, 11]].astype(np.float64)
+        mu = sc.means[0].astype(np.float64)
+        R = _rot_wxyz(sc.quats[0])
+        S = R @ np.diag(np.exp(2.0 * sc.log_scales[0].astype(np.float64))) @ R.T
+        v = mu - oc
+        r = np.linalg.norm(v)
+        Sh = S + (delta * r) ** 2 * (np.eye(3) - np.outer(v, v) / r ** 2)
+        Ai = np.linalg.inv(Sh)
+        rays = [beam * L.n_cols + (col + dc) % L.n_cols for dc in (-1, 0, 1)] + \
+               [(beam + db) * L.n_cols + col for db in (-1, 1)]
+        res = O64.render_lidar(sc, L, opts, rays=rays)
+        for ray, rr in zip(rays, res):
+            ro, rd, _, _ = O64.lidar_ray(L, ray // L.n_cols, ray % L.n_cols)
+            t = np.linspace(0.0, 8.0, 200001)
+            x = ro[None, :] + t[:, None] * rd[None, :] - mu[None, :]
+            d2 = np.einsum("ni,ij,nj->n", x, Ai, x)
+            k = int(np.argmin(d2))
+            tt = np.linspace(t[max(k - 1, 0)], t[min(k + 1, len(t) - 1)], 20001)
+            x = ro[None, :] + tt[:, None] * rd[None, :] - mu[None, :]
+            a = min(0.99, float(np.float32(0.7)) * math.exp(-0.5 * np.einsum(
+                "ni,ij,nj->n", x, Ai, x).min()))
+            assert abs(rr["alpha"] - a) < 1e-7, (trial, ray, rr["alpha"], a)
+        assert abs(res[1]["alpha"] - float(np.float32(0.7))) < 1e-3   # the central ray
+
+
+def test_backward_beam_divergence_matches_central_differences(O64):
+    L = syn.street_lidar(n_cols=64, n_beams=64)
+    L.n_elev_tiles = 1
+    L.max_rays_per_tile = 64 * 64
+    rng = np.random.default_rng(12)
+    n = 10
+    sc = syn.street_scene(n, seed=13, kind="lidar", length=20.0)
+    ang = rng.uniform(-np.pi, np.pi, n)
+    rad = rng.uniform(6, 10, n)
+    sc.means[:] = np.stack([30 + rad * np.cos(ang), rad * np.sin(ang),
+                            rng.uniform(0, 2.5, n)], 1)
+    sc.log_scales[:] = rng.normal(-1.4, 0.2, (n, 3))
+    sc.opacity[:] = rng.uniform(0.2, 0.8, n)
+    opts = O64.opts(cutoffs=0, predicate=0, cull=0, beam_divergence=0.03)
+    nr = L.n_beams * L.n_cols
+    g = [rng.normal(size=nr).astype(np.float32) * s for s in (0.02, 1.0, 1.0, 1.0)]
+    G = O64.backward_lidar(sc, L, *g, opts=opts)
+
+    def loss():
+        r = O64.render_lidar(sc, L, opts)
+        rg, it, dr = O64.lidar_decode(r)
+        return (rg * g[0]).sum() + (it * g[1]).sum() + (dr * g[2]).sum() + (r["alpha"] * g[3]).sum()
+
+    base = O64.render_lidar(sc, L, O64.opts(cutoffs=0, predicate=0, cull=0))
+    assert np.abs(O64.render_lidar(sc, L, opts)["alpha"] - base["alpha"]).max() > 1e-2
+    for name, arr in (("means", sc.means), ("log_scales", sc.log_scales),
+                      ("quats", sc.quats), ("opacity", sc.opacity)):
+        flat = arr.reshape(-1)
+        gflat = G[name].reshape(-1)
+        for i in range(0, flat.size, max(1, flat.size // 10)):
+            x0 = float(flat[i])
+            h = 2.0 ** -14
+            flat[i] = np.float32(x0 + h)
+            hp = float(flat[i]) - x0
+            lp = loss()
+            flat[i] = np.float32(x0 - h)
+            hm = x0 - float(flat[i])
+            lm = loss()
+            flat[i] = np.float32(x0)
+            fd = (lp - lm) / (hp + hm)
+            scale = max(1.0, np.abs(gflat).max())
+            assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])

@@ -310,6 +310,8 @@ def run_ours(args):
         result["lidar"] = lidar_workload(torch, sg, syn, min(args.steps, 100), 5)
         result["lidar"]["sh_features"] = lidar_workload(torch, sg, syn, min(args.steps, 100), 5,
                                                         kind="lidar_sh")
+        result["lidar"]["beam_divergence"] = lidar_workload(torch, sg, syn, min(args.steps, 100),
+                                                            5, beam=0.003)
         result["train_step"] = train_step_workload(torch, sg, syn, min(args.steps, 30), 3)
         result["actors"] = actors_workload(torch, sg, syn, min(args.steps, 100), 5)
     if not args.no_serving:
@@ -331,7 +333,7 @@ def _work(view):
         return None
 
 
-def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar"):
+def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar", beam=0.0):
     """The LiDAR sweep configuration: 2M LiDAR Gaussians, 128 beams x 2048
     columns, per-column poses over a 0.1 s sweep; range, intensity, drop and
     alpha per ray.  CUDA events over `steps` sweeps, inputs resident.
@@ -344,7 +346,7 @@ def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar"):
     frames = [sg.Frame(), sg.Frame()]
     for f in frames:
         sg.sg_frame_set_timing(f.handle, 1)
-    opts = sg.sg_default_opts()
+    opts = sg.sg_default_opts(beam_divergence=beam)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
@@ -370,13 +372,15 @@ def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar"):
     rays = L.n_beams * L.n_cols
     feats = ("intensity, ray-drop logits" if kind == "lidar" else
              "degree-3 SH^l of intensity and ray-drop logits, 48 floats")
+    if beam > 0:
+        feats += f"; beam divergence {beam * 1e3:g} mrad (Eq. 6 smoothing)"
     out = {"workload": f"street LiDAR scene: 2M Gaussians ({feats}), 128-beam "
                        "x 2048-column sweep, per-column poses over 0.1 s; range + intensity + drop",
            "value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_sweep": ms,
            "steps": steps, "stages_ms": {"project": st[0], "depth_sort_offsets": st[1],
                                          "bin_tile_sort_ranges": st[2], "render": st[3]}}
     pairs = _work("lidar")
-    if pairs and kind == "lidar":
+    if pairs and kind == "lidar" and beam == 0:
         pk = peaks()
         peak = SM_COUNT * FP32_LANES * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         ach = pairs * FLOP_PER_PAIR / (st[3] * 1e-3) / 1e12

@@ -163,6 +163,12 @@ typedef struct {
     int pose_iters;   /* LiDAR: fixed-point iterations choosing each sigma
                          point's column pose (0..8) */
     int cull;         /* LiDAR: ray-based culling (App. B) on/off */
+    float beam_divergence; /* LiDAR: beam divergence delta in radians, 0 (default) = off,
+                              at most 0.1.  Eq. 6: a LiDAR Gaussian's covariance becomes
+                              Sigma + (delta r)^2 (I - d d^T), r and d the distance and
+                              direction from the origin of the column pose that sees its
+                              mean; the opacity is not rescaled.  The UT takes its sigma
+                              points along the Cholesky columns of that covariance. */
 } sg_render_opts;
 sg_render_opts sg_default_opts(void);
 

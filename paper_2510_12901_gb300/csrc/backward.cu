@@ -435,7 +435,7 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
 __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, int64_t n,
                               int feature_kind, int sh_degree, int F, float ox, float oy,
                               float oz, const GRec *__restrict__ rec,
-                              const float *__restrict__ poses, ActorParams A,
+                              const float *__restrict__ poses, ActorParams A, float beam,
                               const float *__restrict__ gacc, float *__restrict__ gm,
                               float *__restrict__ gls, float *__restrict__ gq,
                               float *__restrict__ gop, float *__restrict__ gf)
@@ -462,7 +462,63 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
             for (int j = 0; j < 3; ++j) Ra[3 * i + j] = P[4 * i + j];
             ta[i] = P[4 * i + 3];
         }
-        for (int k = 0; k < 4; ++k) {     // the three rows of dL/dM and dL/dmu
+    }
+    // Beam divergence (Eq. 6): the record holds M of the smoothed covariance
+    // (rows m_k orthogonal), and the loss depends on M only through
+    // A = M^T M = Sigma_hat^-1, so dL/dM = 2 M S with S = sym(dL/dA):
+    // S = M^-1 dL/dM / 2, M^-1 = [m_k / |m_k|^2].  Then dL/dSigma_hat =
+    // H = -A S A, and Sigma_hat = Sigma + beam^2 (|v|^2 I - v v^T), v = mu - o,
+    // adds beam^2 (2 v tr(H) - 2 H v) to dL/dmu.
+    float H[9];
+    if (beam > 0.f) {
+        const GRec &rc = rec[g];
+        const float m[9] = {rc.m0.x, rc.m0.y, rc.m0.z, rc.m1.x, rc.m1.y, rc.m1.z,
+                            rc.m2.x, rc.m2.y, rc.m2.z};
+        float S[9], T[9], Am[9];
+        for (int i = 0; i < 9; ++i) S[i] = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            const float mk2 = m[3 * k] * m[3 * k] + m[3 * k + 1] * m[3 * k + 1] +
+                              m[3 * k + 2] * m[3 * k + 2];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) S[3 * i + j] += 0.5f * m[3 * k + i] / mk2 * G[3 * k + j];
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j) {
+                const float a = 0.5f * (S[3 * i + j] + S[3 * j + i]);
+                S[3 * i + j] = S[3 * j + i] = a;
+            }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                Am[3 * i + j] = m[i] * m[j] + m[3 + i] * m[3 + j] + m[6 + i] * m[6 + j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                T[3 * i + j] = S[3 * i] * Am[j] + S[3 * i + 1] * Am[3 + j] + S[3 * i + 2] * Am[6 + j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                H[3 * i + j] = -(Am[3 * i] * T[j] + Am[3 * i + 1] * T[3 + j] + Am[3 * i + 2] * T[6 + j]);
+        const float *P = poses + 12 * __float_as_uint(rc.feat.w);
+        float v[3];
+        for (int i = 0; i < 3; ++i) {
+            const float mw = Ra[3 * i] * planes[(Scene::kMean + 0) * pitch + g] +
+                             Ra[3 * i + 1] * planes[(Scene::kMean + 1) * pitch + g] +
+                             Ra[3 * i + 2] * planes[(Scene::kMean + 2) * pitch + g] + ta[i];
+            v[i] = mw - P[4 * i + 3];
+        }
+        const float tr = H[0] + H[4] + H[8], b2 = beam * beam;
+        for (int i = 0; i < 3; ++i)
+            G[9 + i] += b2 * (2.f * v[i] * tr -
+                              2.f * (H[3 * i] * v[0] + H[3 * i + 1] * v[1] + H[3 * i + 2] * v[2]));
+        if (actor) {    // H in the Gaussian's own frame: Ra^T H Ra
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    T[3 * i + j] = H[3 * i] * Ra[j] + H[3 * i + 1] * Ra[3 + j] + H[3 * i + 2] * Ra[6 + j];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    H[3 * i + j] = Ra[i] * T[j] + Ra[3 + i] * T[3 + j] + Ra[6 + i] * T[6 + j];
+        }
+    }
+    if (actor) {
+        for (int k = beam > 0.f ? 3 : 0; k < 4; ++k) {   // the rows of dL/dM, then dL/dmu
             const float x = G[3 * k], y = G[3 * k + 1], z = G[3 * k + 2];
             G[3 * k] = Ra[0] * x + Ra[3] * y + Ra[6] * z;
             G[3 * k + 1] = Ra[1] * x + Ra[4] * y + Ra[7] * z;
@@ -476,15 +532,28 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
     const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
                         2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
                         2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
-    // M_k = r_k / s_k (r_k = column k of R): dL/dls_k = -G_k . M_k,
-    // dL/dr_k = G_k / s_k
     float gR[9];
-    for (int k = 0; k < 3; ++k) {
-        const float s = expf(planes[(Scene::kLogScale + k) * pitch + g]);
-        const float rk[3] = {R[k], R[3 + k], R[6 + k]};
-        const float Gk[3] = {G[3 * k], G[3 * k + 1], G[3 * k + 2]};
-        if (gls) gls[3 * g + k] += -(Gk[0] * rk[0] + Gk[1] * rk[1] + Gk[2] * rk[2]) / s;
-        for (int i = 0; i < 3; ++i) gR[3 * i + k] = Gk[i] / s;
+    if (beam > 0.f) {
+        // Sigma = sum_k s_k^2 r_k r_k^T: dL/dls_k = 2 s_k^2 r_k^T H r_k,
+        // dL/dr_k = 2 s_k^2 H r_k
+        for (int k = 0; k < 3; ++k) {
+            const float s = expf(planes[(Scene::kLogScale + k) * pitch + g]), s2 = s * s;
+            const float rk[3] = {R[k], R[3 + k], R[6 + k]};
+            float Hr[3];
+            for (int i = 0; i < 3; ++i) Hr[i] = H[3 * i] * rk[0] + H[3 * i + 1] * rk[1] + H[3 * i + 2] * rk[2];
+            if (gls) gls[3 * g + k] += 2.f * s2 * (rk[0] * Hr[0] + rk[1] * Hr[1] + rk[2] * Hr[2]);
+            for (int i = 0; i < 3; ++i) gR[3 * i + k] = 2.f * s2 * Hr[i];
+        }
+    } else {
+        // M_k = r_k / s_k (r_k = column k of R): dL/dls_k = -G_k . M_k,
+        // dL/dr_k = G_k / s_k
+        for (int k = 0; k < 3; ++k) {
+            const float s = expf(planes[(Scene::kLogScale + k) * pitch + g]);
+            const float rk[3] = {R[k], R[3 + k], R[6 + k]};
+            const float Gk[3] = {G[3 * k], G[3 * k + 1], G[3 * k + 2]};
+            if (gls) gls[3 * g + k] += -(Gk[0] * rk[0] + Gk[1] * rk[1] + Gk[2] * rk[2]) / s;
+            for (int i = 0; i < 3; ++i) gR[3 * i + k] = Gk[i] / s;
+        }
     }
     if (gq) {
         // partial derivatives of R(w,x,y,z) (entries row-major), times 2
@@ -554,13 +623,13 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
         for (int k = 0; k < 3; ++k) gm[3 * g + k] += gmu[k];
 }
 
-static sg_status finish(const Scene &sc, Frame &fr, const float o[3], const sg_grads &g,
-                        cudaStream_t st)
+static sg_status finish(const Scene &sc, Frame &fr, const float o[3], float beam,
+                        const sg_grads &g, cudaStream_t st)
 {
     if (sc.n == 0) return SG_OK;
     k_param_grads<<<(unsigned)((sc.n + 127) / 128), 128, 0, st>>>(
         sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, sc.F, o[0], o[1], o[2],
-        (const GRec *)fr.rec.p, fr.d_lidar_poses, actor_params(sc),
+        (const GRec *)fr.rec.p, fr.d_lidar_poses, actor_params(sc), beam,
         (const float *)fr.gacc.p, g.d_g_means, g.d_g_log_scales, g.d_g_quats, g.d_g_opacity,
         g.d_g_features);
     SG_LAUNCHED();
@@ -618,7 +687,7 @@ sg_status backward_camera(const Scene &sc, const Camera &cam, Frame &fr, const f
         g_depth, (float *)fr.gacc.p);
     SG_LAUNCHED();
     const float o[3] = {fr.c2w[3], fr.c2w[7], fr.c2w[11]};
-    return finish(sc, fr, o, g, st);
+    return finish(sc, fr, o, 0.f, g, st);
 }
 
 sg_status backward_lidar(const Scene &sc, const Lidar &L, Frame &fr, const float *g_range,
@@ -648,7 +717,7 @@ sg_status backward_lidar(const Scene &sc, const Lidar &L, Frame &fr, const float
         SG_LAUNCHED();
     }
     const float o[3] = {0.f, 0.f, 0.f};
-    return finish(sc, fr, o, g, st);
+    return finish(sc, fr, o, fr.opts.beam_divergence, g, st);
 }
 
 }  // namespace sg

@@ -141,7 +141,8 @@ static bool opts_ok(const sg_render_opts *o)
     if (!(o->alpha_min > 0.f && o->alpha_min < 1.f) || !(o->alpha_max > 0.f && o->alpha_max <= 1.f) ||
         !(o->t_min >= 0.f && o->t_min < 1.f) || !(o->near_dist > 0.f) ||
         !(o->ut_alpha > 0.f) || !(o->ut_kappa > -3.f) || !isfinite(o->ut_beta) ||
-        o->pose_iters < 0 || o->pose_iters > 8) {
+        o->pose_iters < 0 || o->pose_iters > 8 ||
+        !(o->beam_divergence >= 0.f && o->beam_divergence <= 0.1f)) {
         set_error("render options out of range");
         return false;
     }
@@ -363,6 +364,7 @@ sg_render_opts sg_default_opts(void)
     o.ut_kappa = 0.0f;
     o.pose_iters = 2;
     o.cull = 1;
+    o.beam_divergence = 0.0f;   // the paper does not state delta: off by default
     return o;
 }
 

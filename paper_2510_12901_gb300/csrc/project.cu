@@ -20,6 +20,7 @@ struct CamParams {
 struct UTParams {
     float lam_gamma, w0m, w0c, wi;   // spread sqrt(n+lambda) and the weights
     float alpha_min, near_dist;
+    float beam;                      // LiDAR beam divergence (radians), 0 = off
 };
 
 static UTParams ut_params(const sg_render_opts &o)
@@ -34,6 +35,7 @@ static UTParams ut_params(const sg_render_opts &o)
     u.wi = 1.0f / (2.0f * (n + lam));
     u.alpha_min = o.alpha_min;
     u.near_dist = o.near_dist;
+    u.beam = o.beam_divergence;
     return u;
 }
 
@@ -413,9 +415,84 @@ __device__ __forceinline__ int sat_count_wrap(const LidParams &L, int x0, int x1
     return sat_count(L, a, L.A - 1, y0, y1) + sat_count(L, 0, b, y0, y1);
 }
 
-// kSH: the scene carries SH^l features (evaluated here, as for camera
-// colour); a template so that the raw-feature path keeps its registers.
-template <bool kSH>
+// Beam divergence (Sec. 3.3, Eq. 6): the smoothed covariance
+// Sigma + delta^2 (|v|^2 I - v v^T) of a LiDAR Gaussian with world rotation
+// R and scales s, v = mu - o (o the origin of mu's column pose).
+__device__ __forceinline__ void smoothed_cov(const float R[9], const float s[3],
+                                             const float v[3], float delta, float C[9])
+{
+    const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2], d2 = delta * delta;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * (s[k] * s[k]) * R[3 * j + k];
+            C[3 * i + j] = acc + d2 * ((i == j ? vv : 0.f) - v[i] * v[j]);
+        }
+}
+
+// Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
+// (each zeroes one off-diagonal entry; Golub & Van Loan, Sec. 8.5): C is
+// overwritten, Q gets the eigenvectors as columns, lam the eigenvalues.
+__device__ __forceinline__ void jacobi_eigen3(float C[9], float Q[9], float lam[3])
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Q[i] = (i % 4 == 0) ? 1.f : 0.f;
+    for (int sweep = 0; sweep < 6; ++sweep) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int p = r == 2 ? 1 : 0, q = r == 0 ? 1 : 2;
+            const float apq = C[3 * p + q];
+            if (fabsf(apq) <= 1e-30f) continue;
+            const float theta = (C[3 * q + q] - C[3 * p + p]) / (2.f * apq);
+            const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            const float c = 1.f / sqrtf(t * t + 1.f), sn = t * c;
+            // C <- J^T C J, J the rotation in the (p, q) plane
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float ckp = C[3 * k + p], ckq = C[3 * k + q];
+                C[3 * k + p] = c * ckp - sn * ckq;
+                C[3 * k + q] = sn * ckp + c * ckq;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float cpk = C[3 * p + k], cqk = C[3 * q + k];
+                C[3 * p + k] = c * cpk - sn * cqk;
+                C[3 * q + k] = sn * cpk + c * cqk;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float qkp = Q[3 * k + p], qkq = Q[3 * k + q];
+                Q[3 * k + p] = c * qkp - sn * qkq;
+                Q[3 * k + q] = sn * qkp + c * qkq;
+            }
+        }
+    }
+    lam[0] = fmaxf(C[0], 1e-30f);
+    lam[1] = fmaxf(C[4], 1e-30f);
+    lam[2] = fmaxf(C[8], 1e-30f);
+}
+
+// Lower Cholesky factor (row-major) of a symmetric positive definite 3x3.
+__device__ __forceinline__ void cholesky3(const float C[9], float Lc[9])
+{
+    const float l00 = sqrtf(fmaxf(C[0], 1e-30f));
+    const float l10 = C[3] / l00, l20 = C[6] / l00;
+    const float l11 = sqrtf(fmaxf(C[4] - l10 * l10, 1e-30f));
+    const float l21 = (C[7] - l20 * l10) / l11;
+    const float l22 = sqrtf(fmaxf(C[8] - l20 * l20 - l21 * l21, 1e-30f));
+    Lc[0] = l00; Lc[1] = 0.f; Lc[2] = 0.f;
+    Lc[3] = l10; Lc[4] = l11; Lc[5] = 0.f;
+    Lc[6] = l20; Lc[7] = l21; Lc[8] = l22;
+}
+
+// kSH: the scene carries SH^l features; kBeam: beam divergence on (the UT
+// runs over the smoothed covariance's Cholesky columns, and the record
+// holds its eigen-frame: M = diag(lam)^-1/2 Q^T, the form the compositing
+// takes).  Templates, so that the plain path keeps its registers.
+template <bool kSH, bool kBeam>
 __global__ void __launch_bounds__(256)
 k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int sh_degree,
                 ActorParams A, LidParams Lp, const RenderDesc *__restrict__ D, UTParams U,
@@ -439,6 +516,24 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int 
     int4 tl = make_int4(0, -1, 0, -1);
     float2 m2 = make_float2(0.f, 0.f);
     float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+    // sigma-point directions: the columns of R diag(s), or of the Cholesky
+    // factor of the smoothed covariance
+    float Dm[9];
+    if constexpr (kBeam) {
+        const float *P = L.poses + 12 * col0;
+        const float v[3] = {a.mu[0] - P[3], a.mu[1] - P[7], a.mu[2] - P[11]};
+        float Cs[9], lam[3];
+        smoothed_cov(a.R, a.s, v, U.beam, Cs);
+        cholesky3(Cs, Dm);
+        jacobi_eigen3(Cs, a.R, lam);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.s[k] = sqrtf(lam[k]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) Dm[3 * r + i] = a.s[i] * a.R[3 * r + i];
+    }
     if (a.sigma >= U.alpha_min) {
         float az[7], el[7];
         bool ok = true;
@@ -451,7 +546,7 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int 
             const float sg = ((p - 1) & 1) ? -1.f : 1.f;
             float x[3], xs[3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) x[r] = a.mu[r] + sg * U.lam_gamma * a.s[i] * a.R[3 * r + i];
+            for (int r = 0; r < 3; ++r) x[r] = a.mu[r] + sg * U.lam_gamma * Dm[3 * r + i];
             lidar_col(L, x, xs, &az[p]);
             const float r = sqrtf(xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2]);
             ok = ok && (r > U.near_dist);
@@ -532,9 +627,10 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int 
         write_record(rec, g, a, c[0], c[1], c[2], rect, __uint_as_float((uint32_t)col0));
         return;
     }
+    // the column of mu's pose goes into the record (the backward's origin)
     write_record(rec, g, a, planes[(Scene::kFeat + 0) * pitch + g],
                  planes[(Scene::kFeat + 1) * pitch + g], planes[(Scene::kFeat + 2) * pitch + g],
-                 rect);
+                 rect, __uint_as_float((uint32_t)col0));
 }
 
 sg_status project_lidar(const Scene &sc, const Lidar &Ld, const sg_render_opts &o, Frame &fr,
@@ -556,8 +652,9 @@ sg_status project_lidar(const Scene &sc, const Lidar &Ld, const sg_render_opts &
     UTParams U = ut_params(o);
     if (sc.n == 0) return SG_OK;
     unsigned grid = (unsigned)((sc.n + 255) / 256);
-    auto kern = sc.feature_kind == SG_FEATURES_LIDAR_SH ? k_project_lidar<true>
-                                                         : k_project_lidar<false>;
+    const bool sh = sc.feature_kind == SG_FEATURES_LIDAR_SH, beam = o.beam_divergence > 0.f;
+    auto kern = sh ? (beam ? k_project_lidar<true, true> : k_project_lidar<true, false>)
+                   : (beam ? k_project_lidar<false, true> : k_project_lidar<false, false>);
     kern<<<grid, 256, 0, st>>>(
         sc.d_planes, sc.pitch, sc.n, sc.sh_degree, actor_params(sc), L,
         (const RenderDesc *)fr.desc.p, U, o.cull,

@@ -42,7 +42,8 @@ class sg_gaussians_desc(C.Structure):
 class sg_render_opts(C.Structure):
     _fields_ = [("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float),
                 ("near_dist", C.c_float), ("ut_alpha", C.c_float), ("ut_beta", C.c_float),
-                ("ut_kappa", C.c_float), ("pose_iters", C.c_int), ("cull", C.c_int)]
+                ("ut_kappa", C.c_float), ("pose_iters", C.c_int), ("cull", C.c_int),
+                ("beam_divergence", C.c_float)]
 
 
 class sg_grads(C.Structure):

@@ -200,3 +200,32 @@ def test_autograd_function_matches_oracle(sg, O64):
     (rgb - tgt).abs().mean().backward()
     assert all(torch.isfinite(p.grad).all() for p in params.values())
     assert params["features"].grad.abs().sum() > 0
+
+
+def test_lidar_backward_beam_divergence(sg, O64):
+    """Gradients through the smoothed covariance of Eq. 6 (delta = 0.01):
+    dL/dA -> dL/dSigma_hat -> (log-scales, quaternion) and the mean's term
+    from |v|^2 I - v v^T."""
+    import torch
+    L = syn.street_lidar(n_cols=256)
+    sc = syn.street_scene(1500, seed=3, kind="lidar", length=60.0)
+    delta = 0.01
+    orc = O64.render_lidar(sc, L, O64.opts(beam_divergence=delta))
+    rng = np.random.default_rng(5)
+    ok = ~par.ambiguous_rays(orc, lidar=True)
+    n = len(orc)
+    g = [(0.05 * rng.normal(size=n)).astype(np.float32)] + \
+        [rng.normal(size=n).astype(np.float32) for _ in range(3)]
+    for a in g:
+        a[~ok] = 0
+    Go = O64.backward_lidar(sc, L, *g, opts=O64.opts(beam_divergence=delta))
+    S, Ld = sg.Scene(sc), sg.Lidar(L)
+    out = sg.render_lidar(S, Ld, L.col_c2w, sg.sg_default_opts(beam_divergence=delta))
+    grads = {k: torch.zeros(s, device="cuda") for k, s in
+             zip(NAMES, [(sc.n, 3), (sc.n, 3), (sc.n, 4), (sc.n,), (sc.n, 3)])}
+    ups = [torch.from_numpy(np.ascontiguousarray(u, np.float32)).cuda() for u in g]
+    gs = sg.sg_grads(*[grads[k].data_ptr() for k in NAMES])
+    sg.sg_backward_lidar(S.handle, out["frame"].handle, *[u.data_ptr() for u in ups], gs,
+                         torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    compare_grads({k: v.cpu().numpy() for k, v in grads.items()}, Go, "beam")

@@ -226,3 +226,19 @@ def test_gaussians_straddling_the_azimuth_seam(sg, O32, O64):
 
 def _n_theta(O, L):
     return O.lidar_setup(L)["n_theta"]
+
+
+@pytest.mark.parametrize("delta", [0.003, 0.02])
+def test_beam_divergence_every_ray(sg, O64, delta):
+    """Eq. 6 smoothing (covariance widened across the beam by (delta r)^2,
+    opacity kept): every ray of a 128 x 256 sweep against the oracle with
+    the same delta, for raw and SH^l features."""
+    for kind in ("lidar", "lidar_sh"):
+        sc, L = toy(kind=kind, seed=3)
+        g = gpu_render(sg, sc, L, sg.sg_default_opts(beam_divergence=delta))
+        orc = O64.render_lidar(sc, L, O64.opts(beam_divergence=delta))
+        info = par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
+                                      max_excluded=0.02, label=f"beam-{delta}-{kind}")
+        plain = O64.render_lidar(sc, L)
+        # the filter changes the picture
+        assert np.abs(orc["alpha"] - plain["alpha"]).max() > 1e-2, info

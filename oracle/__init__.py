@@ -53,7 +53,8 @@ def _structs(real):
     class Camera(C.Structure):
         _fields_ = [("model", C.c_int), ("width", C.c_int), ("height", C.c_int),
                     ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
-                    ("cy", C.c_float), ("k", C.c_float * 4), ("c2w", C.c_float * 12)]
+                    ("cy", C.c_float), ("k", C.c_float * 4), ("c2w", C.c_float * 12),
+                    ("row_c2w", C.c_void_p)]
 
     class Lidar(C.Structure):
         _fields_ = [("n_beams", C.c_int), ("n_cols", C.c_int), ("az0_deg", C.c_float),
@@ -154,6 +155,11 @@ class Oracle:
         c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
         c.k[:] = [float(v) for v in np.asarray(cam.k, np.float32)]
         c.c2w[:] = [float(v) for v in np.asarray(cam.c2w, np.float32)]
+        rows = getattr(cam, "row_c2w", None)
+        if rows is not None:
+            rows = np.ascontiguousarray(rows, np.float32).reshape(cam.height, 12)
+            c.row_c2w = self._p(rows)
+            c._keep = rows
         return c
 
     def lidar(self, L):

@@ -300,11 +300,16 @@ double or_fisheye_theta_max(const float k[4])
 
 /* World point -> pixel.  Returns 0 when the point is outside the model's
  * domain (READING: pinhole z > near; fisheye |x| > near and theta <= max). */
-static int cam_project_margin(const or_camera *cam, double theta_max,
-                              const or_opts *o, const real xw[3], real uv[2],
-                              real *margin)
+/* The camera-to-world pose of pixel row `row` (the global pose without a
+ * rolling shutter). */
+static const float *row_pose(const or_camera *cam, int row)
 {
-    const float *M = cam->c2w;
+    return cam->row_c2w ? cam->row_c2w + 12 * row : cam->c2w;
+}
+
+static int cam_project_pose(const or_camera *cam, const float *M, double theta_max,
+                            const or_opts *o, const real xw[3], real uv[2], real *margin)
+{
     real d0 = xw[0] - RL(M[3]), d1 = xw[1] - RL(M[7]), d2 = xw[2] - RL(M[11]);
     /* x_c = R^T (x - t) */
     real x = RL(M[0]) * d0 + RL(M[4]) * d1 + RL(M[8]) * d2;
@@ -341,10 +346,38 @@ static int cam_project_margin(const or_camera *cam, double theta_max,
     return 1;
 }
 
+/* Rolling shutter: the row whose pose sees x (fixed-point iteration from
+ * the middle row, see or_camera); *pmargin gets the smallest distance (in
+ * rows) of an iterate to a row boundary.  Global shutter: row 0, no
+ * iteration. */
+static int cam_row_of(const or_camera *cam, double theta_max, const or_opts *o,
+                      const real x[3], real *pmargin)
+{
+    if (!cam->row_c2w) return 0;
+    int row = cam->height / 2;
+    for (int it = 0; it < o->pose_iters; ++it) {
+        real t[2];
+        if (!cam_project_pose(cam, row_pose(cam, row), theta_max, o, x, t, NULL)) break;
+        real f = t[1], fr = f - floor(f), m = fr < RL(0.5) ? fr : RL(1) - fr;
+        if (pmargin && m < *pmargin) *pmargin = m;
+        int r = f < RL(0) ? 0 : (f >= RL(cam->height) ? cam->height - 1 : (int)floor(f));
+        row = r;
+    }
+    return row;
+}
+
+static int cam_project_margin(const or_camera *cam, double theta_max,
+                              const or_opts *o, const real xw[3], real uv[2],
+                              real *margin, real *pmargin)
+{
+    int row = cam_row_of(cam, theta_max, o, xw, pmargin);
+    return cam_project_pose(cam, row_pose(cam, row), theta_max, o, xw, uv, margin);
+}
+
 int or_camera_project(const or_camera *cam, double theta_max, const or_opts *o,
                       const real xw[3], real uv[2])
 {
-    return cam_project_margin(cam, theta_max, o, xw, uv, NULL);
+    return cam_project_margin(cam, theta_max, o, xw, uv, NULL, NULL);
 }
 
 /* Pixel centre (px+0.5, py+0.5) -> world ray (double).  Fisheye inverse by
@@ -375,7 +408,7 @@ int or_camera_ray(const or_camera *cam, double theta_max, int px, int py,
         }
         dc[2] = cos(th);
     }
-    const float *M = cam->c2w;
+    const float *M = row_pose(cam, py);   /* the ray of row py: that row's pose */
     for (int i = 0; i < 3; ++i)
         d[i] = (double)M[4 * i] * dc[0] + (double)M[4 * i + 1] * dc[1] +
                (double)M[4 * i + 2] * dc[2];
@@ -612,13 +645,15 @@ int or_sat_count_wrap(const or_sensor_setup *S, int A, int x0, int x1, int y0, i
 /* Projection of all Gaussians: UT conic -> extent -> tiles -> counts  */
 /* ------------------------------------------------------------------ */
 
-typedef struct { const or_camera *cam; double theta_max; const or_opts *o; real margin; } cam_ctx;
+typedef struct {
+    const or_camera *cam; double theta_max; const or_opts *o; real margin; real pmargin;
+} cam_ctx;
 
 static int cam_point_map(void *vctx, const real x[3], int idx, real y[2])
 {
     (void)idx;
     cam_ctx *c = vctx;
-    return cam_project_margin(c->cam, c->theta_max, c->o, x, y, &c->margin);
+    return cam_project_margin(c->cam, c->theta_max, c->o, x, y, &c->margin, &c->pmargin);
 }
 
 /* READING of the extent ("culling as in 3DGS", Sec. 3.2): the box of the
@@ -638,14 +673,32 @@ void or_project_camera(const or_scene *sc, const or_camera *cam,
         gauss_world(sc, g, mu, R, NULL);
         for (int k = 0; k < 3; ++k) s[k] = exp(RL(sc->log_scales[3 * g + k]));
         real sigma = RL(sc->opacity[g]), amin = RL(o->alpha_min);
-        real dx = mu[0] - RL(cam->c2w[3]), dy = mu[1] - RL(cam->c2w[7]), dz = mu[2] - RL(cam->c2w[11]);
+        /* the depth key and SH origin: the camera centre, or with a rolling
+         * shutter the origin of the row that sees the mean */
+        real cm = RL(1e30);
+        int row0 = cam_row_of(cam, S->theta_max, o, mu, &cm);
+        const float *C0 = row_pose(cam, row0);
+        real dx = mu[0] - RL(C0[3]), dy = mu[1] - RL(C0[7]), dz = mu[2] - RL(C0[11]);
         /* sort key: 3DGS-style keys carry float32 depth bits (Sec. 3.2 "as in
          * 3DGS"), so the key is the distance rounded to float */
         p->depth = RL((float)sqrt(dx * dx + dy * dy + dz * dz));
+        p->pose_col = row0;
+        if (cam->row_c2w) {
+            p->cmargin = cm;
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                int rr = row0 + sgn;
+                if (rr < 0 || rr >= cam->height) continue;
+                const float *Cn = row_pose(cam, rr);
+                real ex = mu[0] - RL(Cn[3]), ey = mu[1] - RL(Cn[7]), ez = mu[2] - RL(Cn[11]);
+                real kd = fabs(RL((float)sqrt(ex * ex + ey * ey + ez * ez)) - p->depth);
+                if (kd > p->kdelta) p->kdelta = kd;
+            }
+        }
         p->vmargin = fabs(sigma - amin) / amin;
         if (!(sigma >= amin)) continue;
-        cam_ctx ctx = {cam, S->theta_max, o, RL(1e30)};
+        cam_ctx ctx = {cam, S->theta_max, o, RL(1e30), RL(1e30)};
         int ok = or_unscented(o, mu, R, s, cam_point_map, &ctx, 0, p->mean2d, p->cov2d);
+        if (cam->row_c2w) p->pmargin = ctx.pmargin;
         if (ctx.margin < p->vmargin) p->vmargin = ctx.margin;
         if (!ok) continue;
         p->ut = 1;
@@ -1196,6 +1249,20 @@ static int cam_ray_fn(const void *vctx, int64_t r, real o[3], real d[3], real *r
     return 0;
 }
 
+/* Per-Gaussian SH origins of a camera render: the camera centre, or with a
+ * rolling shutter the origin of the row whose pose sees the mean. */
+static real *cam_sh_origins(const or_scene *sc, const or_camera *cam, const or_proj *P)
+{
+    real *o = calloc((size_t)(sc->n > 0 ? sc->n : 1) * 3, sizeof(real));
+    for (int64_t g = 0; g < sc->n; ++g) {
+        const float *T = row_pose(cam, P[g].pose_col);
+        o[3 * g] = RL(T[3]);
+        o[3 * g + 1] = RL(T[7]);
+        o[3 * g + 2] = RL(T[11]);
+    }
+    return o;
+}
+
 int or_render_camera(const or_scene *sc, const or_camera *cam, const or_opts *o,
                      int bruteforce, const int64_t *rays, int64_t n_rays, or_ray *out)
 {
@@ -1203,11 +1270,12 @@ int or_render_camera(const or_scene *sc, const or_camera *cam, const or_opts *o,
     or_camera_setup(cam, o, &S);
     or_proj *P = malloc(sizeof(or_proj) * (size_t)(sc->n > 0 ? sc->n : 1));
     or_project_camera(sc, cam, &S, o, P);
-    real ocam[3] = {RL(cam->c2w[3]), RL(cam->c2w[7]), RL(cam->c2w[11])};
+    real *ocam = cam_sh_origins(sc, cam, P);
     cam_rctx rc = {cam, S.theta_max, o->tile, S.n_tiles_x};
-    render_common(sc, o, P, ocam, 0, 0, S.n_tiles_x, S.n_tiles_y, 0, bruteforce, rays,
+    render_common(sc, o, P, ocam, 1, 0, S.n_tiles_x, S.n_tiles_y, 0, bruteforce, rays,
                   n_rays, (int64_t)cam->width * cam->height, cam_ray_fn, &rc, out,
                   NULL, NULL);
+    free(ocam);
     free(P);
     or_setup_free(&S);
     return 0;
@@ -1535,11 +1603,12 @@ int or_backward_camera(const or_scene *sc, const or_camera *cam, const or_opts *
     or_camera_setup(cam, o, &S);
     or_proj *P = malloc(sizeof(or_proj) * (size_t)(sc->n > 0 ? sc->n : 1));
     or_project_camera(sc, cam, &S, o, P);
-    real ocam[3] = {RL(cam->c2w[3]), RL(cam->c2w[7]), RL(cam->c2w[11])};
+    real *ocam = cam_sh_origins(sc, cam, P);
     cam_rctx rc = {cam, S.theta_max, o->tile, S.n_tiles_x};
-    backward_common(sc, o, P, ocam, 0, 0, S.n_tiles_x, S.n_tiles_y, 0,
+    backward_common(sc, o, P, ocam, 1, 0, S.n_tiles_x, S.n_tiles_y, 0,
                     (int64_t)cam->width * cam->height, rays, n_rays, cam_ray_fn, &rc, 0, g_rgb,
                     g_alpha, g_depth, NULL, gm, gls, gq, gop, gf);
+    free(ocam);
     free(P);
     or_setup_free(&S);
     return 0;

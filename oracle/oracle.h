@@ -59,6 +59,13 @@ typedef struct {
     float fx, fy, cx, cy;
     float k[4];
     float c2w[12];            /* row-major [R | t], OpenCV axes */
+    /* Rolling shutter (Sec. 3.2, time-dependent effects): [height,12]
+     * camera-to-world pose of every pixel row (the row's exposure time), or
+     * NULL for a global shutter (c2w).  A point's pixel comes from the pose
+     * of the row it falls in, found as for the LiDAR columns: start from the
+     * middle row's pose, then pose_iters times take the pose of the row the
+     * point projects to (clamped to the image). */
+    const float *row_c2w;
 } or_camera;
 
 typedef struct {

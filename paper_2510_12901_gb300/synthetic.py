@@ -78,6 +78,7 @@ class Camera:
     cy: float
     k: np.ndarray            # [4] float32, OpenCV fisheye k1..k4 (unused for pinhole)
     c2w: np.ndarray          # [12] float32, row-major 3x4 [R | t], OpenCV axes
+    row_c2w: Optional[np.ndarray] = None   # [height, 12] per-row poses (rolling shutter)
 
 
 @dataclasses.dataclass
@@ -369,6 +370,22 @@ def street_lidar(n_beams: int = 128, n_cols: int = 2048, seed: int = 2,
     if static:
         poses[:] = poses[0]
     return Lidar(elev, n_cols, -180.0, poses, max_rays_per_tile, n_elev_tiles)
+
+
+def rolling_shutter(cam: Camera, speed: float = 15.0, readout_s: float = 0.03,
+                    yaw_rate: float = 0.1) -> Camera:
+    """A copy of `cam` with a rolling shutter: row r is exposed at
+    t_r = ((r + 0.5) / height - 0.5) readout_s around the frame's time, while
+    the vehicle drives along +x at `speed` and turns about +z at `yaw_rate`."""
+    base = np.asarray(cam.c2w, np.float64).reshape(3, 4)
+    rows = np.empty((cam.height, 12), np.float32)
+    for r in range(cam.height):
+        t = ((r + 0.5) / cam.height - 0.5) * readout_s
+        c, s_ = math.cos(yaw_rate * t), math.sin(yaw_rate * t)
+        Rz = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+        P = np.concatenate([Rz @ base[:, :3], (base[:, 3] + np.array([speed * t, 0.0, 0.0]))[:, None]], 1)
+        rows[r] = P.reshape(12)
+    return dataclasses.replace(cam, row_c2w=rows)
 
 
 def random_street_pose_camera(rng, cam: Camera) -> Camera:

@@ -876,3 +876,91 @@ def test_backward_beam_divergence_matches_central_differences(O64):
             fd = (lp - lm) / (hp + hm)
             scale = max(1.0, np.abs(gflat).max())
             assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])
+
+
+# ------------------------------------------------------------ rolling shutter
+def test_rolling_shutter_with_equal_rows_is_the_global_shutter(O64):
+    sc = syn.street_scene(3000, seed=14, length=30.0)
+    cam = dataclasses.replace(syn.street_cameras()[1], width=200, height=120, fx=110.0,
+                              fy=110.0, cx=100.0, cy=60.0)
+    rs = dataclasses.replace(cam, row_c2w=np.tile(cam.c2w, (cam.height, 1)))
+    a = O64.render_camera(sc, cam)
+    b = O64.render_camera(sc, rs)
+    for k in ("out", "alpha", "depth"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_rolling_shutter_ray_is_the_ray_of_its_rows_pose(O64):
+    """A pixel of row y renders what a global-shutter camera with row y's
+    pose renders there (brute force, no extent test; Gaussians at
+    well-separated depths so that every order agrees)."""
+    rng = np.random.default_rng(15)
+    n = 40
+    sc = syn.tiny_scene(n=n)
+    sc.means[:] = np.stack([rng.uniform(4, 40, n), rng.uniform(-3, 3, n), rng.uniform(0.5, 3, n)], 1)
+    sc.means[:, 0] = np.sort(sc.means[:, 0]) + np.arange(n) * 0.5
+    sc.log_scales[:] = rng.normal(-0.7, 0.2, (n, 3))
+    sc.opacity[:] = rng.uniform(0.2, 0.9, n)
+    cam = dataclasses.replace(syn.street_cameras()[1], width=160, height=90, fx=90.0, fy=90.0,
+                              cx=80.0, cy=45.0)
+    rs = syn.rolling_shutter(cam, speed=20.0, readout_s=0.05, yaw_rate=0.5)
+    opts = O64.opts(predicate=0)
+    pix = [(int(x), int(y)) for x, y in zip(rng.integers(0, 160, 12), rng.integers(0, 90, 12))]
+    got = O64.render_camera(sc, rs, opts, bruteforce=True, rays=[y * 160 + x for x, y in pix])
+    for (x, y), r in zip(pix, got):
+        glob = dataclasses.replace(cam, c2w=rs.row_c2w[y].copy())
+        ref = O64.render_camera(sc, glob, opts, bruteforce=True, rays=[y * 160 + x])[0]
+        assert np.allclose(r["out"], ref["out"], atol=1e-12) and abs(r["alpha"] - ref["alpha"]) < 1e-12
+        assert abs(r["depth"] - ref["depth"]) < 1e-9
+    # the rows differ: the first and the last row see the scene from 1 m apart
+    assert np.linalg.norm(rs.row_c2w[0][[3, 7, 11]] - rs.row_c2w[-1][[3, 7, 11]]) > 0.9
+
+
+def test_rolling_shutter_mean_row_is_a_fixed_point(O64):
+    """With enough iterations the row chosen for a Gaussian's mean sees the
+    mean in that row: the mean projected with the row's pose falls in
+    [row, row + 1) (the iteration's fixed point)."""
+    sc = syn.street_scene(4000, seed=16, length=40.0)
+    cam = dataclasses.replace(syn.street_cameras()[1], width=320, height=180, fx=170.0,
+                              fy=170.0, cx=160.0, cy=90.0)
+    rs = syn.rolling_shutter(cam, speed=30.0, readout_s=0.05, yaw_rate=1.0)
+    P, _ = O64.project_camera(sc, rs, O64.opts(pose_iters=8))
+    checked = 0
+    for g in np.nonzero(P["valid"] == 1)[0][:400]:
+        row = int(P["pose_col"][g])
+        ok, uv = O64.camera_project(dataclasses.replace(cam, c2w=rs.row_c2w[row]),
+                                    sc.means[g].astype(np.float64))
+        if not ok or not (0 <= uv[1] < cam.height) or P["cmargin"][g] < 1e-3:
+            continue
+        assert row <= uv[1] < row + 1, (g, row, uv)
+        checked += 1
+    assert checked > 200
+
+
+def test_backward_rolling_shutter_matches_central_differences(O64):
+    sc, cam = _fd_setup()
+    rs = syn.rolling_shutter(cam, speed=40.0, readout_s=0.05, yaw_rate=2.0)
+    opts = O64.opts(cutoffs=0, predicate=0, tile=64)
+    nr = cam.width * cam.height
+    rng = np.random.default_rng(17)
+    gr = rng.normal(size=(nr, 3)).astype(np.float32)
+    ga = rng.normal(size=nr).astype(np.float32)
+    gd = (0.05 * rng.normal(size=nr)).astype(np.float32)
+    G = O64.backward_camera(sc, rs, gr, ga, gd, opts)
+    for name, arr in (("means", sc.means), ("log_scales", sc.log_scales),
+                      ("quats", sc.quats), ("features", sc.features)):
+        flat = arr.reshape(-1)
+        gflat = G[name].reshape(-1)
+        for i in range(0, flat.size, max(1, flat.size // 16)):
+            x0 = float(flat[i])
+            h = 2.0 ** -14
+            flat[i] = np.float32(x0 + h)
+            hp = float(flat[i]) - x0
+            lp = _loss_cam(O64, sc, rs, opts, gr, ga, gd)
+            flat[i] = np.float32(x0 - h)
+            hm = x0 - float(flat[i])
+            lm = _loss_cam(O64, sc, rs, opts, gr, ga, gd)
+            flat[i] = np.float32(x0)
+            fd = (lp - lm) / (hp + hm)
+            scale = max(1.0, np.abs(gflat).max())
+            assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])

@@ -314,6 +314,7 @@ def run_ours(args):
                                                             5, beam=0.003)
         result["train_step"] = train_step_workload(torch, sg, syn, min(args.steps, 30), 3)
         result["actors"] = actors_workload(torch, sg, syn, min(args.steps, 100), 5)
+        result["rolling_shutter"] = rolling_shutter_workload(torch, sg, syn, min(args.steps, 100), 5)
     if not args.no_serving:
         from paper_2510_12901_gb300 import serve
         srv = serve.measure_serving(n_requests=args.serving_requests)
@@ -429,6 +430,46 @@ def actors_workload(torch, sg, syn, steps, warmup):
     rays = sum(c.width * c.height for _, c in cams)
     return {"workload": "street camera scene with 16 car-sized actors holding 10% of the 1M "
                         "Gaussians; fisheye 1920x1280 + pinhole 1920x1080 per step",
+            "value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms,
+            "steps": steps}
+
+
+def rolling_shutter_workload(torch, sg, syn, steps, warmup):
+    """The street camera step with rolling shutters: both views read out
+    top to bottom in 30 ms while the vehicle drives at 15 m/s and turns at
+    0.1 rad/s, every pixel row with its own pose (sg_render_camera_rs, one
+    stream)."""
+    sc = syn.street_scene(N_GAUSS, seed=0, kind="camera")
+    S = sg.Scene(sc)
+    cams = [(sg.Camera(c), syn.rolling_shutter(c)) for c in syn.street_cameras()]
+    rows = [torch.from_numpy(np.ascontiguousarray(c.row_c2w, np.float32)).cuda() for _, c in cams]
+    outs = [[torch.empty((c.height, c.width, 3), device="cuda"),
+             torch.empty((c.height, c.width), device="cuda"),
+             torch.empty((c.height, c.width), device="cuda")] for _, c in cams]
+    frames = [sg.Frame() for _ in cams]
+    opts = sg.sg_default_opts()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for (ch, c), r, o, f in zip(cams, rows, outs, frames):
+            sg.sg_render_camera_rs(S.handle, ch.handle, r.data_ptr(), opts, f.handle,
+                                   o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(),
+                                   stream.cuda_stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rays = sum(c.width * c.height for _, c in cams)
+    return {"workload": "street camera scene, 1M Gaussians; fisheye 1920x1280 + pinhole "
+                        "1920x1080 with rolling shutters (30 ms readout, 15 m/s, 0.1 rad/s), "
+                        "one stream",
             "value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms,
             "steps": steps}
 

@@ -227,6 +227,21 @@ sg_status sg_render_lidar(sg_scene scene, sg_lidar lidar, const float *d_col_c2w
                           float *d_intensity, float *d_drop, float *d_alpha,
                           void *stream);
 
+/* Rolling-shutter camera render (Sec. 3.2, time-dependent effects: sensor
+ * motion in the projection and each ray evaluated with its own time).
+ * d_row_c2w [H,12] (device, the caller keeps it valid until the render and
+ * any sg_backward_camera of this frame have run): the row-major [R | t]
+ * camera-to-world pose of every pixel row at its exposure time.  A pixel's
+ * ray takes its row's origin and rotation; a point's pixel is computed with
+ * the pose of the row it falls in, found from the middle row by taking the
+ * pose of the row the point projects to, opts->pose_iters times (clamped to
+ * the image); the depth key and the SH direction use the row that sees the
+ * mean.  Outputs and errors as sg_render_camera (SG_ERR_INVALID for NULL row
+ * poses, or a frame of sg_render_camera_static). */
+sg_status sg_render_camera_rs(sg_scene scene, sg_camera cam, const float *d_row_c2w,
+                              const sg_render_opts *opts, sg_frame frame, float *d_rgb,
+                              float *d_alpha, float *d_depth, void *stream);
+
 /* Same renders with host output buffers: the device result is copied to
  * h_* (pinned or pageable) on `stream` and the call waits for it.  Inputs
  * stay as above except the LiDAR poses, which are read from host memory. */
@@ -301,8 +316,11 @@ sg_status sg_render_camera_static(sg_scene scene, sg_camera cam, const float h_c
  * d_g_quats [n,4], d_g_opacity [n], d_g_features [n,F].  The caller zeroes
  * them; the call adds (float atomics, so the summation order and the last
  * bits vary run to run).  The unscented transform only selects tiles and is
- * not differentiated.  Errors: SG_ERR_INVALID (frame not rendered from this
- * scene / sensor kind), SG_ERR_CUDA.
+ * not differentiated.  The sensor the frame was rendered with (and, for
+ * LiDAR and rolling-shutter renders, the device poses) must still exist:
+ * the frame refers to them.  With dynamic actors the gradients are in each
+ * Gaussian's own frame.  Errors: SG_ERR_INVALID (frame not rendered from
+ * this scene / sensor kind), SG_ERR_CUDA.
  * ---------------------------------------------------------------------- */
 typedef struct {
     float *d_g_means, *d_g_log_scales, *d_g_quats, *d_g_opacity, *d_g_features;

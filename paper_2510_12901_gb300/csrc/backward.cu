@@ -266,6 +266,114 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
     }
 }
 
+// ------------------------------------------------------------------ rolling shutter
+// The camera backward with a pose per pixel row: the rolling-shutter
+// forward's staging (row slots as LiDAR columns) and ray set-up.
+__global__ void __launch_bounds__(32 * kBwWarps, 4)
+k_backward_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
+                     const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
+                     const uint2 *__restrict__ tile_info, const uint32_t *__restrict__ counts,
+                     const uint8_t *__restrict__ submask, uint32_t *__restrict__ counter,
+                     const float4 *__restrict__ partials, const float4 *__restrict__ pix,
+                     const double *__restrict__ tile_dir, const float *__restrict__ poses,
+                     const float4 *__restrict__ ray_state, const float4 *__restrict__ ray_feat,
+                     const uint32_t *__restrict__ n_contrib, const float *__restrict__ g_rgb,
+                     const float *__restrict__ g_alpha, const float *__restrict__ g_depth,
+                     float *__restrict__ gacc)
+{
+    __shared__ float4 s_all[kBwWarps][kLidPlanes][32];
+    __shared__ uint32_t s_pos[kBwWarps][32], s_lanes[kBwWarps][32], s_gid[kBwWarps][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float4(*s)[32] = s_all[wib];
+    const uint32_t n_items = counts[0];
+    while (true) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const uint2 it = items[item];
+        const int tile = (int)it.x, seg = (int)(it.y >> 3), sub = (int)(it.y & 7);
+        const uint2 ti = tile_info[tile];
+        const int tx = tile % P.ntx, ty = tile / P.ntx;
+        const int sbx = tx * kTile + 8 * (sub & 1), sby = ty * kTile + 4 * (sub >> 1);
+        const int px = sbx + (lane & 7), py = sby + (lane >> 3);
+        const bool inside = px < P.W && py < P.H;
+        const int64_t pidx = (int64_t)py * P.W + px;
+        const float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ray_ok = inside && e.w > 0.f;
+        const uint32_t last = ray_ok ? n_contrib[pidx] : 0u;
+        const uint2 rg = ranges[tile];
+        const uint32_t lo = rg.x + (uint32_t)seg * kSegLen;
+        uint32_t hi = min(rg.y, lo + kSegLen);
+        uint32_t lim = rg.x + last;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lim = max(lim, __shfl_xor_sync(0xffffffffu, lim, o));
+        hi = min(hi, lim);
+        if (hi <= lo) continue;
+        const int nrows = min(4, P.H - sby);
+        const int row = py < P.H ? py : sby;
+        const int sb = 3 + 4 * (row - sby);
+        float dh[3], dl[3], dd[3], d[3];
+        {
+            const double *u = tile_dir + 3 * tile;
+            sensor_ray(poses + 12 * sby, u[0], u[1], u[2], poses + 12 * row, e, dh, dl, dd, d);
+        }
+        float T = 1.f, Qp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (seg > 0) {
+            const float4 *pq = partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2;
+            const float4 u = pq[0], v = pq[1];
+            Qp[0] = u.x; Qp[1] = u.y; Qp[2] = u.z; Qp[3] = v.x; Qp[4] = u.w;
+            T = v.y;
+        }
+        float gQ[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Ut = 0.f, U = 0.f;
+        if (ray_ok) {
+            const float4 st = ray_state[pidx], F = ray_feat[pidx];
+            camera_gQ(g_rgb, g_alpha, g_depth, pidx, st.y, st.z, gQ);
+            Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * st.z + gQ[4] * st.y;
+            U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
+        }
+        for (uint32_t base = lo; base < hi; base += 32) {
+            const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
+            const uint32_t idx = base + lane;
+            uint32_t lm = 0u, g = 0u;
+            if (idx < hi && ((submask[idx] >> sub) & 1u)) {
+                g = ids[idx];
+                lm = subblock_lanes(rec[g].rect, sbx, sby) & act;
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, lm != 0u);
+            if (bal == 0u) continue;
+            __syncwarp();
+            if (lm) {
+                const int pos = __popc(bal & ((1u << lane) - 1u));
+                lidar_entry(rec[g], poses, sby, nrows, dh, dl, s, pos);
+                s_lanes[wib][pos] = lm;
+                s_pos[wib][pos] = idx + 1 - rg.x;
+                s_gid[wib][pos] = g;
+            }
+            __syncwarp();
+            const int cnt = __popc(bal);
+            for (int j = 0; j < cnt; ++j) {
+                PairEval pe;
+                bool ok = lidar_pair_in(s, j, sb, (s_lanes[wib][j] >> lane) & 1u, dd, d,
+                                        P.alpha_min, P.alpha_max, pe);
+                ok = ok && s_pos[wib][j] <= last;
+                if (!__any_sync(0xffffffffu, ok)) continue;
+                float gg[kG];
+#pragma unroll
+                for (int k = 0; k < kG; ++k) gg[k] = 0.f;
+                if (ok) {
+                    const float4 m0 = s[0][j], m1 = s[1][j], m2 = s[2][j];
+                    const float Mr[9] = {m0.x, m0.y, m0.z, m1.x, m1.y, m1.z, m2.x, m2.y, m2.z};
+                    const float q[3] = {m1.w, m2.w, s[sb + 3][j].w};
+                    composite_grads(pe, m0.w, q, gQ, T, U, Ut, Mr, d, gg);
+                }
+                warp_reduce_add16(gg, gacc + (int64_t)s_gid[wib][j] * kG);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------ LiDAR
 __global__ void __launch_bounds__(32 * kBwWarps)
 k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
@@ -436,6 +544,7 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
                               int feature_kind, int sh_degree, int F, float ox, float oy,
                               float oz, const GRec *__restrict__ rec,
                               const float *__restrict__ poses, ActorParams A, float beam,
+                              int posed_origin,
                               const float *__restrict__ gacc, float *__restrict__ gm,
                               float *__restrict__ gls, float *__restrict__ gq,
                               float *__restrict__ gop, float *__restrict__ gf)
@@ -576,8 +685,11 @@ __global__ void k_param_grads(const float *__restrict__ planes, int64_t pitch, i
     float gmu[3] = {G[9], G[10], G[11]};
     const float gc[3] = {G[13], G[14], G[15]};
     if (sh_features(feature_kind)) {
+        // the SH origin: for LiDAR and rolling-shutter cameras, the origin of
+        // the pose (column, row) that saw the mean, whose index the projection
+        // left in the record's feat.w
         const bool lidar = feature_kind == SG_FEATURES_LIDAR_SH;
-        if (lidar) {
+        if (lidar || posed_origin) {
             const float *P = poses + 12 * __float_as_uint(rec[g].feat.w);
             ox = P[3];
             oy = P[7];
@@ -629,7 +741,7 @@ static sg_status finish(const Scene &sc, Frame &fr, const float o[3], float beam
     if (sc.n == 0) return SG_OK;
     k_param_grads<<<(unsigned)((sc.n + 127) / 128), 128, 0, st>>>(
         sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, sc.F, o[0], o[1], o[2],
-        (const GRec *)fr.rec.p, fr.d_lidar_poses, actor_params(sc), beam,
+        (const GRec *)fr.rec.p, fr.d_lidar_poses, actor_params(sc), beam, fr.kind == 2 ? 1 : 0,
         (const float *)fr.gacc.p, g.d_g_means, g.d_g_log_scales, g.d_g_quats, g.d_g_opacity,
         g.d_g_features);
     SG_LAUNCHED();
@@ -675,6 +787,20 @@ sg_status backward_camera(const Scene &sc, const Camera &cam, Frame &fr, const f
     uint32_t *counter = (uint32_t *)fr.scalars.p + 6;
     SG_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), st));
     int64_t grid = 0;
+    if (fr.kind == 2) {     // rolling shutter: poses per pixel row
+        if ((s = persistent_grid((const void *)k_backward_camera_rs, ws.max_items, grid)) != SG_OK)
+            return s;
+        k_backward_camera_rs<<<(unsigned)grid, 32 * kBwWarps, 0, st>>>(
+            P, (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
+            (const uint2 *)fr.ranges.p, (const uint2 *)(cw + ws.info_bytes + ws.off_bytes),
+            (const uint2 *)cw, (const uint32_t *)fr.scalars.p + 4, (const uint8_t *)fr.submask.p,
+            counter, (const float4 *)fr.partials.p, cam.d_pix, cam.d_tile_dir, fr.d_lidar_poses,
+            (const float4 *)fr.ray_state.p, (const float4 *)fr.ray_feat.p,
+            (const uint32_t *)fr.n_contrib.p, g_rgb, g_alpha, g_depth, (float *)fr.gacc.p);
+        SG_LAUNCHED();
+        const float o[3] = {0.f, 0.f, 0.f};
+        return finish(sc, fr, o, 0.f, g, st);
+    }
     if ((s = persistent_grid((const void *)k_backward_camera, ws.max_items, grid)) != SG_OK)
         return s;
     k_backward_camera<<<(unsigned)grid, 32 * kBwWarps, 0, st>>>(

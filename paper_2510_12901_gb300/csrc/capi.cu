@@ -294,7 +294,8 @@ static sg_status sort_and_bin(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
 // sorts and composites.
 static sg_status camera_begin(sg_scene scene, sg_camera cam, const float h_c2w[12],
                               const sg_render_opts *opts, sg_frame frame, float *d_rgb,
-                              float *d_alpha, float *d_depth, cudaStream_t st)
+                              float *d_alpha, float *d_depth, cudaStream_t st,
+                              const float *d_row_c2w = nullptr)
 {
     if (!scene || !cam || !frame || !h_c2w) { set_error("NULL handle or pose"); return SG_ERR_INVALID; }
     if (!opts_ok(opts)) return SG_ERR_INVALID;
@@ -310,21 +311,22 @@ static sg_status camera_begin(sg_scene scene, sg_camera cam, const float h_c2w[1
     int64_t nt = (int64_t)c.ntx * c.nty, nr = (int64_t)c.width * c.height;
     sg_status s = frame_prepare(fr, sc.n, nr, nt);
     if (s != SG_OK) return s;
-    fr.kind = 0;
+    fr.kind = d_row_c2w ? 2 : 0;
     fr.scene = scene;
     fr.sensor = cam;
     fr.opts = *opts;
+    fr.d_lidar_poses = d_row_c2w;
     memcpy(fr.c2w, h_c2w, sizeof(fr.c2w));
     RenderDesc &D = *fr.h_desc;
     memcpy(D.c2w, h_c2w, sizeof(D.c2w));
-    D.poses = nullptr;
+    D.poses = d_row_c2w;
     D.out[0] = d_rgb;
     D.out[1] = d_alpha;
     D.out[2] = d_depth;
     D.out[3] = nullptr;
     if (fr.timing) cudaEventRecord(fr.ev[0], st);
     if ((s = upload_desc(fr, st)) != SG_OK) return s;
-    if ((s = project_camera(sc, c, *opts, fr, st)) != SG_OK) return s;
+    if ((s = project_camera(sc, c, *opts, fr, st, d_row_c2w != nullptr)) != SG_OK) return s;
     if (fr.timing) cudaEventRecord(fr.ev[1], st);
     return sort_and_count(fr, sc.n, st);
 }
@@ -335,7 +337,8 @@ static sg_status camera_finish(sg_camera cam, sg_frame frame, cudaStream_t st)
     Frame &fr = frame->f;
     sg_status s = bin_and_sort(fr, fr.n_gauss, c.ntx, (int64_t)c.ntx * c.nty, 0, st);
     if (s != SG_OK) return s;
-    if ((s = render_camera(c, fr.opts, fr, st)) != SG_OK) return s;
+    s = fr.kind == 2 ? render_camera_rs(c, fr.opts, fr, st) : render_camera(c, fr.opts, fr, st);
+    if (s != SG_OK) return s;
     if (fr.timing) cudaEventRecord(fr.ev[4], st);
     return SG_OK;
 }
@@ -685,6 +688,25 @@ sg_status sg_render_camera(sg_scene scene, sg_camera cam, const float h_c2w[12],
     return s != SG_OK ? s : camera_finish(cam, frame, st);
 }
 
+sg_status sg_render_camera_rs(sg_scene scene, sg_camera cam, const float *d_row_c2w,
+                              const sg_render_opts *opts, sg_frame frame, float *d_rgb,
+                              float *d_alpha, float *d_depth, void *stream)
+{
+    if (!d_row_c2w || !cam) { set_error("NULL camera or row poses"); return SG_ERR_INVALID; }
+    if (!frame) { set_error("frame is NULL"); return SG_ERR_INVALID; }
+    if (frame->f.seg_len != kSegLen) {
+        set_error("sg_render_camera_rs: the frame belongs to the allocation-free render");
+        return SG_ERR_INVALID;
+    }
+    // the global pose of the frame (the middle row's) is read from the device
+    // only by the projection of a global-shutter render: any finite pose does
+    const float eye[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    cudaStream_t st = (cudaStream_t)stream;
+    sg_status s = camera_begin(scene, cam, eye, opts, frame, d_rgb, d_alpha, d_depth, st,
+                               d_row_c2w);
+    return s != SG_OK ? s : camera_finish(cam, frame, st);
+}
+
 sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *views,
                             const sg_render_opts *opts, int host_outputs)
 {
@@ -867,7 +889,7 @@ sg_status sg_backward_camera(sg_scene scene, sg_frame frame, const float *d_g_rg
 {
     if (!scene || !frame || !grads) { set_error("NULL argument"); return SG_ERR_INVALID; }
     Frame &f = frame->f;
-    if (f.kind != 0 || f.scene != scene) {
+    if ((f.kind != 0 && f.kind != 2) || f.scene != scene) {
         set_error("sg_backward_camera: the frame's last render is not a camera render of this scene");
         return SG_ERR_INVALID;
     }

@@ -177,11 +177,12 @@ struct Frame {
     int64_t n_pairs = 0, n_tiles = 0, n_rays = 0, n_gauss = 0;
     int pair_buf = 0;  // which of pkeys/pvals holds the sorted result
     int depth_buf = 0; // which of dkeys/dvals holds the depth-sorted Gaussians
-    int kind = -1;     // 0 camera, 1 lidar
+    int kind = -1;     // 0 camera, 1 lidar, 2 rolling-shutter camera
     const void *scene = nullptr;
     const void *sensor = nullptr;
     float c2w[12];     // camera pose of the last render
-    const float *d_lidar_poses = nullptr;
+    const float *d_lidar_poses = nullptr;   // per-ray poses of the last render (LiDAR
+                                            // columns, rolling-shutter rows)
     sg_render_opts opts;
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -270,13 +271,17 @@ sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStrea
 
 // project.cu
 // The pose and the outputs of a render are read from fr.desc (RenderDesc).
+// rolling: the RenderDesc's poses are per pixel row (rolling shutter)
 sg_status project_camera(const Scene &sc, const Camera &cam, const sg_render_opts &o, Frame &fr,
-                         cudaStream_t st);
+                         cudaStream_t st, bool rolling = false);
 sg_status project_lidar(const Scene &sc, const Lidar &L, const sg_render_opts &o, Frame &fr,
                         cudaStream_t st);
 
 // render.cu
 sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, cudaStream_t st);
+// rolling shutter: the RenderDesc's poses are per pixel row
+sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr,
+                           cudaStream_t st);
 sg_status render_lidar(const Lidar &L, const sg_render_opts &o, Frame &fr, cudaStream_t st);
 
 // sensors.cu

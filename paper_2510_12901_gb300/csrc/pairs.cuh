@@ -215,22 +215,22 @@ __device__ __forceinline__ bool lidar_pair_in(float4 (*s)[32], int j, int sb, bo
     return in_box && pe.tau > 0.f && pe.alpha >= alpha_min;
 }
 
-// LiDAR ray set-up shared by forward and backward: reference direction of
-// the work item (double, split into two floats), the ray's offset from it
-// and its full direction.
-__device__ __forceinline__ void lidar_ray(const LidarItem &it, const double *item_u, int item_id,
-                                          const float *poses, const float4 e, int c, float dh[3],
-                                          float dl[3], float dd[3], float d[3])
+// Ray set-up of a sensor whose rays have their own poses (LiDAR columns,
+// rolling-shutter camera rows), shared by forward and backward: the
+// reference direction of the work item (sensor-frame u under the reference
+// pose Pr, double, split into two floats), the ray's offset from it under
+// its own pose Pc (e: its sensor-frame offset from u) and its full
+// direction.
+__device__ __forceinline__ void sensor_ray(const float *Pr, double u0, double u1, double u2,
+                                           const float *Pc, const float4 e, float dh[3],
+                                           float dl[3], float dd[3], float d[3])
 {
-    const float *Pr = poses + 12 * it.ref_col;
-    const double u0 = item_u[3 * item_id], u1 = item_u[3 * item_id + 1], u2 = item_u[3 * item_id + 2];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         double dv = (double)Pr[4 * i] * u0 + (double)Pr[4 * i + 1] * u1 + (double)Pr[4 * i + 2] * u2;
         dh[i] = (float)dv;
         dl[i] = (float)(dv - (double)dh[i]);
     }
-    const float *Pc = poses + 12 * c;
     const float uf[3] = {(float)u0, (float)u1, (float)u2};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -240,6 +240,15 @@ __device__ __forceinline__ void lidar_ray(const LidarItem &it, const double *ite
                  (Pc[4 * i + 2] - Pr[4 * i + 2]) * uf[2]);
         d[i] = dh[i] + dd[i];
     }
+}
+
+// LiDAR ray set-up: the work item's reference column and direction.
+__device__ __forceinline__ void lidar_ray(const LidarItem &it, const double *item_u, int item_id,
+                                          const float *poses, const float4 e, int c, float dh[3],
+                                          float dl[3], float dd[3], float d[3])
+{
+    sensor_ray(poses + 12 * it.ref_col, item_u[3 * item_id], item_u[3 * item_id + 1],
+               item_u[3 * item_id + 2], poses + 12 * c, e, dh, dl, dd, d);
 }
 
 }  // namespace sg

@@ -13,7 +13,7 @@
 namespace sg {
 
 struct CamParams {
-    int model, W, H, ntx, nty;
+    int model, W, H, ntx, nty, pose_iters;
     float fx, fy, cx, cy, k0, k1, k2, k3, theta_max;
 };
 
@@ -210,6 +210,25 @@ __device__ __forceinline__ bool cam_point(const CamParams &C, const float *c2w, 
 #ifndef SG_PROJ_MINB
 #define SG_PROJ_MINB 4
 #endif
+// Rolling shutter: the pose of the pixel row that sees x, found from the
+// middle row by taking the row x projects to, pose_iters times (clamped to
+// the image; an iterate outside the model's domain stops the iteration).
+__device__ __forceinline__ int cam_row(const CamParams &C, const float *poses, float near_dist,
+                                       const float x[3])
+{
+    int row = C.H / 2;
+    for (int it = 0; it < C.pose_iters; ++it) {
+        float u, v;
+        if (!cam_point(C, poses + 12 * row, near_dist, x, u, v)) break;
+        row = v < 0.f ? 0 : (v >= (float)C.H ? C.H - 1 : (int)floorf(v));
+    }
+    return row;
+}
+
+// kRS: rolling shutter, the RenderDesc's poses are per pixel row; each point
+// (the mean and every sigma point) takes the pose of its row, and the row of
+// the mean goes into the record (the backward's SH origin).
+template <bool kRS>
 __global__ void __launch_bounds__(256, SG_PROJ_MINB)
 k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int feature_kind,
                  int sh_degree, ActorParams A, CamParams C, const RenderDesc *__restrict__ D,
@@ -224,9 +243,17 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     __syncthreads();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
+    const float *poses = kRS ? D->poses : nullptr;
     Activated a = activate(planes, pitch, g);
     to_world(A, g, a);
-    float dx = a.mu[0] - s_c2w[3], dy = a.mu[1] - s_c2w[7], dz = a.mu[2] - s_c2w[11];
+    // the mean's pose: the camera's, or that of the row that sees the mean
+    int row0 = 0;
+    const float *P0 = s_c2w;
+    if constexpr (kRS) {
+        row0 = cam_row(C, poses, U.near_dist, a.mu);
+        P0 = poses + 12 * row0;
+    }
+    float dx = a.mu[0] - P0[3], dy = a.mu[1] - P0[7], dz = a.mu[2] - P0[11];
     float dist = sqrtf(dx * dx + dy * dy + dz * dz);
     depth_out[g] = dist;
     uint32_t count = 0;
@@ -237,7 +264,7 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     if (a.sigma >= U.alpha_min) {
         // sigma points chi_0 = mu, chi_{+-i} = mu +- sqrt(n+lambda) s_i R e_i
         float uu[7], vv[7];
-        bool ok = cam_point(C, s_c2w, U.near_dist, a.mu, uu[0], vv[0]);
+        bool ok = cam_point(C, P0, U.near_dist, a.mu, uu[0], vv[0]);
 #pragma unroll
         for (int p = 1; p < 7; ++p) {
             int i = (p - 1) >> 1;
@@ -245,7 +272,9 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
             float x[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) x[r] = a.mu[r] + sg * U.lam_gamma * a.s[i] * a.R[3 * r + i];
-            ok = cam_point(C, s_c2w, U.near_dist, x, uu[p], vv[p]) && ok;
+            const float *Pp = s_c2w;
+            if constexpr (kRS) Pp = poses + 12 * cam_row(C, poses, U.near_dist, x);
+            ok = cam_point(C, Pp, U.near_dist, x, uu[p], vv[p]) && ok;
         }
         if (ok) {
             float mu_u = U.w0m * uu[0], mu_v = U.w0m * vv[0];
@@ -294,11 +323,11 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     } else {
         for (int ch = 0; ch < 3; ++ch) c[ch] = planes[(Scene::kFeat + ch) * pitch + g];
     }
-    write_record(rec, g, a, c[0], c[1], c[2], rect);
+    write_record(rec, g, a, c[0], c[1], c[2], rect, __uint_as_float((uint32_t)row0));
 }
 
 sg_status project_camera(const Scene &sc, const Camera &cam, const sg_render_opts &o, Frame &fr,
-                         cudaStream_t st)
+                         cudaStream_t st, bool rolling)
 {
     CamParams C;
     C.model = cam.model;
@@ -309,10 +338,12 @@ sg_status project_camera(const Scene &sc, const Camera &cam, const sg_render_opt
     C.fx = cam.fx; C.fy = cam.fy; C.cx = cam.cx; C.cy = cam.cy;
     C.k0 = cam.k[0]; C.k1 = cam.k[1]; C.k2 = cam.k[2]; C.k3 = cam.k[3];
     C.theta_max = (float)cam.theta_max;
+    C.pose_iters = o.pose_iters;
     UTParams U = ut_params(o);
     if (sc.n == 0) return SG_OK;
     unsigned grid = (unsigned)((sc.n + 255) / 256);
-    k_project_camera<<<grid, 256, 0, st>>>(
+    auto kern = rolling ? k_project_camera<true> : k_project_camera<false>;
+    kern<<<grid, 256, 0, st>>>(
         sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, actor_params(sc), C,
         (const RenderDesc *)fr.desc.p, U, (GRec *)fr.rec.p,
         (float4 *)fr.rect.p, (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p,

@@ -534,6 +534,237 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     return SG_OK;
 }
 
+// ------------------------------------------------------------------ rolling shutter
+// Rolling-shutter camera compositing: the camera's work items, lists,
+// segments and merges, with every pixel row under its own pose.  The four
+// rows of an 8x4 sub-block are staged like the columns of a LiDAR work item
+// (lidar_entry: per row slot the P rows, a and u = M v of the row's origin),
+// and a ray's direction is its tile reference ray under the sub-block's
+// first row's pose plus its offset under its own row's pose (sensor_ray).
+
+// Composite entries [lo, hi) that reach sub-block `sub` (first pixel sbx,
+// sby; rows r0 .. r0 + nrows - 1) into the lane's accumulator; sb: the
+// lane's row slot.  As cam_walk.
+__device__ __forceinline__ bool cam_walk_rs(const CamRender &P, const GRec *__restrict__ rec,
+                                            const uint32_t *__restrict__ ids,
+                                            const uint8_t *__restrict__ submask, int sub,
+                                            int sbx, int sby, uint32_t lo, uint32_t hi,
+                                            uint32_t begin, const float *__restrict__ poses,
+                                            int nrows, int sb, const float dh[3],
+                                            const float dl[3], const float dd[3],
+                                            const float d[3], float4 (*s)[32], uint32_t *s_pos,
+                                            uint32_t *s_lanes, CamAcc &a, bool done)
+{
+    const int lane = threadIdx.x & 31;
+    const bool done0 = done;
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t act = __ballot_sync(0xffffffffu, !done);
+        if (act == 0u) break;
+        const uint32_t idx = base + lane;
+        uint32_t lm = 0u, g = 0u;
+        if (idx < hi && ((submask[idx] >> sub) & 1u)) {
+            g = ids[idx];
+            lm = subblock_lanes(rec[g].rect, sbx, sby) & act;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, lm != 0u);
+        if (bal == 0u) continue;
+        __syncwarp();
+        if (lm) {
+            const int pos = __popc(bal & ((1u << lane) - 1u));
+            lidar_entry(rec[g], poses, sby, nrows, dh, dl, s, pos);
+            s_lanes[pos] = lm;
+            s_pos[pos] = idx + 1 - begin;
+        }
+        __syncwarp();
+        const int n = __popc(bal);
+        for (int j = 0; j < n; ++j) {
+            PairEval pe;
+            bool ok = lidar_pair_in(s, j, sb, (s_lanes[j] >> lane) & 1u, dd, d, P.alpha_min,
+                                    P.alpha_max, pe);
+            ok = ok && !done;
+            const float Tn = a.T * (1.f - pe.alpha);
+            const bool stop = ok && Tn < P.t_min;
+            done = done || stop;
+            ok = ok && !stop;
+            const float wgt = ok ? pe.alpha * a.T : 0.f;
+            a.c0 += wgt * s[1][j].w;
+            a.c1 += wgt * s[2][j].w;
+            a.c2 += wgt * s[sb + 3][j].w;
+            a.Z += wgt * pe.tau;
+            a.W += wgt;
+            a.T = ok ? Tn : a.T;
+            a.last = ok ? s_pos[j] : a.last;
+        }
+    }
+    return done && !done0;
+}
+
+// The per-lane ray of a rolling-shutter sub-block: rows, the lane's slot,
+// and its direction (see above).
+__device__ __forceinline__ void cam_rs_ray(const float *__restrict__ poses,
+                                           const double *__restrict__ tile_dir, int tile, int H,
+                                           int sby, int py, const float4 e, int &nrows, int &sb,
+                                           float dh[3], float dl[3], float dd[3], float d[3])
+{
+    nrows = min(4, H - sby);
+    const int row = py < H ? py : sby;
+    sb = 3 + 4 * (row - sby);
+    const double *u = tile_dir + 3 * tile;
+    sensor_ray(poses + 12 * sby, u[0], u[1], u[2], poses + 12 * row, e, dh, dl, dd, d);
+}
+
+template <uint32_t kSeg>
+__global__ void __launch_bounds__(32 * kCamWarps)
+k_render_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
+                   const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
+                   const uint2 *__restrict__ tile_info, const uint32_t *__restrict__ counts,
+                   const uint8_t *__restrict__ submask, uint32_t *__restrict__ counter,
+                   uint32_t *__restrict__ arrive, float4 *__restrict__ partials,
+                   const float4 *__restrict__ pix, const double *__restrict__ tile_dir,
+                   const RenderDesc *__restrict__ D, float4 *__restrict__ ray_state,
+                   float4 *__restrict__ ray_feat, uint32_t *__restrict__ n_contrib)
+{
+    __shared__ float4 s_all[kCamWarps][kLidPlanes][32];
+    __shared__ uint32_t s_pos[kCamWarps][32];
+    __shared__ uint32_t s_lanes[kCamWarps][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float4(*s_e)[32] = s_all[wib];
+    const float *__restrict__ poses = D->poses;
+    const uint32_t n_items = counts[0];
+    while (true) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const uint2 it = items[item];
+        const int tile = (int)it.x, seg = (int)(it.y >> 3), sub = (int)(it.y & 7);
+        const uint2 ti = tile_info[tile];
+        const int tx = tile % P.ntx, ty = tile / P.ntx;
+        const int sbx = tx * kTile + 8 * (sub & 1), sby = ty * kTile + 4 * (sub >> 1);
+        const int px = sbx + (lane & 7), py = sby + (lane >> 3);
+        const bool inside = px < P.W && py < P.H;
+        const int64_t pidx = (int64_t)py * P.W + px;
+        const float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool no_ray = !(inside && e.w > 0.f);
+        int nrows, sb;
+        float dh[3], dl[3], dd[3], d[3];
+        cam_rs_ray(poses, tile_dir, tile, P.H, sby, py, e, nrows, sb, dh, dl, dd, d);
+        const uint2 rg = ranges[tile];
+        const uint32_t lo = rg.x + (uint32_t)seg * kSeg;
+        const uint32_t hi = min(rg.y, lo + kSeg);
+        CamAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+        const bool stopped = cam_walk_rs(P, rec, ids, submask, sub, sbx, sby, lo, hi, rg.x, poses,
+                                         nrows, sb, dh, dl, dd, d, s_e, s_pos[wib], s_lanes[wib],
+                                         a, no_ray);
+        if (ti.x > 1) {
+            put_state(partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2, a, stopped);
+            __threadfence();
+            __syncwarp();
+            uint32_t prev = 0;
+            if (lane == 0) prev = atomicAdd(&arrive[ti.y * 8 + sub], 1u);
+            prev = __shfl_sync(0xffffffffu, prev, 0);
+            if (prev != ti.x - 1) {
+                __syncwarp();
+                continue;
+            }
+            __threadfence();
+            float4 *pq = partials + ((size_t)ti.y * 256 + sub * 32 + lane) * 2;
+            const float4 u0 = __ldcg(pq), v0 = __ldcg(pq + 1);
+            a = get_state(u0, v0);
+            bool fin = no_ray || v0.w != 0.f;
+            for (uint32_t sgi = 1; sgi < ti.x; ++sgi) {
+                if (__all_sync(0xffffffffu, fin)) break;
+                pq += 512;
+                const float4 u = __ldcg(pq), v = __ldcg(pq + 1);
+                put_state(pq, a, false);
+                const bool take = !fin && v.w == 0.f && a.T * v.y >= P.t_min;
+                const bool redo = !fin && !take;
+                if (take) {
+                    a.c0 += a.T * u.x;
+                    a.c1 += a.T * u.y;
+                    a.c2 += a.T * u.z;
+                    a.W += a.T * u.w;
+                    a.Z += a.T * v.x;
+                    a.T *= v.y;
+                    const uint32_t l = __float_as_uint(v.z);
+                    a.last = l ? l : a.last;
+                }
+                if (__any_sync(0xffffffffu, redo)) {
+                    const uint32_t l0 = rg.x + sgi * kSeg;
+                    cam_walk_rs(P, rec, ids, submask, sub, sbx, sby, l0, min(rg.y, l0 + kSeg),
+                                rg.x, poses, nrows, sb, dh, dl, dd, d, s_e, s_pos[wib],
+                                s_lanes[wib], a, !redo);
+                }
+                fin = fin || redo;
+            }
+        }
+        if (inside) {
+            float *const out_rgb = D->out[0], *const out_alpha = D->out[1];
+            float *const out_depth = D->out[2];
+            if (out_rgb) {
+                out_rgb[3 * pidx] = a.c0;
+                out_rgb[3 * pidx + 1] = a.c1;
+                out_rgb[3 * pidx + 2] = a.c2;
+            }
+            if (out_alpha) out_alpha[pidx] = a.W;
+            if (out_depth) out_depth[pidx] = a.W > 0.f ? a.Z / a.W : 0.f;
+            ray_state[pidx] = make_float4(a.T, a.W, a.Z, 0.f);
+            ray_feat[pidx] = make_float4(a.c0, a.c1, a.c2, 0.f);
+            n_contrib[pidx] = a.last;
+        }
+        __syncwarp();
+    }
+}
+
+sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr,
+                           cudaStream_t st)
+{
+    if (fr.seg_len != kSegLen) {
+        set_error("internal: rolling-shutter renders use the default segment length");
+        return SG_ERR_INVALID;
+    }
+    const CamRender P = cam_render_params(cam, o);
+    const int nt = cam.ntx * cam.nty;
+    const int64_t K = fr.n_pairs;
+    const WorkSize ws = work_size(nt, K, fr.seg_len, 8);
+    sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
+    if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
+    if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
+    if (s == SG_OK) s = ensure(fr.submask, K > 0 ? (size_t)K : 1);
+    if (s != SG_OK) return s;
+    unsigned char *cw = (unsigned char *)fr.camwork.p;
+    const uint2 *tile_info = (const uint2 *)cw;
+    const uint2 *items = (const uint2 *)(cw + ws.info_bytes + ws.off_bytes);
+    uint32_t *arrive = (uint32_t *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes);
+    const uint32_t *counts = (const uint32_t *)fr.scalars.p + 4;
+    uint32_t *counter = (uint32_t *)fr.scalars.p + 2;
+    if ((s = launch_work_items(fr, ws, nullptr, nt, 8, fr.seg_len, st)) != SG_OK) return s;
+    const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
+    if (K > 0) {
+        k_submask<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(
+            (const uint32_t *)fr.pkeys[fr.pair_buf].p, ids, (const GRec *)fr.rec.p,
+            (const uint32_t *)fr.scalars.p + 1, cam.ntx, (uint8_t *)fr.submask.p);
+        SG_LAUNCHED();
+    }
+    int dev = 0, sms = 0, nb = 0;
+    SG_CUDA(cudaGetDevice(&dev));
+    SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_camera_rs<kSegLen>,
+                                                      32 * kCamWarps, 0) != cudaSuccess || nb < 1)
+        nb = 4;
+    const int64_t cap = (ws.max_items + kCamWarps - 1) / kCamWarps;
+    int64_t grid = (int64_t)sms * nb;
+    grid = grid < cap ? grid : cap;
+    if (grid < 1) grid = 1;
+    k_render_camera_rs<kSegLen><<<(unsigned)grid, 32 * kCamWarps, 0, st>>>(
+        P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
+        (const uint8_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
+        cam.d_tile_dir, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
+        (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
+    SG_LAUNCHED();
+    return SG_OK;
+}
+
 // ------------------------------------------------------------------ LiDAR
 // LiDAR compositing, persistent warps over (work item, segment) units: a
 // LiDAR work item holds up to 32 rays of one tile (at most kLidarColsMax

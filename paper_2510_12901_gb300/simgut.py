@@ -108,6 +108,8 @@ _SIGNATURES = {
                                    _P, _P, _P, _P]),
     "sg_render_lidar": (C.c_int, [_H, _H, _P, C.POINTER(sg_render_opts), _H, _P, _P, _P, _P,
                                   _P]),
+    "sg_render_camera_rs": (C.c_int, [_H, _H, _P, C.POINTER(sg_render_opts), _H, _P, _P, _P,
+                                      _P]),
     "sg_render_cameras": (C.c_int, [_H, C.c_int, C.POINTER(sg_camera_view),
                                     C.POINTER(sg_render_opts), C.c_int]),
     "sg_render_camera_host": (C.c_int, [_H, _H, C.POINTER(C.c_float),
@@ -258,6 +260,11 @@ def sg_render_lidar(scene, lid, d_col_c2w, opts, frame, d_range, d_int, d_drop, 
                     stream=0):
     _check(load().sg_render_lidar(scene, lid, _P(d_col_c2w), C.byref(opts), frame,
                                   _P(d_range), _P(d_int), _P(d_drop), _P(d_alpha), _P(stream)))
+
+
+def sg_render_camera_rs(scene, cam, d_row_c2w, opts, frame, d_rgb, d_alpha, d_depth, stream=0):
+    _check(load().sg_render_camera_rs(scene, cam, _P(d_row_c2w), C.byref(opts), frame,
+                                      _P(d_rgb), _P(d_alpha), _P(d_depth), _P(stream)))
 
 
 def sg_camera_views(views):
@@ -536,6 +543,24 @@ def render_camera(scene: Scene, cam: Camera, c2w, opts=None, frame: Frame | None
     sg_render_camera(scene.handle, cam.handle, c2w, opts, frame.handle, rgb.data_ptr(),
                      alpha.data_ptr(), depth.data_ptr(), _stream_ptr(stream))
     return dict(rgb=rgb, alpha=alpha, depth=depth, frame=frame)
+
+
+def render_camera_rs(scene: Scene, cam: Camera, row_c2w, opts=None, frame: Frame | None = None,
+                     stream=None):
+    """Rolling-shutter render: row_c2w [H, 12] per-row poses.  The returned
+    dict keeps the device copy of the poses alive (the backward reads them)."""
+    torch = _torch()
+    opts = opts or sg_default_opts()
+    frame = frame or Frame()
+    poses = row_c2w if isinstance(row_c2w, torch.Tensor) else torch.from_numpy(
+        np.ascontiguousarray(row_c2w, np.float32))
+    poses = poses.to("cuda", torch.float32).contiguous()
+    rgb = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    alpha = torch.empty((cam.height, cam.width), dtype=torch.float32, device="cuda")
+    depth = torch.empty((cam.height, cam.width), dtype=torch.float32, device="cuda")
+    sg_render_camera_rs(scene.handle, cam.handle, poses.data_ptr(), opts, frame.handle,
+                        rgb.data_ptr(), alpha.data_ptr(), depth.data_ptr(), _stream_ptr(stream))
+    return dict(rgb=rgb, alpha=alpha, depth=depth, frame=frame, poses=poses)
 
 
 def render_lidar(scene: Scene, lid: Lidar, col_c2w, opts=None, frame: Frame | None = None,

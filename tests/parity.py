@@ -40,9 +40,14 @@ def ambiguous_rays(orc, lidar=False):
     return amb
 
 
-def compare_camera_rays(rgb, alpha, depth, orc, max_excluded=0.01, label=""):
-    """rgb [n,3], alpha [n], depth [n] from the GPU for the rays of `orc`."""
-    amb = ambiguous_rays(orc)
+def compare_camera_rays(rgb, alpha, depth, orc, max_excluded=0.01, label="", posed=False,
+                        also_excluded=None):
+    """rgb [n,3], alpha [n], depth [n] from the GPU for the rays of `orc`.
+    posed: a rolling shutter (per-row poses), whose sort keys can flip with
+    the row chosen for a mean, as for LiDAR columns."""
+    amb = ambiguous_rays(orc, lidar=posed)
+    if also_excluded is not None:
+        amb = amb | also_excluded
     ok = ~amb
     e_rgb = np.abs(rgb.astype(np.float64) - orc["out"]).max(axis=1)
     e_a = np.abs(alpha.astype(np.float64) - orc["alpha"])
@@ -56,6 +61,29 @@ def compare_camera_rays(rgb, alpha, depth, orc, max_excluded=0.01, label=""):
     assert amb.mean() <= max_excluded, (label, info)
     assert not bad.any(), (label, info, np.nonzero(bad)[0][:10])
     return info
+
+
+def camera_rays_seeing(rays, W, gauss, rect_a, rect_b, pad=MARGIN_RECT_PX):
+    """Which pixels (indices into the row-major image of width W) have
+    their centre in the box of one of the Gaussians `gauss` by one of the
+    rect arrays and not by the other (boxes padded by `pad` for "in" and
+    shrunk by it for "out"): e.g. where the GPU and the oracle took
+    different row poses for a sigma point."""
+    rays = np.asarray(rays, np.int64)
+    x = (rays % W).astype(np.float64) + 0.5
+    y = (rays // W).astype(np.float64) + 0.5
+    A = np.asarray(rect_a, np.float64)[gauss]
+    B = np.asarray(rect_b, np.float64)[gauss]
+    out = np.zeros(len(rays), bool)
+
+    def inside(r, p):
+        return ((x[:, None] >= r[None, :, 0] - p) & (x[:, None] <= r[None, :, 1] + p) &
+                (y[:, None] >= r[None, :, 2] - p) & (y[:, None] <= r[None, :, 3] + p))
+
+    for lo in range(0, len(A), 1024):
+        a, b = A[lo:lo + 1024], B[lo:lo + 1024]
+        out |= ((inside(a, pad) & ~inside(b, -pad)) | (inside(b, pad) & ~inside(a, -pad))).any(axis=1)
+    return out
 
 
 def lidar_rays_seeing(rays, L, gauss, rect_a, rect_b, pad=MARGIN_RECT_DEG):

@@ -265,7 +265,8 @@ sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_co
  *
  * views[i]: camera; row-major 3x4 camera-to-world pose (copied); frame
  * (distinct for every view); output buffers rgb [H,W,3], alpha [H,W],
- * depth [H,W] (each may be NULL); stream.  host_outputs = 0: the outputs
+ * depth [H,W] (each may be NULL); stream; row_c2w (NULL, or the per-row
+ * poses of a rolling-shutter view).  host_outputs = 0: the outputs
  * are device buffers and the call returns with the work queued, as
  * sg_render_camera.  host_outputs = 1: the outputs are host buffers
  * (pinned or pageable); each view's result is copied there on its stream
@@ -279,6 +280,8 @@ typedef struct {
     sg_frame frame;
     float *rgb, *alpha, *depth;
     void *stream;
+    const float *row_c2w;   /* device [H,12]: a rolling-shutter view as
+                               sg_render_camera_rs (c2w unused); NULL: global */
 } sg_camera_view;
 sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *views,
                             const sg_render_opts *opts, int host_outputs);

@@ -738,8 +738,12 @@ sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *v
                 out[k] = (float *)v.frame->f.host_stage[k].p;
             }
         }
+        if (v.row_c2w && v.frame->f.seg_len != kSegLen) {
+            set_error("view %d: a rolling-shutter view cannot use an allocation-free frame", i);
+            return SG_ERR_INVALID;
+        }
         s = camera_begin(scene, v.camera, v.c2w, opts, v.frame, out[0], out[1], out[2],
-                         (cudaStream_t)v.stream);
+                         (cudaStream_t)v.stream, v.row_c2w);
         if (s != SG_OK) return s;
     }
     for (int i = 0; i < n_views; ++i) {
@@ -814,7 +818,7 @@ sg_status sg_render_camera_host(sg_scene scene, sg_camera cam, const float h_c2w
                                 float *h_alpha, float *h_depth, void *stream)
 {
     if (!h_c2w) { set_error("pose is NULL"); return SG_ERR_INVALID; }
-    sg_camera_view v;
+    sg_camera_view v{};   // zero: no row poses (global shutter)
     v.camera = cam;
     memcpy(v.c2w, h_c2w, sizeof(v.c2w));
     v.frame = frame;

@@ -55,7 +55,7 @@ class sg_grads(C.Structure):
 class sg_camera_view(C.Structure):
     _fields_ = [("camera", C.c_void_p), ("c2w", C.c_float * 12), ("frame", C.c_void_p),
                 ("rgb", C.c_void_p), ("alpha", C.c_void_p), ("depth", C.c_void_p),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("row_c2w", C.c_void_p)]
 
 
 class sg_server_config(C.Structure):
@@ -269,14 +269,17 @@ def sg_render_camera_rs(scene, cam, d_row_c2w, opts, frame, d_rgb, d_alpha, d_de
 
 def sg_camera_views(views):
     """An array of sg_camera_view from (camera, c2w, frame, rgb, alpha, depth,
-    stream) tuples (handles and raw pointers; None or 0 for no output)."""
+    stream[, row_c2w]) tuples (handles and raw pointers; None or 0 for no
+    output; row_c2w: device pointer of per-row poses, rolling shutter)."""
     arr = (sg_camera_view * len(views))()
-    for v, (cam, c2w, frame, rgb, alpha, depth, stream) in zip(arr, views):
+    for v, t in zip(arr, views):
+        cam, c2w, frame, rgb, alpha, depth, stream = t[:7]
         v.camera = cam
         v.c2w[:] = list(_pose12(c2w))
         v.frame = frame
         v.rgb, v.alpha, v.depth = rgb or None, alpha or None, depth or None
         v.stream = stream or None
+        v.row_c2w = (t[7] if len(t) > 7 else None) or None
     return arr
 
 

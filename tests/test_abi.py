@@ -94,6 +94,7 @@ def test_camera_view_lists_are_checked_before_any_cuda_work(sg):
 def test_camera_view_struct_layout(sg):
     # the C struct: handle, float[12], handle, three pointers, stream
     f = sg.sg_camera_view
-    assert C.sizeof(f) == 96
-    assert [getattr(f, n).offset for n in ("camera", "c2w", "frame", "rgb", "alpha", "depth", "stream")] \
-        == [0, 8, 56, 64, 72, 80, 88]
+    assert C.sizeof(f) == 104
+    assert [getattr(f, n).offset for n in ("camera", "c2w", "frame", "rgb", "alpha", "depth",
+                                           "stream", "row_c2w")] \
+        == [0, 8, 56, 64, 72, 80, 88, 96]

@@ -106,3 +106,38 @@ def test_rolling_shutter_backward(sg, O64):
                           torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     compare_grads({k: v.cpu().numpy() for k, v in grads.items()}, Go, "rs-backward")
+
+
+def test_rolling_shutter_views_in_one_call(sg):
+    """sg_render_cameras with a rolling-shutter and a global-shutter view on
+    two streams gives each view's result alone, bit for bit."""
+    import torch
+    sc = syn.street_scene(60000, seed=21, length=40.0)
+    fish, pin = syn.street_cameras()
+    rs = syn.rolling_shutter(_crop(fish, 320, 214, 107.0), speed=30.0, readout_s=0.05,
+                             yaw_rate=1.0)
+    gl = _crop(pin, 320, 180, 170.0)
+    S = sg.Scene(sc)
+    a = rs_render(sg, sc, rs, S)
+    Cg = sg.Camera(gl)
+    b = sg.render_camera(S, Cg, gl.c2w)
+    torch.cuda.synchronize()
+    Cr = sg.Camera(rs)
+    rows = torch.from_numpy(np.ascontiguousarray(rs.row_c2w, np.float32)).cuda()
+    ss = [torch.cuda.Stream(), torch.cuda.Stream()]
+    frames = [sg.Frame(), sg.Frame()]
+    outs = []
+    for c in (rs, gl):
+        outs.append([torch.full((c.height, c.width, 3), -7.0, device="cuda"),
+                     torch.full((c.height, c.width), -7.0, device="cuda"),
+                     torch.full((c.height, c.width), -7.0, device="cuda")])
+    torch.cuda.synchronize()
+    views = sg.sg_camera_views([
+        (Cr.handle, rs.c2w, frames[0].handle, *[t.data_ptr() for t in outs[0]], ss[0].cuda_stream,
+         rows.data_ptr()),
+        (Cg.handle, gl.c2w, frames[1].handle, *[t.data_ptr() for t in outs[1]], ss[1].cuda_stream)])
+    sg.sg_render_cameras(S.handle, views, sg.sg_default_opts(), 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(outs[0][0].cpu().numpy(), a["rgb"])
+    assert np.array_equal(outs[0][2].cpu().numpy(), a["depth"])
+    assert np.array_equal(outs[1][0].cpu().numpy(), b["rgb"].cpu().numpy())

@@ -256,6 +256,20 @@ def run_ours(args):
               "note": "events on each view's stream; the views overlap, so a view's stage "
                       "may include time the GPU spent on the other view"}
 
+    # per-stage rooflines from a short sequential run (one view at a time on
+    # `stream`, so that each stage's events time that stage alone)
+    seq = []
+    for i in range(12):
+        for (ch, c), o, f in zip(cams, outs, frames[0]):
+            sg.sg_render_camera(S.handle, ch.handle, c.c2w, opts, f.handle, o[0].data_ptr(),
+                                o[1].data_ptr(), o[2].data_ptr(), sp)
+            if i >= 2:
+                seq.append(sg.sg_frame_timing(f.handle))
+    torch.cuda.synchronize()
+    seq_view = np.array(seq).reshape(-1, len(cams), 4).mean(axis=0)
+    pairs = [sg.sg_frame_stats(f.handle)[0] for f in frames[0]]
+    stage_roof = stage_rooflines(seq_view, pairs, N_GAUSS)
+
     # end-to-end through the C-ABI with host (pinned) output buffers
     host = []
     for _, c in cams:
@@ -300,7 +314,7 @@ def run_ours(args):
                        "wall_ms_per_step": wall_ms},
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
             "launches_per_step": launches / args.steps,
-            "clocks": clocks, "stages_ms": stages,
+            "clocks": clocks, "stages_ms": stages, "stage_rooflines": stage_roof,
         }
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(sc, [c for _, c in cams], budget_s=20.0)
@@ -538,6 +552,30 @@ def train_step_workload(torch, sg, syn, steps, warmup):
                         "range loss, backward to all Gaussian parameters",
             "ms_per_step": ms, "steps": steps, "rays_per_step": rays,
             "value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s (forward + backward)"}
+
+
+def stage_rooflines(seq_view, pairs, n_gauss):
+    """Per stage and view, from a sequential run: HBM stages against the
+    measured copy bandwidth with their algorithmic bytes (projection 336 B
+    per Gaussian: 236 read, 100 written; depth sort 64 B per Gaussian: four
+    passes reading and writing an 8-byte key-value pair; binning and tile
+    sort 36 B per pair: written once, then read and written by the sort),
+    the compositing against the FP32 peak (as the headline roofline)."""
+    pk = peaks()
+    hbm = float(pk.get("hbm_gbs", 6699.8))
+    views = ("fisheye", "pinhole")
+    out = {"peak_hbm_gbs": hbm, "views": list(views), "ms": seq_view.tolist()}
+    rows = []
+    for v, (tp, td, tb, tr) in enumerate(seq_view):
+        r = {"project_gbs": 336 * n_gauss / (tp * 1e-3) / 1e9,
+             "depth_sort_gbs": 64 * n_gauss / (td * 1e-3) / 1e9,
+             "bin_tile_sort_gbs": 36 * pairs[v] / (tb * 1e-3) / 1e9, "pairs": int(pairs[v])}
+        r.update({k.replace("_gbs", "_frac"): r[k] / hbm for k in list(r) if k.endswith("_gbs")})
+        rows.append(r)
+    out["per_view"] = rows
+    out["note"] = ("stage times from 10 sequential steps on one stream (the headline step overlaps "
+                   "the views); the sort stages are latency-bound, not HBM-bound (profiles/)")
+    return out
 
 
 def roofline(per_view, cams, clocks):

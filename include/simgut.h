@@ -88,6 +88,10 @@ sg_status sg_create_scene(const sg_gaussians_desc *desc, void *stream, sg_scene 
 /* Overwrites the parameters of an existing scene with the same n and feature
  * layout (a training step).  Same errors as sg_create_scene. */
 sg_status sg_update_scene(sg_scene scene, const sg_gaussians_desc *desc, void *stream);
+/* sg_destroy_*: wait for the device's queued work, then free (a render
+ * still queued may read the object).  A frame keeps referring to the scene
+ * and sensor of its last render: destroy it, or render again, before them
+ * if it is to be used again. */
 void sg_destroy_scene(sg_scene scene);
 int64_t sg_scene_size(sg_scene scene);
 

@@ -233,7 +233,7 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
                 const int pos = __popc(bal & ((1u << lane) - 1u));
                 const uint32_t g = ids[idx];
                 float4 ent[9];
-                cam_entry(rec[g], s_pose.t, dh, dl, ent);
+                cam_entry(rec[g], s_pose.t, dh, dl, ent, kResponseScale);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
                 s_lanes[wib][pos] = subblock_lanes(ent[8], sbx, sby) & act;
@@ -244,9 +244,9 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
             const int n = __popc(bal);
             for (int j = 0; j < n; ++j) {
                 PairEval pe;
-                bool ok = cam_pair_in(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
-                                      s_e[5][j], s_e[6][j], (s_lanes[wib][j] >> lane) & 1u, dd,
-                                      P.alpha_min, P.alpha_max, pe);
+                bool ok = cam_pair_scaled(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
+                                          s_e[5][j], s_e[6][j], (s_lanes[wib][j] >> lane) & 1u, dd,
+                                          P.alpha_min, P.alpha_max, pe);
                 ok = ok && s_pos[wib][j] <= last;
                 if (!__any_sync(0xffffffffu, ok)) continue;
                 float g[kG];

@@ -420,6 +420,7 @@ sg_status sg_update_scene(sg_scene scene, const sg_gaussians_desc *desc, void *s
 void sg_destroy_scene(sg_scene scene)
 {
     if (!scene) return;
+    cudaDeviceSynchronize();   // renders still queued may read the scene
     cudaFree(scene->s.d_planes);
     cudaFree(scene->s.d_actor_of);
     cudaFree(scene->s.d_actor_poses);
@@ -536,6 +537,7 @@ sg_status sg_create_camera(int model, int width, int height, float fx, float fy,
 void sg_destroy_camera(sg_camera cam)
 {
     if (!cam) return;
+    cudaDeviceSynchronize();   // renders still queued may read its ray tables
     cudaFree(cam->c.d_pix);
     cudaFree(cam->c.d_tile_dir);
     delete cam;
@@ -581,6 +583,7 @@ sg_status sg_create_lidar(const float *h_elev_deg, int n_beams, int n_cols, floa
 void sg_destroy_lidar(sg_lidar lidar)
 {
     if (!lidar) return;
+    cudaDeviceSynchronize();   // renders still queued may read its tables
     Lidar &L = lidar->l;
     cudaFree(L.d_T);
     cudaFree(L.d_elev);
@@ -613,6 +616,7 @@ sg_status sg_frame_create(sg_frame *out)
 void sg_frame_destroy(sg_frame frame)
 {
     if (!frame) return;
+    cudaDeviceSynchronize();   // work queued on the frame must finish first
     Frame &f = frame->f;
     for_each_buf(f, [](Buf &b) { release(b); });
     if (f.h_scalars) cudaFreeHost(f.h_scalars);

@@ -39,8 +39,10 @@ __device__ __forceinline__ float dot3(const float a[3], const float b[3])
 // Camera entry, 9 float4 (one per shared-memory plane):
 //   e[0..2] = (P row k, a_k)       e[3..5] = (M row k, M_k . d_T)
 //   e[6]    = (M v, sigma)         e[7] = features      e[8] = extent box
+// pscale multiplies the P rows and a (planes 0..2), so that |num|^2 comes
+// out scaled (the forward folds -1/2 log2(e) of the response into it).
 __device__ __forceinline__ void cam_entry(const GRec &r, const float o[3], const float dh[3],
-                                          const float dl[3], float4 e[9])
+                                          const float dl[3], float4 e[9], float pscale = 1.f)
 {
     const float mu[3] = {r.mu_sigma.x, r.mu_sigma.y, r.mu_sigma.z};
     const float M0[3] = {r.m0.x, r.m0.y, r.m0.z}, M1[3] = {r.m1.x, r.m1.y, r.m1.z},
@@ -48,7 +50,7 @@ __device__ __forceinline__ void cam_entry(const GRec &r, const float o[3], const
     float w[3], vh[3];
     precise_moment(mu, o, dh, dl, w, vh);
     // P rows: f_k (M_k x v), since M_k . (v x dd) = dd . (M_k x v)
-    const float f0 = r.m0.w, f1 = r.m1.w, f2 = r.m2.w;
+    const float f0 = pscale * r.m0.w, f1 = pscale * r.m1.w, f2 = pscale * r.m2.w;
     e[0] = make_float4(f0 * (M0[1] * vh[2] - M0[2] * vh[1]), f0 * (M0[2] * vh[0] - M0[0] * vh[2]),
                        f0 * (M0[0] * vh[1] - M0[1] * vh[0]), f0 * dot3(M0, w));
     e[1] = make_float4(f1 * (M1[1] * vh[2] - M1[2] * vh[1]), f1 * (M1[2] * vh[0] - M1[0] * vh[2]),
@@ -71,51 +73,54 @@ struct PairEval {
     bool clamped;    // alpha hit alpha_max
 };
 
-// Evaluate one camera pair whose extent-box test is already known (in_box);
-// returns false when the entry does not composite at this ray (outside the
-// box, behind the origin, or below alpha_min).  Branch-free: every value is
-// computed and the tests combined at the end, so that evaluations of
-// consecutive entries can overlap.
-__device__ __forceinline__ bool cam_pair_in(const float4 q0, const float4 q1, const float4 q2,
-                                            const float4 m0, const float4 m1, const float4 m2,
-                                            const float4 mv, bool in_box, const float dd[3],
-                                            float alpha_min, float alpha_max, PairEval &pe)
+// Evaluate one camera pair, for an entry staged with pscale =
+// sqrt(log2(e) / 2) (kResponseScale), whose extent-box test is already
+// known (in_box): |num|^2 / |den|^2 is then D^2 log2(e) / 2, and rho =
+// 2^-(that) (the hardware exp2, whose error is that of __expf's) without the
+// two multiplies of exp(-D^2 / 2).  Returns false when the entry does not
+// composite at this ray (outside the box, behind the origin, or below
+// alpha_min).  The forward and the backward both decide through this
+// function, so they take the same decisions; pe gets the unscaled num and
+// D^2 for the gradients.  Branch-free: every value is computed and the tests
+// combined at the end, so that evaluations of consecutive entries overlap.
+constexpr float kResponseScale = 0.84932180028801904f;   // sqrt(log2(e) / 2)
+
+__device__ __forceinline__ float ex2_approx(float x)
 {
-    pe.n[0] = q0.w + q0.x * dd[0] + q0.y * dd[1] + q0.z * dd[2];
-    pe.n[1] = q1.w + q1.x * dd[0] + q1.y * dd[1] + q1.z * dd[2];
-    pe.n[2] = q2.w + q2.x * dd[0] + q2.y * dd[1] + q2.z * dd[2];
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ bool cam_pair_scaled(const float4 q0, const float4 q1, const float4 q2,
+                                                const float4 m0, const float4 m1, const float4 m2,
+                                                const float4 mv, bool in_box, const float dd[3],
+                                                float alpha_min, float alpha_max, PairEval &pe)
+{
+    const float n0 = q0.w + q0.x * dd[0] + q0.y * dd[1] + q0.z * dd[2];
+    const float n1 = q1.w + q1.x * dd[0] + q1.y * dd[1] + q1.z * dd[2];
+    const float n2 = q2.w + q2.x * dd[0] + q2.y * dd[1] + q2.z * dd[2];
     pe.e[0] = m0.w + m0.x * dd[0] + m0.y * dd[1] + m0.z * dd[2];
     pe.e[1] = m1.w + m1.x * dd[0] + m1.y * dd[1] + m1.z * dd[2];
     pe.e[2] = m2.w + m2.x * dd[0] + m2.y * dd[1] + m2.z * dd[2];
     pe.inv = __fdividef(1.f, pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
-    pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
     pe.tau = (mv.x * pe.e[0] + mv.y * pe.e[1] + mv.z * pe.e[2]) * pe.inv;
-    pe.rho = __expf(-0.5f * pe.D2);
+    const float d2s = (n0 * n0 + n1 * n1 + n2 * n2) * pe.inv;
+    pe.rho = ex2_approx(-d2s);
     const float a = mv.w * pe.rho;
     pe.clamped = a > alpha_max;
     pe.alpha = fminf(a, alpha_max);
+    constexpr float kInv = 1.f / kResponseScale;
+    pe.n[0] = n0 * kInv;
+    pe.n[1] = n1 * kInv;
+    pe.n[2] = n2 * kInv;
+    pe.D2 = d2s * (kInv * kInv);
     return in_box && pe.tau > 0.f && pe.alpha >= alpha_min;
-}
-
-// The per-ray extent test: the pixel centre (rx, ry) inside the box rc.
-__device__ __forceinline__ bool in_rect(const float4 rc, float rx, float ry)
-{
-    return rx >= rc.x && rx <= rc.y && ry >= rc.z && ry <= rc.w;
-}
-
-__device__ __forceinline__ bool cam_pair(const float4 q0, const float4 q1, const float4 q2,
-                                         const float4 m0, const float4 m1, const float4 m2,
-                                         const float4 mv, const float4 rc, const float dd[3],
-                                         float rx, float ry, float alpha_min, float alpha_max,
-                                         PairEval &pe)
-{
-    return cam_pair_in(q0, q1, q2, m0, m1, m2, mv, in_rect(rc, rx, ry), dd, alpha_min,
-                       alpha_max, pe);
 }
 
 // Which pixel centres of an 8x4 sub-block with first pixel (x0, y0) lie in
 // the box rc: bit 8 r + c for pixel (x0 + c, y0 + r).  The same float
-// comparisons as in_rect.
+// comparisons as the per-ray extent test.
 __device__ __forceinline__ uint32_t subblock_lanes(const float4 rc, int x0, int y0)
 {
     uint32_t cols = 0, rows = 0;

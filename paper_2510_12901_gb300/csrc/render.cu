@@ -317,7 +317,7 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
         if (ov) {
             const int pos = __popc(bal & ((1u << lane) - 1u));
             float4 ent[9];
-            cam_entry(rec[ids[idx]], pose.t, dh, dl, ent);
+            cam_entry(rec[ids[idx]], pose.t, dh, dl, ent, kResponseScale);
 #pragma unroll
             for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
             s_lanes[pos] = subblock_lanes(ent[8], sbx, sby) & act;
@@ -325,11 +325,12 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
         }
         __syncwarp();
         const int n = __popc(bal);
+        int lastj = -1;            // the batch's last composited entry of this lane
         for (int j = 0; j < n; ++j) {
             PairEval pe;
-            bool ok = cam_pair_in(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
-                                  s_e[5][j], s_e[6][j], (s_lanes[j] >> lane) & 1u, dd,
-                                  P.alpha_min, P.alpha_max, pe);
+            bool ok = cam_pair_scaled(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
+                                      s_e[5][j], s_e[6][j], (s_lanes[j] >> lane) & 1u, dd,
+                                      P.alpha_min, P.alpha_max, pe);
             ok = ok && !done;
             const float Tn = a.T * (1.f - pe.alpha);
             const bool stop = ok && Tn < P.t_min;
@@ -343,8 +344,9 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
             a.Z += wgt * pe.tau;
             a.W += wgt;
             a.T = ok ? Tn : a.T;
-            a.last = ok ? s_pos[j] : a.last;
+            lastj = ok ? j : lastj;
         }
+        if (lastj >= 0) a.last = s_pos[lastj];
     }
     return done && !done0;   // the ray stopped at T_min in this walk
 }

@@ -434,46 +434,61 @@ sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count, const ui
 // so a Gaussian that covers many tiles does not serialise one thread and
 // the writes are coalesced.  Pairs at positions >= cap are not written
 // (capacity mode: the caller learns of them from the dropped-pairs count).
+// Binning, balanced by pairs: block b writes pairs [b C, (b + 1) C) of the
+// depth-ordered expansion (C = kBinChunk; pair p belongs to the valid
+// Gaussian k with offsets[k] <= p < offsets[k + 1]).  The block first finds
+// the owner of its first pair by a cooperative search over the offsets
+// (256 samples per round), loads the offsets and ids of the at most C + 1
+// Gaussians its pairs can belong to, then every thread places its pairs
+// (owner by binary search in shared memory, tile from the owner's range).
+// A Gaussian that covers thousands of tiles is spread over many blocks.
 constexpr int kBinThreads = 256;
+constexpr int kBinChunk = 1024;
 
 __global__ void __launch_bounds__(kBinThreads)
 k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
-      const uint32_t *__restrict__ counts, const uint32_t *__restrict__ d_nvalid,
-      const int4 *__restrict__ tiles, int ntx, int wrap_x, uint32_t cap,
-      uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
+      const uint32_t *__restrict__ d_scal, const int4 *__restrict__ tiles, int ntx, int wrap_x,
+      uint32_t cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
 {
-    __shared__ uint32_t s_off[kBinThreads], s_id[kBinThreads];
-    __shared__ int4 s_rect[kBinThreads];
-    __shared__ uint32_t s_end;
-    const int64_t g0 = (int64_t)blockIdx.x * kBinThreads;
-    const int64_t nvalid = *d_nvalid;
-    if (g0 >= nvalid) return;
-    const int nb = (int)min((int64_t)kBinThreads, nvalid - g0);
+    __shared__ uint32_t s_off[kBinChunk + 1], s_id[kBinChunk + 1];
     const int t = threadIdx.x;
-    if (t < nb) {
-        const uint32_t g = ids[g0 + t];
-        s_id[t] = g;
-        s_off[t] = offsets[g0 + t];
-        s_rect[t] = tiles[g];
-        if (t == nb - 1) s_end = offsets[g0 + t] + counts[g0 + t];
+    const int64_t nvalid = d_scal[0];
+    const int64_t K = min((int64_t)d_scal[1], (int64_t)cap);
+    const int64_t p0 = (int64_t)blockIdx.x * kBinChunk;
+    if (p0 >= K || nvalid == 0) return;
+    const int64_t p1 = min(K, p0 + kBinChunk);
+    // the owner of p0: the largest k with offsets[k] <= p0 (offsets[0] = 0,
+    // strictly increasing: every valid Gaussian has a pair)
+    int64_t lo = 0, hi = nvalid;
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + kBinThreads - 1) / kBinThreads;
+        const int64_t idx = lo + t * step;
+        const bool le = idx < hi && (int64_t)offsets[idx] <= p0;
+        const int c = __syncthreads_count(le);
+        lo = lo + (int64_t)(c - 1) * step;
+        hi = min(hi, lo + step);
+    }
+    const int64_t k0 = lo;
+    const int nk = (int)min((int64_t)kBinChunk + 1, nvalid - k0);
+    for (int i = t; i < nk; i += kBinThreads) {
+        s_off[i] = offsets[k0 + i];
+        s_id[i] = ids[k0 + i];
     }
     __syncthreads();
-    const uint32_t first = s_off[0], total = s_end - first;
-    for (uint32_t o = t; o < total; o += kBinThreads) {
-        const uint32_t pos = first + o;
-        int lo = 0, hi = nb;      // owner: the last k with s_off[k] <= pos
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_off[mid] <= pos) lo = mid; else hi = mid;
+    for (int64_t pos = p0 + t; pos < p1; pos += kBinThreads) {
+        int a = 0, b = nk;             // the last j with s_off[j] <= pos
+        while (b - a > 1) {
+            const int m = (a + b) >> 1;
+            if ((int64_t)s_off[m] <= pos) a = m; else b = m;
         }
-        if (pos >= cap) continue;
-        const int4 r = s_rect[lo];
-        const uint32_t local = pos - s_off[lo], w = (uint32_t)(r.y - r.x + 1);
+        const uint32_t g = s_id[a];
+        const int4 r = tiles[g];
+        const uint32_t local = (uint32_t)(pos - s_off[a]), w = (uint32_t)(r.y - r.x + 1);
         const int ty = r.z + (int)(local / w);
         int x = r.x + (int)(local % w);
         if (wrap_x) { x %= ntx; if (x < 0) x += ntx; }
         keys[pos] = (uint32_t)(ty * ntx + x);
-        vals[pos] = s_id[lo];
+        vals[pos] = g;
     }
 }
 
@@ -481,9 +496,11 @@ sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint
                     const uint32_t *d_nvalid, int64_t n, const int4 *d_tiles, int ntx, int wrap_x,
                     int64_t cap, uint32_t *d_keys, uint32_t *d_vals, cudaStream_t st)
 {
-    if (n == 0) return SG_OK;
-    k_bin<<<(unsigned)((n + kBinThreads - 1) / kBinThreads), kBinThreads, 0, st>>>(
-        d_ids, d_offsets, d_counts, d_nvalid, d_tiles, ntx, wrap_x, (uint32_t)cap, d_keys, d_vals);
+    (void)d_counts;
+    (void)n;
+    if (cap <= 0) return SG_OK;
+    k_bin<<<(unsigned)((cap + kBinChunk - 1) / kBinChunk), kBinThreads, 0, st>>>(
+        d_ids, d_offsets, d_nvalid, d_tiles, ntx, wrap_x, (uint32_t)cap, d_keys, d_vals);
     SG_LAUNCHED();
     return SG_OK;
 }

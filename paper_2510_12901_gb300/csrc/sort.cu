@@ -428,13 +428,9 @@ sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count, const ui
 
 // Expand each valid Gaussian (depth order) into its (tile, Gaussian) pairs:
 // pair o of Gaussian g goes to position offsets[g] + o, tile rows outer and
-// columns inner.  A block takes 256 consecutive Gaussians and writes all of
-// their pairs with its threads striding over the output positions (the
-// owner of a position is found by binary search over the block's offsets),
-// so a Gaussian that covers many tiles does not serialise one thread and
-// the writes are coalesced.  Pairs at positions >= cap are not written
-// (capacity mode: the caller learns of them from the dropped-pairs count).
-// Binning, balanced by pairs: block b writes pairs [b C, (b + 1) C) of the
+// columns inner.  Pairs at positions >= cap are not written (capacity mode:
+// the caller learns of them from the dropped-pairs count).
+// Balanced by pairs: block b writes pairs [b C, (b + 1) C) of the
 // depth-ordered expansion (C = kBinChunk; pair p belongs to the valid
 // Gaussian k with offsets[k] <= p < offsets[k + 1]).  The block first finds
 // the owner of its first pair by a cooperative search over the offsets

@@ -445,6 +445,12 @@ sg_status sg_frame_stats(sg_frame frame, int64_t *n_pairs, int64_t *n_tiles,
  * ---------------------------------------------------------------------- */
 sg_status sg_frame_set_timing(sg_frame frame, int on);
 sg_status sg_frame_timing(sg_frame frame, float ms[4]);
+/* The five stage boundaries of the last render of `frame` (start, after
+ * projection, after the depth stage, after binning, end), in ms after the
+ * start of the last render of `ref` (which may be `frame`; both timed, on
+ * the same device).  Renders on several streams can so be placed on one
+ * time line.  Waits for both renders. */
+sg_status sg_frame_marks(sg_frame frame, sg_frame ref, float ms[5]);
 
 #ifdef __cplusplus
 }

@@ -218,20 +218,32 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
             U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
         const uint32_t act0 = __ballot_sync(0xffffffffu, rg.x + last > lo);
+        // the next batch's mask byte and id, loaded one batch ahead
+        uint32_t nsm = 0u, nid = 0u;
+        if (lo + lane < hi) {
+            nsm = submask[lo + lane];
+            nid = ids[lo + lane];
+        }
         for (uint32_t base = lo; base < hi; base += 32) {
             // lanes whose composited entries reach this batch: once some
             // have ended, an entry that reaches none of the others
             // contributes to no ray and is not staged
             const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
             const uint32_t idx = base + lane;
-            bool ov = idx < hi && ((submask[idx] >> sub) & 1u);
-            if (act != act0 && ov) ov = (subblock_lanes(rec[ids[idx]].rect, sbx, sby) & act) != 0u;
+            const uint32_t g = nid;
+            bool ov = (nsm >> sub) & 1u;
+            if (idx + 32 < hi) {
+                nsm = submask[idx + 32];
+                nid = ids[idx + 32];
+            } else {
+                nsm = 0u;
+            }
+            if (act != act0 && ov) ov = (subblock_lanes(rec[g].rect, sbx, sby) & act) != 0u;
             const uint32_t bal = __ballot_sync(0xffffffffu, ov);
             if (bal == 0u) continue;
             __syncwarp();
             if (ov) {
                 const int pos = __popc(bal & ((1u << lane) - 1u));
-                const uint32_t g = ids[idx];
                 float4 ent[9];
                 cam_entry(rec[g], s_pose.t, dh, dl, ent, kResponseScale);
 #pragma unroll
@@ -332,14 +344,24 @@ k_backward_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *
             Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * st.z + gQ[4] * st.y;
             U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
+        uint32_t nsm = 0u, nid = 0u;    // the next batch's, one batch ahead
+        if (lo + lane < hi) {
+            nsm = submask[lo + lane];
+            nid = ids[lo + lane];
+        }
         for (uint32_t base = lo; base < hi; base += 32) {
             const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
             const uint32_t idx = base + lane;
-            uint32_t lm = 0u, g = 0u;
-            if (idx < hi && ((submask[idx] >> sub) & 1u)) {
-                g = ids[idx];
-                lm = subblock_lanes(rec[g].rect, sbx, sby) & act;
+            const uint32_t g = nid;
+            const bool ov = (nsm >> sub) & 1u;
+            if (idx + 32 < hi) {
+                nsm = submask[idx + 32];
+                nid = ids[idx + 32];
+            } else {
+                nsm = 0u;
             }
+            uint32_t lm = 0u;
+            if (ov) lm = subblock_lanes(rec[g].rect, sbx, sby) & act;
             const uint32_t bal = __ballot_sync(0xffffffffu, lm != 0u);
             if (bal == 0u) continue;
             __syncwarp();
@@ -449,12 +471,14 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
             Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * Z + gQ[4] * W;
             U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
+        uint32_t nid = lo + lane < hi ? ids[lo + lane] : 0u;   // one batch ahead
         for (uint32_t base = lo; base < hi; base += 32) {
             const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
             const uint32_t idx = base + lane;
-            uint32_t m = 0u, g = 0u;
+            const uint32_t g = nid;
+            if (idx + 32 < hi) nid = ids[idx + 32];
+            uint32_t m = 0u;
             if (idx < hi) {
-                g = ids[idx];
                 const float4 rc = rec[g].rect;
                 m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, s_raz[wib], s_rel[wib]) & act;
             }

@@ -165,7 +165,6 @@ static sg_status frame_prepare(Frame &fr, int64_t n, int64_t nrays, int64_t ntil
         SG_ENS(fr.dkeys[i], sizeof(uint32_t) * (n > 0 ? n : 1));
         SG_ENS(fr.dvals[i], sizeof(uint32_t) * (n > 0 ? n : 1));
     }
-    SG_ENS(fr.cnt_sorted, sizeof(uint32_t) * (n > 0 ? n : 1));
     SG_ENS(fr.offsets, sizeof(uint32_t) * (n > 0 ? n : 1));
     SG_ENS(fr.ranges, sizeof(uint2) * (ntiles > 0 ? ntiles : 1));
     SG_ENS(fr.ray_state, sizeof(float4) * (nrays > 0 ? nrays : 1));
@@ -218,18 +217,11 @@ static sg_status sort_and_count(Frame &fr, int64_t n, cudaStream_t st)
     uint32_t *sc = (uint32_t *)fr.scalars.p;   // [0] valid Gaussians, [1] pairs
     uint32_t *dk[2] = {(uint32_t *)fr.dkeys[0].p, (uint32_t *)fr.dkeys[1].p};
     uint32_t *dv[2] = {(uint32_t *)fr.dvals[0].p, (uint32_t *)fr.dvals[1].p};
-    sg_status s = compact_valid((const uint32_t *)fr.count.p, (const float *)fr.depth.p, n,
-                                dk[0], dv[0], sc, fr, st);
-    if (s != SG_OK) return s;
     int rb = 0;
-    s = radix_sort_pairs(dk, dv, n, sc, 0, 32, fr, st, &rb);
+    sg_status s = depth_stage((const uint32_t *)fr.count.p, (const float *)fr.depth.p, n, dk, dv,
+                              sc, (uint32_t *)fr.offsets.p, fr, st, &rb);
     if (s != SG_OK) return s;
     fr.depth_buf = rb;
-    s = gather_counts(dv[rb], (const uint32_t *)fr.count.p, sc, n, (uint32_t *)fr.cnt_sorted.p, st);
-    if (s != SG_OK) return s;
-    s = scan_exclusive_u32((const uint32_t *)fr.cnt_sorted.p, (uint32_t *)fr.offsets.p, sc + 1, n,
-                           fr, st);
-    if (s != SG_OK) return s;
     tmark(fr, 2, st);
     if (fr.k_cap > 0) return clamp_pairs(sc + 1, fr.k_cap, sc + 3, st);
     SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 8, cudaMemcpyDeviceToHost, st));
@@ -264,9 +256,8 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     }
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
-    s = bin_pairs((const uint32_t *)fr.dvals[fr.depth_buf].p, (const uint32_t *)fr.offsets.p,
-                  (const uint32_t *)fr.cnt_sorted.p, sc, n, (const int4 *)fr.tiles.p, ntx, wrap, K,
-                  pk[0], pv[0], st);
+    s = bin_pairs((const uint32_t *)fr.dvals[fr.depth_buf].p, (const uint32_t *)fr.offsets.p, sc,
+                  (const int4 *)fr.tiles.p, ntx, wrap, K, pk[0], pv[0], st);
     if (s != SG_OK) return s;
     int bits = 1;
     while (((int64_t)1 << bits) < ntiles) ++bits;
@@ -643,6 +634,17 @@ sg_status sg_frame_timing(sg_frame frame, float ms[4])
     if (!f.timing) { set_error("timing is off for this frame"); return SG_ERR_INVALID; }
     SG_CUDA(cudaEventSynchronize(f.ev[4]));
     for (int i = 0; i < 4; ++i) SG_CUDA(cudaEventElapsedTime(&ms[i], f.ev[i], f.ev[i + 1]));
+    return SG_OK;
+}
+
+sg_status sg_frame_marks(sg_frame frame, sg_frame ref, float ms[5])
+{
+    if (!frame || !ref || !ms) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    Frame &f = frame->f, &r = ref->f;
+    if (!f.timing || !r.timing) { set_error("timing is off for a frame"); return SG_ERR_INVALID; }
+    SG_CUDA(cudaEventSynchronize(f.ev[4]));
+    SG_CUDA(cudaEventSynchronize(r.ev[0]));
+    for (int i = 0; i < 5; ++i) SG_CUDA(cudaEventElapsedTime(&ms[i], r.ev[0], f.ev[i]));
     return SG_OK;
 }
 

@@ -151,7 +151,7 @@ struct Frame {
     // per-Gaussian
     Buf rec, rect, tiles, depth, count, mean2d, cov2d;
     // depth sort / offsets
-    Buf dkeys[2], dvals[2], cnt_sorted, offsets, flags, scan_tmp, hist;
+    Buf dkeys[2], dvals[2], offsets, hist;
     // pairs
     Buf pkeys[2], pvals[2], ranges, order, submask;
     // camera work items: per-tile (segments, first partial slot), items,
@@ -239,8 +239,6 @@ constexpr WorkSize work_size(int64_t units, int64_t n_pairs, uint32_t seg_len, i
 
 // ------------------------------------------------------------------ launchers
 // sort.cu
-sg_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, uint32_t *d_total,
-                             int64_t n, Frame &fr, cudaStream_t st);
 // Scratch words (fr.hist) of a radix sort of up to n_max pairs in `passes`
 // 8-bit passes: digit counts and offsets (256 per pass), per-pass tile
 // tickets, and the look-back words (256 per tile of kRadixTile pairs and pass).
@@ -253,18 +251,29 @@ constexpr int64_t radix_scratch_words(int64_t n_max, int passes)
     const int64_t tiles = (n_max + kRadixTile - 1) / kRadixTile;
     return 2 * 256 * (int64_t)passes + 16 + (int64_t)passes * (tiles > 0 ? tiles : 1) * 256;
 }
+// The depth stage's scratch (fr.hist): the radix scratch of its 4 passes,
+// then two tickets and a 64-bit look-back word per tile of kChainTile
+// entries for each of its two chained scans.
+constexpr int kChainTile = 4096;
+constexpr int64_t depth_stage_words(int64_t n)
+{
+    return radix_scratch_words(n, 4) + 2 * (2 + 2 * ((n + kChainTile - 1) / kChainTile));
+}
+sg_status radix_prepare(int64_t n_max, int passes, Frame &fr, cudaStream_t st, uint32_t **hist,
+                        int64_t extra);
 sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n,
                            const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
-                           cudaStream_t st, int *result_buf);
-sg_status compact_valid(const uint32_t *d_count, const float *d_depth, int64_t n,
-                        uint32_t *d_keys, uint32_t *d_vals, uint32_t *d_nvalid, Frame &fr,
-                        cudaStream_t st);
-sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count,
-                        const uint32_t *d_nvalid, int64_t n, uint32_t *d_out,
-                        cudaStream_t st);
-sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_counts,
-                    const uint32_t *d_nvalid, int64_t n, const int4 *d_tiles, int ntx, int wrap_x,
-                    int64_t cap, uint32_t *d_keys, uint32_t *d_vals, cudaStream_t st);
+                           cudaStream_t st, int *result_buf, bool counted = false);
+// The depth stage: the Gaussians with a non-zero tile count sorted by depth
+// (keys/vals[*result_buf]: depth bits, ids), d_scal[0] = their number,
+// d_offsets = exclusive scan of their tile counts in that order, d_scal[1]
+// = the pair total.
+sg_status depth_stage(const uint32_t *d_count, const float *d_depth, int64_t n, uint32_t *keys[2],
+                      uint32_t *vals[2], uint32_t *d_scal, uint32_t *d_offsets, Frame &fr,
+                      cudaStream_t st, int *result_buf);
+sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_nvalid,
+                    const int4 *d_tiles, int ntx, int wrap_x, int64_t cap, uint32_t *d_keys,
+                    uint32_t *d_vals, cudaStream_t st);
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
                       int64_t ntiles, cudaStream_t st);
 sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStream_t st);
@@ -305,9 +314,8 @@ namespace sg {
 template <class Fn> inline void for_each_buf(Frame &f, Fn fn)
 {
     Buf *bufs[] = {&f.rec, &f.rect, &f.tiles, &f.depth, &f.count, &f.mean2d, &f.cov2d,
-                   &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.cnt_sorted,
-                   &f.offsets, &f.flags, &f.scan_tmp, &f.hist, &f.pkeys[0], &f.pkeys[1],
-                   &f.pvals[0], &f.pvals[1], &f.ranges, &f.order, &f.submask, &f.camwork,
+                   &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.offsets, &f.hist,
+                   &f.pkeys[0], &f.pkeys[1], &f.pvals[0], &f.pvals[1], &f.ranges, &f.order, &f.submask, &f.camwork,
                    &f.partials, &f.ray_state, &f.n_contrib, &f.ray_feat, &f.gacc, &f.scalars,
                    &f.desc, &f.host_stage[0], &f.host_stage[1], &f.host_stage[2]};
     for (Buf *b : bufs) fn(*b);

@@ -26,16 +26,16 @@ constexpr size_t kStG16 = al(16 * kStMaxGauss);       // float4 / int4 per Gauss
 constexpr size_t kStG8 = al(8 * kStMaxGauss);
 constexpr size_t kStG4 = al(4 * kStMaxGauss);
 constexpr size_t kStP4 = al(4 * kStMaxPairs);
-constexpr size_t kStHist = al(4 * radix_scratch_words(kStMaxPairs > kStMaxGauss ? kStMaxPairs
-                                                                             : kStMaxGauss, 4));
-constexpr size_t kStScan = al(4 * 4096);
+constexpr size_t kStHist = al(4 * (radix_scratch_words(kStMaxPairs, 4) > depth_stage_words(kStMaxGauss)
+                                       ? radix_scratch_words(kStMaxPairs, 4)
+                                       : depth_stage_words(kStMaxGauss)));
 constexpr WorkSize kStWork = work_size(kStMaxTiles, kStMaxPairs, kSegLenStatic, 8);
 constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, tiles, cov2d, mean2d
                             2 * kStG4 +                          // depth, count
                             4 * kStG4 +                          // depth-sort keys/values x2
-                            2 * kStG4 + 2 * kStG4 +              // cnt_sorted, offsets, flags
+                            kStG4 +                              // offsets
                             4 * kStP4 +                          // pair keys/values x2
-                            kStHist + kStScan +
+                            kStHist +
                             al(8 * kStMaxTiles) + al(4 * kStMaxTiles) +  // ranges, order
                             2 * al(16 * kStMaxRays) + al(4 * kStMaxRays) + // ray state, features,
                                                                          // contributors
@@ -131,15 +131,12 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
         carve(fr.dkeys[i], cur, kStG4);
         carve(fr.dvals[i], cur, kStG4);
     }
-    carve(fr.cnt_sorted, cur, kStG4);
     carve(fr.offsets, cur, kStG4);
-    carve(fr.flags, cur, 2 * kStG4);
     for (int i = 0; i < 2; ++i) {
         carve(fr.pkeys[i], cur, kStP4);
         carve(fr.pvals[i], cur, kStP4);
     }
     carve(fr.hist, cur, kStHist);
-    carve(fr.scan_tmp, cur, kStScan);
     carve(fr.ranges, cur, al(8 * kStMaxTiles));
     carve(fr.order, cur, al(4 * kStMaxTiles));
     carve(fr.ray_state, cur, al(16 * kStMaxRays));
@@ -175,16 +172,9 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     uint32_t *scal = (uint32_t *)fr.scalars.p;
     uint32_t *dk[2] = {(uint32_t *)fr.dkeys[0].p, (uint32_t *)fr.dkeys[1].p};
     uint32_t *dv[2] = {(uint32_t *)fr.dvals[0].p, (uint32_t *)fr.dvals[1].p};
-    if ((s = compact_valid((const uint32_t *)fr.count.p, (const float *)fr.depth.p, n, dk[0],
-                           dv[0], scal, fr, st)) != SG_OK)
-        return s;
     int rb = 0;
-    if ((s = radix_sort_pairs(dk, dv, n, scal, 0, 32, fr, st, &rb)) != SG_OK) return s;
-    if ((s = gather_counts(dv[rb], (const uint32_t *)fr.count.p, scal, n,
-                           (uint32_t *)fr.cnt_sorted.p, st)) != SG_OK)
-        return s;
-    if ((s = scan_exclusive_u32((const uint32_t *)fr.cnt_sorted.p, (uint32_t *)fr.offsets.p,
-                                scal + 1, n, fr, st)) != SG_OK)
+    if ((s = depth_stage((const uint32_t *)fr.count.p, (const float *)fr.depth.p, n, dk, dv, scal,
+                         (uint32_t *)fr.offsets.p, fr, st, &rb)) != SG_OK)
         return s;
     uint32_t hs[2] = {0, 0};
     SG_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -198,9 +188,8 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     fr.n_pairs = K;
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
-    if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, (const uint32_t *)fr.cnt_sorted.p,
-                       scal, n, (const int4 *)fr.tiles.p, c.ntx, 0, K, pk[0], pv[0], st)) !=
-        SG_OK)
+    if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, scal, (const int4 *)fr.tiles.p,
+                       c.ntx, 0, K, pk[0], pv[0], st)) != SG_OK)
         return s;
     int bits = 1;
     while (((int64_t)1 << bits) < nt) ++bits;

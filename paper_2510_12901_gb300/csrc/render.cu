@@ -284,6 +284,37 @@ struct CamAcc {
     uint32_t last;                 // list entries up to the last composited one
 };
 
+// Composite the n entries staged in s_e into the lane's accumulator.
+__device__ __forceinline__ void cam_composite(const CamRender &P, float4 (*s_e)[32],
+                                              const uint32_t *s_pos, int n, const float dd[3],
+                                              CamAcc &a, bool &done)
+{
+    const int lane = threadIdx.x & 31;
+    int lastj = -1;            // the batch's last composited entry of this lane
+    for (int j = 0; j < n; ++j) {
+        PairEval pe;
+        // plane 7: features, with the entry's lane mask in .w
+        const float4 col = s_e[7][j];
+        bool ok = cam_pair_scaled(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
+                                  s_e[5][j], s_e[6][j], (__float_as_uint(col.w) >> lane) & 1u,
+                                  dd, P.alpha_min, P.alpha_max, pe);
+        ok = ok && !done;
+        const float Tn = a.T * (1.f - pe.alpha);
+        const bool stop = ok && Tn < P.t_min;
+        done = done || stop;
+        ok = ok && !stop;
+        const float wgt = ok ? pe.alpha * a.T : 0.f;
+        a.c0 += wgt * col.x;
+        a.c1 += wgt * col.y;
+        a.c2 += wgt * col.z;
+        a.Z += wgt * pe.tau;
+        a.W += wgt;
+        a.T = ok ? Tn : a.T;
+        lastj = ok ? j : lastj;
+    }
+    if (lastj >= 0) a.last = s_pos[lastj];
+}
+
 // Composite list entries [lo, hi) of a tile (first entry `begin`) that can
 // reach sub-block `sub` into the lane's accumulator; lanes with done = true
 // take part in the warp's staging but keep their state; `rays` = the lanes
@@ -295,21 +326,35 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
                                          int sbx, int sby, uint32_t lo, uint32_t hi,
                                          uint32_t begin, const float dh[3], const float dl[3],
                                          const float dd[3], float4 (*s_e)[32],
-                                         uint32_t *s_pos, uint32_t *s_lanes, CamAcc &a,
-                                         bool done, uint32_t rays)
+                                         uint32_t *s_pos, CamAcc &a, bool done,
+                                         uint32_t rays)
 {
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
+    // the next batch's mask byte and Gaussian id, loaded one batch ahead so
+    // that staging waits for the record load alone
+    uint32_t nsm = 0u, nid = 0u;
+    if (lo + lane < hi) {
+        nsm = submask[lo + lane];
+        nid = ids[lo + lane];
+    }
     for (uint32_t base = lo; base < hi; base += 32) {
         const uint32_t act = __ballot_sync(0xffffffffu, !done);
         if (act == 0u) break;
         const uint32_t idx = base + lane;
-        bool ov = idx < hi && ((submask[idx] >> sub) & 1u);
+        const uint32_t gid = nid;
+        bool ov = (nsm >> sub) & 1u;
+        if (idx + 32 < hi) {
+            nsm = submask[idx + 32];
+            nid = ids[idx + 32];
+        } else {
+            nsm = 0u;
+        }
         if (act != rays && ov) {
             // some rays are done: stage only entries that reach one still
             // compositing (the box is read before the ballot, which costs a
             // load latency, so not while every ray is live)
-            ov = (subblock_lanes(rec[ids[idx]].rect, sbx, sby) & act) != 0u;
+            ov = (subblock_lanes(rec[gid].rect, sbx, sby) & act) != 0u;
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, ov);
         if (bal == 0u) continue;
@@ -317,36 +362,14 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
         if (ov) {
             const int pos = __popc(bal & ((1u << lane) - 1u));
             float4 ent[9];
-            cam_entry(rec[ids[idx]], pose.t, dh, dl, ent, kResponseScale);
+            cam_entry(rec[gid], pose.t, dh, dl, ent, kResponseScale);
+            ent[7].w = __uint_as_float(subblock_lanes(ent[8], sbx, sby) & act);
 #pragma unroll
             for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
-            s_lanes[pos] = subblock_lanes(ent[8], sbx, sby) & act;
             s_pos[pos] = idx + 1 - begin;
         }
         __syncwarp();
-        const int n = __popc(bal);
-        int lastj = -1;            // the batch's last composited entry of this lane
-        for (int j = 0; j < n; ++j) {
-            PairEval pe;
-            bool ok = cam_pair_scaled(s_e[0][j], s_e[1][j], s_e[2][j], s_e[3][j], s_e[4][j],
-                                      s_e[5][j], s_e[6][j], (s_lanes[j] >> lane) & 1u, dd,
-                                      P.alpha_min, P.alpha_max, pe);
-            ok = ok && !done;
-            const float Tn = a.T * (1.f - pe.alpha);
-            const bool stop = ok && Tn < P.t_min;
-            done = done || stop;
-            ok = ok && !stop;
-            const float wgt = ok ? pe.alpha * a.T : 0.f;
-            const float4 col = s_e[7][j];
-            a.c0 += wgt * col.x;
-            a.c1 += wgt * col.y;
-            a.c2 += wgt * col.z;
-            a.Z += wgt * pe.tau;
-            a.W += wgt;
-            a.T = ok ? Tn : a.T;
-            lastj = ok ? j : lastj;
-        }
-        if (lastj >= 0) a.last = s_pos[lastj];
+        cam_composite(P, s_e, s_pos, __popc(bal), dd, a, done);
     }
     return done && !done0;   // the ray stopped at T_min in this walk
 }
@@ -375,7 +398,6 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
 {
     __shared__ float4 s_all[kCamWarps][8][32];
     __shared__ uint32_t s_pos[kCamWarps][32];
-    __shared__ uint32_t s_lanes[kCamWarps][32];
     __shared__ float s_refs[kCamWarps][6];
     __shared__ CamPose s_pose;
     load_cam_pose(D, s_pose);
@@ -411,7 +433,7 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
         const uint32_t hi = min(rg.y, lo + kSeg);
         CamAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
         const bool stopped = cam_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, lo, hi, rg.x,
-                                      dh, dl, dd, s_e, s_pos[wib], s_lanes[wib], a, no_ray, rays);
+                                      dh, dl, dd, s_e, s_pos[wib], a, no_ray, rays);
         if (ti.x > 1) {
             // long tile: publish this run, and combine if it is the last one
             put_state(partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2, a, stopped);
@@ -451,7 +473,7 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
                     const uint32_t l0 = rg.x + sgi * kSeg;
                     cam_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, l0,
                              min(rg.y, l0 + kSeg), rg.x, dh, dl, dd, s_e, s_pos[wib],
-                             s_lanes[wib], a, !redo, rays);
+                             a, !redo, rays);
                 }
                 fin = fin || redo;
             }
@@ -559,15 +581,25 @@ __device__ __forceinline__ bool cam_walk_rs(const CamRender &P, const GRec *__re
 {
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
+    uint32_t nsm = 0u, nid = 0u;    // the next batch's, as in cam_walk
+    if (lo + lane < hi) {
+        nsm = submask[lo + lane];
+        nid = ids[lo + lane];
+    }
     for (uint32_t base = lo; base < hi; base += 32) {
         const uint32_t act = __ballot_sync(0xffffffffu, !done);
         if (act == 0u) break;
         const uint32_t idx = base + lane;
-        uint32_t lm = 0u, g = 0u;
-        if (idx < hi && ((submask[idx] >> sub) & 1u)) {
-            g = ids[idx];
-            lm = subblock_lanes(rec[g].rect, sbx, sby) & act;
+        const uint32_t g = nid;
+        const bool ov = (nsm >> sub) & 1u;
+        if (idx + 32 < hi) {
+            nsm = submask[idx + 32];
+            nid = ids[idx + 32];
+        } else {
+            nsm = 0u;
         }
+        uint32_t lm = 0u;
+        if (ov) lm = subblock_lanes(rec[g].rect, sbx, sby) & act;
         const uint32_t bal = __ballot_sync(0xffffffffu, lm != 0u);
         if (bal == 0u) continue;
         __syncwarp();
@@ -798,14 +830,17 @@ __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__res
 {
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
+    // the next batch's ids, loaded one batch ahead
+    uint32_t nid = lo + lane < hi ? ids[lo + lane] : 0u;
     for (uint32_t base = lo; base < hi; base += 32) {
         // only entries that reach a ray still compositing
         const uint32_t act = __ballot_sync(0xffffffffu, !done);
         if (act == 0u) break;
         const uint32_t idx = base + lane;
-        uint32_t m = 0u, g = 0u;
+        const uint32_t g = nid;
+        if (idx + 32 < hi) nid = ids[idx + 32];
+        uint32_t m = 0u;
         if (idx < hi) {
-            g = ids[idx];
             const float4 rc = rec[g].rect;
             m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, L.raz, L.rel) & act;
         }

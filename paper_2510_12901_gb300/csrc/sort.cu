@@ -3,10 +3,10 @@
 //
 // Order of work (all on the device, one 4-byte read-back of the pair count):
 //   1. compact the Gaussians that survived projection into (depth bits, id)
-//      pairs, in id order;
+//      pairs, in id order, counting the radix digits as it goes;
 //   2. stable LSD radix sort of those pairs by depth (4 passes of 8 bits):
 //      ties keep id order, so the order is (depth, id);
-//   3. gather tile counts in that order and scan them into pair offsets;
+//   3. scan their tile counts, in that order, into pair offsets;
 //   4. bin: every Gaussian writes (tile, id) for each tile of its range, so
 //      the pair list is in (depth, id) order;
 //   5. stable LSD radix sort of the pairs by tile id only (2 passes for up
@@ -19,10 +19,6 @@
 namespace sg {
 
 // ------------------------------------------------------------------ scan
-constexpr int kScanThreads = 512;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 {
     int lane = threadIdx.x & 31;
@@ -53,103 +49,6 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
     *total = s_warp[32];
     __syncthreads();
     return r;
-}
-
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_reduce(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ part)
-{
-    __shared__ uint32_t s_warp[33];
-    int64_t base = (int64_t)blockIdx.x * kScanTile;
-    uint32_t acc = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
-        if (idx < n) acc += in[idx];
-    }
-    uint32_t tot;
-    block_excl_scan(acc, s_warp, &tot);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-// Exclusive scan of one tile per block, offset by the scanned partials.
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_down(const uint32_t *__restrict__ in, int64_t n, const uint32_t *__restrict__ part_scanned,
-            uint32_t *__restrict__ out, uint32_t *__restrict__ total)
-{
-    __shared__ uint32_t s_val[kScanTile];
-    __shared__ uint32_t s_warp[33];
-    int64_t base = (int64_t)blockIdx.x * kScanTile;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
-        s_val[i * kScanThreads + threadIdx.x] = idx < n ? in[idx] : 0u;
-    }
-    __syncthreads();
-    uint32_t loc[kScanItems], acc = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        loc[i] = acc;
-        acc += s_val[threadIdx.x * kScanItems + i];
-    }
-    uint32_t tot;
-    uint32_t pre = block_excl_scan(acc, s_warp, &tot) + (part_scanned ? part_scanned[blockIdx.x] : 0u);
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) s_val[threadIdx.x * kScanItems + i] = pre + loc[i];
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
-        if (idx < n) out[idx] = s_val[i * kScanThreads + threadIdx.x];
-    }
-    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        // the grand total = scanned offset of this last tile + its sum
-        *total = (part_scanned ? part_scanned[blockIdx.x] : 0u) + tot;
-    }
-}
-
-// Exclusive scan; scratch comes from fr.scan_tmp (grown as needed).  The
-// partial sums are scanned recursively with the same two kernels.
-static sg_status scan_rec(const uint32_t *in, uint32_t *out, uint32_t *total, int64_t n,
-                          uint32_t *scratch, cudaStream_t st)
-{
-    int64_t nb = (n + kScanTile - 1) / kScanTile;
-    if (nb <= 1) {
-        k_scan_down<<<1, kScanThreads, 0, st>>>(in, n, nullptr, out, total);
-        SG_LAUNCHED();
-        return SG_OK;
-    }
-    uint32_t *part = scratch, *part_scanned = scratch + nb;
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, part);
-    SG_LAUNCHED();
-    sg_status s = scan_rec(part, part_scanned, nullptr, nb, scratch + 2 * nb, st);
-    if (s != SG_OK) return s;
-    k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, part_scanned, out, total);
-    SG_LAUNCHED();
-    return SG_OK;
-}
-
-static int64_t scan_scratch_words(int64_t n)
-{
-    int64_t w = 0;
-    while (true) {
-        int64_t nb = (n + kScanTile - 1) / kScanTile;
-        if (nb <= 1) break;
-        w += 2 * nb;
-        n = nb;
-    }
-    return w + 16;
-}
-
-sg_status scan_exclusive_u32(const uint32_t *d_in, uint32_t *d_out, uint32_t *d_total,
-                             int64_t n, Frame &fr, cudaStream_t st)
-{
-    if (n <= 0) {
-        if (d_total) SG_CUDA(cudaMemsetAsync(d_total, 0, 4, st));
-        return SG_OK;
-    }
-    sg_status s = ensure(fr.scan_tmp, sizeof(uint32_t) * scan_scratch_words(n));
-    if (s != SG_OK) return s;
-    return scan_rec(d_in, d_out, d_total, n, (uint32_t *)fr.scan_tmp.p, st);
 }
 
 // ------------------------------------------------------------------ radix sort
@@ -318,9 +217,24 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
     }
 }
 
+// Zero the radix scratch (histograms, tickets, look-back words) for a sort
+// of up to n_max pairs in `passes` passes; *hist gets the histograms, for a
+// caller that counts the digits itself (radix_sort_pairs with counted).
+// `extra` more zeroed words follow the scratch (at hist + radix_scratch_words).
+sg_status radix_prepare(int64_t n_max, int passes, Frame &fr, cudaStream_t st, uint32_t **hist,
+                        int64_t extra)
+{
+    const int64_t words = radix_scratch_words(n_max, passes) + extra;
+    sg_status s = ensure(fr.hist, sizeof(uint32_t) * words);
+    if (s != SG_OK) return s;
+    SG_CUDA(cudaMemsetAsync(fr.hist.p, 0, sizeof(uint32_t) * words, st));
+    *hist = (uint32_t *)fr.hist.p;
+    return SG_OK;
+}
+
 sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                            const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
-                           cudaStream_t st, int *result_buf)
+                           cudaStream_t st, int *result_buf, bool counted)
 {
     *result_buf = 0;
     if (n_max <= 0 || end_bit <= begin_bit) return SG_OK;
@@ -330,25 +244,25 @@ sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
     }
     const int passes = (end_bit - begin_bit + 7) / 8;
     const int64_t tiles = (n_max + kRadixTile - 1) / kRadixTile;
-    const int64_t words = radix_scratch_words(n_max, passes);
-    sg_status s = ensure(fr.hist, sizeof(uint32_t) * words);
-    if (s != SG_OK) return s;
     uint32_t *hist = (uint32_t *)fr.hist.p;
+    sg_status s;
+    if (!counted && (s = radix_prepare(n_max, passes, fr, st, &hist, 0)) != SG_OK) return s;
     uint32_t *offsets = hist + 256 * passes;
     uint32_t *tickets = offsets + 256 * passes;             // [passes], padded to 16
     uint32_t *lookback = tickets + 16;
     uint32_t *err = (uint32_t *)fr.scalars.p + 8;
-    SG_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 256 * passes, st));
-    SG_CUDA(cudaMemsetAsync(tickets, 0, sizeof(uint32_t) * (words - 2 * 256 * passes), st));
-    int dev = 0, sms = 0;
-    SG_CUDA(cudaGetDevice(&dev));
-    SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // about kHistKeys keys per thread, at most two resident blocks per SM
-    const int64_t hist_want = (n_max + kRadixThreads * kHistKeys - 1) / (kRadixThreads * kHistKeys);
-    const int64_t hist_blocks = hist_want < 2 * sms ? hist_want : 2 * sms;
-    k_sort_hist<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys[0], d_n, begin_bit, end_bit,
-                                                                 hist);
-    SG_LAUNCHED();
+    if (!counted) {
+        int dev = 0, sms = 0;
+        SG_CUDA(cudaGetDevice(&dev));
+        SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        // about kHistKeys keys per thread, at most two resident blocks per SM
+        const int64_t hist_want =
+            (n_max + kRadixThreads * kHistKeys - 1) / (kRadixThreads * kHistKeys);
+        const int64_t hist_blocks = hist_want < 2 * sms ? hist_want : 2 * sms;
+        k_sort_hist<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys[0], d_n, begin_bit,
+                                                                     end_bit, hist);
+        SG_LAUNCHED();
+    }
     k_sort_offsets<<<1, 256, 0, st>>>(hist, passes, offsets);
     SG_LAUNCHED();
     int cur = 0;
@@ -365,61 +279,213 @@ sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
     return SG_OK;
 }
 
-// ------------------------------------------------------------------ compaction
+// ------------------------------------------------------------------ depth stage
+// The depth stage as two chained scans around the radix passes.  A block
+// takes the next tile of kChainTile entries (an atomic ticket, so tiles are
+// taken in order), publishes its total, and walks back over earlier tiles'
+// published totals until an inclusive prefix (64-bit words: two flag bits,
+// a 62-bit count), as the radix passes do:
+//   k_compact_depth: the Gaussians with a non-zero tile count, in id order,
+//     as (depth bits, id) pairs, the number of them, and the digit
+//     histograms of the four radix passes over their keys;
+//   k_pair_offsets: in depth order, the exclusive scan of the tile counts
+//     count[ids[i]] (gathered as it goes) into pair offsets, and the total.
+constexpr int kChainThreads = 256;
+constexpr int kChainWarps = kChainThreads / 32;
+constexpr int kChainChunks = kChainTile / kChainThreads;   // 32-entry chunks per warp
+static_assert(kChainChunks * kChainThreads == kChainTile && kChainChunks == 16, "chain tile");
+constexpr unsigned long long kChAgg = 1ull << 62, kChPre = 2ull << 62,
+                             kChCount = (1ull << 62) - 1ull;
 
-__global__ void k_flags(const uint32_t *__restrict__ count, int64_t n, uint32_t *__restrict__ flags)
+// Exclusive prefix of tile `tile` (total `total`) from the earlier tiles'
+// words, 32 of them per round; warp 0 runs it and every lane returns it.  A
+// wait that runs out sets *err (the prefix is then wrong, never unbounded).
+__device__ unsigned long long chain_lookback(unsigned long long *lb, int64_t tile,
+                                             unsigned long long total, uint32_t *err)
 {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < n) flags[g] = count[g] > 0 ? 1u : 0u;
+    const int lane = threadIdx.x & 31;
+    volatile unsigned long long *v = lb;
+    if (lane == 0) v[tile] = (tile == 0 ? kChPre : kChAgg) | total;
+    unsigned long long excl = 0;
+    uint32_t spins = 0;
+    int64_t t = tile - 1;
+    while (t >= 0) {
+        const int64_t tt = t - lane;
+        const unsigned long long w = tt >= 0 ? v[tt] : (unsigned long long)kChPre;   // before tile 0: empty prefix
+        const uint32_t np = __ballot_sync(0xffffffffu, (w & (kChAgg | kChPre)) == 0ull);
+        const uint32_t pre = __ballot_sync(0xffffffffu, (w & kChPre) != 0ull);
+        const int fnp = np ? __ffs(np) - 1 : 32, fp = pre ? __ffs(pre) - 1 : 32;
+        const int take = fp < fnp ? fp + 1 : fnp;   // lanes [0, take) are summed
+        unsigned long long c = lane < take ? (w & kChCount) : 0ull;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        excl += c;
+        if (fp < fnp) break;
+        t -= take;
+        if (take == 0 && ++spins > kLbSpins) {   // gave up: flag it
+            if (lane == 0) atomicOr(err, 1u);
+            break;
+        }
+    }
+    if (lane == 0 && tile > 0) v[tile] = kChPre | (excl + total);
+    return excl;
 }
 
-__global__ void k_compact(const uint32_t *__restrict__ count, const float *__restrict__ depth,
-                          const uint32_t *__restrict__ pos, int64_t n, uint32_t *__restrict__ keys,
-                          uint32_t *__restrict__ vals)
+__global__ void __launch_bounds__(kChainThreads)
+k_compact_depth(const uint32_t *__restrict__ count, const float *__restrict__ depth, int64_t n,
+                int64_t ntiles, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                uint32_t *__restrict__ d_nvalid, uint32_t *__restrict__ hist,
+                unsigned long long *__restrict__ lb, uint32_t *__restrict__ ticket,
+                uint32_t *__restrict__ err)
 {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < n && count[g] > 0) {
-        uint32_t p = pos[g];
-        keys[p] = __float_as_uint(depth[g]);   // depth > 0: bits are monotone
-        vals[p] = (uint32_t)g;
+    __shared__ uint32_t s_h[4][256];
+    __shared__ uint32_t s_warp[kChainWarps];
+    __shared__ uint32_t s_tile;
+    for (int i = threadIdx.x; i < 4 * 256; i += kChainThreads) (&s_h[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp w owns kChainChunks x 32 consecutive entries of the tile
+    const int64_t wbase = tile * kChainTile + (int64_t)warp * 32 * kChainChunks;
+    uint32_t cnt[kChainChunks], bal[kChainChunks], key[kChainChunks];
+#pragma unroll
+    for (int r = 0; r < kChainChunks; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
+        cnt[r] = i < n ? count[i] : 0u;
+        key[r] = i < n ? __float_as_uint(depth[i]) : 0u;   // depth > 0: bits are monotone
+    }
+    uint32_t wtot = 0;
+#pragma unroll
+    for (int r = 0; r < kChainChunks; ++r) {
+        const bool ok = cnt[r] > 0u;
+        bal[r] = __ballot_sync(0xffffffffu, ok);
+        wtot += __popc(bal[r]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const uint32_t d = ok ? (key[r] >> (8 * p)) & 255u : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_h[p][d], (uint32_t)__popc(peers));
+        }
+    }
+    if (lane == 0) s_warp[warp] = wtot;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < kChainWarps ? s_warp[lane] : 0u;
+        const uint32_t inc = warp_incl_scan(v);
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, kChainWarps - 1);
+        const uint32_t excl = (uint32_t)chain_lookback(lb, tile, total, err);
+        if (lane < kChainWarps) s_warp[lane] = excl + inc - v;
+        if (lane == 0 && tile == ntiles - 1) *d_nvalid = excl + total;
+    }
+    __syncthreads();
+    uint32_t pos = s_warp[warp];
+#pragma unroll
+    for (int r = 0; r < kChainChunks; ++r) {
+        if ((bal[r] >> lane) & 1u) {
+            const uint32_t q = pos + __popc(bal[r] & ((1u << lane) - 1u));
+            keys[q] = key[r];
+            vals[q] = (uint32_t)(wbase + r * 32 + lane);
+        }
+        pos += __popc(bal[r]);
+    }
+    for (int i = threadIdx.x; i < 4 * 256; i += kChainThreads) {
+        const uint32_t c = (&s_h[0][0])[i];
+        if (c) atomicAdd(&hist[i], c);
     }
 }
 
-sg_status compact_valid(const uint32_t *d_count, const float *d_depth, int64_t n,
-                        uint32_t *d_keys, uint32_t *d_vals, uint32_t *d_nvalid, Frame &fr,
-                        cudaStream_t st)
+__global__ void __launch_bounds__(kChainThreads)
+k_pair_offsets(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ count,
+               const uint32_t *__restrict__ d_nvalid, uint32_t *__restrict__ offsets,
+               uint32_t *__restrict__ d_total, unsigned long long *__restrict__ lb,
+               uint32_t *__restrict__ ticket, uint32_t *__restrict__ err)
 {
-    if (n == 0) {
-        SG_CUDA(cudaMemsetAsync(d_nvalid, 0, 4, st));
+    __shared__ uint32_t s_warp[kChainWarps];
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t nv = *d_nvalid;
+    const int64_t ntiles = (nv + kChainTile - 1) / kChainTile;
+    if (nv == 0) {
+        if (tile == 0 && threadIdx.x == 0) *d_total = 0u;
+        return;
+    }
+    if (tile >= ntiles) return;   // so is every later tile: nobody waits for this one
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t wbase = tile * kChainTile + (int64_t)warp * 32 * kChainChunks;
+    uint32_t c[kChainChunks];
+#pragma unroll
+    for (int r = 0; r < kChainChunks; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
+        c[r] = i < nv ? ids[i] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int r = 0; r < kChainChunks; ++r) c[r] = c[r] != 0xffffffffu ? count[c[r]] : 0u;
+    uint32_t run = 0;   // the warp's entries before chunk r
+#pragma unroll
+    for (int r = 0; r < kChainChunks; ++r) {
+        const uint32_t inc = warp_incl_scan(c[r]);
+        const uint32_t v = c[r];
+        c[r] = run + inc - v;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) s_warp[warp] = run;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < kChainWarps ? s_warp[lane] : 0u;
+        const uint32_t inc = warp_incl_scan(v);
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, kChainWarps - 1);
+        const unsigned long long excl = chain_lookback(lb, tile, total, err);
+        if (lane < kChainWarps) s_warp[lane] = (uint32_t)excl + inc - v;
+        if (lane == 0 && tile == ntiles - 1) {
+            // saturated, so that a total of 2^32 pairs or more reads as an overflow
+            const unsigned long long tot = excl + total;
+            *d_total = tot > 0xffffffffull ? 0xffffffffu : (uint32_t)tot;
+        }
+    }
+    __syncthreads();
+    const uint32_t pre = s_warp[warp];
+#pragma unroll
+    for (int r = 0; r < kChainChunks; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
+        if (i < nv) offsets[i] = pre + c[r];
+    }
+}
+
+sg_status depth_stage(const uint32_t *d_count, const float *d_depth, int64_t n, uint32_t *keys[2],
+                      uint32_t *vals[2], uint32_t *d_scal, uint32_t *d_offsets, Frame &fr,
+                      cudaStream_t st, int *result_buf)
+{
+    *result_buf = 0;
+    if (n <= 0) {
+        SG_CUDA(cudaMemsetAsync(d_scal, 0, 8, st));
         return SG_OK;
     }
-    sg_status s = ensure(fr.flags, sizeof(uint32_t) * 2 * n);
+    if (n > (int64_t)kLbCount) {
+        set_error("depth sort of %lld Gaussians exceeds 2^30", (long long)n);
+        return SG_ERR_OVERFLOW;
+    }
+    // after the radix scratch, zeroed with it: two tickets, then one 64-bit
+    // word per tile for each of the two chained scans
+    const int64_t ntiles = (n + kChainTile - 1) / kChainTile;
+    uint32_t *hist = nullptr;
+    sg_status s =
+        radix_prepare(n, 4, fr, st, &hist, depth_stage_words(n) - radix_scratch_words(n, 4));
     if (s != SG_OK) return s;
-    uint32_t *flags = (uint32_t *)fr.flags.p, *pos = flags + n;
-    unsigned grid = (unsigned)((n + 255) / 256);
-    k_flags<<<grid, 256, 0, st>>>(d_count, n, flags);
+    static_assert(radix_scratch_words(1, 4) % 2 == 0, "64-bit chain words stay aligned");
+    unsigned long long *chain = (unsigned long long *)(hist + radix_scratch_words(n, 4));
+    uint32_t *tickets = (uint32_t *)chain;                 // [0] compaction, [1] offsets
+    uint32_t *err = (uint32_t *)fr.scalars.p + 8;
+    k_compact_depth<<<(unsigned)ntiles, kChainThreads, 0, st>>>(
+        d_count, d_depth, n, ntiles, keys[0], vals[0], d_scal, hist, chain + 2, tickets, err);
     SG_LAUNCHED();
-    s = scan_exclusive_u32(flags, pos, d_nvalid, n, fr, st);
-    if (s != SG_OK) return s;
-    k_compact<<<grid, 256, 0, st>>>(d_count, d_depth, pos, n, d_keys, d_vals);
-    SG_LAUNCHED();
-    return SG_OK;
-}
-
-__global__ void k_gather_counts(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ count,
-                                const uint32_t *__restrict__ d_nvalid, int64_t n,
-                                uint32_t *__restrict__ out)
-{
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = i < (int64_t)*d_nvalid ? count[ids[i]] : 0u;
-}
-
-sg_status gather_counts(const uint32_t *d_ids, const uint32_t *d_count, const uint32_t *d_nvalid,
-                        int64_t n, uint32_t *d_out, cudaStream_t st)
-{
-    if (n == 0) return SG_OK;
-    k_gather_counts<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_ids, d_count, d_nvalid, n,
-                                                                 d_out);
+    if ((s = radix_sort_pairs(keys, vals, n, d_scal, 0, 32, fr, st, result_buf, true)) != SG_OK)
+        return s;
+    k_pair_offsets<<<(unsigned)ntiles, kChainThreads, 0, st>>>(
+        vals[*result_buf], d_count, d_scal, d_offsets, d_scal + 1, chain + 2 + ntiles,
+        tickets + 1, err);
     SG_LAUNCHED();
     return SG_OK;
 }
@@ -488,12 +554,10 @@ k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
     }
 }
 
-sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_counts,
-                    const uint32_t *d_nvalid, int64_t n, const int4 *d_tiles, int ntx, int wrap_x,
-                    int64_t cap, uint32_t *d_keys, uint32_t *d_vals, cudaStream_t st)
+sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_nvalid,
+                    const int4 *d_tiles, int ntx, int wrap_x, int64_t cap, uint32_t *d_keys,
+                    uint32_t *d_vals, cudaStream_t st)
 {
-    (void)d_counts;
-    (void)n;
     if (cap <= 0) return SG_OK;
     k_bin<<<(unsigned)((cap + kBinChunk - 1) / kBinChunk), kBinThreads, 0, st>>>(
         d_ids, d_offsets, d_nvalid, d_tiles, ntx, wrap_x, (uint32_t)cap, d_keys, d_vals);

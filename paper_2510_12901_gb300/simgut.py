@@ -133,6 +133,7 @@ _SIGNATURES = {
     "sg_server_destroy": (None, [_H]),
     "sg_frame_set_timing": (C.c_int, [_H, C.c_int]),
     "sg_frame_timing": (C.c_int, [_H, C.POINTER(C.c_float)]),
+    "sg_frame_marks": (C.c_int, [_H, _H, C.POINTER(C.c_float)]),
 }
 
 _lib = None
@@ -380,6 +381,12 @@ def sg_frame_set_timing(frame, on):
 def sg_frame_timing(frame):
     ms = (C.c_float * 4)()
     _check(load().sg_frame_timing(frame, ms))
+    return list(ms)
+
+
+def sg_frame_marks(frame, ref):
+    ms = (C.c_float * 5)()
+    _check(load().sg_frame_marks(frame, ref, ms))
     return list(ms)
 
 

@@ -105,3 +105,35 @@ def test_bad_view_lists_are_refused(rig):
     with pytest.raises(sg.SimgutError):
         sg.sg_render_cameras(rig["S"].handle, shared, rig["opts"], 0)
     sg.sg_render_cameras(rig["S"].handle, sg.sg_camera_views([]), rig["opts"], 0)   # no views: no-op
+
+
+def test_stage_marks_place_views_on_one_time_line(rig):
+    """sg_frame_marks: each view's five stage boundaries are non-decreasing,
+    their differences are the view's sg_frame_timing stages, a frame against
+    itself starts at 0, and views on two streams fall within the call."""
+    import torch
+    sg = rig["sg"]
+    ss = [torch.cuda.Stream() for _ in range(2)]
+    frames = [sg.Frame() for _ in rig["cams"][:2]]
+    for f in frames:
+        sg.sg_frame_set_timing(f.handle, 1)
+    outs, views = [], []
+    for i, (ch, c, f) in enumerate(zip(rig["cams"][:2], rig["specs"][:2], frames)):
+        o = [torch.empty((c.height, c.width, 3), device="cuda"),
+             torch.empty((c.height, c.width), device="cuda"),
+             torch.empty((c.height, c.width), device="cuda")]
+        outs.append(o)
+        views.append((ch.handle, c.c2w, f.handle, o[0].data_ptr(), o[1].data_ptr(),
+                      o[2].data_ptr(), ss[i].cuda_stream))
+    torch.cuda.synchronize()
+    sg.sg_render_cameras(rig["S"].handle, sg.sg_camera_views(views), rig["opts"], 0)
+    torch.cuda.synchronize()
+    m0 = sg.sg_frame_marks(frames[0].handle, frames[0].handle)
+    m1 = sg.sg_frame_marks(frames[1].handle, frames[0].handle)
+    assert m0[0] == 0.0
+    for m, f in ((m0, frames[0]), (m1, frames[1])):
+        assert all(b >= a for a, b in zip(m, m[1:]))
+        st = sg.sg_frame_timing(f.handle)
+        assert np.allclose(np.diff(m), st, atol=2e-3)
+    # both views ran within one call: neither starts after the other ends
+    assert m1[0] < m0[4] and m1[4] > 0.0

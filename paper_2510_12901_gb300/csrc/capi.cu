@@ -256,16 +256,25 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     }
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
-    s = bin_pairs((const uint32_t *)fr.dvals[fr.depth_buf].p, (const uint32_t *)fr.offsets.p, sc,
-                  (const int4 *)fr.tiles.p, ntx, wrap, K, pk[0], pv[0], st);
-    if (s != SG_OK) return s;
     int bits = 1;
     while (((int64_t)1 << bits) < ntiles) ++bits;
+    // binning counts the tile sort's digits as it writes the pairs
+    uint32_t *hist = nullptr;
+    if (K > 0 && (s = radix_prepare(K, (bits + 7) / 8, fr, st, &hist, 0)) != SG_OK) return s;
+    s = bin_pairs((const uint32_t *)fr.dvals[fr.depth_buf].p, (const uint32_t *)fr.offsets.p, sc,
+                  (const int4 *)fr.tiles.p, ntx, wrap, K, pk[0], pv[0], st, hist, bits);
+    if (s != SG_OK) return s;
     int pb = 0;
     s = radix_sort_pairs(pk, pv, K, sc + 1, 0, bits, fr, st, &pb);
     if (s != SG_OK) return s;
     fr.pair_buf = pb;
-    s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st);
+    if (fr.kind == 1) {
+        s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st);
+    } else {   // camera lists also get their sub-block masks
+        if ((s = ensure(fr.submask, K > 0 ? (size_t)K : 1)) != SG_OK) return s;
+        s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, pv[pb],
+                        (const GRec *)fr.rec.p, ntx, (uint8_t *)fr.submask.p);
+    }
     if (s != SG_OK) return s;
     if (fr.k_cap > 0)
         SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 16, cudaMemcpyDeviceToHost, st));

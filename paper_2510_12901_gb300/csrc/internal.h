@@ -261,9 +261,11 @@ constexpr int64_t depth_stage_words(int64_t n)
 }
 sg_status radix_prepare(int64_t n_max, int passes, Frame &fr, cudaStream_t st, uint32_t **hist,
                         int64_t extra);
+// Stable sort of up to n pairs (*d_n of them) by key bits [begin_bit,
+// end_bit); the digit counts are in the scratch that radix_prepare returned.
 sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n,
                            const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
-                           cudaStream_t st, int *result_buf, bool counted = false);
+                           cudaStream_t st, int *result_buf);
 // The depth stage: the Gaussians with a non-zero tile count sorted by depth
 // (keys/vals[*result_buf]: depth bits, ids), d_scal[0] = their number,
 // d_offsets = exclusive scan of their tile counts in that order, d_scal[1]
@@ -271,11 +273,18 @@ sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n,
 sg_status depth_stage(const uint32_t *d_count, const float *d_depth, int64_t n, uint32_t *keys[2],
                       uint32_t *vals[2], uint32_t *d_scal, uint32_t *d_offsets, Frame &fr,
                       cudaStream_t st, int *result_buf);
+// With d_hist (zeroed by radix_prepare), k_bin also counts the digits of
+// the tile sort over end_bit bits, for radix_sort_pairs.
 sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_nvalid,
                     const int4 *d_tiles, int ntx, int wrap_x, int64_t cap, uint32_t *d_keys,
-                    uint32_t *d_vals, cudaStream_t st);
+                    uint32_t *d_vals, cudaStream_t st, uint32_t *d_hist = nullptr,
+                    int end_bit = 0);
+// Per-tile ranges of the sorted pairs; with d_mask (camera lists), also the
+// per-pair sub-block masks (d_ids, d_rec, ntx: the pairs' Gaussians, their
+// records, tiles per row).
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
-                      int64_t ntiles, cudaStream_t st);
+                      int64_t ntiles, cudaStream_t st, const uint32_t *d_ids = nullptr,
+                      const GRec *d_rec = nullptr, int ntx = 0, uint8_t *d_mask = nullptr);
 sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStream_t st);
 
 // project.cu

@@ -188,14 +188,19 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     fr.n_pairs = K;
     uint32_t *pk[2] = {(uint32_t *)fr.pkeys[0].p, (uint32_t *)fr.pkeys[1].p};
     uint32_t *pv[2] = {(uint32_t *)fr.pvals[0].p, (uint32_t *)fr.pvals[1].p};
-    if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, scal, (const int4 *)fr.tiles.p,
-                       c.ntx, 0, K, pk[0], pv[0], st)) != SG_OK)
-        return s;
     int bits = 1;
     while (((int64_t)1 << bits) < nt) ++bits;
+    uint32_t *hist = nullptr;
+    if (K > 0 && (s = radix_prepare(K, (bits + 7) / 8, fr, st, &hist, 0)) != SG_OK) return s;
+    if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, scal, (const int4 *)fr.tiles.p,
+                       c.ntx, 0, K, pk[0], pv[0], st, hist, bits)) != SG_OK)
+        return s;
     int pb = 0;
-    if ((s = radix_sort_pairs(pk, pv, K, scal + 1, 0, bits, fr, st, &pb)) != SG_OK) return s;
+    if ((s = radix_sort_pairs(pk, pv, K, scal + 1, 0, bits, fr, st, &pb)) != SG_OK)
+        return s;
     fr.pair_buf = pb;
-    if ((s = tile_ranges(pk[pb], scal + 1, K, (uint2 *)fr.ranges.p, nt, st)) != SG_OK) return s;
+    if ((s = tile_ranges(pk[pb], scal + 1, K, (uint2 *)fr.ranges.p, nt, st, pv[pb],
+                         (const GRec *)fr.rec.p, c.ntx, (uint8_t *)fr.submask.p)) != SG_OK)
+        return s;
     return render_camera(c, *opts, fr, st);
 }

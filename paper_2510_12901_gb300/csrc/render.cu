@@ -218,39 +218,6 @@ static sg_status launch_work_items(Frame &fr, const WorkSize &ws, const LidarIte
     return SG_OK;
 }
 
-// Per (tile, Gaussian) pair of a camera list: which of the tile's eight
-// 8x4 pixel sub-blocks hold a pixel centre inside the Gaussian's extent box
-// (bit w: columns 8*(w&1).., rows 4*(w>>1)..), by the same float comparisons
-// as the per-ray test.  One byte per pair, written after the tile sort, so
-// that the compositing warps scan contiguous bytes and never stage an entry
-// that no pixel of their sub-block can see.
-__global__ void k_submask(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ ids,
-                          const GRec *__restrict__ rec, const uint32_t *__restrict__ d_K, int ntx,
-                          uint8_t *__restrict__ mask)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)*d_K) return;
-    const uint32_t t = keys[i];
-    const float4 rc = rec[ids[i]].rect;
-    const int tx = (int)(t % (uint32_t)ntx), ty = (int)(t / (uint32_t)ntx);
-    uint32_t cols = 0, rows = 0;
-#pragma unroll
-    for (int c = 0; c < kTile; ++c) {
-        const float x = (float)(tx * kTile + c) + 0.5f;
-        const float y = (float)(ty * kTile + c) + 0.5f;
-        cols |= (uint32_t)(x >= rc.x && x <= rc.y) << c;
-        rows |= (uint32_t)(y >= rc.z && y <= rc.w) << c;
-    }
-    uint32_t m = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const bool cx = ((cols >> (8 * (w & 1))) & 0xffu) != 0u;
-        const bool cy = ((rows >> (4 * (w >> 1))) & 0xfu) != 0u;
-        m |= (uint32_t)(cx && cy) << w;
-    }
-    mask[i] = (uint8_t)m;
-}
-
 // Camera compositing, persistent and warp-independent.  A work item is one
 // 8x4 pixel sub-block of a 16x16 tile and one segment of that tile's list
 // (k_camera_items); items are taken in order of decreasing tile-list length
@@ -523,7 +490,10 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
-    if (s == SG_OK) s = ensure(fr.submask, K > 0 ? (size_t)K : 1);
+    if (s == SG_OK && fr.submask.bytes < (size_t)(K > 0 ? K : 1)) {
+        set_error("internal: sub-block masks of the camera list missing");
+        s = SG_ERR_INVALID;
+    }
     if (s != SG_OK) return s;
     unsigned char *cw = (unsigned char *)fr.camwork.p;
     const uint2 *tile_info = (const uint2 *)cw;
@@ -533,12 +503,6 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     uint32_t *counter = (uint32_t *)fr.scalars.p + 2;
     if ((s = launch_work_items(fr, ws, nullptr, nt, 8, fr.seg_len, st)) != SG_OK) return s;
     const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
-    if (K > 0) {
-        k_submask<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(
-            (const uint32_t *)fr.pkeys[fr.pair_buf].p, ids, (const GRec *)fr.rec.p,
-            (const uint32_t *)fr.scalars.p + 1, cam.ntx, (uint8_t *)fr.submask.p);
-        SG_LAUNCHED();
-    }
     int dev = 0, sms = 0;
     SG_CUDA(cudaGetDevice(&dev));
     SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -764,7 +728,10 @@ sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
-    if (s == SG_OK) s = ensure(fr.submask, K > 0 ? (size_t)K : 1);
+    if (s == SG_OK && fr.submask.bytes < (size_t)(K > 0 ? K : 1)) {
+        set_error("internal: sub-block masks of the camera list missing");
+        s = SG_ERR_INVALID;
+    }
     if (s != SG_OK) return s;
     unsigned char *cw = (unsigned char *)fr.camwork.p;
     const uint2 *tile_info = (const uint2 *)cw;
@@ -774,12 +741,6 @@ sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr
     uint32_t *counter = (uint32_t *)fr.scalars.p + 2;
     if ((s = launch_work_items(fr, ws, nullptr, nt, 8, fr.seg_len, st)) != SG_OK) return s;
     const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
-    if (K > 0) {
-        k_submask<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(
-            (const uint32_t *)fr.pkeys[fr.pair_buf].p, ids, (const GRec *)fr.rec.p,
-            (const uint32_t *)fr.scalars.p + 1, cam.ntx, (uint8_t *)fr.submask.p);
-        SG_LAUNCHED();
-    }
     int dev = 0, sms = 0, nb = 0;
     SG_CUDA(cudaGetDevice(&dev));
     SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -71,9 +71,10 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid)
 
 // Stable LSD radix sort of (key, value) pairs, 8-bit digits, one kernel per
 // digit pass with decoupled look-back (the "onesweep" scheme):
-//   1. k_sort_hist: one read of the keys counts the digits of every pass;
-//   2. k_sort_offsets: per pass, the exclusive scan of its 256 counts gives
-//      the first output position of each digit;
+//   1. the kernel that writes the keys counts the digits of every pass
+//      (k_compact_depth, k_bin) into scratch that radix_prepare zeroed;
+//   2. per pass, the exclusive scan of its 256 counts gives the first
+//      output position of each digit (every block of the pass scans them);
 //   3. k_onesweep, per pass: a block takes the next tile of kRadixTile pairs
 //      (an atomic ticket, so tiles are taken in order), ranks them stably
 //      (each warp owns kRadixItems x 32 consecutive pairs, ranks among equal
@@ -97,59 +98,17 @@ constexpr uint32_t kLbSpins = 1u << 22;
 #define SG_LB_BATCH 8
 #endif
 constexpr int kLbBatch = SG_LB_BATCH;   // earlier tiles' words loaded per look-back round
-#ifndef SG_HIST_KEYS
-#define SG_HIST_KEYS 1
-#endif
-constexpr int kHistKeys = SG_HIST_KEYS;
-
-__global__ void __launch_bounds__(kRadixThreads)
-k_sort_hist(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_n, int begin_bit,
-            int end_bit, uint32_t *__restrict__ hist)
-{
-    __shared__ uint32_t s_h[4][256];
-    for (int i = threadIdx.x; i < 4 * 256; i += kRadixThreads) (&s_h[0][0])[i] = 0;
-    __syncthreads();
-    const int64_t n = *d_n;
-    const int passes = (end_bit - begin_bit + 7) / 8;
-    for (int64_t i = (int64_t)blockIdx.x * kRadixThreads + threadIdx.x;
-         i - threadIdx.x < n; i += (int64_t)gridDim.x * kRadixThreads) {
-        const bool in = i < n;
-        const uint32_t k = in ? keys[i] : 0u;
-        for (int p = 0; p < passes; ++p) {
-            const int b = begin_bit + 8 * p;
-            const int bits = end_bit - b < 8 ? end_bit - b : 8;
-            const uint32_t d = in ? (k >> b) & ((1u << bits) - 1u) : 0xffffffffu;
-            const uint32_t peers = digit_peers(d, in);
-            if (in && (threadIdx.x & 31) == __ffs(peers) - 1)
-                atomicAdd(&s_h[p][d], (uint32_t)__popc(peers));
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 256)
-        for (int p = 0; p < passes; ++p)
-            if (s_h[p][threadIdx.x]) atomicAdd(&hist[p * 256 + threadIdx.x], s_h[p][threadIdx.x]);
-}
-
-__global__ void __launch_bounds__(256)
-k_sort_offsets(const uint32_t *__restrict__ hist, int passes, uint32_t *__restrict__ offsets)
-{
-    __shared__ uint32_t s_warp[33];
-    for (int p = 0; p < passes; ++p) {
-        uint32_t tot;
-        offsets[p * 256 + threadIdx.x] =
-            block_excl_scan(hist[p * 256 + threadIdx.x], s_warp, &tot);
-    }
-}
 
 __global__ void __launch_bounds__(kRadixThreads)
 k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
            uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
            const uint32_t *__restrict__ d_n, int shift, uint32_t mask,
-           const uint32_t *__restrict__ offsets, uint32_t *__restrict__ lookback,
+           const uint32_t *__restrict__ hist, uint32_t *__restrict__ lookback,
            uint32_t *__restrict__ ticket, uint32_t *__restrict__ err)
 {
     __shared__ uint32_t s_cnt[kRadixWarps][256];
     __shared__ uint32_t s_pre[256];
+    __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kRadixWarps * 256; i += kRadixThreads) (&s_cnt[0][0])[i] = 0;
@@ -159,6 +118,11 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
     const int64_t n = *d_n;
     const int64_t base = (int64_t)tile * kRadixTile;
     if (base >= n) return;     // so is every later tile: nobody waits for this one
+    // the first output position of this thread's digit (threads < 256): the
+    // exclusive scan of the pass's digit counts, done by every block
+    uint32_t dig_total;
+    const uint32_t dig_off =
+        block_excl_scan(threadIdx.x < 256 ? hist[threadIdx.x] : 0u, s_warp, &dig_total);
     uint32_t k[kRadixItems], v[kRadixItems], d[kRadixItems], rk[kRadixItems];
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
@@ -220,7 +184,7 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
             }
         }
         if (tile > 0) lb[(int64_t)tile * 256 + dg] = kLbPre | (excl + run);
-        s_pre[dg] = offsets[dg] + excl;
+        s_pre[dg] = dig_off + excl;
     }
     __syncthreads();
 #pragma unroll
@@ -235,8 +199,8 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
 }
 
 // Zero the radix scratch (histograms, tickets, look-back words) for a sort
-// of up to n_max pairs in `passes` passes; *hist gets the histograms, for a
-// caller that counts the digits itself (radix_sort_pairs with counted).
+// of up to n_max pairs in `passes` passes; *hist gets the histograms, which
+// the kernel that writes the keys fills before radix_sort_pairs runs.
 // `extra` more zeroed words follow the scratch (at hist + radix_scratch_words).
 sg_status radix_prepare(int64_t n_max, int passes, Frame &fr, cudaStream_t st, uint32_t **hist,
                         int64_t extra)
@@ -251,7 +215,7 @@ sg_status radix_prepare(int64_t n_max, int passes, Frame &fr, cudaStream_t st, u
 
 sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                            const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
-                           cudaStream_t st, int *result_buf, bool counted)
+                           cudaStream_t st, int *result_buf)
 {
     *result_buf = 0;
     if (n_max <= 0 || end_bit <= begin_bit) return SG_OK;
@@ -262,33 +226,16 @@ sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
     const int passes = (end_bit - begin_bit + 7) / 8;
     const int64_t tiles = (n_max + kRadixTile - 1) / kRadixTile;
     uint32_t *hist = (uint32_t *)fr.hist.p;
-    sg_status s;
-    if (!counted && (s = radix_prepare(n_max, passes, fr, st, &hist, 0)) != SG_OK) return s;
-    uint32_t *offsets = hist + 256 * passes;
-    uint32_t *tickets = offsets + 256 * passes;             // [passes], padded to 16
+    uint32_t *tickets = hist + 2 * 256 * passes;            // [passes], padded to 16
     uint32_t *lookback = tickets + 16;
     uint32_t *err = (uint32_t *)fr.scalars.p + 8;
-    if (!counted) {
-        int dev = 0, sms = 0;
-        SG_CUDA(cudaGetDevice(&dev));
-        SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        // about kHistKeys keys per thread, at most two resident blocks per SM
-        const int64_t hist_want =
-            (n_max + kRadixThreads * kHistKeys - 1) / (kRadixThreads * kHistKeys);
-        const int64_t hist_blocks = hist_want < 2 * sms ? hist_want : 2 * sms;
-        k_sort_hist<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys[0], d_n, begin_bit,
-                                                                     end_bit, hist);
-        SG_LAUNCHED();
-    }
-    k_sort_offsets<<<1, 256, 0, st>>>(hist, passes, offsets);
-    SG_LAUNCHED();
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         const int b = begin_bit + 8 * p;
         const int bits = end_bit - b < 8 ? end_bit - b : 8;
         k_onesweep<<<(unsigned)tiles, kRadixThreads, 0, st>>>(
             keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n, b, (1u << bits) - 1u,
-            offsets + 256 * p, lookback + (int64_t)p * tiles * 256, tickets + p, err);
+            hist + 256 * p, lookback + (int64_t)p * tiles * 256, tickets + p, err);
         SG_LAUNCHED();
         cur ^= 1;
     }
@@ -498,7 +445,7 @@ sg_status depth_stage(const uint32_t *d_count, const float *d_depth, int64_t n, 
     k_compact_depth<<<(unsigned)ntiles, kChainThreads, 0, st>>>(
         d_count, d_depth, n, ntiles, keys[0], vals[0], d_scal, hist, chain + 2, tickets, err);
     SG_LAUNCHED();
-    if ((s = radix_sort_pairs(keys, vals, n, d_scal, 0, 32, fr, st, result_buf, true)) != SG_OK)
+    if ((s = radix_sort_pairs(keys, vals, n, d_scal, 0, 32, fr, st, result_buf)) != SG_OK)
         return s;
     k_pair_offsets<<<(unsigned)ntiles, kChainThreads, 0, st>>>(
         vals[*result_buf], d_count, d_scal, d_offsets, d_scal + 1, chain + 2 + ntiles,
@@ -522,15 +469,20 @@ sg_status depth_stage(const uint32_t *d_count, const float *d_depth, int64_t n, 
 // (owner by binary search in shared memory, tile from the owner's range).
 // A Gaussian that covers thousands of tiles is spread over many blocks.
 constexpr int kBinThreads = 256;
+constexpr int kBinPasses = 3;         // tile ids up to 24 bits when k_bin counts the digits
 constexpr int kBinChunk = 1024;
 
 __global__ void __launch_bounds__(kBinThreads)
 k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
       const uint32_t *__restrict__ d_scal, const int4 *__restrict__ tiles, int ntx, int wrap_x,
-      uint32_t cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
+      uint32_t cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+      uint32_t *__restrict__ hist, int end_bit)
 {
     __shared__ uint32_t s_off[kBinChunk + 1], s_id[kBinChunk + 1];
+    __shared__ uint32_t s_h[kBinPasses][256];
     const int t = threadIdx.x;
+    const int passes = (end_bit + 7) / 8;
+    for (int i = t; i < kBinPasses * 256; i += kBinThreads) (&s_h[0][0])[i] = 0u;
     const int64_t nvalid = d_scal[0];
     const int64_t K = min((int64_t)d_scal[1], (int64_t)cap);
     const int64_t p0 = (int64_t)blockIdx.x * kBinChunk;
@@ -554,36 +506,71 @@ k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
         s_id[i] = ids[k0 + i];
     }
     __syncthreads();
-    for (int64_t pos = p0 + t; pos < p1; pos += kBinThreads) {
-        int a = 0, b = nk;             // the last j with s_off[j] <= pos
-        while (b - a > 1) {
-            const int m = (a + b) >> 1;
-            if ((int64_t)s_off[m] <= pos) a = m; else b = m;
+    for (int r0 = 0; r0 < kBinChunk; r0 += kBinThreads) {
+        const int64_t pos = p0 + r0 + t;
+        const bool in = pos < p1;
+        uint32_t key = 0u;
+        if (in) {
+            int a = 0, b = nk;             // the last j with s_off[j] <= pos
+            while (b - a > 1) {
+                const int m = (a + b) >> 1;
+                if ((int64_t)s_off[m] <= pos) a = m; else b = m;
+            }
+            const uint32_t g = s_id[a];
+            const int4 r = tiles[g];
+            const uint32_t local = (uint32_t)(pos - s_off[a]), w = (uint32_t)(r.y - r.x + 1);
+            const int ty = r.z + (int)(local / w);
+            int x = r.x + (int)(local % w);
+            if (wrap_x) { x %= ntx; if (x < 0) x += ntx; }
+            key = (uint32_t)(ty * ntx + x);
+            keys[pos] = key;
+            vals[pos] = g;
         }
-        const uint32_t g = s_id[a];
-        const int4 r = tiles[g];
-        const uint32_t local = (uint32_t)(pos - s_off[a]), w = (uint32_t)(r.y - r.x + 1);
-        const int ty = r.z + (int)(local / w);
-        int x = r.x + (int)(local % w);
-        if (wrap_x) { x %= ntx; if (x < 0) x += ntx; }
-        keys[pos] = (uint32_t)(ty * ntx + x);
-        vals[pos] = g;
+        if (hist) {
+            // the digit counts of every tile-sort pass
+            for (int p = 0; p < passes; ++p) {
+                const int bits = end_bit - 8 * p < 8 ? end_bit - 8 * p : 8;
+                const uint32_t dg = (key >> (8 * p)) & ((1u << bits) - 1u);
+                const uint32_t peers = digit_peers(dg, in);
+                if (in && (t & 31) == __ffs(peers) - 1) atomicAdd(&s_h[p][dg], (uint32_t)__popc(peers));
+            }
+        }
+    }
+    if (hist) {
+        __syncthreads();
+        for (int i = t; i < passes * 256; i += kBinThreads) {
+            const uint32_t c = (&s_h[0][0])[i];
+            if (c) atomicAdd(&hist[i], c);
+        }
     }
 }
 
 sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_nvalid,
                     const int4 *d_tiles, int ntx, int wrap_x, int64_t cap, uint32_t *d_keys,
-                    uint32_t *d_vals, cudaStream_t st)
+                    uint32_t *d_vals, cudaStream_t st, uint32_t *d_hist, int end_bit)
 {
     if (cap <= 0) return SG_OK;
+    if (d_hist && (end_bit < 1 || end_bit > 8 * kBinPasses)) {
+        set_error("internal: %d-bit tile ids", end_bit);
+        return SG_ERR_INVALID;
+    }
     k_bin<<<(unsigned)((cap + kBinChunk - 1) / kBinChunk), kBinThreads, 0, st>>>(
-        d_ids, d_offsets, d_nvalid, d_tiles, ntx, wrap_x, (uint32_t)cap, d_keys, d_vals);
+        d_ids, d_offsets, d_nvalid, d_tiles, ntx, wrap_x, (uint32_t)cap, d_keys, d_vals, d_hist,
+        end_bit);
     SG_LAUNCHED();
     return SG_OK;
 }
 
+// Per-tile [start, end) of the sorted pairs, and for camera lists (kMask)
+// the per-pair sub-block mask: which of the tile's eight 8x4 pixel
+// sub-blocks hold a pixel centre inside the Gaussian's extent box (bit w:
+// columns 8 (w & 1) .., rows 4 (w >> 1) ..), by the same float comparisons
+// as the per-ray test.  The compositing warps scan these contiguous bytes
+// and never stage an entry that no pixel of their sub-block can see.
+template <bool kMask>
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
-                         uint2 *__restrict__ ranges)
+                         uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
+                         const GRec *__restrict__ rec, int ntx, uint8_t *__restrict__ mask)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t K = *d_K;
@@ -591,14 +578,39 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__re
     uint32_t t = keys[i];
     if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
     if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    if (kMask) {
+        const float4 rc = rec[ids[i]].rect;
+        const int tx = (int)(t % (uint32_t)ntx), ty = (int)(t / (uint32_t)ntx);
+        uint32_t cols = 0, rows = 0;
+#pragma unroll
+        for (int c = 0; c < kTile; ++c) {
+            const float x = (float)(tx * kTile + c) + 0.5f;
+            const float y = (float)(ty * kTile + c) + 0.5f;
+            cols |= (uint32_t)(x >= rc.x && x <= rc.y) << c;
+            rows |= (uint32_t)(y >= rc.z && y <= rc.w) << c;
+        }
+        uint32_t m = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const bool cx = ((cols >> (8 * (w & 1))) & 0xffu) != 0u;
+            const bool cy = ((rows >> (4 * (w >> 1))) & 0xfu) != 0u;
+            m |= (uint32_t)(cx && cy) << w;
+        }
+        mask[i] = (uint8_t)m;
+    }
 }
 
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
-                      int64_t ntiles, cudaStream_t st)
+                      int64_t ntiles, cudaStream_t st, const uint32_t *d_ids, const GRec *d_rec,
+                      int ntx, uint8_t *d_mask)
 {
     SG_CUDA(cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * ntiles, st));
     if (K_max == 0) return SG_OK;
-    k_ranges<<<(unsigned)((K_max + 255) / 256), 256, 0, st>>>(d_keys, d_K, d_ranges);
+    const unsigned grid = (unsigned)((K_max + 255) / 256);
+    if (d_mask)
+        k_ranges<true><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rec, ntx, d_mask);
+    else
+        k_ranges<false><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, nullptr, nullptr, 0, nullptr);
     SG_LAUNCHED();
     return SG_OK;
 }

@@ -627,7 +627,9 @@ def roofline(per_view, union_ms, seq_view, clocks):
         tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
         if tr.get("source_sha256") == kernel_source_hash():
             out["traffic"] = tr.get("k_render_camera")
-            out["traffic_note"] = "dram bytes of one fisheye-view launch (ncu), profiles/"
+            out["traffic_note"] = ("dram bytes per launch, mean of the fisheye and pinhole launches "
+                                   "(ncu), profiles/")
+            out["traffic_per_view"] = tr.get("per_view")
         else:
             out["traffic"] = None
             out["traffic_note"] = "kernel changed since the ncu capture in profiles/"

@@ -273,7 +273,7 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     } else {   // camera lists also get their sub-block masks
         if ((s = ensure(fr.submask, K > 0 ? (size_t)K : 1)) != SG_OK) return s;
         s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, pv[pb],
-                        (const GRec *)fr.rec.p, ntx, (uint8_t *)fr.submask.p);
+                        (const float4 *)fr.rect.p, ntx, (uint8_t *)fr.submask.p);
     }
     if (s != SG_OK) return s;
     if (fr.k_cap > 0)

@@ -280,11 +280,11 @@ sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint
                     uint32_t *d_vals, cudaStream_t st, uint32_t *d_hist = nullptr,
                     int end_bit = 0);
 // Per-tile ranges of the sorted pairs; with d_mask (camera lists), also the
-// per-pair sub-block masks (d_ids, d_rec, ntx: the pairs' Gaussians, their
-// records, tiles per row).
+// per-pair sub-block masks (d_ids, d_rects, ntx: the pairs' Gaussians, the
+// per-Gaussian extent boxes, tiles per row).
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
                       int64_t ntiles, cudaStream_t st, const uint32_t *d_ids = nullptr,
-                      const GRec *d_rec = nullptr, int ntx = 0, uint8_t *d_mask = nullptr);
+                      const float4 *d_rects = nullptr, int ntx = 0, uint8_t *d_mask = nullptr);
 sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStream_t st);
 
 // project.cu

@@ -200,7 +200,7 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
         return s;
     fr.pair_buf = pb;
     if ((s = tile_ranges(pk[pb], scal + 1, K, (uint2 *)fr.ranges.p, nt, st, pv[pb],
-                         (const GRec *)fr.rec.p, c.ntx, (uint8_t *)fr.submask.p)) != SG_OK)
+                         (const float4 *)fr.rect.p, c.ntx, (uint8_t *)fr.submask.p)) != SG_OK)
         return s;
     return render_camera(c, *opts, fr, st);
 }

@@ -570,7 +570,7 @@ sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint
 template <bool kMask>
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
                          uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
-                         const GRec *__restrict__ rec, int ntx, uint8_t *__restrict__ mask)
+                         const float4 *__restrict__ rects, int ntx, uint8_t *__restrict__ mask)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t K = *d_K;
@@ -579,7 +579,7 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__re
     if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
     if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
     if (kMask) {
-        const float4 rc = rec[ids[i]].rect;
+        const float4 rc = rects[ids[i]];   // the extent box, 16 B per Gaussian
         const int tx = (int)(t % (uint32_t)ntx), ty = (int)(t / (uint32_t)ntx);
         uint32_t cols = 0, rows = 0;
 #pragma unroll
@@ -601,14 +601,14 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__re
 }
 
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
-                      int64_t ntiles, cudaStream_t st, const uint32_t *d_ids, const GRec *d_rec,
-                      int ntx, uint8_t *d_mask)
+                      int64_t ntiles, cudaStream_t st, const uint32_t *d_ids,
+                      const float4 *d_rects, int ntx, uint8_t *d_mask)
 {
     SG_CUDA(cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * ntiles, st));
     if (K_max == 0) return SG_OK;
     const unsigned grid = (unsigned)((K_max + 255) / 256);
     if (d_mask)
-        k_ranges<true><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rec, ntx, d_mask);
+        k_ranges<true><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rects, ntx, d_mask);
     else
         k_ranges<false><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, nullptr, nullptr, 0, nullptr);
     SG_LAUNCHED();

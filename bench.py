@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the LiDAR sweep and differentiable-step measurements")
+
     return ap.parse_args()
 
 
@@ -321,6 +322,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "gaussians": N_GAUSS,
                        "rays_per_step": rays_per_step, "parallelism": "replicas",
                        "views": "one sg_render_cameras call per step, each view on its own stream",
+                       "pair_counts": "exact (the host waits for each view's pair count)",
                        "l2": "inputs larger than L2 (236 MB of scene planes read per view)",
                        "wall_ms_per_step": wall_ms},
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
@@ -638,17 +640,25 @@ def roofline(per_view, union_ms, seq_view, clocks):
     return out
 
 
-KERNEL_SOURCES = ("render.cu", "pairs.cuh", "render.cuh", "internal.h")
+KERNEL_SOURCES = ("render.cu", "pairs.cuh", "render.cuh")
 
 
-def kernel_source_hash():
-    """sha256 over the compositing kernel's sources, to tell whether the ncu
-    counters in profiles/ were taken on the kernel as it stands."""
+def kernel_source_hash(read=None):
+    """sha256 over the compositing kernel's sources (its files, and the
+    record layout from internal.h), to tell whether the ncu counters in
+    profiles/ were taken on the kernel as it stands.  `read(name)` returns a
+    file's bytes (default: the working tree)."""
     import hashlib
+    if read is None:
+        def read(name):
+            with open(os.path.join(ROOT, "paper_2510_12901_gb300", "csrc", name), "rb") as fh:
+                return fh.read()
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2510_12901_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        h.update(read(f))
+    inc = read("internal.h")
+    a = inc.index(b"struct __align__(16) GRec")
+    h.update(inc[a:inc.index(b"};", a)])
     return h.hexdigest()
 
 

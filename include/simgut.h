@@ -274,7 +274,13 @@ sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_co
  * are device buffers and the call returns with the work queued, as
  * sg_render_camera.  host_outputs = 1: the outputs are host buffers
  * (pinned or pageable); each view's result is copied there on its stream
- * and the call returns once every view's copy is done.  Errors as for
+ * and the call returns once every view's copy is done.  host_outputs = 2:
+ * as 1, but the call returns with the copies queued on the views' streams
+ * (pinned buffers copy asynchronously); the caller synchronizes a view's
+ * stream, or an event recorded on it after the call, before it reads or
+ * reuses that view's host buffers, and gives the next call on the same
+ * frame the same stream (the frame's device staging is reused in stream
+ * order).  SG_ERR_INVALID for another value.  Errors as for
  * sg_render_camera, and SG_ERR_INVALID for n_views < 0, a NULL list,
  * camera or frame, or two views sharing a frame; after an error, views
  * already started may still run on their streams. */

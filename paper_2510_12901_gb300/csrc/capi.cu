@@ -729,6 +729,10 @@ sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *v
         set_error("sg_render_cameras: bad view list");
         return SG_ERR_INVALID;
     }
+    if (host_outputs < 0 || host_outputs > 2) {
+        set_error("sg_render_cameras: host_outputs %d is not 0, 1 or 2", host_outputs);
+        return SG_ERR_INVALID;
+    }
     for (int i = 0; i < n_views; ++i) {
         if (!views[i].camera || !views[i].frame) {
             set_error("view %d: NULL camera or frame", i);
@@ -774,7 +778,7 @@ sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *v
                                         sizeof(float) * (size_t)np * (k == 0 ? 3 : 1),
                                         cudaMemcpyDeviceToHost, st));
     }
-    if (host_outputs)
+    if (host_outputs == 1)
         for (int i = 0; i < n_views; ++i) SG_CUDA(cudaStreamSynchronize((cudaStream_t)views[i].stream));
     return SG_OK;
 }

@@ -83,6 +83,51 @@ def test_views_equal_alone_renders_host_outputs(rig):
             assert np.array_equal(h[2].numpy(), a[2].reshape(-1))
 
 
+def test_asynchronous_host_outputs_pipelined(rig):
+    """host_outputs = 2: the call returns with the copies queued; three
+    calls in a row on two frame sets (the host buffers of a call are read
+    after the next call is queued, as a pipelined caller does) give every
+    view's alone render, bit for bit; a bad mode is refused."""
+    import torch
+    sg = rig["sg"]
+    ss = [torch.cuda.Stream() for _ in rig["cams"]]
+    sets = []
+    for _ in range(2):
+        frames = [sg.Frame() for _ in rig["cams"]]
+        host, views = [], []
+        for i, (ch, c, f) in enumerate(zip(rig["cams"], rig["specs"], frames)):
+            n = c.width * c.height
+            h = [torch.full((3 * n,), -7.0).pin_memory(), torch.full((n,), -7.0).pin_memory(),
+                 torch.full((n,), -7.0).pin_memory()]
+            host.append(h)
+            views.append((ch.handle, c.c2w, f.handle, h[0].data_ptr(), h[1].data_ptr(),
+                          h[2].data_ptr(), ss[i].cuda_stream))
+        sets.append((frames, host, sg.sg_camera_views(views)))
+    events = [None, None]
+    for step in range(3):
+        frames, host, views = sets[step % 2]
+        sg.sg_render_cameras(rig["S"].handle, views, rig["opts"], 2)
+        events[step % 2] = []
+        for st in ss:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            events[step % 2].append(ev)
+        if step > 0:
+            prev = (step - 1) % 2
+            for ev in events[prev]:
+                ev.synchronize()
+            for h, a in zip(sets[prev][1], rig["alone"]):
+                for t, ref in zip(h, a):
+                    assert np.array_equal(t.numpy(), ref.reshape(-1))
+                    t.fill_(-7.0)
+    torch.cuda.synchronize()
+    for h, a in zip(sets[0][1], rig["alone"]):      # the third call's results
+        for t, ref in zip(h, a):
+            assert np.array_equal(t.numpy(), ref.reshape(-1))
+    with pytest.raises(sg.SimgutError):
+        sg.sg_render_cameras(rig["S"].handle, sets[0][2], rig["opts"], 3)
+
+
 def test_single_view_host_call_matches(rig):
     import torch
     sg = rig["sg"]

@@ -302,18 +302,13 @@ def run_ours(args):
               vs.cuda_stream) for (ch, c), h, f, vs in zip(cams, host, ef, vstreams)])))
 
     def e2e_run(steps, mode):
-        evs = [None, None]
         for i in range(steps):
             sg.sg_render_cameras(S.handle, hsets[i % 2][2], opts, mode)
-            if mode == 2:
-                evs[i % 2] = []
-                for vs in vstreams:
-                    ev = torch.cuda.Event()
-                    ev.record(vs)
-                    evs[i % 2].append(ev)
-                if i > 0:
-                    for ev in evs[(i - 1) % 2]:
-                        ev.synchronize()     # step i - 1's results are in host memory
+            if mode == 2 and i > 0:
+                for f in hsets[(i - 1) % 2][1]:
+                    sg.sg_frame_sync_outputs(f.handle)   # step i - 1's results are in host memory
+        for f in hsets[(steps - 1) % 2][1]:
+            sg.sg_frame_sync_outputs(f.handle)
         torch.cuda.synchronize()
 
     e2e_out = {}

@@ -275,12 +275,12 @@ sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_co
  * sg_render_camera.  host_outputs = 1: the outputs are host buffers
  * (pinned or pageable); each view's result is copied there on its stream
  * and the call returns once every view's copy is done.  host_outputs = 2:
- * as 1, but the call returns with the copies queued on the views' streams
- * (pinned buffers copy asynchronously); the caller synchronizes a view's
- * stream, or an event recorded on it after the call, before it reads or
- * reuses that view's host buffers, and gives the next call on the same
- * frame the same stream (the frame's device staging is reused in stream
- * order).  SG_ERR_INVALID for another value.  Errors as for
+ * as 1, but the call returns with the copies queued (pinned buffers copy
+ * asynchronously); the caller calls sg_frame_sync_outputs on a view's frame
+ * before it reads or reuses that view's host buffers.  The copies run on a
+ * stream of the frame's own, after the view's render, so that the view's
+ * stream goes on to its next work; the frame's next render waits for them.
+ * SG_ERR_INVALID for another value.  Errors as for
  * sg_render_camera, and SG_ERR_INVALID for n_views < 0, a NULL list,
  * camera or frame, or two views sharing a frame; after an error, views
  * already started may still run on their streams. */
@@ -295,6 +295,9 @@ typedef struct {
 } sg_camera_view;
 sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *views,
                             const sg_render_opts *opts, int host_outputs);
+/* Wait until the host copies of the frame's last render with host outputs
+ * are done (at once if it has none). */
+sg_status sg_frame_sync_outputs(sg_frame frame);
 
 /* ----------------------------------------------------------------------
  * Camera render that allocates nothing.  The paper has no counterpart: this

@@ -623,6 +623,9 @@ void sg_frame_destroy(sg_frame frame)
     for (auto &e : f.ev)
         if (e) cudaEventDestroy(e);
     if (f.ev_count) cudaEventDestroy(f.ev_count);
+    if (f.ev_rendered) cudaEventDestroy(f.ev_rendered);
+    if (f.ev_copied) cudaEventDestroy(f.ev_copied);
+    if (f.copy_st) cudaStreamDestroy(f.copy_st);
     delete frame;
 }
 
@@ -757,6 +760,8 @@ sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *v
                 out[k] = (float *)v.frame->f.host_stage[k].p;
             }
         }
+        if (host_outputs && v.frame->f.copy_pending)   // the staging is free once copied
+            SG_CUDA(cudaStreamWaitEvent((cudaStream_t)v.stream, v.frame->f.ev_copied, 0));
         if (v.row_c2w && v.frame->f.seg_len != kSegLen) {
             set_error("view %d: a rolling-shutter view cannot use an allocation-free frame", i);
             return SG_ERR_INVALID;
@@ -770,16 +775,36 @@ sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *v
         cudaStream_t st = (cudaStream_t)v.stream;
         if ((s = camera_finish(v.camera, v.frame, st)) != SG_OK) return s;
         if (!host_outputs) continue;
+        // the copies run on the frame's own stream, so that the view's next
+        // work does not queue behind them
+        Frame &f = v.frame->f;
+        if (!f.copy_st) {
+            SG_CUDA(cudaStreamCreateWithFlags(&f.copy_st, cudaStreamNonBlocking));
+            SG_CUDA(cudaEventCreateWithFlags(&f.ev_rendered, cudaEventDisableTiming));
+            SG_CUDA(cudaEventCreateWithFlags(&f.ev_copied, cudaEventDisableTiming));
+        }
+        SG_CUDA(cudaEventRecord(f.ev_rendered, st));
+        SG_CUDA(cudaStreamWaitEvent(f.copy_st, f.ev_rendered, 0));
         const int64_t np = (int64_t)v.camera->c.width * v.camera->c.height;
         float *h[3] = {v.rgb, v.alpha, v.depth};
         for (int k = 0; k < 3; ++k)
             if (h[k])
-                SG_CUDA(cudaMemcpyAsync(h[k], v.frame->f.host_stage[k].p,
+                SG_CUDA(cudaMemcpyAsync(h[k], f.host_stage[k].p,
                                         sizeof(float) * (size_t)np * (k == 0 ? 3 : 1),
-                                        cudaMemcpyDeviceToHost, st));
+                                        cudaMemcpyDeviceToHost, f.copy_st));
+        SG_CUDA(cudaEventRecord(f.ev_copied, f.copy_st));
+        f.copy_pending = true;
     }
     if (host_outputs == 1)
-        for (int i = 0; i < n_views; ++i) SG_CUDA(cudaStreamSynchronize((cudaStream_t)views[i].stream));
+        for (int i = 0; i < n_views; ++i) SG_CUDA(cudaEventSynchronize(views[i].frame->f.ev_copied));
+    return SG_OK;
+}
+
+sg_status sg_frame_sync_outputs(sg_frame frame)
+{
+    if (!frame) { set_error("frame is NULL"); return SG_ERR_INVALID; }
+    Frame &f = frame->f;
+    if (f.copy_pending) SG_CUDA(cudaEventSynchronize(f.ev_copied));
     return SG_OK;
 }
 

@@ -189,6 +189,9 @@ struct Frame {
     float ms[4] = {0, 0, 0, 0};
     cudaEvent_t ev_count = nullptr;  // exact mode: the pair count has reached h_scalars
     Buf host_stage[3];               // device results of a render with host outputs
+    cudaStream_t copy_st = nullptr;  // their copies to the host run here, off the view's stream
+    cudaEvent_t ev_rendered = nullptr, ev_copied = nullptr;
+    bool copy_pending = false;       // ev_copied marks the last copies queued
 };
 
 // Grow b to at least `bytes` (with head-room); growing frees the old buffer.

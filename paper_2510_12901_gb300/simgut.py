@@ -134,6 +134,7 @@ _SIGNATURES = {
     "sg_frame_set_timing": (C.c_int, [_H, C.c_int]),
     "sg_frame_timing": (C.c_int, [_H, C.POINTER(C.c_float)]),
     "sg_frame_marks": (C.c_int, [_H, _H, C.POINTER(C.c_float)]),
+    "sg_frame_sync_outputs": (C.c_int, [_H]),
 }
 
 _lib = None
@@ -382,6 +383,10 @@ def sg_frame_timing(frame):
     ms = (C.c_float * 4)()
     _check(load().sg_frame_timing(frame, ms))
     return list(ms)
+
+
+def sg_frame_sync_outputs(frame):
+    _check(load().sg_frame_sync_outputs(frame))
 
 
 def sg_frame_marks(frame, ref):

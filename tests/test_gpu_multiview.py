@@ -103,24 +103,19 @@ def test_asynchronous_host_outputs_pipelined(rig):
             views.append((ch.handle, c.c2w, f.handle, h[0].data_ptr(), h[1].data_ptr(),
                           h[2].data_ptr(), ss[i].cuda_stream))
         sets.append((frames, host, sg.sg_camera_views(views)))
-    events = [None, None]
     for step in range(3):
         frames, host, views = sets[step % 2]
         sg.sg_render_cameras(rig["S"].handle, views, rig["opts"], 2)
-        events[step % 2] = []
-        for st in ss:
-            ev = torch.cuda.Event()
-            ev.record(st)
-            events[step % 2].append(ev)
         if step > 0:
             prev = (step - 1) % 2
-            for ev in events[prev]:
-                ev.synchronize()
+            for f in sets[prev][0]:
+                sg.sg_frame_sync_outputs(f.handle)
             for h, a in zip(sets[prev][1], rig["alone"]):
                 for t, ref in zip(h, a):
                     assert np.array_equal(t.numpy(), ref.reshape(-1))
                     t.fill_(-7.0)
-    torch.cuda.synchronize()
+    for f in sets[0][0]:
+        sg.sg_frame_sync_outputs(f.handle)
     for h, a in zip(sets[0][1], rig["alone"]):      # the third call's results
         for t, ref in zip(h, a):
             assert np.array_equal(t.numpy(), ref.reshape(-1))

@@ -68,7 +68,7 @@ def _structs(real):
                     ("ut_alpha", C.c_float), ("ut_beta", C.c_float),
                     ("ut_kappa", C.c_float), ("tile", C.c_int), ("pose_iters", C.c_int),
                     ("cull", C.c_int), ("predicate", C.c_int), ("cutoffs", C.c_int),
-                    ("beam_divergence", C.c_float)]
+                    ("beam_divergence", C.c_float), ("sh_per_ray", C.c_int)]
 
     class Setup(C.Structure):
         _fields_ = [("n_tiles_x", C.c_int), ("n_tiles_y", C.c_int),
@@ -137,8 +137,18 @@ class Oracle:
             setattr(o, k, v)
         return o
 
+    def _param(self, a):
+        """A parameter array in the build's precision.  float64 arrays go to
+        the double build unrounded (central differences in double); any
+        other array is first rounded to float32, the precision of the
+        library's inputs."""
+        a = np.asarray(a)
+        if self.bits == 64 and a.dtype == np.float64:
+            return np.ascontiguousarray(a)
+        return np.ascontiguousarray(a, np.float32).astype(self.np_real)
+
     def scene(self, sc):
-        arrs = [np.ascontiguousarray(a, np.float32) for a in
+        arrs = [self._param(a) for a in
                 (sc.means, sc.log_scales, sc.quats, sc.opacity, sc.features)]
         s = self.Scene(sc.n, *[self._p(a) for a in arrs], sc.feature_kind, sc.sh_degree)
         if getattr(sc, "actor_of", None) is not None:
@@ -177,8 +187,8 @@ class Oracle:
 
     # ---------------------------------------------------------------- steps
     def activate(self, log_scales, quats):
-        ls = np.ascontiguousarray(log_scales, np.float32)
-        q = np.ascontiguousarray(quats, np.float32)
+        ls = self._param(log_scales)
+        q = self._param(quats)
         n = ls.shape[0]
         R = np.zeros((n, 9), self.np_real)
         s = np.zeros((n, 3), self.np_real)
@@ -343,14 +353,14 @@ class Oracle:
                                  C.c_int64(nr), out)
         return np.ctypeslib.as_array(out)[:n].copy()
 
-    @staticmethod
-    def lidar_decode(rays):
-        """(range, intensity, drop probability) from raw ray records."""
-        rng = rays["depth"].astype(np.float64)
-        inten = rays["out"][:, 0].astype(np.float64)
-        drop = 1.0 / (1.0 + np.exp(rays["out"][:, 1].astype(np.float64)
-                                   - rays["out"][:, 2].astype(np.float64)))
-        return rng, inten, drop
+    def lidar_decode(self, rays):
+        """(range, intensity, drop probability) from raw ray records
+        (or_lidar_decode, Sec. 3.2), as float64 arrays."""
+        R = np.ascontiguousarray(rays)
+        n = R.shape[0]
+        out = [np.zeros(max(n, 1), self.np_real) for _ in range(3)]
+        self.lib.or_lidar_decode_n(C.c_int64(n), self._p(R), *[self._p(a) for a in out])
+        return tuple(a[:n].astype(np.float64) for a in out)
 
     def _grads(self, sc):
         F = sc.features.shape[1]
@@ -367,10 +377,13 @@ class Oracle:
         ga = [np.ascontiguousarray(a, np.float32) for a in (g_rgb, g_alpha, g_depth)]
         G = self._grads(sc)
         rp, nr, keep = self._rays_arg(rays)
-        self.lib.or_backward_camera(C.byref(s), C.byref(c), C.byref(o), rp, C.c_int64(nr),
-                                    *[self._p(a) for a in ga],
-                                    *[self._p(G[k]) for k in
-                                      ("means", "log_scales", "quats", "opacity", "features")])
+        r = self.lib.or_backward_camera(C.byref(s), C.byref(c), C.byref(o), rp, C.c_int64(nr),
+                                        *[self._p(a) for a in ga],
+                                        *[self._p(G[k]) for k in
+                                          ("means", "log_scales", "quats", "opacity",
+                                           "features")])
+        if r != 0:
+            raise ValueError("or_backward_camera refused the options")
         return G
 
     def backward_lidar(self, sc, L, g_range, g_int, g_drop, g_alpha, opts=None, rays=None):
@@ -380,8 +393,11 @@ class Oracle:
         ga = [np.ascontiguousarray(a, np.float32) for a in (g_range, g_int, g_drop, g_alpha)]
         G = self._grads(sc)
         rp, nr, keep = self._rays_arg(rays)
-        self.lib.or_backward_lidar(C.byref(s), C.byref(lid), C.byref(o), rp, C.c_int64(nr),
-                                   *[self._p(a) for a in ga],
-                                   *[self._p(G[k]) for k in
-                                     ("means", "log_scales", "quats", "opacity", "features")])
+        r = self.lib.or_backward_lidar(C.byref(s), C.byref(lid), C.byref(o), rp, C.c_int64(nr),
+                                       *[self._p(a) for a in ga],
+                                       *[self._p(G[k]) for k in
+                                         ("means", "log_scales", "quats", "opacity",
+                                          "features")])
+        if r != 0:
+            raise ValueError("or_backward_lidar refused the options")
         return G

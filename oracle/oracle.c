@@ -42,6 +42,7 @@ or_opts or_default_opts(void)
     o.predicate = 1;
     o.cutoffs = 1;
     o.beam_divergence = 0.0f;     /* READING: delta is not stated; off by default */
+    o.sh_per_ray = 0;             /* READING: SH once per Gaussian (3DGS practice) */
     return o;
 }
 
@@ -63,7 +64,7 @@ static void quat_to_R(const real q[4], real R[9])
     R[8] = RL(1) - RL(2) * (x * x + y * y);
 }
 
-static void unit_quat(const float *qin, real q[4], real *norm)
+static void unit_quat(const real *qin, real q[4], real *norm)
 {
     real n = sqrt(RL(qin[0]) * RL(qin[0]) + RL(qin[1]) * RL(qin[1]) +
                   RL(qin[2]) * RL(qin[2]) + RL(qin[3]) * RL(qin[3]));
@@ -71,7 +72,7 @@ static void unit_quat(const float *qin, real q[4], real *norm)
     if (norm) *norm = n;
 }
 
-void or_activate(int64_t n, const float *log_scales, const float *quats,
+void or_activate(int64_t n, const real *log_scales, const real *quats,
                  real *R_out, real *s_out)
 {
     for (int64_t i = 0; i < n; ++i) {
@@ -943,6 +944,9 @@ typedef struct {
     int clampc[3];   /* colour channel clamped at 0 (SH) */
     real dir[3];     /* SH direction used */
     real dist;       /* |mu - o_cam| */
+    const real *shc; /* SH coefficients [nc][3] (NULL: features are not SH) */
+    int nc, lidar_sh;
+    real Ra[9];      /* actor rotation (world from the Gaussian's frame) */
 } gauss_rt;
 
 static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3], real beam,
@@ -978,7 +982,7 @@ static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3], rea
         real Y[16];
         or_sh_basis(G->dir, Y);
         int nc = (sc->sh_degree + 1) * (sc->sh_degree + 1);
-        const float *f = sc->features + (size_t)g * nc * 3;
+        const real *f = sc->features + (size_t)g * nc * 3;
         for (int ch = 0; ch < 3; ++ch) {
             real acc = 0;
             for (int k = 0; k < nc; ++k) acc += Y[k] * RL(f[3 * k + ch]);
@@ -988,8 +992,35 @@ static void gauss_prepare(const or_scene *sc, int64_t g, const real ocam[3], rea
             }
             G->feat[ch] = acc;
         }
+        /* for the per-ray reading (or_opts.sh_per_ray) */
+        G->shc = f;
+        G->nc = nc;
+        G->lidar_sh = lidar;
+        for (int k = 0; k < 9; ++k) G->Ra[k] = Ra[k];
     } else {
         for (int ch = 0; ch < 3; ++ch) G->feat[ch] = RL(sc->features[3 * g + ch]);
+        G->shc = NULL;
+    }
+}
+
+/* The features of G seen along ray direction d (or_opts.sh_per_ray): the SH
+ * evaluated at d expressed in the Gaussian's actor frame, with the colour
+ * offset and clamp for camera SH (as for the per-Gaussian reading). */
+static void feat_per_ray(const gauss_rt *G, const real d[3], real feat[3])
+{
+    real u[3], Y[16];
+    for (int k = 0; k < 3; ++k) u[k] = G->Ra[k] * d[0] + G->Ra[3 + k] * d[1] + G->Ra[6 + k] * d[2];
+    real nu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int k = 0; k < 3; ++k) u[k] /= nu;
+    or_sh_basis(u, Y);
+    for (int ch = 0; ch < 3; ++ch) {
+        real acc = 0;
+        for (int k = 0; k < G->nc; ++k) acc += Y[k] * G->shc[3 * k + ch];
+        if (!G->lidar_sh) {
+            acc += RL(0.5);
+            if (acc < RL(0)) acc = 0;
+        }
+        feat[ch] = acc;
     }
 }
 
@@ -1067,7 +1098,14 @@ static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR
         real a, b, c;
         response_quadratic(G, org, dir, &a, &b, &c);
         real tau = -b / a;
-        real D2 = c - b * b / a;
+        /* D2 = q(tau_max), the quadratic evaluated at its minimiser (Sec. 3.2:
+         * the response at tau_max).  Evaluated as w^T A w with w = o + tau d - mu
+         * rather than as c - b^2/a, which cancels badly when the ray passes
+         * far from the Gaussian relative to its size. */
+        real e[3], D2 = 0;
+        for (int k = 0; k < 3; ++k) e[k] = org[k] + tau * dir[k] - G->mu[k];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) D2 += e[i] * G->A[3 * i + j] * e[j];
         if (D2 < RL(0)) D2 = RL(0);
         real rho = exp(RL(-0.5) * D2);
         real alpha = G->sigma * rho;
@@ -1106,7 +1144,13 @@ static void composite_ray(const or_opts *o, const or_proj *P, const gauss_rt *GR
             if (Tn < tmin) break;   /* READING: 3DGS stops before compositing it */
         }
         real w = alpha * T;
-        for (int ch = 0; ch < 3; ++ch) acc[ch] += w * G->feat[ch];
+        real fr[3];
+        const real *feat = G->feat;
+        if (o->sh_per_ray && G->shc) {
+            feat_per_ray(G, dir, fr);
+            feat = fr;
+        }
+        for (int ch = 0; ch < 3; ++ch) acc[ch] += w * feat[ch];
         Z += w * tau;
         W += w;
         if (rec) {
@@ -1351,6 +1395,11 @@ void or_lidar_decode(const or_ray *r, real *range, real *intensity, real *drop)
     *drop = RL(1) / (RL(1) + exp(r->out[1] - r->out[2]));
 }
 
+void or_lidar_decode_n(int64_t n, const or_ray *r, real *range, real *intensity, real *drop)
+{
+    for (int64_t i = 0; i < n; ++i) or_lidar_decode(&r[i], &range[i], &intensity[i], &drop[i]);
+}
+
 /* ------------------------------------------------------------------ */
 /* Backward: plain chain rule through the forward above                */
 /* ------------------------------------------------------------------ */
@@ -1544,7 +1593,7 @@ static void bw_finish(const or_scene *sc, const gauss_rt *GR, const bw_ctx *B,
             real Y[16], dY[16][3];
             or_sh_basis(G->dir, Y);
             or_sh_basis_grad(G->dir, dY);
-            const float *f = sc->features + (size_t)g * nc * 3;
+            const real *f = sc->features + (size_t)g * nc * 3;
             real gdir[3] = {0, 0, 0};
             for (int ch = 0; ch < 3; ++ch) {
                 if (G->clampc[ch]) continue;
@@ -1572,6 +1621,7 @@ static int backward_common(const or_scene *sc, const or_opts *o, const or_proj *
                            const float *gd, real *gm, real *gls, real *gq,
                            real *gop, real *gf)
 {
+    if (o->sh_per_ray) return -1;   /* forward-only reading */
     gauss_rt *GR = malloc(sizeof(gauss_rt) * (size_t)(sc->n > 0 ? sc->n : 1));
     for (int64_t g = 0; g < sc->n; ++g)
         gauss_prepare(sc, g, origin_of(ocam, ocam_per_gauss, g), beam, &GR[g]);
@@ -1599,6 +1649,7 @@ int or_backward_camera(const or_scene *sc, const or_camera *cam, const or_opts *
                        const float *g_rgb, const float *g_alpha, const float *g_depth,
                        real *gm, real *gls, real *gq, real *gop, real *gf)
 {
+    if (o->sh_per_ray) return -1;   /* forward-only reading */
     or_sensor_setup S;
     or_camera_setup(cam, o, &S);
     or_proj *P = malloc(sizeof(or_proj) * (size_t)(sc->n > 0 ? sc->n : 1));
@@ -1620,6 +1671,7 @@ int or_backward_lidar(const or_scene *sc, const or_lidar *L, const or_opts *o,
                       const float *g_alpha, real *gm, real *gls, real *gq, real *gop,
                       real *gf)
 {
+    if (o->sh_per_ray) return -1;   /* forward-only reading */
     or_sensor_setup S;
     or_lidar_setup(L, &S);
     or_proj *P = malloc(sizeof(or_proj) * (size_t)(sc->n > 0 ? sc->n : 1));

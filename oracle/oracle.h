@@ -34,13 +34,16 @@ typedef double real;
 enum { OR_FEAT_RGB = 0, OR_FEAT_SH = 1, OR_FEAT_LIDAR = 2, OR_FEAT_LIDAR_SH = 3 };
 enum { OR_PINHOLE = 0, OR_FISHEYE = 1 };
 
+/* Gaussian parameters are in the build's own precision (`real`): float in
+ * the float build, double in the double build, so that the double build can
+ * be differentiated by central differences in double. */
 typedef struct {
     int64_t n;
-    const float *means;       /* [n,3] */
-    const float *log_scales;  /* [n,3] */
-    const float *quats;       /* [n,4] (w,x,y,z), normalised here */
-    const float *opacity;     /* [n], already in (0,1) */
-    const float *features;    /* [n,F] */
+    const real *means;        /* [n,3] */
+    const real *log_scales;   /* [n,3] */
+    const real *quats;        /* [n,4] (w,x,y,z), normalised here */
+    const real *opacity;      /* [n], already in (0,1) */
+    const real *features;     /* [n,F] */
     int feature_kind;
     int sh_degree;
     /* Dynamic actors (Sec. 3.1 scene graph; NULL actor_of: all static).
@@ -94,6 +97,14 @@ typedef struct {
      * takes its sigma points along the columns of the Cholesky factor of
      * that covariance. */
     float beam_divergence;
+    /* SH evaluated per ray (1) instead of once per Gaussian (0, the
+     * default).  Eq. 1 writes the colour as SH_i(d) with d the ray
+     * direction; 3DGS-style renderers, and this library, evaluate it once
+     * per Gaussian at the direction from the sensor origin to the mean.  This
+     * option evaluates it at each ray's own direction (in the Gaussian's
+     * actor frame), to measure how far the two readings differ.  Forward
+     * only: the backward refuses it. */
+    int sh_per_ray;
 } or_opts;
 
 /* Sensor set-up, computed once per sensor (double in both builds). */
@@ -154,7 +165,7 @@ extern "C" {
 or_opts or_default_opts(void);
 
 /* Sec. 3.1: q -> R, log-scale -> scale.  Pinned: R orthonormal, det 1. */
-void or_activate(int64_t n, const float *log_scales, const float *quats,
+void or_activate(int64_t n, const real *log_scales, const real *quats,
                  real *R_out, real *s_out);
 
 /* Real spherical harmonics up to degree 3 at a unit direction (16 values).
@@ -218,15 +229,21 @@ int or_render_lidar(const or_scene *sc, const or_lidar *L,
                     const or_opts *o, int bruteforce,
                     const int64_t *rays, int64_t n_rays, or_ray *out);
 
-/* Per-ray output decode: LiDAR intensity and ray-drop probability (Sec. 3.2). */
+/* Per-ray output decode: LiDAR intensity and ray-drop probability (Sec. 3.2).
+ * range = Z / omega, intensity = the first channel of zeta, drop =
+ * softmax(zeta_1, zeta_2)[drop] = 1 / (1 + exp(zeta_1 - zeta_2)) with
+ * zeta_1 the accumulated beta_hit and zeta_2 the accumulated beta_drop.
+ * Pinned: a single Gaussian on a beam (closed form), rays that hit nothing. */
 void or_lidar_decode(const or_ray *r, real *range, real *intensity, real *drop);
+void or_lidar_decode_n(int64_t n, const or_ray *r, real *range, real *intensity, real *drop);
 
 /* Analytic gradients (Sec. 3.4 differentiable renderer) of
  * L = sum_rays <g_out, outputs> w.r.t. the raw parameters; upstream arrays
  * are indexed by ray id; `rays` (n_rays < 0: all) selects the rays summed.
  * Camera outputs: rgb[3], alpha, depth.  LiDAR outputs: range, intensity,
  * drop, alpha.  grads are [n,3], [n,3], [n,4], [n], [n,F]; accumulated.
- * Pinned: central finite differences of the forward, closed forms. */
+ * Pinned: central finite differences of the forward, closed forms.
+ * Return -1 (nothing computed) for opts with sh_per_ray set. */
 int or_backward_camera(const or_scene *sc, const or_camera *cam,
                        const or_opts *o, const int64_t *rays, int64_t n_rays,
                        const float *g_rgb,

@@ -123,9 +123,8 @@ def compare_lidar_rays(rng, inten, drop, alpha, orc, max_excluded=0.01, label=""
     if also_excluded is not None:
         amb = amb | also_excluded
     ok = ~amb
-    o_rng = orc["depth"]
-    o_int = orc["out"][:, 0]
-    o_drop = 1.0 / (1.0 + np.exp(orc["out"][:, 1] - orc["out"][:, 2]))
+    from oracle import Oracle
+    o_rng, o_int, o_drop = Oracle(64).lidar_decode(orc)     # Sec. 3.2 decode
     hit = orc["alpha"] > 0
     e_r = np.where(hit, np.abs(rng - o_rng) / np.maximum(o_rng, 1e-12), np.abs(rng))
     e_i = np.abs(inten - o_int)

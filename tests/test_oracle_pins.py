@@ -366,6 +366,139 @@ def test_flat_opaque_disk_returns_ray_plane_distance(O64):
         assert abs(r["depth"][i] - t_plane) < 1e-5 * t_plane
 
 
+# ------------------------------------------------ LiDAR closed forms (Sec. 3.2-3.3)
+def _beam_dir(L, beam, col):
+    """World direction and origin of LiDAR ray (beam, col), written out from
+    the sensor model: column c at azimuth az0 + (c + 1/2) 360 / N_cols, beam b
+    at its table elevation, u = (cos el cos az, cos el sin az, sin el) in the
+    sensor frame, mapped by the column's pose."""
+    az = math.radians(L.az0_deg + (col + 0.5) * 360.0 / L.n_cols)
+    el = math.radians(float(L.elevations_deg[beam]))
+    u = np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+    P = np.asarray(L.col_c2w[col], np.float64).reshape(3, 4)
+    return P[:, 3], P[:, :3] @ u
+
+
+def _one_lidar_gaussian(mu, ls, sigma, feat, q=(1, 0, 0, 0)):
+    sc = syn.street_scene(1, seed=0, kind="lidar")
+    sc.means[0] = mu
+    sc.log_scales[0] = ls
+    sc.quats[0] = q
+    sc.opacity[0] = sigma
+    sc.features[0] = feat
+    return sc
+
+
+@pytest.mark.parametrize("beam,col", [(60, 100), (10, 7), (120, 250)])
+def test_lidar_single_gaussian_on_a_beam_closed_form(O64, beam, col):
+    """A small Gaussian centred on ray (beam, col) at distance r: the ray
+    passes through its mean, so D = 0, alpha = min(0.99, sigma), range = r,
+    intensity = alpha zeta_0, and the drop probability is the softmax of the
+    accumulated (beta_hit, beta_drop) = alpha (b_hit, b_drop):
+    1 / (1 + exp(alpha (b_hit - b_drop))).  The neighbouring columns pass
+    half a column's angle or more beside it and see far less."""
+    L = syn.street_lidar(n_cols=256)
+    o, d = _beam_dir(L, beam, col)
+    r = 9.0
+    mu = (o + r * d).astype(np.float32)
+    sigma, feat = 0.7, [0.42, 1.3, -0.6]          # b_hit != b_drop
+    sc = _one_lidar_gaussian(mu, [math.log(0.01)] * 3, sigma, feat)
+    ray = beam * L.n_cols + col
+    out = O64.render_lidar(sc, L, rays=[ray, ray - 1, ray + 1])
+    rg, it, dr = O64.lidar_decode(out)
+    a = float(np.float32(sigma))
+    f = np.asarray(feat, np.float32).astype(np.float64)
+    assert abs(out["alpha"][0] - a) < 1e-6
+    assert abs(rg[0] - np.linalg.norm(mu - o)) < 1e-6 * r
+    assert abs(it[0] - a * f[0]) < 1e-6
+    assert abs(dr[0] - 1.0 / (1.0 + math.exp(a * (f[1] - f[2])))) < 1e-6
+    # swapping beta_hit and beta_drop would give the complementary probability
+    assert abs(dr[0] - 0.5) > 0.1
+    assert out["alpha"][1] < 0.01 * a and out["alpha"][2] < 0.01 * a
+
+
+def test_lidar_flat_opaque_disk_returns_beam_plane_distance(O64):
+    """A disk-like LiDAR Gaussian (scales a, a, 1e-5; opacity 1): every beam
+    that hits it returns the distance along the beam to the disk's plane,
+    ((mu - o) . n) / (d . n), with d the beam direction written out above."""
+    L = syn.street_lidar(n_cols=512)
+    n = np.array([-0.8, 0.3, 0.52])
+    n /= np.linalg.norm(n)
+    x = np.cross([0, 0, 1.0], n)
+    x /= np.linalg.norm(x)
+    y = np.cross(n, x)
+    Rm = np.stack([x, y, n], 1)
+    w = math.sqrt(1 + np.trace(Rm)) / 2
+    q = [w, (Rm[2, 1] - Rm[1, 2]) / (4 * w), (Rm[0, 2] - Rm[2, 0]) / (4 * w),
+         (Rm[1, 0] - Rm[0, 1]) / (4 * w)]
+    o0 = np.asarray(L.col_c2w[0], np.float64).reshape(3, 4)[:, 3]
+    mu = (o0 + np.array([6.0, 1.0, 0.5])).astype(np.float32)
+    sc = _one_lidar_gaussian(mu, [math.log(1.5), math.log(1.5), math.log(1e-5)], 1.0,
+                             [0.5, 0.0, 0.0], q)
+    out = O64.render_lidar(sc, L)
+    hit = np.nonzero(out["n_contrib"] > 0)[0]
+    assert len(hit) > 200
+    rg, _, _ = O64.lidar_decode(out)
+    for i in hit[::7]:
+        o, d = _beam_dir(L, i // L.n_cols, i % L.n_cols)
+        t_plane = np.dot(mu.astype(np.float64) - o, n) / np.dot(d, n)
+        assert abs(rg[i] - t_plane) < 1e-5 * t_plane, (i, rg[i], t_plane)
+
+
+# ---------------------------------------------------- per-ray SH (Eq. 1, SH_i(d))
+def test_sh_per_ray_degree1_closed_form(O64):
+    """With the per-ray reading a Gaussian's colour along ray d is
+    max(0, 0.5 + Y_0^0 c_0 + sqrt(3 / 4 pi) (-d_y c_1 + d_z c_2 - d_x c_3)):
+    the textbook real SH of degree <= 1 at the ray's own direction."""
+    cam = syn.tiny_camera()
+    ok, o, d = O64.camera_ray(cam, 32, 32)
+    coeffs = np.array([[0.4, -0.3, 0.2], [0.5, 0.1, -0.4], [-0.2, 0.3, 0.6],
+                       [0.3, -0.5, 0.1]], np.float32)
+    sc = _one_gaussian_scene((o + 8.0 * d).astype(np.float32), [-0.2, -0.2, -0.2], 0.6,
+                             [0, 0, 0])
+    sc = dataclasses.replace(sc, features=coeffs.reshape(1, 12), feature_kind=syn.FEATURES_SH,
+                             sh_degree=1)
+    opts = O64.opts(sh_per_ray=1)
+    r = O64.render_camera(sc, cam, opts)
+    one = np.nonzero(r["n_contrib"] == 1)[0]
+    assert len(one) > 200
+    c = coeffs.astype(np.float64)
+    k0, k1 = 0.5 / math.sqrt(math.pi), math.sqrt(3.0 / (4.0 * math.pi))
+    for i in one[::5]:
+        _, _, dd = O64.camera_ray(cam, i % 64, i // 64)
+        col = np.maximum(0.0, 0.5 + k0 * c[0] + k1 * (-dd[1] * c[1] + dd[2] * c[2] - dd[0] * c[3]))
+        assert np.allclose(r["out"][i] / r["alpha"][i], col, rtol=1e-9, atol=1e-12), i
+    # the per-Gaussian reading gives one colour for the whole footprint
+    g = O64.render_camera(sc, cam)
+    cols = g["out"][one] / g["alpha"][one][:, None]
+    assert np.abs(cols - cols[0]).max() < 1e-9
+    assert np.abs(r["out"][one] / r["alpha"][one][:, None] - cols).max() > 1e-3
+
+
+def test_sh_per_ray_equals_per_gaussian_on_the_axis_and_at_degree0(O64):
+    """On the ray through the mean the two directions coincide; with degree-0
+    SH the colour does not depend on the direction at all."""
+    cam = syn.tiny_camera()
+    ok, o, d = O64.camera_ray(cam, 40, 21)
+    rng = np.random.default_rng(3)
+    sc = _one_gaussian_scene((o + 9.0 * d).astype(np.float32), [-0.5, -0.7, -0.6], 0.8,
+                             [0, 0, 0])
+    sc = dataclasses.replace(sc, features=rng.normal(0, 0.4, (1, 48)).astype(np.float32),
+                             feature_kind=syn.FEATURES_SH, sh_degree=3)
+    a = O64.render_camera(sc, cam, O64.opts(sh_per_ray=1), rays=[21 * 64 + 40])[0]
+    b = O64.render_camera(sc, cam, rays=[21 * 64 + 40])[0]
+    assert np.allclose(a["out"], b["out"], atol=1e-6)
+    s0 = dataclasses.replace(syn.tiny_scene(n=300, seed=4), feature_kind=syn.FEATURES_SH,
+                             sh_degree=0)
+    x = O64.render_camera(s0, cam, O64.opts(sh_per_ray=1))
+    y = O64.render_camera(s0, cam)
+    assert np.array_equal(x["out"], y["out"])
+    with pytest.raises(ValueError):
+        O64.backward_camera(s0, cam, np.zeros((4096, 3), np.float32),
+                            np.zeros(4096, np.float32), np.zeros(4096, np.float32),
+                            O64.opts(sh_per_ray=1))
+
+
 @pytest.mark.parametrize("bits", [64, 32])
 def test_tiny_config_invariants(bits):
     from oracle import Oracle
@@ -569,6 +702,137 @@ def test_backward_lidar_matches_central_differences(O64):
             fd = (lp - lm) / (hp + hm)
             scale = max(1.0, np.abs(gflat).max())
             assert abs(fd - gflat[i]) < 2e-4 * scale + 2e-5 * abs(fd), (name, i, fd, gflat[i])
+
+
+# ---------------------------------------- FP64 central differences, 512 Gaussians
+# The gradient check of the differentiable step at its stated size: the 512
+# Gaussians nearest to the sensor among those the projection keeps (the
+# nearest 512 of all lie mostly below the LiDAR's lowest beam or beside the
+# camera), a 32x32 fisheye crop and an 8x64 LiDAR crop, every cutoff off so
+# that the loss is smooth, and central differences with step 1e-6 on a
+# float64 copy of the parameters.  The loss is the mean over the crop's rays
+# of <g, outputs> with g ~ N(0, 1) per output.  Agreement: relative 1e-6 or
+# absolute 1e-9.
+FD_STEP, FD_REL, FD_ABS = 1e-6, 1e-6, 1e-9
+
+
+def _as64(sc):
+    return dataclasses.replace(sc, **{k: getattr(sc, k).astype(np.float64) for k in
+                                      ("means", "log_scales", "quats", "opacity", "features")})
+
+
+def _nearest_visible(full, origin, project, n=512, pre=20000):
+    d = np.linalg.norm(full.means.astype(np.float64) - origin, axis=1)
+    idx = np.argsort(d)[:pre]
+    P = project(full.subset(idx))
+    keep = idx[P["valid"] == 1][:n]
+    assert len(keep) == n
+    return _as64(full.subset(np.sort(keep)))
+
+
+def _fd_check(loss, G, sc, n_top=8, n_random=60, seed=0):
+    """Every parameter of the n_top Gaussians with the largest mean
+    gradients, plus n_random random (Gaussian, parameter) picks."""
+    rng = np.random.default_rng(seed)
+    top = np.argsort(-np.abs(G["means"]).sum(1))[:n_top]
+    picks = []
+    names = ("means", "log_scales", "quats", "opacity", "features")
+    for name in names:
+        per = getattr(sc, name).reshape(sc.n, -1).shape[1]
+        picks += [(name, g * per + k) for g in top for k in range(per)]
+    for _ in range(n_random):
+        name = names[rng.integers(0, len(names))]
+        size = getattr(sc, name).size
+        picks.append((name, int(rng.integers(0, size))))
+    worst = 0.0
+    for name, i in picks:
+        flat = getattr(sc, name).reshape(-1)
+        g = G[name].reshape(-1)[i]
+        x0 = flat[i]
+        flat[i] = x0 + FD_STEP
+        lp = loss()
+        flat[i] = x0 - FD_STEP
+        lm = loss()
+        flat[i] = x0
+        fd = (lp - lm) / (2 * FD_STEP)
+        err = abs(fd - g)
+        assert err <= max(FD_REL * abs(g), FD_ABS), (name, i, fd, g, err)
+        worst = max(worst, err / max(abs(g), 1e-300))
+    nonzero = sum(1 for name, i in picks if G[name].reshape(-1)[i] != 0)
+    return len(picks), nonzero
+
+
+@pytest.mark.slow
+def test_backward_fisheye_crop_512_gaussians_fp64_central_differences(O64):
+    full = syn.street_scene(1_000_000, seed=0, kind="camera")
+    fish, _ = syn.street_cameras()
+    opts = O64.opts(cutoffs=0, predicate=0)
+    o = np.asarray(fish.c2w, np.float64).reshape(3, 4)[:, 3]
+    sc = _nearest_visible(full, o, lambda s: O64.project_camera(s, fish, opts)[0])
+    # the tile-aligned 32x32 crop that the most of their boxes overlap
+    P, _ = O64.project_camera(sc, fish, opts)
+    r, v = P["rect"], P["valid"] == 1
+    best = (-1, 0, 0)
+    for cy in range(0, fish.height - 32 + 1, 16):
+        for cx in range(0, fish.width - 32 + 1, 16):
+            c = int((v & (r[:, 0] <= cx + 32) & (r[:, 1] >= cx) & (r[:, 2] <= cy + 32)
+                     & (r[:, 3] >= cy)).sum())
+            best = max(best, (c, cx, cy))
+    _, cx, cy = best
+    rays = np.array([(cy + j) * fish.width + cx + i for j in range(32) for i in range(32)])
+    nr = fish.width * fish.height
+    rng = np.random.default_rng(1)
+    gr = np.zeros((nr, 3), np.float32)
+    ga = np.zeros(nr, np.float32)
+    gd = np.zeros(nr, np.float32)
+    gr[rays] = rng.normal(size=(len(rays), 3)) / len(rays)
+    ga[rays] = rng.normal(size=len(rays)) / len(rays)
+    gd[rays] = rng.normal(size=len(rays)) / len(rays)
+    G = O64.backward_camera(sc, fish, gr, ga, gd, opts, rays=rays)
+
+    def loss():
+        out = O64.render_camera(sc, fish, opts, rays=rays)
+        return ((out["out"] * gr[rays]).sum() + (out["alpha"] * ga[rays]).sum()
+                + (out["depth"] * gd[rays]).sum())
+
+    n, nonzero = _fd_check(loss, G, sc)
+    assert n > 500 and nonzero > 300
+
+
+@pytest.mark.slow
+def test_backward_lidar_crop_512_gaussians_fp64_central_differences(O64):
+    full = syn.street_scene(2_000_000, seed=1, kind="lidar")
+    L = syn.street_lidar()
+    opts = O64.opts(cutoffs=0, predicate=0, cull=0)
+    o = L.col_c2w[L.n_cols // 2].astype(np.float64).reshape(3, 4)[:, 3]
+    sc = _nearest_visible(full, o, lambda s: O64.project_lidar(s, L, opts)[0])
+    P, _ = O64.project_lidar(sc, L, opts)
+    r, v = P["rect"], P["valid"] == 1
+    az = L.az0_deg + (np.arange(L.n_cols) + 0.5) * 360.0 / L.n_cols
+    el = L.elevations_deg
+    best = (-1, 0, 0)
+    for b0 in range(0, L.n_beams - 8 + 1, 4):
+        for c0 in range(0, L.n_cols - 64 + 1, 32):
+            c = int((v & (r[:, 0] <= az[c0 + 63]) & (r[:, 1] >= az[c0]) & (r[:, 2] <= el[b0 + 7])
+                     & (r[:, 3] >= el[b0])).sum())
+            best = max(best, (c, b0, c0))
+    _, b0, c0 = best
+    rays = np.array([(b0 + j) * L.n_cols + c0 + i for j in range(8) for i in range(64)])
+    nr = L.n_beams * L.n_cols
+    rng = np.random.default_rng(2)
+    g = [np.zeros(nr, np.float32) for _ in range(4)]
+    for k, sd in enumerate((0.02, 1.0, 1.0, 1.0)):     # range, intensity, drop, alpha
+        g[k][rays] = sd * rng.normal(size=len(rays)) / len(rays)
+    G = O64.backward_lidar(sc, L, *g, opts=opts, rays=rays)
+
+    def loss():
+        out = O64.render_lidar(sc, L, opts, rays=rays)
+        rg, it, dr = O64.lidar_decode(out)
+        return ((rg * g[0][rays]).sum() + (it * g[1][rays]).sum() + (dr * g[2][rays]).sum()
+                + (out["alpha"] * g[3][rays]).sum())
+
+    n, nonzero = _fd_check(loss, G, sc)
+    assert n > 150 and nonzero > 100
 
 
 # ------------------------------------------------------------ LiDAR SH^l

@@ -42,7 +42,13 @@ N_GAUSS = 1_000_000
 # alpha (exp, product, clamp: 3), compositing (transmittance 2, weight 1,
 # colour 6, depth 2, opacity 1): 56 flops
 FLOP_PER_PAIR = 56
-SM_COUNT, FP32_LANES = 152, 128
+FP32_LANES = 128          # FP32 lanes per SM (Blackwell SM: 4 partitions x 32)
+
+
+def sm_count():
+    """Multiprocessors of the current device (cudaDevAttrMultiProcessorCount)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 
 def parse():
@@ -432,7 +438,7 @@ def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar", beam=0.0):
     pairs = _work("lidar")
     if pairs and kind == "lidar" and beam == 0:
         pk = peaks()
-        peak = SM_COUNT * FP32_LANES * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        peak = sm_count() * FP32_LANES * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         ach = pairs * FLOP_PER_PAIR / (st[3] * 1e-3) / 1e12
         out["roofline"] = {"kernel": "k_render_lidar", "bound": "alu", "achieved": ach,
                            "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
@@ -623,11 +629,13 @@ def roofline(per_view, union_ms, seq_view, clocks):
     work_path = os.path.join(ROOT, "tests", "golden", "bench_work.json")
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tflops = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    sms = sm_count()
+    peak_tflops = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     render_ms = per_view[:, 3]
     out = {"kernel": "k_render_camera", "bound": "alu", "peak": peak_tflops,
            "unit": "TFLOP/s",
-           "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x "
+           "peak_source": f"derived: {sms} SMs (queried from the device) x {FP32_LANES} FP32 "
+                          f"lanes x 2 flop/FMA x "
                           f"{sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
            "traffic": None}
     try:

@@ -12,9 +12,16 @@
  *   row-major, float32 unless stated.
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream).  Work is enqueued on it; a call returns once its work is
- *   enqueued.  The render calls read back one 4-byte count (the number of
- *   (tile, Gaussian) pairs) and so wait for the projection stage of their
- *   own work; nothing else synchronises.
+ *   enqueued.  The render calls read back the number of (tile, Gaussian)
+ *   pairs and the device status word (below) and so wait for the depth
+ *   stage of their own work; nothing else synchronises.
+ * - Device status.  The sort stages wait on one another's published counts
+ *   (decoupled look-back).  Every such wait is bounded; one that runs out
+ *   sets the frame's status word, leaves every later kernel of the render in
+ *   bounds (the tile lists come out empty) and surfaces as SG_ERR_TIMEOUT:
+ *   from the render call itself when the depth sort gave up (exact mode),
+ *   otherwise from sg_frame_status, sg_frame_sync_outputs, the synchronous
+ *   host-output renders and the request server.
  * - Handles (scene, camera, lidar, frame) are owned by the library; create /
  *   destroy them from one host thread at a time.  Output and gradient
  *   buffers are owned by the caller.
@@ -46,6 +53,8 @@ typedef struct sg_frame_s *sg_frame;
 
 enum { SG_FEATURES_RGB = 0, SG_FEATURES_SH = 1, SG_FEATURES_LIDAR = 2, SG_FEATURES_LIDAR_SH = 3 };
 enum { SG_CAMERA_PINHOLE = 0, SG_CAMERA_FISHEYE = 1 };
+/* Sensor kinds of a request or a workspace query. */
+enum { SG_REQ_CAMERA = 0, SG_REQ_LIDAR = 1 };
 
 /* Library version and the CUDA architecture it was built for (103 for sm_103a). */
 int sg_version(void);
@@ -54,6 +63,10 @@ const char *sg_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads); the difference across a region counts its launches. */
 int64_t sg_launch_count(void);
+/* Number of device and pinned-host allocation and free calls (cudaMalloc,
+ * cudaFree, cudaMallocHost, cudaFreeHost) this library has made in this
+ * process so far (all threads). */
+int64_t sg_alloc_count(void);
 
 /* ----------------------------------------------------------------------
  * Gaussian scene (Sec. 3.1: particles with mean mu, opacity sigma and
@@ -202,6 +215,52 @@ sg_status sg_frame_set_capacity(sg_frame frame, int64_t max_pairs);
  * 0 = the result is complete).  SG_ERR_INVALID in exact mode. */
 sg_status sg_frame_dropped_pairs(sg_frame frame, int64_t *dropped, int64_t *pairs);
 
+/* Device status of the frame's last render: copies the status word on
+ * `stream` (the stream of that render, or one ordered after it) and waits
+ * for it.  SG_OK, or SG_ERR_TIMEOUT when a bounded look-back wait of the
+ * sort stages ran out in that render (its tile lists were left empty, so
+ * its outputs show no Gaussian).  SG_ERR_INVALID for a frame never
+ * rendered or a frame of sg_render_camera_static. */
+sg_status sg_frame_status(sg_frame frame, void *stream);
+
+/* ----------------------------------------------------------------------
+ * Workspace query for admission (a serving loop's memory budget).  The
+ * device bytes a frame's buffers grow to for one render of `scene` into a
+ * sensor of kind sensor_kind (SG_REQ_CAMERA or SG_REQ_LIDAR) with n_rays
+ * rays: the per-Gaussian projection and sort buffers and per-ray state,
+ * which are exact, and the (tile, Gaussian) pairs with their sort scratch,
+ * masks and compositing work items for an allowance of
+ * SG_ADMIT_PAIRS_PER_GAUSSIAN pairs per Gaussian (a render that makes more
+ * pairs grows past the estimate), with the library's growth head-room.  The
+ * tile count is bounded from n_rays: 16x16-pixel camera tiles of images at
+ * least 256 pixels on a side, LiDAR tiles of at least SG_ADMIT_LIDAR_RAYS_PER_TILE
+ * rays.  Errors: SG_ERR_INVALID (NULL scene or bytes, unknown kind, n_rays < 0).
+ * sg_frame_workspace_bytes: the bytes a frame holds now (device buffers).
+ * ---------------------------------------------------------------------- */
+#define SG_ADMIT_PAIRS_PER_GAUSSIAN 4
+#define SG_ADMIT_LIDAR_RAYS_PER_TILE 8
+sg_status sg_workspace_bytes(sg_scene scene, int sensor_kind, int64_t n_rays, size_t *bytes);
+sg_status sg_frame_workspace_bytes(sg_frame frame, size_t *bytes);
+
+/* ----------------------------------------------------------------------
+ * Testing hook for the device status path (not needed in normal use).
+ * max_spins: polling rounds a look-back wait makes before it gives up
+ * (0 = the default, about a second).  hold_site / hold_tile: the kernel
+ * kind and the tile (ticket) whose published counts are withheld, so that
+ * the next tile's wait is certain to run out (hold_site 0: none).  Every
+ * wait stays bounded and every access in bounds.  The values live in the
+ * current device's memory (so that replays of captured CUDA graphs see
+ * them); the call synchronises that device first.  Set them back with
+ * (0, SG_LOOKBACK_NONE, -1) after use. */
+enum {
+    SG_LOOKBACK_NONE = 0,
+    SG_LOOKBACK_COMPACT = 1,     /* depth stage: compaction of the visible Gaussians */
+    SG_LOOKBACK_DEPTH_SORT = 2,  /* depth stage: radix passes over the depth keys */
+    SG_LOOKBACK_OFFSETS = 3,     /* depth stage: scan of the tile counts into pair offsets */
+    SG_LOOKBACK_TILE_SORT = 4    /* radix passes over the pairs' tile ids */
+};
+sg_status sg_debug_lookback(uint32_t max_spins, int hold_site, int64_t hold_tile);
+
 /* ----------------------------------------------------------------------
  * Forward render (Eq. 1: front-to-back compositing of alpha_i = sigma_i
  * rho_i(tau_max) over the per-tile list sorted by (tile, depth, id); Sec. 3.2
@@ -221,7 +280,8 @@ sg_status sg_frame_dropped_pairs(sg_frame frame, int64_t *dropped, int64_t *pair
  *   d_alpha     omega
  * Errors: SG_ERR_INVALID (NULL handle / pose, misaligned poses, opts out of range, LiDAR
  * features on a camera render or vice versa), SG_ERR_OOM, SG_ERR_CUDA,
- * SG_ERR_OVERFLOW (more than 2^31-1 pairs).
+ * SG_ERR_OVERFLOW (more than 2^31-1 pairs), SG_ERR_TIMEOUT (a look-back wait
+ * of the depth sort gave up; later ones are reported by sg_frame_status).
  * ---------------------------------------------------------------------- */
 sg_status sg_render_camera(sg_scene scene, sg_camera cam, const float h_c2w[12],
                            const sg_render_opts *opts, sg_frame frame, float *d_rgb,
@@ -247,7 +307,8 @@ sg_status sg_render_camera_rs(sg_scene scene, sg_camera cam, const float *d_row_
                               float *d_alpha, float *d_depth, void *stream);
 
 /* Same renders with host output buffers: the device result is copied to
- * h_* (pinned or pageable) on `stream` and the call waits for it.  Inputs
+ * h_* (pinned or pageable) on `stream` and the call waits for it (and
+ * returns SG_ERR_TIMEOUT if a look-back wait of the render gave up).  Inputs
  * stay as above except the LiDAR poses, which are read from host memory. */
 sg_status sg_render_camera_host(sg_scene scene, sg_camera cam, const float h_c2w[12],
                                 const sg_render_opts *opts, sg_frame frame, float *h_rgb,
@@ -296,7 +357,8 @@ typedef struct {
 sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *views,
                             const sg_render_opts *opts, int host_outputs);
 /* Wait until the host copies of the frame's last render with host outputs
- * are done (at once if it has none). */
+ * are done (at once if it has none).  SG_ERR_TIMEOUT if a look-back wait of
+ * that render gave up (the copies are done all the same). */
 sg_status sg_frame_sync_outputs(sg_frame frame);
 
 /* ----------------------------------------------------------------------
@@ -318,7 +380,10 @@ sg_status sg_frame_sync_outputs(sg_frame frame);
  * streams of the same device) race and must be serialised by the caller.
  * Nothing in the array needs clearing between calls: every stage writes the
  * parts it later reads.  Like sg_render_camera, the call waits once for the
- * pair count.
+ * pair count; SG_ERR_TIMEOUT when a look-back wait of the depth sort gave
+ * up.  (A wait of the tile sort that gives up leaves the lists empty and is
+ * not reported: the call keeps no frame to query.)  The call makes no
+ * allocation of any kind: sg_alloc_count does not change across it.
  * ---------------------------------------------------------------------- */
 sg_status sg_render_camera_static(sg_scene scene, sg_camera cam, const float h_c2w[12],
                                   const sg_render_opts *opts, float *d_rgb, float *d_alpha,
@@ -381,7 +446,6 @@ typedef struct {
     int queue_capacity;     /* waiting requests before submit returns SG_ERR_BUSY */
     int use_graphs;         /* 1 (default): replay captured CUDA graphs, see below */
 } sg_server_config;
-enum { SG_REQ_CAMERA = 0, SG_REQ_LIDAR = 1 };
 typedef struct {
     int kind;                   /* SG_REQ_CAMERA or SG_REQ_LIDAR */
     sg_scene scene;

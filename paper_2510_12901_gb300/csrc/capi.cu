@@ -20,6 +20,9 @@ static std::atomic<int64_t> g_launches{0};
 
 static thread_local bool g_capture_guard = false;
 static std::atomic<uint64_t> g_uid{1};
+static std::atomic<int64_t> g_allocs{0};
+
+void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 void count_launch()
 {
@@ -46,17 +49,22 @@ sg_status cuda_status(cudaError_t e, const char *what)
 sg_status ensure(Buf &b, size_t bytes)
 {
     if (bytes <= b.bytes && b.p) return SG_OK;
+    if (b.borrowed) {   // a fixed workspace (the allocation-free render): never freed here
+        set_error("a buffer of the static workspace (%zu bytes) is too small for %zu bytes",
+                  b.bytes, bytes);
+        return SG_ERR_OVERFLOW;
+    }
     if (g_capture_guard) {
         set_error("workspace of %zu bytes would grow to %zu during launch capture", b.bytes, bytes);
         return SG_ERR_BUSY;
     }
     size_t nb = bytes < 256 ? 256 : bytes + bytes / 4;   // grow with head-room
     if (b.p) {
-        cudaFree(b.p);   // implicitly waits for work that may still use it
+        dev_free(b.p);   // implicitly waits for work that may still use it
         b.p = nullptr;
         b.bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&b.p, nb);
+    cudaError_t e = dev_malloc(&b.p, nb);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("device allocation of %zu bytes failed", nb);
@@ -68,7 +76,7 @@ sg_status ensure(Buf &b, size_t bytes)
 
 static void release(Buf &b)
 {
-    if (b.p) cudaFree(b.p);
+    if (b.p && !b.borrowed) dev_free(b.p);
     b.p = nullptr;
     b.bytes = 0;
 }
@@ -135,7 +143,7 @@ static sg_status upload_planes(Scene &s, const sg_gaussians_desc *d, cudaStream_
     return SG_OK;
 }
 
-static bool opts_ok(const sg_render_opts *o)
+bool opts_ok(const sg_render_opts *o)
 {
     if (!o) { set_error("opts is NULL"); return false; }
     if (!(o->alpha_min > 0.f && o->alpha_min < 1.f) || !(o->alpha_max > 0.f && o->alpha_max <= 1.f) ||
@@ -175,7 +183,7 @@ static sg_status frame_prepare(Frame &fr, int64_t n, int64_t nrays, int64_t ntil
 #undef SG_ENS
     if (!fr.h_scalars) {
         static_assert(sizeof(RenderDesc) <= 256, "RenderDesc outgrew its pinned slot");
-        if (cudaMallocHost(&fr.h_scalars, 512) != cudaSuccess) {
+        if (host_malloc(&fr.h_scalars, 512) != cudaSuccess) {
             cudaGetLastError();
             set_error("pinned allocation failed");
             return SG_ERR_OOM;
@@ -224,7 +232,8 @@ static sg_status sort_and_count(Frame &fr, int64_t n, cudaStream_t st)
     fr.depth_buf = rb;
     tmark(fr, 2, st);
     if (fr.k_cap > 0) return clamp_pairs(sc + 1, fr.k_cap, sc + 3, st);
-    SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 8, cudaMemcpyDeviceToHost, st));
+    // the counts and the status word in one copy
+    SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 4 * (kScalStatus + 1), cudaMemcpyDeviceToHost, st));
     SG_CUDA(cudaEventRecord(fr.ev_count, st));
     return SG_OK;
 }
@@ -242,6 +251,10 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
         K = fr.k_cap;
     } else {
         SG_CUDA(cudaEventSynchronize(fr.ev_count));
+        if (fr.h_scalars[kScalStatus]) {
+            set_error("a look-back wait of the depth sort gave up (device status word set)");
+            return SG_ERR_TIMEOUT;
+        }
         K = fr.h_scalars[1];
         if (K > 0x7fffffffLL) {
             set_error("%lld (tile, Gaussian) pairs exceed 2^31-1", (long long)K);
@@ -261,23 +274,25 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     // binning counts the tile sort's digits as it writes the pairs
     uint32_t *hist = nullptr;
     if (K > 0 && (s = radix_prepare(K, (bits + 7) / 8, fr, st, &hist, 0)) != SG_OK) return s;
+    const uint32_t *err = sc + kScalStatus;
     s = bin_pairs((const uint32_t *)fr.dvals[fr.depth_buf].p, (const uint32_t *)fr.offsets.p, sc,
-                  (const int4 *)fr.tiles.p, ntx, wrap, K, pk[0], pv[0], st, hist, bits);
+                  (const int4 *)fr.tiles.p, ntx, wrap, K, pk[0], pv[0], st, err, hist, bits);
     if (s != SG_OK) return s;
     int pb = 0;
-    s = radix_sort_pairs(pk, pv, K, sc + 1, 0, bits, fr, st, &pb);
+    s = radix_sort_pairs(pk, pv, K, sc + 1, 0, bits, fr, st, &pb, SG_LOOKBACK_TILE_SORT);
     if (s != SG_OK) return s;
     fr.pair_buf = pb;
     if (fr.kind == 1) {
-        s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st);
+        s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err);
     } else {   // camera lists also get their sub-block masks
         if ((s = ensure(fr.submask, K > 0 ? (size_t)K : 1)) != SG_OK) return s;
-        s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, pv[pb],
+        s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err, pv[pb],
                         (const float4 *)fr.rect.p, ntx, (uint8_t *)fr.submask.p);
     }
     if (s != SG_OK) return s;
-    if (fr.k_cap > 0)
-        SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 16, cudaMemcpyDeviceToHost, st));
+    if (fr.k_cap > 0)   // counts, dropped pairs and the status word, for the caller
+        SG_CUDA(cudaMemcpyAsync(fr.h_scalars, sc, 4 * (kScalStatus + 1), cudaMemcpyDeviceToHost,
+                                st));
     tmark(fr, 3, st);
     return SG_OK;
 }
@@ -352,6 +367,7 @@ extern "C" {
 
 int sg_version(void) { return 100; }
 int64_t sg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+int64_t sg_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }
 int sg_cuda_arch(void) { return 103; }
 const char *sg_last_error(void) { return g_err; }
 
@@ -388,7 +404,7 @@ sg_status sg_create_scene(const sg_gaussians_desc *desc, void *stream, sg_scene 
     sc.pitch = ((desc->n + 31) / 32) * 32;
     if (sc.pitch == 0) sc.pitch = 32;
     size_t bytes = sizeof(float) * (size_t)sc.pitch * (Scene::kFeat + F);
-    if (cudaMalloc(&sc.d_planes, bytes) != cudaSuccess) {
+    if (dev_malloc(&sc.d_planes, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         set_error("scene allocation of %zu bytes failed", bytes);
@@ -396,7 +412,7 @@ sg_status sg_create_scene(const sg_gaussians_desc *desc, void *stream, sg_scene 
     }
     s = upload_planes(sc, desc, (cudaStream_t)stream);
     if (s != SG_OK) {
-        cudaFree(sc.d_planes);
+        dev_free(sc.d_planes);
         delete h;
         return s;
     }
@@ -421,9 +437,9 @@ void sg_destroy_scene(sg_scene scene)
 {
     if (!scene) return;
     cudaDeviceSynchronize();   // renders still queued may read the scene
-    cudaFree(scene->s.d_planes);
-    cudaFree(scene->s.d_actor_of);
-    cudaFree(scene->s.d_actor_poses);
+    dev_free(scene->s.d_planes);
+    dev_free(scene->s.d_actor_of);
+    dev_free(scene->s.d_actor_poses);
     delete scene;
 }
 
@@ -440,8 +456,8 @@ sg_status sg_scene_set_actors(sg_scene scene, const int32_t *d_actor_of, int n_a
     cudaStream_t st = (cudaStream_t)stream;
     // the scene's old buffers may still be read by renders queued on `stream`
     SG_CUDA(cudaStreamSynchronize(st));
-    cudaFree(sc.d_actor_of);
-    cudaFree(sc.d_actor_poses);
+    dev_free(sc.d_actor_of);
+    dev_free(sc.d_actor_poses);
     sc.d_actor_of = nullptr;
     sc.d_actor_poses = nullptr;
     sc.n_actors = 0;
@@ -450,13 +466,13 @@ sg_status sg_scene_set_actors(sg_scene scene, const int32_t *d_actor_of, int n_a
     int32_t *of = nullptr;
     float *poses = nullptr;
     uint32_t *bad = nullptr;
-    if (cudaMalloc(&of, sizeof(int32_t) * (size_t)(sc.n > 0 ? sc.n : 1)) != cudaSuccess ||
-        cudaMalloc(&poses, sizeof(float) * 12 * (size_t)n_actors) != cudaSuccess ||
-        cudaMalloc(&bad, sizeof(uint32_t)) != cudaSuccess) {
+    if (dev_malloc(&of, sizeof(int32_t) * (size_t)(sc.n > 0 ? sc.n : 1)) != cudaSuccess ||
+        dev_malloc(&poses, sizeof(float) * 12 * (size_t)n_actors) != cudaSuccess ||
+        dev_malloc(&bad, sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(of);
-        cudaFree(poses);
-        cudaFree(bad);
+        dev_free(of);
+        dev_free(poses);
+        dev_free(bad);
         set_error("device allocation failed");
         return SG_ERR_OOM;
     }
@@ -476,10 +492,10 @@ sg_status sg_scene_set_actors(sg_scene scene, const int32_t *d_actor_of, int n_a
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(bad);
+    dev_free(bad);
     if (e != cudaSuccess || h_bad) {
-        cudaFree(of);
-        cudaFree(poses);
+        dev_free(of);
+        dev_free(poses);
         if (e != cudaSuccess) return cuda_status(e, "sg_scene_set_actors");
         set_error("an actor index is outside -1..%d", n_actors - 1);
         return SG_ERR_INVALID;
@@ -525,8 +541,8 @@ sg_status sg_create_camera(int model, int width, int height, float fx, float fy,
     for (int i = 0; i < 4; ++i) c.k[i] = (model == SG_CAMERA_FISHEYE && k) ? k[i] : 0.f;
     sg_status s = build_camera(c);
     if (s != SG_OK) {
-        cudaFree(c.d_pix);
-        cudaFree(c.d_tile_dir);
+        dev_free(c.d_pix);
+        dev_free(c.d_tile_dir);
         delete h;
         return s;
     }
@@ -538,8 +554,8 @@ void sg_destroy_camera(sg_camera cam)
 {
     if (!cam) return;
     cudaDeviceSynchronize();   // renders still queued may read its ray tables
-    cudaFree(cam->c.d_pix);
-    cudaFree(cam->c.d_tile_dir);
+    dev_free(cam->c.d_pix);
+    dev_free(cam->c.d_tile_dir);
     delete cam;
 }
 
@@ -585,14 +601,14 @@ void sg_destroy_lidar(sg_lidar lidar)
     if (!lidar) return;
     cudaDeviceSynchronize();   // renders still queued may read its tables
     Lidar &L = lidar->l;
-    cudaFree(L.d_T);
-    cudaFree(L.d_elev);
-    cudaFree(L.d_az);
-    cudaFree(L.d_sat);
-    cudaFree(L.d_items);
-    cudaFree(L.d_item_rays);
-    cudaFree(L.d_ray_e);
-    cudaFree(L.d_tile_u);
+    dev_free(L.d_T);
+    dev_free(L.d_elev);
+    dev_free(L.d_az);
+    dev_free(L.d_sat);
+    dev_free(L.d_items);
+    dev_free(L.d_item_rays);
+    dev_free(L.d_ray_e);
+    dev_free(L.d_tile_u);
     delete lidar;
 }
 
@@ -619,7 +635,7 @@ void sg_frame_destroy(sg_frame frame)
     cudaDeviceSynchronize();   // work queued on the frame must finish first
     Frame &f = frame->f;
     for_each_buf(f, [](Buf &b) { release(b); });
-    if (f.h_scalars) cudaFreeHost(f.h_scalars);
+    if (f.h_scalars) host_free(f.h_scalars);
     for (auto &e : f.ev)
         if (e) cudaEventDestroy(e);
     if (f.ev_count) cudaEventDestroy(f.ev_count);
@@ -752,12 +768,17 @@ sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *v
         const sg_camera_view &v = views[i];
         float *out[3] = {v.rgb, v.alpha, v.depth};
         if (host_outputs) {
+            Frame &f = v.frame->f;
             const int64_t np = (int64_t)v.camera->c.width * v.camera->c.height;
             for (int k = 0; k < 3; ++k) {
                 if (!out[k]) continue;
                 const size_t by = sizeof(float) * (size_t)np * (k == 0 ? 3 : 1);
-                if ((s = ensure(v.frame->f.host_stage[k], by)) != SG_OK) return s;
-                out[k] = (float *)v.frame->f.host_stage[k].p;
+                // growing frees the staging buffer, which the copies of the
+                // frame's previous render may still be reading
+                if (by > f.host_stage[k].bytes && f.copy_pending)
+                    SG_CUDA(cudaEventSynchronize(f.ev_copied));
+                if ((s = ensure(f.host_stage[k], by)) != SG_OK) return s;
+                out[k] = (float *)f.host_stage[k].p;
             }
         }
         if (host_outputs && v.frame->f.copy_pending)   // the staging is free once copied
@@ -792,11 +813,16 @@ sg_status sg_render_cameras(sg_scene scene, int n_views, const sg_camera_view *v
                 SG_CUDA(cudaMemcpyAsync(h[k], f.host_stage[k].p,
                                         sizeof(float) * (size_t)np * (k == 0 ? 3 : 1),
                                         cudaMemcpyDeviceToHost, f.copy_st));
+        // the render's status word travels with its outputs
+        SG_CUDA(cudaMemcpyAsync(f.h_scalars + kHostStatusOutputs,
+                                (const uint32_t *)f.scalars.p + kScalStatus, 4,
+                                cudaMemcpyDeviceToHost, f.copy_st));
         SG_CUDA(cudaEventRecord(f.ev_copied, f.copy_st));
         f.copy_pending = true;
     }
     if (host_outputs == 1)
-        for (int i = 0; i < n_views; ++i) SG_CUDA(cudaEventSynchronize(views[i].frame->f.ev_copied));
+        for (int i = 0; i < n_views; ++i)
+            if ((s = sg_frame_sync_outputs(views[i].frame)) != SG_OK) return s;
     return SG_OK;
 }
 
@@ -804,7 +830,29 @@ sg_status sg_frame_sync_outputs(sg_frame frame)
 {
     if (!frame) { set_error("frame is NULL"); return SG_ERR_INVALID; }
     Frame &f = frame->f;
-    if (f.copy_pending) SG_CUDA(cudaEventSynchronize(f.ev_copied));
+    if (!f.copy_pending) return SG_OK;
+    SG_CUDA(cudaEventSynchronize(f.ev_copied));
+    if (f.h_scalars[kHostStatusOutputs]) {
+        set_error("a look-back wait of the sort gave up in the frame's last render");
+        return SG_ERR_TIMEOUT;
+    }
+    return SG_OK;
+}
+
+sg_status sg_frame_status(sg_frame frame, void *stream)
+{
+    if (!frame) { set_error("frame is NULL"); return SG_ERR_INVALID; }
+    Frame &f = frame->f;
+    if (f.kind < 0 || !f.h_scalars) { set_error("frame has not been rendered"); return SG_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    SG_CUDA(cudaMemcpyAsync(f.h_scalars + kHostStatusQuery,
+                            (const uint32_t *)f.scalars.p + kScalStatus, 4,
+                            cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    if (f.h_scalars[kHostStatusQuery]) {
+        set_error("a look-back wait of the sort gave up in the frame's last render");
+        return SG_ERR_TIMEOUT;
+    }
     return SG_OK;
 }
 
@@ -896,7 +944,55 @@ sg_status sg_render_lidar_host(sg_scene scene, sg_lidar lidar, const float *h_co
     if (s != SG_OK) return s;
     for (int i = 0; i < 4; ++i)
         if (h[i]) SG_CUDA(cudaMemcpyAsync(h[i], d[i], sizeof(float) * nr, cudaMemcpyDeviceToHost, st));
-    SG_CUDA(cudaStreamSynchronize(st));
+    return sg_frame_status(frame, stream);   // also waits for the copies
+}
+
+// The frame bytes one render asks for, buffer by buffer as frame_prepare,
+// bin_and_sort, the sorts and the compositing launchers size them, each
+// grown with ensure()'s head-room.
+static size_t grown(size_t bytes) { return bytes < 256 ? 256 : bytes + bytes / 4; }
+
+sg_status sg_workspace_bytes(sg_scene scene, int sensor_kind, int64_t n_rays, size_t *bytes)
+{
+    if (!scene || !bytes || n_rays < 0 ||
+        (sensor_kind != SG_REQ_CAMERA && sensor_kind != SG_REQ_LIDAR)) {
+        set_error("sg_workspace_bytes: NULL argument, unknown sensor kind or n_rays < 0");
+        return SG_ERR_INVALID;
+    }
+    const bool cam = sensor_kind == SG_REQ_CAMERA;
+    const int64_t n = scene->s.n > 0 ? scene->s.n : 1, nr = n_rays > 0 ? n_rays : 1;
+    // units of the compositing: camera tiles (16x16 pixels, images >= 256 px
+    // a side: at most (17/16)^2 n_rays / 256 of them) or LiDAR work items
+    const int64_t units = cam ? (nr * 289 + 65535) / 65536 + 16
+                              : (nr + SG_ADMIT_LIDAR_RAYS_PER_TILE - 1) / SG_ADMIT_LIDAR_RAYS_PER_TILE;
+    const int64_t K = SG_ADMIT_PAIRS_PER_GAUSSIAN * n;
+    const int per_tile = cam ? 1 : 2;   // LiDAR work items sharing one tile's list
+    size_t b = 0;
+    // per Gaussian: record, box, tile range, depth, count, UT mean and
+    // covariance, depth keys and ids (x2), offsets
+    const size_t g[] = {sizeof(GRec), 16, 16, 4, 4, 8, 16, 4, 4, 4, 4, 4};
+    for (size_t by : g) b += grown(by * (size_t)n);
+    // per ray: state, features, contributor count; per unit: ranges, order
+    b += grown(16 * (size_t)nr) * 2 + grown(4 * (size_t)nr);
+    b += grown(8 * (size_t)units) + grown(4 * (size_t)units);
+    // pairs: keys and ids (x2), camera sub-block masks
+    b += 4 * grown(4 * (size_t)K) + (cam ? grown((size_t)K) : 0);
+    // sort scratch: the larger of the depth stage's and the tile sort's
+    const int64_t hd = depth_stage_words(n), ht = radix_scratch_words(K, 3);
+    b += grown(4 * (size_t)(hd > ht ? hd : ht));
+    const WorkSize ws = work_size(units, K * per_tile, kSegLen, cam ? 8 : 1);
+    b += grown(ws.work_bytes) + grown(ws.partial_bytes);
+    b += grown(64) + grown(sizeof(RenderDesc));   // scalars, descriptor
+    *bytes = b;
+    return SG_OK;
+}
+
+sg_status sg_frame_workspace_bytes(sg_frame frame, size_t *bytes)
+{
+    if (!frame || !bytes) { set_error("NULL argument"); return SG_ERR_INVALID; }
+    size_t b = 0;
+    for_each_buf(frame->f, [&](Buf &x) { if (!x.borrowed) b += x.bytes; });
+    *bytes = b;
     return SG_OK;
 }
 

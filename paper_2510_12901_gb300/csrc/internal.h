@@ -38,7 +38,33 @@ constexpr uint32_t kSegLen = SG_SEG_LEN;
 constexpr uint32_t kSegLenStatic = 1024;
 
 void set_error(const char *fmt, ...);
+bool opts_ok(const sg_render_opts *o);   // render options in range (sets the message)
 sg_status cuda_status(cudaError_t e, const char *what);
+// Every cudaMalloc / cudaFree / cudaMallocHost / cudaFreeHost of the library
+// goes through these, which count the calls (sg_alloc_count).
+void note_alloc();
+template <class T> inline cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    note_alloc();
+    return cudaMalloc((void **)p, bytes);
+}
+inline cudaError_t dev_free(void *p)
+{
+    if (!p) return cudaSuccess;
+    note_alloc();
+    return cudaFree(p);
+}
+template <class T> inline cudaError_t host_malloc(T **p, size_t bytes)
+{
+    note_alloc();
+    return cudaMallocHost((void **)p, bytes);
+}
+inline cudaError_t host_free(void *p)
+{
+    if (!p) return cudaSuccess;
+    note_alloc();
+    return cudaFreeHost(p);
+}
 void count_launch();           // not counted while capture_guard() is set
 void count_launches(int64_t n); // kernels run by a graph replay
 
@@ -145,6 +171,7 @@ struct RenderDesc {
 struct Buf {
     void *p = nullptr;
     size_t bytes = 0;
+    bool borrowed = false;   // memory the frame does not own (a fixed workspace): never grown
 };
 
 struct Frame {
@@ -166,7 +193,7 @@ struct Frame {
     Buf scalars;      // device scalars: [0] valid Gaussians [1] pairs [2] work-item
                       // counter [3] pairs dropped over capacity [4..5] work-item counts
                       // [6] backward work counter [7] deferred re-walks
-                      // [8] radix-sort look-back timeout flag
+                      // [8] status: a look-back wait gave up (kScalStatus)
     Buf desc;         // RenderDesc of the current render (device)
     uint32_t *h_scalars = nullptr;  // pinned: scalars mirror (64 B), then the RenderDesc
     RenderDesc *h_desc = nullptr;   // pinned staging of desc
@@ -202,6 +229,18 @@ bool &capture_guard();
 uint64_t next_uid();            // identity of a scene / sensor handle
 
 constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Index of the status word in a frame's device scalars: non-zero once a
+// look-back wait of the sort stages has given up in the current render.  The
+// projection kernel clears it at the start of every render.  Kernels after
+// the give-up stay in bounds: the binning and the tile ranges write nothing,
+// so every list is empty.  The host reads it with the pair count (exact
+// mode), with the scalars at the end of a capacity-mode render, and in
+// sg_frame_status / with host outputs.
+constexpr int kScalStatus = 8;
+// Pinned-mirror slots (frame h_scalars) of the status word read after the
+// render: by sg_frame_status, and with the host-output copies.
+constexpr int kHostStatusQuery = 12, kHostStatusOutputs = 13;
 
 // Upper bounds of the compositing work-item buffers.  A unit (a camera
 // tile, or a LiDAR work item of up to 32 rays of one tile) whose list holds
@@ -266,9 +305,10 @@ sg_status radix_prepare(int64_t n_max, int passes, Frame &fr, cudaStream_t st, u
                         int64_t extra);
 // Stable sort of up to n pairs (*d_n of them) by key bits [begin_bit,
 // end_bit); the digit counts are in the scratch that radix_prepare returned.
+// site: SG_LOOKBACK_DEPTH_SORT or SG_LOOKBACK_TILE_SORT (the test hook's site).
 sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n,
                            const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
-                           cudaStream_t st, int *result_buf);
+                           cudaStream_t st, int *result_buf, int site);
 // The depth stage: the Gaussians with a non-zero tile count sorted by depth
 // (keys/vals[*result_buf]: depth bits, ids), d_scal[0] = their number,
 // d_offsets = exclusive scan of their tile counts in that order, d_scal[1]
@@ -277,17 +317,19 @@ sg_status depth_stage(const uint32_t *d_count, const float *d_depth, int64_t n, 
                       uint32_t *vals[2], uint32_t *d_scal, uint32_t *d_offsets, Frame &fr,
                       cudaStream_t st, int *result_buf);
 // With d_hist (zeroed by radix_prepare), k_bin also counts the digits of
-// the tile sort over end_bit bits, for radix_sort_pairs.
+// the tile sort over end_bit bits, for radix_sort_pairs.  d_err: the frame's
+// status word (nothing is written once it is set).
 sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_nvalid,
                     const int4 *d_tiles, int ntx, int wrap_x, int64_t cap, uint32_t *d_keys,
-                    uint32_t *d_vals, cudaStream_t st, uint32_t *d_hist = nullptr,
-                    int end_bit = 0);
+                    uint32_t *d_vals, cudaStream_t st, const uint32_t *d_err,
+                    uint32_t *d_hist = nullptr, int end_bit = 0);
 // Per-tile ranges of the sorted pairs; with d_mask (camera lists), also the
 // per-pair sub-block masks (d_ids, d_rects, ntx: the pairs' Gaussians, the
 // per-Gaussian extent boxes, tiles per row).
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
-                      int64_t ntiles, cudaStream_t st, const uint32_t *d_ids = nullptr,
-                      const float4 *d_rects = nullptr, int ntx = 0, uint8_t *d_mask = nullptr);
+                      int64_t ntiles, cudaStream_t st, const uint32_t *d_err,
+                      const uint32_t *d_ids = nullptr, const float4 *d_rects = nullptr,
+                      int ntx = 0, uint8_t *d_mask = nullptr);
 sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStream_t st);
 
 // project.cu

@@ -5,6 +5,7 @@
 // which can block on the whole device, is not acceptable in their loop).
 // The paper has no counterpart; this is a deployment variant of the same
 // kernels.
+#include <math.h>
 #include <string.h>
 
 #include <mutex>
@@ -70,10 +71,13 @@ static sg_status static_workspace(unsigned char **out)
     return SG_OK;
 }
 
+// A frame buffer inside the array: borrowed, so that a launcher asking for
+// more than its size gets SG_ERR_OVERFLOW instead of a reallocation.
 static void carve(Buf &b, unsigned char *&cur, size_t bytes)
 {
     b.p = cur;
     b.bytes = bytes;
+    b.borrowed = true;
     cur += bytes;
 }
 
@@ -104,13 +108,12 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
                   (long long)kStMaxRays, (long long)kStMaxTiles);
         return SG_ERR_INVALID;
     }
-    if (!(opts->alpha_min > 0.f && opts->alpha_min < 1.f) ||
-        !(opts->alpha_max > 0.f && opts->alpha_max <= 1.f) ||
-        !(opts->t_min >= 0.f && opts->t_min < 1.f) || !(opts->near_dist > 0.f) ||
-        !(opts->ut_alpha > 0.f) || !(opts->ut_kappa > -3.f)) {
-        set_error("sg_render_camera_static: render options out of range");
-        return SG_ERR_INVALID;
-    }
+    if (!opts_ok(opts)) return SG_ERR_INVALID;
+    for (int i = 0; i < 12; ++i)
+        if (!isfinite(h_c2w[i])) {
+            set_error("sg_render_camera_static: pose is not finite");
+            return SG_ERR_INVALID;
+        }
     unsigned char *base = nullptr;
     sg_status s = static_workspace(&base);
     if (s != SG_OK) return s;
@@ -176,9 +179,14 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     if ((s = depth_stage((const uint32_t *)fr.count.p, (const float *)fr.depth.p, n, dk, dv, scal,
                          (uint32_t *)fr.offsets.p, fr, st, &rb)) != SG_OK)
         return s;
-    uint32_t hs[2] = {0, 0};
+    // the counts and the status word (pageable: the copy is synchronous here)
+    uint32_t hs[kScalStatus + 1] = {};
     SG_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SG_CUDA(cudaStreamSynchronize(st));
+    if (hs[kScalStatus]) {
+        set_error("sg_render_camera_static: a look-back wait of the depth sort gave up");
+        return SG_ERR_TIMEOUT;
+    }
     const int64_t K = hs[1];
     if (K > kStMaxPairs) {
         set_error("sg_render_camera_static: %lld (tile, Gaussian) pairs exceed the static "
@@ -192,14 +200,16 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     while (((int64_t)1 << bits) < nt) ++bits;
     uint32_t *hist = nullptr;
     if (K > 0 && (s = radix_prepare(K, (bits + 7) / 8, fr, st, &hist, 0)) != SG_OK) return s;
+    const uint32_t *err = scal + kScalStatus;
     if ((s = bin_pairs(dv[rb], (const uint32_t *)fr.offsets.p, scal, (const int4 *)fr.tiles.p,
-                       c.ntx, 0, K, pk[0], pv[0], st, hist, bits)) != SG_OK)
+                       c.ntx, 0, K, pk[0], pv[0], st, err, hist, bits)) != SG_OK)
         return s;
     int pb = 0;
-    if ((s = radix_sort_pairs(pk, pv, K, scal + 1, 0, bits, fr, st, &pb)) != SG_OK)
+    if ((s = radix_sort_pairs(pk, pv, K, scal + 1, 0, bits, fr, st, &pb,
+                              SG_LOOKBACK_TILE_SORT)) != SG_OK)
         return s;
     fr.pair_buf = pb;
-    if ((s = tile_ranges(pk[pb], scal + 1, K, (uint2 *)fr.ranges.p, nt, st, pv[pb],
+    if ((s = tile_ranges(pk[pb], scal + 1, K, (uint2 *)fr.ranges.p, nt, st, err, pv[pb],
                          (const float4 *)fr.rect.p, c.ntx, (uint8_t *)fr.submask.p)) != SG_OK)
         return s;
     return render_camera(c, *opts, fr, st);

@@ -236,12 +236,14 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
                  GRec *__restrict__ rec,
                  float4 *__restrict__ rect_out, int4 *__restrict__ tiles_out,
                  float *__restrict__ depth_out, uint32_t *__restrict__ count_out,
-                 float2 *__restrict__ mean_out, float4 *__restrict__ cov_out)
+                 float2 *__restrict__ mean_out, float4 *__restrict__ cov_out,
+                 uint32_t *__restrict__ status)
 {
     __shared__ float s_c2w[12];   // the pose, from the render's descriptor
     if (threadIdx.x < 12) s_c2w[threadIdx.x] = D->c2w[threadIdx.x];
     __syncthreads();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0) *status = 0u;     // a new render: no look-back wait has given up
     if (g >= n) return;
     const float *poses = kRS ? D->poses : nullptr;
     Activated a = activate(planes, pitch, g);
@@ -347,7 +349,7 @@ sg_status project_camera(const Scene &sc, const Camera &cam, const sg_render_opt
         sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, actor_params(sc), C,
         (const RenderDesc *)fr.desc.p, U, (GRec *)fr.rec.p,
         (float4 *)fr.rect.p, (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p,
-        (float2 *)fr.mean2d.p, (float4 *)fr.cov2d.p);
+        (float2 *)fr.mean2d.p, (float4 *)fr.cov2d.p, (uint32_t *)fr.scalars.p + kScalStatus);
     SG_LAUNCHED();
     return SG_OK;
 }
@@ -530,9 +532,10 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int 
                 int cull, GRec *__restrict__ rec, float4 *__restrict__ rect_out,
                 int4 *__restrict__ tiles_out, float *__restrict__ depth_out,
                 uint32_t *__restrict__ count_out, float2 *__restrict__ mean_out,
-                float4 *__restrict__ cov_out)
+                float4 *__restrict__ cov_out, uint32_t *__restrict__ status)
 {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0) *status = 0u;     // a new render: no look-back wait has given up
     if (g >= n) return;
     LidParams L = Lp;
     L.poses = D->poses;
@@ -691,7 +694,7 @@ sg_status project_lidar(const Scene &sc, const Lidar &Ld, const sg_render_opts &
         (const RenderDesc *)fr.desc.p, U, o.cull,
         (GRec *)fr.rec.p, (float4 *)fr.rect.p,
         (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p, (float2 *)fr.mean2d.p,
-        (float4 *)fr.cov2d.p);
+        (float4 *)fr.cov2d.p, (uint32_t *)fr.scalars.p + kScalStatus);
     SG_LAUNCHED();
     return SG_OK;
 }

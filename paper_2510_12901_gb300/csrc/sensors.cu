@@ -147,12 +147,12 @@ sg_status build_camera(Camera &cam)
     int64_t nt = (int64_t)cam.ntx * cam.nty;
     double *dirs = nullptr;
     unsigned char *valid = nullptr;
-    if (cudaMalloc(&dirs, sizeof(double) * 3 * np) != cudaSuccess ||
-        cudaMalloc(&valid, np) != cudaSuccess ||
-        cudaMalloc(&cam.d_pix, sizeof(float4) * np) != cudaSuccess ||
-        cudaMalloc(&cam.d_tile_dir, sizeof(double) * 3 * nt) != cudaSuccess) {
-        cudaFree(dirs);
-        cudaFree(valid);
+    if (dev_malloc(&dirs, sizeof(double) * 3 * np) != cudaSuccess ||
+        dev_malloc(&valid, np) != cudaSuccess ||
+        dev_malloc(&cam.d_pix, sizeof(float4) * np) != cudaSuccess ||
+        dev_malloc(&cam.d_tile_dir, sizeof(double) * 3 * nt) != cudaSuccess) {
+        dev_free(dirs);
+        dev_free(valid);
         set_error("sg_create_camera: device allocation failed");
         return SG_ERR_OOM;
     }
@@ -164,8 +164,8 @@ sg_status build_camera(Camera &cam)
                                                      valid, cam.d_tile_dir, cam.d_pix);
     count_launch();
     cudaError_t e = cudaDeviceSynchronize();
-    cudaFree(dirs);
-    cudaFree(valid);
+    dev_free(dirs);
+    dev_free(valid);
     if (e != cudaSuccess) return cuda_status(e, "camera ray table");
     return SG_OK;
 }
@@ -341,7 +341,7 @@ sg_status build_lidar(Lidar &L)
 #define SG_ALLOC_COPY(dst, vec)                                                         \
     do {                                                                                \
         size_t by_ = sizeof((vec)[0]) * (vec).size();                                   \
-        if (cudaMalloc((void **)&(dst), by_ ? by_ : 16) != cudaSuccess) {               \
+        if (dev_malloc((void **)&(dst), by_ ? by_ : 16) != cudaSuccess) {               \
             set_error("sg_create_lidar: device allocation failed");                     \
             return SG_ERR_OOM;                                                          \
         }                                                                               \

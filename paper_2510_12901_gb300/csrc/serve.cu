@@ -101,18 +101,18 @@ static int64_t count_kernel_nodes(cudaGraph_t g)
     return k;
 }
 
-// Workspace estimate of one request: per-Gaussian buffers, sort buffers
-// and records, per-ray state, and (tile, Gaussian) pairs at a generous 4
-// tiles per Gaussian.
+// Workspace estimate of one request for admission: sg_workspace_bytes of
+// its scene and sensor.
 static size_t request_bytes(const sg_request &r)
 {
-    const int64_t n = r.scene ? r.scene->s.n : 0;
     int64_t rays = 0;
     if (r.kind == SG_REQ_CAMERA && r.camera)
         rays = (int64_t)r.camera->c.width * r.camera->c.height;
     else if (r.kind == SG_REQ_LIDAR && r.lidar)
         rays = (int64_t)r.lidar->l.n_beams * r.lidar->l.n_cols;
-    return (size_t)n * (sizeof(GRec) + 160) + (size_t)rays * 24 + (size_t)n * 4 * 17;
+    size_t b = 0;
+    if (!r.scene || sg_workspace_bytes(r.scene, r.kind, rays, &b) != SG_OK) return 0;
+    return b;
 }
 
 }  // namespace sg
@@ -153,11 +153,26 @@ static sg_status render_plain(const sg_request &r, sg_frame fr, cudaStream_t st)
                            r.d_out[2], r.d_out[3], st);
 }
 
-static sg_status finish(cudaEvent_t ev, cudaStream_t st)
+// Wait for the request's render on `st` and check its device status word:
+// a capacity-mode render copies it with its scalars; after an exact render
+// it is copied here.
+static sg_status finish(sg_frame frame, cudaEvent_t ev, cudaStream_t st)
 {
-    cudaError_t e = cudaEventRecord(ev, st);
+    Frame &fr = frame->f;
+    const bool exact = fr.k_cap == 0;
+    uint32_t *word = fr.h_scalars + (exact ? kHostStatusQuery : kScalStatus);
+    cudaError_t e = cudaSuccess;
+    if (exact)
+        e = cudaMemcpyAsync(word, (const uint32_t *)fr.scalars.p + kScalStatus, 4,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev);
-    return e == cudaSuccess ? SG_OK : cuda_status(e, "request completion");
+    if (e != cudaSuccess) return cuda_status(e, "request completion");
+    if (*word) {
+        set_error("a look-back wait of the sort gave up in this request's render");
+        return SG_ERR_TIMEOUT;
+    }
+    return SG_OK;
 }
 
 static void note_pairs(sg_server S, const std::string &key, int64_t K)
@@ -200,7 +215,7 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
         cudaError_t e = cudaGraphLaunch(g.exec, st);
         if (e != cudaSuccess) return cuda_status(e, "cudaGraphLaunch");
         count_launches(g.kernels);
-        if ((s = finish(ev, st)) != SG_OK) return s;
+        if ((s = finish(frame, ev, st)) != SG_OK) return s;
         const int64_t dropped = fr.h_scalars[3], kept = fr.h_scalars[1];
         if (dropped == 0) {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -211,7 +226,7 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
         drop_graph(g);
         fr.k_cap = 0;
         if ((s = render_plain(r, frame, st)) != SG_OK) return s;
-        if ((s = finish(ev, st)) != SG_OK) return s;
+        if ((s = finish(frame, ev, st)) != SG_OK) return s;
         note_pairs(S, key, fr.n_pairs > kept + dropped ? fr.n_pairs : kept + dropped);
         std::lock_guard<std::mutex> lk(S->mu);
         S->overflows++;
@@ -227,7 +242,7 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
     if (known < 0) {    // first sight of this combination: exact render
         fr.k_cap = 0;
         if ((s = render_plain(r, frame, st)) != SG_OK) return s;
-        if ((s = finish(ev, st)) != SG_OK) return s;
+        if ((s = finish(frame, ev, st)) != SG_OK) return s;
         note_pairs(S, key, fr.n_pairs);
         return SG_OK;
     }
@@ -235,12 +250,12 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
     const int64_t cap = std::min<int64_t>(known + known / 4 + 65536, 0x7fffffffLL);
     fr.k_cap = cap;
     if ((s = render_plain(r, frame, st)) != SG_OK) return s;
-    if ((s = finish(ev, st)) != SG_OK) return s;
+    if ((s = finish(frame, ev, st)) != SG_OK) return s;
     if (fr.h_scalars[3] != 0) {
         const int64_t need = (int64_t)fr.h_scalars[1] + fr.h_scalars[3];
         fr.k_cap = 0;
         if ((s = render_plain(r, frame, st)) != SG_OK) return s;
-        if ((s = finish(ev, st)) != SG_OK) return s;
+        if ((s = finish(frame, ev, st)) != SG_OK) return s;
         note_pairs(S, key, need);
         return SG_OK;
     }
@@ -302,7 +317,7 @@ static void worker_main(sg_server S, int slot)
         } else {
             fr->f.k_cap = 0;
             s = render_plain(r, fr, st);
-            if (s == SG_OK) s = finish(ev, st);
+            if (s == SG_OK) s = finish(fr, ev, st);
         }
         const Clock::time_point t_done = Clock::now();
 

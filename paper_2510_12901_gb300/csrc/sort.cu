@@ -93,7 +93,21 @@ static_assert(kRadixThreads >= 256 && kRadixItems * kRadixThreads == kRadixTile,
               "radix tile layout");
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr uint32_t kLbAgg = 1u << 30, kLbPre = 2u << 30, kLbCount = (1u << 30) - 1u;
-constexpr uint32_t kLbSpins = 1u << 22;
+// Polling rounds a look-back wait makes before it gives up (about a second
+// on an idle GPU).  Test hook: the tile whose look-back words the kernels
+// of one site never publish (-1: none), so that the next tile's wait runs
+// out.  Both live in device memory, where sg_debug_lookback sets them, so
+// that replays of captured launch sequences see them too.
+constexpr uint32_t kLbSpinsDefault = 1u << 20;
+__device__ uint32_t g_lb_spins = kLbSpinsDefault;
+__device__ int g_hold_site = SG_LOOKBACK_NONE;
+__device__ long long g_hold_tile = -1;
+// The tile this launch (of `site`) withholds, or -1.
+__device__ __forceinline__ int64_t held_tile(int site)
+{
+    return *(volatile int *)&g_hold_site == site ? (int64_t) * (volatile long long *)&g_hold_tile
+                                                 : (int64_t)-1;
+}
 #ifndef SG_LB_BATCH
 #define SG_LB_BATCH 8
 #endif
@@ -104,7 +118,7 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
            uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
            const uint32_t *__restrict__ d_n, int shift, uint32_t mask,
            const uint32_t *__restrict__ hist, uint32_t *__restrict__ lookback,
-           uint32_t *__restrict__ ticket, uint32_t *__restrict__ err)
+           uint32_t *__restrict__ ticket, uint32_t *__restrict__ err, int site)
 {
     __shared__ uint32_t s_cnt[kRadixWarps][256];
     __shared__ uint32_t s_pre[256];
@@ -152,7 +166,9 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
             run += c;
         }
         volatile uint32_t *lb = lookback;
-        lb[(int64_t)tile * 256 + dg] = (tile == 0 ? kLbPre : kLbAgg) | run;
+        const bool publish = (int64_t)tile != held_tile(site);
+        const uint32_t max_spins = g_lb_spins;
+        if (publish) lb[(int64_t)tile * 256 + dg] = (tile == 0 ? kLbPre : kLbAgg) | run;
         uint32_t excl = 0, spins = 0;
         int64_t t = (int64_t)tile - 1;
         while (t >= 0) {
@@ -178,12 +194,12 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
             }
             if (pre) break;
             t -= took;
-            if (took == 0 && ++spins > kLbSpins) {   // gave up: flag it, leave the order wrong
+            if (took == 0 && ++spins > max_spins) {   // gave up: flag it, leave the order wrong
                 atomicOr(err, 1u);
                 break;
             }
         }
-        if (tile > 0) lb[(int64_t)tile * 256 + dg] = kLbPre | (excl + run);
+        if (tile > 0 && publish) lb[(int64_t)tile * 256 + dg] = kLbPre | (excl + run);
         s_pre[dg] = dig_off + excl;
     }
     __syncthreads();
@@ -215,7 +231,7 @@ sg_status radix_prepare(int64_t n_max, int passes, Frame &fr, cudaStream_t st, u
 
 sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
                            const uint32_t *d_n, int begin_bit, int end_bit, Frame &fr,
-                           cudaStream_t st, int *result_buf)
+                           cudaStream_t st, int *result_buf, int site)
 {
     *result_buf = 0;
     if (n_max <= 0 || end_bit <= begin_bit) return SG_OK;
@@ -228,14 +244,14 @@ sg_status radix_sort_pairs(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max,
     uint32_t *hist = (uint32_t *)fr.hist.p;
     uint32_t *tickets = hist + 2 * 256 * passes;            // [passes], padded to 16
     uint32_t *lookback = tickets + 16;
-    uint32_t *err = (uint32_t *)fr.scalars.p + 8;
+    uint32_t *err = (uint32_t *)fr.scalars.p + kScalStatus;
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         const int b = begin_bit + 8 * p;
         const int bits = end_bit - b < 8 ? end_bit - b : 8;
         k_onesweep<<<(unsigned)tiles, kRadixThreads, 0, st>>>(
             keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n, b, (1u << bits) - 1u,
-            hist + 256 * p, lookback + (int64_t)p * tiles * 256, tickets + p, err);
+            hist + 256 * p, lookback + (int64_t)p * tiles * 256, tickets + p, err, site);
         SG_LAUNCHED();
         cur ^= 1;
     }
@@ -265,11 +281,13 @@ constexpr unsigned long long kChAgg = 1ull << 62, kChPre = 2ull << 62,
 // words, 32 of them per round; warp 0 runs it and every lane returns it.  A
 // wait that runs out sets *err (the prefix is then wrong, never unbounded).
 __device__ unsigned long long chain_lookback(unsigned long long *lb, int64_t tile,
-                                             unsigned long long total, uint32_t *err)
+                                             unsigned long long total, uint32_t *err, int site)
 {
     const int lane = threadIdx.x & 31;
     volatile unsigned long long *v = lb;
-    if (lane == 0) v[tile] = (tile == 0 ? kChPre : kChAgg) | total;
+    const bool publish = tile != held_tile(site);
+    const uint32_t max_spins = g_lb_spins;
+    if (lane == 0 && publish) v[tile] = (tile == 0 ? kChPre : kChAgg) | total;
     unsigned long long excl = 0;
     uint32_t spins = 0;
     int64_t t = tile - 1;
@@ -286,12 +304,12 @@ __device__ unsigned long long chain_lookback(unsigned long long *lb, int64_t til
         excl += c;
         if (fp < fnp) break;
         t -= take;
-        if (take == 0 && ++spins > kLbSpins) {   // gave up: flag it
+        if (take == 0 && ++spins > max_spins) {   // gave up: flag it
             if (lane == 0) atomicOr(err, 1u);
             break;
         }
     }
-    if (lane == 0 && tile > 0) v[tile] = kChPre | (excl + total);
+    if (lane == 0 && tile > 0 && publish) v[tile] = kChPre | (excl + total);
     return excl;
 }
 
@@ -338,7 +356,7 @@ k_compact_depth(const uint32_t *__restrict__ count, const float *__restrict__ de
         const uint32_t v = lane < kChainWarps ? s_warp[lane] : 0u;
         const uint32_t inc = warp_incl_scan(v);
         const uint32_t total = __shfl_sync(0xffffffffu, inc, kChainWarps - 1);
-        const uint32_t excl = (uint32_t)chain_lookback(lb, tile, total, err);
+        const uint32_t excl = (uint32_t)chain_lookback(lb, tile, total, err, SG_LOOKBACK_COMPACT);
         if (lane < kChainWarps) s_warp[lane] = excl + inc - v;
         if (lane == 0 && tile == ntiles - 1) *d_nvalid = excl + total;
     }
@@ -360,7 +378,7 @@ k_compact_depth(const uint32_t *__restrict__ count, const float *__restrict__ de
 }
 
 __global__ void __launch_bounds__(kChainThreads)
-k_pair_offsets(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ count,
+k_pair_offsets(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ count, int64_t n,
                const uint32_t *__restrict__ d_nvalid, uint32_t *__restrict__ offsets,
                uint32_t *__restrict__ d_total, unsigned long long *__restrict__ lb,
                uint32_t *__restrict__ ticket, uint32_t *__restrict__ err)
@@ -385,8 +403,10 @@ k_pair_offsets(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ co
         const int64_t i = wbase + r * 32 + lane;
         c[r] = i < nv ? ids[i] : 0xffffffffu;
     }
+    // an id is outside 0..n-1 only after a look-back wait of the depth sort
+    // gave up (err set, the sort's output partly unwritten): count it as 0
 #pragma unroll
-    for (int r = 0; r < kChainChunks; ++r) c[r] = c[r] != 0xffffffffu ? count[c[r]] : 0u;
+    for (int r = 0; r < kChainChunks; ++r) c[r] = (int64_t)c[r] < n ? count[c[r]] : 0u;
     uint32_t run = 0;   // the warp's entries before chunk r
 #pragma unroll
     for (int r = 0; r < kChainChunks; ++r) {
@@ -401,7 +421,7 @@ k_pair_offsets(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ co
         const uint32_t v = lane < kChainWarps ? s_warp[lane] : 0u;
         const uint32_t inc = warp_incl_scan(v);
         const uint32_t total = __shfl_sync(0xffffffffu, inc, kChainWarps - 1);
-        const unsigned long long excl = chain_lookback(lb, tile, total, err);
+        const unsigned long long excl = chain_lookback(lb, tile, total, err, SG_LOOKBACK_OFFSETS);
         if (lane < kChainWarps) s_warp[lane] = (uint32_t)excl + inc - v;
         if (lane == 0 && tile == ntiles - 1) {
             // saturated, so that a total of 2^32 pairs or more reads as an overflow
@@ -423,8 +443,8 @@ sg_status depth_stage(const uint32_t *d_count, const float *d_depth, int64_t n, 
                       cudaStream_t st, int *result_buf)
 {
     *result_buf = 0;
-    if (n <= 0) {
-        SG_CUDA(cudaMemsetAsync(d_scal, 0, 8, st));
+    if (n <= 0) {   // no projection kernel ran: clear the status word too
+        SG_CUDA(cudaMemsetAsync(d_scal, 0, 4 * (kScalStatus + 1), st));
         return SG_OK;
     }
     if (n > (int64_t)kLbCount) {
@@ -441,14 +461,15 @@ sg_status depth_stage(const uint32_t *d_count, const float *d_depth, int64_t n, 
     static_assert(radix_scratch_words(1, 4) % 2 == 0, "64-bit chain words stay aligned");
     unsigned long long *chain = (unsigned long long *)(hist + radix_scratch_words(n, 4));
     uint32_t *tickets = (uint32_t *)chain;                 // [0] compaction, [1] offsets
-    uint32_t *err = (uint32_t *)fr.scalars.p + 8;
+    uint32_t *err = (uint32_t *)fr.scalars.p + kScalStatus;
     k_compact_depth<<<(unsigned)ntiles, kChainThreads, 0, st>>>(
         d_count, d_depth, n, ntiles, keys[0], vals[0], d_scal, hist, chain + 2, tickets, err);
     SG_LAUNCHED();
-    if ((s = radix_sort_pairs(keys, vals, n, d_scal, 0, 32, fr, st, result_buf)) != SG_OK)
+    if ((s = radix_sort_pairs(keys, vals, n, d_scal, 0, 32, fr, st, result_buf,
+                              SG_LOOKBACK_DEPTH_SORT)) != SG_OK)
         return s;
     k_pair_offsets<<<(unsigned)ntiles, kChainThreads, 0, st>>>(
-        vals[*result_buf], d_count, d_scal, d_offsets, d_scal + 1, chain + 2 + ntiles,
+        vals[*result_buf], d_count, n, d_scal, d_offsets, d_scal + 1, chain + 2 + ntiles,
         tickets + 1, err);
     SG_LAUNCHED();
     return SG_OK;
@@ -476,7 +497,7 @@ __global__ void __launch_bounds__(kBinThreads)
 k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
       const uint32_t *__restrict__ d_scal, const int4 *__restrict__ tiles, int ntx, int wrap_x,
       uint32_t cap, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-      uint32_t *__restrict__ hist, int end_bit)
+      uint32_t *__restrict__ hist, int end_bit, const uint32_t *__restrict__ err)
 {
     __shared__ uint32_t s_off[kBinChunk + 1], s_id[kBinChunk + 1];
     __shared__ uint32_t s_h[kBinPasses][256];
@@ -486,7 +507,9 @@ k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
     const int64_t nvalid = d_scal[0];
     const int64_t K = min((int64_t)d_scal[1], (int64_t)cap);
     const int64_t p0 = (int64_t)blockIdx.x * kBinChunk;
-    if (p0 >= K || nvalid == 0) return;
+    // after a look-back wait of the depth stage gave up, the ids and offsets
+    // are not trustworthy (offsets may decrease): write nothing
+    if (p0 >= K || nvalid == 0 || *err) return;
     const int64_t p1 = min(K, p0 + kBinChunk);
     // the owner of p0: the largest k with offsets[k] <= p0 (offsets[0] = 0,
     // strictly increasing: every valid Gaussian has a pair)
@@ -519,7 +542,7 @@ k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
             const uint32_t g = s_id[a];
             const int4 r = tiles[g];
             const uint32_t local = (uint32_t)(pos - s_off[a]), w = (uint32_t)(r.y - r.x + 1);
-            const int ty = r.z + (int)(local / w);
+            const int ty = min(r.w, r.z + (int)(local / w));   // within the range, always
             int x = r.x + (int)(local % w);
             if (wrap_x) { x %= ntx; if (x < 0) x += ntx; }
             key = (uint32_t)(ty * ntx + x);
@@ -547,7 +570,8 @@ k_bin(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ offsets,
 
 sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint32_t *d_nvalid,
                     const int4 *d_tiles, int ntx, int wrap_x, int64_t cap, uint32_t *d_keys,
-                    uint32_t *d_vals, cudaStream_t st, uint32_t *d_hist, int end_bit)
+                    uint32_t *d_vals, cudaStream_t st, const uint32_t *d_err, uint32_t *d_hist,
+                    int end_bit)
 {
     if (cap <= 0) return SG_OK;
     if (d_hist && (end_bit < 1 || end_bit > 8 * kBinPasses)) {
@@ -556,7 +580,7 @@ sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint
     }
     k_bin<<<(unsigned)((cap + kBinChunk - 1) / kBinChunk), kBinThreads, 0, st>>>(
         d_ids, d_offsets, d_nvalid, d_tiles, ntx, wrap_x, (uint32_t)cap, d_keys, d_vals, d_hist,
-        end_bit);
+        end_bit, d_err);
     SG_LAUNCHED();
     return SG_OK;
 }
@@ -567,14 +591,17 @@ sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint
 // columns 8 (w & 1) .., rows 4 (w >> 1) ..), by the same float comparisons
 // as the per-ray test.  The compositing warps scan these contiguous bytes
 // and never stage an entry that no pixel of their sub-block can see.
+// After a look-back wait gave up (*err) the pairs may hold stale tile ids:
+// every range stays empty (zeroed before the launch).
 template <bool kMask>
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
                          uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
-                         const float4 *__restrict__ rects, int ntx, uint8_t *__restrict__ mask)
+                         const float4 *__restrict__ rects, int ntx, uint8_t *__restrict__ mask,
+                         const uint32_t *__restrict__ err)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t K = *d_K;
-    if (i >= K) return;
+    if (i >= K || *err) return;
     uint32_t t = keys[i];
     if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
     if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
@@ -601,16 +628,18 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__re
 }
 
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
-                      int64_t ntiles, cudaStream_t st, const uint32_t *d_ids,
-                      const float4 *d_rects, int ntx, uint8_t *d_mask)
+                      int64_t ntiles, cudaStream_t st, const uint32_t *d_err,
+                      const uint32_t *d_ids, const float4 *d_rects, int ntx, uint8_t *d_mask)
 {
     SG_CUDA(cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * ntiles, st));
     if (K_max == 0) return SG_OK;
     const unsigned grid = (unsigned)((K_max + 255) / 256);
     if (d_mask)
-        k_ranges<true><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rects, ntx, d_mask);
+        k_ranges<true><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rects, ntx, d_mask,
+                                             d_err);
     else
-        k_ranges<false><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, nullptr, nullptr, 0, nullptr);
+        k_ranges<false><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, nullptr, nullptr, 0, nullptr,
+                                              d_err);
     SG_LAUNCHED();
     return SG_OK;
 }
@@ -633,3 +662,19 @@ sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStrea
 }
 
 }  // namespace sg
+
+extern "C" sg_status sg_debug_lookback(uint32_t max_spins, int hold_site, int64_t hold_tile)
+{
+    if (hold_site < 0 || hold_site > SG_LOOKBACK_TILE_SORT || hold_tile < -1) {
+        sg::set_error("sg_debug_lookback: site %d / tile %lld out of range", hold_site,
+                      (long long)hold_tile);
+        return SG_ERR_INVALID;
+    }
+    const uint32_t spins = max_spins ? max_spins : sg::kLbSpinsDefault;
+    const long long tile = hold_site ? (long long)hold_tile : -1;
+    SG_CUDA(cudaDeviceSynchronize());   // no kernel reads them meanwhile
+    SG_CUDA(cudaMemcpyToSymbol(sg::g_lb_spins, &spins, sizeof(spins)));
+    SG_CUDA(cudaMemcpyToSymbol(sg::g_hold_site, &hold_site, sizeof(hold_site)));
+    SG_CUDA(cudaMemcpyToSymbol(sg::g_hold_tile, &tile, sizeof(tile)));
+    return SG_OK;
+}

@@ -79,6 +79,8 @@ class sg_server_report(C.Structure):
 
 
 REQ_CAMERA, REQ_LIDAR = 0, 1
+(LOOKBACK_NONE, LOOKBACK_COMPACT, LOOKBACK_DEPTH_SORT, LOOKBACK_OFFSETS,
+ LOOKBACK_TILE_SORT) = range(5)
 _H = C.c_void_p
 _P = C.c_void_p
 _SIGNATURES = {
@@ -135,6 +137,11 @@ _SIGNATURES = {
     "sg_frame_timing": (C.c_int, [_H, C.POINTER(C.c_float)]),
     "sg_frame_marks": (C.c_int, [_H, _H, C.POINTER(C.c_float)]),
     "sg_frame_sync_outputs": (C.c_int, [_H]),
+    "sg_frame_status": (C.c_int, [_H, _P]),
+    "sg_alloc_count": (C.c_int64, []),
+    "sg_workspace_bytes": (C.c_int, [_H, C.c_int, C.c_int64, C.POINTER(C.c_size_t)]),
+    "sg_frame_workspace_bytes": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
+    "sg_debug_lookback": (C.c_int, [C.c_uint32, C.c_int, C.c_int64]),
 }
 
 _lib = None
@@ -387,6 +394,30 @@ def sg_frame_timing(frame):
 
 def sg_frame_sync_outputs(frame):
     _check(load().sg_frame_sync_outputs(frame))
+
+
+def sg_frame_status(frame, stream=0):
+    _check(load().sg_frame_status(frame, stream))
+
+
+def sg_alloc_count():
+    return load().sg_alloc_count()
+
+
+def sg_workspace_bytes(scene, sensor_kind, n_rays):
+    b = C.c_size_t()
+    _check(load().sg_workspace_bytes(scene, sensor_kind, n_rays, C.byref(b)))
+    return b.value
+
+
+def sg_frame_workspace_bytes(frame):
+    b = C.c_size_t()
+    _check(load().sg_frame_workspace_bytes(frame, C.byref(b)))
+    return b.value
+
+
+def sg_debug_lookback(max_spins=0, hold_site=LOOKBACK_NONE, hold_tile=-1):
+    _check(load().sg_debug_lookback(max_spins, hold_site, hold_tile))
 
 
 def sg_frame_marks(frame, ref):

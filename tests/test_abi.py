@@ -98,3 +98,19 @@ def test_camera_view_struct_layout(sg):
     assert [getattr(f, n).offset for n in ("camera", "c2w", "frame", "rgb", "alpha", "depth",
                                            "stream", "row_c2w")] \
         == [0, 8, 56, 64, 72, 80, 88, 96]
+
+
+def test_status_workspace_and_hook_arguments_are_checked(sg):
+    lib = sg.load()
+    # NULL scene, unknown kind, negative rays: refused before any CUDA work
+    b = C.c_size_t()
+    assert lib.sg_workspace_bytes(None, sg.REQ_CAMERA, 100, C.byref(b)) == -1
+    assert lib.sg_frame_workspace_bytes(None, C.byref(b)) == -1
+    assert lib.sg_frame_status(None, None) == -1
+    fr = sg.sg_frame_create()
+    assert lib.sg_frame_status(fr, None) == -1          # never rendered
+    assert "not been rendered" in sg.sg_last_error()
+    sg.sg_frame_destroy(fr)
+    assert lib.sg_debug_lookback(0, 9, 0) == -1         # unknown site
+    assert lib.sg_debug_lookback(0, sg.LOOKBACK_COMPACT, -2) == -1
+    assert sg.sg_alloc_count() >= 0

@@ -158,17 +158,30 @@ def test_graph_replay_that_outgrows_its_capacity_is_rendered_exactly():
 
 def test_memory_admission_serialises_and_completes(W):
     from paper_2510_12901_gb300 import serve
-    # pinhole requests on the larger scene: each needs ~15 MB of workspace,
-    # so a 20 MB budget admits one at a time even with four free slots
+    from paper_2510_12901_gb300 import simgut as sg
+    # pinhole requests on the larger scene, with a budget of 1.5 times one
+    # request's workspace (sg_workspace_bytes, the server's admission
+    # estimate): one at a time is admitted even with four free slots
     idx = [i for i in range(len(W.kinds)) if W.kinds[i] == 0 and W.scene_of[i] == 1]
     assert len(idx) >= 3
-    srv = serve.Server(n_slots=4, memory_budget=20_000_000)
+    cs, _ = W.scenes[1]
+    pin = W.cams["pinhole"][0]
+    one = sg.sg_workspace_bytes(cs.handle, sg.REQ_CAMERA, pin.width * pin.height)
+    srv = serve.Server(n_slots=4, memory_budget=int(1.5 * one))
     tickets = [srv.submit(W.request(i)) for i in idx]
     for t in tickets:
         srv.wait(t, 120.0)
     st = srv.stats()
     srv.close()
     assert st["completed"] == len(idx) and st["peak_in_flight"] == 1
+    # twice the budget admits two at a time
+    srv = serve.Server(n_slots=4, memory_budget=int(2.5 * one))
+    tickets = [srv.submit(W.request(i)) for i in idx]
+    for t in tickets:
+        srv.wait(t, 120.0)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(idx) and st["peak_in_flight"] <= 2
 
 
 def test_queue_full_and_wait_timeout(W):

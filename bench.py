@@ -150,6 +150,13 @@ def peaks():
         return {}
 
 
+def forward_frame(sg):
+    """A frame for forward renders only: no per-ray state for a backward."""
+    f = sg.Frame()
+    sg.sg_frame_set_backward_state(f.handle, 0)
+    return f
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -178,7 +185,7 @@ def run_ours(args):
     opts = sg.sg_default_opts()
     # two frame sets, alternated, so that the stage events of step i can be
     # read once step i+1 has passed its own mid-render synchronisation
-    frames = [[sg.Frame() for _ in cams] for _ in range(2)]
+    frames = [[forward_frame(sg) for _ in cams] for _ in range(2)]
     for fs in frames:
         for f in fs:
             sg.sg_frame_set_timing(f.handle, 1)
@@ -302,7 +309,7 @@ def run_ours(args):
             host.append([torch.empty(3 * n, dtype=torch.float32).pin_memory(),
                          torch.empty(n, dtype=torch.float32).pin_memory(),
                          torch.empty(n, dtype=torch.float32).pin_memory()])
-        ef = [sg.Frame() for _ in cams]
+        ef = [forward_frame(sg) for _ in cams]
         hsets.append((host, ef, sg.sg_camera_views(
             [(ch.handle, c.c2w, f.handle, h[0].data_ptr(), h[1].data_ptr(), h[2].data_ptr(),
               vs.cuda_stream) for (ch, c), h, f, vs in zip(cams, host, ef, vstreams)])))
@@ -351,6 +358,8 @@ def run_ours(args):
                        "rays_per_step": rays_per_step, "parallelism": "replicas",
                        "views": "one sg_render_cameras call per step, each view on its own stream",
                        "pair_counts": "exact (the host waits for each view's pair count)",
+                       "frames": "forward only (sg_frame_set_backward_state 0: no per-ray "
+                                 "state for a backward is written)",
                        "l2": "inputs larger than L2 (236 MB of scene planes read per view)",
                        "wall_ms_per_step": wall_ms},
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
@@ -399,7 +408,7 @@ def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar", beam=0.0):
     S, Ld = sg.Scene(sc), sg.Lidar(L)
     poses = torch.from_numpy(np.ascontiguousarray(L.col_c2w, np.float32)).cuda()
     outs = [torch.empty((L.n_beams, L.n_cols), device="cuda") for _ in range(4)]
-    frames = [sg.Frame(), sg.Frame()]
+    frames = [forward_frame(sg), forward_frame(sg)]
     for f in frames:
         sg.sg_frame_set_timing(f.handle, 1)
     opts = sg.sg_default_opts(beam_divergence=beam)
@@ -457,7 +466,7 @@ def actors_workload(torch, sg, syn, steps, warmup):
     outs = [[torch.empty((c.height, c.width, 3), device="cuda"),
              torch.empty((c.height, c.width), device="cuda"),
              torch.empty((c.height, c.width), device="cuda")] for _, c in cams]
-    frames = [sg.Frame() for _ in cams]
+    frames = [forward_frame(sg) for _ in cams]
     vs = [torch.cuda.Stream() for _ in cams]
     views = sg.sg_camera_views([(ch.handle, c.c2w, f.handle, o[0].data_ptr(), o[1].data_ptr(),
                                  o[2].data_ptr(), v.cuda_stream)
@@ -501,7 +510,7 @@ def rolling_shutter_workload(torch, sg, syn, steps, warmup):
     outs = [[torch.empty((c.height, c.width, 3), device="cuda"),
              torch.empty((c.height, c.width), device="cuda"),
              torch.empty((c.height, c.width), device="cuda")] for _, c in cams]
-    frames = [sg.Frame() for _ in cams]
+    frames = [forward_frame(sg) for _ in cams]
     opts = sg.sg_default_opts()
     stream = torch.cuda.current_stream()
     vs = [torch.cuda.Stream() for _ in cams]

@@ -197,6 +197,14 @@ sg_render_opts sg_default_opts(void);
  * ---------------------------------------------------------------------- */
 sg_status sg_frame_create(sg_frame *out);
 void sg_frame_destroy(sg_frame frame);
+/* Whether renders with this frame write the per-ray state the backward
+ * reads (final transmittance, sums, contributor count: 36 bytes per ray);
+ * on (1) by default.  A frame used for forward renders only (inference,
+ * serving) can turn it off (0) and save that memory traffic;
+ * sg_backward_* then refuses the frame's renders (SG_ERR_INVALID), and
+ * the SG_FIELD_RAY_STATE / SG_FIELD_N_CONTRIB fields are not updated.
+ * Errors: SG_ERR_INVALID (NULL frame). */
+sg_status sg_frame_set_backward_state(sg_frame frame, int keep);
 
 /* Capacity mode.  With max_pairs > 0 the frame's (tile, Gaussian) pair
  * buffers are sized for max_pairs pairs and sg_render_camera /

@@ -401,8 +401,9 @@ __global__ void __launch_bounds__(32 * kBwWarps)
 k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
                  const uint32_t *__restrict__ item_rays, const float4 *__restrict__ ray_e,
                  const double *__restrict__ item_u, const float *__restrict__ poses,
-                 const float *__restrict__ az_col, const float *__restrict__ elev,
-                 const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
+                 const uint2 *__restrict__ tile_items, const uint32_t *__restrict__ lmask,
+                 int64_t lmask_stride, const GRec *__restrict__ rec,
+                 const uint32_t *__restrict__ ids,
                  const uint2 *__restrict__ ranges, const uint2 *__restrict__ work,
                  const uint2 *__restrict__ unit_info, const uint32_t *__restrict__ counts,
                  uint32_t *__restrict__ counter, const float4 *__restrict__ partials,
@@ -413,7 +414,6 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
 {
     __shared__ float4 s_all[kBwWarps][kLidPlanes][32];
     __shared__ uint32_t s_gid[kBwWarps][32], s_lanes[kBwWarps][32], s_pos[kBwWarps][32];
-    __shared__ float s_raz[kBwWarps][32], s_rel[kBwWarps][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float4(*s)[32] = s_all[wib];
     const uint32_t n_work = counts[0];
@@ -439,13 +439,11 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
         hi = min(hi, lim);
         if (hi <= lo) continue;
         const int c = valid ? (int)(ray % (uint32_t)P.n_cols) : it.col0;
-        const int b = valid ? (int)(ray / (uint32_t)P.n_cols) : 0;
         const int sb = 3 + 4 * (c - it.col0);
         float dh[3], dl[3], dd[3], d[3];
         lidar_ray(it, item_u, item_id, poses, ray_e[it.ray_off + lane], c, dh, dl, dd, d);
-        s_raz[wib][lane] = valid ? az_col[c] : __int_as_float(0x7fc00000);
-        s_rel[wib][lane] = valid ? elev[b] : __int_as_float(0x7fc00000);
-        __syncwarp();
+        // the item's ray masks of the list entries (the forward's own)
+        const uint32_t *lm = lmask + (int64_t)(item_id - (int)tile_items[it.tile].x) * lmask_stride;
         float T = 1.f, Qp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (seg > 0) {
             const float4 *pq = partials + ((size_t)(ui.y + seg) * 32 + lane) * 2;
@@ -471,16 +469,21 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
             Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * Z + gQ[4] * W;
             U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
-        uint32_t nid = lo + lane < hi ? ids[lo + lane] : 0u;   // one batch ahead
+        uint32_t nid = 0u, nm = 0u;   // one batch ahead
+        if (lo + lane < hi) {
+            nid = ids[lo + lane];
+            nm = lm[lo + lane];
+        }
         for (uint32_t base = lo; base < hi; base += 32) {
             const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
             const uint32_t idx = base + lane;
             const uint32_t g = nid;
-            if (idx + 32 < hi) nid = ids[idx + 32];
-            uint32_t m = 0u;
-            if (idx < hi) {
-                const float4 rc = rec[g].rect;
-                m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, s_raz[wib], s_rel[wib]) & act;
+            const uint32_t m = nm & act;
+            if (idx + 32 < hi) {
+                nid = ids[idx + 32];
+                nm = lm[idx + 32];
+            } else {
+                nm = 0u;
             }
             const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
             if (bal == 0u) continue;
@@ -857,8 +860,9 @@ sg_status backward_lidar(const Scene &sc, const Lidar &L, Frame &fr, const float
         if ((s = persistent_grid((const void *)k_backward_lidar, ws.max_items, grid)) != SG_OK)
             return s;
         k_backward_lidar<<<(unsigned)grid, 32 * kBwWarps, 0, st>>>(
-            P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, fr.d_lidar_poses, L.d_az,
-            L.d_elev, (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
+            P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, fr.d_lidar_poses,
+            L.d_tile_items, (const uint32_t *)fr.lmask.p, fr.lmask_stride,
+            (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
             (const uint2 *)fr.ranges.p, (const uint2 *)(cw + ws.info_bytes + ws.off_bytes),
             (const uint2 *)cw, (const uint32_t *)fr.scalars.p + 4, counter,
             (const float4 *)fr.partials.p, (const float4 *)fr.ray_state.p,

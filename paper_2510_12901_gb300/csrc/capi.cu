@@ -198,6 +198,7 @@ static sg_status frame_prepare(Frame &fr, int64_t n, int64_t nrays, int64_t ntil
     fr.n_gauss = n;
     fr.n_rays = nrays;
     fr.n_tiles = ntiles;
+    fr.state_kept = fr.keep_state;
     return SG_OK;
 }
 
@@ -282,8 +283,13 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     s = radix_sort_pairs(pk, pv, K, sc + 1, 0, bits, fr, st, &pb, SG_LOOKBACK_TILE_SORT);
     if (s != SG_OK) return s;
     fr.pair_buf = pb;
-    if (fr.kind == 1) {
-        s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err);
+    if (fr.kind == 1) {   // LiDAR lists also get their per-item ray masks
+        const Lidar &L = static_cast<const sg_lidar_s *>(fr.sensor)->l;
+        const size_t by = sizeof(uint32_t) * (size_t)(K > 0 ? K : 1) * L.max_items_per_tile;
+        if ((s = ensure(fr.lmask, by)) != SG_OK) return s;
+        fr.lmask_stride = K;
+        s = lidar_tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err, pv[pb],
+                              (const float4 *)fr.rect.p, L, (uint32_t *)fr.lmask.p);
     } else {   // camera lists also get their sub-block masks
         if ((s = ensure(fr.submask, K > 0 ? (size_t)K : 1)) != SG_OK) return s;
         s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err, pv[pb],
@@ -609,6 +615,9 @@ void sg_destroy_lidar(sg_lidar lidar)
     dev_free(L.d_item_rays);
     dev_free(L.d_ray_e);
     dev_free(L.d_tile_u);
+    dev_free(L.d_tile_items);
+    dev_free(L.d_item_az);
+    dev_free(L.d_item_el);
     delete lidar;
 }
 
@@ -643,6 +652,13 @@ void sg_frame_destroy(sg_frame frame)
     if (f.ev_copied) cudaEventDestroy(f.ev_copied);
     if (f.copy_st) cudaStreamDestroy(f.copy_st);
     delete frame;
+}
+
+sg_status sg_frame_set_backward_state(sg_frame frame, int keep)
+{
+    if (!frame) { set_error("frame is NULL"); return SG_ERR_INVALID; }
+    frame->f.keep_state = keep != 0;
+    return SG_OK;
 }
 
 sg_status sg_frame_set_timing(sg_frame frame, int on)
@@ -975,8 +991,8 @@ sg_status sg_workspace_bytes(sg_scene scene, int sensor_kind, int64_t n_rays, si
     // per ray: state, features, contributor count; per unit: ranges, order
     b += grown(16 * (size_t)nr) * 2 + grown(4 * (size_t)nr);
     b += grown(8 * (size_t)units) + grown(4 * (size_t)units);
-    // pairs: keys and ids (x2), camera sub-block masks
-    b += 4 * grown(4 * (size_t)K) + (cam ? grown((size_t)K) : 0);
+    // pairs: keys and ids (x2), camera sub-block masks or LiDAR ray masks
+    b += 4 * grown(4 * (size_t)K) + (cam ? grown((size_t)K) : grown(4 * (size_t)K * per_tile));
     // sort scratch: the larger of the depth stage's and the tile sort's
     const int64_t hd = depth_stage_words(n), ht = radix_scratch_words(K, 3);
     b += grown(4 * (size_t)(hd > ht ? hd : ht));
@@ -1037,6 +1053,11 @@ sg_status sg_backward_camera(sg_scene scene, sg_frame frame, const float *d_g_rg
         set_error("sg_backward_camera: the frame's last render is not a camera render of this scene");
         return SG_ERR_INVALID;
     }
+    if (!f.state_kept) {
+        set_error("sg_backward_camera: the frame kept no state for the backward "
+                  "(sg_frame_set_backward_state)");
+        return SG_ERR_INVALID;
+    }
     return backward_camera(scene->s, ((sg_camera)f.sensor)->c, f, d_g_rgb, d_g_alpha, d_g_depth,
                            *grads, (cudaStream_t)stream);
 }
@@ -1049,6 +1070,11 @@ sg_status sg_backward_lidar(sg_scene scene, sg_frame frame, const float *d_g_ran
     Frame &f = frame->f;
     if (f.kind != 1 || f.scene != scene) {
         set_error("sg_backward_lidar: the frame's last render is not a LiDAR render of this scene");
+        return SG_ERR_INVALID;
+    }
+    if (!f.state_kept) {
+        set_error("sg_backward_lidar: the frame kept no state for the backward "
+                  "(sg_frame_set_backward_state)");
         return SG_ERR_INVALID;
     }
     return backward_lidar(scene->s, ((sg_lidar)f.sensor)->l, f, d_g_range, d_g_intensity,

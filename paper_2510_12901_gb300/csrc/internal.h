@@ -144,6 +144,9 @@ struct Lidar {
     uint32_t *d_item_rays = nullptr;  // [n_items*32]: beam*n_cols + col, ~0u = none
     float4 *d_ray_e = nullptr;      // [n_beams*n_cols] sensor dir minus tile reference
     double *d_tile_u = nullptr;     // [ntiles*3] tile reference sensor direction
+    uint2 *d_tile_items = nullptr;  // [ntiles] (first item, number of items) of each tile
+    float *d_item_az = nullptr;     // [n_items*32] azimuth of each ray slot (deg, NaN: none)
+    float *d_item_el = nullptr;     // [n_items*32] elevation of each ray slot
 };
 
 // ------------------------------------------------------------------ records
@@ -179,8 +182,10 @@ struct Frame {
     Buf rec, rect, tiles, depth, count, mean2d, cov2d;
     // depth sort / offsets
     Buf dkeys[2], dvals[2], offsets, hist;
-    // pairs
-    Buf pkeys[2], pvals[2], ranges, order, submask;
+    // pairs; LiDAR: per (work item of the pair's tile, pair) the 32-bit mask
+    // of the item's rays inside the Gaussian's box, planes of lmask_stride
+    Buf pkeys[2], pvals[2], ranges, order, submask, lmask;
+    int64_t lmask_stride = 0;
     // camera work items: per-tile (segments, first partial slot), items,
     // arrival counters of long tiles; per-pixel partials of their segments
     Buf camwork, partials;
@@ -201,6 +206,8 @@ struct Frame {
     // step waits for the pair count (pairs beyond it are dropped and counted)
     int64_t k_cap = 0;
     uint32_t seg_len = kSegLen;     // camera list segment length
+    bool keep_state = true;         // renders write the per-ray state the backward needs
+    bool state_kept = false;        // the last render did
     int64_t n_pairs = 0, n_tiles = 0, n_rays = 0, n_gauss = 0;
     int pair_buf = 0;  // which of pkeys/pvals holds the sorted result
     int depth_buf = 0; // which of dkeys/dvals holds the depth-sorted Gaussians
@@ -330,6 +337,13 @@ sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max
                       int64_t ntiles, cudaStream_t st, const uint32_t *d_err,
                       const uint32_t *d_ids = nullptr, const float4 *d_rects = nullptr,
                       int ntx = 0, uint8_t *d_mask = nullptr);
+// LiDAR lists: ranges, and for every pair and every work item of its tile
+// the item's rays inside the Gaussian's extent box (lmask[k * K_max + i]
+// for the k-th item of the tile, by the compositing's own float test).
+sg_status lidar_tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max,
+                            uint2 *d_ranges, int64_t ntiles, cudaStream_t st,
+                            const uint32_t *d_err, const uint32_t *d_ids,
+                            const float4 *d_rects, const Lidar &L, uint32_t *d_lmask);
 sg_status clamp_pairs(uint32_t *d_K, int64_t cap, uint32_t *d_dropped, cudaStream_t st);
 
 // project.cu
@@ -369,7 +383,8 @@ template <class Fn> inline void for_each_buf(Frame &f, Fn fn)
 {
     Buf *bufs[] = {&f.rec, &f.rect, &f.tiles, &f.depth, &f.count, &f.mean2d, &f.cov2d,
                    &f.dkeys[0], &f.dkeys[1], &f.dvals[0], &f.dvals[1], &f.offsets, &f.hist,
-                   &f.pkeys[0], &f.pkeys[1], &f.pvals[0], &f.pvals[1], &f.ranges, &f.order, &f.submask, &f.camwork,
+                   &f.pkeys[0], &f.pkeys[1], &f.pvals[0], &f.pvals[1], &f.ranges, &f.order, &f.submask,
+                   &f.lmask, &f.camwork,
                    &f.partials, &f.ray_state, &f.n_contrib, &f.ray_feat, &f.gacc, &f.scalars,
                    &f.desc, &f.host_stage[0], &f.host_stage[1], &f.host_stage[2]};
     for (Buf *b : bufs) fn(*b);

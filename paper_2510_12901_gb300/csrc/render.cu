@@ -32,6 +32,14 @@
 
 namespace sg {
 
+// Per-ray state for the backward, written only by frames that keep it.
+static float4 *saved_state(Frame &fr) { return fr.keep_state ? (float4 *)fr.ray_state.p : nullptr; }
+static float4 *saved_feat(Frame &fr) { return fr.keep_state ? (float4 *)fr.ray_feat.p : nullptr; }
+static uint32_t *saved_contrib(Frame &fr)
+{
+    return fr.keep_state ? (uint32_t *)fr.n_contrib.p : nullptr;
+}
+
 // Exclusive sum over a block of 1024 threads; every thread calls it.
 __device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *s_w, uint32_t &total)
 {
@@ -455,9 +463,11 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
             }
             if (out_alpha) out_alpha[pidx] = a.W;
             if (out_depth) out_depth[pidx] = a.W > 0.f ? a.Z / a.W : 0.f;
-            ray_state[pidx] = make_float4(a.T, a.W, a.Z, 0.f);
-            ray_feat[pidx] = make_float4(a.c0, a.c1, a.c2, 0.f);
-            n_contrib[pidx] = a.last;
+            if (ray_state) {   // the state the backward needs (frames that keep it)
+                ray_state[pidx] = make_float4(a.T, a.W, a.Z, 0.f);
+                ray_feat[pidx] = make_float4(a.c0, a.c1, a.c2, 0.f);
+                n_contrib[pidx] = a.last;
+            }
         }
         __syncwarp();
     }
@@ -516,8 +526,8 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     kern<<<(unsigned)grid, 32 * kCamWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
         (const uint8_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
-        cam.d_tile_dir, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
-        (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
+        cam.d_tile_dir, (const RenderDesc *)fr.desc.p, saved_state(fr),
+        saved_feat(fr), saved_contrib(fr));
     SG_LAUNCHED();
     return SG_OK;
 }
@@ -706,9 +716,11 @@ k_render_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *__
             }
             if (out_alpha) out_alpha[pidx] = a.W;
             if (out_depth) out_depth[pidx] = a.W > 0.f ? a.Z / a.W : 0.f;
-            ray_state[pidx] = make_float4(a.T, a.W, a.Z, 0.f);
-            ray_feat[pidx] = make_float4(a.c0, a.c1, a.c2, 0.f);
-            n_contrib[pidx] = a.last;
+            if (ray_state) {   // the state the backward needs (frames that keep it)
+                ray_state[pidx] = make_float4(a.T, a.W, a.Z, 0.f);
+                ray_feat[pidx] = make_float4(a.c0, a.c1, a.c2, 0.f);
+                n_contrib[pidx] = a.last;
+            }
         }
         __syncwarp();
     }
@@ -754,8 +766,8 @@ sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr
     k_render_camera_rs<kSegLen><<<(unsigned)grid, 32 * kCamWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
         (const uint8_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
-        cam.d_tile_dir, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
-        (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
+        cam.d_tile_dir, (const RenderDesc *)fr.desc.p, saved_state(fr),
+        saved_feat(fr), saved_contrib(fr));
     SG_LAUNCHED();
     return SG_OK;
 }
@@ -769,20 +781,20 @@ sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr
 // slice with their per-column moments.
 
 // Per-warp shared state of a LiDAR work item: staged entries, their ray
-// masks and list positions, and the item's ray angles (NaN: no ray).
+// masks and list positions.
 struct LidStage {
     float4 (*s)[32];
     uint32_t *lanes, *pos;
-    float *raz, *rel;
 };
 
-// Composite entries [lo, hi) of the item's list (first entry `begin`): a
-// window of 32 entries is tested against the item's 32 rays (lidar_lanes),
-// only entries that reach a ray still compositing are staged, and each is
-// evaluated for the rays in its mask.  Returns whether the lane's ray
-// stopped at T_min.
+// Composite entries [lo, hi) of the item's list (first entry `begin`): the
+// item's ray masks of a window of 32 entries (written with the tile ranges,
+// lmask[i] for list entry i) select the entries that reach a ray still
+// compositing; only those are staged, and each is evaluated for the rays in
+// its mask.  Returns whether the lane's ray stopped at T_min.
 __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__restrict__ rec,
                                            const uint32_t *__restrict__ ids,
+                                           const uint32_t *__restrict__ lmask,
                                            const float *__restrict__ poses, const LidarItem &it,
                                            int sb, const float dh[3], const float dl[3],
                                            const float dd[3], const float d[3], uint32_t lo,
@@ -791,19 +803,24 @@ __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__res
 {
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
-    // the next batch's ids, loaded one batch ahead
-    uint32_t nid = lo + lane < hi ? ids[lo + lane] : 0u;
+    // the next batch's ray masks and ids, loaded one batch ahead
+    uint32_t nm = 0u, nid = 0u;
+    if (lo + lane < hi) {
+        nm = lmask[lo + lane];
+        nid = ids[lo + lane];
+    }
     for (uint32_t base = lo; base < hi; base += 32) {
         // only entries that reach a ray still compositing
         const uint32_t act = __ballot_sync(0xffffffffu, !done);
         if (act == 0u) break;
         const uint32_t idx = base + lane;
         const uint32_t g = nid;
-        if (idx + 32 < hi) nid = ids[idx + 32];
-        uint32_t m = 0u;
-        if (idx < hi) {
-            const float4 rc = rec[g].rect;
-            m = lidar_lanes(rc.x, rc.y, rc.z, rc.w, L.raz, L.rel) & act;
+        const uint32_t m = nm & act;
+        if (idx + 32 < hi) {
+            nm = lmask[idx + 32];
+            nid = ids[idx + 32];
+        } else {
+            nm = 0u;
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, m != 0u);
         if (bal == 0u) continue;
@@ -851,8 +868,9 @@ template <bool kFix>
 __global__ void __launch_bounds__(32 * kLidarWarps)
 k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
                const uint32_t *__restrict__ item_rays, const float4 *__restrict__ ray_e,
-               const double *__restrict__ item_u, const float *__restrict__ az_col,
-               const float *__restrict__ elev, const GRec *__restrict__ rec,
+               const double *__restrict__ item_u, const uint2 *__restrict__ tile_items,
+               const uint32_t *__restrict__ lmask, int64_t lmask_stride,
+               const GRec *__restrict__ rec,
                const uint32_t *__restrict__ ids, const uint2 *__restrict__ ranges,
                const uint2 *__restrict__ work, const uint2 *__restrict__ unit_info,
                const uint32_t *__restrict__ counts, uint32_t *__restrict__ counter,
@@ -862,9 +880,8 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
 {
     __shared__ float4 s_all[kLidarWarps][kLidPlanes][32];
     __shared__ uint32_t s_lanes[kLidarWarps][32], s_pos[kLidarWarps][32];
-    __shared__ float s_raz[kLidarWarps][32], s_rel[kLidarWarps][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const LidStage stg = {s_all[wib], s_lanes[wib], s_pos[wib], s_raz[wib], s_rel[wib]};
+    const LidStage stg = {s_all[wib], s_lanes[wib], s_pos[wib]};
     const float *__restrict__ poses = D->poses;
     const uint32_t n_work = kFix ? *F.n_fix : counts[0];
     uint32_t fix_next = blockIdx.x * kLidarWarps + wib;
@@ -891,13 +908,11 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
         const uint32_t ray = item_rays[it.ray_off + lane];
         const bool valid = ray != 0xffffffffu;
         const int c = valid ? (int)(ray % (uint32_t)P.n_cols) : it.col0;
-        const int b = valid ? (int)(ray / (uint32_t)P.n_cols) : 0;
         const int sb = 3 + 4 * (c - it.col0);
         float dh[3], dl[3], dd[3], d[3];
         lidar_ray(it, item_u, item_id, poses, ray_e[it.ray_off + lane], c, dh, dl, dd, d);
-        stg.raz[lane] = valid ? az_col[c] : __int_as_float(0x7fc00000);
-        stg.rel[lane] = valid ? elev[b] : __int_as_float(0x7fc00000);
-        __syncwarp();
+        // this item's plane of ray masks
+        const uint32_t *lm = lmask + (int64_t)(item_id - (int)tile_items[it.tile].x) * lmask_stride;
         const uint2 rg = ranges[it.tile];
         const uint32_t lo = rg.x + seg * kSegLen;
         const uint32_t hi = min(rg.y, lo + kSegLen);
@@ -907,11 +922,11 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
             const bool mine = (fix_lanes >> lane) & 1u;
             const float4 *pq = partials + ((size_t)(ui.y + seg) * 32 + lane) * 2;
             if (mine) a = get_state(pq[0], pq[1]);
-            lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, lo, hi, rg.x, stg, a, !mine);
+            lidar_walk(P, rec, ids, lm, poses, it, sb, dh, dl, dd, d, lo, hi, rg.x, stg, a, !mine);
             write = mine;
         } else {
-            const bool stopped = lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, lo, hi,
-                                            rg.x, stg, a, !valid);
+            const bool stopped = lidar_walk(P, rec, ids, lm, poses, it, sb, dh, dl, dd, d, lo,
+                                            hi, rg.x, stg, a, !valid);
             if (ui.x > 1) {
                 // split item: publish this segment, and combine if it is the last one
                 put_state(partials + ((size_t)(ui.y + seg) * 32 + lane) * 2, a, stopped);
@@ -952,7 +967,7 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
                     if (rl && n_inline < kLidarInlineRewalks) {
                         ++n_inline;
                         const uint32_t l0 = rg.x + sgi * kSegLen;
-                        lidar_walk(P, rec, ids, poses, it, sb, dh, dl, dd, d, l0,
+                        lidar_walk(P, rec, ids, lm, poses, it, sb, dh, dl, dd, d, l0,
                                    min(rg.y, l0 + kSegLen), rg.x, stg, a, !redo);
                     } else if (rl) {
                         push_fix(F, (uint32_t)item_id, sgi, rl);
@@ -970,9 +985,11 @@ k_render_lidar(LidRender P, const LidarItem *__restrict__ items,
             if (out_int) out_int[ray] = a.c0;
             if (out_drop) out_drop[ray] = drop;
             if (out_alpha) out_alpha[ray] = a.W;
-            ray_state[ray] = make_float4(a.T, a.W, a.Z, drop);
-            ray_feat[ray] = make_float4(a.c0, a.c1, a.c2, 0.f);
-            n_contrib[ray] = a.last;
+            if (ray_state) {   // the state the backward needs (frames that keep it)
+                ray_state[ray] = make_float4(a.T, a.W, a.Z, drop);
+                ray_feat[ray] = make_float4(a.c0, a.c1, a.c2, 0.f);
+                n_contrib[ray] = a.last;
+            }
         }
         __syncwarp();
     }
@@ -1019,21 +1036,23 @@ sg_status render_lidar(const Lidar &L, const sg_render_opts &o, Frame &fr, cudaS
     if (grid < 1) grid = 1;
     const FixList F = fix_list(fr, ws);
     k_render_lidar<false><<<(unsigned)grid, 32 * kLidarWarps, 0, st>>>(
-        P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, L.d_az, L.d_elev,
+        P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, L.d_tile_items,
+        (const uint32_t *)fr.lmask.p, fr.lmask_stride,
         (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, work, unit_info,
         (const uint32_t *)fr.scalars.p + 4, (uint32_t *)fr.scalars.p + 2, arrive,
-        (float4 *)fr.partials.p, F, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
-        (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
+        (float4 *)fr.partials.p, F, (const RenderDesc *)fr.desc.p, saved_state(fr),
+        saved_feat(fr), saved_contrib(fr));
     SG_LAUNCHED();
     if (ws.max_slots > 0) {       // some item may be split: the deferred re-walks
         const int64_t fcap = (ws.max_fixes + kLidarWarps - 1) / kLidarWarps;
         const int64_t fgrid = grid < fcap ? grid : fcap;
         k_render_lidar<true><<<(unsigned)fgrid, 32 * kLidarWarps, 0, st>>>(
-            P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, L.d_az, L.d_elev,
+            P, L.d_items, L.d_item_rays, L.d_ray_e, L.d_tile_u, L.d_tile_items,
+            (const uint32_t *)fr.lmask.p, fr.lmask_stride,
             (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, work, unit_info,
             (const uint32_t *)fr.scalars.p + 4, (uint32_t *)fr.scalars.p + 2, arrive,
-            (float4 *)fr.partials.p, F, (const RenderDesc *)fr.desc.p, (float4 *)fr.ray_state.p,
-            (float4 *)fr.ray_feat.p, (uint32_t *)fr.n_contrib.p);
+            (float4 *)fr.partials.p, F, (const RenderDesc *)fr.desc.p, saved_state(fr),
+            saved_feat(fr), saved_contrib(fr));
         SG_LAUNCHED();
     }
     return SG_OK;

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <limits>
+
 #include "internal.h"
 
 namespace sg {
@@ -329,13 +331,25 @@ sg_status build_lidar(Lidar &L)
         }
     }
     L.n_items = (int)items.size();
-    {
-        // a tile wider than kLidarColsMax columns or holding more than 32
-        // rays gives several items, each walking the tile's whole list
-        std::vector<int> per_tile((size_t)nphi * L.n_theta, 0);
-        int mx = 1;
-        for (const LidarItem &it : items) mx = std::max(mx, ++per_tile[it.tile]);
-        L.max_items_per_tile = mx;
+    // a tile wider than kLidarColsMax columns or holding more than 32 rays
+    // gives several items, each walking the tile's whole list; the items of
+    // a tile are consecutive (first item, count per tile)
+    std::vector<uint2> tile_items((size_t)nphi * L.n_theta, make_uint2(0u, 0u));
+    for (size_t i = 0; i < items.size(); ++i) {
+        uint2 &ti = tile_items[items[i].tile];
+        if (ti.y == 0) ti.x = (uint32_t)i;
+        ++ti.y;
+    }
+    L.max_items_per_tile = 1;
+    for (const uint2 &ti : tile_items) L.max_items_per_tile = std::max(L.max_items_per_tile, (int)ti.y);
+    // per item, the azimuth and elevation of each of its 32 ray slots (NaN:
+    // no ray), for the per-entry ray masks of the tile ranges kernel
+    std::vector<float> item_az(items.size() * 32), item_el(items.size() * 32);
+    const float qnan = std::numeric_limits<float>::quiet_NaN();
+    for (size_t i = 0; i < rays.size(); ++i) {
+        const uint32_t ray = rays[i];
+        item_az[i] = ray == 0xffffffffu ? qnan : az[ray % (uint32_t)nc];
+        item_el[i] = ray == 0xffffffffu ? qnan : L.elev[ray / (uint32_t)nc];
     }
 
 #define SG_ALLOC_COPY(dst, vec)                                                         \
@@ -355,6 +369,9 @@ sg_status build_lidar(Lidar &L)
     SG_ALLOC_COPY(L.d_item_rays, rays);
     SG_ALLOC_COPY(L.d_ray_e, ray_e);
     SG_ALLOC_COPY(L.d_tile_u, item_u);
+    SG_ALLOC_COPY(L.d_tile_items, tile_items);
+    SG_ALLOC_COPY(L.d_item_az, item_az);
+    SG_ALLOC_COPY(L.d_item_el, item_el);
 #undef SG_ALLOC_COPY
     return SG_OK;
 }

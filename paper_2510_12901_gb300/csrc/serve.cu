@@ -381,6 +381,7 @@ sg_status sg_server_create(const sg_server_config *cfg, sg_server *out)
         S->streams.push_back(st);
         sg_frame f = nullptr;
         sg_frame_create(&f);
+        if (f) f->f.keep_state = false;   // no backward follows a served render
         S->frames.push_back(f);
     }
     for (int i = 0; i < cfg->n_slots; ++i) S->workers.emplace_back(worker_main, S, i);

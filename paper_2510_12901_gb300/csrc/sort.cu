@@ -14,7 +14,7 @@
 //   6. per-tile [start, end) ranges.
 // Sorting the N Gaussians by depth once and the K pairs by tile alone moves
 // 2 passes over K instead of the 6 a 64-bit (tile, depth) key needs.
-#include "internal.h"
+#include "pairs.cuh"
 
 namespace sg {
 
@@ -640,6 +640,47 @@ sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max
     else
         k_ranges<false><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, nullptr, nullptr, 0, nullptr,
                                               d_err);
+    SG_LAUNCHED();
+    return SG_OK;
+}
+
+// LiDAR lists: per-tile ranges, and per pair the ray masks of the work
+// items of its tile (k-th item of the tile: lmask[k * K_max + i]), by the
+// same float comparisons (lidar_lanes) as the compositing's per-ray test,
+// so that the compositing walks skip entries that reach none of their rays
+// without loading their records.
+__global__ void k_ranges_lidar(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
+                               int64_t K_max, uint2 *__restrict__ ranges,
+                               const uint32_t *__restrict__ ids, const float4 *__restrict__ rects,
+                               const uint2 *__restrict__ tile_items,
+                               const float *__restrict__ item_az,
+                               const float *__restrict__ item_el, uint32_t *__restrict__ lmask,
+                               const uint32_t *__restrict__ err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t K = *d_K;
+    if (i >= K || *err) return;
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
+    if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const float4 rc = rects[ids[i]];
+    const uint2 ti = tile_items[t];
+    for (uint32_t k = 0; k < ti.y; ++k) {
+        const size_t it = (size_t)(ti.x + k) * 32;
+        lmask[(int64_t)k * K_max + i] = lidar_lanes(rc.x, rc.y, rc.z, rc.w, item_az + it, item_el + it);
+    }
+}
+
+sg_status lidar_tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max,
+                            uint2 *d_ranges, int64_t ntiles, cudaStream_t st,
+                            const uint32_t *d_err, const uint32_t *d_ids,
+                            const float4 *d_rects, const Lidar &L, uint32_t *d_lmask)
+{
+    SG_CUDA(cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * ntiles, st));
+    if (K_max == 0) return SG_OK;
+    k_ranges_lidar<<<(unsigned)((K_max + 255) / 256), 256, 0, st>>>(
+        d_keys, d_K, K_max, d_ranges, d_ids, d_rects, L.d_tile_items, L.d_item_az, L.d_item_el,
+        d_lmask, d_err);
     SG_LAUNCHED();
     return SG_OK;
 }

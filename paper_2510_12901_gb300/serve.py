@@ -218,6 +218,7 @@ def measure_serving(n_requests=300, loads=(0.5, 0.8, 1.0, 1.2, 2.0), n_slots=4, 
     import torch
     W = ServingWorkload(n_requests=n_requests, seed=seed, **kw)
     frame = sg.Frame()
+    sg.sg_frame_set_backward_state(frame.handle, 0)   # forward renders only, as the server's
     stream = torch.cuda.current_stream().cuda_stream
     for i in range(min(8, n_requests)):                 # warm the frame up
         W.render_plain(i, frame, stream)

@@ -138,6 +138,7 @@ _SIGNATURES = {
     "sg_frame_marks": (C.c_int, [_H, _H, C.POINTER(C.c_float)]),
     "sg_frame_sync_outputs": (C.c_int, [_H]),
     "sg_frame_status": (C.c_int, [_H, _P]),
+    "sg_frame_set_backward_state": (C.c_int, [_H, C.c_int]),
     "sg_alloc_count": (C.c_int64, []),
     "sg_workspace_bytes": (C.c_int, [_H, C.c_int, C.c_int64, C.POINTER(C.c_size_t)]),
     "sg_frame_workspace_bytes": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
@@ -394,6 +395,10 @@ def sg_frame_timing(frame):
 
 def sg_frame_sync_outputs(frame):
     _check(load().sg_frame_sync_outputs(frame))
+
+
+def sg_frame_set_backward_state(frame, keep):
+    _check(load().sg_frame_set_backward_state(frame, int(bool(keep))))
 
 
 def sg_frame_status(frame, stream=0):

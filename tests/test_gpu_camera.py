@@ -38,6 +38,10 @@ def gpu_render(sg, sc, cam, opts=None, scene=None):
 
 
 def check_projection(sg, fr, sc, cam, O32, O64, label):
+    """Every Gaussian: box edges within the rounding band of the float32
+    oracle's, tile count and range equal except where an edge lies within
+    that band of a tile boundary (at most 0.01% of the Gaussians), sort
+    keys within 2 float32 ulps."""
     P32, (ntx, nty) = O32.project_camera(sc, cam)
     P64, _ = O64.project_camera(sc, cam)
     count = fr.field(sg.FIELD_COUNT, np.uint32)
@@ -45,29 +49,26 @@ def check_projection(sg, fr, sc, cam, O32, O64, label):
     rect = fr.field(sg.FIELD_RECT, np.float32, 4)
     key = fr.field(sg.FIELD_DEPTH, np.float32)
     amb, band = par.tile_ambiguous_camera(P32, P64, cam.width, cam.height)
-    ok = ~amb
-    assert amb.mean() < 5e-3, (label, amb.sum())
-    # box edges of every Gaussian the UT projected agree within half the band
-    v = ok & (P64["ut"] == 1)
+    v = (P64["ut"] == 1) & (P32["ut"] == 1)
     d = np.abs(rect[v].astype(np.float64) - P32["rect"][v])
     assert np.all(d <= band[v]), (label, d.max(), (d / band[v]).max())
-    o_count = np.where(P32["valid"] == 1, P32["count"], 0)
-    assert np.array_equal(count[ok], o_count[ok]), label
-    v = ok & (o_count > 0)
-    assert np.array_equal(tiles[v], P32["tiles"][v]), label
-    assert np.allclose(key, P32["depth"], rtol=5e-7, atol=0), label
-    return P32, amb, key, (ntx, nty)
+    mism = par.range_mismatch(count, tiles, P32)
+    assert not (mism & ~amb).any(), (label, np.nonzero(mism & ~amb)[0][:10])
+    assert mism.mean() <= par.MAX_RANGE_MISMATCH, (label, int(mism.sum()))
+    binned = (count > 0) | (P32["valid"] == 1)
+    ku = par.key_ulps(key[binned], P32["depth"][binned])
+    assert ku.max() <= par.MAX_KEY_ULPS, (label, int(ku.max()))
+    return P32, mism, key, (ntx, nty)
 
 
-def check_lists(sg, fr, P32, amb, key, ntx, nty, O32, tiles, label):
-    ids = fr.field(sg.FIELD_PAIR_IDS, np.uint32)
-    ranges = fr.field(sg.FIELD_RANGES, np.uint32, 2)
-    o_ids, o_tiles, o_ranges = O32.bin_sort(P32, ntx, nty, False)
-    n = par.compare_lists(ids, ranges, o_ids, o_ranges, tiles, amb, key, label)
-    assert n > 0
-    # the pair count differs from the oracle's only through ambiguous Gaussians
-    o_cnt = np.where(P32["valid"] == 1, P32["count"], 0)
-    assert abs(len(ids) - len(o_ids)) <= int(o_cnt[amb].sum()) + 0
+def check_lists(sg, fr, sc, P32, mism, ntx, nty, O32, label):
+    """Policy (i) on every tile, and the pair count against the oracle's
+    own lists: equal up to the tiles of the Gaussians whose ranges differ."""
+    K = par.rebin_exact(O32, sg, fr, sc.n, ntx, nty, False, label)
+    assert K > 0
+    o_count = np.where(P32["valid"] == 1, P32["count"], 0).astype(np.int64)
+    g_count = fr.field(sg.FIELD_COUNT, np.uint32).astype(np.int64)
+    assert K - o_count.sum() == (g_count - o_count)[mism].sum(), label
 
 
 # ---------------------------------------------------------------- tiny cube
@@ -78,8 +79,8 @@ def test_tiny_scene_every_pixel_and_list(sg, O32, O64):
     info = par.compare_camera_rays(g["rgb"].reshape(-1, 3), g["alpha"].reshape(-1),
                                    g["depth"].reshape(-1), orc, label="tiny")
     assert info["excluded"] <= 0.01 * len(orc)
-    P32, amb, key, (ntx, nty) = check_projection(sg, g["frame"], sc, cam, O32, O64, "tiny")
-    check_lists(sg, g["frame"], P32, amb, key, ntx, nty, O32, range(ntx * nty), "tiny")
+    P32, mism, key, (ntx, nty) = check_projection(sg, g["frame"], sc, cam, O32, O64, "tiny")
+    check_lists(sg, g["frame"], sc, P32, mism, ntx, nty, O32, "tiny")
     # the saved state for the backward pass: T_final and omega = 1 - T_final
     st = g["frame"].field(sg.FIELD_RAY_STATE, np.float32, 4)
     assert np.allclose(1.0 - st[:, 0], g["alpha"].reshape(-1), atol=2e-6)
@@ -179,10 +180,11 @@ def test_long_lists_composited_in_segments(sg, O64):
     per_seg = np.bincount(seg[stopped], minlength=32)
     assert per_seg[0] >= 500 and (per_seg[1:] >= 20).sum() >= 20, per_seg
     assert (~stopped & (visited > SEG_LEN)).sum() >= 500
-    # thousands of threshold decisions per ray: ~6.5% of the rays see one
-    # within rounding of its threshold (alpha_min, box edge, T_min)
+    # thousands of threshold decisions per ray: 6.5% of the rays see one
+    # within rounding of its threshold (3.1% alpha_min, 3.3% a box edge,
+    # 0.1% T_min)
     par.compare_camera_rays(g["rgb"].reshape(-1, 3), g["alpha"].reshape(-1),
-                            g["depth"].reshape(-1), orc, max_excluded=0.08, label="layered")
+                            g["depth"].reshape(-1), orc, max_excluded=0.07, label="layered")
     ok = ~par.ambiguous_rays(orc)
     st = g["frame"].field(sg.FIELD_RAY_STATE, np.float32, 4)
     assert np.abs(st[ok, 0] - orc["t_final"][ok]).max() <= par.TOL_ABS
@@ -191,6 +193,32 @@ def test_long_lists_composited_in_segments(sg, O64):
     last = g["frame"].field(sg.FIELD_N_CONTRIB, np.uint32).astype(np.int64)
     assert np.all(last[ok & stopped] < visited[ok & stopped])
     assert np.all(last <= lens[tile])
+
+
+def test_forward_only_frame_renders_the_same_and_refuses_the_backward(sg):
+    import torch
+    sc, cam = syn.tiny_scene(), syn.tiny_camera()
+    a = gpu_render(sg, sc, cam)
+    fr = sg.Frame()
+    sg.sg_frame_set_backward_state(fr.handle, 0)
+    b = sg.render_camera(a["scene"], a["cam"], cam.c2w, frame=fr)
+    torch.cuda.synchronize()
+    for k in ("rgb", "alpha", "depth"):
+        assert np.array_equal(a[k], b[k].cpu().numpy()), k
+    n = cam.width * cam.height
+    grads = {k: torch.zeros(s, device="cuda") for k, s in
+             (("m", (sc.n, 3)), ("l", (sc.n, 3)), ("q", (sc.n, 4)), ("o", (sc.n,)), ("f", (sc.n, 3)))}
+    gs = sg.sg_grads(*[t.data_ptr() for t in grads.values()])
+    up = torch.zeros(n * 3, device="cuda")
+    with pytest.raises(sg.SimgutError) as e:
+        sg.sg_backward_camera(a["scene"].handle, fr.handle, up.data_ptr(), None, None, gs,
+                              torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == -1 and "kept no state" in str(e.value)
+    sg.sg_frame_set_backward_state(fr.handle, 1)       # back on: the backward runs
+    sg.render_camera(a["scene"], a["cam"], cam.c2w, frame=fr)
+    sg.sg_backward_camera(a["scene"].handle, fr.handle, up.data_ptr(), None, None, gs,
+                          torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
 
 
 def test_repeated_renders_are_deterministic(sg):
@@ -235,10 +263,8 @@ def test_street_scene_sampled_parity(sg, O32, O64, street, which):
     # the sample includes the three densest tiles (up to ~20k entries): a few
     # per cent of their rays see a decision within rounding of its threshold
     info = par.compare_camera_rays(g["rgb"].reshape(-1, 3)[rays], g["alpha"].reshape(-1)[rays],
-                                   g["depth"].reshape(-1)[rays], orc, max_excluded=0.02,
+                                   g["depth"].reshape(-1)[rays], orc, max_excluded=0.01,
                                    label=which)
     assert (orc["alpha"] > 0.5).mean() > 0.3, info     # the sample sees the scene
-    P32, amb, key, (ntx, nty) = check_projection(sg, g["frame"], sc, cam, O32, O64, which)
-    rng = np.random.default_rng(1)
-    tiles = rng.choice(ntx * nty, 200, replace=False)
-    check_lists(sg, g["frame"], P32, amb, key, ntx, nty, O32, tiles, which)
+    P32, mism, key, (ntx, nty) = check_projection(sg, g["frame"], sc, cam, O32, O64, which)
+    check_lists(sg, g["frame"], sc, P32, mism, ntx, nty, O32, which)

@@ -49,6 +49,12 @@ def test_tiling_matches_oracle(sg, O64):
 
 
 def check_projection(sg, fr, sc, L, O32, O64, label):
+    """Every Gaussian: box edges within the rounding band, tile count and
+    range equal except where a box edge lies within that band of a tile or
+    culling-cell boundary or a sigma point's column choice is within
+    rounding (at most 0.01% of the Gaussians), sort keys within 2 float32
+    ulps except where the mean's own column choice is within rounding (the
+    key is the distance to that column's origin)."""
     P32, (nth, nphi) = O32.project_lidar(sc, L)
     P64, _ = O64.project_lidar(sc, L)
     S = O32.lidar_setup(L)
@@ -58,20 +64,24 @@ def check_projection(sg, fr, sc, L, O32, O64, label):
     rect = fr.field(sg.FIELD_RECT, np.float32, 4)
     amb, band = par.tile_ambiguous_lidar(P32, P64, S["T"], nth, L.az0_deg, L.cull_az,
                                          L.cull_el_per_tile)
-    ok = ~amb
-    # 14 column-pose decisions per Gaussian make ~1% of them ambiguous
-    assert amb.mean() < 2e-2, (label, amb.sum())
-    v = ok & (P64["ut"] == 1)
+    pose = (P64["ut"] == 1) & (P64["pmargin"] < par.MARGIN_POSE_COLS)
+    v = (P64["ut"] == 1) & (P32["ut"] == 1) & ~pose
     d = np.abs(rect[v].astype(np.float64) - P32["rect"][v])
     assert np.all(d <= band[v]), (label, d.max(), (d / band[v]).max())
-    o_count = np.where(P32["valid"] == 1, P32["count"], 0)
-    assert np.array_equal(count[ok], o_count[ok]), (label, np.nonzero(count[ok] != o_count[ok]))
-    v = ok & (o_count > 0)
-    assert np.array_equal(tiles[v], P32["tiles"][v]), label
-    # the key is the distance to the origin of the centre's column: compared
-    # where that column choice is not ambiguous and the Gaussian is binned
-    assert np.allclose(key[v], P32["depth"][v], rtol=5e-7, atol=0), label
-    return P32, amb, key, nth, nphi
+    mism = par.range_mismatch(count, tiles, P32)
+    assert not (mism & ~amb).any(), (label, np.nonzero(mism & ~amb)[0][:10])
+    assert mism.mean() <= par.MAX_RANGE_MISMATCH, (label, int(mism.sum()))
+    binned = ((count > 0) | (P32["valid"] == 1)) & ~(P64["cmargin"] < par.MARGIN_POSE_COLS)
+    ku = par.key_ulps(key[binned], P32["depth"][binned])
+    assert ku.max() <= par.MAX_KEY_ULPS, (label, int(ku.max()))
+    return P32, mism, key, nth, nphi
+
+
+def check_lists(sg, fr, sc, P32, mism, nth, nphi, O32, label):
+    K = par.rebin_exact(O32, sg, fr, sc.n, nth, nphi, True, label)
+    o_count = np.where(P32["valid"] == 1, P32["count"], 0).astype(np.int64)
+    g_count = fr.field(sg.FIELD_COUNT, np.uint32).astype(np.int64)
+    assert K - o_count.sum() == (g_count - o_count)[mism].sum(), label
 
 
 @pytest.mark.parametrize("kind", ["lidar", "lidar_sh"])
@@ -84,11 +94,8 @@ def test_toy_sweep_every_ray_and_list(sg, O32, O64, kind):
     info = par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
                                   label="toy")
     assert (orc["n_contrib"] > 0).sum() > 1000, info
-    P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, O64, "toy")
-    ids = g["frame"].field(sg.FIELD_PAIR_IDS, np.uint32)
-    ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)
-    o_ids, _, o_ranges = O32.bin_sort(P32, nth, nphi, True)
-    par.compare_lists(ids, ranges, o_ids, o_ranges, range(nth * nphi), amb, key, "toy")
+    P32, mism, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, O64, "toy")
+    check_lists(sg, g["frame"], sc, P32, mism, nth, nphi, O32, "toy")
 
 
 def test_culling_changes_nothing_but_the_lists(sg):
@@ -148,6 +155,18 @@ def test_ragged_sensor_and_empty_scene(sg, O64):
     assert not e["alpha"].any() and np.all(e["drop"] == 0.5) and not e["range"].any()
 
 
+def test_forward_only_frame_renders_the_same(sg):
+    import torch
+    sc, L = toy(1500, seed=6)
+    a = gpu_render(sg, sc, L)
+    fr = sg.Frame()
+    sg.sg_frame_set_backward_state(fr.handle, 0)
+    b = sg.render_lidar(a["scene"], a["lidar"], L.col_c2w, frame=fr)
+    torch.cuda.synchronize()
+    for k in ("range", "intensity", "drop", "alpha"):
+        assert np.array_equal(a[k], b[k].cpu().numpy().reshape(-1)), k
+
+
 def test_host_output_path_matches_device_path(sg):
     import torch
     sc, L = toy(600, seed=5)
@@ -177,7 +196,7 @@ def test_full_sweep_sampled_parity(sg, O32, O64, beams, kind):
     rng = np.random.default_rng(0)
     rays = np.unique(rng.choice(L.n_beams * L.n_cols, 4000, replace=False))
     orc = O64.render_lidar(sc, L, rays=rays)
-    P32, amb, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, O64, "full")
+    P32, mism, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, O64, "full")
     # rays inside the box of a Gaussian whose column-pose choice is within
     # rounding (its box differs by up to a column's motion between the two)
     P64, _ = O64.project_lidar(sc, L)
@@ -188,14 +207,10 @@ def test_full_sweep_sampled_parity(sg, O32, O64, beams, kind):
     # one within rounding (box or key order), more with 64 beams (two work
     # items per tile, larger per-column motion)
     info = par.compare_lidar_rays(g["range"][rays], g["intensity"][rays], g["drop"][rays],
-                                  g["alpha"][rays], orc, max_excluded=0.02,
+                                  g["alpha"][rays], orc, max_excluded=0.015,
                                   label=f"full-{beams}-{kind}", also_excluded=seen)
     assert (orc["n_contrib"] > 0).mean() > 0.3, info
-    ids = g["frame"].field(sg.FIELD_PAIR_IDS, np.uint32)
-    ranges = g["frame"].field(sg.FIELD_RANGES, np.uint32, 2)
-    o_ids, _, o_ranges = O32.bin_sort(P32, nth, nphi, True)
-    tiles = rng.choice(nth * nphi, 300, replace=False)
-    par.compare_lists(ids, ranges, o_ids, o_ranges, tiles, amb, key, "full")
+    check_lists(sg, g["frame"], sc, P32, mism, nth, nphi, O32, f"full-{beams}-{kind}")
 
 
 def test_gaussians_straddling_the_azimuth_seam(sg, O32, O64):

@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the LiDAR sweep and differentiable-step measurements")
+    ap.add_argument("--only", choices=["lidar"], default=None,
+                    help="run one extra workload alone (for profiling) and print its line")
 
     return ap.parse_args()
 
@@ -172,6 +174,8 @@ def run_ours(args):
     from paper_2510_12901_gb300 import simgut as sg
     from paper_2510_12901_gb300 import synthetic as syn
 
+    if args.only == "lidar":
+        return lidar_workload(torch, sg, syn, args.steps, args.warmup)
     sc = syn.street_scene(N_GAUSS, seed=0, kind="camera")
     fish, pin = syn.street_cameras()
     S = sg.Scene(sc)

@@ -386,7 +386,7 @@ k_backward_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *
                 if (ok) {
                     const float4 m0 = s[0][j], m1 = s[1][j], m2 = s[2][j];
                     const float Mr[9] = {m0.x, m0.y, m0.z, m1.x, m1.y, m1.z, m2.x, m2.y, m2.z};
-                    const float q[3] = {m1.w, m2.w, s[sb + 3][j].w};
+                    const float q[3] = {m1.w, m2.w, lid_u(s, j, sb).w};
                     composite_grads(pe, m0.w, q, gQ, T, U, Ut, Mr, d, gg);
                 }
                 warp_reduce_add16(gg, gacc + (int64_t)s_gid[wib][j] * kG);
@@ -509,7 +509,7 @@ k_backward_lidar(LidRender P, const LidarItem *__restrict__ items,
                 if (ok) {
                     const float4 m0 = s[0][j], m1 = s[1][j], m2 = s[2][j];
                     const float Mr[9] = {m0.x, m0.y, m0.z, m1.x, m1.y, m1.z, m2.x, m2.y, m2.z};
-                    const float q[3] = {m1.w, m2.w, s[sb + 3][j].w};
+                    const float q[3] = {m1.w, m2.w, lid_u(s, j, sb).w};
                     composite_grads(pe, m0.w, q, gQ, T, U, Ut, Mr, d, g);
                 }
                 warp_reduce_add16(g, gacc + (int64_t)s_gid[wib][j] * kG);

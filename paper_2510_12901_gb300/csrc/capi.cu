@@ -616,8 +616,7 @@ void sg_destroy_lidar(sg_lidar lidar)
     dev_free(L.d_ray_e);
     dev_free(L.d_tile_u);
     dev_free(L.d_tile_items);
-    dev_free(L.d_item_az);
-    dev_free(L.d_item_el);
+    dev_free(L.d_item_ray_tab);
     delete lidar;
 }
 

@@ -129,6 +129,17 @@ struct LidarItem {       // one warp of LiDAR rendering
     uint32_t ref_col;    // column whose rotation defines the tile reference ray
 };
 
+// The ray slots of a LiDAR work item, factorised: slot k holds the ray of
+// column col0 + s (bit k of col_bits[s]) and of the beam at elevation
+// beam_el[j] (bit k of beam_bits[j]); empty slots are in no mask.
+struct LidarItemRays {
+    int ncols, nbeams;
+    float col_az[kLidarColsMax];
+    uint32_t col_bits[kLidarColsMax];
+    float beam_el[32];
+    uint32_t beam_bits[32];
+};
+
 struct Lidar {
     int n_beams = 0, n_cols = 0;
     float az0 = 0;
@@ -145,8 +156,7 @@ struct Lidar {
     float4 *d_ray_e = nullptr;      // [n_beams*n_cols] sensor dir minus tile reference
     double *d_tile_u = nullptr;     // [ntiles*3] tile reference sensor direction
     uint2 *d_tile_items = nullptr;  // [ntiles] (first item, number of items) of each tile
-    float *d_item_az = nullptr;     // [n_items*32] azimuth of each ray slot (deg, NaN: none)
-    float *d_item_el = nullptr;     // [n_items*32] elevation of each ray slot
+    LidarItemRays *d_item_ray_tab = nullptr;   // [n_items] factorised ray slots
 };
 
 // ------------------------------------------------------------------ records

@@ -141,12 +141,29 @@ __device__ __forceinline__ uint32_t subblock_lanes(const float4 rc, int x0, int 
 }
 
 // LiDAR entries keep per-column quantities (each column has its own sensor
-// origin o_c), as float4 planes of a warp's shared block s[kLidPlanes][32]:
-//   0: (M row 0, sigma)   1: (M row 1, f0)   2: (M row 2, f1)   (f: features)
-//   per column slot sl, planes 3 + 4 sl ..: (P row k, a_k) for k = 0..2 and
-//   (u = M v, f2), with v = mu - o_c, a = diag(f') M (v x d_T) and P rows
-//   f'_k (M_k x v) as for cameras (f'_k = s_k / (s_i s_j)).
-constexpr int kLidPlanes = 3 + 4 * kLidarColsMax;
+// origin o_c), in a warp's shared block s[kLidPlanes][32] of float4:
+//   planes 0..2, entry j at s[k][j]: (M row 0, sigma), (M row 1, f0),
+//     (M row 2, f1)   (f: features);
+//   then per entry j, quantity k and column slot sl (lid_col): k = 0..2
+//   (P row k, a_k) and k = 3 (u = M v, f2), with v = mu - o_c, a = diag(f')
+//   M (v x d_T) and P rows f'_k (M_k x v) as for cameras (f'_k = s_k /
+//   (s_i s_j)).  The column slots of one (entry, quantity) are adjacent, so
+//   the lanes of a warp, whose rays lie in different columns, read one
+//   entry's quantity without bank conflicts; entries are 17 float4 apart (16
+//   used), so that the lanes staging 32 entries at once write to distinct
+//   banks.
+constexpr int kLidEntryStride = 4 * kLidarColsMax + 1;
+constexpr int kLidPlanes = (3 * 32 + 32 * kLidEntryStride + 31) / 32;   // float4 rows of 32
+
+__device__ __forceinline__ float4 &lid_col(float4 (*s)[32], int j, int k, int sl)
+{
+    return (&s[0][0])[3 * 32 + j * kLidEntryStride + k * kLidarColsMax + sl];
+}
+// the (u, f2) quantity of entry j for the column slot of plane base sb = 3 + 4 sl
+__device__ __forceinline__ float4 lid_u(float4 (*s)[32], int j, int sb)
+{
+    return lid_col(s, j, 3, (sb - 3) >> 2);
+}
 
 __device__ __forceinline__ void lidar_entry(const GRec &r, const float *poses, int col0,
                                             int ncols, const float dh[3], const float dl[3],
@@ -164,36 +181,17 @@ __device__ __forceinline__ void lidar_entry(const GRec &r, const float *poses, i
         const float o[3] = {Po[3], Po[7], Po[11]};
         float w[3], vh[3];
         precise_moment(mu, o, dh, dl, w, vh);
-        const int b = 3 + 4 * sl;
-        s[b][pos] = make_float4(f0 * (M0[1] * vh[2] - M0[2] * vh[1]),
-                                f0 * (M0[2] * vh[0] - M0[0] * vh[2]),
-                                f0 * (M0[0] * vh[1] - M0[1] * vh[0]), f0 * dot3(M0, w));
-        s[b + 1][pos] = make_float4(f1 * (M1[1] * vh[2] - M1[2] * vh[1]),
-                                    f1 * (M1[2] * vh[0] - M1[0] * vh[2]),
-                                    f1 * (M1[0] * vh[1] - M1[1] * vh[0]), f1 * dot3(M1, w));
-        s[b + 2][pos] = make_float4(f2 * (M2[1] * vh[2] - M2[2] * vh[1]),
-                                    f2 * (M2[2] * vh[0] - M2[0] * vh[2]),
-                                    f2 * (M2[0] * vh[1] - M2[1] * vh[0]), f2 * dot3(M2, w));
-        s[b + 3][pos] = make_float4(dot3(M0, vh), dot3(M1, vh), dot3(M2, vh), r.feat.z);
+        lid_col(s, pos, 0, sl) = make_float4(f0 * (M0[1] * vh[2] - M0[2] * vh[1]),
+                                             f0 * (M0[2] * vh[0] - M0[0] * vh[2]),
+                                             f0 * (M0[0] * vh[1] - M0[1] * vh[0]), f0 * dot3(M0, w));
+        lid_col(s, pos, 1, sl) = make_float4(f1 * (M1[1] * vh[2] - M1[2] * vh[1]),
+                                             f1 * (M1[2] * vh[0] - M1[0] * vh[2]),
+                                             f1 * (M1[0] * vh[1] - M1[1] * vh[0]), f1 * dot3(M1, w));
+        lid_col(s, pos, 2, sl) = make_float4(f2 * (M2[1] * vh[2] - M2[2] * vh[1]),
+                                             f2 * (M2[2] * vh[0] - M2[0] * vh[2]),
+                                             f2 * (M2[0] * vh[1] - M2[1] * vh[0]), f2 * dot3(M2, w));
+        lid_col(s, pos, 3, sl) = make_float4(dot3(M0, vh), dot3(M1, vh), dot3(M2, vh), r.feat.z);
     }
-}
-
-// Which of a LiDAR work item's rays (angles raz[r], rel[r], NaN for an
-// empty lane) lie in an entry's box (bx0, bx1, by0, by1): bit r, taking for
-// each ray the azimuth alias nearest the box centre.  The same float
-// operations as the per-ray test of lidar_pair.
-__device__ __forceinline__ uint32_t lidar_lanes(float bx0, float bx1, float by0, float by1,
-                                                const float *raz, const float *rel)
-{
-    const float cx = 0.5f * (bx0 + bx1);
-    uint32_t m = 0;
-#pragma unroll 8
-    for (int r = 0; r < 32; ++r) {
-        const float kk = rintf((cx - raz[r]) * (1.f / 360.f));
-        const float ra = raz[r] + 360.f * kk;
-        m |= (uint32_t)(ra >= bx0 && ra <= bx1 && rel[r] >= by0 && rel[r] <= by1) << r;
-    }
-    return m;
 }
 
 // Evaluate one LiDAR pair (entry j of the warp's block, planes of its
@@ -202,19 +200,30 @@ __device__ __forceinline__ bool lidar_pair_in(float4 (*s)[32], int j, int sb, bo
                                               const float dd[3], const float d[3],
                                               float alpha_min, float alpha_max, PairEval &pe)
 {
+    // every operation spelled out (fused multiply-adds in a fixed order), so
+    // that each call site computes the same bits: the forward evaluates a
+    // pair in whichever lane its compaction gives it, the backward in the
+    // ray's own lane
     const float4 m0 = s[0][j], m1 = s[1][j], m2 = s[2][j];
-    const float4 q0 = s[sb][j], q1 = s[sb + 1][j], q2 = s[sb + 2][j], u = s[sb + 3][j];
-    pe.n[0] = q0.w + q0.x * dd[0] + q0.y * dd[1] + q0.z * dd[2];
-    pe.n[1] = q1.w + q1.x * dd[0] + q1.y * dd[1] + q1.z * dd[2];
-    pe.n[2] = q2.w + q2.x * dd[0] + q2.y * dd[1] + q2.z * dd[2];
-    pe.e[0] = m0.x * d[0] + m0.y * d[1] + m0.z * d[2];
-    pe.e[1] = m1.x * d[0] + m1.y * d[1] + m1.z * d[2];
-    pe.e[2] = m2.x * d[0] + m2.y * d[1] + m2.z * d[2];
-    pe.inv = __fdividef(1.f, pe.e[0] * pe.e[0] + pe.e[1] * pe.e[1] + pe.e[2] * pe.e[2]);
-    pe.D2 = (pe.n[0] * pe.n[0] + pe.n[1] * pe.n[1] + pe.n[2] * pe.n[2]) * pe.inv;
-    pe.tau = (u.x * pe.e[0] + u.y * pe.e[1] + u.z * pe.e[2]) * pe.inv;
-    pe.rho = __expf(-0.5f * pe.D2);
-    const float a = m0.w * pe.rho;
+    const int sl = (sb - 3) >> 2;
+    const float4 q0 = lid_col(s, j, 0, sl), q1 = lid_col(s, j, 1, sl), q2 = lid_col(s, j, 2, sl),
+                 u = lid_col(s, j, 3, sl);
+    pe.n[0] = __fmaf_rn(q0.z, dd[2], __fmaf_rn(q0.y, dd[1], __fmaf_rn(q0.x, dd[0], q0.w)));
+    pe.n[1] = __fmaf_rn(q1.z, dd[2], __fmaf_rn(q1.y, dd[1], __fmaf_rn(q1.x, dd[0], q1.w)));
+    pe.n[2] = __fmaf_rn(q2.z, dd[2], __fmaf_rn(q2.y, dd[1], __fmaf_rn(q2.x, dd[0], q2.w)));
+    pe.e[0] = __fmaf_rn(m0.z, d[2], __fmaf_rn(m0.y, d[1], __fmul_rn(m0.x, d[0])));
+    pe.e[1] = __fmaf_rn(m1.z, d[2], __fmaf_rn(m1.y, d[1], __fmul_rn(m1.x, d[0])));
+    pe.e[2] = __fmaf_rn(m2.z, d[2], __fmaf_rn(m2.y, d[1], __fmul_rn(m2.x, d[0])));
+    const float ee = __fmaf_rn(pe.e[2], pe.e[2],
+                               __fmaf_rn(pe.e[1], pe.e[1], __fmul_rn(pe.e[0], pe.e[0])));
+    pe.inv = __fdividef(1.f, ee);
+    const float nn = __fmaf_rn(pe.n[2], pe.n[2],
+                               __fmaf_rn(pe.n[1], pe.n[1], __fmul_rn(pe.n[0], pe.n[0])));
+    pe.D2 = __fmul_rn(nn, pe.inv);
+    const float ue = __fmaf_rn(u.z, pe.e[2], __fmaf_rn(u.y, pe.e[1], __fmul_rn(u.x, pe.e[0])));
+    pe.tau = __fmul_rn(ue, pe.inv);
+    pe.rho = __expf(__fmul_rn(-0.5f, pe.D2));
+    const float a = __fmul_rn(m0.w, pe.rho);
     pe.clamped = a > alpha_max;
     pe.alpha = fminf(a, alpha_max);
     return in_box && pe.tau > 0.f && pe.alpha >= alpha_min;

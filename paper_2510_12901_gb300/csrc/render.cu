@@ -597,7 +597,7 @@ __device__ __forceinline__ bool cam_walk_rs(const CamRender &P, const GRec *__re
             const float wgt = ok ? pe.alpha * a.T : 0.f;
             a.c0 += wgt * s[1][j].w;
             a.c1 += wgt * s[2][j].w;
-            a.c2 += wgt * s[sb + 3][j].w;
+            a.c2 += wgt * lid_u(s, j, sb).w;
             a.Z += wgt * pe.tau;
             a.W += wgt;
             a.T = ok ? Tn : a.T;
@@ -845,7 +845,7 @@ __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__res
             const float wgt = ok ? pe.alpha * a.T : 0.f;
             a.c0 += wgt * L.s[1][j].w;
             a.c1 += wgt * L.s[2][j].w;
-            a.c2 += wgt * L.s[sb + 3][j].w;
+            a.c2 += wgt * lid_u(L.s, j, sb).w;
             a.Z += wgt * pe.tau;
             a.W += wgt;
             a.T = ok ? Tn : a.T;

@@ -14,7 +14,7 @@
 #include <algorithm>
 #include <vector>
 
-#include <limits>
+#include <string.h>
 
 #include "internal.h"
 
@@ -342,14 +342,28 @@ sg_status build_lidar(Lidar &L)
     }
     L.max_items_per_tile = 1;
     for (const uint2 &ti : tile_items) L.max_items_per_tile = std::max(L.max_items_per_tile, (int)ti.y);
-    // per item, the azimuth and elevation of each of its 32 ray slots (NaN:
-    // no ray), for the per-entry ray masks of the tile ranges kernel
-    std::vector<float> item_az(items.size() * 32), item_el(items.size() * 32);
-    const float qnan = std::numeric_limits<float>::quiet_NaN();
-    for (size_t i = 0; i < rays.size(); ++i) {
-        const uint32_t ray = rays[i];
-        item_az[i] = ray == 0xffffffffu ? qnan : az[ray % (uint32_t)nc];
-        item_el[i] = ray == 0xffffffffu ? qnan : L.elev[ray / (uint32_t)nc];
+    // per item, its ray slots factorised into columns and beams (a ray is in
+    // a box iff its column's azimuth and its beam's elevation are): the
+    // azimuths of its (at most kLidarColsMax) columns and the elevations of
+    // its distinct beams (at most 32), each with the mask of its ray slots
+    std::vector<LidarItemRays> item_rays(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
+        LidarItemRays &R = item_rays[i];
+        memset(&R, 0, sizeof(R));
+        const LidarItem &it = items[i];
+        R.ncols = it.ncols;
+        for (int sl = 0; sl < kLidarColsMax; ++sl)
+            R.col_az[sl] = sl < it.ncols ? az[it.col0 + sl] : 0.f;
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t ray = rays[(size_t)it.ray_off + k];
+            if (ray == 0xffffffffu) continue;
+            const int c = (int)(ray % (uint32_t)nc), b = (int)(ray / (uint32_t)nc);
+            R.col_bits[c - it.col0] |= 1u << k;
+            int j = 0;
+            while (j < R.nbeams && R.beam_el[j] != L.elev[b]) ++j;
+            if (j == R.nbeams) R.beam_el[R.nbeams++] = L.elev[b];
+            R.beam_bits[j] |= 1u << k;
+        }
     }
 
 #define SG_ALLOC_COPY(dst, vec)                                                         \
@@ -370,8 +384,7 @@ sg_status build_lidar(Lidar &L)
     SG_ALLOC_COPY(L.d_ray_e, ray_e);
     SG_ALLOC_COPY(L.d_tile_u, item_u);
     SG_ALLOC_COPY(L.d_tile_items, tile_items);
-    SG_ALLOC_COPY(L.d_item_az, item_az);
-    SG_ALLOC_COPY(L.d_item_el, item_el);
+    SG_ALLOC_COPY(L.d_item_ray_tab, item_rays);
 #undef SG_ALLOC_COPY
     return SG_OK;
 }

@@ -14,7 +14,7 @@
 //   6. per-tile [start, end) ranges.
 // Sorting the N Gaussians by depth once and the K pairs by tile alone moves
 // 2 passes over K instead of the 6 a 64-bit (tile, depth) key needs.
-#include "pairs.cuh"
+#include "internal.h"
 
 namespace sg {
 
@@ -645,17 +645,18 @@ sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max
 }
 
 // LiDAR lists: per-tile ranges, and per pair the ray masks of the work
-// items of its tile (k-th item of the tile: lmask[k * K_max + i]), by the
-// same float comparisons (lidar_lanes) as the compositing's per-ray test,
-// so that the compositing walks skip entries that reach none of their rays
-// without loading their records.
+// items of its tile (k-th item of the tile: lmask[k * K_max + i]), so that
+// the compositing walks skip entries that reach none of their rays without
+// loading their records.  A ray is in the box iff its column's azimuth (the
+// alias nearest the box centre) and its beam's elevation are, so the mask
+// takes one test per column and one per beam of the item.  Both the forward
+// and the backward walks read these masks, so they take the same decisions.
 __global__ void k_ranges_lidar(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
                                int64_t K_max, uint2 *__restrict__ ranges,
                                const uint32_t *__restrict__ ids, const float4 *__restrict__ rects,
                                const uint2 *__restrict__ tile_items,
-                               const float *__restrict__ item_az,
-                               const float *__restrict__ item_el, uint32_t *__restrict__ lmask,
-                               const uint32_t *__restrict__ err)
+                               const LidarItemRays *__restrict__ tab,
+                               uint32_t *__restrict__ lmask, const uint32_t *__restrict__ err)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t K = *d_K;
@@ -664,10 +665,21 @@ __global__ void k_ranges_lidar(const uint32_t *__restrict__ keys, const uint32_t
     if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
     if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
     const float4 rc = rects[ids[i]];
+    const float cx = 0.5f * (rc.x + rc.y);
     const uint2 ti = tile_items[t];
     for (uint32_t k = 0; k < ti.y; ++k) {
-        const size_t it = (size_t)(ti.x + k) * 32;
-        lmask[(int64_t)k * K_max + i] = lidar_lanes(rc.x, rc.y, rc.z, rc.w, item_az + it, item_el + it);
+        const LidarItemRays &R = tab[ti.x + k];
+        uint32_t mc = 0u, me = 0u;
+        for (int s = 0; s < R.ncols; ++s) {
+            const float az = R.col_az[s];
+            const float ra = az + 360.f * rintf((cx - az) * (1.f / 360.f));
+            mc |= (ra >= rc.x && ra <= rc.y) ? R.col_bits[s] : 0u;
+        }
+        for (int j = 0; j < R.nbeams; ++j) {
+            const float el = R.beam_el[j];
+            me |= (el >= rc.z && el <= rc.w) ? R.beam_bits[j] : 0u;
+        }
+        lmask[(int64_t)k * K_max + i] = mc & me;
     }
 }
 
@@ -679,8 +691,8 @@ sg_status lidar_tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t
     SG_CUDA(cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * ntiles, st));
     if (K_max == 0) return SG_OK;
     k_ranges_lidar<<<(unsigned)((K_max + 255) / 256), 256, 0, st>>>(
-        d_keys, d_K, K_max, d_ranges, d_ids, d_rects, L.d_tile_items, L.d_item_az, L.d_item_el,
-        d_lmask, d_err);
+        d_keys, d_K, K_max, d_ranges, d_ids, d_rects, L.d_tile_items, L.d_item_ray_tab, d_lmask,
+        d_err);
     SG_LAUNCHED();
     return SG_OK;
 }

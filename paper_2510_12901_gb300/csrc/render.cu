@@ -790,8 +790,10 @@ struct LidStage {
 // Composite entries [lo, hi) of the item's list (first entry `begin`): the
 // item's ray masks of a window of 32 entries (written with the tile ranges,
 // lmask[i] for list entry i) select the entries that reach a ray still
-// compositing; only those are staged, and each is evaluated for the rays in
-// its mask.  Returns whether the lane's ray stopped at T_min.
+// compositing; only those are staged.  The lanes of one column (a group)
+// then evaluate, in list order, the staged entries whose box holds a ray of
+// that column, while the other groups evaluate theirs.  Returns whether the
+// lane's ray stopped at T_min.
 __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__restrict__ rec,
                                            const uint32_t *__restrict__ ids,
                                            const uint32_t *__restrict__ lmask,
@@ -803,6 +805,7 @@ __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__res
 {
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
+    const uint32_t gm = __match_any_sync(0xffffffffu, sb);   // lanes of this lane's column
     // the next batch's ray masks and ids, loaded one batch ahead
     uint32_t nm = 0u, nid = 0u;
     if (lo + lane < hi) {
@@ -832,11 +835,26 @@ __device__ __forceinline__ bool lidar_walk(const LidRender &P, const GRec *__res
             L.pos[pos] = idx + 1 - begin;
         }
         __syncwarp();
+        // the staged entries that reach a ray of this lane's column group:
+        // the groups (lanes of one column) walk their own entries side by
+        // side, so an entry whose box holds rays of one column takes one
+        // step of that group only
         const int n = __popc(bal);
-        for (int j = 0; j < n; ++j) {
+        const uint32_t lj = lane < n ? L.lanes[lane] : 0u;
+        uint32_t G = 0u;
+        for (uint32_t rest = 0xffffffffu; rest;) {
+            const uint32_t gm_g = __shfl_sync(0xffffffffu, gm, __ffs(rest) - 1);
+            const uint32_t Gg = __ballot_sync(0xffffffffu, (lj & gm_g) != 0u);
+            G = gm == gm_g ? Gg : G;
+            rest &= ~gm_g;
+        }
+        while (__any_sync(0xffffffffu, G != 0u)) {
+            const bool has = G != 0u;
+            const int j = has ? __ffs(G) - 1 : 0;
+            G &= G - 1u;
             PairEval pe;
-            bool ok = lidar_pair_in(L.s, j, sb, (L.lanes[j] >> lane) & 1u, dd, d, P.alpha_min,
-                                    P.alpha_max, pe);
+            bool ok = lidar_pair_in(L.s, j, sb, has && ((L.lanes[j] >> lane) & 1u), dd, d,
+                                    P.alpha_min, P.alpha_max, pe);
             ok = ok && !done;
             const float Tn = a.T * (1.f - pe.alpha);
             const bool stop = ok && Tn < P.t_min;

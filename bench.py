@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the LiDAR sweep and differentiable-step measurements")
-    ap.add_argument("--only", choices=["lidar"], default=None,
+    ap.add_argument("--only", choices=["lidar", "serving"], default=None,
                     help="run one extra workload alone (for profiling) and print its line")
 
     return ap.parse_args()
@@ -176,6 +176,9 @@ def run_ours(args):
 
     if args.only == "lidar":
         return lidar_workload(torch, sg, syn, args.steps, args.warmup)
+    if args.only == "serving":
+        from paper_2510_12901_gb300 import serve
+        return serve.measure_serving(n_requests=args.serving_requests)
     sc = syn.street_scene(N_GAUSS, seed=0, kind="camera")
     fish, pin = syn.street_cameras()
     S = sg.Scene(sc)

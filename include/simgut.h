@@ -453,6 +453,9 @@ typedef struct {
     size_t memory_budget;   /* device bytes for running requests' workspaces, 0 = unlimited */
     int queue_capacity;     /* waiting requests before submit returns SG_ERR_BUSY */
     int use_graphs;         /* 1 (default): replay captured CUDA graphs, see below */
+    int fifo_priority;      /* 1 (default): a request admitted behind k others in flight
+                               runs on a stream of the k-th CUDA priority level (older
+                               requests first); 0: all at one priority */
 } sg_server_config;
 typedef struct {
     int kind;                   /* SG_REQ_CAMERA or SG_REQ_LIDAR */

@@ -18,6 +18,12 @@
 // has been reallocated since its capture, and after a replay that ran out of
 // pair capacity (that request is rendered again exactly).
 //
+// FIFO priority: each slot has one stream per CUDA stream-priority level
+// (up to n_slots levels); a request admitted while k others are in flight is
+// launched on the k-th level, so that the block scheduler serves the older
+// requests first and newer ones fill the SMs they leave idle, instead of
+// every request in flight sharing the GPU equally.
+//
 // Every wait here is a host-side condition-variable wait with a timeout; no
 // kernel waits on another.
 #include <math.h>
@@ -127,7 +133,8 @@ struct sg_server_s {
     std::deque<Job> queue;
     std::unordered_map<uint64_t, Result> results;
     std::vector<std::thread> workers;
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;   // [slot * n_prio + level], level 0 the highest
+    int n_prio = 1, prio_hi = 0;
     std::vector<sg_frame> frames;
     size_t bytes_in_flight = 0;
     uint64_t next_ticket = 1;
@@ -284,7 +291,7 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
 static void worker_main(sg_server S, int slot)
 {
     cudaSetDevice(S->device);
-    cudaStream_t st = S->streams[slot];
+    const cudaStream_t *slot_streams = &S->streams[(size_t)slot * S->n_prio];
     sg_frame fr = S->frames[slot];
     cudaEvent_t ev;
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -302,6 +309,10 @@ static void worker_main(sg_server S, int slot)
         Job job = S->queue.front();
         S->queue.pop_front();
         S->bytes_in_flight += job.bytes;
+        // FIFO priority: a request admitted behind k others in flight runs at
+        // the k-th priority level, so the oldest ones take the SMs first
+        const int level = S->cfg.fifo_priority ? std::min(S->in_flight, S->n_prio - 1) : 0;
+        const cudaStream_t st = slot_streams[level];
         S->in_flight++;
         S->busy_peak = std::max<int64_t>(S->busy_peak, S->in_flight);
         lk.unlock();
@@ -354,6 +365,7 @@ sg_server_config sg_default_server_config(void)
     c.memory_budget = 0;
     c.queue_capacity = 4096;
     c.use_graphs = 1;
+    c.fifo_priority = 1;
     return c;
 }
 
@@ -370,15 +382,25 @@ sg_status sg_server_create(const sg_server_config *cfg, sg_server *out)
     S->cfg = *cfg;
     S->graphs.resize(cfg->n_slots);
     cudaGetDevice(&S->device);
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
+    S->n_prio = cfg->fifo_priority ? std::max(1, std::min(cfg->n_slots, least - greatest + 1)) : 1;
+    S->prio_hi = greatest;
     for (int i = 0; i < cfg->n_slots; ++i) {
-        cudaStream_t st;
-        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            sg_status r = cuda_status(e, "cudaStreamCreate");
-            sg_server_destroy(S);
-            return r;
+        for (int k = 0; k < S->n_prio; ++k) {
+            cudaStream_t st;
+            cudaError_t e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking,
+                                                         std::min(least, greatest + k));
+            if (e != cudaSuccess) {
+                sg_status r = cuda_status(e, "cudaStreamCreateWithPriority");
+                sg_server_destroy(S);
+                return r;
+            }
+            S->streams.push_back(st);
         }
-        S->streams.push_back(st);
         sg_frame f = nullptr;
         sg_frame_create(&f);
         if (f) f->f.keep_state = false;   // no backward follows a served render

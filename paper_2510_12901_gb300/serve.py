@@ -16,10 +16,12 @@ from . import simgut as sg
 
 
 class Server:
-    def __init__(self, n_slots=4, memory_budget=0, queue_capacity=4096, use_graphs=True):
+    def __init__(self, n_slots=4, memory_budget=0, queue_capacity=4096, use_graphs=True,
+                 fifo_priority=True):
         cfg = sg.sg_default_server_config(n_slots=n_slots, memory_budget=memory_budget,
                                           queue_capacity=queue_capacity,
-                                          use_graphs=int(bool(use_graphs)))
+                                          use_graphs=int(bool(use_graphs)),
+                                          fifo_priority=int(bool(fifo_priority)))
         self.handle = sg.sg_server_create(cfg)
 
     @staticmethod
@@ -126,6 +128,26 @@ def run_one_per_launch(requests, render_fn):
     return len(requests) / span, rays / span / 1e6, np.array(lat)
 
 
+def run_one_per_launch_open_loop(requests, arrivals, render_fn):
+    """The same baseline under the server's arrival process: one host thread
+    renders the requests one at a time in arrival order (each waits for the
+    one before it), latency from arrival to completion.  Returns (Mrays/s
+    over the span, latencies in ms)."""
+    import torch
+    lat = []
+    rays = 0
+    t0 = time.perf_counter()
+    for req, t in zip(requests, arrivals):
+        dt = t0 + t - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        rays += render_fn(req)
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - (t0 + t)) * 1e3)
+    span = time.perf_counter() - (t0 + arrivals[0])
+    return rays / span / 1e6, np.array(lat)
+
+
 # ---------------------------------------------------------------- workload
 class ServingWorkload:
     """Resident scenes, sensors and a seeded request stream.
@@ -227,27 +249,48 @@ def measure_serving(n_requests=300, loads=(0.5, 0.8, 1.0, 1.2, 2.0), n_slots=4, 
                                          lambda i: W.render_plain(i, frame, stream))
     base = {"requests_per_s": rps, "mrays_per_s": mrays,
             "latency_p50_ms": float(np.percentile(lat, 50)),
-            "latency_p99_ms": float(np.percentile(lat, 99))}
-    srv = Server(n_slots=n_slots, memory_budget=memory_budget)
-    reqs = [W.request(i) for i in range(n_requests)]
-    # warm up: two bursts of the whole stream, so that every slot has grown
-    # its workspace and captured the graphs of the combinations it serves
-    for _ in range(2):
-        warm = [srv.submit(r) for r in reqs]
-        for t in warm:
-            srv.wait(t)
-    out = []
-    for load in loads:
+            "latency_p99_ms": float(np.percentile(lat, 99)),
+            "latency_note": "closed loop: each request's render alone, no queueing"}
+    # the baseline under the same Poisson arrivals as the server (queueing
+    # included), at the loads where it can keep up or nearly so
+    base_open = []
+    for load in [l for l in loads if l <= 1.0]:
         arr = poisson_arrivals(n_requests, load * rps, seed + int(load * 100))
-        st = run_open_loop(srv, reqs, arr)
-        out.append({"load": load, "offered_requests_per_s": load * rps,
-                    "mrays_per_s": st["mrays_per_s"], "latency_p50_ms": st["latency_p50_ms"],
-                    "latency_p99_ms": st["latency_p99_ms"], "completed": st["completed"],
-                    "peak_in_flight": st["peak_in_flight"],
-                    "graph_replays": st["graph_replays"], "graph_captures": st["graph_captures"],
-                    "overflow_rerenders": st["overflow_rerenders"]})
-    srv.close()
-    return {"one_request_per_launch": base, "server": out, "n_slots": n_slots,
+        m, lo = run_one_per_launch_open_loop(range(n_requests), arr,
+                                             lambda i: W.render_plain(i, frame, stream))
+        base_open.append({"load": load, "mrays_per_s": m,
+                          "latency_p50_ms": float(np.percentile(lo, 50)),
+                          "latency_p99_ms": float(np.percentile(lo, 99))})
+    reqs = [W.request(i) for i in range(n_requests)]
+
+    def sweep(fifo, load_list):
+        srv = Server(n_slots=n_slots, memory_budget=memory_budget, fifo_priority=fifo)
+        # warm up: two bursts of the whole stream, so that every slot has
+        # grown its workspace and captured the graphs of the combinations
+        for _ in range(2):
+            warm = [srv.submit(r) for r in reqs]
+            for t in warm:
+                srv.wait(t)
+        res = []
+        for load in load_list:
+            arr = poisson_arrivals(n_requests, load * rps, seed + int(load * 100))
+            st = run_open_loop(srv, reqs, arr)
+            res.append({"load": load, "offered_requests_per_s": load * rps,
+                        "mrays_per_s": st["mrays_per_s"], "latency_p50_ms": st["latency_p50_ms"],
+                        "latency_p99_ms": st["latency_p99_ms"], "completed": st["completed"],
+                        "peak_in_flight": st["peak_in_flight"],
+                        "graph_replays": st["graph_replays"],
+                        "graph_captures": st["graph_captures"],
+                        "overflow_rerenders": st["overflow_rerenders"]})
+        srv.close()
+        return res
+
+    out = sweep(True, loads)
+    # the same server with every request at one stream priority
+    flat = sweep(False, [l for l in loads if l <= 1.2])
+    return {"one_request_per_launch": base, "one_request_per_launch_open_loop": base_open,
+            "server": out, "server_one_priority": flat,
+            "n_slots": n_slots,
             "requests_per_load": n_requests,
             "mix": "25% each pinhole 1920x1080, fisheye 1280x960, LiDAR 64x1024, LiDAR 128x2048; "
                    "scenes of 0.5M/1.5M/3M Gaussians (2/3 camera, 1/3 LiDAR)"}

@@ -60,7 +60,8 @@ class sg_camera_view(C.Structure):
 
 class sg_server_config(C.Structure):
     _fields_ = [("n_slots", C.c_int), ("memory_budget", C.c_size_t),
-                ("queue_capacity", C.c_int), ("use_graphs", C.c_int)]
+                ("queue_capacity", C.c_int), ("use_graphs", C.c_int),
+                ("fifo_priority", C.c_int)]
 
 
 class sg_request(C.Structure):

@@ -446,6 +446,15 @@ sg_status sg_backward_lidar(sg_scene scene, sg_frame frame, const float *d_g_ran
  * memory that the graph copies to the device first.  A replay whose pairs
  * exceed the capacity is rendered again exactly (the result is always
  * complete) and the graph is captured anew with a larger capacity.
+ *
+ * Batching (max_batch > 1): when a request is admitted, the requests already
+ * waiting (among the next 32 in the queue) of the same combination (scene,
+ * sensor, options) join it, up to max_batch, as far as the memory budget
+ * allows; the others keep their order.  A batch renders as one launch
+ * sequence: its requests on the slot's frames, forked onto per-request
+ * streams (cameras through one sg_render_cameras call), and, with graphs,
+ * as one captured graph per (combination, batch size), replayed with one
+ * launch.  Every request of a batch completes when the batch does.
  * ---------------------------------------------------------------------- */
 typedef struct sg_server_s *sg_server;
 typedef struct {
@@ -456,6 +465,8 @@ typedef struct {
     int fifo_priority;      /* 1 (default): a request admitted behind k others in flight
                                runs on a stream of the k-th CUDA priority level (older
                                requests first); 0: all at one priority */
+    int max_batch;          /* 1..16 (default 4): queued requests of the admitted one's
+                               combination join it, up to this many, see below */
 } sg_server_config;
 typedef struct {
     int kind;                   /* SG_REQ_CAMERA or SG_REQ_LIDAR */
@@ -473,6 +484,8 @@ typedef struct {
     int64_t graph_replays;      /* requests served by replaying a captured graph */
     int64_t graph_captures;     /* graphs captured (one per slot and combination) */
     int64_t overflow_rerenders; /* replays whose pairs outgrew the capacity, redone exactly */
+    int64_t batches;            /* renders that served several requests at once */
+    int64_t batched_requests;   /* requests served by those */
     double latency_mean_ms, latency_p50_ms, latency_p99_ms, latency_max_ms;
     double span_s;              /* first arrival to last completion */
     double mrays_per_s;         /* rays of completed requests / span */

@@ -65,6 +65,7 @@ struct Result {
     bool done = false;
     sg_status status = SG_OK;
     double latency_ms = 0;
+    std::string message;   // the worker's error message when status != SG_OK
 };
 
 // A captured render of one (scene, sensor, options) combination on one slot.
@@ -135,18 +136,28 @@ struct sg_server_s {
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;   // [slot * n_prio + level], level 0 the highest
     int n_prio = 1, prio_hi = 0;
-    std::vector<sg_frame> frames;
+    // per slot and batch position: a frame and a view stream (forked from the
+    // slot's stream for batches of several requests), and the fork / join events
+    std::vector<std::vector<sg_frame>> frames;
+    std::vector<std::vector<cudaStream_t>> vstreams;
+    std::vector<cudaEvent_t> fork_ev;
+    std::vector<std::vector<cudaEvent_t>> join_ev;
+    // batches: timed events at the start and at each request's end (recorded
+    // as graph nodes in captures), for each request's own completion time
+    std::vector<cudaEvent_t> start_ev;
+    std::vector<std::vector<cudaEvent_t>> done_ev;
     size_t bytes_in_flight = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
     int in_flight = 0;
-    // graphs: per slot, per combination; largest pair count seen per combination
+    // graphs: per slot, per (combination, batch size); largest pair count seen
+    // per combination
     std::vector<std::unordered_map<std::string, GraphEntry>> graphs;
     std::unordered_map<std::string, int64_t> max_pairs;
     // statistics
     std::vector<double> latencies;
     int64_t completed = 0, failed = 0, rays = 0, busy_peak = 0;
-    int64_t replays = 0, captures = 0, overflows = 0;
+    int64_t replays = 0, captures = 0, overflows = 0, batches = 0, batched = 0;
     Clock::time_point t_first, t_last;
     bool any = false;
 };
@@ -160,24 +171,78 @@ static sg_status render_plain(const sg_request &r, sg_frame fr, cudaStream_t st)
                            r.d_out[2], r.d_out[3], st);
 }
 
-// Wait for the request's render on `st` and check its device status word:
-// a capacity-mode render copies it with its scalars; after an exact render
-// it is copied here.
-static sg_status finish(sg_frame frame, cudaEvent_t ev, cudaStream_t st)
+// A batch of requests of one combination (same scene, sensor and options),
+// request i on the slot's frame i.  One request renders on `st` itself;
+// several are forked onto the slot's view streams (waiting for `st`), cameras
+// as one sg_render_cameras call (their pair counts all on the way before the
+// host waits for one), LiDAR sweeps one after another, and joined back into
+// `st`.  The same sequence is what a captured graph of the batch holds.
+static sg_status render_batch(sg_server S, int slot, const std::vector<const sg_request *> &rs,
+                              cudaStream_t st)
 {
-    Frame &fr = frame->f;
-    const bool exact = fr.k_cap == 0;
-    uint32_t *word = fr.h_scalars + (exact ? kHostStatusQuery : kScalStatus);
+    const size_t B = rs.size();
+    const std::vector<sg_frame> &F = S->frames[slot];
+    if (B == 1) return render_plain(*rs[0], F[0], st);
+    const std::vector<cudaStream_t> &V = S->vstreams[slot];
+    // the timing events become graph nodes when the batch is being captured
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    SG_CUDA(cudaStreamIsCapturing(st, &cap_st));
+    const unsigned rec_flags =
+        cap_st == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    SG_CUDA(cudaEventRecordWithFlags(S->start_ev[slot], st, rec_flags));
+    SG_CUDA(cudaEventRecord(S->fork_ev[slot], st));
+    for (size_t i = 0; i < B; ++i) SG_CUDA(cudaStreamWaitEvent(V[i], S->fork_ev[slot], 0));
+    sg_status s = SG_OK;
+    if (rs[0]->kind == SG_REQ_CAMERA) {
+        std::vector<sg_camera_view> views(B);
+        for (size_t i = 0; i < B; ++i) {
+            const sg_request &r = *rs[i];
+            sg_camera_view &v = views[i];
+            memset(&v, 0, sizeof(v));
+            v.camera = r.camera;
+            memcpy(v.c2w, r.c2w, sizeof(v.c2w));
+            v.frame = F[i];
+            v.rgb = r.d_out[0];
+            v.alpha = r.d_out[1];
+            v.depth = r.d_out[2];
+            v.stream = V[i];
+        }
+        s = sg_render_cameras(rs[0]->scene, (int)B, views.data(), &rs[0]->opts, 0);
+    } else {
+        for (size_t i = 0; i < B && s == SG_OK; ++i) s = render_plain(*rs[i], F[i], V[i]);
+    }
+    // join every view stream (also after an error: nothing is left forked)
+    for (size_t i = 0; i < B; ++i) {
+        cudaError_t e = cudaEventRecordWithFlags(S->done_ev[slot][i], V[i], rec_flags);
+        if (e == cudaSuccess) e = cudaEventRecord(S->join_ev[slot][i], V[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, S->join_ev[slot][i], 0);
+        if (e != cudaSuccess && s == SG_OK) s = cuda_status(e, "joining a batch's streams");
+    }
+    return s;
+}
+
+// Wait for the batch's renders on `st` and check their device status words:
+// a capacity-mode render copies its word with its scalars; after an exact
+// render it is copied here.
+static sg_status finish(const std::vector<sg_frame> &F, size_t B, cudaEvent_t ev, cudaStream_t st)
+{
     cudaError_t e = cudaSuccess;
-    if (exact)
-        e = cudaMemcpyAsync(word, (const uint32_t *)fr.scalars.p + kScalStatus, 4,
-                            cudaMemcpyDeviceToHost, st);
+    for (size_t i = 0; i < B && e == cudaSuccess; ++i) {
+        Frame &fr = F[i]->f;
+        if (fr.k_cap == 0)
+            e = cudaMemcpyAsync(fr.h_scalars + kHostStatusQuery,
+                                (const uint32_t *)fr.scalars.p + kScalStatus, 4,
+                                cudaMemcpyDeviceToHost, st);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev);
     if (e != cudaSuccess) return cuda_status(e, "request completion");
-    if (*word) {
-        set_error("a look-back wait of the sort gave up in this request's render");
-        return SG_ERR_TIMEOUT;
+    for (size_t i = 0; i < B; ++i) {
+        const Frame &fr = F[i]->f;
+        if (fr.h_scalars[fr.k_cap == 0 ? kHostStatusQuery : kScalStatus]) {
+            set_error("a look-back wait of the sort gave up in this request's render");
+            return SG_ERR_TIMEOUT;
+        }
     }
     return SG_OK;
 }
@@ -195,46 +260,83 @@ static void drop_graph(GraphEntry &g)
     g = GraphEntry();
 }
 
-// One request on `slot`, with graphs: replay, or warm up and capture.
-static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_frame frame,
+static std::vector<void *> batch_bufs(const std::vector<sg_frame> &F, size_t B)
+{
+    std::vector<void *> v;
+    for (size_t i = 0; i < B; ++i) {
+        std::vector<void *> b = frame_bufs(F[i]->f);
+        v.insert(v.end(), b.begin(), b.end());
+    }
+    return v;
+}
+
+static void set_capacity(const std::vector<sg_frame> &F, size_t B, int64_t cap)
+{
+    for (size_t i = 0; i < B; ++i) F[i]->f.k_cap = cap;
+}
+
+// A batch of requests of one combination on `slot`, with graphs: replay the
+// graph of (combination, batch size), or warm up and capture it.  The first
+// batch of a combination renders exactly; the next one in capacity mode
+// (room for 1.25x the largest pair count seen plus 64K) and is captured.
+static sg_status render_graphed(sg_server S, int slot, const std::vector<const sg_request *> &rs,
                                 cudaStream_t st, cudaEvent_t ev)
 {
-    Frame &fr = frame->f;
-    const std::string key = graph_key(r);
-    GraphEntry &g = S->graphs[slot][key];
+    const size_t B = rs.size();
+    const std::vector<sg_frame> &F = S->frames[slot];
+    const std::string key = graph_key(*rs[0]);
+    GraphEntry &g = S->graphs[slot][key + "#" + std::to_string(B)];
     sg_status s;
-    if (g.exec && g.bufs == frame_bufs(fr)) {
-        // replay: the request's parameters through the pinned descriptor
-        RenderDesc &D = *fr.h_desc;
-        if (r.kind == SG_REQ_CAMERA) {
-            memcpy(D.c2w, r.c2w, sizeof(D.c2w));
-            D.poses = nullptr;
-            for (int i = 0; i < 3; ++i) D.out[i] = r.d_out[i];
-            D.out[3] = nullptr;
-            memcpy(fr.c2w, r.c2w, sizeof(fr.c2w));
-        } else {
-            memset(D.c2w, 0, sizeof(D.c2w));
-            D.poses = r.d_col_c2w;
-            for (int i = 0; i < 4; ++i) D.out[i] = r.d_out[i];
-            fr.d_lidar_poses = r.d_col_c2w;
+    auto pairs_needed = [&]() {
+        int64_t need = 0;
+        for (size_t i = 0; i < B; ++i) {
+            const Frame &fr = F[i]->f;
+            const int64_t n = fr.k_cap > 0 ? (int64_t)fr.h_scalars[1] + fr.h_scalars[3] : fr.n_pairs;
+            need = std::max(need, n);
         }
-        fr.k_cap = g.cap;
+        return need;
+    };
+    auto dropped_any = [&]() {
+        for (size_t i = 0; i < B; ++i)
+            if (F[i]->f.h_scalars[3] != 0) return true;
+        return false;
+    };
+    if (g.exec && g.bufs == batch_bufs(F, B)) {
+        // replay: each request's parameters through its frame's pinned descriptor
+        for (size_t i = 0; i < B; ++i) {
+            const sg_request &r = *rs[i];
+            Frame &fr = F[i]->f;
+            RenderDesc &D = *fr.h_desc;
+            if (r.kind == SG_REQ_CAMERA) {
+                memcpy(D.c2w, r.c2w, sizeof(D.c2w));
+                D.poses = nullptr;
+                for (int k = 0; k < 3; ++k) D.out[k] = r.d_out[k];
+                D.out[3] = nullptr;
+                memcpy(fr.c2w, r.c2w, sizeof(fr.c2w));
+            } else {
+                memset(D.c2w, 0, sizeof(D.c2w));
+                D.poses = r.d_col_c2w;
+                for (int k = 0; k < 4; ++k) D.out[k] = r.d_out[k];
+                fr.d_lidar_poses = r.d_col_c2w;
+            }
+        }
+        set_capacity(F, B, g.cap);
         cudaError_t e = cudaGraphLaunch(g.exec, st);
         if (e != cudaSuccess) return cuda_status(e, "cudaGraphLaunch");
         count_launches(g.kernels);
-        if ((s = finish(frame, ev, st)) != SG_OK) return s;
-        const int64_t dropped = fr.h_scalars[3], kept = fr.h_scalars[1];
-        if (dropped == 0) {
+        if ((s = finish(F, B, ev, st)) != SG_OK) return s;
+        if (!dropped_any()) {
             std::lock_guard<std::mutex> lk(S->mu);
-            S->replays++;
+            S->replays += (int64_t)B;
             return SG_OK;
         }
         // out of pair capacity: render exactly, capture anew next time
+        const int64_t need = pairs_needed();
         drop_graph(g);
-        fr.k_cap = 0;
-        if ((s = render_plain(r, frame, st)) != SG_OK) return s;
-        if ((s = finish(frame, ev, st)) != SG_OK) return s;
-        note_pairs(S, key, fr.n_pairs > kept + dropped ? fr.n_pairs : kept + dropped);
+        set_capacity(F, B, 0);
+        if ((s = render_batch(S, slot, rs, st)) != SG_OK) return s;
+        if ((s = finish(F, B, ev, st)) != SG_OK) return s;
+        note_pairs(S, key, std::max(need, pairs_needed()));
         std::lock_guard<std::mutex> lk(S->mu);
         S->overflows++;
         return SG_OK;
@@ -247,29 +349,29 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
         if (it != S->max_pairs.end()) known = it->second;
     }
     if (known < 0) {    // first sight of this combination: exact render
-        fr.k_cap = 0;
-        if ((s = render_plain(r, frame, st)) != SG_OK) return s;
-        if ((s = finish(frame, ev, st)) != SG_OK) return s;
-        note_pairs(S, key, fr.n_pairs);
+        set_capacity(F, B, 0);
+        if ((s = render_batch(S, slot, rs, st)) != SG_OK) return s;
+        if ((s = finish(F, B, ev, st)) != SG_OK) return s;
+        note_pairs(S, key, pairs_needed());
         return SG_OK;
     }
     // capacity-mode render (grows the workspace as needed), then capture
     const int64_t cap = std::min<int64_t>(known + known / 4 + 65536, 0x7fffffffLL);
-    fr.k_cap = cap;
-    if ((s = render_plain(r, frame, st)) != SG_OK) return s;
-    if ((s = finish(frame, ev, st)) != SG_OK) return s;
-    if (fr.h_scalars[3] != 0) {
-        const int64_t need = (int64_t)fr.h_scalars[1] + fr.h_scalars[3];
-        fr.k_cap = 0;
-        if ((s = render_plain(r, frame, st)) != SG_OK) return s;
-        if ((s = finish(frame, ev, st)) != SG_OK) return s;
+    set_capacity(F, B, cap);
+    if ((s = render_batch(S, slot, rs, st)) != SG_OK) return s;
+    if ((s = finish(F, B, ev, st)) != SG_OK) return s;
+    if (dropped_any()) {
+        const int64_t need = pairs_needed();
+        set_capacity(F, B, 0);
+        if ((s = render_batch(S, slot, rs, st)) != SG_OK) return s;
+        if ((s = finish(F, B, ev, st)) != SG_OK) return s;
         note_pairs(S, key, need);
         return SG_OK;
     }
     cudaGraph_t graph = nullptr;
     capture_guard() = true;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    sg_status cs = e == cudaSuccess ? render_plain(r, frame, st) : SG_ERR_CUDA;
+    sg_status cs = e == cudaSuccess ? render_batch(S, slot, rs, st) : SG_ERR_CUDA;
     if (e == cudaSuccess) e = cudaStreamEndCapture(st, &graph);
     capture_guard() = false;
     if (cs == SG_OK && e == cudaSuccess && graph) {
@@ -278,7 +380,7 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
             g.exec = exec;
             g.kernels = count_kernel_nodes(graph);
             g.cap = cap;
-            g.bufs = frame_bufs(fr);
+            g.bufs = batch_bufs(F, B);
             std::lock_guard<std::mutex> lk(S->mu);
             S->captures++;
         }
@@ -288,11 +390,17 @@ static sg_status render_graphed(sg_server S, int slot, const sg_request &r, sg_f
     return SG_OK;
 }
 
+static int64_t request_rays(const sg_request &r)
+{
+    return r.kind == SG_REQ_CAMERA ? (int64_t)r.camera->c.width * r.camera->c.height
+                                   : (int64_t)r.lidar->l.n_beams * r.lidar->l.n_cols;
+}
+
 static void worker_main(sg_server S, int slot)
 {
     cudaSetDevice(S->device);
     const cudaStream_t *slot_streams = &S->streams[(size_t)slot * S->n_prio];
-    sg_frame fr = S->frames[slot];
+    const std::vector<sg_frame> &F = S->frames[slot];
     cudaEvent_t ev;
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     std::unique_lock<std::mutex> lk(S->mu);
@@ -306,47 +414,94 @@ static void worker_main(sg_server S, int slot)
                    S->bytes_in_flight + j.bytes <= S->cfg.memory_budget;
         });
         if (S->stop) break;   // requests not yet started are dropped
-        Job job = S->queue.front();
+        std::vector<Job> jobs(1, S->queue.front());
         S->queue.pop_front();
-        S->bytes_in_flight += job.bytes;
-        // FIFO priority: a request admitted behind k others in flight runs at
+        size_t bytes = jobs[0].bytes;
+        // batching: queued requests of the same combination join it, up to
+        // max_batch, as far as the memory budget allows (a look at the first
+        // kBatchScan waiting requests; the others keep their order)
+        constexpr int kBatchScan = 32;
+        if (S->cfg.max_batch > 1 && !S->queue.empty()) {
+            const std::string k0 = graph_key(jobs[0].req);
+            int scanned = 0;
+            for (auto it = S->queue.begin();
+                 it != S->queue.end() && (int)jobs.size() < S->cfg.max_batch && scanned < kBatchScan;
+                 ++scanned) {
+                const bool fits = S->cfg.memory_budget == 0 ||
+                                  S->bytes_in_flight + bytes + it->bytes <= S->cfg.memory_budget;
+                if (fits && graph_key(it->req) == k0) {
+                    bytes += it->bytes;
+                    jobs.push_back(*it);
+                    it = S->queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        const int B = (int)jobs.size();
+        S->bytes_in_flight += bytes;
+        // FIFO priority: a batch admitted behind k others in flight runs at
         // the k-th priority level, so the oldest ones take the SMs first
         const int level = S->cfg.fifo_priority ? std::min(S->in_flight, S->n_prio - 1) : 0;
         const cudaStream_t st = slot_streams[level];
-        S->in_flight++;
+        S->in_flight += B;
         S->busy_peak = std::max<int64_t>(S->busy_peak, S->in_flight);
+        if (B > 1) {
+            S->batches++;
+            S->batched += B;
+        }
         lk.unlock();
         S->cv_work.notify_all();
 
-        const sg_request &r = job.req;
+        std::vector<const sg_request *> rs;
+        for (const Job &j : jobs) rs.push_back(&j.req);
         sg_status s;
-        const int64_t nrays = r.kind == SG_REQ_CAMERA
-                                  ? (int64_t)r.camera->c.width * r.camera->c.height
-                                  : (int64_t)r.lidar->l.n_beams * r.lidar->l.n_cols;
         if (S->cfg.use_graphs) {
-            s = render_graphed(S, slot, r, fr, st, ev);
+            s = render_graphed(S, slot, rs, st, ev);
         } else {
-            fr->f.k_cap = 0;
-            s = render_plain(r, fr, st);
-            if (s == SG_OK) s = finish(fr, ev, st);
+            set_capacity(F, (size_t)B, 0);
+            s = render_batch(S, slot, rs, st);
+            if (s == SG_OK) s = finish(F, (size_t)B, ev, st);
         }
         const Clock::time_point t_done = Clock::now();
+        // in a batch each request completes with its own view: its end, on
+        // the device clock, against the batch's last one
+        std::vector<double> early_ms((size_t)B, 0.0);
+        if (B > 1 && s == SG_OK) {
+            std::vector<float> at((size_t)B, 0.f);
+            bool ok = true;
+            for (int i = 0; i < B && ok; ++i)
+                ok = cudaEventElapsedTime(&at[i], S->start_ev[slot], S->done_ev[slot][i]) ==
+                     cudaSuccess;
+            if (ok) {
+                const float last = *std::max_element(at.begin(), at.end());
+                for (int i = 0; i < B; ++i) early_ms[i] = (double)(last - at[i]);
+            } else {
+                cudaGetLastError();
+            }
+        }
 
         lk.lock();
-        S->bytes_in_flight -= job.bytes;
-        S->in_flight--;
-        Result &res = S->results[job.ticket];
-        res.done = true;
-        res.status = s;
-        res.latency_ms = std::chrono::duration<double, std::milli>(t_done - job.arrival).count();
-        if (s == SG_OK) {
-            S->completed++;
-            S->rays += nrays;
-            S->latencies.push_back(res.latency_ms);
-        } else {
-            S->failed++;
+        S->bytes_in_flight -= bytes;
+        S->in_flight -= B;
+        for (int bi = 0; bi < B; ++bi) {
+            const Job &job = jobs[bi];
+            Result &res = S->results[job.ticket];
+            res.done = true;
+            res.status = s;
+            if (s != SG_OK) res.message = sg_last_error();
+            res.latency_ms =
+                std::chrono::duration<double, std::milli>(t_done - job.arrival).count() -
+                early_ms[bi];
+            if (s == SG_OK) {
+                S->completed++;
+                S->rays += request_rays(job.req);
+                S->latencies.push_back(res.latency_ms);
+            } else {
+                S->failed++;
+            }
+            if (!S->any) { S->t_first = job.arrival; S->any = true; }
         }
-        if (!S->any) { S->t_first = job.arrival; S->any = true; }
         S->t_last = t_done;
         S->cv_done.notify_all();
         S->cv_work.notify_all();
@@ -366,6 +521,7 @@ sg_server_config sg_default_server_config(void)
     c.queue_capacity = 4096;
     c.use_graphs = 1;
     c.fifo_priority = 1;
+    c.max_batch = 4;
     return c;
 }
 
@@ -373,8 +529,10 @@ sg_status sg_server_create(const sg_server_config *cfg, sg_server *out)
 {
     if (!cfg || !out) { set_error("NULL argument"); return SG_ERR_INVALID; }
     *out = nullptr;
-    if (cfg->n_slots < 1 || cfg->n_slots > 64 || cfg->queue_capacity < 1) {
-        set_error("sg_server_create: n_slots must be in 1..64 and queue_capacity >= 1");
+    if (cfg->n_slots < 1 || cfg->n_slots > 64 || cfg->queue_capacity < 1 ||
+        cfg->max_batch < 1 || cfg->max_batch > 16) {
+        set_error("sg_server_create: n_slots must be in 1..64, queue_capacity >= 1 and "
+                  "max_batch in 1..16");
         return SG_ERR_INVALID;
     }
     sg_server S = new (std::nothrow) sg_server_s;
@@ -401,10 +559,38 @@ sg_status sg_server_create(const sg_server_config *cfg, sg_server *out)
             }
             S->streams.push_back(st);
         }
-        sg_frame f = nullptr;
-        sg_frame_create(&f);
-        if (f) f->f.keep_state = false;   // no backward follows a served render
-        S->frames.push_back(f);
+        // a frame and a view stream per batch position, fork and join events
+        S->frames.emplace_back();
+        S->vstreams.emplace_back();
+        S->join_ev.emplace_back();
+        S->done_ev.emplace_back();
+        S->fork_ev.push_back(nullptr);
+        S->start_ev.push_back(nullptr);
+        cudaError_t e = cudaEventCreateWithFlags(&S->fork_ev.back(), cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&S->start_ev.back());
+        for (int b = 0; b < cfg->max_batch && e == cudaSuccess; ++b) {
+            sg_frame f = nullptr;
+            if (sg_frame_create(&f) != SG_OK) {
+                sg_server_destroy(S);
+                return SG_ERR_OOM;
+            }
+            f->f.keep_state = false;   // no backward follows a served render
+            S->frames.back().push_back(f);
+            cudaStream_t vs = nullptr;
+            e = cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) S->vstreams.back().push_back(vs);
+            cudaEvent_t je = nullptr;
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&je, cudaEventDisableTiming);
+            if (e == cudaSuccess) S->join_ev.back().push_back(je);
+            cudaEvent_t de = nullptr;
+            if (e == cudaSuccess) e = cudaEventCreate(&de);
+            if (e == cudaSuccess) S->done_ev.back().push_back(de);
+        }
+        if (e != cudaSuccess) {
+            sg_status r = cuda_status(e, "server streams and events");
+            sg_server_destroy(S);
+            return r;
+        }
     }
     for (int i = 0; i < cfg->n_slots; ++i) S->workers.emplace_back(worker_main, S, i);
     *out = S;
@@ -460,7 +646,9 @@ sg_status sg_server_wait(sg_server S, uint64_t ticket, double timeout_s, double 
     Result r = S->results[ticket];
     S->results.erase(ticket);
     if (latency_ms) *latency_ms = r.latency_ms;
-    if (r.status != SG_OK) set_error("request %llu failed (status %d)", (unsigned long long)ticket, r.status);
+    if (r.status != SG_OK)
+        set_error("request %llu failed (status %d): %s", (unsigned long long)ticket, r.status,
+                  r.message.c_str());
     return r.status;
 }
 
@@ -489,6 +677,8 @@ sg_status sg_server_stats(sg_server S, sg_server_report *out)
     out->graph_replays = S->replays;
     out->graph_captures = S->captures;
     out->overflow_rerenders = S->overflows;
+    out->batches = S->batches;
+    out->batched_requests = S->batched;
     std::vector<double> l = S->latencies;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
@@ -518,7 +708,7 @@ sg_status sg_server_reset_stats(sg_server S)
     std::lock_guard<std::mutex> lk(S->mu);
     S->latencies.clear();
     S->completed = S->failed = S->rays = S->busy_peak = 0;
-    S->replays = S->captures = S->overflows = 0;
+    S->replays = S->captures = S->overflows = S->batches = S->batched = 0;
     S->any = false;
     return SG_OK;
 }
@@ -536,7 +726,18 @@ void sg_server_destroy(sg_server S)
     for (auto &m : S->graphs)
         for (auto &kv : m) drop_graph(kv.second);
     for (auto st : S->streams) cudaStreamDestroy(st);
-    for (auto f : S->frames) sg_frame_destroy(f);
+    for (auto &v : S->vstreams)
+        for (auto st : v) cudaStreamDestroy(st);
+    for (auto e : S->fork_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &v : S->join_ev)
+        for (auto e : v) cudaEventDestroy(e);
+    for (auto e : S->start_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &v : S->done_ev)
+        for (auto e : v) cudaEventDestroy(e);
+    for (auto &v : S->frames)
+        for (auto f : v) sg_frame_destroy(f);
     delete S;
 }
 

@@ -17,11 +17,12 @@ from . import simgut as sg
 
 class Server:
     def __init__(self, n_slots=4, memory_budget=0, queue_capacity=4096, use_graphs=True,
-                 fifo_priority=True):
+                 fifo_priority=True, max_batch=4):
         cfg = sg.sg_default_server_config(n_slots=n_slots, memory_budget=memory_budget,
                                           queue_capacity=queue_capacity,
                                           use_graphs=int(bool(use_graphs)),
-                                          fifo_priority=int(bool(fifo_priority)))
+                                          fifo_priority=int(bool(fifo_priority)),
+                                          max_batch=int(max_batch))
         self.handle = sg.sg_server_create(cfg)
 
     @staticmethod
@@ -263,14 +264,16 @@ def measure_serving(n_requests=300, loads=(0.5, 0.8, 1.0, 1.2, 2.0), n_slots=4, 
                           "latency_p99_ms": float(np.percentile(lo, 99))})
     reqs = [W.request(i) for i in range(n_requests)]
 
-    def sweep(fifo, load_list):
-        srv = Server(n_slots=n_slots, memory_budget=memory_budget, fifo_priority=fifo)
-        # warm up: two bursts of the whole stream, so that every slot has
-        # grown its workspace and captured the graphs of the combinations
+    def sweep(max_batch, load_list):
+        srv = Server(n_slots=n_slots, memory_budget=memory_budget, max_batch=max_batch)
+        # warm up: two bursts of the whole stream and one pass at the highest
+        # load, so that every slot has grown its workspace and captured the
+        # graphs of the combinations (and batch sizes) it serves
         for _ in range(2):
             warm = [srv.submit(r) for r in reqs]
             for t in warm:
                 srv.wait(t)
+        run_open_loop(srv, reqs, poisson_arrivals(n_requests, max(load_list) * rps, seed + 999))
         res = []
         for load in load_list:
             arr = poisson_arrivals(n_requests, load * rps, seed + int(load * 100))
@@ -281,15 +284,16 @@ def measure_serving(n_requests=300, loads=(0.5, 0.8, 1.0, 1.2, 2.0), n_slots=4, 
                         "peak_in_flight": st["peak_in_flight"],
                         "graph_replays": st["graph_replays"],
                         "graph_captures": st["graph_captures"],
-                        "overflow_rerenders": st["overflow_rerenders"]})
+                        "overflow_rerenders": st["overflow_rerenders"],
+                        "batches": st["batches"], "batched_requests": st["batched_requests"]})
         srv.close()
         return res
 
-    out = sweep(True, loads)
-    # the same server with every request at one stream priority
-    flat = sweep(False, [l for l in loads if l <= 1.2])
+    out = sweep(4, loads)
+    # the same server without batching
+    single = sweep(1, loads)
     return {"one_request_per_launch": base, "one_request_per_launch_open_loop": base_open,
-            "server": out, "server_one_priority": flat,
+            "server": out, "server_no_batching": single,
             "n_slots": n_slots,
             "requests_per_load": n_requests,
             "mix": "25% each pinhole 1920x1080, fisheye 1280x960, LiDAR 64x1024, LiDAR 128x2048; "

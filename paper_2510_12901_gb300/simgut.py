@@ -61,7 +61,7 @@ class sg_camera_view(C.Structure):
 class sg_server_config(C.Structure):
     _fields_ = [("n_slots", C.c_int), ("memory_budget", C.c_size_t),
                 ("queue_capacity", C.c_int), ("use_graphs", C.c_int),
-                ("fifo_priority", C.c_int)]
+                ("fifo_priority", C.c_int), ("max_batch", C.c_int)]
 
 
 class sg_request(C.Structure):
@@ -74,7 +74,9 @@ class sg_server_report(C.Structure):
     _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("rays", C.c_int64),
                 ("peak_in_flight", C.c_int64), ("queued", C.c_int64),
                 ("graph_replays", C.c_int64), ("graph_captures", C.c_int64),
-                ("overflow_rerenders", C.c_int64), ("latency_mean_ms", C.c_double), ("latency_p50_ms", C.c_double),
+                ("overflow_rerenders", C.c_int64), ("batches", C.c_int64),
+                ("batched_requests", C.c_int64), ("latency_mean_ms", C.c_double),
+                ("latency_p50_ms", C.c_double),
                 ("latency_p99_ms", C.c_double), ("latency_max_ms", C.c_double),
                 ("span_s", C.c_double), ("mrays_per_s", C.c_double)]
 

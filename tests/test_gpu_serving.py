@@ -1,6 +1,7 @@
 """The request server: requests that arrive while others run are admitted as
-slots and memory free up, run concurrently on separate streams, and each
-result equals the same request rendered alone (bit for bit: the forward
+slots and memory free up, run concurrently on separate streams (waiting
+requests of the same combination batched into one launch sequence), and
+each result equals the same request rendered alone (bit for bit: the forward
 pass is deterministic)."""
 import numpy as np
 import pytest
@@ -46,15 +47,17 @@ def alone(W):
     return out
 
 
-@pytest.mark.parametrize("graphs", [False, True])
-def test_results_identical_alone_and_in_the_mix(W, alone, graphs):
+@pytest.mark.parametrize("graphs,max_batch", [(False, 1), (True, 1), (False, 4), (True, 4)])
+def test_results_identical_alone_and_in_the_mix(W, alone, graphs, max_batch):
     """Three bursts of the whole request stream.  With graphs, the first
-    request of each combination on a slot renders exactly, the second
-    captures, the rest replay; every result must equal the alone render."""
+    batch of each combination on a slot renders exactly, the second
+    captures, the rest replay; with batching, requests of one combination
+    that wait together render as one batch.  Every result must equal the
+    alone render."""
     import torch
     from paper_2510_12901_gb300 import serve
     n = len(W.kinds)
-    srv = serve.Server(n_slots=4, use_graphs=graphs)
+    srv = serve.Server(n_slots=4, use_graphs=graphs, max_batch=max_batch)
     for burst in range(3):
         mixed = [_outs(W, i) for i in range(n)]
         tickets = [srv.submit(W.request(i, outs=mixed[i])) for i in range(n)]
@@ -67,9 +70,16 @@ def test_results_identical_alone_and_in_the_mix(W, alone, graphs):
     srv.close()
     assert st["completed"] == 3 * n and st["failed"] == 0
     assert st["peak_in_flight"] > 1            # requests really overlapped
+    if max_batch > 1:                          # bursts queue up: batches form
+        assert st["batches"] > 0 and st["batched_requests"] >= 2 * st["batches"]
+    else:
+        assert st["batches"] == 0
     assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
     if graphs:
-        assert st["graph_captures"] >= 8 and st["graph_replays"] >= n
+        # one graph per slot, combination and batch size: with batching,
+        # three bursts capture many and replay a few of them
+        assert st["graph_captures"] >= 8
+        assert st["graph_replays"] >= (n if max_batch == 1 else 1)
         assert st["overflow_rerenders"] == 0
     else:
         assert st["graph_captures"] == 0 and st["graph_replays"] == 0

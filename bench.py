@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the LiDAR sweep and differentiable-step measurements")
+    ap.add_argument("--stream-sets", type=int, default=1, choices=[1, 2],
+                    help="stream (and output) sets the steps alternate between: 2 lets a step's "
+                         "front stages start while the previous step's compositing runs")
     ap.add_argument("--only", choices=["lidar", "serving"], default=None,
                     help="run one extra workload alone (for profiling) and print its line")
 
@@ -184,11 +187,13 @@ def run_ours(args):
     S = sg.Scene(sc)
     cams = [(sg.Camera(fish), fish), (sg.Camera(pin), pin)]
     rays_per_step = sum(c.width * c.height for _, c in cams)
-    outs = []
-    for _, c in cams:
-        outs.append([torch.empty((c.height, c.width, 3), device="cuda"),
-                     torch.empty((c.height, c.width), device="cuda"),
-                     torch.empty((c.height, c.width), device="cuda")])
+    nset = args.stream_sets
+    out_sets = []
+    for _ in range(nset):
+        out_sets.append([[torch.empty((c.height, c.width, 3), device="cuda"),
+                          torch.empty((c.height, c.width), device="cuda"),
+                          torch.empty((c.height, c.width), device="cuda")] for _, c in cams])
+    outs = out_sets[0]
     opts = sg.sg_default_opts()
     # two frame sets, alternated, so that the stage events of step i can be
     # read once step i+1 has passed its own mid-render synchronisation
@@ -200,23 +205,29 @@ def run_ours(args):
     sp = stream.cuda_stream
     # the two views of a step are one sg_render_cameras call, each view on
     # its own stream (a camera rig rendered per frame)
-    vstreams = [torch.cuda.Stream() for _ in cams]
+    # with two sets, step i uses stream set i % 2 (and output set i % 2), so
+    # that step i+1's front stages can run while step i's compositing does
+    vsets = [[torch.cuda.Stream() for _ in cams] for _ in range(nset)]
+    vstreams = vsets[0]
     views = [sg.sg_camera_views([(ch.handle, c.c2w, f.handle, o[0].data_ptr(), o[1].data_ptr(),
                                   o[2].data_ptr(), vs.cuda_stream)
-                                 for (ch, c), o, f, vs in zip(cams, outs, fs, vstreams)])
-             for fs in frames]
+                                 for (ch, c), o, f, vs in zip(cams, out_sets[k % nset], fs,
+                                                              vsets[k % nset])])
+             for k, fs in enumerate(frames)]
 
     def fork():          # the view streams start after the work queued on `stream`
         ev = torch.cuda.Event()
         ev.record(stream)
-        for vs in vstreams:
-            vs.wait_event(ev)
+        for vset in vsets:
+            for vs in vset:
+                vs.wait_event(ev)
 
     def join():          # `stream` continues once every view stream is done
-        for vs in vstreams:
-            ev = torch.cuda.Event()
-            ev.record(vs)
-            stream.wait_event(ev)
+        for vset in vsets:
+            for vs in vset:
+                ev = torch.cuda.Event()
+                ev.record(vs)
+                stream.wait_event(ev)
 
     def step(i):
         sg.sg_render_cameras(S.handle, views[i % 2], opts, 0)
@@ -364,6 +375,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "gaussians": N_GAUSS,
                        "rays_per_step": rays_per_step, "parallelism": "replicas",
                        "views": "one sg_render_cameras call per step, each view on its own stream",
+                       "stream_sets": nset,
                        "pair_counts": "exact (the host waits for each view's pair count)",
                        "frames": "forward only (sg_frame_set_backward_state 0: no per-ray "
                                  "state for a backward is written)",

@@ -660,7 +660,7 @@ def roofline(per_view, union_ms, seq_view, clocks):
     sms = sm_count()
     peak_tflops = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     render_ms = per_view[:, 3]
-    out = {"kernel": "k_render_camera", "bound": "alu", "peak": peak_tflops,
+    out = {"kernel": "k_render_camera_fwd", "bound": "alu", "peak": peak_tflops,
            "unit": "TFLOP/s",
            "peak_source": f"derived: {sms} SMs (queried from the device) x {FP32_LANES} FP32 "
                           f"lanes x 2 flop/FMA x "
@@ -686,7 +686,7 @@ def roofline(per_view, union_ms, seq_view, clocks):
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
         if tr.get("source_sha256") == kernel_source_hash():
-            out["traffic"] = tr.get("k_render_camera")
+            out["traffic"] = tr.get("k_render_camera_fwd")
             out["traffic_note"] = ("dram bytes per launch, mean of the fisheye and pinhole launches "
                                    "(ncu), profiles/")
             out["traffic_per_view"] = tr.get("per_view")
@@ -698,7 +698,7 @@ def roofline(per_view, union_ms, seq_view, clocks):
     return out
 
 
-KERNEL_SOURCES = ("render.cu", "pairs.cuh", "render.cuh")
+KERNEL_SOURCES = ("render_fwd.cu", "pairs.cuh", "render.cuh")
 
 
 def kernel_source_hash(read=None):

@@ -203,6 +203,11 @@ void sg_frame_destroy(sg_frame frame);
  * serving) can turn it off (0) and save that memory traffic;
  * sg_backward_* then refuses the frame's renders (SG_ERR_INVALID), and
  * the SG_FIELD_RAY_STATE / SG_FIELD_N_CONTRIB fields are not updated.
+ * Camera renders of such a frame use a compositing kernel that tracks no
+ * backward state and parameterises each ray in its tile's tangent plane
+ * (fewer operations per ray-Gaussian pair): its images equal the
+ * state-keeping kernel's up to float rounding, not bit for bit, and are
+ * deterministic from one render to the next.
  * Errors: SG_ERR_INVALID (NULL frame). */
 sg_status sg_frame_set_backward_state(sg_frame frame, int keep);
 

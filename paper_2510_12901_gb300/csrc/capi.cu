@@ -549,6 +549,8 @@ sg_status sg_create_camera(int model, int width, int height, float fx, float fy,
     if (s != SG_OK) {
         dev_free(c.d_pix);
         dev_free(c.d_tile_dir);
+        dev_free(c.d_pix2);
+        dev_free(c.d_tile_basis);
         delete h;
         return s;
     }
@@ -562,6 +564,8 @@ void sg_destroy_camera(sg_camera cam)
     cudaDeviceSynchronize();   // renders still queued may read its ray tables
     dev_free(cam->c.d_pix);
     dev_free(cam->c.d_tile_dir);
+    dev_free(cam->c.d_pix2);
+    dev_free(cam->c.d_tile_basis);
     delete cam;
 }
 

@@ -118,6 +118,14 @@ struct Camera {
     // (w = 1 valid, 0 no ray); per tile: reference direction (double)
     float4 *d_pix = nullptr;
     double *d_tile_dir = nullptr;  // [ntiles*3]
+    // per pixel: tangent-plane coordinates (u1, u2) of the direction over its
+    // cosine to the tile's reference direction, that length |d'|, valid;
+    // per tile: the tangent basis e1, e2 (camera frame, float [ntiles*6]).
+    // tangent_ok: every valid pixel is within 75 degrees of its tile's
+    // reference direction (|d'| <= 4), which the forward-only kernel assumes.
+    float4 *d_pix2 = nullptr;
+    float *d_tile_basis = nullptr;
+    bool tangent_ok = false;
 };
 
 struct LidarItem {       // one warp of LiDAR rendering
@@ -366,6 +374,17 @@ sg_status project_lidar(const Scene &sc, const Lidar &L, const sg_render_opts &o
 
 // render.cu
 sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, cudaStream_t st);
+// render_fwd.cu: the compositing of frames that keep no backward state
+// (two rays per lane, tangent-plane rays); render_camera dispatches to it
+// when camera_forward_only holds.
+bool camera_forward_only(const Camera &cam, const Frame &fr);
+sg_status render_camera_fwd(const Camera &cam, const sg_render_opts &o, Frame &fr,
+                            cudaStream_t st);
+// render.cu: the compositing's work items (k_work_items, k_emit_items) of
+// n_units units with `subs` sub-units each, in the camwork layout of ws.
+
+sg_status launch_work_items(Frame &fr, const WorkSize &ws, const LidarItem *unit_tile,
+                            int n_units, int subs, uint32_t seg_len, cudaStream_t st);
 // rolling shutter: the RenderDesc's poses are per pixel row
 sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr,
                            cudaStream_t st);

@@ -179,35 +179,10 @@ __global__ void k_emit_items(const uint32_t *__restrict__ order,
     if (ui.x > 1 && lane < subs) arrive[ui.y * subs + lane] = 0u;
 }
 
-// Deferred re-walks of the compositing (scalars[7] of them): (unit, work
-// code, lane mask, 0), the work code as in the work items.
-struct FixList {
-    uint4 *fix;
-    uint32_t *n_fix;
-    uint32_t cap;
-};
-
-__device__ __forceinline__ void push_fix(const FixList &F, uint32_t unit, uint32_t code,
-                                         uint32_t lanes)
-{
-    if ((threadIdx.x & 31) == 0) {
-        const uint32_t k = atomicAdd(F.n_fix, 1u);
-        if (k < F.cap) F.fix[k] = make_uint4(unit, code, lanes, 0u);   // < cap by construction
-    }
-}
-
-// The deferred re-walks' list in the frame's camwork buffer laid out by ws.
-static FixList fix_list(Frame &fr, const WorkSize &ws)
-{
-    unsigned char *cw = (unsigned char *)fr.camwork.p;
-    return {(uint4 *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes + ws.arrive_bytes),
-            (uint32_t *)fr.scalars.p + 7, (uint32_t)ws.max_fixes};
-}
-
 // Launch both: the work items of `n_units` units into the frame's camwork
 // buffer laid out by ws.
-static sg_status launch_work_items(Frame &fr, const WorkSize &ws, const LidarItem *unit_tile,
-                                   int n_units, int subs, uint32_t seg_len, cudaStream_t st)
+sg_status launch_work_items(Frame &fr, const WorkSize &ws, const LidarItem *unit_tile,
+                            int n_units, int subs, uint32_t seg_len, cudaStream_t st)
 {
     unsigned char *cw = (unsigned char *)fr.camwork.p;
     uint2 *unit_info = (uint2 *)cw;
@@ -493,6 +468,7 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
         set_error("internal: camera list segment length %u not compiled", fr.seg_len);
         return SG_ERR_INVALID;
     }
+    if (camera_forward_only(cam, fr)) return render_camera_fwd(cam, o, fr, st);
     const CamRender P = cam_render_params(cam, o);
     const int nt = cam.ntx * cam.nty;
     const int64_t K = fr.n_pairs;

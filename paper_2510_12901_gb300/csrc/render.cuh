@@ -1,5 +1,5 @@
 // render.cuh -- launch parameters and per-ray set-up shared by the forward
-// (render.cu) and backward (backward.cu) kernels.
+// (render.cu, render_fwd.cu) and backward (backward.cu) kernels.
 #pragma once
 
 #include "internal.h"
@@ -82,6 +82,31 @@ __device__ __forceinline__ void cam_ray_offset(const CamPose &P, const float4 e,
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i) dd[i] = P.R[3 * i] * e.x + P.R[3 * i + 1] * e.y + P.R[3 * i + 2] * e.z;
+}
+
+// Deferred re-walks of the compositing (scalars[7] of them): (unit, work
+// code, lane mask, 0), the work code as in the work items.
+struct FixList {
+    uint4 *fix;
+    uint32_t *n_fix;
+    uint32_t cap;
+};
+
+__device__ __forceinline__ void push_fix(const FixList &F, uint32_t unit, uint32_t code,
+                                         uint32_t lanes)
+{
+    if ((threadIdx.x & 31) == 0) {
+        const uint32_t k = atomicAdd(F.n_fix, 1u);
+        if (k < F.cap) F.fix[k] = make_uint4(unit, code, lanes, 0u);   // < cap by construction
+    }
+}
+
+// The deferred re-walks' list in the frame's camwork buffer laid out by ws.
+inline FixList fix_list(Frame &fr, const WorkSize &ws)
+{
+    unsigned char *cw = (unsigned char *)fr.camwork.p;
+    return {(uint4 *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes + ws.arrive_bytes),
+            (uint32_t *)fr.scalars.p + 7, (uint32_t)ws.max_fixes};
 }
 
 }  // namespace sg

@@ -105,10 +105,19 @@ __global__ void k_camera_dirs(int model, int W, int H, double fx, double fy, dou
     valid[p] = ok;
 }
 
+// Smallest cosine between a pixel's direction and its tile's reference
+// direction for which the tangent-plane table is used (|d'| <= 4).
+constexpr double kTangentMinCos = 0.25;
+
 // One block per tile: reference direction = normalised mean of the tile's
-// valid pixel directions; each pixel stores its offset from it.
+// valid pixel directions; each pixel stores its offset from it.  Also the
+// tile's tangent basis (e1 normal to the reference direction and to the
+// coordinate axis least aligned with it, e2 = reference x e1) and each
+// pixel's direction over its cosine to the reference, in that basis; `far`
+// is set when a cosine is below kTangentMinCos.
 __global__ void k_camera_tile_ref(int W, int H, int ntx, const double *dirs,
-                                  const unsigned char *valid, double *tile_dir, float4 *pix)
+                                  const unsigned char *valid, double *tile_dir, float4 *pix,
+                                  float *tile_basis, float4 *pix2, int *far)
 {
     __shared__ double red[3][kCamThreads];
     int t = blockIdx.x;
@@ -138,6 +147,34 @@ __global__ void k_camera_tile_ref(int W, int H, int ntx, const double *dirs,
         pix[p] = ok ? make_float4((float)(dirs[3 * p] - r0), (float)(dirs[3 * p + 1] - r1),
                                   (float)(dirs[3 * p + 2] - r2), 1.0f)
                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    const double a0 = fabs(r0), a1 = fabs(r1), a2 = fabs(r2);
+    const double x0 = (a0 <= a1 && a0 <= a2) ? 1.0 : 0.0;
+    const double x1 = x0 == 0.0 && a1 <= a2 ? 1.0 : 0.0;
+    const double x2 = x0 == 0.0 && x1 == 0.0 ? 1.0 : 0.0;
+    double e10 = x1 * r2 - x2 * r1, e11 = x2 * r0 - x0 * r2, e12 = x0 * r1 - x1 * r0;
+    const double ne = sqrt(e10 * e10 + e11 * e11 + e12 * e12);
+    e10 /= ne; e11 /= ne; e12 /= ne;
+    const double e20 = r1 * e12 - r2 * e11, e21 = r2 * e10 - r0 * e12, e22 = r0 * e11 - r1 * e10;
+    if (threadIdx.x == 0) {
+        float *b = tile_basis + 6 * t;
+        b[0] = (float)e10; b[1] = (float)e11; b[2] = (float)e12;
+        b[3] = (float)e20; b[4] = (float)e21; b[5] = (float)e22;
+    }
+    if (in) {
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok) {
+            const double d0 = dirs[3 * p], d1 = dirs[3 * p + 1], d2 = dirs[3 * p + 2];
+            const double c = d0 * r0 + d1 * r1 + d2 * r2;
+            if (!(c >= kTangentMinCos)) {
+                atomicOr(far, 1);
+            } else {
+                q = make_float4((float)((d0 * e10 + d1 * e11 + d2 * e12) / c),
+                                (float)((d0 * e20 + d1 * e21 + d2 * e22) / c), (float)(1.0 / c),
+                                1.0f);
+            }
+        }
+        pix2[p] = q;
+    }
 }
 
 sg_status build_camera(Camera &cam)
@@ -149,26 +186,36 @@ sg_status build_camera(Camera &cam)
     int64_t nt = (int64_t)cam.ntx * cam.nty;
     double *dirs = nullptr;
     unsigned char *valid = nullptr;
+    int *far = nullptr;
     if (dev_malloc(&dirs, sizeof(double) * 3 * np) != cudaSuccess ||
-        dev_malloc(&valid, np) != cudaSuccess ||
+        dev_malloc(&valid, np) != cudaSuccess || dev_malloc(&far, sizeof(int)) != cudaSuccess ||
         dev_malloc(&cam.d_pix, sizeof(float4) * np) != cudaSuccess ||
-        dev_malloc(&cam.d_tile_dir, sizeof(double) * 3 * nt) != cudaSuccess) {
+        dev_malloc(&cam.d_tile_dir, sizeof(double) * 3 * nt) != cudaSuccess ||
+        dev_malloc(&cam.d_pix2, sizeof(float4) * np) != cudaSuccess ||
+        dev_malloc(&cam.d_tile_basis, sizeof(float) * 6 * nt) != cudaSuccess) {
         dev_free(dirs);
         dev_free(valid);
+        dev_free(far);
         set_error("sg_create_camera: device allocation failed");
         return SG_ERR_OOM;
     }
+    cudaMemset(far, 0, sizeof(int));
     k_camera_dirs<<<(unsigned)((np + 255) / 256), 256>>>(
         cam.model, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, cam.k[0], cam.k[1],
         cam.k[2], cam.k[3], cam.theta_max, dirs, valid);
     count_launch();
     k_camera_tile_ref<<<(unsigned)nt, kCamThreads>>>(cam.width, cam.height, cam.ntx, dirs,
-                                                     valid, cam.d_tile_dir, cam.d_pix);
+                                                     valid, cam.d_tile_dir, cam.d_pix,
+                                                     cam.d_tile_basis, cam.d_pix2, far);
     count_launch();
     cudaError_t e = cudaDeviceSynchronize();
+    int h_far = 1;
+    if (e == cudaSuccess) e = cudaMemcpy(&h_far, far, sizeof(int), cudaMemcpyDeviceToHost);
     dev_free(dirs);
     dev_free(valid);
+    dev_free(far);
     if (e != cudaSuccess) return cuda_status(e, "camera ray table");
+    cam.tangent_ok = h_far == 0;
     return SG_OK;
 }
 

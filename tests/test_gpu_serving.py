@@ -34,11 +34,13 @@ def _outs(W, i):
 
 @pytest.fixture(scope="module")
 def alone(W):
-    """Every request rendered alone through the plain render call."""
+    """Every request rendered alone through the plain render call, into a
+    frame that keeps no backward state, as the server's frames."""
     import torch
     from paper_2510_12901_gb300 import simgut as sg
     out = []
     fr = sg.Frame()
+    sg.sg_frame_set_backward_state(fr.handle, 0)
     for i in range(len(W.kinds)):
         o = _outs(W, i)
         W.render_plain(i, fr, torch.cuda.current_stream().cuda_stream, outs=o)
@@ -145,6 +147,7 @@ def test_graph_replay_that_outgrows_its_capacity_is_rendered_exactly():
 
     alone = []
     fr = sg.Frame()
+    sg.sg_frame_set_backward_state(fr.handle, 0)      # as the server's frames
     st = torch.cuda.current_stream().cuda_stream
     for p in poses:
         o = outs()

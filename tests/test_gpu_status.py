@@ -164,7 +164,9 @@ def test_server_request_fails_with_timeout_and_the_next_one_succeeds(sg, hook):
     from paper_2510_12901_gb300 import serve
     sc, cam = _scene(sg)
     S, C = sg.Scene(sc), sg.Camera(cam)
-    ref = _render(sg, S, C, cam, sg.Frame())
+    fr = sg.Frame()
+    sg.sg_frame_set_backward_state(fr.handle, 0)      # as the server's frames
+    ref = _render(sg, S, C, cam, fr)
     outs = [torch.zeros((cam.height, cam.width, 3), device="cuda"),
             torch.zeros((cam.height, cam.width), device="cuda"),
             torch.zeros((cam.height, cam.width), device="cuda")]

@@ -290,10 +290,15 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
         fr.lmask_stride = K;
         s = lidar_tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err, pv[pb],
                               (const float4 *)fr.rect.p, L, (uint32_t *)fr.lmask.p);
-    } else {   // camera lists also get their sub-block masks
-        if ((s = ensure(fr.submask, K > 0 ? (size_t)K : 1)) != SG_OK) return s;
+    } else {   // camera lists also get their sub-block masks (column/row words
+               // for the forward-only compositing)
+        const bool words = fr.kind == 0 &&
+            camera_forward_only(static_cast<const sg_camera_s *>(fr.sensor)->c, fr);
+        const size_t by = (words ? 4 : 1) * (size_t)(K > 0 ? K : 1);
+        if ((s = ensure(fr.submask, by)) != SG_OK) return s;
         s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err, pv[pb],
-                        (const float4 *)fr.rect.p, ntx, (uint8_t *)fr.submask.p);
+                        (const float4 *)fr.rect.p, ntx, words ? nullptr : (uint8_t *)fr.submask.p,
+                        words ? (uint32_t *)fr.submask.p : nullptr);
     }
     if (s != SG_OK) return s;
     if (fr.k_cap > 0)   // counts, dropped pairs and the status word, for the caller
@@ -994,8 +999,8 @@ sg_status sg_workspace_bytes(sg_scene scene, int sensor_kind, int64_t n_rays, si
     // per ray: state, features, contributor count; per unit: ranges, order
     b += grown(16 * (size_t)nr) * 2 + grown(4 * (size_t)nr);
     b += grown(8 * (size_t)units) + grown(4 * (size_t)units);
-    // pairs: keys and ids (x2), camera sub-block masks or LiDAR ray masks
-    b += 4 * grown(4 * (size_t)K) + (cam ? grown((size_t)K) : grown(4 * (size_t)K * per_tile));
+    // pairs: keys and ids (x2), camera column/row masks or LiDAR ray masks
+    b += 4 * grown(4 * (size_t)K) + grown(4 * (size_t)K * per_tile);
     // sort scratch: the larger of the depth stage's and the tile sort's
     const int64_t hd = depth_stage_words(n), ht = radix_scratch_words(K, 3);
     b += grown(4 * (size_t)(hd > ht ? hd : ht));

@@ -133,23 +133,35 @@ __device__ __forceinline__ void fwd_composite(const CamRender &P, float4 (*s)[32
     }
 }
 
+// The lanes of 8x4 sub-block `sub` whose pixel centres lie in an entry's
+// box, from the entry's word of tile columns and rows in the box (bits 0-15:
+// the tile's columns, 16-31: its rows; written with the tile ranges by the
+// same float comparisons as the per-ray test): the sub-block's 8 column bits
+// in every byte, a byte kept where the sub-block's row is in the box (the
+// multiply by 0x00204081 moves bit r of the 4 row bits to bit 8 r).
+__device__ __forceinline__ uint32_t word_lanes(uint32_t cr, int sub)
+{
+    const uint32_t cols = (cr >> (8 * (sub & 1))) & 0xffu;
+    const uint32_t rows = (cr >> (16 + 4 * (sub >> 1))) & 0xfu;
+    return (cols * 0x01010101u) & ((((rows * 0x00204081u) & 0x01010101u)) * 0xffu);
+}
+
 // Composite list entries [lo, hi) of a tile that can reach sub-block `sub`
-// (first pixel sbx, sby) into the lane's accumulator.  Lanes whose ray is
-// done take part in the staging and keep their state; rays = the lanes with a
-// ray.
+// into the lane's accumulator.  Lanes whose ray is done take part in the
+// staging and keep their state; only entries whose box holds a live ray are
+// staged (their lane masks come from the column/row words, no record load).
 __device__ __forceinline__ void fwd_walk(const CamRender &P, const CamPose &pose,
                                          const GRec *__restrict__ rec,
                                          const uint32_t *__restrict__ ids,
-                                         const uint8_t *__restrict__ submask, int sub, int sbx,
-                                         int sby, uint32_t lo, uint32_t hi, const float *ref,
-                                         float x, float y, float4 (*s)[32], FwdAcc &a,
-                                         bool &done, uint32_t rays)
+                                         const uint32_t *__restrict__ crw, int sub, uint32_t lo,
+                                         uint32_t hi, const float *ref, float x, float y,
+                                         float4 (*s)[32], FwdAcc &a, bool &done)
 {
     const int lane = threadIdx.x & 31;
-    // the next batch's mask byte and Gaussian id, loaded one batch ahead
-    uint32_t nsm = 0u, nid = 0u;
+    // the next batch's column/row words and Gaussian ids, loaded one batch ahead
+    uint32_t ncr = 0u, nid = 0u;
     if (lo + lane < hi) {
-        nsm = submask[lo + lane];
+        ncr = crw[lo + lane];
         nid = ids[lo + lane];
     }
     for (uint32_t base = lo; base < hi; base += 32) {
@@ -157,29 +169,21 @@ __device__ __forceinline__ void fwd_walk(const CamRender &P, const CamPose &pose
         if (act == 0u) break;
         const uint32_t idx = base + lane;
         const uint32_t gid = nid;
-        bool ov = (nsm >> sub) & 1u;
+        const uint32_t lm = word_lanes(ncr, sub) & act;
         if (idx + 32 < hi) {
-            nsm = submask[idx + 32];
+            ncr = crw[idx + 32];
             nid = ids[idx + 32];
         } else {
-            nsm = 0u;
+            ncr = 0u;
         }
-        if (act != rays && ov) {
-            // some rays are done: stage only entries that reach a live one.
-            // The record's first bytes are prefetched into L1 with the box,
-            // so that staging does not wait for a second round trip.
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + gid));
-            ov = (subblock_lanes(rec[gid].rect, sbx, sby) & act) != 0u;
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, ov);
+        const uint32_t bal = __ballot_sync(0xffffffffu, lm != 0u);
         if (bal == 0u) continue;
         __syncwarp();
-        if (ov) {
+        if (lm) {
             const int pos = __popc(bal & ((1u << lane) - 1u));
-            const GRec r = rec[gid];
             float4 e[7];
-            fwd_entry(r, pose.t, ref, e);
-            e[6].y = __uint_as_float(subblock_lanes(r.rect, sbx, sby) & act);
+            fwd_entry(rec[gid], pose.t, ref, e);
+            e[6].y = __uint_as_float(lm);
 #pragma unroll
             for (int k = 0; k < 7; ++k) s[k][pos] = e[k];
         }
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(32 * kFwdWarps, kFwdBlocks)
 k_render_camera_fwd(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
                     const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
                     const uint2 *__restrict__ tile_info, const uint32_t *__restrict__ counts,
-                    const uint8_t *__restrict__ submask, uint32_t *__restrict__ counter,
+                    const uint32_t *__restrict__ crw, uint32_t *__restrict__ counter,
                     uint32_t *__restrict__ arrive, float4 *__restrict__ partials,
                     const float4 *__restrict__ pix2, const double *__restrict__ tile_dir,
                     const float *__restrict__ tile_basis, const RenderDesc *__restrict__ D)
@@ -232,14 +236,12 @@ k_render_camera_fwd(CamRender P, const GRec *__restrict__ rec, const uint32_t *_
         const int64_t pidx = inside ? (int64_t)py * P.W + px : -1;
         const float4 e = inside ? pix2[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool no_ray = !(inside && e.w > 0.f);
-        const uint32_t rays = __ballot_sync(0xffffffffu, !no_ray);
         const uint2 rg = ranges[tile];
         const uint32_t lo = rg.x + (uint32_t)seg * kSeg;
         const uint32_t hi = min(rg.y, lo + kSeg);
         FwdAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool done = no_ray;
-        fwd_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, lo, hi, s_ref, e.x, e.y, s_e, a,
-                 done, rays);
+        fwd_walk(P, s_pose, rec, ids, crw, sub, lo, hi, s_ref, e.x, e.y, s_e, a, done);
         if (ti.x > 1) {
             // long tile: publish this run, and combine if it is the last one
             fwd_put(partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2, a,
@@ -300,8 +302,8 @@ k_render_camera_fwd(CamRender P, const GRec *__restrict__ rec, const uint32_t *_
                 const bool mine = pend && stop_run == r;
                 bool dn = !mine;
                 const uint32_t l0 = rg.x + r * kSeg;
-                fwd_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, l0, min(rg.y, l0 + kSeg),
-                         s_ref, e.x, e.y, s_e, a, dn, rays);
+                fwd_walk(P, s_pose, rec, ids, crw, sub, l0, min(rg.y, l0 + kSeg), s_ref, e.x, e.y,
+                         s_e, a, dn);
                 pend = pend && !mine;
             }
         }
@@ -350,7 +352,7 @@ sg_status render_camera_fwd(const Camera &cam, const sg_render_opts &o, Frame &f
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
-    if (s == SG_OK && fr.submask.bytes < (size_t)(K > 0 ? K : 1)) {
+    if (s == SG_OK && fr.submask.bytes < 4 * (size_t)(K > 0 ? K : 1)) {
         set_error("internal: sub-block masks of the camera list missing");
         s = SG_ERR_INVALID;
     }
@@ -372,7 +374,7 @@ sg_status render_camera_fwd(const Camera &cam, const sg_render_opts &o, Frame &f
     if (grid < 1) grid = 1;
     k_render_camera_fwd<kSegLen><<<(unsigned)grid, 32 * kFwdWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
-        (const uint8_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix2,
+        (const uint32_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix2,
         cam.d_tile_dir, cam.d_tile_basis, (const RenderDesc *)fr.desc.p);
     SG_LAUNCHED();
     return SG_OK;

@@ -239,6 +239,15 @@ static sg_status sort_and_count(Frame &fr, int64_t n, cudaStream_t st)
     return SG_OK;
 }
 
+// The message of a non-zero device status word (kStatus* bits).
+static const char *status_cause(uint32_t w)
+{
+    if ((w & kStatusLookback) && (w & kStatusBulkCopy))
+        return "a look-back wait of the sort and a bulk-copy wait of the projection gave up";
+    if (w & kStatusBulkCopy) return "a bulk-copy wait of the projection gave up";
+    return "a look-back wait of the sort gave up";
+}
+
 // bin_and_sort: waits for the pair count (exact mode), which sizes the pair
 // buffers, then binning, tile sort and ranges; in capacity mode nothing
 // waits and the scalars are copied to h_scalars at the end for the caller
@@ -253,7 +262,8 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
     } else {
         SG_CUDA(cudaEventSynchronize(fr.ev_count));
         if (fr.h_scalars[kScalStatus]) {
-            set_error("a look-back wait of the depth sort gave up (device status word set)");
+            set_error("%s before the pair count (device status word set)",
+                      status_cause(fr.h_scalars[kScalStatus]));
             return SG_ERR_TIMEOUT;
         }
         K = fr.h_scalars[1];
@@ -857,7 +867,7 @@ sg_status sg_frame_sync_outputs(sg_frame frame)
     if (!f.copy_pending) return SG_OK;
     SG_CUDA(cudaEventSynchronize(f.ev_copied));
     if (f.h_scalars[kHostStatusOutputs]) {
-        set_error("a look-back wait of the sort gave up in the frame's last render");
+        set_error("%s in the frame's last render", status_cause(f.h_scalars[kHostStatusOutputs]));
         return SG_ERR_TIMEOUT;
     }
     return SG_OK;
@@ -874,7 +884,7 @@ sg_status sg_frame_status(sg_frame frame, void *stream)
                             cudaMemcpyDeviceToHost, st));
     SG_CUDA(cudaStreamSynchronize(st));
     if (f.h_scalars[kHostStatusQuery]) {
-        set_error("a look-back wait of the sort gave up in the frame's last render");
+        set_error("%s in the frame's last render", status_cause(f.h_scalars[kHostStatusQuery]));
         return SG_ERR_TIMEOUT;
     }
     return SG_OK;

@@ -256,13 +256,18 @@ uint64_t next_uid();            // identity of a scene / sensor handle
 constexpr size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Index of the status word in a frame's device scalars: non-zero once a
-// look-back wait of the sort stages has given up in the current render.  The
+// bounded device wait has given up in the current render (a look-back wait
+// of the sort stages, or the projection's wait for bulk copies).  The
 // projection kernel clears it at the start of every render.  Kernels after
 // the give-up stay in bounds: the binning and the tile ranges write nothing,
 // so every list is empty.  The host reads it with the pair count (exact
 // mode), with the scalars at the end of a capacity-mode render, and in
 // sg_frame_status / with host outputs.
 constexpr int kScalStatus = 8;
+// Bits of the status word: a look-back wait of a sort pass gave up; a
+// wait for the projection's bulk copies of feature planes gave up.
+constexpr uint32_t kStatusLookback = 1u;
+constexpr uint32_t kStatusBulkCopy = 2u;
 // Pinned-mirror slots (frame h_scalars) of the status word read after the
 // render: by sg_frame_status, and with the host-output copies.
 constexpr int kHostStatusQuery = 12, kHostStatusOutputs = 13;

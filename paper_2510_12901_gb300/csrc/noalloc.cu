@@ -184,7 +184,7 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     SG_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SG_CUDA(cudaStreamSynchronize(st));
     if (hs[kScalStatus]) {
-        set_error("sg_render_camera_static: a look-back wait of the depth sort gave up");
+        set_error("sg_render_camera_static: a bounded device wait (sort look-back or projection bulk copy) gave up");
         return SG_ERR_TIMEOUT;
     }
     const int64_t K = hs[1];

@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "tma.cuh"
 
 namespace sg {
 
@@ -131,9 +132,10 @@ __device__ __forceinline__ void write_record(GRec *rec, int64_t g, const Activat
 // Real spherical harmonics of degree <= 3 (normalised, Condon-Shortley
 // phase, m = -l..l order).  Constants: sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!),
 // times sqrt(2) for m != 0, times the leading factor of P_l^|m|.
-__device__ __forceinline__ void sh_eval(const float *__restrict__ planes, int64_t pitch,
-                                        int64_t g, int deg, float x, float y, float z,
-                                        float c[3])
+// base[(3 k + ch) stride]: coefficient k of channel ch (the Gaussian's entry
+// of the SH planes, in global memory or staged in shared memory).
+__device__ __forceinline__ void sh_eval(const float *__restrict__ base, int64_t stride, int deg,
+                                        float x, float y, float z, float c[3])
 {
     float Y[16];
     const float xx = x * x, yy = y * y, zz = z * z;
@@ -167,7 +169,7 @@ __device__ __forceinline__ void sh_eval(const float *__restrict__ planes, int64_
         float f[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            f[k] = k < nc ? planes[(Scene::kFeat + 3 * k + ch) * pitch + g] : 0.f;
+            f[k] = k < nc ? base[(3 * k + ch) * stride] : 0.f;
         float acc = 0.f;
 #pragma unroll
         for (int k = 0; k < 16; ++k) acc += k < nc ? Y[k] * f[k] : 0.f;
@@ -240,11 +242,29 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
                  uint32_t *__restrict__ status)
 {
     __shared__ float s_c2w[12];   // the pose, from the render's descriptor
+    // SH features: the block's run of every coefficient plane, [plane][thread],
+    // brought in by bulk copies (TMA) while the sigma points are projected
+    extern __shared__ float s_feat[];
+    __shared__ uint64_t s_bar;
+    const int n_stage =
+        feature_kind == SG_FEATURES_SH ? 3 * (sh_degree + 1) * (sh_degree + 1) : 0;
     if (threadIdx.x < 12) s_c2w[threadIdx.x] = D->c2w[threadIdx.x];
+    if (threadIdx.x == 0 && n_stage) mbar_init(&s_bar);
     __syncthreads();
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g == 0) *status = 0u;     // a new render: no look-back wait has given up
-    if (g >= n) return;
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+    if (threadIdx.x == 0 && n_stage) {
+        // planes are 128-byte aligned and pitch floats long (a multiple of
+        // 32), so each run starts 16-byte aligned and ends inside its plane
+        const int64_t run = pitch - g0 < (int64_t)blockDim.x ? pitch - g0 : (int64_t)blockDim.x;
+        const uint32_t bytes = 4u * (uint32_t)run;
+        mbar_arrive_expect(&s_bar, bytes * (uint32_t)n_stage);
+        for (int p = 0; p < n_stage; ++p)
+            bulk_copy_g2s(s_feat + p * blockDim.x, planes + (Scene::kFeat + p) * pitch + g0, bytes,
+                          &s_bar);
+    }
+    int64_t g = g0 + threadIdx.x;
+    if (g == 0) *status = 0u;     // a new render: no device wait has given up
+    if (g >= n) return;           // (thread 0 of a block always has a Gaussian)
     const float *poses = kRS ? D->poses : nullptr;
     Activated a = activate(planes, pitch, g);
     to_world(A, g, a);
@@ -314,13 +334,26 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     tiles_out[g] = tl;
     mean_out[g] = m2;
     cov_out[g] = cv;
-    if (count == 0) return;
+    if (count == 0) {
+        // the block's copies land before its last thread leaves
+        if (threadIdx.x == 0 && n_stage && !mbar_wait(&s_bar, 0)) {
+            atomicOr(status, kStatusBulkCopy);
+            mbar_wait(&s_bar, 0);
+        }
+        return;
+    }
     float c[3];
     if (feature_kind == SG_FEATURES_SH) {
+        if (!mbar_wait(&s_bar, 0)) {
+            // the copies did not land in time: the render reports it, and
+            // thread 0 waits once more before the block may exit
+            atomicOr(status, kStatusBulkCopy);
+            if (threadIdx.x == 0) mbar_wait(&s_bar, 0);
+        }
         float inv = 1.f / dist;
         float d[3] = {dx * inv, dy * inv, dz * inv};
         dir_to_actor(A, g, d);
-        sh_eval(planes, pitch, g, sh_degree, d[0], d[1], d[2], c);
+        sh_eval(s_feat + threadIdx.x, blockDim.x, sh_degree, d[0], d[1], d[2], c);
         for (int ch = 0; ch < 3; ++ch) c[ch] = fmaxf(c[ch] + 0.5f, 0.f);   // colour offset, clamp
     } else {
         for (int ch = 0; ch < 3; ++ch) c[ch] = planes[(Scene::kFeat + ch) * pitch + g];
@@ -345,7 +378,17 @@ sg_status project_camera(const Scene &sc, const Camera &cam, const sg_render_opt
     if (sc.n == 0) return SG_OK;
     unsigned grid = (unsigned)((sc.n + 255) / 256);
     auto kern = rolling ? k_project_camera<true> : k_project_camera<false>;
-    kern<<<grid, 256, 0, st>>>(
+    // shared memory for the SH planes the kernel stages (48 KB at degree 3)
+    const int n_stage =
+        sc.feature_kind == SG_FEATURES_SH ? 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1) : 0;
+    const size_t smem = sizeof(float) * 256 * (size_t)n_stage;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[rolling ? 1 : 0]) {
+        SG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(float) * 256 * 48)));
+        attr_set[rolling ? 1 : 0] = true;
+    }
+    kern<<<grid, 256, smem, st>>>(
         sc.d_planes, sc.pitch, sc.n, sc.feature_kind, sc.sh_degree, actor_params(sc), C,
         (const RenderDesc *)fr.desc.p, U, (GRec *)fr.rec.p,
         (float4 *)fr.rect.p, (int4 *)fr.tiles.p, (float *)fr.depth.p, (uint32_t *)fr.count.p,
@@ -657,7 +700,7 @@ k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int 
         const float inv = 1.f / sqrtf(vx * vx + vy * vy + vz * vz);
         float d[3] = {vx * inv, vy * inv, vz * inv}, c[3];
         dir_to_actor(A, g, d);
-        sh_eval(planes, pitch, g, sh_degree, d[0], d[1], d[2], c);
+        sh_eval(planes + Scene::kFeat * pitch + g, pitch, sh_degree, d[0], d[1], d[2], c);
         write_record(rec, g, a, c[0], c[1], c[2], rect, __uint_as_float((uint32_t)col0));
         return;
     }

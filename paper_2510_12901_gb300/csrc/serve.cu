@@ -240,7 +240,7 @@ static sg_status finish(const std::vector<sg_frame> &F, size_t B, cudaEvent_t ev
     for (size_t i = 0; i < B; ++i) {
         const Frame &fr = F[i]->f;
         if (fr.h_scalars[fr.k_cap == 0 ? kHostStatusQuery : kScalStatus]) {
-            set_error("a look-back wait of the sort gave up in this request's render");
+            set_error("a bounded device wait (sort look-back or projection bulk copy) gave up in this request's render");
             return SG_ERR_TIMEOUT;
         }
     }

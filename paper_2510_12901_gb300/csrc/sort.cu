@@ -195,7 +195,7 @@ k_onesweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ va
             if (pre) break;
             t -= took;
             if (took == 0 && ++spins > max_spins) {   // gave up: flag it, leave the order wrong
-                atomicOr(err, 1u);
+                atomicOr(err, kStatusLookback);
                 break;
             }
         }
@@ -305,7 +305,7 @@ __device__ unsigned long long chain_lookback(unsigned long long *lb, int64_t til
         if (fp < fnp) break;
         t -= take;
         if (take == 0 && ++spins > max_spins) {   // gave up: flag it
-            if (lane == 0) atomicOr(err, 1u);
+            if (lane == 0) atomicOr(err, kStatusLookback);
             break;
         }
     }

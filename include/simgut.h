@@ -273,6 +273,14 @@ enum {
     SG_LOOKBACK_TILE_SORT = 4    /* radix passes over the pairs' tile ids */
 };
 sg_status sg_debug_lookback(uint32_t max_spins, int hold_site, int64_t hold_tile);
+/* Testing hook for the device status path (not needed in normal use):
+ * give_up != 0 makes the camera projection's first wait for its bulk copies
+ * of SH planes give up at once (status word set, SG_ERR_TIMEOUT from the
+ * render); a second bounded wait still precedes every read of the staged
+ * planes, so the render stays in bounds.  0 restores the normal wait.  The
+ * value lives in the current device's memory; the call synchronises that
+ * device first.  Errors: SG_ERR_CUDA. */
+sg_status sg_debug_bulk_wait(int give_up);
 
 /* ----------------------------------------------------------------------
  * Forward render (Eq. 1: front-to-back compositing of alpha_i = sigma_i

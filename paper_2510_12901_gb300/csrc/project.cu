@@ -209,6 +209,24 @@ __device__ __forceinline__ bool cam_point(const CamParams &C, const float *c2w, 
     return true;
 }
 
+// Testing hook (sg_debug_bulk_wait): non-zero makes the projection's first
+// wait for its bulk copies give up at once, so that the status path runs;
+// the wait that follows (before any staged value is read and before the
+// block exits) keeps its full bound.  In device memory, so that replays of
+// captured launch sequences see it.
+__device__ uint32_t g_bulk_give_up = 0u;
+
+// The block's bulk copies: false if the first wait gave up (the status word
+// is then set and a second bounded wait follows).
+__device__ __forceinline__ void bulk_wait(uint64_t *bar, uint32_t *status)
+{
+    const bool forced = *(volatile uint32_t *)&g_bulk_give_up != 0u;
+    if (forced || !mbar_wait(bar, 0)) {
+        atomicOr(status, kStatusBulkCopy);
+        mbar_wait(bar, 0);
+    }
+}
+
 #ifndef SG_PROJ_MINB
 #define SG_PROJ_MINB 4
 #endif
@@ -336,20 +354,12 @@ k_project_camera(const float *__restrict__ planes, int64_t pitch, int64_t n, int
     cov_out[g] = cv;
     if (count == 0) {
         // the block's copies land before its last thread leaves
-        if (threadIdx.x == 0 && n_stage && !mbar_wait(&s_bar, 0)) {
-            atomicOr(status, kStatusBulkCopy);
-            mbar_wait(&s_bar, 0);
-        }
+        if (threadIdx.x == 0 && n_stage) bulk_wait(&s_bar, status);
         return;
     }
     float c[3];
     if (feature_kind == SG_FEATURES_SH) {
-        if (!mbar_wait(&s_bar, 0)) {
-            // the copies did not land in time: the render reports it, and
-            // thread 0 waits once more before the block may exit
-            atomicOr(status, kStatusBulkCopy);
-            if (threadIdx.x == 0) mbar_wait(&s_bar, 0);
-        }
+        bulk_wait(&s_bar, status);
         float inv = 1.f / dist;
         float d[3] = {dx * inv, dy * inv, dz * inv};
         dir_to_actor(A, g, d);
@@ -743,3 +753,11 @@ sg_status project_lidar(const Scene &sc, const Lidar &Ld, const sg_render_opts &
 }
 
 }  // namespace sg
+
+extern "C" sg_status sg_debug_bulk_wait(int give_up)
+{
+    const uint32_t v = give_up ? 1u : 0u;
+    SG_CUDA(cudaDeviceSynchronize());   // no kernel reads it meanwhile
+    SG_CUDA(cudaMemcpyToSymbol(sg::g_bulk_give_up, &v, sizeof(v)));
+    return SG_OK;
+}

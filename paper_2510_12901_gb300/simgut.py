@@ -146,6 +146,7 @@ _SIGNATURES = {
     "sg_workspace_bytes": (C.c_int, [_H, C.c_int, C.c_int64, C.POINTER(C.c_size_t)]),
     "sg_frame_workspace_bytes": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
     "sg_debug_lookback": (C.c_int, [C.c_uint32, C.c_int, C.c_int64]),
+    "sg_debug_bulk_wait": (C.c_int, [C.c_int]),
 }
 
 _lib = None
@@ -426,6 +427,10 @@ def sg_frame_workspace_bytes(frame):
 
 def sg_debug_lookback(max_spins=0, hold_site=LOOKBACK_NONE, hold_tile=-1):
     _check(load().sg_debug_lookback(max_spins, hold_site, hold_tile))
+
+
+def sg_debug_bulk_wait(give_up):
+    _check(load().sg_debug_bulk_wait(1 if give_up else 0))
 
 
 def sg_frame_marks(frame, ref):

@@ -220,3 +220,30 @@ def test_workspace_estimate_bounds_the_frame(sg):
         assert est < 4 * have + (64 << 20), (kind, have, est)   # and not absurdly loose
     with pytest.raises(sg.SimgutError):
         sg.sg_workspace_bytes(S.handle, 7, 100)
+
+
+def test_projection_bulk_copy_wait_reports_timeout(sg):
+    """The camera projection stages the SH planes by bulk copies and waits for
+    them with a bounded wait.  The hook makes the first wait give up at once:
+    the render must report SG_ERR_TIMEOUT naming the bulk copy (a second,
+    full wait still precedes every read, so nothing runs out of bounds), and
+    the next render, hook off, equals one made before."""
+    import torch
+    sc = syn.street_scene(60000, seed=3, kind="camera")       # degree-3 SH features
+    _, cam = syn.street_cameras()
+    S, C = sg.Scene(sc), sg.Camera(cam)
+    for forward_only in (False, True):
+        fr = sg.Frame()
+        if forward_only:
+            sg.sg_frame_set_backward_state(fr.handle, 0)
+        ref = _render(sg, S, C, cam, fr)
+        assert ref["alpha"].max() > 0.5
+        sg.sg_debug_bulk_wait(True)
+        try:
+            with pytest.raises(sg.SimgutError) as e:
+                _render(sg, S, C, cam, fr)
+        finally:
+            sg.sg_debug_bulk_wait(False)
+        assert e.value.status == TIMEOUT and "bulk-copy" in str(e.value)
+        assert _same(_render(sg, S, C, cam, fr), ref)
+        sg.sg_frame_status(fr.handle, torch.cuda.current_stream().cuda_stream)

@@ -298,7 +298,7 @@ constexpr WorkSize work_size(int64_t units, int64_t n_pairs, uint32_t seg_len, i
     const int64_t items1 = w.max_items > 0 ? w.max_items : 1;
     const int64_t slots1 = w.max_slots > 0 ? w.max_slots : 1;
     w.info_bytes = al256(8 * (size_t)u1);
-    w.off_bytes = al256(4 * (size_t)u1);
+    w.off_bytes = al256(4 * (size_t)(u1 > 128 ? u1 : 128));   // >= the work-item scratch
     w.items_bytes = al256(8 * (size_t)items1);
     w.arrive_bytes = al256(4 * (size_t)subs * (size_t)slots1);
     // deferred re-walks: at most one per (split unit, sub-unit, segment >= 1)
@@ -385,7 +385,7 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
 bool camera_forward_only(const Camera &cam, const Frame &fr);
 sg_status render_camera_fwd(const Camera &cam, const sg_render_opts &o, Frame &fr,
                             cudaStream_t st);
-// render.cu: the compositing's work items (k_work_items, k_emit_items) of
+// render.cu: the compositing's work items (k_work_count, k_work_emit) of
 // n_units units with `subs` sub-units each, in the camwork layout of ws.
 
 sg_status launch_work_items(Frame &fr, const WorkSize &ws, const LidarItem *unit_tile,

@@ -76,126 +76,122 @@ __device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t *s
 // first.  A unit whose list is longer than seg_len entries is split along
 // the list into ceil(len / seg_len) segments; every (unit, segment) gives
 // `subs` work items (the eight 8x4 sub-blocks of a camera tile, or one).
-// k_work_items (one CTA) orders the units and assigns per unit (segments,
-// first partial slot) and its first work item; k_emit_items (one warp per
-// unit) writes the work items (unit, subs * seg + sub) and resets the
-// arrival counters of split units.  The work counter of the compositing
-// kernel is reset here too.
+// Two grid-wide kernels build them: k_work_count sums the work items of each
+// length bucket (32 - floor(log2 len), longest first) and of the split
+// units' partial slots, and its last block turns the bucket sums into the
+// buckets' first items; k_work_emit (a warp per unit) takes its unit's run of
+// items within its bucket and its first partial slot from atomic cursors,
+// writes the items (unit, subs * seg + sub) and resets the arrival counters
+// of a split unit.  The order of units within a bucket is immaterial: every
+// item is independent and the merges combine segments in list order.  The
+// work counter of the compositing kernel is reset here too.
 __device__ __forceinline__ uint32_t unit_len(const uint2 *ranges, const LidarItem *unit_tile, int u)
 {
     const uint2 r = ranges[unit_tile ? unit_tile[u].tile : (uint32_t)u];
     return r.y - r.x;
 }
 
-constexpr int kWorkCache = 8192;   // unit lengths k_work_items keeps in shared memory
-
 __device__ __forceinline__ uint32_t len_bucket(uint32_t len)
 {
     return 32u - (len ? 32u - __clz(len) : 0u);        // longest first: 0 .. 32
 }
 
-__global__ void __launch_bounds__(1024)
-k_work_items(const uint2 *__restrict__ ranges, const LidarItem *__restrict__ unit_tile,
-             int n_units, int subs, uint32_t seg_len, uint32_t *__restrict__ order,
-             uint2 *__restrict__ unit_info, uint32_t *__restrict__ unit_off,
+__device__ __forceinline__ uint32_t unit_segments(uint32_t len, uint32_t seg_len)
+{
+    return len > seg_len ? (len + seg_len - 1) / seg_len : 1u;
+}
+
+// Scratch words (zeroed before k_work_count): the work items per bucket, the
+// buckets' first items, the partial slots, the blocks done, the slot cursor
+// and the buckets' item cursors.
+constexpr int kWsBucketItems = 0, kWsBucketBase = 33, kWsSlots = 66, kWsDone = 67,
+              kWsSlotCursor = 68, kWsBucketCursor = 69, kWsWords = 102;
+
+__global__ void __launch_bounds__(256)
+k_work_count(const uint2 *__restrict__ ranges, const LidarItem *__restrict__ unit_tile,
+             int n_units, int subs, uint32_t seg_len, uint32_t *__restrict__ ws,
              uint32_t *__restrict__ counts, uint32_t *__restrict__ counter)
 {
-    __shared__ uint32_t s_len[kWorkCache];
-    __shared__ uint32_t s_cnt[33], s_off[33], s_w[33];
-    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+    __shared__ uint32_t s_b[33], s_slots;
+    __shared__ bool s_last;
+    const int t = threadIdx.x;
+    if (t < 33) s_b[t] = 0u;
+    if (t == 0) s_slots = 0u;
     __syncthreads();
-    auto len_of = [&](uint32_t u) {
-        return u < (uint32_t)kWorkCache ? s_len[u] : unit_len(ranges, unit_tile, (int)u);
-    };
-    // list lengths (four units' loads in flight per thread) and bucket sizes
-    for (int u0 = threadIdx.x; u0 < n_units; u0 += 4 * 1024) {
-        uint32_t len[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int u = u0 + k * 1024;
-            len[k] = u < n_units ? unit_len(ranges, unit_tile, u) : 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int u = u0 + k * 1024;
-            if (u < n_units) {
-                if (u < kWorkCache) s_len[u] = len[k];
-                atomicAdd(&s_cnt[len_bucket(len[k])], 1u);
-            }
-        }
+    const int u = blockIdx.x * blockDim.x + t;
+    if (u < n_units) {
+        const uint32_t len = unit_len(ranges, unit_tile, u), nseg = unit_segments(len, seg_len);
+        atomicAdd(&s_b[len_bucket(len)], (uint32_t)subs * nseg);
+        if (nseg > 1) atomicAdd(&s_slots, nseg);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (t < 33 && s_b[t]) atomicAdd(&ws[kWsBucketItems + t], s_b[t]);
+    if (t == 33 && s_slots) atomicAdd(&ws[kWsSlots], s_slots);
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = atomicAdd(&ws[kWsDone], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && t == 0) {       // every block's sums are in: the buckets' first items
+        __threadfence();
         uint32_t run = 0;
-        for (int i = 0; i < 33; ++i) { s_off[i] = run; run += s_cnt[i]; }
-    }
-    __syncthreads();
-    for (int u = threadIdx.x; u < n_units; u += blockDim.x)
-        order[atomicAdd(&s_off[len_bucket(len_of((uint32_t)u))], 1u)] = (uint32_t)u;
-    __syncthreads();
-    // each thread takes a contiguous run of launch positions: sums, one
-    // block scan per quantity, then the offsets along the run
-    const int per = (n_units + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int k0 = min(n_units, (int)threadIdx.x * per), k1 = min(n_units, k0 + per);
-    auto nseg_of = [&](uint32_t u) {
-        const uint32_t len = len_of(u);
-        return len > seg_len ? (len + seg_len - 1) / seg_len : 1u;
-    };
-    uint32_t ni = 0, np = 0;
-    for (int k = k0; k < k1; ++k) {
-        const uint32_t nseg = nseg_of(order[k]);
-        ni += subs * nseg;
-        np += nseg > 1 ? nseg : 0u;
-    }
-    uint32_t tot_items, tot_parts;
-    uint32_t ib = block_excl_scan_1024(ni, s_w, tot_items);
-    uint32_t pb = block_excl_scan_1024(np, s_w, tot_parts);
-    for (int k = k0; k < k1; ++k) {
-        const uint32_t u = order[k], nseg = nseg_of(u);
-        unit_info[u] = make_uint2(nseg, pb);
-        unit_off[k] = ib;
-        ib += subs * nseg;
-        pb += nseg > 1 ? nseg : 0u;
-    }
-    if (threadIdx.x == 0) {
-        counts[0] = tot_items;
-        counts[1] = tot_parts;
+        for (int b = 0; b < 33; ++b) {
+            const uint32_t c = __ldcg(&ws[kWsBucketItems + b]);
+            ws[kWsBucketBase + b] = run;
+            run += c;
+        }
+        counts[0] = run;
+        counts[1] = __ldcg(&ws[kWsSlots]);
         counts[3] = 0u;      // deferred re-walks
         *counter = 0u;
     }
 }
 
-__global__ void k_emit_items(const uint32_t *__restrict__ order,
-                             const uint2 *__restrict__ unit_info,
-                             const uint32_t *__restrict__ unit_off, int n_units, int subs,
-                             uint2 *__restrict__ items, uint32_t *__restrict__ arrive)
+__global__ void __launch_bounds__(256)
+k_work_emit(const uint2 *__restrict__ ranges, const LidarItem *__restrict__ unit_tile,
+            int n_units, int subs, uint32_t seg_len, uint32_t *__restrict__ ws,
+            uint2 *__restrict__ unit_info, uint2 *__restrict__ items, uint32_t *__restrict__ arrive)
 {
-    const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (k >= n_units) return;
-    const uint32_t u = order[k];
-    const uint2 ui = unit_info[u];
-    const uint32_t ib = unit_off[k], n = subs * ui.x;
-    for (uint32_t i = lane; i < n; i += 32) items[ib + i] = make_uint2(u, i);
-    if (ui.x > 1 && lane < subs) arrive[ui.y * subs + lane] = 0u;
+    const int u = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (u >= n_units) return;
+    const uint32_t len = unit_len(ranges, unit_tile, u), nseg = unit_segments(len, seg_len);
+    const uint32_t n = (uint32_t)subs * nseg, b = len_bucket(len);
+    uint32_t ib = 0, pb = 0;
+    if (lane == 0) {
+        ib = ws[kWsBucketBase + b] + atomicAdd(&ws[kWsBucketCursor + b], n);
+        if (nseg > 1) pb = atomicAdd(&ws[kWsSlotCursor], nseg);
+        unit_info[u] = make_uint2(nseg, pb);
+    }
+    ib = __shfl_sync(0xffffffffu, ib, 0);
+    pb = __shfl_sync(0xffffffffu, pb, 0);
+    for (uint32_t i = lane; i < n; i += 32) items[ib + i] = make_uint2((uint32_t)u, i);
+    if (nseg > 1 && lane < subs) arrive[pb * subs + lane] = 0u;
 }
 
 // Launch both: the work items of `n_units` units into the frame's camwork
-// buffer laid out by ws.
+// buffer laid out by ws (its unit-offset region holds the scratch words).
 sg_status launch_work_items(Frame &fr, const WorkSize &ws, const LidarItem *unit_tile,
                             int n_units, int subs, uint32_t seg_len, cudaStream_t st)
 {
     unsigned char *cw = (unsigned char *)fr.camwork.p;
     uint2 *unit_info = (uint2 *)cw;
-    uint32_t *unit_off = (uint32_t *)(cw + ws.info_bytes);
+    uint32_t *scratch = (uint32_t *)(cw + ws.info_bytes);
     uint2 *items = (uint2 *)(cw + ws.info_bytes + ws.off_bytes);
     uint32_t *arrive = (uint32_t *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes);
-    k_work_items<<<1, 1024, 0, st>>>((const uint2 *)fr.ranges.p, unit_tile, n_units, subs,
-                                     seg_len, (uint32_t *)fr.order.p, unit_info, unit_off,
-                                     (uint32_t *)fr.scalars.p + 4, (uint32_t *)fr.scalars.p + 2);
+    if (ws.off_bytes < sizeof(uint32_t) * kWsWords) {
+        set_error("internal: work-item scratch too small");
+        return SG_ERR_INVALID;
+    }
+    SG_CUDA(cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * kWsWords, st));
+    const unsigned g1 = (unsigned)((n_units + 255) / 256);
+    k_work_count<<<g1 > 0 ? g1 : 1, 256, 0, st>>>((const uint2 *)fr.ranges.p, unit_tile, n_units,
+                                                  subs, seg_len, scratch,
+                                                  (uint32_t *)fr.scalars.p + 4,
+                                                  (uint32_t *)fr.scalars.p + 2);
     SG_LAUNCHED();
     if (n_units > 0) {
-        k_emit_items<<<(unsigned)((n_units + 7) / 8), 256, 0, st>>>(
-            (const uint32_t *)fr.order.p, unit_info, unit_off, n_units, subs, items, arrive);
+        k_work_emit<<<(unsigned)((n_units + 7) / 8), 256, 0, st>>>(
+            (const uint2 *)fr.ranges.p, unit_tile, n_units, subs, seg_len, scratch, unit_info,
+            items, arrive);
         SG_LAUNCHED();
     }
     return SG_OK;

@@ -596,40 +596,66 @@ sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint
 // of their sub-block can see.  After a look-back wait gave up (*err) the
 // pairs may hold stale tile ids: every range stays empty (zeroed before the
 // launch).
+// Each thread takes kRangePer consecutive pairs, their loads (keys, ids,
+// then the boxes by id) issued together, so that a thread waits for two
+// rounds of loads for all of them.
+constexpr int kRangePer = 4;
+
 template <int kMask>
-__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
-                         uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
-                         const float4 *__restrict__ rects, int ntx, void *__restrict__ mask,
-                         const uint32_t *__restrict__ err)
+__global__ void __launch_bounds__(256)
+k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
+         uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
+         const float4 *__restrict__ rects, int ntx, void *__restrict__ mask,
+         const uint32_t *__restrict__ err)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kRangePer;
     const int64_t K = *d_K;
-    if (i >= K || *err) return;
-    uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-    if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    if (i0 >= K || *err) return;
+    uint32_t t[kRangePer], id[kRangePer];
+    float4 rc[kRangePer];
+#pragma unroll
+    for (int j = 0; j < kRangePer; ++j) {
+        const bool in = i0 + j < K;
+        t[j] = in ? keys[i0 + j] : 0u;
+        if (kMask) id[j] = in ? ids[i0 + j] : 0u;
+    }
+    const uint32_t before = i0 > 0 ? keys[i0 - 1] : 0u;
+    const uint32_t after = i0 + kRangePer < K ? keys[i0 + kRangePer] : 0u;
     if (kMask) {
-        const float4 rc = rects[ids[i]];   // the extent box, 16 B per Gaussian
-        const int tx = (int)(t % (uint32_t)ntx), ty = (int)(t / (uint32_t)ntx);
-        uint32_t cols = 0, rows = 0;
 #pragma unroll
-        for (int c = 0; c < kTile; ++c) {
-            const float x = (float)(tx * kTile + c) + 0.5f;
-            const float y = (float)(ty * kTile + c) + 0.5f;
-            cols |= (uint32_t)(x >= rc.x && x <= rc.y) << c;
-            rows |= (uint32_t)(y >= rc.z && y <= rc.w) << c;
-        }
-        if (kMask == 2) {
-            ((uint32_t *)mask)[i] = cols | (rows << 16);
-        } else {
-            uint32_t m = 0;
+        for (int j = 0; j < kRangePer; ++j)
+            if (i0 + j < K) rc[j] = rects[id[j]];   // the extent box, 16 B per Gaussian
+    }
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                const bool cx = ((cols >> (8 * (w & 1))) & 0xffu) != 0u;
-                const bool cy = ((rows >> (4 * (w >> 1))) & 0xfu) != 0u;
-                m |= (uint32_t)(cx && cy) << w;
+    for (int j = 0; j < kRangePer; ++j) {
+        const int64_t i = i0 + j;
+        if (i >= K) break;
+        const uint32_t left = j > 0 ? t[j - 1] : before;
+        const uint32_t right = j + 1 < kRangePer ? t[j + 1] : after;
+        if (i == 0 || left != t[j]) ranges[t[j]].x = (uint32_t)i;
+        if (i == K - 1 || right != t[j]) ranges[t[j]].y = (uint32_t)(i + 1);
+        if (kMask) {
+            const int tx = (int)(t[j] % (uint32_t)ntx), ty = (int)(t[j] / (uint32_t)ntx);
+            uint32_t cols = 0, rows = 0;
+#pragma unroll
+            for (int c = 0; c < kTile; ++c) {
+                const float x = (float)(tx * kTile + c) + 0.5f;
+                const float y = (float)(ty * kTile + c) + 0.5f;
+                cols |= (uint32_t)(x >= rc[j].x && x <= rc[j].y) << c;
+                rows |= (uint32_t)(y >= rc[j].z && y <= rc[j].w) << c;
             }
-            ((uint8_t *)mask)[i] = (uint8_t)m;
+            if (kMask == 2) {
+                ((uint32_t *)mask)[i] = cols | (rows << 16);
+            } else {
+                uint32_t m = 0;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    const bool cx = ((cols >> (8 * (w & 1))) & 0xffu) != 0u;
+                    const bool cy = ((rows >> (4 * (w >> 1))) & 0xfu) != 0u;
+                    m |= (uint32_t)(cx && cy) << w;
+                }
+                ((uint8_t *)mask)[i] = (uint8_t)m;
+            }
         }
     }
 }
@@ -641,7 +667,7 @@ sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max
 {
     SG_CUDA(cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * ntiles, st));
     if (K_max == 0) return SG_OK;
-    const unsigned grid = (unsigned)((K_max + 255) / 256);
+    const unsigned grid = (unsigned)((K_max + 256 * kRangePer - 1) / (256 * kRangePer));
     if (d_words)
         k_ranges<2><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rects, ntx, d_words,
                                           d_err);

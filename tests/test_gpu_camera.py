@@ -128,6 +128,29 @@ def test_small_fisheye_with_rayless_corners(sg, O64, mode):
     assert corner.any()
 
 
+def test_forward_only_frame_falls_back_for_wide_tiles(sg, O64):
+    """A fisheye whose single 16x16 tile spans nearly a hemisphere: some pixel
+    is more than 75 degrees from the tile's reference direction, so the
+    camera keeps no tangent-plane table and forward-only frames composite
+    with the state-keeping kernel: bit-identical to a frame that keeps the
+    state, and both match the oracle."""
+    import torch
+    sc = syn.tiny_scene()
+    cam = syn.tiny_camera()
+    cam.model = syn.CAMERA_FISHEYE
+    cam.width, cam.height, cam.cx, cam.cy = 16, 16, 8.0, 8.0
+    cam.fx = cam.fy = 2.5
+    cam.k = np.zeros(4, np.float32)
+    a = gpu_render(sg, sc, cam, mode="saved")
+    b = gpu_render(sg, sc, cam, mode="forward", scene=a["scene"])
+    for k in ("rgb", "alpha", "depth"):
+        assert np.array_equal(a[k], b[k]), k
+    orc = O64.render_camera(sc, cam)
+    assert (orc["n_visited"] > 0).any()
+    par.compare_camera_rays(b["rgb"].reshape(-1, 3), b["alpha"].reshape(-1),
+                            b["depth"].reshape(-1), orc, max_excluded=0.05, label="wide-fisheye")
+
+
 def test_empty_and_fully_culled_scenes(sg):
     sc, cam = syn.tiny_scene(), syn.tiny_camera()
     empty = sc.subset(np.zeros(0, np.int64))

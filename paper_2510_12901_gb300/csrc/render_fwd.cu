@@ -34,6 +34,19 @@ constexpr int kFwdWarps = 4;        // warps per block of the persistent grid
 // two-view step: 6 blocks 0.387 / 0.547 ms, 3122 Mrays/s; 7 blocks 0.383 /
 // 0.534 ms, 3189-3200 Mrays/s; 8 blocks 0.418 / 0.545 ms, 3237 Mrays/s.
 constexpr int kFwdBlocks = 7;
+// List entries a warp scans per batch: kFwdPer per lane.  The entries of
+// the window that reach a live ray of the sub-block (about a third of them
+// on the street views) are staged together, so that the staging pass, one
+// entry per lane, runs with more of its lanes busy than over a 32-entry
+// window.  Measured (street views, compositing alone / bench): 32 entries
+// 0.374 / 0.528 ms, 3219 Mrays/s; 64 entries 0.364 / 0.519 ms, 3284; 96
+// entries 0.362 / 0.514 ms, 3305; 128 entries 0.361 / 0.524 ms, 3265.
+#ifndef SG_FWD_PER_LANE
+#define SG_FWD_PER_LANE 3
+#endif
+constexpr int kFwdPer = SG_FWD_PER_LANE;
+constexpr int kFwdWin = 32 * kFwdPer;
+constexpr int kFwdStage = 64;   // staged entries held in shared memory at once
 
 // The tile's reference frame in world coordinates: d_T = dh + dl (from the
 // double direction, as cam_tile_ref) and e_1, e_2 rotated in float.
@@ -104,7 +117,7 @@ struct FwdAcc {
 
 // Composite the n staged entries into the lane's accumulator (ray with
 // tangent-plane coordinates (x, y)); done: the ray has stopped (or has none).
-__device__ __forceinline__ void fwd_composite(const CamRender &P, float4 (*s)[32], int n,
+__device__ __forceinline__ void fwd_composite(const CamRender &P, float4 (*s)[kFwdStage], int n,
                                               float x, float y, FwdAcc &a, bool &done)
 {
     const uint32_t bit = 1u << (threadIdx.x & 31);
@@ -155,45 +168,70 @@ __device__ __forceinline__ uint32_t word_lanes(uint32_t cr, int sub)
 // into the lane's accumulator.  Lanes whose ray is done take part in the
 // staging and keep their state; only entries whose box holds a live ray are
 // staged (their lane masks come from the column/row words, no record load).
+// cand: the warp's (Gaussian, lane mask) list of a window's staged entries.
 __device__ __forceinline__ void fwd_walk(const CamRender &P, const CamPose &pose,
                                          const GRec *__restrict__ rec,
                                          const uint32_t *__restrict__ ids,
                                          const uint32_t *__restrict__ crw, int sub, uint32_t lo,
                                          uint32_t hi, const float *ref, float x, float y,
-                                         float4 (*s)[32], FwdAcc &a, bool &done)
+                                         float4 (*s)[kFwdStage], uint2 *cand, FwdAcc &a,
+                                         bool &done)
 {
     const int lane = threadIdx.x & 31;
-    // the next batch's column/row words and Gaussian ids, loaded one batch ahead
-    uint32_t ncr = 0u, nid = 0u;
-    if (lo + lane < hi) {
-        ncr = crw[lo + lane];
-        nid = ids[lo + lane];
+    const uint32_t below = (1u << lane) - 1u;
+    // the next window's column/row words and Gaussian ids (entries lane + 32 w
+    // of it), loaded one window ahead
+    uint32_t ncr[kFwdPer], nid[kFwdPer];
+#pragma unroll
+    for (int w = 0; w < kFwdPer; ++w) {
+        const uint32_t i = lo + 32 * w + lane;
+        ncr[w] = i < hi ? crw[i] : 0u;
+        nid[w] = i < hi ? ids[i] : 0u;
     }
-    for (uint32_t base = lo; base < hi; base += 32) {
+    for (uint32_t base = lo; base < hi; base += kFwdWin) {
         const uint32_t act = __ballot_sync(0xffffffffu, !done);
         if (act == 0u) break;
-        const uint32_t idx = base + lane;
-        const uint32_t gid = nid;
-        const uint32_t lm = word_lanes(ncr, sub) & act;
-        if (idx + 32 < hi) {
-            ncr = crw[idx + 32];
-            nid = ids[idx + 32];
-        } else {
-            ncr = 0u;
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, lm != 0u);
-        if (bal == 0u) continue;
-        __syncwarp();
-        if (lm) {
-            const int pos = __popc(bal & ((1u << lane) - 1u));
-            float4 e[7];
-            fwd_entry(rec[gid], pose.t, ref, e);
-            e[6].y = __uint_as_float(lm);
+        uint32_t g[kFwdPer], lm[kFwdPer], bw[kFwdPer];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) s[k][pos] = e[k];
+        for (int w = 0; w < kFwdPer; ++w) {
+            g[w] = nid[w];
+            lm[w] = word_lanes(ncr[w], sub) & act;
+            const uint32_t i = base + kFwdWin + 32 * w + lane;
+            ncr[w] = 0u;
+            if (i < hi) {
+                ncr[w] = crw[i];
+                nid[w] = ids[i];
+            }
         }
+        int n = 0;
+#pragma unroll
+        for (int w = 0; w < kFwdPer; ++w) {
+            bw[w] = __ballot_sync(0xffffffffu, lm[w] != 0u);
+            n += __popc(bw[w]);
+        }
+        if (n == 0) continue;
         __syncwarp();
-        fwd_composite(P, s, __popc(bal), x, y, a, done);
+        int off = 0;
+#pragma unroll
+        for (int w = 0; w < kFwdPer; ++w) {
+            if (lm[w]) cand[off + __popc(bw[w] & below)] = make_uint2(g[w], lm[w]);
+            off += __popc(bw[w]);
+        }
+        // stage and composite them, in list order, kFwdStage at a time
+        for (int c0 = 0; c0 < n; c0 += kFwdStage) {
+            const int m = n - c0 < kFwdStage ? n - c0 : kFwdStage;
+            __syncwarp();
+            for (int t = lane; t < m; t += 32) {
+                const uint2 c = cand[c0 + t];
+                float4 e[7];
+                fwd_entry(rec[c.x], pose.t, ref, e);
+                e[6].y = __uint_as_float(c.y);
+#pragma unroll
+                for (int k = 0; k < 7; ++k) s[k][t] = e[k];
+            }
+            __syncwarp();
+            fwd_composite(P, s, m, x, y, a, done);
+        }
     }
 }
 
@@ -215,13 +253,15 @@ k_render_camera_fwd(CamRender P, const GRec *__restrict__ rec, const uint32_t *_
                     const float4 *__restrict__ pix2, const double *__restrict__ tile_dir,
                     const float *__restrict__ tile_basis, const RenderDesc *__restrict__ D)
 {
-    __shared__ float4 s_all[kFwdWarps][7][32];
+    __shared__ float4 s_all[kFwdWarps][7][kFwdStage];
+    __shared__ uint2 s_cand[kFwdWarps][kFwdWin];
     __shared__ float s_refs[kFwdWarps][12];
     __shared__ CamPose s_pose;
     load_cam_pose(D, s_pose);
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float4(*s_e)[32] = s_all[wib];
+    float4(*s_e)[kFwdStage] = s_all[wib];
+    uint2 *cand = s_cand[wib];
     float *s_ref = s_refs[wib];
     const uint32_t n_items = counts[0];
     while (true) {
@@ -246,7 +286,7 @@ k_render_camera_fwd(CamRender P, const GRec *__restrict__ rec, const uint32_t *_
         const uint32_t hi = min(rg.y, lo + kSeg);
         FwdAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool done = no_ray;
-        fwd_walk(P, s_pose, rec, ids, crw, sub, lo, hi, s_ref, e.x, e.y, s_e, a, done);
+        fwd_walk(P, s_pose, rec, ids, crw, sub, lo, hi, s_ref, e.x, e.y, s_e, cand, a, done);
         if (ti.x > 1) {
             // long tile: publish this run, and combine if it is the last one
             fwd_put(partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2, a,
@@ -308,7 +348,7 @@ k_render_camera_fwd(CamRender P, const GRec *__restrict__ rec, const uint32_t *_
                 bool dn = !mine;
                 const uint32_t l0 = rg.x + r * kSeg;
                 fwd_walk(P, s_pose, rec, ids, crw, sub, l0, min(rg.y, l0 + kSeg), s_ref, e.x, e.y,
-                         s_e, a, dn);
+                         s_e, cand, a, dn);
                 pend = pend && !mine;
             }
         }

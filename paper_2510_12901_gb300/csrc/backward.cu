@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(32 * kBwWarps, 4)
 k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
                   const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
                   const uint2 *__restrict__ tile_info, const uint32_t *__restrict__ counts,
-                  const uint8_t *__restrict__ submask, uint32_t *__restrict__ counter,
+                  const uint32_t *__restrict__ crw, uint32_t *__restrict__ counter,
                   const float4 *__restrict__ partials, const float4 *__restrict__ pix,
                   const double *__restrict__ tile_dir, const RenderDesc *__restrict__ D,
                   const float4 *__restrict__ ray_state, const float4 *__restrict__ ray_feat,
@@ -217,28 +217,26 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
             Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * st.z + gQ[4] * st.y;
             U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
-        const uint32_t act0 = __ballot_sync(0xffffffffu, rg.x + last > lo);
-        // the next batch's mask byte and id, loaded one batch ahead
-        uint32_t nsm = 0u, nid = 0u;
+        // the next batch's column/row word and id, loaded one batch ahead
+        uint32_t ncr = 0u, nid = 0u;
         if (lo + lane < hi) {
-            nsm = submask[lo + lane];
+            ncr = crw[lo + lane];
             nid = ids[lo + lane];
         }
         for (uint32_t base = lo; base < hi; base += 32) {
-            // lanes whose composited entries reach this batch: once some
-            // have ended, an entry that reaches none of the others
-            // contributes to no ray and is not staged
+            // lanes whose composited entries reach this batch: an entry that
+            // reaches none of them contributes to no ray and is not staged
             const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
             const uint32_t idx = base + lane;
             const uint32_t g = nid;
-            bool ov = (nsm >> sub) & 1u;
+            const uint32_t lm = word_lanes(ncr, sub) & act;
+            const bool ov = lm != 0u;
             if (idx + 32 < hi) {
-                nsm = submask[idx + 32];
+                ncr = crw[idx + 32];
                 nid = ids[idx + 32];
             } else {
-                nsm = 0u;
+                ncr = 0u;
             }
-            if (act != act0 && ov) ov = (subblock_lanes(rec[g].rect, sbx, sby) & act) != 0u;
             const uint32_t bal = __ballot_sync(0xffffffffu, ov);
             if (bal == 0u) continue;
             __syncwarp();
@@ -248,7 +246,7 @@ k_backward_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__r
                 cam_entry(rec[g], s_pose.t, dh, dl, ent, kResponseScale);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
-                s_lanes[wib][pos] = subblock_lanes(ent[8], sbx, sby) & act;
+                s_lanes[wib][pos] = lm;
                 s_pos[wib][pos] = idx + 1 - rg.x;
                 s_gid[wib][pos] = g;
             }
@@ -285,7 +283,7 @@ __global__ void __launch_bounds__(32 * kBwWarps, 4)
 k_backward_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
                      const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
                      const uint2 *__restrict__ tile_info, const uint32_t *__restrict__ counts,
-                     const uint8_t *__restrict__ submask, uint32_t *__restrict__ counter,
+                     const uint32_t *__restrict__ crw, uint32_t *__restrict__ counter,
                      const float4 *__restrict__ partials, const float4 *__restrict__ pix,
                      const double *__restrict__ tile_dir, const float *__restrict__ poses,
                      const float4 *__restrict__ ray_state, const float4 *__restrict__ ray_feat,
@@ -344,24 +342,22 @@ k_backward_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *
             Ut = gQ[0] * F.x + gQ[1] * F.y + gQ[2] * F.z + gQ[3] * st.z + gQ[4] * st.y;
             U = gQ[0] * Qp[0] + gQ[1] * Qp[1] + gQ[2] * Qp[2] + gQ[3] * Qp[3] + gQ[4] * Qp[4];
         }
-        uint32_t nsm = 0u, nid = 0u;    // the next batch's, one batch ahead
+        uint32_t ncr = 0u, nid = 0u;    // the next batch's, one batch ahead
         if (lo + lane < hi) {
-            nsm = submask[lo + lane];
+            ncr = crw[lo + lane];
             nid = ids[lo + lane];
         }
         for (uint32_t base = lo; base < hi; base += 32) {
             const uint32_t act = __ballot_sync(0xffffffffu, rg.x + last > base);
             const uint32_t idx = base + lane;
             const uint32_t g = nid;
-            const bool ov = (nsm >> sub) & 1u;
+            const uint32_t lm = word_lanes(ncr, sub) & act;
             if (idx + 32 < hi) {
-                nsm = submask[idx + 32];
+                ncr = crw[idx + 32];
                 nid = ids[idx + 32];
             } else {
-                nsm = 0u;
+                ncr = 0u;
             }
-            uint32_t lm = 0u;
-            if (ov) lm = subblock_lanes(rec[g].rect, sbx, sby) & act;
             const uint32_t bal = __ballot_sync(0xffffffffu, lm != 0u);
             if (bal == 0u) continue;
             __syncwarp();
@@ -820,7 +816,7 @@ sg_status backward_camera(const Scene &sc, const Camera &cam, Frame &fr, const f
         k_backward_camera_rs<<<(unsigned)grid, 32 * kBwWarps, 0, st>>>(
             P, (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
             (const uint2 *)fr.ranges.p, (const uint2 *)(cw + ws.info_bytes + ws.off_bytes),
-            (const uint2 *)cw, (const uint32_t *)fr.scalars.p + 4, (const uint8_t *)fr.submask.p,
+            (const uint2 *)cw, (const uint32_t *)fr.scalars.p + 4, (const uint32_t *)fr.submask.p,
             counter, (const float4 *)fr.partials.p, cam.d_pix, cam.d_tile_dir, fr.d_lidar_poses,
             (const float4 *)fr.ray_state.p, (const float4 *)fr.ray_feat.p,
             (const uint32_t *)fr.n_contrib.p, g_rgb, g_alpha, g_depth, (float *)fr.gacc.p);
@@ -833,7 +829,7 @@ sg_status backward_camera(const Scene &sc, const Camera &cam, Frame &fr, const f
     k_backward_camera<<<(unsigned)grid, 32 * kBwWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, (const uint32_t *)fr.pvals[fr.pair_buf].p,
         (const uint2 *)fr.ranges.p, (const uint2 *)(cw + ws.info_bytes + ws.off_bytes),
-        (const uint2 *)cw, (const uint32_t *)fr.scalars.p + 4, (const uint8_t *)fr.submask.p,
+        (const uint2 *)cw, (const uint32_t *)fr.scalars.p + 4, (const uint32_t *)fr.submask.p,
         counter, (const float4 *)fr.partials.p, cam.d_pix, cam.d_tile_dir,
         (const RenderDesc *)fr.desc.p, (const float4 *)fr.ray_state.p,
         (const float4 *)fr.ray_feat.p, (const uint32_t *)fr.n_contrib.p, g_rgb, g_alpha,

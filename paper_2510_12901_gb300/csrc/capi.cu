@@ -300,15 +300,10 @@ static sg_status bin_and_sort(Frame &fr, int64_t n, int ntx, int64_t ntiles, int
         fr.lmask_stride = K;
         s = lidar_tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err, pv[pb],
                               (const float4 *)fr.rect.p, L, (uint32_t *)fr.lmask.p);
-    } else {   // camera lists also get their sub-block masks (column/row words
-               // for the forward-only compositing)
-        const bool words = fr.kind == 0 &&
-            camera_forward_only(static_cast<const sg_camera_s *>(fr.sensor)->c, fr);
-        const size_t by = (words ? 4 : 1) * (size_t)(K > 0 ? K : 1);
-        if ((s = ensure(fr.submask, by)) != SG_OK) return s;
+    } else {   // camera lists also get their column/row words
+        if ((s = ensure(fr.submask, 4 * (size_t)(K > 0 ? K : 1))) != SG_OK) return s;
         s = tile_ranges(pk[pb], sc + 1, K, (uint2 *)fr.ranges.p, ntiles, st, err, pv[pb],
-                        (const float4 *)fr.rect.p, ntx, words ? nullptr : (uint8_t *)fr.submask.p,
-                        words ? (uint32_t *)fr.submask.p : nullptr);
+                        (const float4 *)fr.rect.p, ntx, (uint32_t *)fr.submask.p);
     }
     if (s != SG_OK) return s;
     if (fr.k_cap > 0)   // counts, dropped pairs and the status word, for the caller

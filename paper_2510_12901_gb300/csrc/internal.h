@@ -359,7 +359,7 @@ sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
                       int64_t ntiles, cudaStream_t st, const uint32_t *d_err,
                       const uint32_t *d_ids = nullptr, const float4 *d_rects = nullptr,
-                      int ntx = 0, uint8_t *d_mask = nullptr, uint32_t *d_words = nullptr);
+                      int ntx = 0, uint32_t *d_words = nullptr);
 // LiDAR lists: ranges, and for every pair and every work item of its tile
 // the item's rays inside the Gaussian's extent box (lmask[k * K_max + i]
 // for the k-th item of the tile, by the compositing's own float test).

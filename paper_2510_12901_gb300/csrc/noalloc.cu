@@ -40,7 +40,7 @@ constexpr size_t kStBytes = kStRec + 3 * kStG16 + kStG8 +       // rec, rect, ti
                             al(8 * kStMaxTiles) + al(4 * kStMaxTiles) +  // ranges, order
                             2 * al(16 * kStMaxRays) + al(4 * kStMaxRays) + // ray state, features,
                                                                          // contributors
-                            al(kStMaxPairs) +                            // sub-block masks
+                            kStP4 +                                      // column/row words
                             kStWork.work_bytes + kStWork.partial_bytes + // work items, partials
                             al(64) +                                     // device scalars
                             al(sizeof(RenderDesc));                      // render descriptor
@@ -145,7 +145,7 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
     carve(fr.ray_state, cur, al(16 * kStMaxRays));
     carve(fr.ray_feat, cur, al(16 * kStMaxRays));
     carve(fr.n_contrib, cur, al(4 * kStMaxRays));
-    carve(fr.submask, cur, al(kStMaxPairs));
+    carve(fr.submask, cur, kStP4);
     carve(fr.camwork, cur, kStWork.work_bytes);
     carve(fr.partials, cur, kStWork.partial_bytes);
     fr.seg_len = kSegLenStatic;
@@ -210,7 +210,7 @@ extern "C" sg_status sg_render_camera_static(sg_scene scene, sg_camera cam,
         return s;
     fr.pair_buf = pb;
     if ((s = tile_ranges(pk[pb], scal + 1, K, (uint2 *)fr.ranges.p, nt, st, err, pv[pb],
-                         (const float4 *)fr.rect.p, c.ntx, (uint8_t *)fr.submask.p)) != SG_OK)
+                         (const float4 *)fr.rect.p, c.ntx, (uint32_t *)fr.submask.p)) != SG_OK)
         return s;
     return render_camera(c, *opts, fr, st);
 }

@@ -118,26 +118,17 @@ __device__ __forceinline__ bool cam_pair_scaled(const float4 q0, const float4 q1
     return in_box && pe.tau > 0.f && pe.alpha >= alpha_min;
 }
 
-// Which pixel centres of an 8x4 sub-block with first pixel (x0, y0) lie in
-// the box rc: bit 8 r + c for pixel (x0 + c, y0 + r).  The same float
-// comparisons as the per-ray extent test.
-__device__ __forceinline__ uint32_t subblock_lanes(const float4 rc, int x0, int y0)
+// The lanes of 8x4 sub-block `sub` whose pixel centres lie in an entry's
+// box, from the entry's word of tile columns and rows in the box (bits 0-15:
+// the tile's columns, 16-31: its rows; written with the tile ranges by the
+// same float comparisons as the per-ray test): the sub-block's 8 column bits
+// in every byte, a byte kept where the sub-block's row is in the box (the
+// multiply by 0x00204081 moves bit r of the 4 row bits to bit 8 r).
+__device__ __forceinline__ uint32_t word_lanes(uint32_t cr, int sub)
 {
-    uint32_t cols = 0, rows = 0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float x = (float)(x0 + c) + 0.5f;
-        cols |= (uint32_t)(x >= rc.x && x <= rc.y) << c;
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const float y = (float)(y0 + r) + 0.5f;
-        rows |= (uint32_t)(y >= rc.z && y <= rc.w) << r;
-    }
-    uint32_t m = 0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) m |= ((rows >> r) & 1u) ? cols << (8 * r) : 0u;
-    return m;
+    const uint32_t cols = (cr >> (8 * (sub & 1))) & 0xffu;
+    const uint32_t rows = (cr >> (16 + 4 * (sub >> 1))) & 0xfu;
+    return (cols * 0x01010101u) & ((((rows * 0x00204081u) & 0x01010101u)) * 0xffu);
 }
 
 // LiDAR entries keep per-column quantities (each column has its own sensor

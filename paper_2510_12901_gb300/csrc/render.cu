@@ -268,20 +268,19 @@ __device__ __forceinline__ void cam_composite(const CamRender &P, float4 (*s_e)[
 __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose,
                                          const GRec *__restrict__ rec,
                                          const uint32_t *__restrict__ ids,
-                                         const uint8_t *__restrict__ submask, int sub,
-                                         int sbx, int sby, uint32_t lo, uint32_t hi,
+                                         const uint32_t *__restrict__ crw, int sub,
+                                         uint32_t lo, uint32_t hi,
                                          uint32_t begin, const float dh[3], const float dl[3],
                                          const float dd[3], float4 (*s_e)[32],
-                                         uint32_t *s_pos, CamAcc &a, bool done,
-                                         uint32_t rays)
+                                         uint32_t *s_pos, CamAcc &a, bool done)
 {
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
     // the next batch's mask byte and Gaussian id, loaded one batch ahead so
     // that staging waits for the record load alone
-    uint32_t nsm = 0u, nid = 0u;
+    uint32_t ncr = 0u, nid = 0u;
     if (lo + lane < hi) {
-        nsm = submask[lo + lane];
+        ncr = crw[lo + lane];
         nid = ids[lo + lane];
     }
     for (uint32_t base = lo; base < hi; base += 32) {
@@ -289,18 +288,15 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
         if (act == 0u) break;
         const uint32_t idx = base + lane;
         const uint32_t gid = nid;
-        bool ov = (nsm >> sub) & 1u;
+        // the entry's lanes in the sub-block, from its column/row word: only
+        // entries that reach a ray still compositing are staged
+        const uint32_t lm = word_lanes(ncr, sub) & act;
+        const bool ov = lm != 0u;
         if (idx + 32 < hi) {
-            nsm = submask[idx + 32];
+            ncr = crw[idx + 32];
             nid = ids[idx + 32];
         } else {
-            nsm = 0u;
-        }
-        if (act != rays && ov) {
-            // some rays are done: stage only entries that reach one still
-            // compositing (the box is read before the ballot, which costs a
-            // load latency, so not while every ray is live)
-            ov = (subblock_lanes(rec[gid].rect, sbx, sby) & act) != 0u;
+            ncr = 0u;
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, ov);
         if (bal == 0u) continue;
@@ -309,7 +305,7 @@ __device__ __forceinline__ bool cam_walk(const CamRender &P, const CamPose &pose
             const int pos = __popc(bal & ((1u << lane) - 1u));
             float4 ent[9];
             cam_entry(rec[gid], pose.t, dh, dl, ent, kResponseScale);
-            ent[7].w = __uint_as_float(subblock_lanes(ent[8], sbx, sby) & act);
+            ent[7].w = __uint_as_float(lm);
 #pragma unroll
             for (int k = 0; k < 8; ++k) s_e[k][pos] = ent[k];
             s_pos[pos] = idx + 1 - begin;
@@ -336,7 +332,7 @@ __global__ void __launch_bounds__(32 * kCamWarps, 6)
 k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
                 const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
                 const uint2 *__restrict__ tile_info, const uint32_t *__restrict__ counts,
-                const uint8_t *__restrict__ submask, uint32_t *__restrict__ counter,
+                const uint32_t *__restrict__ crw, uint32_t *__restrict__ counter,
                 uint32_t *__restrict__ arrive, float4 *__restrict__ partials,
                 const float4 *__restrict__ pix, const double *__restrict__ tile_dir,
                 const RenderDesc *__restrict__ D, float4 *__restrict__ ray_state,
@@ -371,15 +367,14 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
         const int64_t pidx = (int64_t)py * P.W + px;
         const float4 e = inside ? pix[pidx] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool no_ray = !(inside && e.w > 0.f);
-        const uint32_t rays = __ballot_sync(0xffffffffu, !no_ray);
         float dd[3];
         cam_ray_offset(s_pose, e, dd);
         const uint2 rg = ranges[tile];
         const uint32_t lo = rg.x + (uint32_t)seg * kSeg;
         const uint32_t hi = min(rg.y, lo + kSeg);
         CamAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
-        const bool stopped = cam_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, lo, hi, rg.x,
-                                      dh, dl, dd, s_e, s_pos[wib], a, no_ray, rays);
+        const bool stopped = cam_walk(P, s_pose, rec, ids, crw, sub, lo, hi, rg.x, dh, dl, dd,
+                                      s_e, s_pos[wib], a, no_ray);
         if (ti.x > 1) {
             // long tile: publish this run, and combine if it is the last one
             put_state(partials + ((size_t)(ti.y + seg) * 256 + sub * 32 + lane) * 2, a, stopped);
@@ -417,9 +412,9 @@ k_render_camera(CamRender P, const GRec *__restrict__ rec, const uint32_t *__res
                 }
                 if (__any_sync(0xffffffffu, redo)) {
                     const uint32_t l0 = rg.x + sgi * kSeg;
-                    cam_walk(P, s_pose, rec, ids, submask, sub, sbx, sby, l0,
+                    cam_walk(P, s_pose, rec, ids, crw, sub, l0,
                              min(rg.y, l0 + kSeg), rg.x, dh, dl, dd, s_e, s_pos[wib],
-                             a, !redo, rays);
+                             a, !redo);
                 }
                 fin = fin || redo;
             }
@@ -472,7 +467,7 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
-    if (s == SG_OK && fr.submask.bytes < (size_t)(K > 0 ? K : 1)) {
+    if (s == SG_OK && fr.submask.bytes < 4 * (size_t)(K > 0 ? K : 1)) {
         set_error("internal: sub-block masks of the camera list missing");
         s = SG_ERR_INVALID;
     }
@@ -497,7 +492,7 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
     auto kern = dflt ? k_render_camera<kSegLen> : k_render_camera<kSegLenStatic>;
     kern<<<(unsigned)grid, 32 * kCamWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
-        (const uint8_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
+        (const uint32_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
         cam.d_tile_dir, (const RenderDesc *)fr.desc.p, saved_state(fr),
         saved_feat(fr), saved_contrib(fr));
     SG_LAUNCHED();
@@ -517,7 +512,7 @@ sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, c
 // lane's row slot.  As cam_walk.
 __device__ __forceinline__ bool cam_walk_rs(const CamRender &P, const GRec *__restrict__ rec,
                                             const uint32_t *__restrict__ ids,
-                                            const uint8_t *__restrict__ submask, int sub,
+                                            const uint32_t *__restrict__ crw, int sub,
                                             int sbx, int sby, uint32_t lo, uint32_t hi,
                                             uint32_t begin, const float *__restrict__ poses,
                                             int nrows, int sb, const float dh[3],
@@ -527,9 +522,9 @@ __device__ __forceinline__ bool cam_walk_rs(const CamRender &P, const GRec *__re
 {
     const int lane = threadIdx.x & 31;
     const bool done0 = done;
-    uint32_t nsm = 0u, nid = 0u;    // the next batch's, as in cam_walk
+    uint32_t ncr = 0u, nid = 0u;    // the next batch's, as in cam_walk
     if (lo + lane < hi) {
-        nsm = submask[lo + lane];
+        ncr = crw[lo + lane];
         nid = ids[lo + lane];
     }
     for (uint32_t base = lo; base < hi; base += 32) {
@@ -537,15 +532,13 @@ __device__ __forceinline__ bool cam_walk_rs(const CamRender &P, const GRec *__re
         if (act == 0u) break;
         const uint32_t idx = base + lane;
         const uint32_t g = nid;
-        const bool ov = (nsm >> sub) & 1u;
+        const uint32_t lm = word_lanes(ncr, sub) & act;
         if (idx + 32 < hi) {
-            nsm = submask[idx + 32];
+            ncr = crw[idx + 32];
             nid = ids[idx + 32];
         } else {
-            nsm = 0u;
+            ncr = 0u;
         }
-        uint32_t lm = 0u;
-        if (ov) lm = subblock_lanes(rec[g].rect, sbx, sby) & act;
         const uint32_t bal = __ballot_sync(0xffffffffu, lm != 0u);
         if (bal == 0u) continue;
         __syncwarp();
@@ -598,7 +591,7 @@ __global__ void __launch_bounds__(32 * kCamWarps)
 k_render_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *__restrict__ ids,
                    const uint2 *__restrict__ ranges, const uint2 *__restrict__ items,
                    const uint2 *__restrict__ tile_info, const uint32_t *__restrict__ counts,
-                   const uint8_t *__restrict__ submask, uint32_t *__restrict__ counter,
+                   const uint32_t *__restrict__ crw, uint32_t *__restrict__ counter,
                    uint32_t *__restrict__ arrive, float4 *__restrict__ partials,
                    const float4 *__restrict__ pix, const double *__restrict__ tile_dir,
                    const RenderDesc *__restrict__ D, float4 *__restrict__ ray_state,
@@ -633,7 +626,7 @@ k_render_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *__
         const uint32_t lo = rg.x + (uint32_t)seg * kSeg;
         const uint32_t hi = min(rg.y, lo + kSeg);
         CamAcc a = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
-        const bool stopped = cam_walk_rs(P, rec, ids, submask, sub, sbx, sby, lo, hi, rg.x, poses,
+        const bool stopped = cam_walk_rs(P, rec, ids, crw, sub, sbx, sby, lo, hi, rg.x, poses,
                                          nrows, sb, dh, dl, dd, d, s_e, s_pos[wib], s_lanes[wib],
                                          a, no_ray);
         if (ti.x > 1) {
@@ -671,7 +664,7 @@ k_render_camera_rs(CamRender P, const GRec *__restrict__ rec, const uint32_t *__
                 }
                 if (__any_sync(0xffffffffu, redo)) {
                     const uint32_t l0 = rg.x + sgi * kSeg;
-                    cam_walk_rs(P, rec, ids, submask, sub, sbx, sby, l0, min(rg.y, l0 + kSeg),
+                    cam_walk_rs(P, rec, ids, crw, sub, sbx, sby, l0, min(rg.y, l0 + kSeg),
                                 rg.x, poses, nrows, sb, dh, dl, dd, d, s_e, s_pos[wib],
                                 s_lanes[wib], a, !redo);
                 }
@@ -712,7 +705,7 @@ sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
-    if (s == SG_OK && fr.submask.bytes < (size_t)(K > 0 ? K : 1)) {
+    if (s == SG_OK && fr.submask.bytes < 4 * (size_t)(K > 0 ? K : 1)) {
         set_error("internal: sub-block masks of the camera list missing");
         s = SG_ERR_INVALID;
     }
@@ -737,7 +730,7 @@ sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr
     if (grid < 1) grid = 1;
     k_render_camera_rs<kSegLen><<<(unsigned)grid, 32 * kCamWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
-        (const uint8_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
+        (const uint32_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix,
         cam.d_tile_dir, (const RenderDesc *)fr.desc.p, saved_state(fr),
         saved_feat(fr), saved_contrib(fr));
     SG_LAUNCHED();

@@ -151,19 +151,6 @@ __device__ __forceinline__ void fwd_composite(const CamRender &P, float4 (*s)[kF
     }
 }
 
-// The lanes of 8x4 sub-block `sub` whose pixel centres lie in an entry's
-// box, from the entry's word of tile columns and rows in the box (bits 0-15:
-// the tile's columns, 16-31: its rows; written with the tile ranges by the
-// same float comparisons as the per-ray test): the sub-block's 8 column bits
-// in every byte, a byte kept where the sub-block's row is in the box (the
-// multiply by 0x00204081 moves bit r of the 4 row bits to bit 8 r).
-__device__ __forceinline__ uint32_t word_lanes(uint32_t cr, int sub)
-{
-    const uint32_t cols = (cr >> (8 * (sub & 1))) & 0xffu;
-    const uint32_t rows = (cr >> (16 + 4 * (sub >> 1))) & 0xfu;
-    return (cols * 0x01010101u) & ((((rows * 0x00204081u) & 0x01010101u)) * 0xffu);
-}
-
 // Composite list entries [lo, hi) of a tile that can reach sub-block `sub`
 // into the lane's accumulator.  Lanes whose ray is done take part in the
 // staging and keep their state; only entries whose box holds a live ray are

@@ -585,27 +585,25 @@ sg_status bin_pairs(const uint32_t *d_ids, const uint32_t *d_offsets, const uint
     return SG_OK;
 }
 
-// Per-tile [start, end) of the sorted pairs, and for camera lists a per-pair
-// mask of the tile's pixel columns and rows whose centres lie inside the
-// Gaussian's extent box, by the same float comparisons as the per-ray test.
-// kMask = 1 writes it as one byte per pair: which of the tile's eight 8x4
-// sub-blocks hold such a pixel (bit w: columns 8 (w & 1) .., rows 4 (w >> 1)
-// ..); kMask = 2 as a 32-bit word (bits 0-15 the columns, 16-31 the rows),
-// from which a warp also gets its sub-block's lane mask.  The compositing
-// warps scan these contiguous masks and never stage an entry that no pixel
-// of their sub-block can see.  After a look-back wait gave up (*err) the
-// pairs may hold stale tile ids: every range stays empty (zeroed before the
-// launch).
+// Per-tile [start, end) of the sorted pairs, and for camera lists (kMask)
+// a per-pair 32-bit word of the tile's pixel columns (bits 0-15) and rows
+// (bits 16-31) whose centres lie inside the Gaussian's extent box, by the
+// same float comparisons as the per-ray test.  A compositing warp gets from
+// it, in a few integer operations, whether the entry reaches its 8x4
+// sub-block and which of its lanes the box holds, so it never stages an
+// entry that no live ray of its sub-block can see and loads no box.  After a
+// look-back wait gave up (*err) the pairs may hold stale tile ids: every
+// range stays empty (zeroed before the launch).
 // Each thread takes kRangePer consecutive pairs, their loads (keys, ids,
 // then the boxes by id) issued together, so that a thread waits for two
 // rounds of loads for all of them.
 constexpr int kRangePer = 4;
 
-template <int kMask>
+template <bool kMask>
 __global__ void __launch_bounds__(256)
 k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
          uint2 *__restrict__ ranges, const uint32_t *__restrict__ ids,
-         const float4 *__restrict__ rects, int ntx, void *__restrict__ mask,
+         const float4 *__restrict__ rects, int ntx, uint32_t *__restrict__ mask,
          const uint32_t *__restrict__ err)
 {
     const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kRangePer;
@@ -644,39 +642,24 @@ k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ d_K,
                 cols |= (uint32_t)(x >= rc[j].x && x <= rc[j].y) << c;
                 rows |= (uint32_t)(y >= rc[j].z && y <= rc[j].w) << c;
             }
-            if (kMask == 2) {
-                ((uint32_t *)mask)[i] = cols | (rows << 16);
-            } else {
-                uint32_t m = 0;
-#pragma unroll
-                for (int w = 0; w < 8; ++w) {
-                    const bool cx = ((cols >> (8 * (w & 1))) & 0xffu) != 0u;
-                    const bool cy = ((rows >> (4 * (w >> 1))) & 0xfu) != 0u;
-                    m |= (uint32_t)(cx && cy) << w;
-                }
-                ((uint8_t *)mask)[i] = (uint8_t)m;
-            }
+            mask[i] = cols | (rows << 16);
         }
     }
 }
 
 sg_status tile_ranges(const uint32_t *d_keys, const uint32_t *d_K, int64_t K_max, uint2 *d_ranges,
                       int64_t ntiles, cudaStream_t st, const uint32_t *d_err,
-                      const uint32_t *d_ids, const float4 *d_rects, int ntx, uint8_t *d_mask,
-                      uint32_t *d_words)
+                      const uint32_t *d_ids, const float4 *d_rects, int ntx, uint32_t *d_words)
 {
     SG_CUDA(cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * ntiles, st));
     if (K_max == 0) return SG_OK;
     const unsigned grid = (unsigned)((K_max + 256 * kRangePer - 1) / (256 * kRangePer));
     if (d_words)
-        k_ranges<2><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rects, ntx, d_words,
-                                          d_err);
-    else if (d_mask)
-        k_ranges<1><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rects, ntx, d_mask,
-                                          d_err);
+        k_ranges<true><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, d_ids, d_rects, ntx, d_words,
+                                             d_err);
     else
-        k_ranges<0><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, nullptr, nullptr, 0, nullptr,
-                                          d_err);
+        k_ranges<false><<<grid, 256, 0, st>>>(d_keys, d_K, d_ranges, nullptr, nullptr, 0, nullptr,
+                                              d_err);
     SG_LAUNCHED();
     return SG_OK;
 }

@@ -468,7 +468,7 @@ def lidar_workload(torch, sg, syn, steps, warmup, kind="lidar", beam=0.0):
         pk = peaks()
         peak = sm_count() * FP32_LANES * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         ach = pairs * FLOP_PER_PAIR / (st[3] * 1e-3) / 1e12
-        out["roofline"] = {"kernel": "k_render_lidar", "bound": "alu", "achieved": ach,
+        out["roofline"] = {"kernel": "k_render_lidar_fwd", "bound": "alu", "achieved": ach,
                            "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                            "evaluated_pairs": pairs}
     return out

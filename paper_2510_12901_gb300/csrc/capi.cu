@@ -628,6 +628,8 @@ void sg_destroy_lidar(sg_lidar lidar)
     dev_free(L.d_items);
     dev_free(L.d_item_rays);
     dev_free(L.d_ray_e);
+    dev_free(L.d_item_ref);
+    dev_free(L.d_ray_tau);
     dev_free(L.d_tile_u);
     dev_free(L.d_tile_items);
     dev_free(L.d_item_ray_tab);

@@ -165,6 +165,11 @@ struct Lidar {
     double *d_tile_u = nullptr;     // [ntiles*3] tile reference sensor direction
     uint2 *d_tile_items = nullptr;  // [ntiles] (first item, number of items) of each tile
     LidarItemRays *d_item_ray_tab = nullptr;   // [n_items] factorised ray slots
+    // forward-only compositing (render_lidar_fwd.cu): per item and column
+    // slot the sensor-frame reference (cos az, sin az, tan el_r), double; per
+    // ray slot (tan el - tan el_r, 1 / cos el)
+    double *d_item_ref = nullptr;   // [n_items * kLidarColsMax * 3]
+    float2 *d_ray_tau = nullptr;    // [n_items * 32]
 };
 
 // ------------------------------------------------------------------ records
@@ -380,8 +385,8 @@ sg_status project_lidar(const Scene &sc, const Lidar &L, const sg_render_opts &o
 // render.cu
 sg_status render_camera(const Camera &cam, const sg_render_opts &o, Frame &fr, cudaStream_t st);
 // render_fwd.cu: the compositing of frames that keep no backward state
-// (two rays per lane, tangent-plane rays); render_camera dispatches to it
-// when camera_forward_only holds.
+// (tangent-plane rays); render_camera dispatches to it when
+// camera_forward_only holds.
 bool camera_forward_only(const Camera &cam, const Frame &fr);
 sg_status render_camera_fwd(const Camera &cam, const sg_render_opts &o, Frame &fr,
                             cudaStream_t st);
@@ -394,6 +399,12 @@ sg_status launch_work_items(Frame &fr, const WorkSize &ws, const LidarItem *unit
 sg_status render_camera_rs(const Camera &cam, const sg_render_opts &o, Frame &fr,
                            cudaStream_t st);
 sg_status render_lidar(const Lidar &L, const sg_render_opts &o, Frame &fr, cudaStream_t st);
+// render_lidar_fwd.cu: the LiDAR compositing of frames that keep no backward
+// state (beam groups, one ray parameter); render_lidar dispatches to it when
+// lidar_forward_only holds.
+bool lidar_forward_only(const Frame &fr);
+sg_status render_lidar_fwd(const Lidar &L, const sg_render_opts &o, Frame &fr,
+                           cudaStream_t st);
 
 // sensors.cu
 sg_status build_camera(Camera &cam);

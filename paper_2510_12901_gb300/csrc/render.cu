@@ -994,6 +994,7 @@ static int lidar_blocks_per_sm()
 
 sg_status render_lidar(const Lidar &L, const sg_render_opts &o, Frame &fr, cudaStream_t st)
 {
+    if (lidar_forward_only(fr)) return render_lidar_fwd(L, o, fr, st);
     const LidRender P = lidar_render_params(L, o);
     if (L.n_items == 0) return SG_OK;
     const int64_t K = fr.n_pairs;

@@ -328,6 +328,8 @@ sg_status build_lidar(Lidar &L)
     std::vector<uint32_t> rays;
     std::vector<float4> ray_e;
     std::vector<double> item_u;
+    std::vector<double> item_ref;     // per item and column slot: cos az, sin az, tan el_r
+    std::vector<float2> ray_tau;      // per ray slot: tan el - tan el_r, 1 / cos el
     const double d2r = M_PI / 180.0;
     for (int e = 0; e < nphi; ++e) {
         const std::vector<int> &bs = tile_beams[e];
@@ -359,6 +361,23 @@ sg_status build_lidar(Lidar &L)
                     item_u.push_back(u0);
                     item_u.push_back(u1);
                     item_u.push_back(u2);
+                    // the forward-only kernel's rays: d / cos el = h_c + tan el z_c
+                    // around tan el_r, the middle of the item's range of tan el
+                    double t_lo = 1e300, t_hi = -1e300;
+                    for (size_t k = k0; k < k1; ++k) {
+                        const double t = tan((double)L.elev[rr[k] / (uint32_t)nc] * d2r);
+                        t_lo = std::min(t_lo, t);
+                        t_hi = std::max(t_hi, t);
+                    }
+                    const double t_ref = 0.5 * (t_lo + t_hi);
+                    for (int sl = 0; sl < kLidarColsMax; ++sl) {
+                        // column azimuth in double, as the ray definition has it
+                        const double azc =
+                            ((double)L.az0 + (g0 + sl + 0.5) * 360.0 / nc) * d2r;
+                        item_ref.push_back(sl <= g1 - g0 ? cos(azc) : 0.0);
+                        item_ref.push_back(sl <= g1 - g0 ? sin(azc) : 0.0);
+                        item_ref.push_back(sl <= g1 - g0 ? t_ref : 0.0);
+                    }
                     for (size_t k = k0; k < k0 + 32; ++k) {
                         if (k < k1) {
                             uint32_t ray = rr[k];
@@ -368,9 +387,12 @@ sg_status build_lidar(Lidar &L)
                             rays.push_back(ray);
                             ray_e.push_back(make_float4((float)(w0 - u0), (float)(w1 - u1),
                                                         (float)(w2 - u2), 1.0f));
+                            ray_tau.push_back(make_float2((float)(tan(el) - t_ref),
+                                                          (float)(1.0 / cos(el))));
                         } else {
                             rays.push_back(0xffffffffu);
                             ray_e.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+                            ray_tau.push_back(make_float2(0.f, 1.f));
                         }
                     }
                 }
@@ -432,6 +454,8 @@ sg_status build_lidar(Lidar &L)
     SG_ALLOC_COPY(L.d_tile_u, item_u);
     SG_ALLOC_COPY(L.d_tile_items, tile_items);
     SG_ALLOC_COPY(L.d_item_ray_tab, item_rays);
+    SG_ALLOC_COPY(L.d_item_ref, item_ref);
+    SG_ALLOC_COPY(L.d_ray_tau, ray_tau);
 #undef SG_ALLOC_COPY
     return SG_OK;
 }

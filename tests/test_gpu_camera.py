@@ -29,7 +29,7 @@ def sg():
 
 # Frames that keep the state for a backward run k_render_camera; frames that
 # keep none (serving, the benchmark) run k_render_camera_fwd, a different
-# kernel (two rays per lane, tangent-plane rays).  The parity tests run both.
+# kernel (tangent-plane rays).  The parity tests run both.
 MODES = ["saved", "forward"]
 
 

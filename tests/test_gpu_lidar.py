@@ -22,11 +22,21 @@ def sg():
     return simgut
 
 
-def gpu_render(sg, sc, L, opts=None, scene=None, lidar=None):
+# Frames that keep the state for a backward run k_render_lidar; frames that
+# keep none (serving, the benchmark) run k_render_lidar_fwd, a different
+# kernel (beam groups, one ray parameter per column).  The parity tests run
+# both.
+MODES = ["saved", "forward"]
+
+
+def gpu_render(sg, sc, L, opts=None, scene=None, lidar=None, mode="saved"):
     import torch
     S = scene or sg.Scene(sc)
     Ld = lidar or sg.Lidar(L)
-    out = sg.render_lidar(S, Ld, L.col_c2w, opts)
+    fr = sg.Frame()
+    if mode == "forward":
+        sg.sg_frame_set_backward_state(fr.handle, 0)
+    out = sg.render_lidar(S, Ld, L.col_c2w, opts, frame=fr)
     torch.cuda.synchronize()
     res = {k: out[k].cpu().numpy().reshape(-1) for k in ("range", "intensity", "drop", "alpha")}
     res.update(frame=out["frame"], scene=S, lidar=Ld)
@@ -84,15 +94,16 @@ def check_lists(sg, fr, sc, P32, mism, nth, nphi, O32, label):
     assert K - o_count.sum() == (g_count - o_count)[mism].sum(), label
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("kind", ["lidar", "lidar_sh"])
-def test_toy_sweep_every_ray_and_list(sg, O32, O64, kind):
+def test_toy_sweep_every_ray_and_list(sg, O32, O64, kind, mode):
     """Every ray of a 128 x 256 sweep; kind lidar_sh: degree-3 SH^l
     features evaluated per Gaussian from the origin of its column pose."""
     sc, L = toy(kind=kind)
-    g = gpu_render(sg, sc, L)
+    g = gpu_render(sg, sc, L, mode=mode)
     orc = O64.render_lidar(sc, L)
     info = par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
-                                  label="toy")
+                                  label=f"toy-{mode}")
     assert (orc["n_contrib"] > 0).sum() > 1000, info
     P32, mism, key, nth, nphi = check_projection(sg, g["frame"], sc, L, O32, O64, "toy")
     check_lists(sg, g["frame"], sc, P32, mism, nth, nphi, O32, "toy")
@@ -144,18 +155,19 @@ def test_misaligned_poses_are_refused(sg):
     assert e.value.status == -1 and "aligned" in str(e.value)
 
 
-def test_ragged_sensor_and_empty_scene(sg, O64):
+@pytest.mark.parametrize("mode", MODES)
+def test_ragged_sensor_and_empty_scene(sg, O64, mode):
     sc, _ = toy(800, seed=4)
     L = syn.street_lidar(n_beams=64, n_cols=333)    # columns not divisible by N_theta
-    g = gpu_render(sg, sc, L)
+    g = gpu_render(sg, sc, L, mode=mode)
     orc = O64.render_lidar(sc, L)
     par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
-                           label="ragged")
-    e = gpu_render(sg, sc.subset(np.zeros(0, np.int64)), L)
+                           label=f"ragged-{mode}")
+    e = gpu_render(sg, sc.subset(np.zeros(0, np.int64)), L, mode=mode)
     assert not e["alpha"].any() and np.all(e["drop"] == 0.5) and not e["range"].any()
 
 
-def test_forward_only_frame_renders_the_same(sg):
+def test_forward_only_frame_agrees_and_refuses_the_backward(sg):
     import torch
     sc, L = toy(1500, seed=6)
     a = gpu_render(sg, sc, L)
@@ -163,8 +175,26 @@ def test_forward_only_frame_renders_the_same(sg):
     sg.sg_frame_set_backward_state(fr.handle, 0)
     b = sg.render_lidar(a["scene"], a["lidar"], L.col_c2w, frame=fr)
     torch.cuda.synchronize()
+    # another kernel and another ray parameterisation: equal up to rounding
+    # away from threshold decisions (each is checked against the oracle above)
     for k in ("range", "intensity", "drop", "alpha"):
-        assert np.array_equal(a[k], b[k].cpu().numpy().reshape(-1)), k
+        d = np.abs(a[k] - b[k].cpu().numpy().reshape(-1))
+        assert np.quantile(d, 0.99) <= 1e-5 and d.max() <= 0.05, (k, d.max())
+    # a second forward-only render is bit-identical
+    c = sg.render_lidar(a["scene"], a["lidar"], L.col_c2w, frame=fr)
+    torch.cuda.synchronize()
+    for k in ("range", "intensity", "drop", "alpha"):
+        assert torch.equal(b[k], c[k]), k
+    n = L.n_beams * L.n_cols
+    grads = {k: torch.zeros(s, device="cuda") for k, s in
+             (("m", (sc.n, 3)), ("l", (sc.n, 3)), ("q", (sc.n, 4)), ("o", (sc.n,)),
+              ("f", (sc.n, sc.features.shape[1])))}
+    gs = sg.sg_grads(*[t.data_ptr() for t in grads.values()])
+    up = torch.zeros(n, device="cuda")
+    with pytest.raises(sg.SimgutError) as e:
+        sg.sg_backward_lidar(a["scene"].handle, fr.handle, up.data_ptr(), None, None, None, gs,
+                             torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == -1 and "kept no state" in str(e.value)
 
 
 def test_host_output_path_matches_device_path(sg):
@@ -182,15 +212,17 @@ def test_host_output_path_matches_device_path(sg):
         assert np.array_equal(o, g[k]), k
 
 
-@pytest.mark.parametrize("beams,kind", [(128, "lidar"), (64, "lidar"), (128, "lidar_sh")])
-def test_full_sweep_sampled_parity(sg, O32, O64, beams, kind):
+@pytest.mark.parametrize("beams,kind,mode", [(128, "lidar", "saved"), (64, "lidar", "saved"),
+                                             (128, "lidar_sh", "saved"),
+                                             (128, "lidar", "forward"), (64, "lidar", "forward")])
+def test_full_sweep_sampled_parity(sg, O32, O64, beams, kind, mode):
     """2M Gaussians, 128 beams x 2048 columns (or 64 x 1024, where a tile of
     32 rays spans 8 columns and is walked by two work items), per-column
     poses over 0.1 s; tile lists of thousands of entries, split in segments.
     lidar_sh: degree-3 SH^l features."""
     sc = syn.street_scene(2_000_000, seed=10, kind=kind)
     L = syn.street_lidar() if beams == 128 else syn.street_lidar(n_beams=64, n_cols=1024)
-    g = gpu_render(sg, sc, L)
+    g = gpu_render(sg, sc, L, mode=mode)
     lens = np.diff(g["frame"].field(sg.FIELD_RANGES, np.uint32, 2).astype(np.int64), axis=1)
     assert lens.max() > 8 * 256
     rng = np.random.default_rng(0)
@@ -208,12 +240,13 @@ def test_full_sweep_sampled_parity(sg, O32, O64, beams, kind):
     # items per tile, larger per-column motion)
     info = par.compare_lidar_rays(g["range"][rays], g["intensity"][rays], g["drop"][rays],
                                   g["alpha"][rays], orc, max_excluded=0.015,
-                                  label=f"full-{beams}-{kind}", also_excluded=seen)
+                                  label=f"full-{beams}-{kind}-{mode}", also_excluded=seen)
     assert (orc["n_contrib"] > 0).mean() > 0.3, info
     check_lists(sg, g["frame"], sc, P32, mism, nth, nphi, O32, f"full-{beams}-{kind}")
 
 
-def test_gaussians_straddling_the_azimuth_seam(sg, O32, O64):
+@pytest.mark.parametrize("mode", MODES)
+def test_gaussians_straddling_the_azimuth_seam(sg, O32, O64, mode):
     """Gaussians right behind the sensor (azimuth +-180 deg, where column 0
     and the last column meet): the tile range wraps, the culling query splits
     in two, and the rays on both sides of the seam see the same Gaussian."""
@@ -228,10 +261,10 @@ def test_gaussians_straddling_the_azimuth_seam(sg, O32, O64):
                             oz + rng.uniform(-1.5, 0.5, n)], 1).astype(np.float32)
     sc.log_scales[:] = np.log(rng.uniform(0.05, 0.3, (n, 3))).astype(np.float32)
     sc.opacity[:] = rng.uniform(0.3, 0.95, n).astype(np.float32)
-    g = gpu_render(sg, sc, L)
+    g = gpu_render(sg, sc, L, mode=mode)
     orc = O64.render_lidar(sc, L)
     par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
-                           max_excluded=0.02, label="seam")
+                           max_excluded=0.02, label=f"seam-{mode}")
     P, _ = O64.project_lidar(sc, L)
     wraps = (P["valid"] == 1) & ((P["tiles"][:, 0] < 0) | (P["tiles"][:, 1] >= _n_theta(O64, L)))
     assert wraps.sum() > 20                       # the case is exercised
@@ -243,17 +276,18 @@ def _n_theta(O, L):
     return O.lidar_setup(L)["n_theta"]
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("delta", [0.003, 0.02])
-def test_beam_divergence_every_ray(sg, O64, delta):
+def test_beam_divergence_every_ray(sg, O64, delta, mode):
     """Eq. 6 smoothing (covariance widened across the beam by (delta r)^2,
     opacity kept): every ray of a 128 x 256 sweep against the oracle with
     the same delta, for raw and SH^l features."""
     for kind in ("lidar", "lidar_sh"):
         sc, L = toy(kind=kind, seed=3)
-        g = gpu_render(sg, sc, L, sg.sg_default_opts(beam_divergence=delta))
+        g = gpu_render(sg, sc, L, sg.sg_default_opts(beam_divergence=delta), mode=mode)
         orc = O64.render_lidar(sc, L, O64.opts(beam_divergence=delta))
         info = par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
-                                      max_excluded=0.02, label=f"beam-{delta}-{kind}")
+                                      max_excluded=0.02, label=f"beam-{delta}-{kind}-{mode}")
         plain = O64.render_lidar(sc, L)
         # the filter changes the picture
         assert np.abs(orc["alpha"] - plain["alpha"]).max() > 1e-2, info

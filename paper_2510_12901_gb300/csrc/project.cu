@@ -577,9 +577,14 @@ __device__ __forceinline__ void cholesky3(const float C[9], float Lc[9])
 // kSH: the scene carries SH^l features; kBeam: beam divergence on (the UT
 // runs over the smoothed covariance's Cholesky columns, and the record
 // holds its eigen-frame: M = diag(lam)^-1/2 Q^T, the form the compositing
-// takes).  Templates, so that the plain path keeps its registers.
+// takes).  Templates, so that the plain path keeps its registers.  Four
+// blocks per SM (64 registers, a few bytes spilled): the kernel waits on
+// dependent pose loads and atan2f / asinf chains, and 32 warps per SM hide
+// more of that than 24 at 76 registers (street sweep, 2M Gaussians: 0.266 ->
+// 0.253 ms; with SH^l features 0.400 -> 0.337 ms; beam divergence 0.435 ->
+// 0.407 ms).
 template <bool kSH, bool kBeam>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_project_lidar(const float *__restrict__ planes, int64_t pitch, int64_t n, int sh_degree,
                 ActorParams A, LidParams Lp, const RenderDesc *__restrict__ D, UTParams U,
                 int cull, GRec *__restrict__ rec, float4 *__restrict__ rect_out,

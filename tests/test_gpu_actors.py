@@ -51,13 +51,14 @@ def test_camera_with_actors_every_pixel(sg, O32, O64, which):
     check_projection(sg, g["frame"], sc, cam, O32, O64, f"actors-{which}")
 
 
-def test_lidar_with_actors_every_ray(sg, O64):
+@pytest.mark.parametrize("mode", ["saved", "forward"])
+def test_lidar_with_actors_every_ray(sg, O64, mode):
     sc = _actor_scene(20000, seed=9, kind="lidar_sh")
     L = syn.street_lidar(n_cols=256, start_xyz=(20.0, 0.0, 1.8))
-    g = lid_render(sg, sc, L)
+    g = lid_render(sg, sc, L, mode=mode)
     orc = O64.render_lidar(sc, L)
     info = par.compare_lidar_rays(g["range"], g["intensity"], g["drop"], g["alpha"], orc,
-                                  max_excluded=0.02, label="actors-lidar")
+                                  max_excluded=0.02, label=f"actors-lidar-{mode}")
     assert (orc["alpha"] > 0).mean() > 0.2, info
 
 

@@ -56,6 +56,16 @@ def test_invalid_arguments_are_rejected_before_any_cuda_work(sg):
         sg.sg_create_lidar([0.0, 1.0], 0, -180.0, 32, 16, 1600, 8)
     with pytest.raises(sg.SimgutError):
         sg.sg_create_lidar([0.0, 95.0], 64, -180.0, 32, 16, 1600, 8)
+    # sensor limits, checked on the host before any device allocation
+    with pytest.raises(sg.SimgutError):
+        sg.sg_create_camera(0, 16385, 64, 60, 60, 32, 32, [0, 0, 0, 0])
+    assert "size" in sg.sg_last_error()
+    with pytest.raises(sg.SimgutError):       # Proc. 1 needs an elevation range
+        sg.sg_create_lidar([5.0, 5.0, 5.0], 64, -180.0, 32, 16, 1600, 8)
+    assert "equal" in sg.sg_last_error()
+    with pytest.raises(sg.SimgutError):       # 64 x 65535 rays at one ray per tile
+        sg.sg_create_lidar(np.linspace(-20.0, 10.0, 64), 65535, -180.0, 1, 1, 1600, 8)
+    assert "65535" in sg.sg_last_error()
     lib = sg.load()
     h = C.c_void_p()
     assert lib.sg_create_scene(None, None, C.byref(h)) == -1

@@ -46,7 +46,14 @@ constexpr int kFwdBlocks = 7;
 #endif
 constexpr int kFwdPer = SG_FWD_PER_LANE;
 constexpr int kFwdWin = 32 * kFwdPer;
-constexpr int kFwdStage = 64;   // staged entries held in shared memory at once
+constexpr int kFwdStage = 64;
+// Segment length of this kernel's work items (frames that keep no backward
+// state need not match the segments of a backward).  Measured on the street
+// views (compositing alone fisheye / pinhole, two-view step): 128 entries
+// 0.390 / 0.562 ms, 3102 Mrays/s; 256 0.363 / 0.513 ms, 3310; 384 0.367 /
+// 0.503 ms, 3364; 512 0.381 / 0.508 ms, 3384.  Longer runs mean fewer
+// merges; shorter ones split the densest tiles (the fisheye's) finer.
+constexpr uint32_t kFwdSeg = 384;   // staged entries held in shared memory at once
 
 // The tile's reference frame in world coordinates: d_T = dh + dl (from the
 // double direction, as cam_tile_ref) and e_1, e_2 rotated in float.
@@ -360,7 +367,7 @@ static int fwd_blocks_per_sm()
     static int cached = 0;
     if (!cached) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_camera_fwd<kSegLen>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_camera_fwd<kFwdSeg>,
                                                           32 * kFwdWarps, 0) != cudaSuccess ||
             nb < 1)
             nb = 4;
@@ -380,7 +387,7 @@ sg_status render_camera_fwd(const Camera &cam, const sg_render_opts &o, Frame &f
     const CamRender P = cam_render_params(cam, o);
     const int nt = cam.ntx * cam.nty;
     const int64_t K = fr.n_pairs;
-    const WorkSize ws = work_size(nt, K, kSegLen, 8);
+    const WorkSize ws = work_size(nt, K, kFwdSeg, 8);
     sg_status s = ensure(fr.order, sizeof(uint32_t) * (nt > 0 ? nt : 1));
     if (s == SG_OK) s = ensure(fr.camwork, ws.work_bytes);
     if (s == SG_OK) s = ensure(fr.partials, ws.partial_bytes);
@@ -395,7 +402,7 @@ sg_status render_camera_fwd(const Camera &cam, const sg_render_opts &o, Frame &f
     uint32_t *arrive = (uint32_t *)(cw + ws.info_bytes + ws.off_bytes + ws.items_bytes);
     const uint32_t *counts = (const uint32_t *)fr.scalars.p + 4;    // [0] items [1] slots
     uint32_t *counter = (uint32_t *)fr.scalars.p + 2;
-    if ((s = launch_work_items(fr, ws, nullptr, nt, 8, kSegLen, st)) != SG_OK) return s;
+    if ((s = launch_work_items(fr, ws, nullptr, nt, 8, kFwdSeg, st)) != SG_OK) return s;
     const uint32_t *ids = (const uint32_t *)fr.pvals[fr.pair_buf].p;
     int dev = 0, sms = 0;
     SG_CUDA(cudaGetDevice(&dev));
@@ -404,7 +411,7 @@ sg_status render_camera_fwd(const Camera &cam, const sg_render_opts &o, Frame &f
     int64_t grid = (int64_t)sms * fwd_blocks_per_sm();
     grid = grid < cap ? grid : cap;
     if (grid < 1) grid = 1;
-    k_render_camera_fwd<kSegLen><<<(unsigned)grid, 32 * kFwdWarps, 0, st>>>(
+    k_render_camera_fwd<kFwdSeg><<<(unsigned)grid, 32 * kFwdWarps, 0, st>>>(
         P, (const GRec *)fr.rec.p, ids, (const uint2 *)fr.ranges.p, items, tile_info, counts,
         (const uint32_t *)fr.submask.p, counter, arrive, (float4 *)fr.partials.p, cam.d_pix2,
         cam.d_tile_dir, cam.d_tile_basis, (const RenderDesc *)fr.desc.p);

@@ -58,6 +58,7 @@ struct LfShared {
     float ref[kLidarColsMax][12];      // per column slot: d_r (hi, lo), z_c, o_c
 };
 
+static_assert(kLidarColsMax == 4, "the slot swizzle below assumes four column slots");
 __device__ __forceinline__ int lf_qi(int j, int sl) { return 4 * j + (sl ^ ((j >> 1) & 3)); }
 __device__ __forceinline__ int lf_ti(int j, int sl) { return 4 * j + (sl ^ ((j >> 2) & 3)); }
 
